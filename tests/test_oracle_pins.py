@@ -1,0 +1,524 @@
+"""Pins for the FP64 CPU oracle: each test checks the oracle against something other than
+itself (a closed form, an independent numeric method, an invariant, the paper's worked
+example) so that a plausible mistake anywhere in it fails at least one test. CPU only."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2601_20429_gb300 import scenes
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+Y00 = 0.5 / math.sqrt(math.pi)
+
+
+def qmul(a, b):
+    aw, ax, ay, az = a
+    bw, bx, by, bz = b
+    return np.array([aw * bw - ax * bx - ay * by - az * bz, aw * bx + ax * bw + ay * bz - az * by,
+                     aw * by - ax * bz + ay * bw + az * bx, aw * bz + ax * by - ay * bx + az * bw])
+
+
+def rotate(q, v):
+    """Hamilton sandwich q v q*, an independent way to apply a quaternion rotation."""
+    q = np.asarray(q, float) / np.linalg.norm(q)
+    qc = q * np.array([1, -1, -1, -1])
+    return qmul(qmul(q, np.concatenate([[0.0], v])), qc)[1:]
+
+
+def make_scene(means, scales, quats, opac, colors=None, sh=None, sh_degree=0):
+    means = np.atleast_2d(np.asarray(means, float))
+    n = means.shape[0]
+    log_scales = np.log(np.broadcast_to(np.asarray(scales, float), (n, 3)))
+    quats = np.broadcast_to(np.asarray(quats, float), (n, 4))
+    o = np.broadcast_to(np.asarray(opac, float), (n,))
+    logits = np.log(o) - np.log1p(-o)
+    if sh is None:
+        colors = np.broadcast_to(np.asarray(colors, float), (n, 3))
+        sh = ((colors - 0.5) / Y00).reshape(n, 1, 3)
+    return O.Scene(means, log_scales, quats, logits, sh, sh_degree)
+
+
+def one_ray(o, d, tn=0.0, tf=math.inf):
+    return (np.array([o], float), np.array([d], float), np.array([tn]), np.array([tf]))
+
+
+# ---------------------------------------------------------------- closed forms
+
+
+@pytest.mark.parametrize("b", [0.0, 0.03, 0.11])
+def test_single_isotropic_gaussian(b):
+    sigma, o, c = 0.07, 0.8, np.array([0.2, 0.5, 0.9])
+    S = make_scene([[0, 0, 0]], sigma, [0.3, -0.5, 0.7, 0.1], o, c)
+    t, d2, alpha = S.response(0, [b, 0, -3], [0, 0, 1])
+    assert t == pytest.approx(3.0, abs=1e-12)
+    assert d2 == pytest.approx(b * b / sigma ** 2, rel=1e-12, abs=1e-14)
+    expect_alpha = o * math.exp(-0.5 * b * b / sigma ** 2)
+    assert alpha == pytest.approx(expect_alpha, rel=1e-12)
+    r = S.render(one_ray([b, 0, -3], [0, 0, 1]))
+    if expect_alpha >= 0.01:
+        np.testing.assert_allclose(r["out"][0, :3], expect_alpha * c, rtol=1e-12)
+        assert r["out"][0, 3] == pytest.approx(1 - expect_alpha, rel=1e-12)
+        assert r["n_blend"][0] == 1
+    else:
+        assert r["n_blend"][0] == 0
+
+
+def test_hit_boundary_is_alpha_min():
+    sigma, o = 0.05, 0.6
+    S = make_scene([[0, 0, 0]], sigma, [1, 0, 0, 0], o, [1, 1, 1])
+    b_star = sigma * math.sqrt(2 * math.log(o / 0.01))
+    inside = S.render(one_ray([b_star * (1 - 1e-9), 0, -3], [0, 0, 1]))
+    outside = S.render(one_ray([b_star * (1 + 1e-9), 0, -3], [0, 0, 1]))
+    assert inside["n_blend"][0] == 1 and outside["n_blend"][0] == 0
+    assert inside["out"][0, 0] == pytest.approx(0.01, rel=1e-6)
+
+
+def test_rotated_anisotropic_axis_convention():
+    """45 degrees about +z turns local x to (1,1,0)/sqrt2; an offset along that direction
+    must be measured against s_x (the opposite rotation convention would give s_y)."""
+    sx, sy, sz = 0.3, 0.1, 0.2
+    h = math.radians(22.5)
+    q = [math.cos(h), 0, 0, math.sin(h)]
+    S = make_scene([[0.1, 0.2, 0.3]], [sx, sy, sz], q, 0.9, [1, 1, 1])
+    b = 0.05
+    off = b * np.array([1, 1, 0]) / math.sqrt(2)
+    t, d2, _ = S.response(0, np.array([0.1, 0.2, -2.0]) + off, [0, 0, 1])
+    assert d2 == pytest.approx(b * b / sx ** 2, rel=1e-12)
+    assert t == pytest.approx(2.3, rel=1e-12)
+
+
+def test_t_alpha_is_the_minimiser_along_an_oblique_ray():
+    """Eq. t-max-resp against a numeric minimisation of the Mahalanobis distance along the
+    ray, with the local frame applied through the quaternion sandwich."""
+    from scipy.optimize import minimize_scalar
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        mu = rng.uniform(-1, 1, 3)
+        s = np.exp(rng.uniform(-3, -0.5, 3))
+        q = rng.standard_normal(4)
+        S = make_scene([mu], s, q, 0.7, [1, 1, 1])
+        ro = rng.uniform(-3, 3, 3)
+        rd = mu + rng.normal(0, 0.05, 3) - ro
+        rd /= np.linalg.norm(rd)
+        qc = np.asarray(q) / np.linalg.norm(q) * np.array([1, -1, -1, -1])
+
+        def m2(t):
+            v = rotate(qc, ro + t * rd - mu)     # world -> local is the inverse rotation
+            return float(np.sum((v / s) ** 2))
+
+        t0 = float(np.dot(mu - ro, rd))
+        res = minimize_scalar(m2, bracket=(t0 - 1, t0, t0 + 1), tol=1e-14)
+        t, d2, alpha = S.response(0, ro, rd)
+        assert t == pytest.approx(res.x, rel=1e-6, abs=1e-7)
+        assert d2 == pytest.approx(m2(t), rel=1e-9, abs=1e-12)
+        assert d2 <= res.fun + 1e-9 * max(1.0, res.fun)
+        assert alpha == pytest.approx(0.7 * math.exp(-0.5 * d2), rel=1e-12)
+
+
+# ---------------------------------------------------------------- unit-sphere view (Sec. IV-A)
+
+
+def test_unit_sphere_transform_matches_covariance_form():
+    g = scenes.tiny_scene(seed=11, n=200)
+    S = O.Scene.from_params(g)
+    ex = S.export()
+    rng = np.random.default_rng(1)
+    checked = 0
+    for i in np.nonzero(ex["valid"])[0][:60]:
+        for _ in range(3):
+            ro = rng.uniform(-3, 3, 3)
+            rd = g.means[i].astype(float) + rng.normal(0, 0.05, 3) - ro
+            rd /= np.linalg.norm(rd)
+            t, d2, alpha = S.response(i, ro, rd)
+            tu, D2 = S.unit_sphere(i, ro, rd)
+            assert tu == pytest.approx(t, rel=1e-10, abs=1e-12)
+            assert ex["kappa"][i] ** 2 * D2 == pytest.approx(d2, rel=1e-8, abs=1e-10)
+            if abs(D2 - 1) > 1e-9:
+                assert (D2 <= 1) == (alpha >= 0.01)
+            checked += 1
+    assert checked > 100
+
+
+def test_unit_sphere_t_invariant_under_rescaling():
+    """Scaling A (the sphere radius kappa) leaves t_alpha unchanged: shrink the opacity."""
+    g = scenes.tiny_scene(seed=12, n=50)
+    S1 = O.Scene.from_params(g)
+    g2 = g.copy()
+    g2.logits[:] = 4.0
+    S2 = O.Scene.from_params(g2)
+    rng = np.random.default_rng(2)
+    for i in range(50):
+        ro = rng.uniform(-3, 3, 3)
+        rd = rng.standard_normal(3)
+        t1, _ = S1.unit_sphere(i, ro, rd) if S1.export()["valid"][i] else (None, None)
+        if t1 is None:
+            continue
+        t2, _ = S2.unit_sphere(i, ro, rd)
+        assert t1 == pytest.approx(t2, rel=1e-10, abs=1e-12)
+
+
+def test_aabb_bounds_the_ellipsoid_tightly():
+    g = scenes.tiny_scene(seed=13, n=40)
+    S = O.Scene.from_params(g)
+    ex = S.export()
+    th = np.linspace(0, math.pi, 181)
+    ph = np.linspace(0, 2 * math.pi, 361)
+    TH, PH = np.meshgrid(th, ph)
+    U = np.stack([np.sin(TH) * np.cos(PH), np.sin(TH) * np.sin(PH), np.cos(TH)], -1).reshape(-1, 3)
+    for i in np.nonzero(ex["valid"])[0]:
+        q = g.quats[i].astype(float)
+        s = np.exp(g.log_scales[i].astype(float))
+        k = ex["kappa"][i]
+        pts = np.array([rotate(q, k * s * u) for u in U[::7]]) + g.means[i]
+        lo, hi = ex["aabb"][i, :3], ex["aabb"][i, 3:]
+        ext = hi - lo
+        assert np.all(pts >= lo - 1e-12) and np.all(pts <= hi + 1e-12)
+        assert np.all(pts.min(0) - lo < 2e-3 * ext) and np.all(hi - pts.max(0) < 2e-3 * ext)
+
+
+def test_rotation_matrix_matches_quaternion_sandwich():
+    g = scenes.tiny_scene(seed=14, n=30)
+    g.quats[:] = np.random.default_rng(3).standard_normal((30, 4)) * 3   # not unit length
+    S = O.Scene.from_params(g)
+    R = S.export()["R"]
+    rng = np.random.default_rng(4)
+    for i in range(30):
+        v = rng.standard_normal(3)
+        np.testing.assert_allclose(R[i] @ v, rotate(g.quats[i].astype(float), v), atol=1e-12)
+        np.testing.assert_allclose(R[i] @ R[i].T, np.eye(3), atol=1e-12)
+        assert np.linalg.det(R[i]) == pytest.approx(1.0, abs=1e-12)
+
+
+# ---------------------------------------------------------------- spherical harmonics
+
+
+def test_sh_basis_orthonormal_on_the_sphere():
+    zs, wz = np.polynomial.legendre.leggauss(24)
+    nph = 48
+    phis = 2 * math.pi * np.arange(nph) / nph
+    G = np.zeros((16, 16))
+    for z, w in zip(zs, wz):
+        r = math.sqrt(max(0.0, 1 - z * z))
+        for p in phis:
+            Y = O.sh_basis(3, [r * math.cos(p), r * math.sin(p), z])
+            G += np.outer(Y, Y) * w * (2 * math.pi / nph)
+    np.testing.assert_allclose(G, np.eye(16), atol=1e-12)
+
+
+def test_sh_addition_theorem_and_parity():
+    rng = np.random.default_rng(6)
+    for _ in range(50):
+        d = rng.standard_normal(3)
+        d /= np.linalg.norm(d)
+        Y = O.sh_basis(3, d)
+        Ym = O.sh_basis(3, -d)
+        for l in range(4):
+            band = Y[l * l:(l + 1) * (l + 1)]
+            assert np.sum(band ** 2) == pytest.approx((2 * l + 1) / (4 * math.pi), rel=1e-12)
+            np.testing.assert_allclose(Ym[l * l:(l + 1) * (l + 1)], (-1) ** l * band, atol=1e-14)
+
+
+def test_sh_colour_offset_and_clamp():
+    """c = max(0, sum_k Y_k f_k + 0.5): degree-0 coefficient (c-0.5)/Y00 reproduces c, and a
+    negative raw value clamps to 0."""
+    S = make_scene([[0, 0, 0]], 0.05, [1, 0, 0, 0], 0.5, [0.25, -0.3, 1.0])
+    r = S.render(one_ray([0, 0, -3], [0, 0, 1]))
+    np.testing.assert_allclose(r["out"][0, :3], 0.5 * np.array([0.25, 0.0, 1.0]), rtol=1e-12, atol=1e-15)
+
+
+# ---------------------------------------------------------------- compositing (Eq. volume-render)
+
+
+def test_three_gaussians_on_axis_in_depth_order():
+    # nearest Gaussian has the largest id, so sorting by depth matters
+    means = [[0, 0, 1.0], [0, 0, 0.5], [0, 0, 0.0]]
+    ops = [0.8, 0.3, 0.5]
+    cols = np.array([[0.9, 0.1, 0.1], [0.1, 0.9, 0.1], [0.1, 0.1, 0.9]])
+    S = make_scene(means, 0.05, [1, 0, 0, 0], ops, cols)
+    r = S.render(one_ray([0, 0, -3], [0, 0, 1]), ids_cap=4)
+    a1, a2, a3 = ops[2], ops[1], ops[0]
+    c1, c2, c3 = cols[2], cols[1], cols[0]
+    C = a1 * c1 + (1 - a1) * a2 * c2 + (1 - a1) * (1 - a2) * a3 * c3
+    np.testing.assert_allclose(r["out"][0, :3], C, rtol=1e-12)
+    assert r["out"][0, 3] == pytest.approx((1 - a1) * (1 - a2) * (1 - a3), rel=1e-12)
+    assert list(r["ids"][0, :3]) == [2, 1, 0]
+
+
+def test_early_termination_after_the_crossing_gaussian():
+    means = [[0, 0, 0.0], [0, 0, 0.5], [0, 0, 1.0]]
+    ops = [0.95, 0.995, 0.5]            # second alpha clamps to 0.99; T = 0.05*0.01 < 1e-3
+    cols = np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1]], float)
+    S = make_scene(means, 0.05, [1, 0, 0, 0], ops, cols)
+    r = S.render(one_ray([0, 0, -3], [0, 0, 1]))
+    assert r["n_blend"][0] == 2
+    np.testing.assert_allclose(r["out"][0, :3], [0.95, 0.05 * 0.99, 0.0], rtol=1e-12, atol=1e-15)
+    assert r["out"][0, 3] == pytest.approx(0.05 * 0.01, rel=1e-12)
+    r0 = S.render(one_ray([0, 0, -3], [0, 0, 1]), params=O.make_params(T_min=0.0))
+    assert r0["n_blend"][0] == 3
+
+
+def test_alpha_clamp():
+    S = make_scene([[0, 0, 0]], 0.05, [1, 0, 0, 0], 0.999, [1, 1, 1])
+    r = S.render(one_ray([0, 0, -3], [0, 0, 1]))
+    np.testing.assert_allclose(r["out"][0], [0.99, 0.99, 0.99, 0.01], rtol=1e-12)
+
+
+def test_equal_depth_ties_break_by_id():
+    cols = np.array([[1, 0, 0], [0, 0, 1]], float)
+    S = make_scene([[0, 0, 0], [0, 0, 0]], 0.05, [1, 0, 0, 0], [0.4, 0.7], cols)
+    r = S.render(one_ray([0, 0, -3], [0, 0, 1]), ids_cap=2)
+    assert list(r["ids"][0]) == [0, 1]
+    np.testing.assert_allclose(r["out"][0, :3], 0.4 * cols[0] + 0.6 * 0.7 * cols[1], rtol=1e-12)
+
+
+def test_background_and_near_far_window():
+    S = make_scene([[0, 0, 0], [0, 0, 2]], 0.05, [1, 0, 0, 0], [0.5, 0.5], [[1, 0, 0], [0, 1, 0]])
+    p = O.make_params(bg=(0.0, 0.0, 1.0))
+    r = S.render(one_ray([0, 0, -3], [0, 0, 1], tn=0.0, tf=4.0), params=p)
+    np.testing.assert_allclose(r["out"][0], [0.5, 0, 0.5, 0.5], rtol=1e-12, atol=1e-15)
+    r = S.render(one_ray([0, 0, -3], [0, 0, 1], tn=3.5, tf=math.inf), params=p)
+    np.testing.assert_allclose(r["out"][0], [0, 0.5, 0.5, 0.5], rtol=1e-12, atol=1e-15)
+
+
+def test_ert_error_bound_on_dense_scene():
+    g = scenes.tiny_scene(seed=0, n=20000)
+    cam = scenes.pinhole_camera(32, 32, (0.0, 0.0, -3.0), (0, 0, 0), 60.0)
+    S = O.Scene.from_params(g)
+    rays = O.camera_rays(cam)
+    a = S.render(rays)
+    b = S.render(rays, params=O.make_params(T_min=0.0))
+    Tstop = a["out"][:, 3]
+    diff = np.abs(a["out"][:, :3] - b["out"][:, :3]).max(1)
+    assert np.all(diff <= Tstop * 1.0 + 1e-12)
+    assert (a["n_blend"] < b["n_blend"]).sum() > 10
+
+
+# ---------------------------------------------------------------- round loop (Listing 1)
+
+
+@pytest.fixture(scope="module", params=["tiny", "dense"])
+def tiny_rounds(request):
+    if request.param == "tiny":
+        g, cam, _ = scenes.config_tiny()
+    else:   # enough depth complexity that most rays terminate early
+        g = scenes.tiny_scene(seed=0, n=20000)
+        cam = scenes.pinhole_camera(32, 32, (0.0, 0.0, -3.0), (0, 0, 0), 60.0)
+    S = O.Scene.from_params(g)
+    rays = O.camera_rays(cam)
+    ref = S.render(rays)
+    return S, rays, ref
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 8, 16, 32, 4096])
+@pytest.mark.parametrize("checkpoint", [True, False])
+def test_rounds_equal_one_sorted_pass(tiny_rounds, k, checkpoint):
+    S, rays, ref = tiny_rounds
+    r = S.render_rounds(rays, k=k, checkpoint=checkpoint)
+    assert np.array_equal(r["out"], ref["out"])
+    assert np.array_equal(r["n_blend"], ref["n_blend"])
+    assert r["stats"]["fallbacks"] == 0
+
+
+@pytest.mark.parametrize("caps", [(2, -1), (-1, 1), (3, 3)])
+def test_rounds_with_tiny_capacities_fall_back_exactly(tiny_rounds, caps):
+    S, rays, ref = tiny_rounds
+    r = S.render_rounds(rays, k=4, checkpoint=True, ckpt_cap=caps[0], evict_cap=caps[1])
+    assert r["stats"]["fallbacks"] > 0
+    assert np.array_equal(r["out"], ref["out"])
+
+
+def test_checkpointing_removes_revisits(tiny_rounds):
+    S, rays, ref = tiny_rounds
+    a = S.render_rounds(rays, k=4, checkpoint=True, count_unique=True)["stats"]
+    b = S.render_rounds(rays, k=4, checkpoint=False, count_unique=True)["stats"]
+    assert a["nodes"] + a["leaves"] == a["unique_nodes"]       # no node is fetched twice
+    assert b["nodes"] + b["leaves"] > b["unique_nodes"]        # restart revisits nodes
+    assert a["nodes"] < b["nodes"]
+    assert a["rounds"] == b["rounds"]
+
+
+def test_worked_example_kbuffer_walkthrough():
+    fx = json.load(open(os.path.join(GOLDEN, "kbuffer_walkthrough.json")))
+    k = fx["k"]
+    kt = np.array([e[0] for e in fx["kbuffer_before"]], float)
+    kid = np.array([e[1] for e in fx["kbuffer_before"]], np.int32)
+    cnt, rej = O.kbuf_insert(kt, kid, k, k, *fx["new_hit"])
+    assert cnt == k and rej == (pytest.approx(fx["expect_rejected"][0]), fx["expect_rejected"][1])
+    assert [[float(a), int(b)] for a, b in zip(kt, kid)] == fx["expect_kbuffer_after"]
+    # Listing 1: the hit is ignored only if it is nearer than the rejected entry; here it is
+    # the rejected entry itself, so it is reported and t_max becomes its t_hit
+    tmax_listing = fx["new_hit"][0] if not fx["new_hit"][0] < rej[0] else math.inf
+    assert tmax_listing == fx["expect_listing1_tmax_after"]
+    assert kt[-1] == fx["expect_tight_tmax_after"]
+    ck = [t for t in fx["node_entries_after"] if t > tmax_listing]
+    assert ck == fx["expect_checkpointed_listing1"]
+    # a nearer hit pushes the farthest entry (id 33) out instead
+    cnt, rej = O.kbuf_insert(kt, kid, cnt, k, 2.0, 7)
+    assert rej == (pytest.approx(2.85), 33)
+    assert list(kid) == [12, 40, 7, 8]
+
+
+# ---------------------------------------------------------------- gradients
+
+
+def _fd_scene(seed=21, n=24):
+    rng = np.random.default_rng(seed)
+    means = rng.uniform(-0.4, 0.4, (n, 3))
+    log_scales = rng.uniform(-2.2, -1.2, (n, 3))
+    quats = rng.standard_normal((n, 4))
+    o = rng.uniform(0.15, 0.85, n)     # alpha stays below the 0.99 clamp
+    logits = np.log(o) - np.log1p(-o)
+    sh = rng.normal(0, 0.3, (n, 16, 3))
+    return [means, log_scales, quats, logits, sh]
+
+
+def test_backward_matches_central_differences():
+    params = _fd_scene()
+    n = params[3].shape[0]
+    cam = scenes.pinhole_camera(10, 10, (0.0, 0.0, -2.5), (0, 0, 0), 40.0)
+    rays = O.camera_rays(cam)
+    w = np.random.default_rng(7).normal(0, 1, (rays[0].shape[0], 4))
+
+    def run(p):
+        S = O.Scene(*p, sh_degree=3)
+        r = S.render(rays, ids_cap=n)
+        sig = (tuple(r["n_blend"]), r["ids"].tobytes())
+        return float(np.sum(w * r["out"])), sig, S
+
+    L0, sig0, S0 = run(params)
+    grads = S0.backward(rays, w)
+    names = ["means", "log_scales", "quats", "logits", "sh"]
+    h = 1e-6
+    compared = 0
+    for pi, name in enumerate(names):
+        flat = params[pi].reshape(-1)
+        g_an = grads[name].reshape(-1)
+        scale = np.abs(g_an).max()
+        for j in range(flat.size):
+            pp = [a.copy() for a in params]
+            pm = [a.copy() for a in params]
+            pp[pi].reshape(-1)[j] += h
+            pm[pi].reshape(-1)[j] -= h
+            Lp, sp, _ = run(pp)
+            Lm, sm, _ = run(pm)
+            if sp != sig0 or sm != sig0:
+                continue
+            g_fd = (Lp - Lm) / (2 * h)
+            assert abs(g_fd - g_an[j]) <= 1e-5 * max(abs(g_an[j]), 1e-3 * scale) + 1e-9, (name, j, g_fd, g_an[j])
+            compared += 1
+    assert compared > 0.9 * sum(a.size for a in params)
+
+
+# ---------------------------------------------------------------- LBVH building blocks
+
+
+def test_morton_known_codes():
+    bounds = np.array([0, 0, 0, 1, 1, 1], np.float32)
+    pts = np.array([[0, 0, 0], [1, 1, 1], [0.5, 0, 0], [0, 0.5, 0], [0, 0, 0.5], [0.75, 0, 0],
+                    [0.25, 0.25, 0.25]], np.float32)
+    aabb = np.concatenate([pts, pts], 1)
+    codes = O.morton63(aabb, bounds)
+    expect = [0, 2 ** 63 - 1, 2 ** 62, 2 ** 61, 2 ** 60, 2 ** 62 + 2 ** 59, 2 ** 59 + 2 ** 58 + 2 ** 57]
+    assert [int(c) for c in codes] == expect
+
+
+def test_centroid_bounds():
+    rng = np.random.default_rng(8)
+    a = rng.uniform(-5, 5, (100, 6)).astype(np.float32)
+    lo = np.minimum(a[:, :3], a[:, 3:]); hi = np.maximum(a[:, :3], a[:, 3:])
+    aabb = np.concatenate([lo, hi], 1)
+    c = (np.float32(0.5) * (aabb[:, :3] + aabb[:, 3:])).astype(np.float32)
+    np.testing.assert_array_equal(O.centroid_bounds(aabb), np.concatenate([c.min(0), c.max(0)]))
+
+
+def _aug_prefix(keys, i, j):
+    a = (int(keys[i]) << 32) | i
+    b = (int(keys[j]) << 32) | j
+    return 96 - (a ^ b).bit_length()
+
+
+@pytest.mark.parametrize("n,dups", [(2, False), (3, True), (17, False), (500, True), (1000, False)])
+def test_radix_tree_is_the_binary_radix_tree(n, dups):
+    rng = np.random.default_rng(n)
+    hi = 64 if dups else 2 ** 63
+    keys = np.sort(rng.integers(0, hi, n, dtype=np.uint64))
+    left, right = O.radix_tree(keys)
+    child_count = {}
+    rng_of = {}
+
+    def walk(ref, a_hint=None):
+        if ref & O.LEAF:
+            j = ref & ~O.LEAF
+            child_count[("L", j)] = child_count.get(("L", j), 0) + 1
+            return j, j
+        child_count[("I", ref)] = child_count.get(("I", ref), 0) + 1
+        a, g = walk(int(left[ref]))
+        g1, b = walk(int(right[ref]))
+        assert g1 == g + 1
+        common = _aug_prefix(keys, a, b)
+        assert _aug_prefix(keys, a, g) > common and _aug_prefix(keys, g + 1, b) > common
+        assert ref in (a, b)
+        rng_of[ref] = (a, b)
+        return a, b
+
+    a, b = walk(0)
+    assert (a, b) == (0, n - 1)
+    assert all(v == 1 for v in child_count.values())
+    assert len([1 for k_ in child_count if k_[0] == "L"]) == n
+    assert len([1 for k_ in child_count if k_[0] == "I"]) == n - 1
+    node_box = O.refit(left, right, np.zeros((n, 6), np.float32))
+    assert node_box.shape == (n - 1, 6)
+
+
+def test_refit_is_the_union_of_each_range():
+    rng = np.random.default_rng(9)
+    n = 300
+    keys = np.sort(rng.integers(0, 2 ** 20, n, dtype=np.uint64))
+    left, right = O.radix_tree(keys)
+    c = rng.uniform(-1, 1, (n, 3)).astype(np.float32)
+    e = rng.uniform(0, 0.1, (n, 3)).astype(np.float32)
+    leaf = np.concatenate([c - e, c + e], 1)
+    nodes = O.refit(left, right, leaf)
+
+    def rng_of(ref):
+        if ref & O.LEAF:
+            j = ref & ~O.LEAF
+            return j, j
+        return rng_of(int(left[ref]))[0], rng_of(int(right[ref]))[1]
+
+    for i in range(n - 1):
+        a, b = rng_of(i)
+        np.testing.assert_array_equal(nodes[i, :3], leaf[a:b + 1, :3].min(0))
+        np.testing.assert_array_equal(nodes[i, 3:], leaf[a:b + 1, 3:].max(0))
+
+
+# ---------------------------------------------------------------- cameras
+
+
+def test_pinhole_rays_linear_in_tangent_space():
+    cam = scenes.pinhole_camera(64, 48, (1.0, 2.0, -3.0), (0, 0, 0), 50.0)
+    o, d, tn, tf = O.camera_rays(cam)
+    np.testing.assert_allclose(np.linalg.norm(d, axis=1), 1.0, atol=1e-14)
+    R = np.array([cam["right"], cam["up"], cam["forward"]])
+    loc = d @ R.T
+    tx = (loc[:, 0] / loc[:, 2]).reshape(48, 64)
+    ty = (loc[:, 1] / loc[:, 2]).reshape(48, 64)
+    step_y = 2 * math.tan(math.radians(25)) / 48
+    np.testing.assert_allclose(np.diff(ty, axis=0), -step_y, atol=1e-12)
+    np.testing.assert_allclose(np.diff(tx, axis=1), step_y, atol=1e-12)   # square pixels
+    np.testing.assert_allclose(tx[:, ::-1], -tx, atol=1e-12)
+    np.testing.assert_allclose(ty[::-1, :], -ty, atol=1e-12)
+    np.testing.assert_allclose(o, np.tile([1.0, 2.0, -3.0], (64 * 48, 1)))
+
+
+def test_fisheye_angle_proportional_to_radius():
+    cam = scenes.fisheye_camera(40, 30, (0, 1.7, 0), (1, 0, 0), 90.0)
+    o, d, tn, tf = O.camera_rays(cam)
+    ys, xs = np.meshgrid(np.arange(30) + 0.5 - 15, np.arange(40) + 0.5 - 20, indexing="ij")
+    r = np.hypot(xs, ys).reshape(-1)
+    ang = np.arccos(np.clip(d @ np.array(cam["forward"]), -1, 1))
+    np.testing.assert_allclose(ang, r * (math.pi / 2) / 20, atol=1e-12)
