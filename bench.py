@@ -1,0 +1,434 @@
+"""Benchmark: GRTX Gaussian ray tracing on one GB300 (or N replicas).
+
+Workload: the 1M-Gaussian surface-like scene (SH degree 3) rendered at 1920x1080 through a
+pinhole camera with k = 16 (the configuration the headline metric is quoted on). A step is
+one frame: every ray traced through the resident scene (ray generation, checkpointed
+k-buffer rounds, compositing with early termination) in one persistent launch. The BVH is
+built once per scene, outside the timed region, and its build time is reported separately.
+
+Printed (rank 0, one JSON line): Mrays/s of the GRTX form (sphere instances, checkpointed
+resume) as `value`, with the plain form (20-triangle proxy BVH, restart from the root) beside
+it, BVH nodes per ray for both, the roofline of the trace kernel, an end-to-end figure through
+the Python API with the image read back to pinned host memory, serving latency (p50/p99) for
+the four-scene request stream, and the FP64 CPU oracle timed on a sample of the same rays.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from collections import deque
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="grtx", choices=["grtx", "reference"])
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ------------------------------------------------------------------------------------------
+# distributed (one process per GPU; replicas: every rank renders the full workload)
+# ------------------------------------------------------------------------------------------
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl" if os.environ.get("GRTX_BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        dev = "cuda" if torch.cuda.is_available() and self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+def aggregate_throughput(units_per_rank: float, seconds_per_rank: float, world: int, max_fn) -> tuple:
+    """Whole-job throughput of `world` replicas: all units over the slowest rank's time."""
+    t = max_fn(seconds_per_rank)
+    return units_per_rank * world / t, t
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int = 0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.25)
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                if int(p[0]) != self.gpu:
+                    continue
+                rows.append((float(p[1]), float(p[2]), p[5], p[6], p[7], p[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        reasons = set()
+        for r in rows:
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), r[2:]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle baseline
+# ------------------------------------------------------------------------------------------
+def oracle_rate(g, cam, seconds: float, seed: int = 0, max_rays: int = 1 << 16):
+    """Rays per second of the FP64 brute-force oracle on a seeded sample of the camera's rays,
+    sized to take about `seconds`. Returns (rays/s, sample size, cores)."""
+    from oracle import oracle as O
+    S = O.Scene.from_params(g)
+    o, d, tn, tf = O.camera_rays(cam)
+    rng = np.random.default_rng(seed)
+    n = 16
+    while True:
+        idx = rng.choice(o.shape[0], n, replace=False)
+        t0 = time.perf_counter()
+        S.render((o[idx], d[idx], tn[idx], tf[idx]))
+        dt = time.perf_counter() - t0
+        if dt >= seconds or n >= max_rays:
+            return n / dt, n, O.num_threads()
+        n = min(max_rays, max(n * 2, int(n * seconds / max(dt, 1e-3) * 1.05)))
+
+
+def run_reference(args, dist: Dist):
+    """The FP64 CPU oracle as the reference arm: each step traces a bounded sample of the
+    workload's rays on the host cores; same metric and unit as the GPU arm."""
+    if dist.rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2601_20429_gb300 import scenes
+    g, cam, cfg = scenes.config_surface()
+    S = O.Scene.from_params(g)
+    o, d, tn, tf = O.camera_rays(cam)
+    rng = np.random.default_rng(123)
+    per_step = 128
+    for _ in range(max(args.warmup, 0)):
+        idx = rng.choice(o.shape[0], per_step, replace=False)
+        S.render((o[idx], d[idx], tn[idx], tf[idx]))
+    t_all = 0.0
+    for _ in range(args.steps):
+        idx = rng.choice(o.shape[0], per_step, replace=False)
+        t0 = time.perf_counter()
+        S.render((o[idx], d[idx], tn[idx], tf[idx]))
+        t_all += time.perf_counter() - t0
+    value = per_step * args.steps / t_all / 1e6
+    cores = O.num_threads()
+    line = {
+        "impl": "reference", "metric": "Mrays/s (GRTX form, 1920x1080, 1M Gaussians, k=16)", "value": value,
+        "unit": "Mrays/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "surface-like scene, 1M Gaussians, SH degree 3, 1920x1080 pinhole, k=16",
+                   "reference": "FP64 brute-force CPU oracle", "rays_per_step": per_step},
+        "cpu_baseline": {"value": value, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} seeded random pixels of the 1920x1080 frame per step"},
+        "e2e": {"value": value, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+def time_frames(fn, steps: int, warmup: int, flush, stream):
+    """Per-step device time (ms) of fn() with CUDA events on `stream`, L2 flushed between steps."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    times = []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush()
+        ev[i][0].record(stream)
+        fn()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    for a, b in ev:
+        times.append(a.elapsed_time(b))
+    return times
+
+
+def nodes_per_ray(st: dict) -> dict:
+    r = max(st["rays"], 1)
+    return {"internal": st["nodes"] / r, "leaf": st["leaves"] / r, "total": (st["nodes"] + st["leaves"]) / r,
+            "blended": st["blended"] / r, "rounds": st["rounds"] / r, "ckpt_writes": st["ckpt_writes"] / r,
+            "evictions": st["evictions"] / r, "fallback_rays": st["fallbacks"]}
+
+
+def bench_serving(n_requests: int):
+    import torch
+    from paper_2601_20429_gb300 import render as R
+    from paper_2601_20429_gb300 import scenes
+    from paper_2601_20429_gb300.serve import Server
+    scs, reqs, cfg = scenes.config_serving(n_requests=n_requests)
+    gpu_scenes = [R.Scene.from_params(g) for g in scs]
+    del scs
+    srv = Server(gpu_scenes, k=cfg["k"], max_rays_per_step=4 << 20, max_inflight=64)
+    max_px = 1920 * 1080
+    pool = deque(torch.empty((max_px, 4), dtype=torch.float32, device="cuda") for _ in range(80))
+    # warm-up: a few requests of each size
+    warm = [(j % 4, reqs[j]["camera"], pool[j], 10 ** 9 + j) for j in range(8)]
+    srv.render_requests(warm)
+    torch.cuda.synchronize()
+    n = len(reqs)
+    lat = [None] * n
+    busy = {}
+    t0 = time.monotonic()
+    i = 0
+    waiting = deque()
+    done_n = 0
+    t_first = None
+    t_last = 0.0
+    while done_n < n:
+        now = time.monotonic() - t0
+        while i < n and reqs[i]["arrival"] <= now:
+            waiting.append(i)
+            i += 1
+        batch = []
+        while waiting and pool:
+            j = waiting.popleft()
+            buf = pool.popleft()
+            busy[j] = buf
+            batch.append((reqs[j]["scene"], reqs[j]["camera"], buf, j))
+        if batch:
+            srv.submit(batch)
+        got = srv.poll(wait=False)
+        for c in got:
+            j = c["tag"]
+            lat[j] = (c["t_done"] - t0) - reqs[j]["arrival"]
+            t_last = max(t_last, c["t_done"] - t0)
+            pool.append(busy.pop(j))
+            done_n += 1
+        if not got and not batch:
+            time.sleep(0.0002)
+    rays = sum(reqs[j]["camera"]["width"] * reqs[j]["camera"]["height"] for j in range(n))
+    makespan = t_last - reqs[0]["arrival"]
+    lat_ms = np.array(lat) * 1e3
+    srv.close()
+    for s in gpu_scenes:
+        s.close()
+    return {"requests": n, "rate_hz": 200.0, "p50_ms": float(np.percentile(lat_ms, 50)),
+            "p99_ms": float(np.percentile(lat_ms, 99)), "mean_ms": float(lat_ms.mean()),
+            "Mrays_per_s": rays / makespan / 1e6, "makespan_s": makespan,
+            "offered_Mrays_per_s": rays / (reqs[-1]["arrival"] - reqs[0]["arrival"]) / 1e6}
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    if args.impl == "reference":
+        run_reference(args, dist)
+        dist.close()
+        return
+    import torch
+    from paper_2601_20429_gb300 import native as N
+    from paper_2601_20429_gb300 import render as R
+    from paper_2601_20429_gb300 import scenes
+
+    torch.cuda.set_device(dist.local)
+    N.lib()
+    peaks = load_peaks()
+    g, cam, cfg = scenes.config_surface()
+    k = cfg["k"]
+    n_rays = cam["width"] * cam["height"]
+    stream = torch.cuda.current_stream()
+
+    t0 = time.perf_counter()
+    sc = R.Scene.from_params(g, form="sphere")
+    torch.cuda.synchronize()
+    build_sphere_ms = (time.perf_counter() - t0) * 1e3
+    t0 = time.perf_counter()
+    sc_plain = R.Scene.from_params(g, form="proxy20")
+    torch.cuda.synchronize()
+    build_plain_ms = (time.perf_counter() - t0) * 1e3
+    info, info_plain = sc.info(), sc_plain.info()
+
+    out = torch.empty((n_rays, 4), dtype=torch.float32, device="cuda")
+    flush_buf = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
+
+    def flush():
+        flush_buf.fill_(1)
+
+    # counters (instrumented run, not timed)
+    st_grtx = N.stats_dict(R.render(sc, cam, k=k, out=out, want_stats=True)["stats"])
+    st_plain = N.stats_dict(R.render(sc_plain, cam, k=k, out=out, want_stats=True)["stats"])
+    st_restart = N.stats_dict(R.render(sc, cam, k=k, traversal="restart", out=out, want_stats=True)["stats"])
+
+    def frame():
+        R.render(sc, cam, k=k, out=out)
+
+    def frame_plain():
+        R.render(sc_plain, cam, k=k, out=out)
+
+    def frame_restart():
+        R.render(sc, cam, k=k, traversal="restart", out=out)
+
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    times = time_frames(frame, args.steps, args.warmup, flush, stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    dist.barrier()
+    ms = statistics.mean(times)
+    value, t_max = aggregate_throughput(n_rays * args.steps, sum(times) / 1e3, dist.world, dist.max)
+    value /= 1e6
+    times_plain = time_frames(frame_plain, max(5, args.steps // 3), 2, flush, stream)
+    times_restart = time_frames(frame_restart, max(5, args.steps // 3), 2, flush, stream)
+
+    # end to end through the public API: render + read the image back to pinned host memory
+    host = torch.empty((n_rays, 4), dtype=torch.float32, pin_memory=True)
+    for _ in range(2):
+        R.render(sc, cam, k=k, out=out)
+        host.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_steps = max(5, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        R.render(sc, cam, k=k, out=out)
+        host.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_val, _ = aggregate_throughput(n_rays * e2e_steps, e2e_s, dist.world, dist.max)
+
+    # roofline of the trace kernel: logical bytes per ray from the counters (nodes and leaf
+    # records 64 B each, blended Gaussians 64 B geometry + SH record, checkpoint / eviction
+    # entries 8 B written + 8 B read, 16 B output) over the event-timed launch
+    sh_bytes = 4 * info["bytes_appearance"] // max(info["n_valid"], 1) // 4
+    st = st_grtx
+    logical = (64 * (st["nodes"] + st["leaves"]) + (64 + sh_bytes) * st["blended"] +
+               16 * (st["ckpt_writes"] + st["evictions"]) + 16 * st["rays"])
+    achieved = logical / (ms / 1e3) / 1e9
+    peak = peaks.get("hbm_gbs", 6800.0)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_trace<16, sphere>",
+                "bytes_per_ray": logical / max(st["rays"], 1),
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+
+    serving = None
+    if dist.world == 1 and not args.no_serving:
+        serving = bench_serving(args.serve_requests)
+
+    cpu = None
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        rate, nsamp, cores = oracle_rate(g, cam, args.cpu_seconds)
+        cpu = {"value": rate / 1e6, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
+               "sample": f"{nsamp} seeded random pixels of the 1920x1080 frame (FP64 brute force over 1M Gaussians)"}
+
+    if dist.rank == 0:
+        line = {
+            "metric": "Mrays/s (GRTX form, 1920x1080, 1M Gaussians, k=16)",
+            "value": value, "unit": "Mrays/s", "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "surface-like scene: 1M Gaussians on 200 spheres/patches, SH degree 3; "
+                                   "1920x1080 pinhole at (0,0,-4); k=16, alpha_min=0.01, T_min=1e-3",
+                       "step": "one frame traced on the resident scene (BVH built once, timed separately)",
+                       "l2": "flushed (256 MB write) between timed steps",
+                       "parallelism": f"replicas x{dist.world}"},
+            "gpu_launches": args.steps,
+            "grtx": {"Mrays_per_s": value, "ms_per_frame": ms, "nodes_per_ray": nodes_per_ray(st_grtx),
+                     "build_ms": build_sphere_ms, "bvh_bytes": info["bytes_nodes"] + info["bytes_leaves"],
+                     "depth": info["depth"], "workspace_bytes": info["bytes_workspace"]},
+            "grtx_restart": {"Mrays_per_s": n_rays / (statistics.mean(times_restart) / 1e3) / 1e6,
+                             "ms_per_frame": statistics.mean(times_restart), "nodes_per_ray": nodes_per_ray(st_restart)},
+            "plain": {"Mrays_per_s": n_rays / (statistics.mean(times_plain) / 1e3) / 1e6,
+                      "ms_per_frame": statistics.mean(times_plain), "nodes_per_ray": nodes_per_ray(st_plain),
+                      "build_ms": build_plain_ms, "bvh_bytes": info_plain["bytes_nodes"] + info_plain["bytes_leaves"],
+                      "depth": info_plain["depth"]},
+            "roofline": roofline,
+            "e2e": {"value": e2e_val / 1e6, "unit": "Mrays/s", "h2d_bytes_per_step": 112,
+                    "d2h_bytes_per_step": n_rays * 16},
+            "serving": serving,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    sc.close()
+    sc_plain.close()
+    dist.close()
+
+
+if __name__ == "__main__":
+    main()

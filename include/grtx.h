@@ -1,0 +1,362 @@
+/*
+ * grtx.h -- C ABI of libgrtx.so, a GB300 (sm_103a) Gaussian ray tracer after GRTX
+ * (arXiv 2601.20429): every anisotropic Gaussian is a unit sphere in its own instance space
+ * (Sec. IV-A), rays traverse an LBVH whose leaves are those instances, and tracing runs in
+ * rounds that gather the k nearest hits in a k-buffer (Sec. III-A), composite them front to
+ * back with early termination (Sec. II-B Eq. volume-render, Sec. III-A), and resume the next
+ * round from checkpointed nodes and evicted hits instead of the root (Sec. IV-B, Listing 1).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* or documented as "device" point to device memory on the current
+ *     CUDA device; the caller owns them unless stated. Host structs are read during the call
+ *     only and may be freed when it returns.
+ *   - All work is enqueued on the given stream (a cudaStream_t passed as void*, NULL = the
+ *     legacy default stream) and is asynchronous unless stated. Outputs are valid once the
+ *     stream reaches the point after the call.
+ *   - Every call returns a grtx_status. No exception or longjmp crosses the ABI. Argument
+ *     errors are detected on the host before anything is enqueued. Device-side capacity
+ *     overflows are never fatal: the affected ray falls back to restarting from the root
+ *     (always correct) and the event is counted in grtx_stats.
+ *   - Floating point is IEEE FP32 throughout; arrays are C-contiguous structure-of-arrays.
+ *   - A scene or server may be used from one host thread at a time.
+ */
+#ifndef GRTX_H
+#define GRTX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GRTX_API __attribute__((visibility("default")))
+#define GRTX_VERSION 1
+
+/* ---------------------------------------------------------------------------------------- */
+/* Status codes                                                                             */
+/* ---------------------------------------------------------------------------------------- */
+typedef enum grtx_status {
+    GRTX_OK = 0,
+    GRTX_ERR_INVALID_ARG = 1,     /* a pointer, size or parameter is out of its documented range */
+    GRTX_ERR_OOM = 2,             /* a device allocation failed                                 */
+    GRTX_ERR_CUDA = 3,            /* a CUDA runtime call failed (sticky device error, launch)  */
+    GRTX_ERR_OVERFLOW_FATAL = 4,  /* a fixed limit was exceeded with no fallback (BVH depth)   */
+    GRTX_ERR_TIMEOUT = 5,         /* a bounded wait ran out                                    */
+    GRTX_ERR_BUSY = 6,            /* the server has no free slot or memory for the request     */
+    GRTX_ERR_NOT_FOUND = 7        /* an id (scene, request) is unknown                          */
+} grtx_status;
+
+/* ---------------------------------------------------------------------------------------- */
+/* Plain data types                                                                         */
+/* ---------------------------------------------------------------------------------------- */
+
+/* Raw Gaussian parameters (Sec. II-B: mean, covariance from rotation and scale, opacity,
+ * SH coefficients). All device pointers, caller-owned, FP32:
+ *   means [n][3]; log_scales [n][3] (s = exp); quats [n][4] as (w,x,y,z), any non-zero length
+ *   (normalised inside); opacity_logits [n] (o = sigmoid); sh [n][(L+1)^2][3], L = sh_degree. */
+typedef struct grtx_gaussians {
+    const float *means;
+    const float *log_scales;
+    const float *quats;
+    const float *opacity_logits;
+    const float *sh;
+    int64_t n;
+    int32_t sh_degree;           /* 0..3 */
+    int32_t reserved;
+} grtx_gaussians;
+
+/* Gradients w.r.t. the raw parameters, same shapes as grtx_gaussians, device, caller-owned.
+ * grtx_trace_backward ADDS into them (the caller zeroes them first). A NULL member skips
+ * that parameter. */
+typedef struct grtx_grads {
+    float *means;
+    float *log_scales;
+    float *quats;
+    float *opacity_logits;
+    float *sh;
+} grtx_grads;
+
+enum { GRTX_FORM_SPHERE = 0,        /* one leaf per Gaussian, analytic unit sphere (Sec. IV-A) */
+       GRTX_FORM_PROXY20 = 1 };     /* one leaf per proxy triangle: 20-triangle icosahedron
+                                       around each Gaussian, monolithic BVH (Sec. III-C Obs. I) */
+enum { GRTX_TRAVERSAL_CHECKPOINT = 0, /* resume from checkpointed nodes + eviction list (IV-B) */
+       GRTX_TRAVERSAL_RESTART = 1 };  /* restart from the root every round (Sec. III-A)       */
+
+/* Tracing parameters. k: k-buffer size, one of 1, 2, 4, 8, 16, 32 (Sec. III-A).
+ * alpha_min: a Gaussian is hit where its response reaches alpha_min (0.01); it also sets the
+ * ellipsoid radius kappa = sqrt(2 ln(o / alpha_min)) used at build time. T_min: a ray stops
+ * right after the Gaussian that takes its transmittance below T_min (1e-3). alpha_max: clamp
+ * on alpha before compositing (0.99). bg: background colour added as T * bg.
+ * ckpt_capacity / evict_capacity: checkpoint and eviction entries per resident ray slot
+ * (Sec. IV-B "Checkpoint and Eviction Buffer"); 0 selects the defaults (128 / 64).
+ * traversal: GRTX_TRAVERSAL_*; ignored (always restart) for GRTX_FORM_PROXY20 scenes. */
+typedef struct grtx_params {
+    int32_t k;
+    int32_t traversal;
+    float alpha_min;
+    float T_min;
+    float alpha_max;
+    float bg[3];
+    int32_t ckpt_capacity;
+    int32_t evict_capacity;
+} grtx_params;
+
+enum { GRTX_CAMERA_PINHOLE = 0, GRTX_CAMERA_FISHEYE = 1, GRTX_CAMERA_RAYS = 2 };
+
+/* A camera (rays generated in-kernel) or an explicit ray list.
+ * Pinhole: pixel (x, y), y = 0 the top row, has direction
+ *   normalize(forward + u right + v up), u = (2(x+.5)/W - 1) tan(fov/2) W/H,
+ *   v = (1 - 2(y+.5)/H) tan(fov/2); fov is the vertical field of view in radians.
+ * Fisheye (equidistant): the angle from forward is r / f with r the distance in pixels of
+ *   the pixel centre from the image centre and f = (W/2) / fov, i.e. fov is the angle
+ *   reached at half the image width.
+ * Rays: width*height rays (height may be 1) from device arrays ray_origins [n][3],
+ *   ray_dirs [n][3] (any non-zero length; t is measured in units of |dir|), and optional
+ *   ray_tnear / ray_tfar [n] (NULL: the scalar t_near / t_far below).
+ * Every ray accepts hits with t_near < t <= t_far. Output pixel index = y * width + x. */
+typedef struct grtx_camera {
+    int32_t type;
+    int32_t width, height;
+    float pos[3], right[3], up[3], forward[3];
+    float fov;
+    float t_near, t_far;
+    const float *ray_origins;
+    const float *ray_dirs;
+    const float *ray_tnear;
+    const float *ray_tfar;
+} grtx_camera;
+
+/* Device counters, summed (+=) over rays by the trace calls when a grtx_stats* is given.
+ * nodes: internal BVH nodes fetched; leaves: leaf records tested (Gaussians or triangles);
+ * blended: Gaussians composited; rounds: tracing rounds; ckpt_writes: checkpoint entries
+ * written; evictions: entries written to the eviction list; fallbacks: rays that exceeded a
+ * capacity and restarted from the root; stack_overflow: traversal stack overflows (never
+ * expected: the build rejects trees deeper than the stack). */
+typedef struct grtx_stats {
+    unsigned long long rays, nodes, leaves, blended, rounds, ckpt_writes, evictions, fallbacks,
+        stack_overflow, reserved;
+} grtx_stats;
+
+/* Outputs of a forward trace. rgbT: device [n_rays][4] = (C + T bg, T), required.
+ * n_blended: optional device [n_rays], Gaussians composited per ray. blended_ids: optional
+ * device [n_rays][ids_cap], the first ids_cap composited Gaussian ids per ray in blend order
+ * (unused tail entries are 0xFFFFFFFF). stats: optional device grtx_stats (accumulated).
+ * With any optional output requested the kernel takes a slower instrumented path. */
+typedef struct grtx_trace_outputs {
+    float *rgbT;
+    int32_t *n_blended;
+    uint32_t *blended_ids;
+    int32_t ids_cap;
+    int32_t reserved;
+    grtx_stats *stats;
+} grtx_trace_outputs;
+
+/* Host-readable description of a built scene. */
+typedef struct grtx_scene_info {
+    int64_t n_gaussians;       /* n given to the build                                     */
+    int64_t n_valid;           /* Gaussians with o > alpha_min, i.e. in the BVH            */
+    int64_t n_leaves;          /* BVH leaves: n_valid (sphere) or 20 n_valid (proxy)        */
+    int64_t n_nodes;           /* internal BVH nodes (n_leaves - 1, at least 1)             */
+    int32_t depth;             /* deepest leaf, root = 0                                    */
+    int32_t form;              /* GRTX_FORM_*                                              */
+    int32_t sh_degree;
+    int32_t reserved;
+    int64_t bytes_nodes;       /* device bytes of BVH nodes                                */
+    int64_t bytes_leaves;      /* device bytes of leaf records (geometry / triangles)      */
+    int64_t bytes_appearance;  /* device bytes of the appearance (SH) records              */
+    int64_t bytes_workspace;   /* device bytes of the per-slot checkpoint/eviction buffers */
+    float bounds[6];           /* world AABB of all leaves                                 */
+} grtx_scene_info;
+
+typedef struct grtx_scene grtx_scene;
+
+/* ---------------------------------------------------------------------------------------- */
+/* Utilities                                                                                */
+/* ---------------------------------------------------------------------------------------- */
+
+/* Static English text for a status code (never NULL). */
+GRTX_API const char *grtx_status_string(int status);
+/* GRTX_VERSION of the library. */
+GRTX_API int grtx_version(void);
+/* Host-side text of the last error detected in this thread (never NULL; "" if none). */
+GRTX_API const char *grtx_last_error(void);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Building blocks of the BVH build (each also runs inside grtx_build_bvh)                  */
+/* ---------------------------------------------------------------------------------------- */
+
+/* Parameter activation and instance transform (Sec. II-B; Sec. IV-A "the ray is
+ * transformed to the local coordinate system ... derived from its rotation and scaling").
+ * For each Gaussian i: o = sigmoid(logit); s = exp(log_scale); R from the normalised
+ * quaternion; kappa = sqrt(2 ln(o/alpha_min)). If o > alpha_min, writes
+ *   d_geom[i] (16 floats): the rows of A = diag(1/(kappa s)) R^T with the mean, as three float4
+ *     (A_j0, A_j1, A_j2, mu_j), so that x_unit = A (x - mu); then (o, -0.5 kappa^2 log2(e),
+ *     bits of i, 0);
+ *   d_aabb[i] (6 floats): lo xyz, hi xyz of the ellipsoid {x : |A x + b| <= 1}, widened by a
+ *     relative 4e-6 so it stays conservative under FP32 rounding;
+ * otherwise d_geom[i] is all zero and d_aabb[i] is the empty box (+inf, -inf).
+ * d_geom, d_aabb: device, caller-owned, 16-byte aligned. */
+GRTX_API int grtx_prep_gaussians(const grtx_gaussians *g, float alpha_min, float *d_geom,
+                                 float *d_aabb, void *stream);
+
+/* Morton order of AABB centroids (LBVH construction; the paper builds its BVH with a
+ * third-party builder, Sec. V-A). centroid = 0.5 (lo + hi) in FP32; each coordinate is
+ * quantised to 21 bits as floor((c - blo) * (2^21 / (bhi - blo))) clamped to [0, 2^21 - 1]
+ * (0 when bhi == blo), all in FP32, and the bits are interleaved x, y, z from the most
+ * significant triple down into a 63-bit code. An empty box (lo > hi on any axis) gets the
+ * code 2^64 - 1. d_bounds: device float[6] (lo xyz, hi xyz) of the centroids, or NULL to
+ * have them computed over the non-empty boxes (written to d_bounds_out if non-NULL).
+ * d_aabb [n][6] in, d_codes [n] out; device, caller-owned. */
+GRTX_API int grtx_morton_codes(const float *d_aabb, int64_t n, const float *d_bounds,
+                               float *d_bounds_out, uint64_t *d_codes, void *stream);
+
+/* Stable ascending LSD radix sort of (key, value) pairs in place, over the low key_bits bits
+ * of the keys (1..64; bits above are ignored for ordering). d_temp / *temp_bytes: scratch;
+ * call with d_temp == NULL to get the required size in *temp_bytes (nothing is enqueued).
+ * d_keys [n], d_values [n], d_temp: device, caller-owned. n < 2^31. */
+GRTX_API int grtx_sort_pairs(uint64_t *d_keys, uint32_t *d_values, int64_t n, int key_bits,
+                             void *d_temp, size_t *temp_bytes, void *stream);
+
+/* Binary radix tree over n >= 2 sorted keys (index appended to break ties between equal
+ * keys): internal node 0 is the root; node i covers a key range with i at one end; a range
+ * [a, b] split at g has children [a, g] and [g+1, b], numbered g and g+1 if internal or
+ * encoded as (0x80000000 | leaf index) if they hold one key. Writes d_left / d_right [n-1]
+ * and d_parent [2n-1] (entries 0..n-2: internal nodes, n-1+j: leaf j; root's is 0xFFFFFFFF).
+ * Device, caller-owned. */
+GRTX_API int grtx_radix_tree(const uint64_t *d_sorted_keys, int64_t n, uint32_t *d_left,
+                             uint32_t *d_right, uint32_t *d_parent, void *stream);
+
+/* Bottom-up bounds: box of every internal node = union of its children's boxes, leaves'
+ * boxes given in sorted order (d_leaf_aabb [n][6]); FP32 min/max, hence exact. Uses the tree
+ * of grtx_radix_tree. d_node_aabb [n-1][6] out; d_counters: device scratch of n-1 uint32
+ * (contents on entry ignored). Device, caller-owned. */
+GRTX_API int grtx_refit(const uint32_t *d_left, const uint32_t *d_right, const uint32_t *d_parent,
+                        const float *d_leaf_aabb, int64_t n, float *d_node_aabb,
+                        uint32_t *d_counters, void *stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Scenes                                                                                   */
+/* ---------------------------------------------------------------------------------------- */
+
+/* Build the acceleration structure for one set of Gaussians (Sec. IV-A "Bounding
+ * Primitives": form GRTX_FORM_SPHERE keeps one instance per Gaussian over a shared analytic
+ * unit sphere; GRTX_FORM_PROXY20 is the 20-triangle monolithic baseline of Sec. III-C).
+ * Steps: grtx_prep_gaussians -> (proxy: expand 20 triangles per Gaussian) -> Morton codes ->
+ * radix sort -> radix tree -> refit -> node compaction. p->alpha_min fixes the ellipsoid
+ * radius; later traces must use the same alpha_min. The library allocates (stream-ordered)
+ * and owns all scene memory: packed copies of the geometry and appearance, the BVH and a
+ * per-slot trace workspace grown on demand; the caller's arrays may be freed once the
+ * stream passes the call. Synchronises the stream once at the end (to read the node count
+ * and tree depth). *out is set only on success. Fails with GRTX_ERR_OVERFLOW_FATAL if the
+ * tree is deeper than the traversal stack (64). */
+GRTX_API int grtx_build_bvh(const grtx_gaussians *g, const grtx_params *p, int form, void *stream,
+                            grtx_scene **out);
+
+/* Fill *info (host) for a built scene. Host-only, no stream work. */
+GRTX_API int grtx_scene_info_get(const grtx_scene *scene, grtx_scene_info *info);
+
+/* Copy the scene's internal arrays to caller device buffers (for tests and tools); any
+ * pointer may be NULL. d_nodes: [n_nodes][16] floats (child 0 box lo xyz, hi x | hi yz,
+ * child 1 box lo xy | lo z, hi xyz | child refs as uint32 bits, then per child the largest
+ * proxy diameter in its subtree, 0 for the sphere form); d_leaf_ids: [n_leaves]
+ * uint32 Gaussian id of each leaf in leaf order; d_codes: [n_leaves] sorted Morton codes. */
+GRTX_API int grtx_scene_export(const grtx_scene *scene, float *d_nodes, uint32_t *d_leaf_ids,
+                               uint64_t *d_codes, void *stream);
+
+/* Release a scene (stream-ordered on the scene's build stream; NULL is a no-op). */
+GRTX_API void grtx_scene_destroy(grtx_scene *scene);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Rendering                                                                                */
+/* ---------------------------------------------------------------------------------------- */
+
+/* The rays a camera generates (for tests; the trace kernels generate them in-kernel).
+ * d_origins / d_dirs [n][3], d_tnear / d_tfar [n]; device, caller-owned; n = W*H. */
+GRTX_API int grtx_generate_rays(const grtx_camera *cam, float *d_origins, float *d_dirs,
+                                float *d_tnear, float *d_tfar, void *stream);
+
+/* Render every ray of cam (Sec. III-A pipeline: ray generation, traversal gathering the k
+ * nearest hits per round, blending in depth order, early termination; Sec. IV-B checkpointed
+ * resume). Hits are Gaussians whose max response along the ray (Sec. III-A Eq. t-max-resp)
+ * reaches alpha_min with t_near < t_alpha <= t_far, ordered by (t_alpha, leaf index); colour
+ * is max(0, SH(ray direction) + 0.5). One persistent launch; per resident ray slot the
+ * checkpoint lists and eviction list live in the scene's workspace (grown on demand with a
+ * stream-ordered allocation). */
+GRTX_API int grtx_trace_forward(grtx_scene *scene, const grtx_camera *cam, const grtx_params *p,
+                                const grtx_trace_outputs *out, void *stream);
+
+/* Gradients of a loss L w.r.t. the raw Gaussian parameters for the image of
+ * grtx_trace_forward. g must hold the parameters the scene was built from; d_rgbT is the
+ * forward output [n_rays][4] and d_dL_drgbT the upstream gradient [n_rays][4]. The kernel
+ * re-traverses the same rounds and accumulates, front to back, the derivative of Eq.
+ * volume-render and of alpha = o G(r_o + t_alpha r_d) through the unit-sphere transform
+ * (the hit set, order and termination index are piecewise constant and not differentiated).
+ * Accumulates with atomics into *grads (caller zeroes). */
+GRTX_API int grtx_trace_backward(grtx_scene *scene, const grtx_gaussians *g,
+                                 const grtx_camera *cam, const grtx_params *p,
+                                 const float *d_rgbT, const float *d_dL_drgbT,
+                                 const grtx_grads *grads, void *stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Serving: several resident scenes, camera requests batched into persistent launches.      */
+/* ---------------------------------------------------------------------------------------- */
+
+typedef struct grtx_server grtx_server;
+
+/* A camera request: render cam on scene scene_id into d_rgbT (device [W*H][4], caller-owned,
+ * must stay valid until the request completes). tag is returned with the completion. */
+typedef struct grtx_request {
+    int32_t scene_id;
+    int32_t reserved;
+    grtx_camera cam;
+    float *d_rgbT;
+    uint64_t tag;
+} grtx_request;
+
+/* A finished request: tag, status, and host wall-clock times in seconds (CLOCK_MONOTONIC)
+ * of admission (work first enqueued) and completion (its last step observed complete). */
+typedef struct grtx_completion {
+    uint64_t tag;
+    int32_t status;
+    int32_t reserved;
+    double t_admit;
+    double t_done;
+} grtx_completion;
+
+/* Create a server over n_scenes built scenes (not owned; they must outlive the server).
+ * max_rays_per_step: rays per persistent launch (0: 4M); max_inflight: requests admitted at
+ * once (0: 64); p: tracing parameters for every request. Host call; allocates a step table
+ * in device memory on `stream`, which all later server work uses. */
+GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scenes, const grtx_params *p,
+                                int64_t max_rays_per_step, int max_inflight, void *stream,
+                                grtx_server **out);
+
+/* Queue n requests (host array, copied). Returns GRTX_ERR_BUSY, queueing none of them, if
+ * the pending queue would exceed 65536 entries. Non-blocking. */
+GRTX_API int grtx_server_submit(grtx_server *srv, const grtx_request *reqs, int n);
+
+/* Advance the server: admit pending requests into free slots (continuous batching), enqueue
+ * one step if there is work and fewer than 2 steps are in flight, and report requests whose
+ * last step has completed. Writes at most max_done completions to done (host) and their
+ * count to *n_done. Non-blocking unless wait != 0, in which case it blocks until at least one
+ * request completes or nothing is in flight. */
+GRTX_API int grtx_server_poll(grtx_server *srv, grtx_completion *done, int max_done, int *n_done,
+                              int wait);
+
+/* Submit n requests and poll until all of them complete (a blocking convenience over
+ * grtx_server_submit / grtx_server_poll). done: host array of n completions. */
+GRTX_API int grtx_render_requests(grtx_server *srv, const grtx_request *reqs, int n,
+                                  grtx_completion *done, int *n_done, void *stream);
+
+/* Number of requests admitted but not yet completed, and pending in the queue. */
+GRTX_API int grtx_server_load(const grtx_server *srv, int *n_inflight, int *n_pending);
+
+/* Wait for all in-flight work and release the server (NULL is a no-op). */
+GRTX_API void grtx_server_destroy(grtx_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRTX_H */

@@ -1,0 +1,985 @@
+// BVH build on the GPU: Gaussian activation and instance transform, Morton codes, an LSD
+// radix sort, the binary radix tree (Karras 2012), bottom-up bounds and node compaction.
+// The paper builds an Embree BVH-6 on the host (Sec. V-A); this build is an LBVH so that the
+// whole build stays on the device.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "grtx_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ------------------------------------------------------------------------------------------
+// Activation and instance transform (Sec. II-B parameters; Sec. IV-A unit sphere).
+// ------------------------------------------------------------------------------------------
+__global__ void k_prep(const float *__restrict__ means, const float *__restrict__ log_scales,
+                       const float *__restrict__ quats, const float *__restrict__ logits, int64_t n,
+                       float alpha_min, float4 *__restrict__ geom, float *__restrict__ aabb)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float o = 1.0f / (1.0f + expf(-logits[i]));
+    float *bb = aabb + 6 * i;
+    if (!(o > alpha_min)) {
+        geom[4 * i + 0] = geom[4 * i + 1] = geom[4 * i + 2] = geom[4 * i + 3] = make_float4(0, 0, 0, 0);
+        bb[0] = bb[1] = bb[2] = INFINITY;
+        bb[3] = bb[4] = bb[5] = -INFINITY;
+        return;
+    }
+    float kap = sqrtf(2.0f * logf(o / alpha_min));
+    float mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
+    float s[3] = {expf(log_scales[3 * i]), expf(log_scales[3 * i + 1]), expf(log_scales[3 * i + 2])};
+    float w = quats[4 * i], x = quats[4 * i + 1], y = quats[4 * i + 2], z = quats[4 * i + 3];
+    float inv = rsqrtf(w * w + x * x + y * y + z * z);
+    w *= inv; x *= inv; y *= inv; z *= inv;
+    // rotation matrix of the unit quaternion, row-major R[a][j]; column j = local axis j
+    float R[3][3] = {{1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y)},
+                     {2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x)},
+                     {2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)}};
+    float4 rows[3];
+    for (int j = 0; j < 3; ++j) {
+        float f = 1.0f / (kap * s[j]);
+        rows[j] = make_float4(R[0][j] * f, R[1][j] * f, R[2][j] * f, mu[j]);
+    }
+    geom[4 * i + 0] = rows[0];
+    geom[4 * i + 1] = rows[1];
+    geom[4 * i + 2] = rows[2];
+    geom[4 * i + 3] = make_float4(o, -0.5f * kap * kap * 1.4426950408889634f, __int_as_float((int)i), 0.f);
+    for (int a = 0; a < 3; ++a) {
+        float var = R[a][0] * R[a][0] * s[0] * s[0] + R[a][1] * R[a][1] * s[1] * s[1] +
+                    R[a][2] * R[a][2] * s[2] * s[2];
+        float h = kap * sqrtf(var);
+        h = h * (1.0f + 1e-5f) + 1e-6f * fabsf(mu[a]);   // conservative under FP32 rounding
+        bb[a] = mu[a] - h;
+        bb[3 + a] = mu[a] + h;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Centroid bounds and Morton codes.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void atomic_min_f(float *a, float v)
+{
+    if (v >= 0.0f) atomicMin(reinterpret_cast<int *>(a), __float_as_int(v));
+    else atomicMax(reinterpret_cast<unsigned *>(a), __float_as_uint(v));
+}
+__device__ __forceinline__ void atomic_max_f(float *a, float v)
+{
+    if (v >= 0.0f) atomicMax(reinterpret_cast<int *>(a), __float_as_int(v));
+    else atomicMin(reinterpret_cast<unsigned *>(a), __float_as_uint(v));
+}
+
+__global__ void k_init_bounds(float *b)
+{
+    if (threadIdx.x < 3) b[threadIdx.x] = INFINITY;
+    else if (threadIdx.x < 6) b[threadIdx.x] = -INFINITY;
+}
+
+__device__ __forceinline__ bool box_empty(const float *bb)
+{
+    return !(bb[0] <= bb[3] && bb[1] <= bb[4] && bb[2] <= bb[5]);
+}
+
+__global__ void k_centroid_bounds(const float *__restrict__ aabb, int64_t n, float *__restrict__ bounds)
+{
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float *bb = aabb + 6 * i;
+        if (box_empty(bb)) continue;
+        for (int a = 0; a < 3; ++a) {
+            float c = __fmul_rn(0.5f, __fadd_rn(bb[a], bb[3 + a]));
+            lo[a] = fminf(lo[a], c);
+            hi[a] = fmaxf(hi[a], c);
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1)
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], off));
+            hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], off));
+        }
+    if ((threadIdx.x & 31) == 0)
+        for (int a = 0; a < 3; ++a) {
+            if (lo[a] <= hi[a]) {
+                atomic_min_f(bounds + a, lo[a]);
+                atomic_max_f(bounds + 3 + a, hi[a]);
+            }
+        }
+}
+
+// Spread the low 21 bits of v so that bit b lands at bit 3b.
+__host__ __device__ __forceinline__ uint64_t spread3(uint32_t v)
+{
+    uint64_t x = v & 0x1fffffu;
+    x = (x | (x << 32)) & 0x001f00000000ffffull;
+    x = (x | (x << 16)) & 0x001f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+__global__ void k_morton(const float *__restrict__ aabb, int64_t n, const float *__restrict__ bounds,
+                         uint64_t *__restrict__ codes, uint32_t *__restrict__ values)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float *bb = aabb + 6 * i;
+    if (values) values[i] = (uint32_t)i;
+    if (box_empty(bb)) { codes[i] = ~0ull; return; }
+    uint32_t q[3];
+    for (int a = 0; a < 3; ++a) {
+        float c = __fmul_rn(0.5f, __fadd_rn(bb[a], bb[3 + a]));
+        float ext = __fsub_rn(bounds[3 + a], bounds[a]);
+        float scale = ext > 0.0f ? __fdiv_rn(2097152.0f, ext) : 0.0f;
+        float u = __fmul_rn(__fsub_rn(c, bounds[a]), scale);
+        q[a] = u <= 0.0f ? 0u : (u >= 2097151.0f ? 2097151u : (uint32_t)u);
+    }
+    codes[i] = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
+}
+
+// ------------------------------------------------------------------------------------------
+// Exclusive scan of uint32 (tiles of 4096, recursive over tile sums).
+// ------------------------------------------------------------------------------------------
+constexpr int kScanThreads = 1024, kScanItems = 4, kScanTile = kScanThreads * kScanItems;
+
+__global__ void k_scan_tiles(uint32_t *__restrict__ d, int64_t m, uint32_t *__restrict__ tile_sums)
+{
+    __shared__ uint32_t warp_sums[32];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t local = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        v[j] = (base + j < m) ? d[base + j] : 0u;
+        local += v[j];
+    }
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t incl = local;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += t;
+    }
+    if (lane == 31) warp_sums[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = warp_sums[lane];
+        uint32_t wi = w;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            uint32_t t = __shfl_up_sync(0xffffffffu, wi, off);
+            if (lane >= off) wi += t;
+        }
+        warp_sums[lane] = wi - w;
+        if (lane == 31 && tile_sums) tile_sums[blockIdx.x] = wi;
+    }
+    __syncthreads();
+    uint32_t run = warp_sums[wid] + incl - local;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        if (base + j < m) d[base + j] = run;
+        run += v[j];
+    }
+}
+
+__global__ void k_scan_add(uint32_t *__restrict__ d, int64_t m, const uint32_t *__restrict__ tile_off)
+{
+    int64_t i = (int64_t)blockIdx.x * kScanTile + threadIdx.x;
+    uint32_t add = tile_off[blockIdx.x];
+    for (int j = 0; j < kScanItems; ++j, i += kScanThreads)
+        if (i < m) d[i] += add;
+}
+
+// ------------------------------------------------------------------------------------------
+// LSD radix sort, 8-bit digits: per-tile digit histograms, a global exclusive scan laid out
+// digit-major, then a stable scatter that ranks keys inside a tile with warp matching.
+// ------------------------------------------------------------------------------------------
+constexpr int kSortThreads = 256, kSortItems = 16, kSortTile = kSortThreads * kSortItems;
+
+__global__ void k_sort_hist(const uint64_t *__restrict__ keys, int n, int shift, unsigned dmask,
+                            uint32_t *__restrict__ counts, int n_tiles)
+{
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int base = blockIdx.x * kSortTile;
+#pragma unroll 4
+    for (int it = 0; it < kSortItems; ++it) {
+        int i = base + it * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(unsigned)(keys[i] >> shift) & dmask], 1u);
+    }
+    __syncthreads();
+    counts[(int64_t)threadIdx.x * n_tiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void k_sort_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+                               uint64_t *__restrict__ kout, uint32_t *__restrict__ vout, int n, int shift,
+                               unsigned dmask, const uint32_t *__restrict__ offsets, int n_tiles)
+{
+    __shared__ uint32_t wc[kSortThreads / 32][256];
+    __shared__ uint32_t run[256];
+    int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    run[tid] = offsets[(int64_t)tid * n_tiles + blockIdx.x];
+    int base = blockIdx.x * kSortTile;
+    unsigned lt_mask = (1u << lane) - 1u;
+    for (int it = 0; it < kSortItems; ++it) {
+#pragma unroll
+        for (int w = 0; w < kSortThreads / 32; ++w) wc[w][tid] = 0;
+        __syncthreads();
+        int i = base + it * kSortThreads + tid;
+        bool valid = i < n;
+        uint64_t k = valid ? kin[i] : 0ull;
+        uint32_t v = valid ? vin[i] : 0u;
+        unsigned digit = (unsigned)(k >> shift) & dmask;
+        unsigned vmask = __ballot_sync(0xffffffffu, valid);
+        unsigned rank = 0;
+        if (valid) {
+            unsigned peers = __match_any_sync(vmask, digit);
+            rank = __popc(peers & lt_mask);
+            if (rank == 0) wc[wid][digit] = __popc(peers);
+        }
+        __syncthreads();
+        {
+            uint32_t acc = run[tid];
+#pragma unroll
+            for (int w = 0; w < kSortThreads / 32; ++w) {
+                uint32_t c = wc[w][tid];
+                wc[w][tid] = acc;
+                acc += c;
+            }
+            run[tid] = acc;
+        }
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = wc[wid][digit] + rank;
+            kout[pos] = k;
+            vout[pos] = v;
+        }
+        __syncthreads();
+    }
+}
+
+struct SortTemp {
+    size_t off_keys, off_vals, off_counts, off_scan, total;
+};
+
+SortTemp sort_layout(int64_t n)
+{
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    int n_tiles = std::max(1, grtx_div_up(n, kSortTile));
+    SortTemp t;
+    t.off_keys = 0;
+    t.off_vals = al(t.off_keys + (size_t)n * 8);
+    t.off_counts = al(t.off_vals + (size_t)n * 4);
+    t.off_scan = al(t.off_counts + (size_t)256 * n_tiles * 4);
+    t.total = al(t.off_scan + grtx_scan_temp_bytes((int64_t)256 * n_tiles));
+    return t;
+}
+
+int sort_pairs(uint64_t *keys, uint32_t *vals, int64_t n, int key_bits, void *temp, cudaStream_t s)
+{
+    if (n <= 1) return GRTX_OK;
+    SortTemp L = sort_layout(n);
+    char *t = (char *)temp;
+    uint64_t *k_alt = (uint64_t *)(t + L.off_keys);
+    uint32_t *v_alt = (uint32_t *)(t + L.off_vals);
+    uint32_t *counts = (uint32_t *)(t + L.off_counts);
+    void *scan_tmp = t + L.off_scan;
+    int n_tiles = grtx_div_up(n, kSortTile);
+    int passes = (key_bits + 7) / 8;
+    uint64_t *kin = keys, *kout = k_alt;
+    uint32_t *vin = vals, *vout = v_alt;
+    for (int p = 0; p < passes; ++p) {
+        int shift = 8 * p;
+        int bits = std::min(8, key_bits - shift);            // the last digit may be narrower
+        unsigned dmask = (1u << bits) - 1u;
+        k_sort_hist<<<n_tiles, kSortThreads, 0, s>>>(kin, (int)n, shift, dmask, counts, n_tiles);
+        int st = grtx_scan_exclusive(counts, (int64_t)256 * n_tiles, scan_tmp, s);
+        if (st != GRTX_OK) return st;
+        k_sort_scatter<<<n_tiles, kSortThreads, 0, s>>>(kin, vin, kout, vout, (int)n, shift, dmask, counts, n_tiles);
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+    }
+    GRTX_CHECK_LAUNCH("radix sort");
+    if (kin != keys) {
+        GRTX_CUDA(cudaMemcpyAsync(keys, kin, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+        GRTX_CUDA(cudaMemcpyAsync(vals, vin, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+    }
+    return GRTX_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Binary radix tree (Karras 2012) and bottom-up bounds.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ int rt_delta(const uint64_t *__restrict__ k, int n, int i, int j)
+{
+    if (j < 0 || j >= n) return -1;
+    uint64_t a = k[i], b = k[j];
+    if (a != b) return __clzll((long long)(a ^ b));
+    return 64 + __clz((int)((unsigned)i ^ (unsigned)j));
+}
+
+__global__ void k_radix_tree(const uint64_t *__restrict__ k, int n, uint32_t *__restrict__ left,
+                             uint32_t *__restrict__ right, uint32_t *__restrict__ parent)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int d = (rt_delta(k, n, i, i + 1) - rt_delta(k, n, i, i - 1)) > 0 ? 1 : -1;
+    int dmin = rt_delta(k, n, i, i - d);
+    int lmax = 2;
+    while (rt_delta(k, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (rt_delta(k, n, i, i + (l + t) * d) > dmin) l += t;
+    int j = i + l * d;
+    int dnode = rt_delta(k, n, i, j);
+    int s = 0;
+    for (int div = 2;; div <<= 1) {
+        int t = (l + div - 1) / div;
+        if (rt_delta(k, n, i, i + (s + t) * d) > dnode) s += t;
+        if (t <= 1) break;
+    }
+    int gamma = i + s * d + min(d, 0);
+    uint32_t L = (min(i, j) == gamma) ? (GRTX_LEAF | (uint32_t)gamma) : (uint32_t)gamma;
+    uint32_t R = (max(i, j) == gamma + 1) ? (GRTX_LEAF | (uint32_t)(gamma + 1)) : (uint32_t)(gamma + 1);
+    left[i] = L;
+    right[i] = R;
+    parent[(L & GRTX_LEAF) ? (n - 1 + (L & ~GRTX_LEAF)) : L] = (uint32_t)i;
+    parent[(R & GRTX_LEAF) ? (n - 1 + (R & ~GRTX_LEAF)) : R] = (uint32_t)i;
+    if (i == 0) parent[0] = GRTX_NONE;
+}
+
+__device__ __forceinline__ void load_box(uint32_t ref, const float *__restrict__ leaf_aabb,
+                                         const float *node_aabb, float b[6])
+{
+    if (ref & GRTX_LEAF) {
+        const float *p = leaf_aabb + 6 * (size_t)(ref & ~GRTX_LEAF);
+        for (int c = 0; c < 6; ++c) b[c] = p[c];
+    } else {
+        const float *p = node_aabb + 6 * (size_t)ref;
+        for (int c = 0; c < 6; ++c) b[c] = __ldcg(p + c);   // written by another thread: bypass L1
+    }
+}
+
+__device__ __forceinline__ float load_slack(uint32_t ref, const float *__restrict__ leaf_slack, const float *node_slack)
+{
+    return (ref & GRTX_LEAF) ? leaf_slack[ref & ~GRTX_LEAF] : __ldcg(node_slack + ref);
+}
+
+// leaf_slack / node_slack (optional): a per-leaf scalar propagated as the maximum over each
+// subtree (the proxy form's largest proxy diameter).
+__global__ void k_refit(const uint32_t *__restrict__ left, const uint32_t *__restrict__ right,
+                        const uint32_t *__restrict__ parent, const float *__restrict__ leaf_aabb, int n,
+                        float *node_aabb, uint32_t *counters, const float *__restrict__ leaf_slack = nullptr,
+                        float *node_slack = nullptr)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    uint32_t node = parent[n - 1 + j];
+    while (node != GRTX_NONE) {
+        __threadfence();
+        if (atomicAdd(&counters[node], 1u) == 0u) return;   // the sibling subtree is not done yet
+        __threadfence();
+        float a[6], b[6];
+        load_box(left[node], leaf_aabb, node_aabb, a);
+        load_box(right[node], leaf_aabb, node_aabb, b);
+        float *out = node_aabb + 6 * (size_t)node;
+        for (int c = 0; c < 3; ++c) {
+            __stcg(out + c, fminf(a[c], b[c]));
+            __stcg(out + 3 + c, fmaxf(a[3 + c], b[3 + c]));
+        }
+        if (node_slack)
+            __stcg(node_slack + node, fmaxf(load_slack(left[node], leaf_slack, node_slack),
+                                            load_slack(right[node], leaf_slack, node_slack)));
+        node = parent[node];
+    }
+}
+
+__global__ void k_depth(const uint32_t *__restrict__ parent, int n, int *__restrict__ max_depth)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int d = 0;
+    uint32_t node = parent[n - 1 + j];
+    while (node != GRTX_NONE && d < 100000) { ++d; node = parent[node]; }
+    atomicMax(max_depth, d);
+}
+
+// BVH2 node: child 0 box, child 1 box, child refs (see grtx_scene_export).
+__global__ void k_emit_nodes(const uint32_t *__restrict__ left, const uint32_t *__restrict__ right,
+                             const float *__restrict__ leaf_aabb, const float *__restrict__ node_aabb, int n,
+                             float4 *__restrict__ nodes, const float *__restrict__ leaf_slack,
+                             const float *__restrict__ node_slack)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    float a[6], b[6];
+    uint32_t L = left[i], R = right[i];
+    load_box(L, leaf_aabb, node_aabb, a);
+    load_box(R, leaf_aabb, node_aabb, b);
+    nodes[4 * (size_t)i + 0] = make_float4(a[0], a[1], a[2], a[3]);
+    nodes[4 * (size_t)i + 1] = make_float4(a[4], a[5], b[0], b[1]);
+    nodes[4 * (size_t)i + 2] = make_float4(b[2], b[3], b[4], b[5]);
+    float s0 = 0.f, s1 = 0.f;
+    if (leaf_slack) {
+        s0 = load_slack(L, leaf_slack, node_slack);
+        s1 = load_slack(R, leaf_slack, node_slack);
+    }
+    nodes[4 * (size_t)i + 3] = make_float4(__uint_as_float(L), __uint_as_float(R), s0, s1);
+}
+
+// One-leaf scene: a root whose second child is an empty box that no ray hits.
+__global__ void k_emit_single(const float *__restrict__ leaf_aabb, float4 *__restrict__ nodes)
+{
+    const float *a = leaf_aabb;
+    nodes[0] = make_float4(a[0], a[1], a[2], a[3]);
+    nodes[1] = make_float4(a[4], a[5], INFINITY, INFINITY);
+    nodes[2] = make_float4(INFINITY, -INFINITY, -INFINITY, -INFINITY);
+    nodes[3] = make_float4(__uint_as_float(GRTX_LEAF | 0u), __uint_as_float(GRTX_NONE), 0.f, 0.f);
+}
+
+__global__ void k_count_valid(const uint64_t *codes, int64_t n, unsigned long long *out)
+{
+    unsigned long long c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        c += codes[i] != ~0ull;
+    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+// ------------------------------------------------------------------------------------------
+// Leaf-order gather of Gaussian records and appearance.
+// ------------------------------------------------------------------------------------------
+__global__ void k_gather_gaussians(const uint32_t *__restrict__ order, int64_t n_valid,
+                                   const float4 *__restrict__ geom_in, const float *__restrict__ aabb_in,
+                                   const float *__restrict__ sh, int n_sh, int app_stride,
+                                   float4 *__restrict__ geom, float *__restrict__ aabb,
+                                   float *__restrict__ app, uint32_t *__restrict__ gid)
+{
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_valid) return;
+    uint32_t i = order[s];
+    for (int r = 0; r < 4; ++r) geom[4 * s + r] = geom_in[4 * (size_t)i + r];
+    for (int c = 0; c < 6; ++c) aabb[6 * s + c] = aabb_in[6 * (size_t)i + c];
+    const float *src = sh + (size_t)i * n_sh;
+    float *dst = app + (size_t)s * app_stride;
+    for (int c = 0; c < app_stride; ++c) dst[c] = c < n_sh ? src[c] : 0.f;
+    gid[s] = i;
+}
+
+// ------------------------------------------------------------------------------------------
+// Proxy form: 20-triangle icosahedron around each Gaussian (Sec. III-C Observation I).
+// ------------------------------------------------------------------------------------------
+__constant__ float c_ico_v[12][3];
+__constant__ int c_ico_f[20][3];
+
+__global__ void k_proxy_expand(const float4 *__restrict__ geom_sorted, const float *__restrict__ means,
+                               const float *__restrict__ log_scales, const float *__restrict__ quats,
+                               const uint32_t *__restrict__ gid, int64_t n_valid, float ico_circ,
+                               float4 *__restrict__ tris, float *__restrict__ tri_aabb, float *__restrict__ tri_slack)
+{
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_valid) return;
+    uint32_t i = gid[s];
+    float4 g3 = geom_sorted[4 * s + 3];
+    float kap = sqrtf(-2.0f * g3.y / 1.4426950408889634f);
+    float mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
+    float sc[3] = {expf(log_scales[3 * i]) * kap, expf(log_scales[3 * i + 1]) * kap,
+                   expf(log_scales[3 * i + 2]) * kap};
+    float w = quats[4 * i], x = quats[4 * i + 1], y = quats[4 * i + 2], z = quats[4 * i + 3];
+    float inv = rsqrtf(w * w + x * x + y * y + z * z);
+    w *= inv; x *= inv; y *= inv; z *= inv;
+    float R[3][3] = {{1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y)},
+                     {2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x)},
+                     {2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)}};
+    // every point of the proxy lies within kappa * max(s) * circumradius of the mean
+    float diam = 2.0f * ico_circ * fmaxf(sc[0], fmaxf(sc[1], sc[2])) * (1.0f + 1e-4f);
+    float V[12][3];
+    for (int v = 0; v < 12; ++v)
+        for (int a = 0; a < 3; ++a)
+            V[v][a] = mu[a] + R[a][0] * sc[0] * c_ico_v[v][0] + R[a][1] * sc[1] * c_ico_v[v][1] +
+                      R[a][2] * sc[2] * c_ico_v[v][2];
+    for (int f = 0; f < 20; ++f) {
+        const float *p0 = V[c_ico_f[f][0]], *p1 = V[c_ico_f[f][1]], *p2 = V[c_ico_f[f][2]];
+        size_t t = (size_t)s * 20 + f;
+        tris[3 * t + 0] = make_float4(p0[0], p0[1], p0[2], __uint_as_float((uint32_t)s));
+        tris[3 * t + 1] = make_float4(p1[0], p1[1], p1[2], 0.f);
+        tris[3 * t + 2] = make_float4(p2[0], p2[1], p2[2], 0.f);
+        tri_slack[t] = diam;
+        float *bb = tri_aabb + 6 * t;
+        for (int a = 0; a < 3; ++a) {
+            float lo = fminf(p0[a], fminf(p1[a], p2[a])), hi = fmaxf(p0[a], fmaxf(p1[a], p2[a]));
+            float pad = 1e-6f * (hi - lo) + 1e-7f * fabsf(lo) + 1e-7f * fabsf(hi);
+            bb[a] = lo - pad;
+            bb[3 + a] = hi + pad;
+        }
+    }
+}
+
+__global__ void k_gather_tris(const uint32_t *__restrict__ order, int64_t n, const float4 *__restrict__ tin,
+                              const float *__restrict__ ain, const float *__restrict__ slack_in,
+                              const uint32_t *__restrict__ gid, float4 *__restrict__ tout, float *__restrict__ aout,
+                              float *__restrict__ slack_out, uint32_t *__restrict__ leaf_ids)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    uint32_t src = order[t];
+    slack_out[t] = slack_in[src];
+    for (int r = 0; r < 3; ++r) tout[3 * t + r] = tin[3 * (size_t)src + r];
+    for (int c = 0; c < 6; ++c) aout[6 * t + c] = ain[6 * (size_t)src + c];
+    leaf_ids[t] = gid[__float_as_uint(tin[3 * (size_t)src].w)];
+}
+
+bool g_ico_ready = false;
+float g_ico_circ = 0.f;   // circumradius of the uploaded proxy in unit-sphere units
+
+int upload_icosahedron(cudaStream_t s)
+{
+    // Regular icosahedron from the cyclic permutations of (0, +-1, +-phi), scaled so that its
+    // inradius is 1 + 1e-3: it encloses the unit sphere with a margin for FP32 rounding.
+    const double phi = (1.0 + std::sqrt(5.0)) / 2.0;
+    std::vector<std::array<double, 3>> v;
+    for (int s1 = -1; s1 <= 1; s1 += 2)
+        for (int s2 = -1; s2 <= 1; s2 += 2) {
+            v.push_back({0.0, (double)s1, s2 * phi});
+            v.push_back({(double)s1, s2 * phi, 0.0});
+            v.push_back({s2 * phi, 0.0, (double)s1});
+        }
+    // faces: vertex triples that are pairwise at the edge length 2
+    std::vector<std::array<int, 3>> f;
+    auto d2 = [&](int a, int b) {
+        double s = 0;
+        for (int c = 0; c < 3; ++c) s += (v[a][c] - v[b][c]) * (v[a][c] - v[b][c]);
+        return s;
+    };
+    for (int a = 0; a < 12; ++a)
+        for (int b = a + 1; b < 12; ++b)
+            for (int c = b + 1; c < 12; ++c)
+                if (std::fabs(d2(a, b) - 4) < 1e-9 && std::fabs(d2(b, c) - 4) < 1e-9 && std::fabs(d2(a, c) - 4) < 1e-9)
+                    f.push_back({a, b, c});
+    if (f.size() != 20) return grtx_fail(GRTX_ERR_CUDA, "icosahedron face enumeration failed");
+    // inradius of this icosahedron: distance from the origin to a face plane
+    const double* p0 = v[f[0][0]].data(); const double* p1 = v[f[0][1]].data(); const double* p2 = v[f[0][2]].data();
+    double e1[3], e2[3], nrm[3];
+    for (int c = 0; c < 3; ++c) { e1[c] = p1[c] - p0[c]; e2[c] = p2[c] - p0[c]; }
+    nrm[0] = e1[1] * e2[2] - e1[2] * e2[1]; nrm[1] = e1[2] * e2[0] - e1[0] * e2[2]; nrm[2] = e1[0] * e2[1] - e1[1] * e2[0];
+    double nl = std::sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+    double inr = std::fabs(nrm[0] * p0[0] + nrm[1] * p0[1] + nrm[2] * p0[2]) / nl;
+    static float hv[12][3];   // static: the async copies below read them after return
+    static int hf[20][3];
+    for (int a = 0; a < 12; ++a)
+        for (int c = 0; c < 3; ++c) hv[a][c] = (float)(v[a][c] * (1.0 + 1e-3) / inr);
+    g_ico_circ = (float)(std::sqrt(1.0 + phi * phi) * (1.0 + 1e-3) / inr);
+    for (int a = 0; a < 20; ++a)
+        for (int c = 0; c < 3; ++c) hf[a][c] = f[a][c];
+    GRTX_CUDA(cudaMemcpyToSymbolAsync(c_ico_v, hv, sizeof(hv), 0, cudaMemcpyHostToDevice, s));
+    GRTX_CUDA(cudaMemcpyToSymbolAsync(c_ico_f, hf, sizeof(hf), 0, cudaMemcpyHostToDevice, s));
+    return GRTX_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Stream-ordered allocation helper.
+// ------------------------------------------------------------------------------------------
+struct Alloc {
+    cudaStream_t s;
+    std::vector<void *> tmp;
+    explicit Alloc(cudaStream_t st) : s(st) {}
+    template <class T>
+    int get(T **p, size_t count, bool temp)
+    {
+        size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+        cudaError_t e = cudaMallocAsync((void **)p, bytes, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            *p = nullptr;
+            return grtx_fail(GRTX_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+        }
+        if (temp) tmp.push_back(*p);
+        return GRTX_OK;
+    }
+    ~Alloc()
+    {
+        for (void *p : tmp) cudaFreeAsync(p, s);
+    }
+};
+
+#define TRY(x)                         \
+    do {                               \
+        int st__ = (x);                \
+        if (st__ != GRTX_OK) return st__; \
+    } while (0)
+
+void free_scene_arrays(grtx_scene *sc)
+{
+    cudaStream_t s = sc->stream;
+    void *ptrs[] = {sc->nodes, sc->geom, sc->tris, sc->app, sc->gid, sc->leaf_ids, sc->codes, sc->ws, sc->d_counter};
+    for (void *p : ptrs)
+        if (p) cudaFreeAsync(p, s);
+}
+
+// Morton -> sort -> radix tree -> refit -> nodes over n leaf boxes (sorted in place with
+// `order`). Writes sc->nodes, sc->codes, sc->depth.
+int build_tree(grtx_scene *sc, Alloc &A, float *leaf_aabb, int64_t n, uint32_t *order, uint64_t *codes,
+               float *bounds_dev)
+{
+    cudaStream_t s = sc->stream;
+    int blocks = grtx_div_up(n, kThreads);
+    k_init_bounds<<<1, 32, 0, s>>>(bounds_dev);
+    k_centroid_bounds<<<std::min(blocks, 4096), kThreads, 0, s>>>(leaf_aabb, n, bounds_dev);
+    k_morton<<<blocks, kThreads, 0, s>>>(leaf_aabb, n, bounds_dev, codes, order);
+    GRTX_CHECK_LAUNCH("morton");
+    void *stmp;
+    TRY(A.get((char **)&stmp, sort_layout(n).total, true));
+    TRY(sort_pairs(codes, order, n, 64, stmp, s));
+    return GRTX_OK;
+}
+
+int finish_tree(grtx_scene *sc, Alloc &A, const float *leaf_aabb_sorted, int64_t n, const float *leaf_slack = nullptr)
+{
+    cudaStream_t s = sc->stream;
+    int64_t n_nodes = std::max<int64_t>(n - 1, 1);
+    TRY(A.get(&sc->nodes, (size_t)n_nodes * 4, false));
+    sc->n_nodes = n_nodes;
+    int *d_depth;
+    TRY(A.get(&d_depth, 1, true));
+    GRTX_CUDA(cudaMemsetAsync(d_depth, 0, sizeof(int), s));
+    if (n == 1) {
+        k_emit_single<<<1, 1, 0, s>>>(leaf_aabb_sorted, sc->nodes);
+    } else {
+        uint32_t *left, *right, *parent, *cnt;
+        float *node_aabb, *node_slack = nullptr;
+        if (leaf_slack) TRY(A.get(&node_slack, n - 1, true));
+        TRY(A.get(&left, n - 1, true));
+        TRY(A.get(&right, n - 1, true));
+        TRY(A.get(&parent, 2 * n - 1, true));
+        TRY(A.get(&cnt, n - 1, true));
+        TRY(A.get(&node_aabb, 6 * (n - 1), true));
+        GRTX_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (n - 1), s));
+        k_radix_tree<<<grtx_div_up(n - 1, kThreads), kThreads, 0, s>>>(sc->codes, (int)n, left, right, parent);
+        k_refit<<<grtx_div_up(n, kThreads), kThreads, 0, s>>>(left, right, parent, leaf_aabb_sorted, (int)n,
+                                                              node_aabb, cnt, leaf_slack, node_slack);
+        k_depth<<<grtx_div_up(n, kThreads), kThreads, 0, s>>>(parent, (int)n, d_depth);
+        k_emit_nodes<<<grtx_div_up(n - 1, kThreads), kThreads, 0, s>>>(left, right, leaf_aabb_sorted, node_aabb,
+                                                                       (int)n, sc->nodes, leaf_slack, node_slack);
+        GRTX_CHECK_LAUNCH("radix tree / refit");
+    }
+    int h_depth = 0;
+    GRTX_CUDA(cudaMemcpyAsync(&h_depth, d_depth, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GRTX_CUDA(cudaStreamSynchronize(s));
+    sc->depth = n == 1 ? 1 : h_depth;
+    return GRTX_OK;
+}
+
+int build_scene(const grtx_gaussians *g, const grtx_params *p, int form, grtx_scene *sc)
+{
+    cudaStream_t s = sc->stream;
+    Alloc A(s);
+    int64_t n = g->n;
+    sc->n = n;
+    sc->form = form;
+    sc->sh_degree = g->sh_degree;
+    sc->n_coef = (g->sh_degree + 1) * (g->sh_degree + 1);
+    int n_sh = sc->n_coef * 3;
+    sc->app_stride = (n_sh + 3) & ~3;
+    sc->alpha_min = p->alpha_min;
+    TRY(A.get(&sc->d_counter, 8, false));
+    GRTX_CUDA(cudaMemsetAsync(sc->d_counter, 0, 8 * sizeof(unsigned), s));
+    if (n == 0) {
+        sc->n_valid = sc->n_leaves = 0;
+        sc->n_nodes = 0;
+        return GRTX_OK;
+    }
+    float4 *geom_raw;
+    float *aabb_raw, *bounds_dev;
+    uint64_t *codes;
+    uint32_t *order;
+    TRY(A.get(&geom_raw, 4 * n, true));
+    TRY(A.get(&aabb_raw, 6 * n, true));
+    TRY(A.get(&bounds_dev, 6, true));
+    TRY(A.get(&codes, n, true));
+    TRY(A.get(&order, n, true));
+    int blocks = grtx_div_up(n, kThreads);
+    k_prep<<<blocks, kThreads, 0, s>>>(g->means, g->log_scales, g->quats, g->opacity_logits, n, p->alpha_min,
+                                       geom_raw, aabb_raw);
+    GRTX_CHECK_LAUNCH("prep");
+    TRY(build_tree(sc, A, aabb_raw, n, order, codes, bounds_dev));
+    // number of valid Gaussians: their codes sort before the 2^64-1 of the empty boxes
+    unsigned long long *d_nvalid;
+    TRY(A.get(&d_nvalid, 1, true));
+    GRTX_CUDA(cudaMemsetAsync(d_nvalid, 0, 8, s));
+    k_count_valid<<<std::min(blocks, 4096), kThreads, 0, s>>>(codes, n, d_nvalid);
+    unsigned long long h_nvalid = 0;
+    GRTX_CUDA(cudaMemcpyAsync(&h_nvalid, d_nvalid, 8, cudaMemcpyDeviceToHost, s));
+    GRTX_CUDA(cudaStreamSynchronize(s));
+    int64_t nv = (int64_t)h_nvalid;
+    sc->n_valid = nv;
+    if (nv == 0) {
+        sc->n_leaves = 0;
+        sc->n_nodes = 0;
+        return GRTX_OK;
+    }
+    float *leaf_aabb;
+    TRY(A.get(&sc->geom, 4 * nv, false));
+    TRY(A.get(&sc->app, (size_t)sc->app_stride * nv, false));
+    TRY(A.get(&sc->gid, nv, false));
+    TRY(A.get(&leaf_aabb, 6 * nv, true));
+    k_gather_gaussians<<<grtx_div_up(nv, kThreads), kThreads, 0, s>>>(order, nv, geom_raw, aabb_raw, g->sh, n_sh,
+                                                                      sc->app_stride, sc->geom, leaf_aabb,
+                                                                      sc->app, sc->gid);
+    GRTX_CHECK_LAUNCH("gather");
+    if (form == GRTX_FORM_SPHERE) {
+        sc->n_leaves = nv;
+        TRY(A.get(&sc->codes, nv, false));
+        GRTX_CUDA(cudaMemcpyAsync(sc->codes, codes, (size_t)nv * 8, cudaMemcpyDeviceToDevice, s));
+        TRY(A.get(&sc->leaf_ids, nv, false));
+        GRTX_CUDA(cudaMemcpyAsync(sc->leaf_ids, sc->gid, (size_t)nv * 4, cudaMemcpyDeviceToDevice, s));
+        TRY(finish_tree(sc, A, leaf_aabb, nv));
+    } else {
+        if (!g_ico_ready) {
+            TRY(upload_icosahedron(s));
+            g_ico_ready = true;
+        }
+        int64_t nt = 20 * nv;
+        if (nt >= (int64_t)1 << 31) return grtx_fail(GRTX_ERR_INVALID_ARG, "too many proxy triangles");
+        float4 *tris_raw;
+        float *tri_aabb_raw, *tri_aabb, *slack_raw, *slack;
+        uint64_t *tcodes;
+        uint32_t *torder;
+        TRY(A.get(&tris_raw, 3 * nt, true));
+        TRY(A.get(&tri_aabb_raw, 6 * nt, true));
+        TRY(A.get(&slack_raw, nt, true));
+        TRY(A.get(&slack, nt, true));
+        TRY(A.get(&tcodes, nt, true));
+        TRY(A.get(&torder, nt, true));
+        k_proxy_expand<<<grtx_div_up(nv, kThreads), kThreads, 0, s>>>(sc->geom, g->means, g->log_scales, g->quats,
+                                                                      sc->gid, nv, g_ico_circ, tris_raw,
+                                                                      tri_aabb_raw, slack_raw);
+        GRTX_CHECK_LAUNCH("proxy expand");
+        TRY(build_tree(sc, A, tri_aabb_raw, nt, torder, tcodes, bounds_dev));
+        sc->n_leaves = nt;
+        TRY(A.get(&sc->tris, 3 * nt, false));
+        TRY(A.get(&tri_aabb, 6 * nt, true));
+        TRY(A.get(&sc->leaf_ids, nt, false));
+        k_gather_tris<<<grtx_div_up(nt, kThreads), kThreads, 0, s>>>(torder, nt, tris_raw, tri_aabb_raw, slack_raw,
+                                                                     sc->gid, sc->tris, tri_aabb, slack, sc->leaf_ids);
+        GRTX_CHECK_LAUNCH("gather triangles");
+        TRY(A.get(&sc->codes, nt, false));
+        GRTX_CUDA(cudaMemcpyAsync(sc->codes, tcodes, (size_t)nt * 8, cudaMemcpyDeviceToDevice, s));
+        TRY(finish_tree(sc, A, tri_aabb, nt, slack));
+    }
+    // world bounds of all leaves = union of the root's two child boxes
+    float h_root[16];
+    GRTX_CUDA(cudaMemcpyAsync(h_root, sc->nodes, sizeof(h_root), cudaMemcpyDeviceToHost, s));
+    GRTX_CUDA(cudaStreamSynchronize(s));
+    float a[6] = {h_root[0], h_root[1], h_root[2], h_root[3], h_root[4], h_root[5]};
+    float b[6] = {h_root[6], h_root[7], h_root[8], h_root[9], h_root[10], h_root[11]};
+    for (int c = 0; c < 3; ++c) {
+        sc->bounds[c] = std::min(a[c], b[c]);
+        sc->bounds[3 + c] = std::max(a[3 + c], b[3 + c]);
+    }
+    if (sc->depth >= GRTX_STACK)
+        return grtx_fail(GRTX_ERR_OVERFLOW_FATAL, "BVH depth " + std::to_string(sc->depth) +
+                                                      " exceeds the traversal stack");
+    return GRTX_OK;
+}
+
+}  // namespace
+
+size_t grtx_scan_temp_bytes(int64_t m)
+{
+    size_t total = 0;
+    while (m > kScanTile) {
+        m = (m + kScanTile - 1) / kScanTile;
+        total += ((size_t)m * 4 + 255) & ~(size_t)255;
+    }
+    return total + 256;
+}
+
+int grtx_scan_exclusive(uint32_t *d, int64_t m, void *temp, cudaStream_t s)
+{
+    if (m <= 0) return GRTX_OK;
+    if (m <= kScanTile) {
+        k_scan_tiles<<<1, kScanThreads, 0, s>>>(d, m, nullptr);
+        return GRTX_OK;
+    }
+    int64_t tiles = (m + kScanTile - 1) / kScanTile;
+    uint32_t *sums = (uint32_t *)temp;
+    char *rest = (char *)temp + (((size_t)tiles * 4 + 255) & ~(size_t)255);
+    k_scan_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(d, m, sums);
+    int st = grtx_scan_exclusive(sums, tiles, rest, s);
+    if (st != GRTX_OK) return st;
+    k_scan_add<<<(unsigned)tiles, kScanThreads, 0, s>>>(d, m, sums);
+    return GRTX_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// ABI entry points of the build.
+// ------------------------------------------------------------------------------------------
+static int check_gaussians(const grtx_gaussians *g)
+{
+    if (!g) return grtx_fail(GRTX_ERR_INVALID_ARG, "gaussians is NULL");
+    if (g->n < 0 || g->n >= ((int64_t)1 << 31)) return grtx_fail(GRTX_ERR_INVALID_ARG, "n out of range");
+    if (g->sh_degree < 0 || g->sh_degree > 3) return grtx_fail(GRTX_ERR_INVALID_ARG, "sh_degree must be 0..3");
+    if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh))
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "a parameter array is NULL");
+    return GRTX_OK;
+}
+
+extern "C" GRTX_API int grtx_prep_gaussians(const grtx_gaussians *g, float alpha_min, float *d_geom, float *d_aabb,
+                                            void *stream)
+{
+    int st = check_gaussians(g);
+    if (st) return st;
+    if (!(alpha_min > 0.f && alpha_min < 1.f)) return grtx_fail(GRTX_ERR_INVALID_ARG, "alpha_min must be in (0,1)");
+    if (g->n == 0) return GRTX_OK;
+    if (!d_geom || !d_aabb || ((uintptr_t)d_geom & 15)) return grtx_fail(GRTX_ERR_INVALID_ARG, "bad output pointer");
+    k_prep<<<grtx_div_up(g->n, kThreads), kThreads, 0, S(stream)>>>(g->means, g->log_scales, g->quats,
+                                                                     g->opacity_logits, g->n, alpha_min,
+                                                                     (float4 *)d_geom, d_aabb);
+    GRTX_CHECK_LAUNCH("grtx_prep_gaussians");
+    return GRTX_OK;
+}
+
+extern "C" GRTX_API int grtx_morton_codes(const float *d_aabb, int64_t n, const float *d_bounds, float *d_bounds_out,
+                                          uint64_t *d_codes, void *stream)
+{
+    if (n < 0 || n >= ((int64_t)1 << 31)) return grtx_fail(GRTX_ERR_INVALID_ARG, "n out of range");
+    if (n == 0) return GRTX_OK;
+    if (!d_aabb || !d_codes) return grtx_fail(GRTX_ERR_INVALID_ARG, "NULL pointer");
+    cudaStream_t s = S(stream);
+    const float *bounds = d_bounds;
+    float *tmp = nullptr;
+    if (!bounds) {
+        float *b = d_bounds_out;
+        if (!b) {
+            GRTX_CUDA(cudaMallocAsync((void **)&tmp, 6 * sizeof(float), s));
+            b = tmp;
+        }
+        k_init_bounds<<<1, 32, 0, s>>>(b);
+        k_centroid_bounds<<<std::min(grtx_div_up(n, kThreads), 4096), kThreads, 0, s>>>(d_aabb, n, b);
+        bounds = b;
+    }
+    k_morton<<<grtx_div_up(n, kThreads), kThreads, 0, s>>>(d_aabb, n, bounds, d_codes, nullptr);
+    if (tmp) cudaFreeAsync(tmp, s);
+    GRTX_CHECK_LAUNCH("grtx_morton_codes");
+    return GRTX_OK;
+}
+
+extern "C" GRTX_API int grtx_sort_pairs(uint64_t *d_keys, uint32_t *d_values, int64_t n, int key_bits, void *d_temp,
+                                        size_t *temp_bytes, void *stream)
+{
+    if (!temp_bytes) return grtx_fail(GRTX_ERR_INVALID_ARG, "temp_bytes is NULL");
+    if (n < 0 || n >= ((int64_t)1 << 31)) return grtx_fail(GRTX_ERR_INVALID_ARG, "n out of range");
+    if (key_bits < 1 || key_bits > 64) return grtx_fail(GRTX_ERR_INVALID_ARG, "key_bits must be 1..64");
+    size_t need = sort_layout(std::max<int64_t>(n, 1)).total;
+    if (!d_temp) {
+        *temp_bytes = need;
+        return GRTX_OK;
+    }
+    if (*temp_bytes < need) return grtx_fail(GRTX_ERR_INVALID_ARG, "temp buffer too small");
+    if (n > 1 && (!d_keys || !d_values)) return grtx_fail(GRTX_ERR_INVALID_ARG, "NULL pointer");
+    return sort_pairs(d_keys, d_values, n, key_bits, d_temp, S(stream));
+}
+
+extern "C" GRTX_API int grtx_radix_tree(const uint64_t *d_sorted_keys, int64_t n, uint32_t *d_left, uint32_t *d_right,
+                                        uint32_t *d_parent, void *stream)
+{
+    if (n < 2 || n >= ((int64_t)1 << 30)) return grtx_fail(GRTX_ERR_INVALID_ARG, "n must be in [2, 2^30)");
+    if (!d_sorted_keys || !d_left || !d_right || !d_parent) return grtx_fail(GRTX_ERR_INVALID_ARG, "NULL pointer");
+    k_radix_tree<<<grtx_div_up(n - 1, kThreads), kThreads, 0, S(stream)>>>(d_sorted_keys, (int)n, d_left, d_right,
+                                                                             d_parent);
+    GRTX_CHECK_LAUNCH("grtx_radix_tree");
+    return GRTX_OK;
+}
+
+extern "C" GRTX_API int grtx_refit(const uint32_t *d_left, const uint32_t *d_right, const uint32_t *d_parent,
+                                   const float *d_leaf_aabb, int64_t n, float *d_node_aabb, uint32_t *d_counters,
+                                   void *stream)
+{
+    if (n < 2 || n >= ((int64_t)1 << 30)) return grtx_fail(GRTX_ERR_INVALID_ARG, "n must be in [2, 2^30)");
+    if (!d_left || !d_right || !d_parent || !d_leaf_aabb || !d_node_aabb || !d_counters)
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "NULL pointer");
+    cudaStream_t s = S(stream);
+    GRTX_CUDA(cudaMemsetAsync(d_counters, 0, sizeof(uint32_t) * (n - 1), s));
+    k_refit<<<grtx_div_up(n, kThreads), kThreads, 0, s>>>(d_left, d_right, d_parent, d_leaf_aabb, (int)n,
+                                                           d_node_aabb, d_counters);
+    GRTX_CHECK_LAUNCH("grtx_refit");
+    return GRTX_OK;
+}
+
+extern "C" GRTX_API int grtx_build_bvh(const grtx_gaussians *g, const grtx_params *p, int form, void *stream,
+                                       grtx_scene **out)
+{
+    int st = check_gaussians(g);
+    if (st) return st;
+    if (!p || !out) return grtx_fail(GRTX_ERR_INVALID_ARG, "params or out is NULL");
+    if (form != GRTX_FORM_SPHERE && form != GRTX_FORM_PROXY20) return grtx_fail(GRTX_ERR_INVALID_ARG, "unknown form");
+    if (!(p->alpha_min > 0.f && p->alpha_min < 1.f)) return grtx_fail(GRTX_ERR_INVALID_ARG, "alpha_min must be in (0,1)");
+    grtx_scene *sc = new (std::nothrow) grtx_scene();
+    if (!sc) return grtx_fail(GRTX_ERR_OOM, "host allocation failed");
+    sc->stream = S(stream);
+    st = build_scene(g, p, form, sc);
+    if (st != GRTX_OK) {
+        free_scene_arrays(sc);
+        cudaStreamSynchronize(sc->stream);
+        delete sc;
+        return st;
+    }
+    *out = sc;
+    return GRTX_OK;
+}
+
+extern "C" GRTX_API int grtx_scene_info_get(const grtx_scene *sc, grtx_scene_info *info)
+{
+    if (!sc || !info) return grtx_fail(GRTX_ERR_INVALID_ARG, "NULL pointer");
+    std::memset(info, 0, sizeof(*info));
+    info->n_gaussians = sc->n;
+    info->n_valid = sc->n_valid;
+    info->n_leaves = sc->n_leaves;
+    info->n_nodes = sc->n_nodes;
+    info->depth = sc->depth;
+    info->form = sc->form;
+    info->sh_degree = sc->sh_degree;
+    info->bytes_nodes = sc->n_nodes * 64;
+    info->bytes_leaves = sc->form == GRTX_FORM_SPHERE ? sc->n_valid * 64 : sc->n_leaves * 48 + sc->n_valid * 64;
+    info->bytes_appearance = sc->n_valid * sc->app_stride * 4;
+    info->bytes_workspace = (int64_t)sc->ws_bytes;
+    for (int c = 0; c < 6; ++c) info->bounds[c] = sc->bounds[c];
+    return GRTX_OK;
+}
+
+extern "C" GRTX_API int grtx_scene_export(const grtx_scene *sc, float *d_nodes, uint32_t *d_leaf_ids, uint64_t *d_codes,
+                                          void *stream)
+{
+    if (!sc) return grtx_fail(GRTX_ERR_INVALID_ARG, "scene is NULL");
+    cudaStream_t s = S(stream);
+    if (d_nodes && sc->n_nodes)
+        GRTX_CUDA(cudaMemcpyAsync(d_nodes, sc->nodes, (size_t)sc->n_nodes * 64, cudaMemcpyDeviceToDevice, s));
+    if (d_leaf_ids && sc->n_leaves)
+        GRTX_CUDA(cudaMemcpyAsync(d_leaf_ids, sc->leaf_ids, (size_t)sc->n_leaves * 4, cudaMemcpyDeviceToDevice, s));
+    if (d_codes && sc->n_leaves)
+        GRTX_CUDA(cudaMemcpyAsync(d_codes, sc->codes, (size_t)sc->n_leaves * 8, cudaMemcpyDeviceToDevice, s));
+    return GRTX_OK;
+}
+
+extern "C" GRTX_API void grtx_scene_destroy(grtx_scene *sc)
+{
+    if (!sc) return;
+    free_scene_arrays(sc);
+    cudaStreamSynchronize(sc->stream);
+    delete sc;
+}

@@ -1,0 +1,346 @@
+// Serving: several resident scenes and a stream of camera requests. Requests are admitted
+// into a bounded set of slots as earlier ones finish (continuous batching); each step is one
+// persistent launch whose queue concatenates pieces of every admitted request (mixed scenes
+// and resolutions), so rays of new and old requests share the device. Two steps may be in
+// flight: the host prepares and enqueues the next while the current one runs.
+#include <cuda_runtime.h>
+#include <time.h>
+
+#include <algorithm>
+#include <deque>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "trace_impl.cuh"
+
+#define GRTX_EXTERN_SERVE(K)                                                                                 \
+    extern template int serve_launch<K>(const TraceArgs &, const ServeSeg *, int, int, cudaStream_t);        \
+    extern template int serve_occupancy<K>(int *);
+GRTX_EXTERN_SERVE(1)
+GRTX_EXTERN_SERVE(2)
+GRTX_EXTERN_SERVE(4)
+GRTX_EXTERN_SERVE(8)
+GRTX_EXTERN_SERVE(16)
+GRTX_EXTERN_SERVE(32)
+
+int grtx_fill_camera(CamRef &a, unsigned &n_items_out, const grtx_camera *cam);
+SceneRef grtx_scene_ref(const grtx_scene *sc);
+int grtx_check_params(const grtx_params *p);
+
+namespace {
+
+constexpr int kMaxPending = 65536;
+constexpr int kSteps = 2;
+
+double now_s()
+{
+    timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
+
+int serve_launch_k(int k, const TraceArgs &a, const ServeSeg *segs, int n, int blocks, cudaStream_t s)
+{
+    switch (k) {
+    case 1: return serve_launch<1>(a, segs, n, blocks, s);
+    case 2: return serve_launch<2>(a, segs, n, blocks, s);
+    case 4: return serve_launch<4>(a, segs, n, blocks, s);
+    case 8: return serve_launch<8>(a, segs, n, blocks, s);
+    case 16: return serve_launch<16>(a, segs, n, blocks, s);
+    default: return serve_launch<32>(a, segs, n, blocks, s);
+    }
+}
+
+int serve_occupancy_k(int k, int *bps)
+{
+    switch (k) {
+    case 1: return serve_occupancy<1>(bps);
+    case 2: return serve_occupancy<2>(bps);
+    case 4: return serve_occupancy<4>(bps);
+    case 8: return serve_occupancy<8>(bps);
+    case 16: return serve_occupancy<16>(bps);
+    default: return serve_occupancy<32>(bps);
+    }
+}
+
+struct SrvReq {
+    grtx_request r;
+    CamRef cam;
+    unsigned n_items = 0;      // queue items of the whole request (32 per warp tile)
+    unsigned next = 0;         // first item not yet scheduled
+    double t_admit = 0;
+};
+
+struct SrvStep {
+    cudaEvent_t ev = nullptr;
+    ServeSeg *h = nullptr;     // pinned host copy of the segment table
+    ServeSeg *d = nullptr;     // device segment table
+    std::vector<SrvReq *> finishing;
+    bool busy = false;
+};
+
+}  // namespace
+
+struct grtx_server {
+    std::vector<grtx_scene *> scenes;
+    grtx_params p;
+    int64_t max_rays = 0;
+    int max_inflight = 0;
+    cudaStream_t s = nullptr;
+    std::deque<SrvReq *> pending;
+    std::deque<SrvReq *> active;
+    SrvStep steps[kSteps];
+    std::deque<int> inflight;
+    std::deque<grtx_completion> backlog;
+    TraceArgs a;
+    int blocks = 0;
+    void *ws = nullptr;
+    unsigned *queue = nullptr;
+};
+
+namespace {
+
+void server_free(grtx_server *v)
+{
+    if (v->s) cudaStreamSynchronize(v->s);
+    for (auto &st : v->steps) {
+        if (st.ev) cudaEventDestroy(st.ev);
+        if (st.h) cudaFreeHost(st.h);
+        if (st.d) cudaFree(st.d);
+    }
+    if (v->ws) cudaFree(v->ws);
+    if (v->queue) cudaFree(v->queue);
+    for (auto *r : v->pending) delete r;
+    for (auto *r : v->active) delete r;
+    delete v;
+}
+
+// Enqueue one step over the admitted requests' unscheduled items (FIFO, up to max_rays).
+int schedule_step(grtx_server *v, int si)
+{
+    SrvStep &st = v->steps[si];
+    st.finishing.clear();
+    int64_t budget = std::max<int64_t>(32, v->max_rays / 32 * 32);
+    unsigned total = 0;
+    int n = 0;
+    for (SrvReq *r : v->active) {
+        if (r->next >= r->n_items) continue;
+        if (budget <= 0) break;
+        unsigned take = (unsigned)std::min<int64_t>((int64_t)(r->n_items - r->next), budget);
+        ServeSeg &g = st.h[n++];
+        g.sc = grtx_scene_ref(v->scenes[r->r.scene_id]);
+        g.cam = r->cam;
+        g.out = (float4 *)r->r.d_rgbT;
+        g.item_begin = r->next;
+        g.step_begin = total;
+        g.count = take;
+        g.pad = 0;
+        r->next += take;
+        total += take;
+        budget -= take;
+        if (r->next >= r->n_items) st.finishing.push_back(r);
+    }
+    if (n == 0) return GRTX_OK;
+    GRTX_CUDA(cudaMemcpyAsync(st.d, st.h, sizeof(ServeSeg) * n, cudaMemcpyHostToDevice, v->s));
+    GRTX_CUDA(cudaMemsetAsync(v->queue, 0, sizeof(unsigned), v->s));
+    TraceArgs a = v->a;
+    a.n_items = total;
+    if (serve_launch_k(v->p.k, a, st.d, n, v->blocks, v->s) != GRTX_OK) {
+        cudaError_t e = cudaGetLastError();
+        return grtx_cuda_fail(e == cudaSuccess ? cudaErrorLaunchFailure : e, "serve step launch");
+    }
+    GRTX_CUDA(cudaEventRecord(st.ev, v->s));
+    st.busy = true;
+    v->inflight.push_back(si);
+    return GRTX_OK;
+}
+
+bool has_unscheduled(const grtx_server *v)
+{
+    for (const SrvReq *r : v->active)
+        if (r->next < r->n_items) return true;
+    return false;
+}
+
+}  // namespace
+
+extern "C" GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scenes, const grtx_params *p,
+                                           int64_t max_rays_per_step, int max_inflight, void *stream,
+                                           grtx_server **out)
+{
+    if (!scenes || n_scenes <= 0 || !out) return grtx_fail(GRTX_ERR_INVALID_ARG, "need scenes and out");
+    int st = grtx_check_params(p);
+    if (st) return st;
+    for (int i = 0; i < n_scenes; ++i) {
+        if (!scenes[i]) return grtx_fail(GRTX_ERR_INVALID_ARG, "scene is NULL");
+        if (scenes[i]->form != GRTX_FORM_SPHERE) return grtx_fail(GRTX_ERR_INVALID_ARG, "serving needs sphere-form scenes");
+        if (scenes[i]->alpha_min != p->alpha_min) return grtx_fail(GRTX_ERR_INVALID_ARG, "alpha_min mismatch");
+    }
+    if (max_rays_per_step < 0 || max_inflight < 0 || max_inflight > 4096)
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "bad server limits");
+    grtx_server *v = new (std::nothrow) grtx_server();
+    if (!v) return grtx_fail(GRTX_ERR_OOM, "host allocation failed");
+    v->scenes.assign(scenes, scenes + n_scenes);
+    v->p = *p;
+    v->max_rays = max_rays_per_step > 0 ? max_rays_per_step : (int64_t)4 << 20;
+    v->max_inflight = max_inflight > 0 ? max_inflight : 64;
+    v->s = reinterpret_cast<cudaStream_t>(stream);
+    TraceArgs &a = v->a;
+    a = TraceArgs{};
+    a.traversal = p->traversal;
+    a.T_min = p->T_min;
+    a.alpha_max = p->alpha_max;
+    a.bg0 = p->bg[0];
+    a.bg1 = p->bg[1];
+    a.bg2 = p->bg[2];
+    a.ckpt_cap = p->ckpt_capacity > 0 ? p->ckpt_capacity : 128;
+    a.evict_cap = p->evict_capacity > 0 ? p->evict_capacity : 64;
+    int bps = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (serve_occupancy_k(p->k, &bps) != GRTX_OK || bps <= 0 || sms <= 0) {
+        server_free(v);
+        return grtx_fail(GRTX_ERR_CUDA, "occupancy query failed");
+    }
+    v->blocks = sms * bps;
+    int n_slots = v->blocks * 128;
+    size_t ws = (size_t)n_slots * (2 * (size_t)a.ckpt_cap + (size_t)a.evict_cap) * sizeof(uint2);
+    cudaError_t e = cudaMalloc(&v->ws, ws);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&v->queue, 4 * sizeof(unsigned));
+    for (int i = 0; i < kSteps && e == cudaSuccess; ++i) {
+        e = cudaEventCreateWithFlags(&v->steps[i].ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&v->steps[i].h, sizeof(ServeSeg) * v->max_inflight);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&v->steps[i].d, sizeof(ServeSeg) * v->max_inflight);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        server_free(v);
+        return grtx_fail(GRTX_ERR_OOM, "server allocation failed");
+    }
+    uint2 *base = (uint2 *)v->ws;
+    a.ck0 = base;
+    a.ck1 = base + (size_t)n_slots * a.ckpt_cap;
+    a.ev = base + (size_t)n_slots * 2 * a.ckpt_cap;
+    a.n_slots = n_slots;
+    a.queue = v->queue;
+    *out = v;
+    return GRTX_OK;
+}
+
+extern "C" GRTX_API int grtx_server_submit(grtx_server *v, const grtx_request *reqs, int n)
+{
+    if (!v || (n > 0 && !reqs) || n < 0) return grtx_fail(GRTX_ERR_INVALID_ARG, "bad submit arguments");
+    if ((int64_t)v->pending.size() + n > kMaxPending) return grtx_fail(GRTX_ERR_BUSY, "pending queue is full");
+    std::vector<SrvReq *> add;
+    for (int i = 0; i < n; ++i) {
+        const grtx_request &q = reqs[i];
+        int st = GRTX_OK;
+        if (q.scene_id < 0 || q.scene_id >= (int)v->scenes.size()) st = grtx_fail(GRTX_ERR_NOT_FOUND, "unknown scene id");
+        else if (!q.d_rgbT || ((uintptr_t)q.d_rgbT & 15)) st = grtx_fail(GRTX_ERR_INVALID_ARG, "bad output buffer");
+        SrvReq *r = nullptr;
+        if (st == GRTX_OK) {
+            r = new (std::nothrow) SrvReq();
+            if (!r) st = grtx_fail(GRTX_ERR_OOM, "host allocation failed");
+        }
+        if (st == GRTX_OK) {
+            r->r = q;
+            st = grtx_fill_camera(r->cam, r->n_items, &q.cam);
+        }
+        if (st != GRTX_OK) {
+            delete r;
+            for (auto *x : add) delete x;
+            return st;
+        }
+        add.push_back(r);
+    }
+    for (auto *r : add) v->pending.push_back(r);
+    return GRTX_OK;
+}
+
+extern "C" GRTX_API int grtx_server_poll(grtx_server *v, grtx_completion *done, int max_done, int *n_done, int wait)
+{
+    if (!v || !n_done || max_done < 0 || (max_done > 0 && !done)) return grtx_fail(GRTX_ERR_INVALID_ARG, "bad poll arguments");
+    *n_done = 0;
+    int got = 0;
+    for (;;) {
+        // completions of finished steps
+        while (!v->inflight.empty()) {
+            SrvStep &st = v->steps[v->inflight.front()];
+            cudaError_t q = cudaEventQuery(st.ev);
+            if (q == cudaErrorNotReady) break;
+            if (q != cudaSuccess) return grtx_cuda_fail(q, "serve step");
+            double t = now_s();
+            for (SrvReq *r : st.finishing) {
+                grtx_completion c;
+                c.tag = r->r.tag;
+                c.status = GRTX_OK;
+                c.reserved = 0;
+                c.t_admit = r->t_admit;
+                c.t_done = t;
+                v->backlog.push_back(c);
+                v->active.erase(std::find(v->active.begin(), v->active.end(), r));
+                delete r;
+                ++got;
+            }
+            st.finishing.clear();
+            st.busy = false;
+            v->inflight.pop_front();
+        }
+        // admission of pending requests into free slots
+        while ((int)v->active.size() < v->max_inflight && !v->pending.empty()) {
+            SrvReq *r = v->pending.front();
+            v->pending.pop_front();
+            r->t_admit = now_s();
+            v->active.push_back(r);
+        }
+        // keep up to two steps enqueued
+        while ((int)v->inflight.size() < kSteps && has_unscheduled(v)) {
+            int si = -1;
+            for (int i = 0; i < kSteps; ++i)
+                if (!v->steps[i].busy) { si = i; break; }
+            if (si < 0) break;
+            int st = schedule_step(v, si);
+            if (st != GRTX_OK) return st;
+        }
+        if (!wait || got > 0 || v->inflight.empty()) break;
+        cudaError_t e = cudaEventSynchronize(v->steps[v->inflight.front()].ev);
+        if (e != cudaSuccess) return grtx_cuda_fail(e, "serve step");
+    }
+    while (*n_done < max_done && !v->backlog.empty()) {
+        done[(*n_done)++] = v->backlog.front();
+        v->backlog.pop_front();
+    }
+    return GRTX_OK;
+}
+
+extern "C" GRTX_API int grtx_render_requests(grtx_server *v, const grtx_request *reqs, int n, grtx_completion *done,
+                                             int *n_done, void *stream)
+{
+    (void)stream;   // all server work runs on the server's stream
+    if (!v || !n_done || (n > 0 && !done)) return grtx_fail(GRTX_ERR_INVALID_ARG, "bad arguments");
+    int st = grtx_server_submit(v, reqs, n);
+    if (st) return st;
+    *n_done = 0;
+    while (*n_done < n) {
+        int got = 0;
+        st = grtx_server_poll(v, done + *n_done, n - *n_done, &got, 1);
+        if (st) return st;
+        *n_done += got;
+        if (got == 0 && v->inflight.empty() && v->active.empty() && v->pending.empty() && v->backlog.empty()) break;
+    }
+    return GRTX_OK;
+}
+
+extern "C" GRTX_API int grtx_server_load(const grtx_server *v, int *n_inflight, int *n_pending)
+{
+    if (!v) return grtx_fail(GRTX_ERR_INVALID_ARG, "server is NULL");
+    if (n_inflight) *n_inflight = (int)v->active.size();
+    if (n_pending) *n_pending = (int)v->pending.size();
+    return GRTX_OK;
+}
+
+extern "C" GRTX_API void grtx_server_destroy(grtx_server *v)
+{
+    if (v) server_free(v);
+}

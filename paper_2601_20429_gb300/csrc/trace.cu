@@ -1,0 +1,296 @@
+// C-ABI entry points of the trace: argument checks, camera set-up, the per-slot workspace
+// and the persistent launch (the kernels themselves are in trace_impl.cuh).
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+#include <string>
+
+#include "trace_impl.cuh"
+
+#define GRTX_EXTERN_TRACE(K)                                                                     \
+    extern template int trace_launch<K>(const TraceArgs &, bool, bool, bool, int, cudaStream_t); \
+    extern template int trace_occupancy<K>(bool, bool, bool, int *);
+GRTX_EXTERN_TRACE(1)
+GRTX_EXTERN_TRACE(2)
+GRTX_EXTERN_TRACE(4)
+GRTX_EXTERN_TRACE(8)
+GRTX_EXTERN_TRACE(16)
+GRTX_EXTERN_TRACE(32)
+
+namespace {
+
+inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+bool valid_k(int k) { return k == 1 || k == 2 || k == 4 || k == 8 || k == 16 || k == 32; }
+
+int launch_k(int k, const TraceArgs &a, bool proxy, bool instr, bool bwd, int blocks, cudaStream_t s)
+{
+    switch (k) {
+    case 1: return trace_launch<1>(a, proxy, instr, bwd, blocks, s);
+    case 2: return trace_launch<2>(a, proxy, instr, bwd, blocks, s);
+    case 4: return trace_launch<4>(a, proxy, instr, bwd, blocks, s);
+    case 8: return trace_launch<8>(a, proxy, instr, bwd, blocks, s);
+    case 16: return trace_launch<16>(a, proxy, instr, bwd, blocks, s);
+    default: return trace_launch<32>(a, proxy, instr, bwd, blocks, s);
+    }
+}
+
+int occupancy_k(int k, bool proxy, bool instr, bool bwd, int *bps)
+{
+    switch (k) {
+    case 1: return trace_occupancy<1>(proxy, instr, bwd, bps);
+    case 2: return trace_occupancy<2>(proxy, instr, bwd, bps);
+    case 4: return trace_occupancy<4>(proxy, instr, bwd, bps);
+    case 8: return trace_occupancy<8>(proxy, instr, bwd, bps);
+    case 16: return trace_occupancy<16>(proxy, instr, bwd, bps);
+    default: return trace_occupancy<32>(proxy, instr, bwd, bps);
+    }
+}
+
+int check_params(const grtx_params *p)
+{
+    if (!p) return grtx_fail(GRTX_ERR_INVALID_ARG, "params is NULL");
+    if (!valid_k(p->k)) return grtx_fail(GRTX_ERR_INVALID_ARG, "k must be one of 1, 2, 4, 8, 16, 32");
+    if (p->traversal != GRTX_TRAVERSAL_CHECKPOINT && p->traversal != GRTX_TRAVERSAL_RESTART)
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "unknown traversal mode");
+    if (!(p->T_min >= 0.f && p->T_min < 1.f)) return grtx_fail(GRTX_ERR_INVALID_ARG, "T_min must be in [0,1)");
+    if (!(p->alpha_max > 0.f && p->alpha_max < 1.f)) return grtx_fail(GRTX_ERR_INVALID_ARG, "alpha_max must be in (0,1)");
+    if (p->ckpt_capacity < 0 || p->evict_capacity < 0 || p->ckpt_capacity > 65536 || p->evict_capacity > 65536)
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "capacities must be in [0, 65536]");
+    return GRTX_OK;
+}
+
+}  // namespace
+
+int grtx_fill_camera(CamRef &a, unsigned &n_items_out, const grtx_camera *cam)
+{
+    if (!cam) return grtx_fail(GRTX_ERR_INVALID_ARG, "camera is NULL");
+    if (cam->width <= 0 || cam->height <= 0) return grtx_fail(GRTX_ERR_INVALID_ARG, "camera size must be positive");
+    if (!(cam->t_near >= 0.f) || !(cam->t_far > cam->t_near))
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "need 0 <= t_near < t_far");
+    a.cam_type = cam->type;
+    a.width = cam->width;
+    a.height = cam->height;
+    a.t_near = cam->t_near;
+    a.t_far = cam->t_far;
+    int64_t n_items;
+    if (cam->type == GRTX_CAMERA_RAYS) {
+        if (!cam->ray_origins || !cam->ray_dirs) return grtx_fail(GRTX_ERR_INVALID_ARG, "ray buffers are NULL");
+        a.ray_o = cam->ray_origins;
+        a.ray_d = cam->ray_dirs;
+        a.ray_tn = cam->ray_tnear;
+        a.ray_tf = cam->ray_tfar;
+        n_items = ((int64_t)cam->width * cam->height + 31) / 32 * 32;
+    } else if (cam->type == GRTX_CAMERA_PINHOLE || cam->type == GRTX_CAMERA_FISHEYE) {
+        if (!(cam->fov > 0.f) || (cam->type == GRTX_CAMERA_PINHOLE && !(cam->fov < 3.14159f)))
+            return grtx_fail(GRTX_ERR_INVALID_ARG, "bad field of view");
+        a.pos = make_float3(cam->pos[0], cam->pos[1], cam->pos[2]);
+        a.right = make_float3(cam->right[0], cam->right[1], cam->right[2]);
+        a.up = make_float3(cam->up[0], cam->up[1], cam->up[2]);
+        a.fwd = make_float3(cam->forward[0], cam->forward[1], cam->forward[2]);
+        a.tan_half = tanf(0.5f * cam->fov);
+        a.aspect = (float)cam->width / (float)cam->height;
+        a.fish_f = (0.5f * cam->width) / cam->fov;
+        a.tiles_x = (cam->width + 7) / 8;
+        int tiles_y = (cam->height + 3) / 4;
+        n_items = (int64_t)a.tiles_x * tiles_y * 32;
+    } else {
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "unknown camera type");
+    }
+    if (n_items >= ((int64_t)1 << 31)) return grtx_fail(GRTX_ERR_INVALID_ARG, "too many rays");
+    n_items_out = (unsigned)n_items;
+    return GRTX_OK;
+}
+
+namespace {
+
+int fill_camera(TraceArgs &a, const grtx_camera *cam) { return grtx_fill_camera(a.cam, a.n_items, cam); }
+
+int sm_count()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+// Per-slot checkpoint lists (ping-pong) and eviction list, grown on demand.
+int ensure_workspace(grtx_scene *sc, int n_slots, int C, int E, cudaStream_t s, TraceArgs &a)
+{
+    size_t need = (size_t)n_slots * (2 * (size_t)C + (size_t)E) * sizeof(uint2);
+    if (need > sc->ws_bytes) {
+        if (sc->ws) {
+            GRTX_CUDA(cudaDeviceSynchronize());   // earlier traces on any stream may still use it
+            GRTX_CUDA(cudaFree(sc->ws));
+            sc->ws = nullptr;
+            sc->ws_bytes = 0;
+        }
+        cudaError_t e = cudaMallocAsync(&sc->ws, need, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            sc->ws = nullptr;
+            return grtx_fail(GRTX_ERR_OOM, "trace workspace allocation failed");
+        }
+        sc->ws_bytes = need;
+    }
+    uint2 *base = (uint2 *)sc->ws;
+    a.ck0 = base;
+    a.ck1 = base + (size_t)n_slots * C;
+    a.ev = base + (size_t)n_slots * 2 * C;
+    a.n_slots = n_slots;
+    return GRTX_OK;
+}
+
+}  // namespace
+
+SceneRef grtx_scene_ref(const grtx_scene *sc)
+{
+    SceneRef r;
+    r.nodes = sc->nodes;
+    r.geom = sc->geom;
+    r.tris = sc->tris;
+    r.app = sc->app;
+    r.gid = sc->gid;
+    r.app_stride = sc->app_stride;
+    r.sh_degree = sc->sh_degree;
+    r.has_tree = sc->n_valid > 0;
+    r.pad = 0;
+    return r;
+}
+
+int grtx_check_params(const grtx_params *p) { return check_params(p); }
+
+namespace {
+
+int setup(grtx_scene *sc, const grtx_camera *cam, const grtx_params *p, TraceArgs &a)
+{
+    if (!sc) return grtx_fail(GRTX_ERR_INVALID_ARG, "scene is NULL");
+    int st = check_params(p);
+    if (st) return st;
+    if (p->alpha_min != sc->alpha_min)
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "alpha_min differs from the one the scene was built with");
+    st = fill_camera(a, cam);
+    if (st) return st;
+    a.sc = grtx_scene_ref(sc);
+    a.traversal = sc->form == GRTX_FORM_PROXY20 ? GRTX_TRAVERSAL_RESTART : p->traversal;
+    a.T_min = p->T_min;
+    a.alpha_max = p->alpha_max;
+    a.bg0 = p->bg[0];
+    a.bg1 = p->bg[1];
+    a.bg2 = p->bg[2];
+    a.ckpt_cap = p->ckpt_capacity > 0 ? p->ckpt_capacity : 128;
+    a.evict_cap = p->evict_capacity > 0 ? p->evict_capacity : 64;
+    return GRTX_OK;
+}
+
+int run(grtx_scene *sc, TraceArgs &a, int k, bool instr, bool bwd, unsigned *queue, cudaStream_t s)
+{
+    bool proxy = sc->form == GRTX_FORM_PROXY20;
+    int bps = 0;
+    if (occupancy_k(k, proxy, instr, bwd, &bps) != GRTX_OK || bps <= 0)
+        return grtx_fail(GRTX_ERR_CUDA, "occupancy query failed");
+    int blocks = sm_count() * bps;
+    bool ckpt = !proxy && a.traversal == GRTX_TRAVERSAL_CHECKPOINT;
+    int C = ckpt ? a.ckpt_cap : 0, E = ckpt ? a.evict_cap : 0;
+    int st = ensure_workspace(sc, blocks * 128, std::max(C, 1), std::max(E, 1), s, a);
+    if (st) return st;
+    a.queue = queue;
+    GRTX_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned), s));
+    if (launch_k(k, a, proxy, instr, bwd, blocks, s) != GRTX_OK) {
+        cudaError_t e = cudaGetLastError();
+        return grtx_cuda_fail(e == cudaSuccess ? cudaErrorLaunchFailure : e, "trace launch");
+    }
+    return GRTX_OK;
+}
+
+__global__ void k_gen_rays(CamRef a, float *o, float *d, float *tn, float *tf)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= (int64_t)a.width * a.height) return;
+    unsigned item;
+    if (a.cam_type == GRTX_CAMERA_RAYS) {
+        item = (unsigned)p;
+    } else {
+        int x = (int)(p % a.width), y = (int)(p / a.width);
+        item = (unsigned)(((y / 4) * a.tiles_x + (x / 8)) * 32 + (y % 4) * 8 + (x % 8));
+    }
+    int64_t pix;
+    float3 ro, rd;
+    float a0, a1;
+    if (!make_ray(a, item, pix, ro, rd, a0, a1)) return;
+    o[3 * pix] = ro.x; o[3 * pix + 1] = ro.y; o[3 * pix + 2] = ro.z;
+    d[3 * pix] = rd.x; d[3 * pix + 1] = rd.y; d[3 * pix + 2] = rd.z;
+    if (tn) tn[pix] = a0;
+    if (tf) tf[pix] = a1;
+}
+
+}  // namespace
+
+extern "C" GRTX_API int grtx_generate_rays(const grtx_camera *cam, float *d_origins, float *d_dirs, float *d_tnear,
+                                           float *d_tfar, void *stream)
+{
+    TraceArgs a = {};
+    int st = fill_camera(a, cam);
+    if (st) return st;
+    if (!d_origins || !d_dirs) return grtx_fail(GRTX_ERR_INVALID_ARG, "NULL output");
+    int64_t n = (int64_t)cam->width * cam->height;
+    k_gen_rays<<<grtx_div_up(n, 256), 256, 0, S(stream)>>>(a.cam, d_origins, d_dirs, d_tnear, d_tfar);
+    GRTX_CHECK_LAUNCH("grtx_generate_rays");
+    return GRTX_OK;
+}
+
+extern "C" GRTX_API int grtx_trace_forward(grtx_scene *sc, const grtx_camera *cam, const grtx_params *p,
+                                           const grtx_trace_outputs *out, void *stream)
+{
+    TraceArgs a = {};
+    int st = setup(sc, cam, p, a);
+    if (st) return st;
+    if (!out || !out->rgbT) return grtx_fail(GRTX_ERR_INVALID_ARG, "rgbT output is NULL");
+    if (((uintptr_t)out->rgbT & 15) != 0) return grtx_fail(GRTX_ERR_INVALID_ARG, "rgbT must be 16-byte aligned");
+    if (out->blended_ids && out->ids_cap <= 0) return grtx_fail(GRTX_ERR_INVALID_ARG, "ids_cap must be positive");
+    a.rgbT = (float4 *)out->rgbT;
+    a.n_blended = out->n_blended;
+    a.ids = out->blended_ids;
+    a.ids_cap = out->ids_cap;
+    a.stats = out->stats;
+    cudaStream_t s = S(stream);
+    bool instr = out->n_blended || out->blended_ids || out->stats;
+    if (out->blended_ids)
+        GRTX_CUDA(cudaMemsetAsync(out->blended_ids, 0xff, (size_t)cam->width * cam->height * out->ids_cap * 4, s));
+    return run(sc, a, p->k, instr, false, sc->d_counter, s);
+}
+
+extern "C" GRTX_API int grtx_trace_backward(grtx_scene *sc, const grtx_gaussians *g, const grtx_camera *cam,
+                                            const grtx_params *p, const float *d_rgbT, const float *d_dL_drgbT,
+                                            const grtx_grads *grads, void *stream)
+{
+    TraceArgs a = {};
+    int st = setup(sc, cam, p, a);
+    if (st) return st;
+    if (sc->form != GRTX_FORM_SPHERE) return grtx_fail(GRTX_ERR_INVALID_ARG, "backward needs a sphere-form scene");
+    if (!g || g->n != sc->n || g->sh_degree != sc->sh_degree)
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "gaussians do not match the scene");
+    if (sc->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits))
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "a parameter array is NULL");
+    if (!d_rgbT || !d_dL_drgbT || !grads) return grtx_fail(GRTX_ERR_INVALID_ARG, "NULL pointer");
+    if (((uintptr_t)d_rgbT & 15) || ((uintptr_t)d_dL_drgbT & 15))
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "image buffers must be 16-byte aligned");
+    a.fwd_rgbT = (const float4 *)d_rgbT;
+    a.dL_drgbT = (const float4 *)d_dL_drgbT;
+    a.means = g->means;
+    a.log_scales = g->log_scales;
+    a.quats = g->quats;
+    a.logits = g->opacity_logits;
+    a.g_means = grads->means;
+    a.g_log_scales = grads->log_scales;
+    a.g_quats = grads->quats;
+    a.g_logits = grads->opacity_logits;
+    a.g_sh = grads->sh;
+    a.n_sh = sc->n_coef * 3;
+    return run(sc, a, p->k, false, true, sc->d_counter + 1, S(stream));
+}

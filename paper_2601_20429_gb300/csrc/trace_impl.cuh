@@ -1,0 +1,749 @@
+// Trace kernels: one thread per ray, persistent warps pulling 8x4-pixel tiles from a queue.
+// Per ray: rounds of {pre-fill the k-buffer from the eviction list; traverse from the root
+// (first round / restart) or from the checkpointed nodes (later rounds); blend the k-buffer
+// in depth order with early termination} (Sec. III-A; Sec. IV-B, Listing 1).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "grtx_internal.cuh"
+
+// Scene arrays a trace reads (leaf order; see grtx_scene).
+struct SceneRef {
+    const float4 *nodes;
+    const float4 *geom;
+    const float4 *tris;
+    const float *app;
+    const uint32_t *gid;
+    int app_stride, sh_degree, has_tree, pad;
+};
+
+// A camera (rays generated in-kernel) or an explicit ray list.
+struct CamRef {
+    int cam_type, width, height, tiles_x;
+    float3 pos, right, up, fwd;
+    float tan_half, aspect, fish_f;
+    float t_near, t_far;
+    const float *ray_o, *ray_d, *ray_tn, *ray_tf;
+};
+
+struct TraceArgs {
+    SceneRef sc;
+    CamRef cam;
+    unsigned n_items;            // queue items: 32 per warp tile (camera) or rays rounded up
+    // parameters
+    int traversal;               // GRTX_TRAVERSAL_*
+    float T_min, alpha_max;
+    float bg0, bg1, bg2;
+    int ckpt_cap, evict_cap;
+    // per-slot workspace, interleaved [entry][slot]
+    uint2 *ck0, *ck1, *ev;
+    int n_slots;
+    unsigned *queue;
+    // outputs
+    float4 *rgbT;
+    int32_t *n_blended;
+    uint32_t *ids;
+    int ids_cap;
+    grtx_stats *stats;
+    // backward
+    const float4 *fwd_rgbT, *dL_drgbT;
+    const float *means, *log_scales, *quats, *logits;
+    float *g_means, *g_log_scales, *g_quats, *g_logits, *g_sh;
+    int n_sh;
+};
+
+// One request of a serving step: its scene, camera, output, and which of its queue items
+// this step covers (items [item_begin, item_begin + count) of the request map to step items
+// [step_begin, step_begin + count)). Counts are multiples of 32.
+struct ServeSeg {
+    SceneRef sc;
+    CamRef cam;
+    float4 *out;
+    unsigned item_begin, step_begin, count, pad;
+};
+
+struct Counters {
+    unsigned nodes, leaves, blended, rounds, ckpt, evictions, fallbacks, overflow;
+};
+
+#define GRTX_INF __int_as_float(0x7f800000)
+
+// ------------------------------------------------------------------------------------------
+// Rays
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ bool make_ray(const CamRef &a, unsigned item, int64_t &pix, float3 &o, float3 &d,
+                                         float &tn, float &tf)
+{
+    if (a.cam_type == GRTX_CAMERA_RAYS) {
+        if ((int64_t)item >= (int64_t)a.width * a.height) return false;
+        pix = item;
+        o = make_float3(a.ray_o[3 * pix], a.ray_o[3 * pix + 1], a.ray_o[3 * pix + 2]);
+        d = make_float3(a.ray_d[3 * pix], a.ray_d[3 * pix + 1], a.ray_d[3 * pix + 2]);
+        tn = a.ray_tn ? a.ray_tn[pix] : a.t_near;
+        tf = a.ray_tf ? a.ray_tf[pix] : a.t_far;
+        return true;
+    }
+    unsigned tile = item >> 5, l = item & 31u;
+    int px = (int)(tile % (unsigned)a.tiles_x) * 8 + (int)(l & 7u);
+    int py = (int)(tile / (unsigned)a.tiles_x) * 4 + (int)(l >> 3);
+    if (px >= a.width || py >= a.height) return false;
+    pix = (int64_t)py * a.width + px;
+    float dx, dy, dz;
+    if (a.cam_type == GRTX_CAMERA_PINHOLE) {
+        float u = (2.0f * (px + 0.5f) / a.width - 1.0f) * a.tan_half * a.aspect;
+        float v = (1.0f - 2.0f * (py + 0.5f) / a.height) * a.tan_half;
+        dx = a.fwd.x + u * a.right.x + v * a.up.x;
+        dy = a.fwd.y + u * a.right.y + v * a.up.y;
+        dz = a.fwd.z + u * a.right.z + v * a.up.z;
+    } else {
+        float ex = px + 0.5f - 0.5f * a.width, ey = 0.5f * a.height - (py + 0.5f);
+        float r = sqrtf(ex * ex + ey * ey);
+        float th = r / a.fish_f;
+        float cp = r > 0.f ? ex / r : 1.f, sp = r > 0.f ? ey / r : 0.f;
+        float st, ct;
+        sincosf(th, &st, &ct);
+        dx = st * cp * a.right.x + st * sp * a.up.x + ct * a.fwd.x;
+        dy = st * cp * a.right.y + st * sp * a.up.y + ct * a.fwd.y;
+        dz = st * cp * a.right.z + st * sp * a.up.z + ct * a.fwd.z;
+    }
+    float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+    o = a.pos;
+    d = make_float3(dx * inv, dy * inv, dz * inv);
+    tn = a.t_near;
+    tf = a.t_far;
+    return true;
+}
+
+__device__ __forceinline__ float safe_rcp(float x)
+{
+    return fabsf(x) > 1e-30f ? 1.0f / x : copysignf(1e30f, x);
+}
+
+// ------------------------------------------------------------------------------------------
+// k-buffer (Sec. III-A): ascending keys (t, leaf index) in registers. Insertion bubbles the
+// new key into place; the key that falls off the end (the farthest, or +inf if there was a
+// free slot) is left in (ct, ci).
+// ------------------------------------------------------------------------------------------
+template <int K>
+__device__ __forceinline__ void kbuf_insert(float (&kt)[K], uint32_t (&ki)[K], float &ct, uint32_t &ci)
+{
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        bool lt = ct < kt[j] || (ct == kt[j] && ci < ki[j]);
+        float tt = lt ? kt[j] : ct;
+        uint32_t ti = lt ? ki[j] : ci;
+        kt[j] = lt ? ct : kt[j];
+        ki[j] = lt ? ci : ki[j];
+        ct = tt;
+        ci = ti;
+    }
+}
+
+__device__ __forceinline__ bool key_after(float t, uint32_t i, float Lt, uint32_t Li)
+{
+    return t > Lt || (t == Lt && i > Li);
+}
+
+// Closest approach of the ray to the centre of a Gaussian in its unit-sphere space (Sec. IV-A):
+// with the record rows (A_j | mu_j), o_l = A (o - mu), d_l = A d, t = -(o_l.d_l)/(d_l.d_l) and
+// D2 = |o_l + t d_l|^2. t is the max-response depth of Sec. III-A Eq. t-max-resp, and D2 <= 1
+// iff alpha >= alpha_min. Stage 1 runs for every leaf and only filters: in FP32 its absolute
+// error in D2 grows like |o_l| (the ray origin measured in Gaussian widths), so the threshold
+// is widened accordingly.
+__device__ __forceinline__ bool sphere_candidate(float4 r0, float4 r1, float4 r2, float3 o, float3 d, float &t)
+{
+    float vx = o.x - r0.w, vy = o.y - r1.w, vz = o.z - r2.w;
+    float olx = fmaf(r0.x, vx, fmaf(r0.y, vy, r0.z * vz));
+    float oly = fmaf(r1.x, vx, fmaf(r1.y, vy, r1.z * vz));
+    float olz = fmaf(r2.x, vx, fmaf(r2.y, vy, r2.z * vz));
+    float dlx = fmaf(r0.x, d.x, fmaf(r0.y, d.y, r0.z * d.z));
+    float dly = fmaf(r1.x, d.x, fmaf(r1.y, d.y, r1.z * d.z));
+    float dlz = fmaf(r2.x, d.x, fmaf(r2.y, d.y, r2.z * d.z));
+    float aa = fmaf(dlx, dlx, fmaf(dly, dly, dlz * dlz));
+    float bb = fmaf(olx, dlx, fmaf(oly, dly, olz * dlz));
+    t = -bb / aa;
+    float px = fmaf(t, dlx, olx), py = fmaf(t, dly, oly), pz = fmaf(t, dlz, olz);
+    float D2 = fmaf(px, px, fmaf(py, py, pz * pz));
+    float oo = fmaf(olx, olx, fmaf(oly, oly, olz * olz));
+    return D2 <= 1.0f + 1e-5f + 4e-6f * sqrtf(oo);
+}
+
+// Error-free a + b = s + e (Knuth's two-sum).
+__device__ __forceinline__ float two_sum(float a, float b, float &e)
+{
+    float s = __fadd_rn(a, b);
+    float bv = __fsub_rn(s, a);
+    float av = __fsub_rn(s, bv);
+    e = __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
+    return s;
+}
+
+// Stage 2 for candidates: the world offset w = o + t d - mu is formed as an unevaluated sum of
+// two floats (two-sum for o - mu, an FMA for the rounding error of t d), mapped to unit-sphere
+// space, and t is moved to the exact minimiser along the line by one Newton step. D2 is then
+// accurate to a few ulp of 1 whatever the distance from the ray origin. w receives the world
+// offset of the closest point from the mean.
+__device__ __forceinline__ void sphere_refine(float4 r0, float4 r1, float4 r2, float3 o, float3 d, float &t, float &D2,
+                                              float w[3])
+{
+    const float oc[3] = {o.x, o.y, o.z}, dc[3] = {d.x, d.y, d.z}, mu[3] = {r0.w, r1.w, r2.w};
+    float wh[3], wl[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float vl, e1;
+        float vh = two_sum(oc[c], -mu[c], vl);
+        float ph = __fmul_rn(t, dc[c]);
+        float pl = fmaf(t, dc[c], -ph);
+        wh[c] = two_sum(vh, ph, e1);
+        wl[c] = e1 + vl + pl;
+    }
+    const float4 R[3] = {r0, r1, r2};
+    float p[3], dl[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        float lo = fmaf(R[j].x, wl[0], fmaf(R[j].y, wl[1], R[j].z * wl[2]));
+        p[j] = fmaf(R[j].x, wh[0], fmaf(R[j].y, wh[1], fmaf(R[j].z, wh[2], lo)));
+        dl[j] = fmaf(R[j].x, d.x, fmaf(R[j].y, d.y, R[j].z * d.z));
+    }
+    float delta = fmaf(p[0], dl[0], fmaf(p[1], dl[1], p[2] * dl[2])) / fmaf(dl[0], dl[0], fmaf(dl[1], dl[1], dl[2] * dl[2]));
+    t -= delta;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) p[j] = fmaf(-delta, dl[j], p[j]);
+    D2 = fmaf(p[0], p[0], fmaf(p[1], p[1], p[2] * p[2]));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) w[c] = fmaf(-delta, dc[c], wh[c] + wl[c]);
+}
+
+// Full test of one Gaussian record: returns true for a hit candidate and then (t, D2, w).
+__device__ __forceinline__ bool sphere_test(const float4 *__restrict__ g, float3 o, float3 d, float &t, float &D2,
+                                            float w[3])
+{
+    float4 r0 = __ldg(g), r1 = __ldg(g + 1), r2 = __ldg(g + 2);
+    if (!sphere_candidate(r0, r1, r2, o, d, t)) return false;
+    sphere_refine(r0, r1, r2, o, d, t, D2, w);
+    return true;
+}
+
+// Real spherical harmonics up to degree 3 (no Condon-Shortley phase), index l*l + l + m,
+// times the coefficients: c = max(0, sum_k Y_k(dir) f_k + 0.5). raw receives the sum + 0.5.
+__device__ __forceinline__ void sh_color(const float *__restrict__ f, int deg, float3 n, float c[3], float raw[3],
+                                         float Y[16])
+{
+    float x = n.x, y = n.y, z = n.z;
+    Y[0] = 0.28209479177387814f;
+    int nk = 1;
+    if (deg >= 1) {
+        Y[1] = 0.4886025119029199f * y;
+        Y[2] = 0.4886025119029199f * z;
+        Y[3] = 0.4886025119029199f * x;
+        nk = 4;
+    }
+    if (deg >= 2) {
+        Y[4] = 1.0925484305920792f * x * y;
+        Y[5] = 1.0925484305920792f * y * z;
+        Y[6] = 0.31539156525252005f * (3.f * z * z - 1.f);
+        Y[7] = 1.0925484305920792f * x * z;
+        Y[8] = 0.5462742152960396f * (x * x - y * y);
+        nk = 9;
+    }
+    if (deg >= 3) {
+        Y[9] = 0.5900435899266435f * y * (3.f * x * x - y * y);
+        Y[10] = 2.890611442640554f * x * y * z;
+        Y[11] = 0.4570457994644658f * y * (5.f * z * z - 1.f);
+        Y[12] = 0.3731763325901154f * z * (5.f * z * z - 3.f);
+        Y[13] = 0.4570457994644658f * x * (5.f * z * z - 1.f);
+        Y[14] = 1.445305721320277f * z * (x * x - y * y);
+        Y[15] = 0.5900435899266435f * x * (x * x - 3.f * y * y);
+        nk = 16;
+    }
+    float r0 = 0.5f, r1 = 0.5f, r2 = 0.5f;
+    for (int k = 0; k < nk; ++k) {
+        r0 = fmaf(Y[k], __ldg(f + 3 * k), r0);
+        r1 = fmaf(Y[k], __ldg(f + 3 * k + 1), r1);
+        r2 = fmaf(Y[k], __ldg(f + 3 * k + 2), r2);
+    }
+    raw[0] = r0; raw[1] = r1; raw[2] = r2;
+    c[0] = fmaxf(r0, 0.f); c[1] = fmaxf(r1, 0.f); c[2] = fmaxf(r2, 0.f);
+}
+
+// Slab test of one child box against the ray over [tn, tf]: entry / exit distances.
+__device__ __forceinline__ void slab(float lx, float ly, float lz, float hx, float hy, float hz, float3 o, float3 inv,
+                                     float tn, float tf, float &t0, float &t1)
+{
+    float ax = (lx - o.x) * inv.x, bx = (hx - o.x) * inv.x;
+    float ay = (ly - o.y) * inv.y, by = (hy - o.y) * inv.y;
+    float az = (lz - o.z) * inv.z, bz = (hz - o.z) * inv.z;
+    t0 = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fmaxf(fminf(az, bz), tn));
+    t1 = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fminf(fmaxf(az, bz), tf));
+}
+
+// Ray / triangle (Moller-Trumbore) with a small barycentric tolerance so that shared edges
+// of the proxy never leak; returns the hit distance or +inf.
+__device__ __forceinline__ float tri_hit(float4 v0, float4 v1, float4 v2, float3 o, float3 d)
+{
+    float e1x = v1.x - v0.x, e1y = v1.y - v0.y, e1z = v1.z - v0.z;
+    float e2x = v2.x - v0.x, e2y = v2.y - v0.y, e2z = v2.z - v0.z;
+    float px = d.y * e2z - d.z * e2y, py = d.z * e2x - d.x * e2z, pz = d.x * e2y - d.y * e2x;
+    float det = e1x * px + e1y * py + e1z * pz;
+    if (fabsf(det) < 1e-30f) return GRTX_INF;
+    float id = 1.0f / det;
+    float sx = o.x - v0.x, sy = o.y - v0.y, sz = o.z - v0.z;
+    float u = (sx * px + sy * py + sz * pz) * id;
+    const float eps = 1e-5f;
+    if (u < -eps || u > 1.f + eps) return GRTX_INF;
+    float qx = sy * e1z - sz * e1y, qy = sz * e1x - sx * e1z, qz = sx * e1y - sy * e1x;
+    float v = (d.x * qx + d.y * qy + d.z * qz) * id;
+    if (v < -eps || u + v > 1.f + eps) return GRTX_INF;
+    return (e2x * qx + e2y * qy + e2z * qz) * id;
+}
+
+// ------------------------------------------------------------------------------------------
+// One traversal round over keys in (L, t_max] (Sec. III-A). With ckpt, it starts from the
+// checkpoint source list (or the root in the first round), writes nodes failing the t_max
+// test to the destination list and rejected hits to the eviction list (Sec. IV-B);
+// otherwise it starts at the root and culls. Returns false when a capacity is exceeded.
+// ------------------------------------------------------------------------------------------
+template <int K, bool PROXY, bool INSTR>
+__device__ __forceinline__ bool trace_round(const TraceArgs &a, const SceneRef &sc, float3 o, float3 d, float3 inv,
+                                            float inv_len, float tn, float tf,
+                                            float Lt, uint32_t Li, bool ckpt, bool from_root,
+                                            const uint2 *__restrict__ src, int n_src, uint2 *__restrict__ dst,
+                                            int &n_dst, uint2 *__restrict__ ev, int &n_ev, float (&kt)[K],
+                                            uint32_t (&ki)[K], Counters &cnt)
+{
+    const size_t S = (size_t)a.n_slots;
+    uint2 stack[GRTX_STACK];
+    int sp = 0, si = 0;
+    float tmax = kt[K - 1];
+    uint32_t ref;
+    float te;
+    n_dst = 0;
+    if (from_root) {
+        n_src = 0;                    // a restart never resumes checkpointed subtrees
+        ref = 0u;
+        te = tn;
+    } else {
+        if (n_src == 0) return true;
+        uint2 v = src[0];
+        ref = v.x;
+        te = __uint_as_float(v.y);
+        si = 1;
+    }
+    for (;;) {
+        if (te > tmax) {                              // fails the t_max test
+            if (ckpt) {
+                if (n_dst >= a.ckpt_cap) return false;
+                dst[(size_t)n_dst * S] = make_uint2(ref, __float_as_uint(te));
+                ++n_dst;
+                if (INSTR) cnt.ckpt++;
+            }
+        } else if (ref & GRTX_LEAF) {
+            uint32_t idx = ref & ~GRTX_LEAF;
+            if (INSTR) cnt.leaves++;
+            uint32_t gi;
+            bool touch = true;
+            if (PROXY) {
+                const float4 *tr = sc.tris + 3 * (size_t)idx;
+                float4 v0 = __ldg(tr), v1 = __ldg(tr + 1), v2 = __ldg(tr + 2);
+                gi = __float_as_uint(v0.w);
+                touch = tri_hit(v0, v1, v2, o, d) > tn;
+            } else {
+                gi = idx;
+            }
+            float t, D2, w[3];
+            if (touch && sphere_test(sc.geom + 4 * (size_t)gi, o, d, t, D2, w)) {
+                if (D2 <= 1.0f && t > tn && t <= tf && key_after(t, gi, Lt, Li)) {
+                    bool dup = false;
+                    if (PROXY) {
+#pragma unroll
+                        for (int j = 0; j < K; ++j) dup |= (kt[j] == t && ki[j] == gi);
+                    }
+                    if (!dup) {
+                        float ct = t;
+                        uint32_t ci = gi;
+                        kbuf_insert<K>(kt, ki, ct, ci);
+                        if (ct != GRTX_INF && ckpt) {          // any-hit: rejected -> eviction list
+                            if (n_ev >= a.evict_cap) return false;
+                            ev[(size_t)n_ev * S] = make_uint2(__float_as_uint(ct), ci);
+                            ++n_ev;
+                            if (INSTR) cnt.evictions++;
+                        }
+                        tmax = kt[K - 1];                      // farthest kept key
+                    }
+                }
+            }
+        } else {
+            if (INSTR) cnt.nodes++;
+            const float4 *nd = sc.nodes + 4 * (size_t)ref;
+            float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+            uint32_t c0 = __float_as_uint(n3.x), c1 = __float_as_uint(n3.y);
+            float e0, x0, e1, x1;
+            slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, o, inv, tn, tf, e0, x0);
+            slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, o, inv, tn, tf, e1, x1);
+            bool h0 = e0 <= x0 && !(x0 < Lt);
+            bool h1 = e1 <= x1 && !(x1 < Lt) && c1 != GRTX_NONE;
+            bool near0 = e0 <= e1;
+            if (PROXY) {
+                // a proxy face can lie up to one proxy diameter beyond the Gaussian's key, so
+                // the t_max test of a proxy subtree is taken at entry - (its largest diameter)
+                e0 = fmaf(-n3.z, inv_len, e0);
+                e1 = fmaf(-n3.w, inv_len, e1);
+            }
+            if (h0 && h1) {
+                uint32_t far_ref = near0 ? c1 : c0;
+                float far_t = near0 ? e1 : e0;
+                ref = near0 ? c0 : c1;
+                te = near0 ? e0 : e1;
+                if (far_t > tmax) {
+                    if (ckpt) {
+                        if (n_dst >= a.ckpt_cap) return false;
+                        dst[(size_t)n_dst * S] = make_uint2(far_ref, __float_as_uint(far_t));
+                        ++n_dst;
+                        if (INSTR) cnt.ckpt++;
+                    }
+                } else if (sp < GRTX_STACK) {
+                    stack[sp++] = make_uint2(far_ref, __float_as_uint(far_t));
+                } else if (INSTR) {
+                    cnt.overflow++;
+                }
+                continue;
+            }
+            if (h0 || h1) {
+                ref = h0 ? c0 : c1;
+                te = h0 ? e0 : e1;
+                continue;
+            }
+        }
+        if (sp > 0) {
+            --sp;
+            ref = stack[sp].x;
+            te = __uint_as_float(stack[sp].y);
+        } else if (si < n_src) {
+            uint2 v = src[(size_t)si * S];
+            ++si;
+            ref = v.x;
+            te = __uint_as_float(v.y);
+        } else {
+            break;
+        }
+    }
+    return true;
+}
+
+// ------------------------------------------------------------------------------------------
+// Blending (Sec. II-B Eq. volume-render) and its derivative.
+// ------------------------------------------------------------------------------------------
+struct BlendState {
+    float C[3];
+    float T;
+    // backward
+    float G[4];        // dL/d(r, g, b, T_out)
+    float Cf[3];       // forward colour without background
+    float Tf;          // forward transmittance at termination
+    float dLdT;        // dL/dT_out + bg . dL/dC
+};
+
+__device__ __forceinline__ float atomic_add_f(float *p, float v)
+{
+    return atomicAdd(p, v);
+}
+
+template <bool BWD>
+__device__ __forceinline__ void blend_one(const TraceArgs &a, const SceneRef &sc, BlendState &st, uint32_t idx,
+                                          float3 o, float3 d, float3 dn)
+{
+    const float4 *g = sc.geom + 4 * (size_t)idx;
+    float t, D2, e[3];
+    {
+        float4 r0 = __ldg(g), r1 = __ldg(g + 1), r2 = __ldg(g + 2);
+        sphere_candidate(r0, r1, r2, o, d, t);
+        sphere_refine(r0, r1, r2, o, d, t, D2, e);
+    }
+    float4 r3 = __ldg(g + 3);
+    float al_raw = r3.x * exp2f(r3.y * D2);
+    bool clamped = !(al_raw < a.alpha_max);
+    float al = clamped ? a.alpha_max : al_raw;
+    float c[3], raw[3], Y[16];
+    sh_color(sc.app + (size_t)idx * sc.app_stride, sc.sh_degree, dn, c, raw, Y);
+    float w = st.T * al;
+    if (!BWD) {
+        st.C[0] = fmaf(w, c[0], st.C[0]);
+        st.C[1] = fmaf(w, c[1], st.C[1]);
+        st.C[2] = fmaf(w, c[2], st.C[2]);
+        st.T *= (1.0f - al);
+        return;
+    }
+    uint32_t gi = sc.gid[idx];
+    // colour: dC/dc = T alpha; c = max(0, raw)
+    if (a.g_sh) {
+        int nk = (sc.sh_degree + 1) * (sc.sh_degree + 1);
+        float *gs = a.g_sh + (size_t)gi * a.n_sh;
+        for (int ch = 0; ch < 3; ++ch) {
+            if (!(raw[ch] > 0.f)) continue;
+            float dc = st.G[ch] * w;
+            if (dc == 0.f) continue;
+            for (int k = 0; k < nk; ++k) atomic_add_f(gs + 3 * k + ch, dc * Y[k]);
+        }
+    }
+    st.C[0] = fmaf(w, c[0], st.C[0]);
+    st.C[1] = fmaf(w, c[1], st.C[1]);
+    st.C[2] = fmaf(w, c[2], st.C[2]);
+    float inv1m = 1.0f / (1.0f - al);
+    float dLda = -st.dLdT * st.Tf * inv1m;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) dLda += st.G[ch] * (st.T * c[ch] - (st.Cf[ch] - st.C[ch]) * inv1m);
+    st.T *= (1.0f - al);
+    if (clamped || dLda == 0.f) return;
+    // alpha = o exp(-d2/2), d2 = |S^-1 R^T (x* - mu)|^2 at x* = o + t d (t fixed: envelope)
+    float lam = a.logits[gi];
+    float op = 1.0f / (1.0f + expf(-lam));
+    if (a.g_logits) atomic_add_f(a.g_logits + gi, dLda * al_raw * (1.0f - op));
+    float dLdd2 = -0.5f * dLda * al_raw;
+    float mu[3] = {a.means[3 * gi], a.means[3 * gi + 1], a.means[3 * gi + 2]};
+    float s[3] = {expf(a.log_scales[3 * gi]), expf(a.log_scales[3 * gi + 1]), expf(a.log_scales[3 * gi + 2])};
+    float qw = a.quats[4 * gi], qx = a.quats[4 * gi + 1], qy = a.quats[4 * gi + 2], qz = a.quats[4 * gi + 3];
+    float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+    float iq = 1.0f / qn;
+    float w_ = qw * iq, x = qx * iq, y = qy * iq, z = qz * iq;
+    float R[3][3] = {{1.f - 2.f * (y * y + z * z), 2.f * (x * y - w_ * z), 2.f * (x * z + w_ * y)},
+                     {2.f * (x * y + w_ * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w_ * x)},
+                     {2.f * (x * z - w_ * y), 2.f * (y * z + w_ * x), 1.f - 2.f * (x * x + y * y)}};
+    float v[3], vs[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        float u = R[0][j] * e[0] + R[1][j] * e[1] + R[2][j] * e[2];
+        v[j] = u / s[j];
+        vs[j] = v[j] / s[j];
+    }
+    if (a.g_means) {
+#pragma unroll
+        for (int c2 = 0; c2 < 3; ++c2) {
+            float gm = R[c2][0] * vs[0] + R[c2][1] * vs[1] + R[c2][2] * vs[2];
+            atomic_add_f(a.g_means + 3 * gi + c2, -2.0f * dLdd2 * gm);
+        }
+    }
+    if (a.g_log_scales) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) atomic_add_f(a.g_log_scales + 3 * gi + j, -2.0f * dLdd2 * v[j] * v[j]);
+    }
+    if (a.g_quats) {
+        float Gr[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) Gr[r][j] = 2.0f * dLdd2 * vs[j] * e[r];
+        float gw = 2.f * (-z * Gr[0][1] + y * Gr[0][2] + z * Gr[1][0] - x * Gr[1][2] - y * Gr[2][0] + x * Gr[2][1]);
+        float gx = 2.f * (y * Gr[0][1] + z * Gr[0][2] + y * Gr[1][0] - 2.f * x * Gr[1][1] - w_ * Gr[1][2] +
+                          z * Gr[2][0] + w_ * Gr[2][1] - 2.f * x * Gr[2][2]);
+        float gy = 2.f * (-2.f * y * Gr[0][0] + x * Gr[0][1] + w_ * Gr[0][2] + x * Gr[1][0] + z * Gr[1][2] -
+                          w_ * Gr[2][0] + z * Gr[2][1] - 2.f * y * Gr[2][2]);
+        float gz = 2.f * (-2.f * z * Gr[0][0] - w_ * Gr[0][1] + x * Gr[0][2] + w_ * Gr[1][0] - 2.f * z * Gr[1][1] +
+                          y * Gr[1][2] + x * Gr[2][0] + y * Gr[2][1]);
+        float dot = w_ * gw + x * gx + y * gy + z * gz;
+        atomic_add_f(a.g_quats + 4 * gi + 0, (gw - w_ * dot) * iq);
+        atomic_add_f(a.g_quats + 4 * gi + 1, (gx - x * dot) * iq);
+        atomic_add_f(a.g_quats + 4 * gi + 2, (gy - y * dot) * iq);
+        atomic_add_f(a.g_quats + 4 * gi + 3, (gz - z * dot) * iq);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// One ray: the round loop of Listing 1's raygen shader.
+// ------------------------------------------------------------------------------------------
+template <int K, bool PROXY, bool INSTR, bool BWD>
+__device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc, float4 *__restrict__ out, int slot,
+                                          int64_t pix, float3 o, float3 d, float tn, float tf, Counters &cnt)
+{
+    const size_t S = (size_t)a.n_slots;
+    float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+    float nrm = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+    float3 dn = make_float3(d.x * nrm, d.y * nrm, d.z * nrm);
+    const float inv_len = nrm;
+    BlendState st;
+    st.C[0] = st.C[1] = st.C[2] = 0.f;
+    st.T = 1.f;
+    if (BWD) {
+        float4 F = a.fwd_rgbT[pix], G = a.dL_drgbT[pix];
+        st.G[0] = G.x; st.G[1] = G.y; st.G[2] = G.z; st.G[3] = G.w;
+        st.Tf = F.w;
+        st.Cf[0] = F.x - F.w * a.bg0;
+        st.Cf[1] = F.y - F.w * a.bg1;
+        st.Cf[2] = F.z - F.w * a.bg2;
+        st.dLdT = G.w + a.bg0 * G.x + a.bg1 * G.y + a.bg2 * G.z;
+    }
+    float Lt = tn;
+    uint32_t Li = GRTX_NONE;
+    bool ckpt = !PROXY && a.traversal == GRTX_TRAVERSAL_CHECKPOINT;
+    bool from_root = true;
+    int n_src = 0, n_ev = 0, nb = 0;
+    uint2 *src = a.ck0 + slot, *dst = a.ck1 + slot, *ev = a.ev + slot;
+    bool done = !sc.has_tree;
+    while (!done) {
+        if (INSTR) cnt.rounds++;
+        float kt[K];
+        uint32_t ki[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) { kt[j] = GRTX_INF; ki[j] = GRTX_NONE; }
+        if (ckpt && n_ev > 0) {            // raygen: closest evicted hits -> k-buffer
+            int w = 0;
+            for (int e = 0; e < n_ev; ++e) {
+                uint2 v = ev[(size_t)e * S];
+                float ct = __uint_as_float(v.x);
+                uint32_t ci = v.y;
+                kbuf_insert<K>(kt, ki, ct, ci);
+                if (ct != GRTX_INF) {
+                    ev[(size_t)w * S] = make_uint2(__float_as_uint(ct), ci);
+                    ++w;
+                }
+            }
+            n_ev = w;
+        }
+        int n_dst = 0;
+        if (!trace_round<K, PROXY, INSTR>(a, sc, o, d, inv, inv_len, tn, tf, Lt, Li, ckpt, from_root, src, n_src, dst, n_dst,
+                                          ev, n_ev, kt, ki, cnt)) {
+            // a capacity was exceeded: redo this round from the root and stay in restart mode
+            if (INSTR) cnt.fallbacks++;
+            ckpt = false;
+            from_root = true;
+            n_src = 0;
+            n_ev = 0;
+#pragma unroll
+            for (int j = 0; j < K; ++j) { kt[j] = GRTX_INF; ki[j] = GRTX_NONE; }
+            trace_round<K, PROXY, INSTR>(a, sc, o, d, inv, inv_len, tn, tf, Lt, Li, false, true, src, 0, dst, n_dst, ev, n_ev,
+                                         kt, ki, cnt);
+        }
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            if (kt[j] == GRTX_INF) break;
+            blend_one<BWD>(a, sc, st, ki[j], o, d, dn);
+            if (INSTR) {
+                if (a.ids && nb < a.ids_cap) a.ids[(size_t)pix * a.ids_cap + nb] = sc.gid[ki[j]];
+                cnt.blended++;
+            }
+            ++nb;
+            if (st.T < a.T_min) { done = true; break; }
+        }
+        if (done || kt[K - 1] == GRTX_INF) break;
+        Lt = kt[K - 1];
+        Li = ki[K - 1];
+        if (ckpt) {
+            uint2 *tmp = src; src = dst; dst = tmp;
+            n_src = n_dst;
+            from_root = false;
+        }
+    }
+    if (!BWD) out[pix] = make_float4(st.C[0] + st.T * a.bg0, st.C[1] + st.T * a.bg1, st.C[2] + st.T * a.bg2, st.T);
+    if (INSTR && a.n_blended) a.n_blended[pix] = nb;
+}
+
+template <int K, bool PROXY, bool INSTR, bool BWD>
+__global__ void __launch_bounds__(128) k_trace(TraceArgs a)
+{
+    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
+    unsigned rays = 0;
+    for (;;) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(a.queue, 32u);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= a.n_items) break;
+        int64_t pix;
+        float3 o, d;
+        float tn, tf;
+        if (make_ray(a.cam, base + lane, pix, o, d, tn, tf)) {
+            ++rays;
+            trace_ray<K, PROXY, INSTR, BWD>(a, a.sc, a.rgbT, slot, pix, o, d, tn, tf, cnt);
+        }
+        __syncwarp();
+    }
+    if (INSTR && a.stats) {
+        unsigned long long v[9] = {rays, cnt.nodes, cnt.leaves, cnt.blended, cnt.rounds, cnt.ckpt, cnt.evictions,
+                                   cnt.fallbacks, cnt.overflow};
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            unsigned long long x = v[q];
+            for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+            if (lane == 0 && x) atomicAdd((&a.stats->rays) + q, x);
+        }
+    }
+}
+
+// Serving step: one persistent launch over the queue items of several requests (each with
+// its own scene, camera and output); a warp's 32 items always belong to one request.
+template <int K>
+__global__ void __launch_bounds__(128) k_serve(TraceArgs a, const ServeSeg *__restrict__ segs, int n_segs)
+{
+    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (;;) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(a.queue, 32u);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= a.n_items) break;
+        int lo = 0, hi = n_segs - 1;              // last segment with step_begin <= base
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (segs[mid].step_begin <= base) lo = mid; else hi = mid - 1;
+        }
+        const ServeSeg &sg = segs[lo];
+        SceneRef sc = sg.sc;
+        CamRef cam = sg.cam;
+        unsigned item = sg.item_begin + (base - sg.step_begin) + lane;
+        int64_t pix;
+        float3 o, d;
+        float tn, tf;
+        if (make_ray(cam, item, pix, o, d, tn, tf))
+            trace_ray<K, false, false, false>(a, sc, sg.out, slot, pix, o, d, tn, tf, cnt);
+        __syncwarp();
+    }
+}
+
+// Launch helpers, instantiated per k in the trace_k*.cu units.
+template <int K>
+int trace_launch(const TraceArgs &a, bool proxy, bool instr, bool bwd, int blocks, cudaStream_t s)
+{
+    dim3 g(blocks), b(128);
+    if (bwd) k_trace<K, false, false, true><<<g, b, 0, s>>>(a);
+    else if (proxy && instr) k_trace<K, true, true, false><<<g, b, 0, s>>>(a);
+    else if (proxy) k_trace<K, true, false, false><<<g, b, 0, s>>>(a);
+    else if (instr) k_trace<K, false, true, false><<<g, b, 0, s>>>(a);
+    else k_trace<K, false, false, false><<<g, b, 0, s>>>(a);
+    return cudaGetLastError() == cudaSuccess ? GRTX_OK : GRTX_ERR_CUDA;
+}
+
+template <int K>
+int trace_occupancy(bool proxy, bool instr, bool bwd, int *blocks_per_sm)
+{
+    cudaError_t e;
+    if (bwd) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, false, false, true>, 128, 0);
+    else if (proxy && instr) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, true, true, false>, 128, 0);
+    else if (proxy) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, true, false, false>, 128, 0);
+    else if (instr) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, false, true, false>, 128, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, false, false, false>, 128, 0);
+    return e == cudaSuccess ? GRTX_OK : GRTX_ERR_CUDA;
+}
+
+template <int K>
+int serve_launch(const TraceArgs &a, const ServeSeg *segs, int n_segs, int blocks, cudaStream_t s)
+{
+    k_serve<K><<<blocks, 128, 0, s>>>(a, segs, n_segs);
+    return cudaGetLastError() == cudaSuccess ? GRTX_OK : GRTX_ERR_CUDA;
+}
+
+template <int K>
+int serve_occupancy(int *blocks_per_sm)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_serve<K>, 128, 0) == cudaSuccess
+               ? GRTX_OK : GRTX_ERR_CUDA;
+}
+
+#define GRTX_INSTANTIATE_TRACE(K)                                                                  \
+    template int trace_launch<K>(const TraceArgs &, bool, bool, bool, int, cudaStream_t);         \
+    template int trace_occupancy<K>(bool, bool, bool, int *);                                       \
+    template int serve_launch<K>(const TraceArgs &, const ServeSeg *, int, int, cudaStream_t);     \
+    template int serve_occupancy<K>(int *);

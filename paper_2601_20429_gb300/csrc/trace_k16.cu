@@ -1,0 +1,4 @@
+// Trace kernels for a k-buffer of 16 entries (one translation unit per k keeps builds parallel).
+#include "trace_impl.cuh"
+
+GRTX_INSTANTIATE_TRACE(16)

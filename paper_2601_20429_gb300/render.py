@@ -1,0 +1,142 @@
+"""User-facing API over libgrtx: scenes, rendering, and a torch.autograd.Function.
+
+Tensors live on the current CUDA device; all work goes through the C ABI (native.py).
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import native as N
+
+FORMS = {"sphere": 0, "proxy20": 1}
+TRAVERSALS = {"checkpoint": 0, "restart": 1}
+
+
+def _cuda_f32(a, device) -> torch.Tensor:
+    if isinstance(a, np.ndarray):
+        a = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32))
+    return a.to(device=device, dtype=torch.float32).contiguous()
+
+
+def params_to_device(g, device="cuda"):
+    """(means, log_scales, quats, logits, sh) as contiguous float32 CUDA tensors."""
+    return tuple(_cuda_f32(a, device) for a in (g.means, g.log_scales, g.quats, g.logits, g.sh))
+
+
+class Scene:
+    """A built acceleration structure (library-owned) for one set of Gaussians.
+
+    form: "sphere" (one unit-sphere instance per Gaussian, Sec. IV-A) or "proxy20" (20
+    triangles per Gaussian in one monolithic BVH, the baseline of Sec. III-C)."""
+
+    def __init__(self, means, log_scales, quats, logits, sh, sh_degree: int, form: str = "sphere",
+                 alpha_min: float = 0.01, stream=None):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.tensors = tuple(_cuda_f32(a, dev) for a in (means, log_scales, quats, logits, sh))
+        self.sh_degree = int(sh_degree)
+        self.form = form
+        self.alpha_min = float(alpha_min)
+        self._g = N.make_gaussians(*self.tensors, self.sh_degree)
+        p = N.make_params(alpha_min=alpha_min)
+        self.handle = N.grtx_build_bvh(self._g, p, FORMS[form], stream)
+
+    @classmethod
+    def from_params(cls, g, form="sphere", alpha_min=0.01, stream=None):
+        return cls(g.means, g.log_scales, g.quats, g.logits, g.sh, g.sh_degree, form, alpha_min, stream)
+
+    @property
+    def n(self) -> int:
+        return int(self.tensors[3].shape[0])
+
+    def info(self) -> dict:
+        return N.grtx_scene_info_get(self.handle)
+
+    def export(self):
+        info = self.info()
+        dev = self.tensors[0].device
+        nodes = torch.empty((max(info["n_nodes"], 1), 16), dtype=torch.float32, device=dev)
+        ids = torch.empty(max(info["n_leaves"], 1), dtype=torch.int32, device=dev)
+        codes = torch.empty(max(info["n_leaves"], 1), dtype=torch.int64, device=dev)
+        N.grtx_scene_export(self.handle, nodes, ids, codes)
+        return nodes[: info["n_nodes"]], ids[: info["n_leaves"]], codes[: info["n_leaves"]]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            N.grtx_scene_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def trace_params(k=16, traversal="checkpoint", alpha_min=0.01, T_min=1e-3, alpha_max=0.99, bg=(0.0, 0.0, 0.0),
+                 ckpt_capacity=0, evict_capacity=0):
+    return N.make_params(k, TRAVERSALS[traversal] if isinstance(traversal, str) else traversal, alpha_min, T_min,
+                         alpha_max, bg, ckpt_capacity, evict_capacity)
+
+
+def n_rays_of(cam: dict, rays=None) -> int:
+    return int(rays[0].shape[0]) if rays is not None else int(cam["width"]) * int(cam["height"])
+
+
+def render(scene: Scene, cam: dict | None, rays=None, out=None, ids_cap: int = 0, want_n_blended=False,
+           want_stats=False, stream=None, **params):
+    """Forward trace. Returns dict(rgbT [n_rays, 4], n_blended?, ids?, stats?)."""
+    p = trace_params(alpha_min=scene.alpha_min, **params)
+    c = N.make_camera(cam, rays)
+    n = n_rays_of(cam, rays)
+    dev = scene.tensors[0].device
+    rgbT = out if out is not None else torch.empty((n, 4), dtype=torch.float32, device=dev)
+    nb = torch.empty(n, dtype=torch.int32, device=dev) if want_n_blended else None
+    ids = torch.empty((n, ids_cap), dtype=torch.int32, device=dev) if ids_cap > 0 else None
+    st = N.stats_tensor(dev) if want_stats else None
+    N.grtx_trace_forward(scene.handle, c, p, rgbT, nb, ids, st, stream)
+    res = {"rgbT": rgbT}
+    if nb is not None:
+        res["n_blended"] = nb
+    if ids is not None:
+        res["ids"] = ids
+    if st is not None:
+        res["stats"] = st
+    return res
+
+
+def backward(scene: Scene, cam: dict | None, rgbT, dL_drgbT, rays=None, stream=None, **params):
+    """Gradients of the raw parameters the scene was built from, given dL/d(rgbT)."""
+    p = trace_params(alpha_min=scene.alpha_min, **params)
+    c = N.make_camera(cam, rays)
+    grads = {name: torch.zeros_like(t) for name, t in
+             zip(("means", "log_scales", "quats", "opacity_logits", "sh"), scene.tensors)}
+    N.grtx_trace_backward(scene.handle, scene._g, c, p, rgbT.contiguous(), dL_drgbT.contiguous(), grads, stream)
+    return grads
+
+
+class RenderFunction(torch.autograd.Function):
+    """Differentiable render: builds the BVH from the current parameters, traces forward,
+    and in backward re-traverses the same rounds to accumulate parameter gradients."""
+
+    @staticmethod
+    def forward(ctx, means, log_scales, quats, logits, sh, sh_degree, cam, opts):
+        scene = Scene(means.detach(), log_scales.detach(), quats.detach(), logits.detach(), sh.detach(), sh_degree,
+                      "sphere", opts.get("alpha_min", 0.01))
+        o = dict(opts)
+        o.pop("alpha_min", None)
+        rgbT = render(scene, cam, **o)["rgbT"]
+        ctx.scene, ctx.cam, ctx.opts = scene, cam, o
+        ctx.save_for_backward(rgbT)
+        return rgbT
+
+    @staticmethod
+    def backward(ctx, grad_rgbT):
+        (rgbT,) = ctx.saved_tensors
+        g = backward(ctx.scene, ctx.cam, rgbT, grad_rgbT.float().contiguous(), **ctx.opts)
+        ctx.scene.close()
+        return g["means"], g["log_scales"], g["quats"], g["opacity_logits"], g["sh"], None, None, None
+
+
+def render_differentiable(means, log_scales, quats, logits, sh, sh_degree: int, cam: dict, **opts):
+    return RenderFunction.apply(means, log_scales, quats, logits, sh, sh_degree, cam, opts)

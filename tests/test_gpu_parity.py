@@ -1,0 +1,360 @@
+"""GPU parity: every step of the hot path, called through the C ABI, against the FP64 oracle
+on the same seeded inputs."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O  # noqa: E402
+from paper_2601_20429_gb300 import native as N  # noqa: E402
+from paper_2601_20429_gb300 import render as R  # noqa: E402
+from paper_2601_20429_gb300 import scenes  # noqa: E402
+from tests.gpu_util import RGB_TOL, compare_hit_lists, rel_err  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    g, cam, cfg = scenes.config_tiny()
+    S = O.Scene.from_params(g)
+    rays = O.camera_rays(cam)
+    ref = S.render(rays, ids_cap=64)
+    return g, cam, S, rays, ref
+
+
+def _dense():
+    g = scenes.tiny_scene(seed=0, n=20000)
+    g.sh = np.random.default_rng(5).normal(0, 0.3, (g.n, 16, 3)).astype(np.float32)
+    g.sh_degree = 3
+    cam = scenes.pinhole_camera(40, 36, (0.0, 0.0, -3.0), (0, 0, 0), 60.0)
+    return g, cam
+
+
+@pytest.fixture(scope="module")
+def dense():
+    g, cam = _dense()
+    S = O.Scene.from_params(g)
+    rays = O.camera_rays(cam)
+    ref = S.render(rays, ids_cap=256)
+    return g, cam, S, rays, ref
+
+
+# ------------------------------------------------------------------ a1: activation / transform
+
+
+def test_prep_matches_oracle():
+    g = scenes.surface_scene(n=5000, seed=7)
+    t = R.params_to_device(g)
+    gg = N.make_gaussians(*t, g.sh_degree)
+    geom = torch.empty((g.n, 16), dtype=torch.float32, device="cuda")
+    aabb = torch.empty((g.n, 6), dtype=torch.float32, device="cuda")
+    N.grtx_prep_gaussians(gg, 0.01, geom, aabb)
+    torch.cuda.synchronize()
+    ex = O.Scene.from_params(g).export()
+    geom = geom.cpu().numpy().astype(np.float64)
+    aabb = aabb.cpu().numpy().astype(np.float64)
+    v = ex["valid"]
+    A = geom[:, :12].reshape(-1, 3, 4)
+    scale = np.abs(ex["A"][v, :, :3]).max(axis=(1, 2))[:, None, None]
+    assert np.all(np.abs(A[v, :, :3] - ex["A"][v, :, :3]) <= 2e-5 * scale)
+    np.testing.assert_array_equal(A[v, :, 3], g.means[v].astype(np.float64))     # mean, exactly
+    np.testing.assert_allclose(geom[v, 12], ex["o"][v], rtol=1e-5)
+    np.testing.assert_allclose(-2 * geom[v, 13] / 1.4426950408889634, ex["kappa"][v] ** 2, rtol=2e-5)
+    assert np.array_equal(geom[v, 14].astype(np.float32).view(np.int32), np.nonzero(v)[0].astype(np.int32))
+    ext = (ex["aabb"][v, 3:] - ex["aabb"][v, :3]).max(1, keepdims=True)
+    # the GPU machine is the oracle box widened slightly (conservative), never narrower
+    assert np.all(aabb[v, :3] <= ex["aabb"][v, :3] + 1e-6 * ext)
+    assert np.all(aabb[v, 3:] >= ex["aabb"][v, 3:] - 1e-6 * ext)
+    pad = 2e-5 * ext + 4e-6 * (1.0 + np.abs(g.means[v]).max(1, keepdims=True))     # documented widening
+    assert np.all(np.abs(aabb[v] - ex["aabb"][v]) <= pad)
+    assert np.all(geom[~v] == 0) and np.all(np.isinf(aabb[~v]))
+
+
+# ------------------------------------------------------------------ a2/a3: LBVH building blocks
+
+
+def _random_boxes(n, seed, dups=False):
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(-3, 5, (n, 3)).astype(np.float32)
+    if dups:
+        c[n // 2:] = c[: n - n // 2]
+    e = rng.uniform(0, 0.2, (n, 3)).astype(np.float32)
+    return np.concatenate([c - e, c + e], 1).astype(np.float32)
+
+
+@pytest.mark.parametrize("n,dups", [(1, False), (2, False), (1000, False), (4097, True), (300_001, False)])
+def test_morton_bit_exact(n, dups):
+    boxes = _random_boxes(n, n, dups)
+    boxes[::97] = [np.inf, np.inf, np.inf, -np.inf, -np.inf, -np.inf]     # empty boxes
+    d = torch.from_numpy(boxes).cuda()
+    codes = torch.empty(n, dtype=torch.int64, device="cuda")
+    bounds = torch.empty(6, dtype=torch.float32, device="cuda")
+    N.grtx_morton_codes(d, None, codes, bounds_out=bounds)
+    torch.cuda.synchronize()
+    valid = np.all(boxes[:, :3] <= boxes[:, 3:], axis=1)
+    ob = O.centroid_bounds(boxes[valid]) if valid.any() else np.zeros(6, np.float32)
+    np.testing.assert_array_equal(bounds.cpu().numpy()[: 6] if valid.any() else ob, ob)
+    oc = np.full(n, np.iinfo(np.uint64).max, dtype=np.uint64)
+    if valid.any():
+        oc[valid] = O.morton63(boxes[valid], ob)
+    assert np.array_equal(codes.cpu().numpy().view(np.uint64), oc)
+
+
+@pytest.mark.parametrize("n,bits", [(1, 64), (5, 64), (4096, 64), (100_000, 21), (1_000_003, 64)])
+def test_sort_pairs_stable_bit_exact(n, bits):
+    rng = np.random.default_rng(n)
+    keys = rng.integers(0, 2 ** 63, n, dtype=np.uint64)
+    dup = rng.integers(0, n, n // 3)
+    keys[dup] = keys[(dup * 7 + 1) % n]                                   # many equal keys
+    vals = np.arange(n, dtype=np.uint32)
+    k = torch.from_numpy(keys.view(np.int64)).cuda()
+    v = torch.from_numpy(vals.view(np.int32)).cuda()
+    N.grtx_sort_pairs(k, v, bits)
+    torch.cuda.synchronize()
+    masked = keys & np.uint64((1 << bits) - 1) if bits < 64 else keys
+    order = np.argsort(masked, kind="stable")
+    assert np.array_equal(v.cpu().numpy().view(np.uint32), order.astype(np.uint32))
+    assert np.array_equal(k.cpu().numpy().view(np.uint64), keys[order])
+
+
+@pytest.mark.parametrize("n,dups", [(2, False), (3, True), (1000, False), (65_537, True)])
+def test_radix_tree_and_refit_bit_exact(n, dups):
+    rng = np.random.default_rng(n + 1)
+    keys = np.sort(rng.integers(0, 64 if dups else 2 ** 63, n, dtype=np.uint64))
+    kd = torch.from_numpy(keys.view(np.int64)).cuda()
+    left = torch.empty(n - 1, dtype=torch.int32, device="cuda")
+    right = torch.empty(n - 1, dtype=torch.int32, device="cuda")
+    parent = torch.empty(2 * n - 1, dtype=torch.int32, device="cuda")
+    N.grtx_radix_tree(kd, left, right, parent)
+    boxes = _random_boxes(n, n + 2)
+    lb = torch.from_numpy(boxes).cuda()
+    nb = torch.empty((n - 1, 6), dtype=torch.float32, device="cuda")
+    cnt = torch.empty(n - 1, dtype=torch.int32, device="cuda")
+    N.grtx_refit(left, right, parent, lb, nb, cnt)
+    torch.cuda.synchronize()
+    ol, orr = O.radix_tree(keys)
+    assert np.array_equal(left.cpu().numpy().view(np.uint32), ol)
+    assert np.array_equal(right.cpu().numpy().view(np.uint32), orr)
+    assert np.array_equal(nb.cpu().numpy(), O.refit(ol, orr, boxes))
+    par = parent.cpu().numpy().view(np.uint32)
+    assert par[0] == 0xFFFFFFFF
+    for i in range(n - 1):
+        for c in (ol[i], orr[i]):
+            j = (n - 1 + (c & 0x7FFFFFFF)) if c & 0x80000000 else c
+            assert par[j] == i
+
+
+def test_scene_tree_is_valid_lbvh():
+    g = scenes.surface_scene(n=20000, seed=9)
+    sc = R.Scene.from_params(g)
+    info = sc.info()
+    nodes, ids, codes = sc.export()
+    nodes = nodes.cpu().numpy()
+    ids = ids.cpu().numpy()
+    codes = codes.cpu().numpy().view(np.uint64)
+    valid = O.Scene.from_params(g).export()["valid"]
+    assert info["n_valid"] == valid.sum() == info["n_leaves"] == info["n_nodes"] + 1
+    assert np.all(np.diff(codes.astype(np.float64)) >= 0)
+    assert sorted(ids.tolist()) == np.nonzero(valid)[0].tolist()
+    refs = nodes[:, 12:14].copy().view(np.uint32)
+    assert np.all(nodes[:, 14:16] == 0)          # no proxy slack in the sphere form
+    seen_leaf = np.zeros(info["n_leaves"], int)
+    seen_node = np.zeros(info["n_nodes"], int)
+    for r in refs.reshape(-1):
+        if r & 0x80000000:
+            seen_leaf[r & 0x7FFFFFFF] += 1
+        else:
+            seen_node[r] += 1
+    assert np.all(seen_leaf == 1) and seen_node[0] == 0 and np.all(seen_node[1:] == 1)
+    # every child box nests in its parent's slot box
+    box_of = {}
+    for i in range(info["n_nodes"]):
+        for c, off in ((refs[i, 0], 0), (refs[i, 1], 6)):
+            if not c & 0x80000000:
+                box_of[int(c)] = nodes[i, off:off + 6]
+    for i, pb in box_of.items():
+        for off in (0, 6):
+            cb = nodes[i, off:off + 6]
+            assert np.all(cb[:3] >= pb[:3]) and np.all(cb[3:] <= pb[3:])
+    assert 0 < info["depth"] < 64
+
+
+# ------------------------------------------------------------------ a4: rays
+
+
+@pytest.mark.parametrize("kind", ["pinhole", "fisheye"])
+def test_rays_match_oracle(kind):
+    if kind == "pinhole":
+        cam = scenes.pinhole_camera(37, 23, (1.0, 2.0, -3.0), (0, 0, 0), 50.0, t_near=0.1, t_far=30.0)
+    else:
+        cam = scenes.fisheye_camera(41, 29, (0.0, 1.7, 0.0), (1, 0, 0), 90.0)
+    n = cam["width"] * cam["height"]
+    o = torch.empty((n, 3), device="cuda"); d = torch.empty((n, 3), device="cuda")
+    tn = torch.empty(n, device="cuda"); tf = torch.empty(n, device="cuda")
+    N.grtx_generate_rays(N.make_camera(cam), o, d, tn, tf)
+    torch.cuda.synchronize()
+    oo, od, otn, otf = O.camera_rays(cam)
+    np.testing.assert_allclose(o.cpu().numpy(), oo, atol=1e-6)
+    np.testing.assert_allclose(d.cpu().numpy(), od, atol=2e-6)
+    np.testing.assert_allclose(tn.cpu().numpy(), otn.astype(np.float32))
+    np.testing.assert_array_equal(tf.cpu().numpy(), otf.astype(np.float32))
+
+
+# ------------------------------------------------------------------ a5-a9: forward trace
+
+
+def _gpu_render(g, cam, form="sphere", rays=None, **kw):
+    sc = R.Scene.from_params(g, form=form)
+    out = R.render(sc, cam, rays=rays, ids_cap=kw.pop("ids_cap", 64), want_n_blended=True, want_stats=True, **kw)
+    torch.cuda.synchronize()
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    res["stats"] = N.stats_dict(out["stats"])
+    sc.close()
+    return res
+
+
+def _check_image(res, ref, S, rays):
+    err = np.abs(res["rgbT"].astype(np.float64) - ref["out"]).max(0)
+    assert err[:3].max() <= RGB_TOL and err[3] <= RGB_TOL, err
+    bad = compare_hit_lists(S, rays, res["ids"], res["n_blended"], ref["ids"], ref["n_blend"])
+    assert not bad, f"{len(bad)} rays with different hit lists, e.g. {bad[:5]}"
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("traversal", ["checkpoint", "restart"])
+def test_forward_tiny_parity(tiny, k, traversal):
+    g, cam, S, rays, ref = tiny
+    res = _gpu_render(g, cam, k=k, traversal=traversal)
+    _check_image(res, ref, S, rays)
+    st = res["stats"]
+    assert st["rays"] == cam["width"] * cam["height"]
+    assert st["fallbacks"] == 0 and st["stack_overflow"] == 0
+    assert st["blended"] == int(ref["n_blend"].sum())
+
+
+@pytest.mark.parametrize("k", [4, 16])
+def test_forward_dense_parity_both_traversals(dense, k):
+    g, cam, S, rays, ref = dense
+    a = _gpu_render(g, cam, k=k, traversal="checkpoint", ids_cap=256)
+    b = _gpu_render(g, cam, k=k, traversal="restart", ids_cap=256)
+    _check_image(a, ref, S, rays)
+    _check_image(b, ref, S, rays)
+    assert a["stats"]["nodes"] < b["stats"]["nodes"]         # resume skips the revisits
+    assert a["stats"]["rounds"] == b["stats"]["rounds"]
+    assert (ref["n_blend"] < ref["n_hits"]).sum() > 100       # early termination is exercised
+
+
+@pytest.mark.parametrize("caps", [(2, 0), (0, 1), (3, 3)])
+def test_forward_capacity_fallback_is_exact(dense, caps):
+    g, cam, S, rays, ref = dense
+    res = _gpu_render(g, cam, k=4, ckpt_capacity=caps[0], evict_capacity=caps[1], ids_cap=256)
+    assert res["stats"]["fallbacks"] > 0
+    _check_image(res, ref, S, rays)
+
+
+@pytest.mark.parametrize("k", [4, 16])
+def test_forward_proxy_form_parity(dense, k):
+    g, cam, S, rays, ref = dense
+    res = _gpu_render(g, cam, form="proxy20", k=k, ids_cap=256)
+    _check_image(res, ref, S, rays)
+
+
+def test_forward_explicit_rays_and_window(dense):
+    g, cam, S, rays, ref = dense
+    rng = np.random.default_rng(3)
+    n = 700
+    o = rng.uniform(-2.5, 2.5, (n, 3))
+    d = rng.standard_normal((n, 3)) * rng.uniform(0.5, 2.0, (n, 1))     # not unit length
+    tn = rng.uniform(0.0, 0.5, n)
+    tf = tn + rng.uniform(0.5, 6.0, n)
+    orays = (o, d, tn, tf)
+    oref = S.render(orays, ids_cap=256)
+    trays = tuple(torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda() for a in orays)
+    res = _gpu_render(g, None, rays=trays, k=8, ids_cap=256)
+    o32 = tuple(a.astype(np.float32).astype(np.float64) for a in orays)
+    oref = S.render(o32, ids_cap=256)
+    _check_image(res, oref, S, o32)
+
+
+def test_forward_background_and_empty_scene():
+    g = scenes.tiny_scene(seed=3, n=50)
+    cam = scenes.pinhole_camera(16, 16, (0.0, 0.0, -3.0), (0, 0, 0), 60.0)
+    S = O.Scene.from_params(g)
+    rays = O.camera_rays(cam)
+    ref = S.render(rays, params=O.make_params(bg=(0.2, 0.4, 0.6)), ids_cap=64)
+    res = _gpu_render(g, cam, k=4, bg=(0.2, 0.4, 0.6))
+    _check_image(res, ref, S, rays)
+    g0 = g.copy()
+    g0.logits[:] = -20.0                  # every opacity below alpha_min: nothing is hit
+    res = _gpu_render(g0, cam, k=4, bg=(0.2, 0.4, 0.6))
+    np.testing.assert_allclose(res["rgbT"], np.tile([0.2, 0.4, 0.6, 1.0], (256, 1)), atol=0)
+    g1 = g.subset([int(np.argmax(g.logits))])
+    S1 = O.Scene.from_params(g1)
+    ref1 = S1.render(rays, ids_cap=4)
+    res1 = _gpu_render(g1, cam, k=2)
+    _check_image(res1, ref1, S1, rays)
+
+
+@pytest.mark.slow
+def test_forward_surface_full_size_sampled():
+    """1M-Gaussian surface scene at 1920x1080, k = 16: full GPU frame, oracle on 4 seeded
+    16x16 crops (brute force over every Gaussian)."""
+    g, cam, cfg = scenes.config_surface()
+    sc = R.Scene.from_params(g)
+    out = R.render(sc, cam, k=16, ids_cap=512, want_n_blended=True)
+    torch.cuda.synchronize()
+    rgbT = out["rgbT"].cpu().numpy()
+    ids = out["ids"].cpu().numpy()
+    nb = out["n_blended"].cpu().numpy()
+    S = O.Scene.from_params(g)
+    rays = O.camera_rays(cam)
+    rng = np.random.default_rng(11)
+    idx = np.concatenate([scenes.crop_rays_index(cam["width"], int(rng.integers(0, cam["width"] - 16)),
+                                                 int(rng.integers(0, cam["height"] - 16)), 16, 16)
+                          for _ in range(4)])
+    sub = tuple(a[idx] for a in rays)
+    ref = S.render(sub, ids_cap=512)
+    err = np.abs(rgbT[idx].astype(np.float64) - ref["out"]).max(0)
+    assert err.max() <= RGB_TOL, err
+    bad = compare_hit_lists(S, sub, ids[idx], nb[idx], ref["ids"], ref["n_blend"])
+    assert not bad
+    assert np.all(rgbT[:, 3] >= 0) and np.all(rgbT[:, 3] <= 1) and np.isfinite(rgbT).all()
+
+
+# ------------------------------------------------------------------ a10: backward
+
+
+def test_backward_matches_oracle_gradient():
+    g, cam = _dense()
+    g = g.subset(np.arange(3000))
+    cam = scenes.pinhole_camera(24, 20, (0.0, 0.0, -3.0), (0, 0, 0), 45.0)
+    rng = np.random.default_rng(8)
+    w = rng.normal(0, 1, (cam["width"] * cam["height"], 4))
+    sc = R.Scene.from_params(g)
+    fwd = R.render(sc, cam, k=4)["rgbT"]
+    grads = R.backward(sc, cam, fwd, torch.from_numpy(w.astype(np.float32)).cuda(), k=4)
+    torch.cuda.synchronize()
+    S = O.Scene.from_params(g)
+    rays = O.camera_rays(cam)
+    ref = S.backward(rays, w)
+    names = {"means": "means", "log_scales": "log_scales", "quats": "quats", "opacity_logits": "logits", "sh": "sh"}
+    for k_gpu, k_or in names.items():
+        e = rel_err(grads[k_gpu].cpu().numpy(), ref[k_or])
+        assert e <= 1e-3, (k_gpu, e)
+
+
+def test_autograd_function_runs_and_matches_backward():
+    g, cam = _dense()
+    g = g.subset(np.arange(2000))
+    cam = scenes.pinhole_camera(16, 16, (0.0, 0.0, -3.0), (0, 0, 0), 45.0)
+    params = [torch.from_numpy(a).cuda().requires_grad_(True) for a in g.arrays()]
+    out = R.render_differentiable(*params, g.sh_degree, cam, k=8)
+    w = torch.randn_like(out)
+    (out * w).sum().backward()
+    S = O.Scene.from_params(g)
+    ref = S.backward(O.camera_rays(cam), w.cpu().numpy().astype(np.float64))
+    assert rel_err(params[0].grad.cpu().numpy(), ref["means"]) <= 1e-3
+    assert rel_err(params[4].grad.cpu().numpy(), ref["sh"]) <= 1e-3
