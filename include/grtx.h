@@ -299,6 +299,30 @@ GRTX_API int grtx_trace_backward(grtx_scene *scene, const grtx_gaussians *g,
                                  const grtx_grads *grads, void *stream);
 
 /* ---------------------------------------------------------------------------------------- */
+/* Allocation-free forward trace                                                             */
+/* ---------------------------------------------------------------------------------------- */
+
+/* The paper has no counterpart to this entry point. It is for callers that must not allocate
+ * device memory while they render: a renderer that reserves its whole memory budget at
+ * start-up and may not grow it, or a frame loop that cannot afford to wait on the allocator.
+ * grtx_trace_forward may allocate (it grows a per-scene workspace on first use); this variant
+ * never does. It renders cam like grtx_trace_forward with rgbT = d_rgbT (device [n_rays][4],
+ * 16-byte aligned, caller-owned) and no optional outputs. Its scratch -- the ray-queue
+ * counter and the per-ray-slot checkpoint and eviction lists -- lives in one library-owned
+ * device array of GRTX_NOALLOC_SCRATCH_BYTES (32 MiB) that every GPU which loads the library
+ * holds until the process exits. The number of rays in flight is whatever fits in that array
+ * (about 13,000 with the default capacities 128 / 64, against about 58,000 for
+ * grtx_trace_forward at k = 16), so a frame may take longer. If one block of 128 ray slots
+ * does not fit (large ckpt_capacity / evict_capacity) it returns GRTX_ERR_INVALID_ARG and says
+ * so in grtx_last_error(). The first call on a device looks up the array's device address
+ * with that device current; make that first call before any stream capture begins. Every
+ * call uses the same array: calls whose work overlaps on the GPU (different streams, or
+ * threads without ordering) race and produce wrong images, so order them on one stream. */
+#define GRTX_NOALLOC_SCRATCH_BYTES (32u << 20)
+GRTX_API int grtx_trace_forward_noalloc(grtx_scene *scene, const grtx_camera *cam,
+                                        const grtx_params *p, float *d_rgbT, void *stream);
+
+/* ---------------------------------------------------------------------------------------- */
 /* Serving: several resident scenes, camera requests batched into persistent launches.      */
 /* ---------------------------------------------------------------------------------------- */
 

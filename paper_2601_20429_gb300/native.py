@@ -154,6 +154,7 @@ _SIGS = {
                                      C.POINTER(grtx_trace_outputs), _fp]),
     "grtx_trace_backward": (C.c_int, [_fp, C.POINTER(grtx_gaussians), C.POINTER(grtx_camera), C.POINTER(grtx_params),
                                       _fp, _fp, C.POINTER(grtx_grads), _fp]),
+    "grtx_trace_forward_noalloc": (C.c_int, [_fp, C.POINTER(grtx_camera), C.POINTER(grtx_params), _fp, _fp]),
     "grtx_server_create": (C.c_int, [C.POINTER(_fp), C.c_int, C.POINTER(grtx_params), C.c_int64, C.c_int, _fp,
                                      C.POINTER(_fp)]),
     "grtx_server_submit": (C.c_int, [_fp, C.POINTER(grtx_request), C.c_int]),
@@ -331,6 +332,11 @@ def grtx_trace_forward(scene: int, cam: grtx_camera, p: grtx_params, rgbT, n_ble
     out.stats = ptr(stats)
     check(lib().grtx_trace_forward(C.c_void_p(scene), C.byref(cam), C.byref(p), C.byref(out), stream_handle(stream)),
           "grtx_trace_forward")
+
+
+def grtx_trace_forward_noalloc(scene: int, cam: grtx_camera, p: grtx_params, rgbT, stream=None):
+    check(lib().grtx_trace_forward_noalloc(C.c_void_p(scene), C.byref(cam), C.byref(p), ptr(rgbT),
+                                           stream_handle(stream)), "grtx_trace_forward_noalloc")
 
 
 def grtx_trace_backward(scene: int, g: grtx_gaussians, cam: grtx_camera, p: grtx_params, rgbT, dL_drgbT,
