@@ -48,6 +48,35 @@ def parse():
     return ap.parse_args()
 
 
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("trace_impl.cuh", "trace.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2601_20429_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(name: str):
+    """DRAM bytes per launch recorded in profiles/<name>.md by an ncu capture, if the trace
+    kernel's source is unchanged since (its hash is recorded beside the figure)."""
+    path = os.path.join(ROOT, "profiles", name + ".md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -381,9 +410,12 @@ def main():
                16 * (st["ckpt_writes"] + st["evictions"]) + 16 * st["rays"])
     achieved = logical / (ms / 1e3) / 1e9
     peak = peaks.get("hbm_gbs", 6800.0)
+    traffic = profiled_traffic("k_trace16_surface1M_1080p")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_trace<16, sphere>",
+                "traffic": traffic, "kernel": "k_trace<16, sphere>",
                 "bytes_per_ray": logical / max(st["rays"], 1),
+                "dram_frac": (traffic / (ms / 1e3) / 1e9 / peak) if traffic else None,
+                "kernel_source_hash": kernel_source_hash(),
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
 
     serving = None

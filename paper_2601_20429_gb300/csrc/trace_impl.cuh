@@ -123,24 +123,65 @@ __device__ __forceinline__ float safe_rcp(float x)
 }
 
 // ------------------------------------------------------------------------------------------
-// k-buffer (Sec. III-A): ascending keys (t, leaf index) in registers. Insertion bubbles the
-// new key into place; the key that falls off the end (the farthest, or +inf if there was a
-// free slot) is left in (ct, ci).
+// k-buffer (Sec. III-A): the k nearest keys (t, leaf index) found so far, ascending. It lives in
+// shared memory as a structure of arrays over the block's 128 threads (entry j of thread x at
+// [j * 128 + x], so a warp touching one entry hits 32 distinct banks), which keeps its 2k
+// words out of the register file; t_max, the farthest kept depth once full, stays in a register.
 // ------------------------------------------------------------------------------------------
+constexpr int kBlock = 128;
+
 template <int K>
-__device__ __forceinline__ void kbuf_insert(float (&kt)[K], uint32_t (&ki)[K], float &ct, uint32_t &ci)
-{
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-        bool lt = ct < kt[j] || (ct == kt[j] && ci < ki[j]);
-        float tt = lt ? kt[j] : ct;
-        uint32_t ti = lt ? ki[j] : ci;
-        kt[j] = lt ? ct : kt[j];
-        ki[j] = lt ? ci : ki[j];
-        ct = tt;
-        ci = ti;
+struct KBuf {
+    float *t;
+    uint32_t *id;
+    int n;
+    float tmax;
+    __device__ __forceinline__ void clear()
+    {
+        n = 0;
+        tmax = GRTX_INF;
     }
-}
+    __device__ __forceinline__ float T(int j) const { return t[j * kBlock]; }
+    __device__ __forceinline__ uint32_t I(int j) const { return id[j * kBlock]; }
+    __device__ __forceinline__ bool contains(float ct, uint32_t ci) const
+    {
+        for (int j = 0; j < n; ++j)
+            if (t[j * kBlock] == ct && id[j * kBlock] == ci) return true;
+        return false;
+    }
+    // Insert (ct, ci) in key order. When the buffer was already full the larger of {new key,
+    // farthest kept key} is rejected: it is returned in (ct, ci) and the result is true.
+    __device__ __forceinline__ bool insert(float &ct, uint32_t &ci)
+    {
+        int pos;
+        bool rejected = false;
+        float nt = ct;
+        uint32_t ni = ci;
+        if (n == K) {
+            float lt = t[(K - 1) * kBlock];
+            uint32_t li = id[(K - 1) * kBlock];
+            if (!(nt < lt || (nt == lt && ni < li))) return true;
+            ct = lt;
+            ci = li;
+            rejected = true;
+            pos = K - 1;
+        } else {
+            pos = n++;
+        }
+        while (pos > 0) {
+            float pt = t[(pos - 1) * kBlock];
+            uint32_t pi = id[(pos - 1) * kBlock];
+            if (!(nt < pt || (nt == pt && ni < pi))) break;
+            t[pos * kBlock] = pt;
+            id[pos * kBlock] = pi;
+            --pos;
+        }
+        t[pos * kBlock] = nt;
+        id[pos * kBlock] = ni;
+        if (n == K) tmax = t[(K - 1) * kBlock];
+        return rejected;
+    }
+};
 
 __device__ __forceinline__ bool key_after(float t, uint32_t i, float Lt, uint32_t Li)
 {
@@ -228,18 +269,20 @@ __device__ __forceinline__ bool sphere_test(const float4 *__restrict__ g, float3
 }
 
 // Real spherical harmonics up to degree 3 (no Condon-Shortley phase), index l*l + l + m,
-// times the coefficients: c = max(0, sum_k Y_k(dir) f_k + 0.5). raw receives the sum + 0.5.
-__device__ __forceinline__ void sh_color(const float *__restrict__ f, int deg, float3 n, float c[3], float raw[3],
-                                         float Y[16])
+// times the coefficients: c = max(0, sum_k Y_k(dir) f_k + 0.5); raw receives the sum + 0.5.
+// The record holds the coefficients as (k, channel) pairs padded to a multiple of 4 floats
+// and is read with float4 loads.
+__device__ __forceinline__ void sh_color(const float *__restrict__ f, int deg, int stride, float3 n, float c[3],
+                                         float raw[3], float Y[16])
 {
     float x = n.x, y = n.y, z = n.z;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) Y[k] = 0.f;
     Y[0] = 0.28209479177387814f;
-    int nk = 1;
     if (deg >= 1) {
         Y[1] = 0.4886025119029199f * y;
         Y[2] = 0.4886025119029199f * z;
         Y[3] = 0.4886025119029199f * x;
-        nk = 4;
     }
     if (deg >= 2) {
         Y[4] = 1.0925484305920792f * x * y;
@@ -247,7 +290,6 @@ __device__ __forceinline__ void sh_color(const float *__restrict__ f, int deg, f
         Y[6] = 0.31539156525252005f * (3.f * z * z - 1.f);
         Y[7] = 1.0925484305920792f * x * z;
         Y[8] = 0.5462742152960396f * (x * x - y * y);
-        nk = 9;
     }
     if (deg >= 3) {
         Y[9] = 0.5900435899266435f * y * (3.f * x * x - y * y);
@@ -257,16 +299,24 @@ __device__ __forceinline__ void sh_color(const float *__restrict__ f, int deg, f
         Y[13] = 0.4570457994644658f * x * (5.f * z * z - 1.f);
         Y[14] = 1.445305721320277f * z * (x * x - y * y);
         Y[15] = 0.5900435899266435f * x * (x * x - 3.f * y * y);
-        nk = 16;
     }
-    float r0 = 0.5f, r1 = 0.5f, r2 = 0.5f;
-    for (int k = 0; k < nk; ++k) {
-        r0 = fmaf(Y[k], __ldg(f + 3 * k), r0);
-        r1 = fmaf(Y[k], __ldg(f + 3 * k + 1), r1);
-        r2 = fmaf(Y[k], __ldg(f + 3 * k + 2), r2);
+    float acc[3] = {0.5f, 0.5f, 0.5f};
+    const int n_vec = stride >> 2;
+    const float4 *f4 = reinterpret_cast<const float4 *>(f);
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+        if (j < n_vec) {
+            float4 q = __ldg(f4 + j);
+            const float qq[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int i = 4 * j + e;                // flat index = 3 k + channel
+                if (i < 48) acc[i % 3] = fmaf(Y[i / 3], qq[e], acc[i % 3]);
+            }
+        }
     }
-    raw[0] = r0; raw[1] = r1; raw[2] = r2;
-    c[0] = fmaxf(r0, 0.f); c[1] = fmaxf(r1, 0.f); c[2] = fmaxf(r2, 0.f);
+    raw[0] = acc[0]; raw[1] = acc[1]; raw[2] = acc[2];
+    c[0] = fmaxf(acc[0], 0.f); c[1] = fmaxf(acc[1], 0.f); c[2] = fmaxf(acc[2], 0.f);
 }
 
 // Slab test of one child box against the ray over [tn, tf]: entry / exit distances.
@@ -311,13 +361,13 @@ __device__ __forceinline__ bool trace_round(const TraceArgs &a, const SceneRef &
                                             float inv_len, float tn, float tf,
                                             float Lt, uint32_t Li, bool ckpt, bool from_root,
                                             const uint2 *__restrict__ src, int n_src, uint2 *__restrict__ dst,
-                                            int &n_dst, uint2 *__restrict__ ev, int &n_ev, float (&kt)[K],
-                                            uint32_t (&ki)[K], Counters &cnt)
+                                            int &n_dst, uint2 *__restrict__ ev, int &n_ev, KBuf<K> &kb,
+                                            Counters &cnt)
 {
     const size_t S = (size_t)a.n_slots;
     uint2 stack[GRTX_STACK];
     int sp = 0, si = 0;
-    float tmax = kt[K - 1];
+    float tmax = kb.tmax;
     uint32_t ref;
     float te;
     n_dst = 0;
@@ -356,22 +406,16 @@ __device__ __forceinline__ bool trace_round(const TraceArgs &a, const SceneRef &
             float t, D2, w[3];
             if (touch && sphere_test(sc.geom + 4 * (size_t)gi, o, d, t, D2, w)) {
                 if (D2 <= 1.0f && t > tn && t <= tf && key_after(t, gi, Lt, Li)) {
-                    bool dup = false;
-                    if (PROXY) {
-#pragma unroll
-                        for (int j = 0; j < K; ++j) dup |= (kt[j] == t && ki[j] == gi);
-                    }
-                    if (!dup) {
+                    if (!PROXY || !kb.contains(t, gi)) {
                         float ct = t;
                         uint32_t ci = gi;
-                        kbuf_insert<K>(kt, ki, ct, ci);
-                        if (ct != GRTX_INF && ckpt) {          // any-hit: rejected -> eviction list
+                        if (kb.insert(ct, ci) && ckpt) {       // any-hit: rejected -> eviction list
                             if (n_ev >= a.evict_cap) return false;
                             ev[(size_t)n_ev * S] = make_uint2(__float_as_uint(ct), ci);
                             ++n_ev;
                             if (INSTR) cnt.evictions++;
                         }
-                        tmax = kt[K - 1];                      // farthest kept key
+                        tmax = kb.tmax;                        // farthest kept key
                     }
                 }
             }
@@ -467,7 +511,7 @@ __device__ __forceinline__ void blend_one(const TraceArgs &a, const SceneRef &sc
     bool clamped = !(al_raw < a.alpha_max);
     float al = clamped ? a.alpha_max : al_raw;
     float c[3], raw[3], Y[16];
-    sh_color(sc.app + (size_t)idx * sc.app_stride, sc.sh_degree, dn, c, raw, Y);
+    sh_color(sc.app + (size_t)idx * sc.app_stride, sc.sh_degree, sc.app_stride, dn, c, raw, Y);
     float w = st.T * al;
     if (!BWD) {
         st.C[0] = fmaf(w, c[0], st.C[0]);
@@ -555,7 +599,8 @@ __device__ __forceinline__ void blend_one(const TraceArgs &a, const SceneRef &sc
 // ------------------------------------------------------------------------------------------
 template <int K, bool PROXY, bool INSTR, bool BWD>
 __device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc, float4 *__restrict__ out, int slot,
-                                          int64_t pix, float3 o, float3 d, float tn, float tf, Counters &cnt)
+                                          int64_t pix, float3 o, float3 d, float tn, float tf, KBuf<K> &kb,
+                                          Counters &cnt)
 {
     const size_t S = (size_t)a.n_slots;
     float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
@@ -583,18 +628,14 @@ __device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc
     bool done = !sc.has_tree;
     while (!done) {
         if (INSTR) cnt.rounds++;
-        float kt[K];
-        uint32_t ki[K];
-#pragma unroll
-        for (int j = 0; j < K; ++j) { kt[j] = GRTX_INF; ki[j] = GRTX_NONE; }
+        kb.clear();
         if (ckpt && n_ev > 0) {            // raygen: closest evicted hits -> k-buffer
             int w = 0;
             for (int e = 0; e < n_ev; ++e) {
                 uint2 v = ev[(size_t)e * S];
                 float ct = __uint_as_float(v.x);
                 uint32_t ci = v.y;
-                kbuf_insert<K>(kt, ki, ct, ci);
-                if (ct != GRTX_INF) {
+                if (kb.insert(ct, ci)) {
                     ev[(size_t)w * S] = make_uint2(__float_as_uint(ct), ci);
                     ++w;
                 }
@@ -603,32 +644,30 @@ __device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc
         }
         int n_dst = 0;
         if (!trace_round<K, PROXY, INSTR>(a, sc, o, d, inv, inv_len, tn, tf, Lt, Li, ckpt, from_root, src, n_src, dst, n_dst,
-                                          ev, n_ev, kt, ki, cnt)) {
+                                          ev, n_ev, kb, cnt)) {
             // a capacity was exceeded: redo this round from the root and stay in restart mode
             if (INSTR) cnt.fallbacks++;
             ckpt = false;
             from_root = true;
             n_src = 0;
             n_ev = 0;
-#pragma unroll
-            for (int j = 0; j < K; ++j) { kt[j] = GRTX_INF; ki[j] = GRTX_NONE; }
+            kb.clear();
             trace_round<K, PROXY, INSTR>(a, sc, o, d, inv, inv_len, tn, tf, Lt, Li, false, true, src, 0, dst, n_dst, ev, n_ev,
-                                         kt, ki, cnt);
+                                         kb, cnt);
         }
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            if (kt[j] == GRTX_INF) break;
-            blend_one<BWD>(a, sc, st, ki[j], o, d, dn);
+        for (int j = 0; j < kb.n; ++j) {
+            uint32_t idx = kb.I(j);
+            blend_one<BWD>(a, sc, st, idx, o, d, dn);
             if (INSTR) {
-                if (a.ids && nb < a.ids_cap) a.ids[(size_t)pix * a.ids_cap + nb] = sc.gid[ki[j]];
+                if (a.ids && nb < a.ids_cap) a.ids[(size_t)pix * a.ids_cap + nb] = sc.gid[idx];
                 cnt.blended++;
             }
             ++nb;
             if (st.T < a.T_min) { done = true; break; }
         }
-        if (done || kt[K - 1] == GRTX_INF) break;
-        Lt = kt[K - 1];
-        Li = ki[K - 1];
+        if (done || kb.n < K) break;
+        Lt = kb.T(K - 1);
+        Li = kb.I(K - 1);
         if (ckpt) {
             uint2 *tmp = src; src = dst; dst = tmp;
             n_src = n_dst;
@@ -639,11 +678,22 @@ __device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc
     if (INSTR && a.n_blended) a.n_blended[pix] = nb;
 }
 
+// Resident blocks per SM the trace kernels are compiled for. The traversal is latency-bound,
+// so occupancy pays even at the cost of a few spilled registers (measured on GB300: 8 blocks of
+// 128 threads is the best forward setting for k <= 16; the k = 32 k-buffer's 32 KB of shared
+// memory per block allows 6; the backward keeps more live state and prefers 7).
+__host__ __device__ constexpr int trace_min_blocks(int k, bool bwd) { return k >= 32 ? 6 : (bwd ? 7 : 8); }
+
 template <int K, bool PROXY, bool INSTR, bool BWD>
-__global__ void __launch_bounds__(128) k_trace(TraceArgs a)
+__global__ void __launch_bounds__(kBlock, trace_min_blocks(K, BWD)) k_trace(TraceArgs a)
 {
+    __shared__ float s_kt[K * kBlock];
+    __shared__ uint32_t s_ki[K * kBlock];
     const int slot = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
+    KBuf<K> kb;
+    kb.t = s_kt + threadIdx.x;
+    kb.id = s_ki + threadIdx.x;
     Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
     unsigned rays = 0;
     for (;;) {
@@ -656,7 +706,7 @@ __global__ void __launch_bounds__(128) k_trace(TraceArgs a)
         float tn, tf;
         if (make_ray(a.cam, base + lane, pix, o, d, tn, tf)) {
             ++rays;
-            trace_ray<K, PROXY, INSTR, BWD>(a, a.sc, a.rgbT, slot, pix, o, d, tn, tf, cnt);
+            trace_ray<K, PROXY, INSTR, BWD>(a, a.sc, a.rgbT, slot, pix, o, d, tn, tf, kb, cnt);
         }
         __syncwarp();
     }
@@ -675,10 +725,15 @@ __global__ void __launch_bounds__(128) k_trace(TraceArgs a)
 // Serving step: one persistent launch over the queue items of several requests (each with
 // its own scene, camera and output); a warp's 32 items always belong to one request.
 template <int K>
-__global__ void __launch_bounds__(128) k_serve(TraceArgs a, const ServeSeg *__restrict__ segs, int n_segs)
+__global__ void __launch_bounds__(kBlock, trace_min_blocks(K, false)) k_serve(TraceArgs a, const ServeSeg *__restrict__ segs, int n_segs)
 {
+    __shared__ float s_kt[K * kBlock];
+    __shared__ uint32_t s_ki[K * kBlock];
     const int slot = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
+    KBuf<K> kb;
+    kb.t = s_kt + threadIdx.x;
+    kb.id = s_ki + threadIdx.x;
     Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
     for (;;) {
         unsigned base = 0;
@@ -698,7 +753,7 @@ __global__ void __launch_bounds__(128) k_serve(TraceArgs a, const ServeSeg *__re
         float3 o, d;
         float tn, tf;
         if (make_ray(cam, item, pix, o, d, tn, tf))
-            trace_ray<K, false, false, false>(a, sc, sg.out, slot, pix, o, d, tn, tf, cnt);
+            trace_ray<K, false, false, false>(a, sc, sg.out, slot, pix, o, d, tn, tf, kb, cnt);
         __syncwarp();
     }
 }
