@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-extra", action="store_true", help="skip the differentiable and outdoor measurements")
     return ap.parse_args()
 
 
@@ -322,6 +323,81 @@ def bench_serving(n_requests: int):
             "offered_Mrays_per_s": rays / (reqs[-1]["arrival"] - reqs[0]["arrival"]) / 1e6}
 
 
+def bench_differentiable(steps: int, warmup: int, stream):
+    """Training-style step on the 256K-Gaussian scene at 800x800: rebuild the BVH from the
+    current parameters, render, L2 loss against the target image, backward."""
+    import torch
+    from paper_2601_20429_gb300 import render as R
+    from paper_2601_20429_gb300 import scenes
+    g, target_g, cam, cfg = scenes.config_differentiable()
+    tsc = R.Scene.from_params(target_g)
+    target = R.render(tsc, cam, k=cfg["k"])["rgbT"].clone()
+    tsc.close()
+    params = [t.requires_grad_(True) for t in R.params_to_device(g)]
+
+    def step():
+        for t in params:
+            t.grad = None
+        out = R.render_differentiable(*params, g.sh_degree, cam, k=cfg["k"])
+        loss = ((out[:, :3] - target[:, :3]) ** 2).mean()
+        loss.backward()
+        return loss
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        loss = step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    rays = cam["width"] * cam["height"]
+    return {"workload": "256K surface Gaussians, 800x800, L2 loss vs perturbed-parameter target, k=16",
+            "ms_per_step": ms, "Mrays_per_s": rays / (ms / 1e3) / 1e6, "loss": float(loss.item()),
+            "step": "BVH build + forward + backward (atomics into all five parameter tensors)"}
+
+
+def bench_outdoor(steps: int, stream, flush):
+    """6M-Gaussian outdoor scene, 1920x1080 fisheye plus one mirror bounce: primary and
+    secondary rays timed separately (explicit ray lists), k = 16."""
+    import torch
+    from paper_2601_20429_gb300 import native as N
+    from paper_2601_20429_gb300 import render as R
+    from paper_2601_20429_gb300 import scenes
+    g, cam, mirror, cfg = scenes.config_outdoor()
+    t0 = time.perf_counter()
+    sc = R.Scene.from_params(g)
+    torch.cuda.synchronize()
+    build_ms = (time.perf_counter() - t0) * 1e3
+    del g
+    n = cam["width"] * cam["height"]
+    prim = [torch.empty((n, 3), device="cuda"), torch.empty((n, 3), device="cuda"), torch.empty(n, device="cuda"),
+            torch.empty(n, device="cuda")]
+    sec = [torch.empty((n, 3), device="cuda"), torch.empty((n, 3), device="cuda"), torch.empty(n, device="cuda"),
+           torch.empty(n, device="cuda")]
+    spix = torch.empty(n, dtype=torch.int32, device="cuda")
+    ns = torch.zeros(1, dtype=torch.int32, device="cuda")
+    N.grtx_mirror_rays(N.make_camera(cam), N.make_mirror(mirror), prim, sec, spix, ns)
+    m = int(ns.item())
+    sec_rays = [t[:m] for t in sec]
+    out_p = torch.empty((n, 4), device="cuda")
+    out_s = torch.empty((max(m, 1), 4), device="cuda")
+    tp = time_frames(lambda: R.render(sc, None, rays=prim, k=cfg["k"], out=out_p), steps, 2, flush, stream)
+    ts = time_frames(lambda: R.render(sc, None, rays=sec_rays, k=cfg["k"], out=out_s), steps, 2, flush, stream)
+    st_p = N.stats_dict(R.render(sc, None, rays=prim, k=cfg["k"], want_stats=True)["stats"])
+    st_s = N.stats_dict(R.render(sc, None, rays=sec_rays, k=cfg["k"], want_stats=True)["stats"])
+    sc.close()
+    return {"workload": "6M outdoor Gaussians, 1920x1080 equidistant fisheye, one 4x3 m mirror, k=16",
+            "build_ms": build_ms, "secondary_rays": m,
+            "primary": {"Mrays_per_s": n / (statistics.mean(tp) / 1e3) / 1e6, "ms": statistics.mean(tp),
+                        "nodes_per_ray": nodes_per_ray(st_p)},
+            "secondary": {"Mrays_per_s": m / (statistics.mean(ts) / 1e3) / 1e6, "ms": statistics.mean(ts),
+                          "nodes_per_ray": nodes_per_ray(st_s)}}
+
+
 def main():
     args = parse()
     dist = Dist()
@@ -422,6 +498,11 @@ def main():
     if dist.world == 1 and not args.no_serving:
         serving = bench_serving(args.serve_requests)
 
+    differentiable = outdoor = None
+    if dist.world == 1 and not args.no_extra:
+        differentiable = bench_differentiable(max(3, args.steps // 3), 2, stream)
+        outdoor = bench_outdoor(max(3, args.steps // 3), stream, flush)
+
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         rate, nsamp, cores = oracle_rate(g, cam, args.cpu_seconds)
@@ -453,6 +534,8 @@ def main():
             "e2e": {"value": e2e_val / 1e6, "unit": "Mrays/s", "h2d_bytes_per_step": 112,
                     "d2h_bytes_per_step": n_rays * 16},
             "serving": serving,
+            "differentiable": differentiable,
+            "outdoor": outdoor,
             "cpu_baseline": cpu,
             "clocks": clk,
         }

@@ -298,6 +298,40 @@ GRTX_API int grtx_trace_backward(grtx_scene *scene, const grtx_gaussians *g,
                                  const float *d_rgbT, const float *d_dL_drgbT,
                                  const grtx_grads *grads, void *stream);
 
+/* A rectangular planar mirror for secondary rays (Sec. VI "GRTX-HW on Secondary Rays").
+ * center: a point of the mirror; normal: unit normal; axis_u / axis_v: unit in-plane axes;
+ * the mirror is {center + a axis_u + b axis_v : |a| <= half_u, |b| <= half_v}.
+ * t_near_secondary: t_near of the reflected rays (keeps them off the mirror). */
+typedef struct grtx_mirror {
+    float center[3], normal[3], axis_u[3], axis_v[3];
+    float half_u, half_v;
+    float t_near_secondary;
+    float reserved;
+} grtx_mirror;
+
+/* Rays of a camera with one mirror bounce. Every primary ray (width*height, pixel order) is
+ * written to the d_prim_* arrays with t_far clipped to the mirror where it hits it (in
+ * (t_near, t_far)). Each primary that hits spawns one secondary ray: origin at the hit point,
+ * direction reflected about the normal (d - 2 (d.n) n), t_near = m->t_near_secondary,
+ * t_far = +inf. Secondaries are compacted into d_sec_* (capacity width*height) with their
+ * pixel in d_sec_pixel; their count is written to *d_n_sec (device). The order of the
+ * secondary list is unspecified; d_sec_pixel identifies each ray. All device, caller-owned:
+ * origins/dirs [n][3], tnear/tfar [n]. */
+GRTX_API int grtx_mirror_rays(const grtx_camera *cam, const grtx_mirror *m, float *d_prim_origins,
+                              float *d_prim_dirs, float *d_prim_tnear, float *d_prim_tfar,
+                              float *d_sec_origins, float *d_sec_dirs, float *d_sec_tnear,
+                              float *d_sec_tfar, int32_t *d_sec_pixel, int32_t *d_n_sec,
+                              void *stream);
+
+/* Composite the secondary image behind the primary one: for each of the *d_n_sec secondary
+ * rays j (at most max_sec) with pixel p = d_sec_pixel[j], the primary pixel (C + T bg, T)
+ * becomes (C + T C2, T T2) where (C2, T2) = d_sec_rgbT[j] rendered with the same bg, i.e.
+ * the reflection replaces the primary's background term (Eq. volume-render continued past
+ * the mirror). d_rgbT [n_pixels][4] in/out, d_sec_rgbT [max_sec][4]; device, 16-byte aligned. */
+GRTX_API int grtx_composite_bounce(float *d_rgbT, const float *d_sec_rgbT, const int32_t *d_sec_pixel,
+                                   const int32_t *d_n_sec, int64_t max_sec, const float bg[3],
+                                   void *stream);
+
 /* ---------------------------------------------------------------------------------------- */
 /* Allocation-free forward trace                                                             */
 /* ---------------------------------------------------------------------------------------- */

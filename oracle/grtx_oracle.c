@@ -950,3 +950,60 @@ OG_API void og_refit(int n, const uint32_t *left, const uint32_t *right, const f
     float root[6];
     if (n >= 2) og_refit_rec(0u, left, right, leaf_aabb, node_aabb, root);
 }
+
+/* ------------------------------------------------------------------------------------ */
+/* One bounce off a rectangular planar mirror (Sec. VI "GRTX-HW on Secondary Rays").     */
+/* ------------------------------------------------------------------------------------ */
+
+typedef struct og_mirror {
+    double center[3], normal[3], axis_u[3], axis_v[3];
+    double half_u, half_v, t_near_secondary;
+} og_mirror;
+
+/* Primary rays of cam with t_far clipped where they hit the mirror, and one reflected ray per
+ * such primary (origin at the hit point, direction d - 2 (d.n) n, t in (t_near_secondary, inf)).
+ * Secondaries are listed in pixel order; returns their number. */
+OG_API int og_mirror_rays(const og_camera *cam, const og_mirror *m, double *po, double *pd, double *ptn,
+                          double *ptf, double *so, double *sd, double *stn, double *stf, int *spix)
+{
+    og_camera_rays(cam, po, pd, ptn, ptf);
+    int n = cam->width * cam->height, ns = 0;
+    for (int p = 0; p < n; ++p) {
+        const double *o = po + 3 * p, *d = pd + 3 * p;
+        double den = 0, num = 0;
+        for (int a = 0; a < 3; ++a) { den += d[a] * m->normal[a]; num += (m->center[a] - o[a]) * m->normal[a]; }
+        if (den == 0.0) continue;
+        double t = num / den;
+        if (!(t > ptn[p] && t < ptf[p])) continue;
+        double q[3], du = 0, dv = 0;
+        for (int a = 0; a < 3; ++a) q[a] = o[a] + t * d[a];
+        for (int a = 0; a < 3; ++a) {
+            du += (q[a] - m->center[a]) * m->axis_u[a];
+            dv += (q[a] - m->center[a]) * m->axis_v[a];
+        }
+        if (fabs(du) > m->half_u || fabs(dv) > m->half_v) continue;
+        ptf[p] = t;
+        for (int a = 0; a < 3; ++a) {
+            so[3 * ns + a] = q[a];
+            sd[3 * ns + a] = d[a] - 2.0 * den * m->normal[a];
+        }
+        stn[ns] = m->t_near_secondary;
+        stf[ns] = INFINITY;
+        spix[ns] = p;
+        ++ns;
+    }
+    return ns;
+}
+
+/* Continue Eq. volume-render past the mirror: the primary pixel (C + T bg, T) becomes
+ * (C + T C2, T T2) with (C2, T2) the secondary ray's pixel rendered against the same bg. */
+OG_API void og_composite_bounce(double *rgbT, const double *sec_rgbT, const int *spix, int n_sec, const double bg[3])
+{
+    for (int j = 0; j < n_sec; ++j) {
+        double *a = rgbT + 4 * spix[j];
+        const double *b = sec_rgbT + 4 * j;
+        double T = a[3];
+        for (int c = 0; c < 3; ++c) a[c] = (a[c] - T * bg[c]) + T * b[c];
+        a[3] = T * b[3];
+    }
+}

@@ -56,6 +56,12 @@ class OgRoundStats(C.Structure):
                 ("nodes", "leaves", "rounds", "ckpt_writes", "evictions", "fallbacks", "unique_nodes")]
 
 
+class OgMirror(C.Structure):
+    _fields_ = [("center", C.c_double * 3), ("normal", C.c_double * 3), ("axis_u", C.c_double * 3),
+                ("axis_v", C.c_double * 3), ("half_u", C.c_double), ("half_v", C.c_double),
+                ("t_near_secondary", C.c_double)]
+
+
 class OgGrads(C.Structure):
     _fields_ = [(n, C.POINTER(C.c_double)) for n in ("means", "log_scales", "quats", "logits", "sh")]
 
@@ -95,6 +101,9 @@ def lib():
                                            _ip, C.POINTER(OgRoundStats), C.c_int]
             L.og_backward.argtypes = [C.c_void_p, C.POINTER(OgParams), C.c_int, _dp, _dp, _dp, _dp, _dp,
                                       C.POINTER(OgGrads)]
+            L.og_mirror_rays.restype = C.c_int
+            L.og_mirror_rays.argtypes = [C.POINTER(OgCamera), C.POINTER(OgMirror)] + [_dp] * 8 + [_ip]
+            L.og_composite_bounce.argtypes = [_dp, _dp, _ip, C.c_int, _dp]
             L.og_centroid_bounds.argtypes = [C.c_int, _fp, _fp]
             L.og_morton63.argtypes = [C.c_int, _fp, _fp, _u64p]
             L.og_radix_tree.argtypes = [C.c_int, _u64p, _u32p, _u32p]
@@ -291,3 +300,34 @@ def refit(left: np.ndarray, right: np.ndarray, leaf_aabb_f32: np.ndarray) -> np.
         lib().og_refit(n, _p(np.ascontiguousarray(left, dtype=np.uint32), _u32p),
                        _p(np.ascontiguousarray(right, dtype=np.uint32), _u32p), _p(la, _fp), _p(node, _fp))
     return node
+
+
+def make_mirror(m: dict) -> OgMirror:
+    g = OgMirror()
+    for name in ("center", "normal", "axis_u", "axis_v"):
+        arr = getattr(g, name)
+        for i in range(3):
+            arr[i] = float(m[name][i])
+    g.half_u, g.half_v, g.t_near_secondary = float(m["half_u"]), float(m["half_v"]), float(m["t_near_secondary"])
+    return g
+
+
+def mirror_rays(cam: dict, mirror: dict):
+    """(primary rays, secondary rays, secondary pixel indices): primaries clipped at the mirror."""
+    c = make_camera(cam)
+    n = c.width * c.height
+    prim = [np.empty((n, 3)), np.empty((n, 3)), np.empty(n), np.empty(n)]
+    sec = [np.empty((n, 3)), np.empty((n, 3)), np.empty(n), np.empty(n)]
+    spix = np.empty(n, dtype=np.int32)
+    ns = lib().og_mirror_rays(C.byref(c), C.byref(make_mirror(mirror)), *[_p(a) for a in prim],
+                              *[_p(a) for a in sec], _p(spix, _ip))
+    return tuple(prim), tuple(a[:ns] for a in sec), spix[:ns].copy()
+
+
+def composite_bounce(rgbT: np.ndarray, sec_rgbT: np.ndarray, spix: np.ndarray, bg=(0.0, 0.0, 0.0)) -> np.ndarray:
+    out = np.ascontiguousarray(rgbT, dtype=np.float64).copy()
+    sec = np.ascontiguousarray(sec_rgbT, dtype=np.float64)
+    sp = np.ascontiguousarray(spix, dtype=np.int32)
+    b = np.asarray(bg, dtype=np.float64)
+    lib().og_composite_bounce(_p(out), _p(sec), _p(sp, _ip), int(sp.shape[0]), _p(b))
+    return out

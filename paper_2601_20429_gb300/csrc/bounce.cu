@@ -1,0 +1,121 @@
+// Secondary rays off a planar rectangular mirror (Sec. VI "GRTX-HW on Secondary Rays": a
+// rectangular mirror placed in the scene, primary and secondary rays traced separately).
+// Primary rays stop at the mirror; each primary that hits it spawns one reflected ray; the
+// reflection is composited behind the primary's Gaussians.
+#include <cuda_runtime.h>
+
+#include "trace_impl.cuh"
+
+int grtx_fill_camera(CamRef &a, unsigned &n_items_out, const grtx_camera *cam);
+
+namespace {
+
+__global__ void k_mirror_rays(CamRef cam, grtx_mirror m, float *__restrict__ po, float *__restrict__ pd,
+                              float *__restrict__ ptn, float *__restrict__ ptf, float *__restrict__ so,
+                              float *__restrict__ sd, float *__restrict__ stn, float *__restrict__ stf,
+                              int32_t *__restrict__ spix, int32_t *__restrict__ n_sec)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t n = (int64_t)cam.width * cam.height;
+    bool hit = false;
+    float3 o = make_float3(0.f, 0.f, 0.f), d = o, q = o, r = o;
+    int64_t pix = -1;
+    if (p < n) {
+        unsigned item;
+        if (cam.cam_type == GRTX_CAMERA_RAYS) {
+            item = (unsigned)p;
+        } else {
+            int x = (int)(p % cam.width), y = (int)(p / cam.width);
+            item = (unsigned)(((y / 4) * cam.tiles_x + (x / 8)) * 32 + (y % 4) * 8 + (x % 8));
+        }
+        float tn, tf;
+        if (make_ray(cam, item, pix, o, d, tn, tf)) {
+            const float3 c = make_float3(m.center[0], m.center[1], m.center[2]);
+            const float3 nn = make_float3(m.normal[0], m.normal[1], m.normal[2]);
+            float den = d.x * nn.x + d.y * nn.y + d.z * nn.z;
+            if (fabsf(den) > 1e-20f) {
+                float t = ((c.x - o.x) * nn.x + (c.y - o.y) * nn.y + (c.z - o.z) * nn.z) / den;
+                if (t > tn && t < tf) {
+                    q = make_float3(fmaf(t, d.x, o.x), fmaf(t, d.y, o.y), fmaf(t, d.z, o.z));
+                    float du = (q.x - c.x) * m.axis_u[0] + (q.y - c.y) * m.axis_u[1] + (q.z - c.z) * m.axis_u[2];
+                    float dv = (q.x - c.x) * m.axis_v[0] + (q.y - c.y) * m.axis_v[1] + (q.z - c.z) * m.axis_v[2];
+                    if (fabsf(du) <= m.half_u && fabsf(dv) <= m.half_v) {
+                        hit = true;
+                        tf = t;
+                        float k2 = 2.0f * den;
+                        r = make_float3(d.x - k2 * nn.x, d.y - k2 * nn.y, d.z - k2 * nn.z);
+                    }
+                }
+            }
+            po[3 * pix] = o.x; po[3 * pix + 1] = o.y; po[3 * pix + 2] = o.z;
+            pd[3 * pix] = d.x; pd[3 * pix + 1] = d.y; pd[3 * pix + 2] = d.z;
+            ptn[pix] = tn;
+            ptf[pix] = tf;
+        }
+    }
+    // warp-aggregated compaction keeps each warp's secondary rays together and in pixel order
+    unsigned mask = __ballot_sync(0xffffffffu, hit);
+    int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0 && mask) base = atomicAdd(n_sec, __popc(mask));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (hit) {
+        int j = base + __popc(mask & ((1u << lane) - 1u));
+        so[3 * j] = q.x; so[3 * j + 1] = q.y; so[3 * j + 2] = q.z;
+        sd[3 * j] = r.x; sd[3 * j + 1] = r.y; sd[3 * j + 2] = r.z;
+        stn[j] = m.t_near_secondary;
+        stf[j] = INFINITY;
+        spix[j] = (int32_t)pix;
+    }
+}
+
+__global__ void k_composite_bounce(float4 *__restrict__ rgbT, const float4 *__restrict__ sec, const int32_t *__restrict__ spix,
+                                   const int32_t *__restrict__ n_sec, float bg0, float bg1, float bg2)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= *n_sec) return;
+    int p = spix[j];
+    float4 a = rgbT[p], b = sec[j];
+    // the primary's background term T bg is replaced by T times the reflected radiance
+    rgbT[p] = make_float4(a.x + a.w * (b.x - bg0), a.y + a.w * (b.y - bg1), a.z + a.w * (b.z - bg2), a.w * b.w);
+}
+
+}  // namespace
+
+extern "C" GRTX_API int grtx_mirror_rays(const grtx_camera *cam, const grtx_mirror *m, float *d_prim_origins,
+                                         float *d_prim_dirs, float *d_prim_tnear, float *d_prim_tfar,
+                                         float *d_sec_origins, float *d_sec_dirs, float *d_sec_tnear,
+                                         float *d_sec_tfar, int32_t *d_sec_pixel, int32_t *d_n_sec, void *stream)
+{
+    CamRef c = {};
+    unsigned items = 0;
+    int st = grtx_fill_camera(c, items, cam);
+    if (st) return st;
+    if (!m || !(m->half_u >= 0.f) || !(m->half_v >= 0.f) || !(m->t_near_secondary >= 0.f))
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "bad mirror");
+    if (!d_prim_origins || !d_prim_dirs || !d_prim_tnear || !d_prim_tfar || !d_sec_origins || !d_sec_dirs ||
+        !d_sec_tnear || !d_sec_tfar || !d_sec_pixel || !d_n_sec)
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "NULL output");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int64_t n = (int64_t)cam->width * cam->height;
+    GRTX_CUDA(cudaMemsetAsync(d_n_sec, 0, sizeof(int32_t), s));
+    k_mirror_rays<<<grtx_div_up(n, 256), 256, 0, s>>>(c, *m, d_prim_origins, d_prim_dirs, d_prim_tnear, d_prim_tfar,
+                                                      d_sec_origins, d_sec_dirs, d_sec_tnear, d_sec_tfar, d_sec_pixel,
+                                                      d_n_sec);
+    GRTX_CHECK_LAUNCH("grtx_mirror_rays");
+    return GRTX_OK;
+}
+
+extern "C" GRTX_API int grtx_composite_bounce(float *d_rgbT, const float *d_sec_rgbT, const int32_t *d_sec_pixel,
+                                              const int32_t *d_n_sec, int64_t max_sec, const float bg[3], void *stream)
+{
+    if (!d_rgbT || !d_sec_rgbT || !d_sec_pixel || !d_n_sec || !bg || max_sec < 0)
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "bad composite arguments");
+    if (((uintptr_t)d_rgbT & 15) || ((uintptr_t)d_sec_rgbT & 15))
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "image buffers must be 16-byte aligned");
+    if (max_sec == 0) return GRTX_OK;
+    k_composite_bounce<<<grtx_div_up(max_sec, 256), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        (float4 *)d_rgbT, (const float4 *)d_sec_rgbT, d_sec_pixel, d_n_sec, bg[0], bg[1], bg[2]);
+    GRTX_CHECK_LAUNCH("grtx_composite_bounce");
+    return GRTX_OK;
+}

@@ -125,6 +125,12 @@ class grtx_scene_info(C.Structure):
                 ("bytes_workspace", C.c_int64), ("bounds", C.c_float * 6)]
 
 
+class grtx_mirror(C.Structure):
+    _fields_ = [("center", C.c_float * 3), ("normal", C.c_float * 3), ("axis_u", C.c_float * 3),
+                ("axis_v", C.c_float * 3), ("half_u", C.c_float), ("half_v", C.c_float),
+                ("t_near_secondary", C.c_float), ("reserved", C.c_float)]
+
+
 class grtx_request(C.Structure):
     _fields_ = [("scene_id", C.c_int32), ("reserved", C.c_int32), ("cam", grtx_camera), ("d_rgbT", _fp),
                 ("tag", C.c_uint64)]
@@ -154,6 +160,8 @@ _SIGS = {
                                      C.POINTER(grtx_trace_outputs), _fp]),
     "grtx_trace_backward": (C.c_int, [_fp, C.POINTER(grtx_gaussians), C.POINTER(grtx_camera), C.POINTER(grtx_params),
                                       _fp, _fp, C.POINTER(grtx_grads), _fp]),
+    "grtx_mirror_rays": (C.c_int, [C.POINTER(grtx_camera), C.POINTER(grtx_mirror)] + [_fp] * 11),
+    "grtx_composite_bounce": (C.c_int, [_fp, _fp, _fp, _fp, C.c_int64, C.POINTER(C.c_float * 3), _fp]),
     "grtx_trace_forward_noalloc": (C.c_int, [_fp, C.POINTER(grtx_camera), C.POINTER(grtx_params), _fp, _fp]),
     "grtx_server_create": (C.c_int, [C.POINTER(_fp), C.c_int, C.POINTER(grtx_params), C.c_int64, C.c_int, _fp,
                                      C.POINTER(_fp)]),
@@ -332,6 +340,28 @@ def grtx_trace_forward(scene: int, cam: grtx_camera, p: grtx_params, rgbT, n_ble
     out.stats = ptr(stats)
     check(lib().grtx_trace_forward(C.c_void_p(scene), C.byref(cam), C.byref(p), C.byref(out), stream_handle(stream)),
           "grtx_trace_forward")
+
+
+def make_mirror(m: dict) -> grtx_mirror:
+    g = grtx_mirror()
+    for name in ("center", "normal", "axis_u", "axis_v"):
+        arr = getattr(g, name)
+        for i in range(3):
+            arr[i] = float(m[name][i])
+    g.half_u, g.half_v, g.t_near_secondary = float(m["half_u"]), float(m["half_v"]), float(m["t_near_secondary"])
+    return g
+
+
+def grtx_mirror_rays(cam: grtx_camera, mirror: grtx_mirror, prim, sec, sec_pixel, n_sec, stream=None):
+    """prim / sec: (origins [n,3], dirs [n,3], tnear [n], tfar [n]) CUDA tensors."""
+    check(lib().grtx_mirror_rays(C.byref(cam), C.byref(mirror), *[ptr(t) for t in prim], *[ptr(t) for t in sec],
+                                 ptr(sec_pixel), ptr(n_sec), stream_handle(stream)), "grtx_mirror_rays")
+
+
+def grtx_composite_bounce(rgbT, sec_rgbT, sec_pixel, n_sec, bg=(0.0, 0.0, 0.0), stream=None):
+    b = (C.c_float * 3)(*bg)
+    check(lib().grtx_composite_bounce(ptr(rgbT), ptr(sec_rgbT), ptr(sec_pixel), ptr(n_sec), int(sec_rgbT.shape[0]),
+                                      C.byref(b), stream_handle(stream)), "grtx_composite_bounce")
 
 
 def grtx_trace_forward_noalloc(scene: int, cam: grtx_camera, p: grtx_params, rgbT, stream=None):

@@ -203,8 +203,10 @@ def surface_scene(n: int = 1_000_000, seed: int = 1, n_spheres: int = 100, n_pat
 def outdoor_scene(n: int = 6_000_000, seed: int = 2, size: float = 100.0, n_clusters: int = 500,
                   sh_degree: int = 3) -> GaussianParams:
     """Half the Gaussians on a size x size ground plane (y = 0), half in clusters (blobs or
-    spherical shells, radii log-uniform in [0.2, 5]) scattered over it. Base scales are
-    log-uniform over [0.005, 5] m (three decades), anisotropy as on surfaces."""
+    spherical shells, radii log-uniform in [0.2, 5]) scattered over it. Base scales span
+    three decades, [0.005, 5] m, log-normally distributed (median 3 cm, sigma of ln 1.0, as
+    trained scenes put most Gaussians in the centimetre range with a long tail); anisotropy
+    as on surfaces."""
     rng = np.random.default_rng(seed)
     n_ground = n // 2
     n_cl = n - n_ground
@@ -222,7 +224,7 @@ def outdoor_scene(n: int = 6_000_000, seed: int = 2, size: float = 100.0, n_clus
     c_pts = c_center[cid] + rad[:, None] * u
     pts = np.concatenate([g_pts, c_pts])
     nrm = np.concatenate([g_nrm, u])
-    base = np.exp(rng.uniform(math.log(0.005), math.log(5.0), n))
+    base = np.clip(np.exp(rng.normal(math.log(0.03), 1.0, n)), 0.005, 5.0)
     means, log_scales, quats, logits, sh = _surface_gaussians(rng, pts, nrm, sh_degree, noise=0.0)
     log_scales = log_scales - math.log(0.01) + np.log(base)[:, None]
     return GaussianParams(_f32(means), _f32(log_scales), _f32(quats), _f32(logits), _f32(sh), sh_degree,
@@ -294,3 +296,35 @@ def config_serving(sizes=(500_000, 1_000_000, 2_000_000, 3_000_000), n_requests:
     scenes = [surface_scene(n=s, seed=40 + i) for i, s in enumerate(sizes)]
     reqs = request_stream(n_requests=n_requests, rate_hz=200.0, n_scenes=len(sizes), seed=4)
     return scenes, reqs, dict(k=16, alpha_min=0.01, T_min=1e-3)
+
+
+def outdoor_mirror(seed: int = 2, cam_pos=(0.0, 1.7, 0.0), view=(1.0, 0.0, 0.0)) -> dict:
+    """A 4 x 3 m rectangular mirror at a seeded pose in front of the camera: centre 5-15 m away
+    within +-30 degrees of the view direction at a height of 1.5-2.5 m, facing back towards
+    the camera with a random tilt of up to 20 degrees."""
+    rng = np.random.default_rng(seed + 1000)
+    yaw = math.radians(rng.uniform(-30.0, 30.0))
+    dist = rng.uniform(5.0, 15.0)
+    v = np.asarray(view, dtype=np.float64)
+    side = np.cross(v, [0.0, 1.0, 0.0])
+    horiz = math.cos(yaw) * v + math.sin(yaw) * side
+    center = np.asarray(cam_pos, dtype=np.float64) + dist * horiz
+    center[1] = rng.uniform(1.5, 2.5)
+    to_cam = np.asarray(cam_pos, dtype=np.float64) - center
+    to_cam /= np.linalg.norm(to_cam)
+    tilt = _random_unit(rng, 1)[0] * math.sin(math.radians(rng.uniform(0.0, 20.0)))
+    normal = to_cam + tilt
+    normal /= np.linalg.norm(normal)
+    u = np.cross([0.0, 1.0, 0.0], normal)
+    u /= np.linalg.norm(u)
+    w = np.cross(normal, u)
+    return dict(center=tuple(center), normal=tuple(normal), axis_u=tuple(u), axis_v=tuple(w), half_u=2.0,
+                half_v=1.5, t_near_secondary=1e-3)
+
+
+def config_outdoor(n: int = 6_000_000, width: int = 1920, height: int = 1080):
+    """6M-Gaussian outdoor-like scene (seed 2), equidistant fisheye at (0, 1.7, 0) looking
+    along +x with 90 degrees at half the width, one mirror bounce; k = 16 and 32."""
+    g = outdoor_scene(n=n, seed=2)
+    cam = fisheye_camera(width, height, (0.0, 1.7, 0.0), (1.0, 0.0, 0.0), 90.0)
+    return g, cam, outdoor_mirror(seed=2), dict(k=16, alpha_min=0.01, T_min=1e-3)

@@ -522,3 +522,45 @@ def test_fisheye_angle_proportional_to_radius():
     r = np.hypot(xs, ys).reshape(-1)
     ang = np.arccos(np.clip(d @ np.array(cam["forward"]), -1, 1))
     np.testing.assert_allclose(ang, r * (math.pi / 2) / 20, atol=1e-12)
+
+
+# ---------------------------------------------------------------- mirror bounce
+
+
+def _facing_mirror():
+    return dict(center=(0.0, 0.0, 0.0), normal=(0.0, 0.0, -1.0), axis_u=(1.0, 0.0, 0.0), axis_v=(0.0, 1.0, 0.0),
+                half_u=0.5, half_v=0.5, t_near_secondary=1e-4)
+
+
+def test_mirror_reflects_back_through_the_same_gaussian():
+    """Camera at z = -3 looking at a mirror at z = 0 facing it; one Gaussian at z = -1 on the
+    axis is met by the primary (t = 2) and by the reflected ray (t = 1 from the mirror), so
+    C = a c + (1 - a) a c and T = (1 - a)^2."""
+    a, col = 0.6, np.array([0.9, 0.3, 0.1])
+    S = make_scene([[0, 0, -1.0]], 0.02, [1, 0, 0, 0], a, col)
+    cam = scenes.pinhole_camera(3, 3, (0.0, 0.0, -3.0), (0, 0, 0), 10.0)
+    prim, sec, spix = O.mirror_rays(cam, _facing_mirror())
+    assert list(spix) == list(range(9))                  # every pixel sees the mirror
+    c = 4                                                # centre pixel: the axis ray
+    assert prim[3][c] == pytest.approx(3.0)
+    np.testing.assert_allclose(sec[0][c], [0, 0, 0], atol=1e-15)
+    np.testing.assert_allclose(sec[1][c], [0, 0, -1], atol=1e-15)
+    p = S.render(prim)["out"]
+    s = S.render(sec)["out"]
+    out = O.composite_bounce(p, s, spix)
+    np.testing.assert_allclose(out[c, :3], a * col + (1 - a) * a * col, rtol=1e-12)
+    assert out[c, 3] == pytest.approx((1 - a) ** 2, rel=1e-12)
+
+
+def test_mirror_misses_outside_the_rectangle_and_keeps_background():
+    m = _facing_mirror()
+    m["half_u"] = m["half_v"] = 0.01
+    cam = scenes.pinhole_camera(5, 5, (0.0, 0.0, -3.0), (0, 0, 0), 20.0)
+    prim, sec, spix = O.mirror_rays(cam, m)
+    assert list(spix) == [12]                            # only the centre pixel
+    assert np.isinf(prim[3][np.arange(25) != 12]).all()
+    rgbT = np.tile([0.1, 0.2, 0.3, 0.5], (25, 1))
+    sec_rgbT = np.array([[0.4, 0.4, 0.4, 0.25]])
+    out = O.composite_bounce(rgbT, sec_rgbT, spix, bg=(0.2, 0.2, 0.2))
+    np.testing.assert_allclose(out[12], [0.1 - 0.1 + 0.2, 0.2 - 0.1 + 0.2, 0.3 - 0.1 + 0.2, 0.125])
+    np.testing.assert_array_equal(out[:12], rgbT[:12])
