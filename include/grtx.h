@@ -32,6 +32,8 @@ extern "C" {
 
 #define GRTX_API __attribute__((visibility("default")))
 #define GRTX_VERSION 1
+#define GRTX_DEFAULT_CKPT_CAPACITY 256
+#define GRTX_DEFAULT_EVICT_CAPACITY 128
 
 /* ---------------------------------------------------------------------------------------- */
 /* Status codes                                                                             */
@@ -89,7 +91,8 @@ enum { GRTX_TRAVERSAL_CHECKPOINT = 0, /* resume from checkpointed nodes + evicti
  * right after the Gaussian that takes its transmittance below T_min (1e-3). alpha_max: clamp
  * on alpha before compositing (0.99). bg: background colour added as T * bg.
  * ckpt_capacity / evict_capacity: checkpoint and eviction entries per resident ray slot
- * (Sec. IV-B "Checkpoint and Eviction Buffer"); 0 selects the defaults (128 / 64).
+ * (Sec. IV-B "Checkpoint and Eviction Buffer"); 0 selects GRTX_DEFAULT_CKPT_CAPACITY (256)
+ * and GRTX_DEFAULT_EVICT_CAPACITY (128).
  * traversal: GRTX_TRAVERSAL_*; ignored (always restart) for GRTX_FORM_PROXY20 scenes. */
 typedef struct grtx_params {
     int32_t k;
@@ -345,8 +348,8 @@ GRTX_API int grtx_composite_bounce(float *d_rgbT, const float *d_sec_rgbT, const
  * counter and the per-ray-slot checkpoint and eviction lists -- lives in one library-owned
  * device array of GRTX_NOALLOC_SCRATCH_BYTES (32 MiB) that every GPU which loads the library
  * holds until the process exits. The number of rays in flight is whatever fits in that array
- * (about 13,000 with the default capacities 128 / 64, against about 58,000 for
- * grtx_trace_forward at k = 16), so a frame may take longer. If one block of 128 ray slots
+ * (about 6,500 with the default capacities 256 / 128, against 155,648 for
+ * grtx_trace_forward at k = 16 on 152 SMs), so a frame may take longer. If one block of 128 ray slots
  * does not fit (large ckpt_capacity / evict_capacity) it returns GRTX_ERR_INVALID_ARG and says
  * so in grtx_last_error(). The first call on a device looks up the array's device address
  * with that device current; make that first call before any stream capture begins. Every

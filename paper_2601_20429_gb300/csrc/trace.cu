@@ -183,8 +183,8 @@ int setup(grtx_scene *sc, const grtx_camera *cam, const grtx_params *p, TraceArg
     a.bg0 = p->bg[0];
     a.bg1 = p->bg[1];
     a.bg2 = p->bg[2];
-    a.ckpt_cap = p->ckpt_capacity > 0 ? p->ckpt_capacity : 128;
-    a.evict_cap = p->evict_capacity > 0 ? p->evict_capacity : 64;
+    a.ckpt_cap = p->ckpt_capacity > 0 ? p->ckpt_capacity : GRTX_DEFAULT_CKPT_CAPACITY;
+    a.evict_cap = p->evict_capacity > 0 ? p->evict_capacity : GRTX_DEFAULT_EVICT_CAPACITY;
     return GRTX_OK;
 }
 
@@ -292,5 +292,7 @@ extern "C" GRTX_API int grtx_trace_backward(grtx_scene *sc, const grtx_gaussians
     a.g_logits = grads->opacity_logits;
     a.g_sh = grads->sh;
     a.n_sh = sc->n_coef * 3;
+    a.vec_sh = a.n_sh == 48 && ((uintptr_t)grads->sh & 15) == 0;
+    a.vec_q = ((uintptr_t)grads->quats & 15) == 0;
     return run(sc, a, p->k, false, true, sc->d_counter + 1, S(stream));
 }

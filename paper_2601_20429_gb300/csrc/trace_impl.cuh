@@ -53,6 +53,7 @@ struct TraceArgs {
     const float *means, *log_scales, *quats, *logits;
     float *g_means, *g_log_scales, *g_quats, *g_logits, *g_sh;
     int n_sh;
+    int vec_sh, vec_q;           // gradients of SH (48 floats) / quaternions may use float4 atomics
 };
 
 // One request of a serving step: its scene, camera, output, and which of its queue items
@@ -523,13 +524,26 @@ __device__ __forceinline__ void blend_one(const TraceArgs &a, const SceneRef &sc
     uint32_t gi = sc.gid[idx];
     // colour: dC/dc = T alpha; c = max(0, raw)
     if (a.g_sh) {
-        int nk = (sc.sh_degree + 1) * (sc.sh_degree + 1);
+        const float dc[3] = {raw[0] > 0.f ? st.G[0] * w : 0.f, raw[1] > 0.f ? st.G[1] * w : 0.f,
+                             raw[2] > 0.f ? st.G[2] * w : 0.f};
         float *gs = a.g_sh + (size_t)gi * a.n_sh;
-        for (int ch = 0; ch < 3; ++ch) {
-            if (!(raw[ch] > 0.f)) continue;
-            float dc = st.G[ch] * w;
-            if (dc == 0.f) continue;
-            for (int k = 0; k < nk; ++k) atomic_add_f(gs + 3 * k + ch, dc * Y[k]);
+        if (a.vec_sh) {
+            // degree 3: the 48 coefficient gradients as 12 vector atomics (sm_90+ float4 add)
+            if (dc[0] != 0.f || dc[1] != 0.f || dc[2] != 0.f) {
+#pragma unroll
+                for (int j = 0; j < 12; ++j) {
+                    float v[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) v[e] = Y[(4 * j + e) / 3] * dc[(4 * j + e) % 3];
+                    atomicAdd(reinterpret_cast<float4 *>(gs) + j, make_float4(v[0], v[1], v[2], v[3]));
+                }
+            }
+        } else {
+            int nk = (sc.sh_degree + 1) * (sc.sh_degree + 1);
+            for (int ch = 0; ch < 3; ++ch) {
+                if (dc[ch] == 0.f) continue;
+                for (int k = 0; k < nk; ++k) atomic_add_f(gs + 3 * k + ch, dc[ch] * Y[k]);
+            }
         }
     }
     st.C[0] = fmaf(w, c[0], st.C[0]);
@@ -587,10 +601,16 @@ __device__ __forceinline__ void blend_one(const TraceArgs &a, const SceneRef &sc
         float gz = 2.f * (-2.f * z * Gr[0][0] - w_ * Gr[0][1] + x * Gr[0][2] + w_ * Gr[1][0] - 2.f * z * Gr[1][1] +
                           y * Gr[1][2] + x * Gr[2][0] + y * Gr[2][1]);
         float dot = w_ * gw + x * gx + y * gy + z * gz;
-        atomic_add_f(a.g_quats + 4 * gi + 0, (gw - w_ * dot) * iq);
-        atomic_add_f(a.g_quats + 4 * gi + 1, (gx - x * dot) * iq);
-        atomic_add_f(a.g_quats + 4 * gi + 2, (gy - y * dot) * iq);
-        atomic_add_f(a.g_quats + 4 * gi + 3, (gz - z * dot) * iq);
+        const float4 gq = make_float4((gw - w_ * dot) * iq, (gx - x * dot) * iq, (gy - y * dot) * iq,
+                                      (gz - z * dot) * iq);
+        if (a.vec_q) {
+            atomicAdd(reinterpret_cast<float4 *>(a.g_quats) + gi, gq);
+        } else {
+            atomic_add_f(a.g_quats + 4 * gi + 0, gq.x);
+            atomic_add_f(a.g_quats + 4 * gi + 1, gq.y);
+            atomic_add_f(a.g_quats + 4 * gi + 2, gq.z);
+            atomic_add_f(a.g_quats + 4 * gi + 3, gq.w);
+        }
     }
 }
 
