@@ -436,14 +436,19 @@ def main():
 
     # counters (instrumented run, not timed)
     st_grtx = N.stats_dict(R.render(sc, cam, k=k, out=out, want_stats=True)["stats"])
-    st_plain = N.stats_dict(R.render(sc_plain, cam, k=k, out=out, want_stats=True)["stats"])
+    st_plain = N.stats_dict(R.render(sc_plain, cam, k=k, traversal="restart", out=out, want_stats=True)["stats"])
     st_restart = N.stats_dict(R.render(sc, cam, k=k, traversal="restart", out=out, want_stats=True)["stats"])
+    st_plain_ckpt = N.stats_dict(R.render(sc_plain, cam, k=k, traversal="checkpoint", out=out,
+                                          want_stats=True)["stats"])
 
     def frame():
         R.render(sc, cam, k=k, out=out)
 
     def frame_plain():
-        R.render(sc_plain, cam, k=k, out=out)
+        R.render(sc_plain, cam, k=k, traversal="restart", out=out)
+
+    def frame_plain_ckpt():
+        R.render(sc_plain, cam, k=k, traversal="checkpoint", out=out)
 
     def frame_restart():
         R.render(sc, cam, k=k, traversal="restart", out=out)
@@ -461,6 +466,12 @@ def main():
     value /= 1e6
     times_plain = time_frames(frame_plain, max(5, args.steps // 3), 2, flush, stream)
     times_restart = time_frames(frame_restart, max(5, args.steps // 3), 2, flush, stream)
+    times_plain_ckpt = time_frames(frame_plain_ckpt, max(5, args.steps // 3), 2, flush, stream)
+    k_sweep = {}
+    for kk in (4, 8, 32):
+        tk = time_frames(lambda: R.render(sc, cam, k=kk, out=out), max(5, args.steps // 3), 2, flush, stream)
+        k_sweep[str(kk)] = n_rays / (statistics.mean(tk) / 1e3) / 1e6
+    k_sweep[str(k)] = value
 
     # end to end through the public API: render + read the image back to pinned host memory
     host = torch.empty((n_rays, 4), dtype=torch.float32, pin_memory=True)
@@ -526,6 +537,10 @@ def main():
                      "depth": info["depth"], "workspace_bytes": info["bytes_workspace"]},
             "grtx_restart": {"Mrays_per_s": n_rays / (statistics.mean(times_restart) / 1e3) / 1e6,
                              "ms_per_frame": statistics.mean(times_restart), "nodes_per_ray": nodes_per_ray(st_restart)},
+            "plain_checkpoint": {"Mrays_per_s": n_rays / (statistics.mean(times_plain_ckpt) / 1e3) / 1e6,
+                                 "ms_per_frame": statistics.mean(times_plain_ckpt),
+                                 "nodes_per_ray": nodes_per_ray(st_plain_ckpt)},
+            "k_sweep_Mrays_per_s": k_sweep,
             "plain": {"Mrays_per_s": n_rays / (statistics.mean(times_plain) / 1e3) / 1e6,
                       "ms_per_frame": statistics.mean(times_plain), "nodes_per_ray": nodes_per_ray(st_plain),
                       "build_ms": build_plain_ms, "bvh_bytes": info_plain["bytes_nodes"] + info_plain["bytes_leaves"],

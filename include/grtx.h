@@ -93,7 +93,9 @@ enum { GRTX_TRAVERSAL_CHECKPOINT = 0, /* resume from checkpointed nodes + evicti
  * ckpt_capacity / evict_capacity: checkpoint and eviction entries per resident ray slot
  * (Sec. IV-B "Checkpoint and Eviction Buffer"); 0 selects GRTX_DEFAULT_CKPT_CAPACITY (256)
  * and GRTX_DEFAULT_EVICT_CAPACITY (128).
- * traversal: GRTX_TRAVERSAL_*; ignored (always restart) for GRTX_FORM_PROXY20 scenes. */
+ * traversal: GRTX_TRAVERSAL_*, for either form: {sphere, proxy} x {checkpoint, restart} are the
+ * paper's GRTX, GRTX-HW only (proxy + checkpoint), GRTX-SW only (sphere + restart) and the
+ * baseline (proxy + restart) of Sec. V-B. */
 typedef struct grtx_params {
     int32_t k;
     int32_t traversal;

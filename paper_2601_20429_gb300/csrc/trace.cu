@@ -177,7 +177,7 @@ int setup(grtx_scene *sc, const grtx_camera *cam, const grtx_params *p, TraceArg
     st = fill_camera(a, cam);
     if (st) return st;
     a.sc = grtx_scene_ref(sc);
-    a.traversal = sc->form == GRTX_FORM_PROXY20 ? GRTX_TRAVERSAL_RESTART : p->traversal;
+    a.traversal = p->traversal;
     a.T_min = p->T_min;
     a.alpha_max = p->alpha_max;
     a.bg0 = p->bg[0];
@@ -195,7 +195,7 @@ int run(grtx_scene *sc, TraceArgs &a, int k, bool instr, bool bwd, unsigned *que
     if (occupancy_k(k, proxy, instr, bwd, &bps) != GRTX_OK || bps <= 0)
         return grtx_fail(GRTX_ERR_CUDA, "occupancy query failed");
     int blocks = sm_count() * bps;
-    bool ckpt = !proxy && a.traversal == GRTX_TRAVERSAL_CHECKPOINT;
+    bool ckpt = a.traversal == GRTX_TRAVERSAL_CHECKPOINT;
     int C = ckpt ? a.ckpt_cap : 0, E = ckpt ? a.evict_cap : 0;
     int st = ensure_workspace(sc, blocks * 128, std::max(C, 1), std::max(E, 1), s, a);
     if (st) return st;

@@ -641,7 +641,7 @@ __device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc
     }
     float Lt = tn;
     uint32_t Li = GRTX_NONE;
-    bool ckpt = !PROXY && a.traversal == GRTX_TRAVERSAL_CHECKPOINT;
+    bool ckpt = a.traversal == GRTX_TRAVERSAL_CHECKPOINT;
     bool from_root = true;
     int n_src = 0, n_ev = 0, nb = 0;
     uint2 *src = a.ck0 + slot, *dst = a.ck1 + slot, *ev = a.ev + slot;
@@ -655,6 +655,9 @@ __device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc
                 uint2 v = ev[(size_t)e * S];
                 float ct = __uint_as_float(v.x);
                 uint32_t ci = v.y;
+                // the proxy form can find one Gaussian through several triangles, so an evicted
+                // copy may already be blended (key <= L) or already be in the buffer
+                if (PROXY && (!key_after(ct, ci, Lt, Li) || kb.contains(ct, ci))) continue;
                 if (kb.insert(ct, ci)) {
                     ev[(size_t)w * S] = make_uint2(__float_as_uint(ct), ci);
                     ++w;

@@ -101,7 +101,7 @@ extern "C" GRTX_API int grtx_trace_forward_noalloc(grtx_scene *sc, const grtx_ca
     if (st) return st;
     bool proxy = sc->form == GRTX_FORM_PROXY20;
     a.sc = grtx_scene_ref(sc);
-    a.traversal = proxy ? GRTX_TRAVERSAL_RESTART : p->traversal;
+    a.traversal = p->traversal;
     a.T_min = p->T_min;
     a.alpha_max = p->alpha_max;
     a.bg0 = p->bg[0];
@@ -110,7 +110,7 @@ extern "C" GRTX_API int grtx_trace_forward_noalloc(grtx_scene *sc, const grtx_ca
     a.ckpt_cap = p->ckpt_capacity > 0 ? p->ckpt_capacity : GRTX_DEFAULT_CKPT_CAPACITY;
     a.evict_cap = p->evict_capacity > 0 ? p->evict_capacity : GRTX_DEFAULT_EVICT_CAPACITY;
     a.rgbT = (float4 *)d_rgbT;
-    bool ckpt = !proxy && a.traversal == GRTX_TRAVERSAL_CHECKPOINT;
+    bool ckpt = a.traversal == GRTX_TRAVERSAL_CHECKPOINT;
     size_t C = ckpt ? (size_t)a.ckpt_cap : 1, E = ckpt ? (size_t)a.evict_cap : 1;
     size_t per_block = 128 * (2 * C + E) * sizeof(uint2);
     const size_t room = GRTX_NOALLOC_SCRATCH_BYTES - kCounterBytes;

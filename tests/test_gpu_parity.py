@@ -256,9 +256,19 @@ def test_forward_capacity_fallback_is_exact(dense, caps):
 
 
 @pytest.mark.parametrize("k", [4, 16])
-def test_forward_proxy_form_parity(dense, k):
+@pytest.mark.parametrize("traversal", ["restart", "checkpoint"])
+def test_forward_proxy_form_parity(dense, k, traversal):
     g, cam, S, rays, ref = dense
-    res = _gpu_render(g, cam, form="proxy20", k=k, ids_cap=256)
+    res = _gpu_render(g, cam, form="proxy20", k=k, traversal=traversal, ids_cap=256)
+    _check_image(res, ref, S, rays)
+    assert res["stats"]["blended"] == int(ref["n_blend"].sum())
+
+
+def test_forward_proxy_checkpoint_fallback_is_exact(dense):
+    g, cam, S, rays, ref = dense
+    res = _gpu_render(g, cam, form="proxy20", k=4, traversal="checkpoint", ckpt_capacity=3, evict_capacity=2,
+                      ids_cap=256)
+    assert res["stats"]["fallbacks"] > 0
     _check_image(res, ref, S, rays)
 
 
@@ -358,3 +368,70 @@ def test_autograd_function_runs_and_matches_backward():
     ref = S.backward(O.camera_rays(cam), w.cpu().numpy().astype(np.float64))
     assert rel_err(params[0].grad.cpu().numpy(), ref["means"]) <= 1e-3
     assert rel_err(params[4].grad.cpu().numpy(), ref["sh"]) <= 1e-3
+
+
+@pytest.mark.slow
+def test_backward_fd_cut_of_the_differentiable_scene():
+    """The 256K-Gaussian differentiable scene: the FD cut is the 2,000 Gaussians with the
+    largest total blend weight in the centre 32x32 crop of the 800x800 view (chosen by the
+    oracle). On the cut, the oracle's analytic gradient is checked by FP64 central differences
+    on a random subset of raw parameters (where the blend lists do not change), and the GPU
+    gradient must match the oracle's to 1e-3 per parameter tensor."""
+    g, target, cam, cfg = scenes.config_differentiable()
+    o, d, tn, tf = O.camera_rays(cam)
+    idx = scenes.crop_rays_index(cam["width"], 384, 384, 32, 32)
+    crop = tuple(np.ascontiguousarray(a[idx].astype(np.float32).astype(np.float64)) for a in (o, d, tn, tf))
+    S_full = O.Scene.from_params(g)
+    ref = S_full.render(crop, ids_cap=512)
+    weight = np.zeros(g.n)
+    for r in range(len(idx)):
+        T = 1.0
+        for h in ref["ids"][r, : ref["n_blend"][r]]:
+            a = min(S_full.response(int(h), crop[0][r], crop[1][r])[2], 0.99)
+            weight[h] += T * a
+            T *= 1 - a
+    cut = np.argsort(-weight)[:2000]
+    cut = cut[weight[cut] > 0]
+    gc = g.subset(np.sort(cut))
+    S = O.Scene.from_params(gc)
+    w = np.random.default_rng(12).normal(0, 1, (len(idx), 4))
+    ref_g = S.backward(crop, w)
+    names = {"means": "means", "log_scales": "log_scales", "quats": "quats", "opacity_logits": "logits", "sh": "sh"}
+    # FP64 central differences of the oracle on a random subset of raw parameters
+    rng = np.random.default_rng(13)
+    base = [a.astype(np.float64) for a in gc.arrays()]
+
+    def loss(params):
+        Sx = O.Scene(*params, sh_degree=gc.sh_degree)
+        r = Sx.render(crop, ids_cap=512)
+        return float(np.sum(w * r["out"])), (r["n_blend"].tobytes(), r["ids"].tobytes())
+
+    L0, sig0 = loss(base)
+    h = 1e-6
+    compared = 0
+    for pi, key in enumerate(("means", "log_scales", "quats", "logits", "sh")):
+        flat_n = base[pi].size
+        for j in rng.choice(flat_n, 24, replace=False):
+            pp = [a.copy() for a in base]
+            pm = [a.copy() for a in base]
+            pp[pi].reshape(-1)[j] += h
+            pm[pi].reshape(-1)[j] -= h
+            Lp, sp = loss(pp)
+            Lm, sm = loss(pm)
+            if sp != sig0 or sm != sig0:
+                continue
+            gfd = (Lp - Lm) / (2 * h)
+            gan = ref_g[key].reshape(-1)[j]
+            scale = np.abs(ref_g[key]).max()
+            assert abs(gfd - gan) <= 1e-4 * max(abs(gan), 1e-3 * scale) + 1e-8, (key, j, gfd, gan)
+            compared += 1
+    assert compared >= 80
+    # GPU analytic gradient on the same cut and the same FP32 rays
+    sc = R.Scene.from_params(gc)
+    rays = tuple(torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda() for a in crop)
+    fwd = R.render(sc, None, rays=rays, k=cfg["k"])["rgbT"]
+    grads = R.backward(sc, None, fwd, torch.from_numpy(w.astype(np.float32)).cuda(), rays=rays, k=cfg["k"])
+    torch.cuda.synchronize()
+    for kg, ko in names.items():
+        e = rel_err(grads[kg].cpu().numpy(), ref_g[ko])
+        assert e <= 1e-3, (kg, e)
