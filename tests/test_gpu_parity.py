@@ -344,16 +344,10 @@ def test_backward_matches_oracle_gradient():
     rng = np.random.default_rng(8)
     w = rng.normal(0, 1, (cam["width"] * cam["height"], 4))
     sc = R.Scene.from_params(g)
-    fwd = R.render(sc, cam, k=4)["rgbT"]
-    grads = R.backward(sc, cam, fwd, torch.from_numpy(w.astype(np.float32)).cuda(), k=4)
-    torch.cuda.synchronize()
     S = O.Scene.from_params(g)
     rays = O.camera_rays(cam)
     ref = S.backward(rays, w)
-    names = {"means": "means", "log_scales": "log_scales", "quats": "quats", "opacity_logits": "logits", "sh": "sh"}
-    for k_gpu, k_or in names.items():
-        e = rel_err(grads[k_gpu].cpu().numpy(), ref[k_or])
-        assert e <= 1e-3, (k_gpu, e)
+    _compare_gradients_with_oracle(S, sc, cam, None, rays, w, ref, 4)
 
 
 def test_autograd_function_runs_and_matches_backward():
@@ -429,9 +423,30 @@ def test_backward_fd_cut_of_the_differentiable_scene():
     # GPU analytic gradient on the same cut and the same FP32 rays
     sc = R.Scene.from_params(gc)
     rays = tuple(torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda() for a in crop)
-    fwd = R.render(sc, None, rays=rays, k=cfg["k"])["rgbT"]
-    grads = R.backward(sc, None, fwd, torch.from_numpy(w.astype(np.float32)).cuda(), rays=rays, k=cfg["k"])
+    _compare_gradients_with_oracle(S, sc, None, rays, crop, w, ref_g, cfg["k"])
+
+
+def _compare_gradients_with_oracle(S, sc, cam, rays_dev, rays_np, w, ref_g, k):
+    """GPU gradients against the oracle's, per parameter tensor (relative L2 <= 1e-3), over the
+    Gaussians whose hit status is the same on both sides. A Gaussian hit on one side only must
+    be a legitimate FP32/FP64 boundary case (compare_hit_lists), and is left out because its
+    gradient exists on one side only."""
+    out = R.render(sc, cam, rays=rays_dev, k=k, ids_cap=512, want_n_blended=True)
+    fwd = out["rgbT"]
+    grads = R.backward(sc, cam, fwd, torch.from_numpy(w.astype(np.float32)).cuda(), rays=rays_dev, k=k)
     torch.cuda.synchronize()
+    ref = S.render(rays_np, ids_cap=512)
+    gid, gnb = out["ids"].cpu().numpy(), out["n_blended"].cpu().numpy()
+    assert not compare_hit_lists(S, rays_np, gid, gnb, ref["ids"], ref["n_blend"])
+    differ = set()
+    for r in range(gnb.shape[0]):
+        a = set(int(x) for x in gid[r, : gnb[r]])
+        b = set(int(x) for x in ref["ids"][r, : ref["n_blend"][r]])
+        differ |= a ^ b
+    keep = np.ones(S.n, bool)
+    keep[list(differ)] = False
+    assert keep.mean() > 0.98
+    names = {"means": "means", "log_scales": "log_scales", "quats": "quats", "opacity_logits": "logits", "sh": "sh"}
     for kg, ko in names.items():
-        e = rel_err(grads[kg].cpu().numpy(), ref_g[ko])
-        assert e <= 1e-3, (kg, e)
+        e = rel_err(grads[kg].cpu().numpy()[keep], ref_g[ko][keep])
+        assert e <= 1e-3, (kg, e, len(differ))
