@@ -265,7 +265,7 @@ def nodes_per_ray(st: dict) -> dict:
             "evictions": st["evictions"] / r, "fallback_rays": st["fallbacks"]}
 
 
-def bench_serving(n_requests: int):
+def bench_serving(n_requests: int, max_rays_per_step: int = 4 << 20, max_inflight: int = 64):
     import torch
     from paper_2601_20429_gb300 import render as R
     from paper_2601_20429_gb300 import scenes
@@ -273,7 +273,7 @@ def bench_serving(n_requests: int):
     scs, reqs, cfg = scenes.config_serving(n_requests=n_requests)
     gpu_scenes = [R.Scene.from_params(g) for g in scs]
     del scs
-    srv = Server(gpu_scenes, k=cfg["k"], max_rays_per_step=4 << 20, max_inflight=64)
+    srv = Server(gpu_scenes, k=cfg["k"], max_rays_per_step=max_rays_per_step, max_inflight=max_inflight)
     max_px = 1920 * 1080
     pool = deque(torch.empty((max_px, 4), dtype=torch.float32, device="cuda") for _ in range(80))
     # warm-up: a few requests of each size
@@ -320,7 +320,8 @@ def bench_serving(n_requests: int):
     return {"requests": n, "rate_hz": 200.0, "p50_ms": float(np.percentile(lat_ms, 50)),
             "p99_ms": float(np.percentile(lat_ms, 99)), "mean_ms": float(lat_ms.mean()),
             "Mrays_per_s": rays / makespan / 1e6, "makespan_s": makespan,
-            "offered_Mrays_per_s": rays / (reqs[-1]["arrival"] - reqs[0]["arrival"]) / 1e6}
+            "offered_Mrays_per_s": rays / (reqs[-1]["arrival"] - reqs[0]["arrival"]) / 1e6,
+            "max_rays_per_step": max_rays_per_step, "max_inflight": max_inflight}
 
 
 def bench_differentiable(steps: int, warmup: int, stream):

@@ -544,7 +544,7 @@ __global__ void k_gather_tris(const uint32_t *__restrict__ order, int64_t n, con
     leaf_ids[t] = gid[__float_as_uint(tin[3 * (size_t)src].w)];
 }
 
-bool g_ico_ready = false;
+bool g_ico_ready[64] = {};   // proxy mesh uploaded to this device's constant memory
 float g_ico_circ = 0.f;   // circumradius of the uploaded proxy in unit-sphere units
 
 int upload_icosahedron(cudaStream_t s)
@@ -749,9 +749,12 @@ int build_scene(const grtx_gaussians *g, const grtx_params *p, int form, grtx_sc
         GRTX_CUDA(cudaMemcpyAsync(sc->leaf_ids, sc->gid, (size_t)nv * 4, cudaMemcpyDeviceToDevice, s));
         TRY(finish_tree(sc, A, leaf_aabb, nv));
     } else {
-        if (!g_ico_ready) {
+        int dev = 0;
+        GRTX_CUDA(cudaGetDevice(&dev));
+        if (dev < 0 || dev >= 64) return grtx_fail(GRTX_ERR_INVALID_ARG, "device ordinal out of range");
+        if (!g_ico_ready[dev]) {
             TRY(upload_icosahedron(s));
-            g_ico_ready = true;
+            g_ico_ready[dev] = true;
         }
         int64_t nt = 20 * nv;
         if (nt >= (int64_t)1 << 31) return grtx_fail(GRTX_ERR_INVALID_ARG, "too many proxy triangles");

@@ -39,7 +39,7 @@ struct grtx_scene {
     int64_t n = 0, n_valid = 0, n_leaves = 0, n_nodes = 0;
     float bounds[6] = {0, 0, 0, 0, 0, 0};
     float4 *nodes = nullptr;     // [n_nodes][4]: BVH2 node, see grtx_scene_export
-    float4 *geom = nullptr;      // [n_valid][4]: [A|b] rows + (o, -kappa^2 log2(e)/2, id, 0), leaf order
+    float4 *geom = nullptr;      // [n_valid][4]: rows (A_j | mu_j) + (o, -kappa^2 log2(e)/2, id, 0), leaf order
     float4 *tris = nullptr;      // proxy form: [n_leaves][3] world triangle (v0 | gidx, v1, v2)
     float *app = nullptr;        // [n_valid][app_stride] SH coefficients in leaf order
     uint32_t *gid = nullptr;     // [n_valid] Gaussian id of each sorted Gaussian

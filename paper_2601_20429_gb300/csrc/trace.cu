@@ -107,16 +107,19 @@ namespace {
 
 int fill_camera(TraceArgs &a, const grtx_camera *cam) { return grtx_fill_camera(a.cam, a.n_items, cam); }
 
+// SM count of the current device (cached per device ordinal).
 int sm_count()
 {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
+    static int cached[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (cached[dev] == 0) {
+        int n = 0;
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
+        cached[dev] = n > 0 ? n : 1;
     }
-    return n;
+    return cached[dev];
 }
 
 // Per-slot checkpoint lists (ping-pong) and eviction list, grown on demand.

@@ -217,10 +217,20 @@ def _gpu_render(g, cam, form="sphere", rays=None, **kw):
 
 
 def _check_image(res, ref, S, rays):
-    err = np.abs(res["rgbT"].astype(np.float64) - ref["out"]).max(0)
-    assert err[:3].max() <= RGB_TOL and err[3] <= RGB_TOL, err
+    """Pixels within RGB_TOL of the oracle, and blend lists equal up to the excused FP32/FP64
+    boundary cases. A pixel may exceed RGB_TOL only where its blend list legitimately differs
+    (a termination index that flips because T lands within rounding of T_min changes the
+    pixel by at most T_min times one colour)."""
     bad = compare_hit_lists(S, rays, res["ids"], res["n_blended"], ref["ids"], ref["n_blend"])
     assert not bad, f"{len(bad)} rays with different hit lists, e.g. {bad[:5]}"
+    err = np.abs(res["rgbT"].astype(np.float64) - ref["out"]).max(1)
+    for r in np.nonzero(err > RGB_TOL)[0]:
+        a = [int(x) for x in res["ids"][r, : res["n_blended"][r]]]
+        b = [int(x) for x in ref["ids"][r, : ref["n_blend"][r]]]
+        detail = (f"ray {r}: error {err[r]:.3g}, gpu blended {len(a)}, oracle {len(b)}, "
+                  f"T gpu {res['rgbT'][r, 3]:.6g} oracle {ref['out'][r, 3]:.6g}")
+        assert a != b, detail + " (same blend list)"
+        assert err[r] <= 3.0 * 1e-3, detail
 
 
 @pytest.mark.parametrize("k", [1, 2, 4, 8, 16, 32])
@@ -270,6 +280,25 @@ def test_forward_proxy_checkpoint_fallback_is_exact(dense):
                       ids_cap=256)
     assert res["stats"]["fallbacks"] > 0
     _check_image(res, ref, S, rays)
+
+
+@pytest.mark.parametrize("form,traversal", [("sphere", "checkpoint"), ("sphere", "restart"), ("proxy20", "checkpoint")])
+def test_forward_ragged_image(form, traversal):
+    """An image whose sides are not multiples of the 8x4 warp tile (ragged tiles on the right
+    and bottom edges), with a fisheye camera."""
+    g, _ = _dense()
+    cam = scenes.fisheye_camera(37, 23, (0.0, 0.0, -3.0), (0.0, 0.0, 1.0), 40.0)
+    S = O.Scene.from_params(g)
+    rays = O.camera_rays(cam)
+    r32 = tuple(a.astype(np.float32).astype(np.float64) for a in rays)
+    ref = S.render(r32, ids_cap=256)
+    trays = tuple(torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda() for a in rays)
+    res = _gpu_render(g, None, form=form, rays=trays, k=8, traversal=traversal, ids_cap=256)
+    _check_image(res, ref, S, r32)
+    # the same camera generated in-kernel covers every pixel exactly once
+    res2 = _gpu_render(g, cam, form=form, k=8, traversal=traversal, ids_cap=256)
+    assert res2["stats"]["rays"] == 37 * 23
+    assert np.abs(res2["rgbT"] - res["rgbT"]).max() <= 1e-3
 
 
 def test_forward_explicit_rays_and_window(dense):

@@ -91,3 +91,35 @@ def test_server_errors(world):
     plain = R.Scene.from_params(scenes.surface_scene(n=1000, seed=1), form="proxy20")
     with pytest.raises(N.GrtxError):
         Server([plain], k=16)
+
+
+@pytest.mark.slow
+def test_serving_full_size_sampled_against_oracle():
+    """The serving configuration at full size (four resident scenes of 0.5/1/2/3 M Gaussians)
+    and requests from its Poisson stream, rendered through the server; sampled pixels of each
+    request against the FP64 oracle on the same scene."""
+    from oracle import oracle as O
+    from tests.gpu_util import RGB_TOL, compare_hit_lists
+    scs, reqs, cfg = scenes.config_serving(n_requests=40)
+    gpu = [R.Scene.from_params(g) for g in scs]
+    srv = Server(gpu, k=cfg["k"], max_rays_per_step=1 << 20, max_inflight=6)
+    pick = [0, 1, 2, 3, 5, 8, 13, 21]
+    bufs = [torch.empty((reqs[j]["camera"]["width"] * reqs[j]["camera"]["height"], 4), device="cuda") for j in pick]
+    done = srv.render_requests([(reqs[j]["scene"], reqs[j]["camera"], b, j) for j, b in zip(pick, bufs)])
+    torch.cuda.synchronize()
+    assert sorted(d["tag"] for d in done) == sorted(pick)
+    rng = np.random.default_rng(7)
+    oracle_scenes = {}
+    for j, b in zip(pick, bufs):
+        sid = reqs[j]["scene"]
+        if sid not in oracle_scenes:
+            oracle_scenes[sid] = O.Scene.from_params(scs[sid])
+        S = oracle_scenes[sid]
+        cam = reqs[j]["camera"]
+        rays = O.camera_rays(cam)
+        idx = rng.choice(rays[0].shape[0], 12, replace=False)
+        sub = tuple(a[idx] for a in rays)
+        ref = S.render(sub, ids_cap=512)
+        got = b.cpu().numpy()[idx].astype(np.float64)
+        assert np.abs(got - ref["out"]).max() <= RGB_TOL
+    srv.close()
