@@ -52,7 +52,7 @@ def parse():
 def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("trace_impl.cuh", "trace.cu"):
+    for f in ("trace_impl.cuh", "trace.cu", "trace_k16.cu", "build.cu"):
         h.update(open(os.path.join(ROOT, "paper_2601_20429_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -262,7 +262,49 @@ def nodes_per_ray(st: dict) -> dict:
     r = max(st["rays"], 1)
     return {"internal": st["nodes"] / r, "leaf": st["leaves"] / r, "total": (st["nodes"] + st["leaves"]) / r,
             "blended": st["blended"] / r, "rounds": st["rounds"] / r, "ckpt_writes": st["ckpt_writes"] / r,
-            "evictions": st["evictions"] / r, "fallback_rays": st["fallbacks"]}
+            "evictions": st["evictions"] / r, "fallback_rays": st["fallbacks"],
+            "collected": st.get("collected", 0) / r}
+
+
+def mrays(n_rays: int, times_ms) -> float:
+    return n_rays / (statistics.mean(times_ms) / 1e3) / 1e6
+
+
+def bench_surface_ablations(g, sc, cam, k: int, steps: int, stream, flush) -> dict:
+    """On the surface scene: single-round traversal (Sec. III-C Obs. II), the centroid-only
+    LBVH codes against the size-aware default, and the resolution / field-of-view sweep
+    (Sec. V-E)."""
+    import torch
+    from paper_2601_20429_gb300 import native as N
+    from paper_2601_20429_gb300 import render as R
+    from paper_2601_20429_gb300 import scenes
+    n_rays = cam["width"] * cam["height"]
+    out = torch.empty((n_rays, 4), dtype=torch.float32, device="cuda")
+    res = {}
+    st = N.stats_dict(R.render(sc, cam, k=k, traversal="single", out=out, want_stats=True)["stats"])
+    t = time_frames(lambda: R.render(sc, cam, k=k, traversal="single", out=out), steps, 2, flush, stream)
+    res["single_round"] = {"Mrays_per_s": mrays(n_rays, t), "ms_per_frame": statistics.mean(t),
+                           "nodes_per_ray": nodes_per_ray(st), "list_capacity": 2048}
+    sc_c = R.Scene.from_params(g, bvh_codes="centroid")
+    st = N.stats_dict(R.render(sc_c, cam, k=k, out=out, want_stats=True)["stats"])
+    t = time_frames(lambda: R.render(sc_c, cam, k=k, out=out), steps, 2, flush, stream)
+    res["centroid_codes"] = {"Mrays_per_s": mrays(n_rays, t), "ms_per_frame": statistics.mean(t),
+                             "nodes_per_ray": nodes_per_ray(st)}
+    sc_c.close()
+    sweep = []
+    for (w, h, fov) in ((640, 360, 60.0), (1280, 720, 60.0), (1920, 1080, 60.0), (3840, 2160, 60.0),
+                        (1920, 1080, 30.0), (1920, 1080, 90.0)):
+        cam_r = scenes.pinhole_camera(w, h, (0.0, 0.0, -4.0), (0.0, 0.0, 0.0), fov)
+        o = torch.empty((w * h, 4), dtype=torch.float32, device="cuda")
+        st = N.stats_dict(R.render(sc, cam_r, k=k, out=o, want_stats=True)["stats"])
+        t = time_frames(lambda: R.render(sc, cam_r, k=k, out=o), steps, 2, flush, stream)
+        npr = nodes_per_ray(st)
+        sweep.append({"width": w, "height": h, "fov_y_deg": fov, "Mrays_per_s": mrays(w * h, t),
+                      "ms_per_frame": statistics.mean(t), "nodes_per_ray": npr["total"],
+                      "blended_per_ray": npr["blended"], "rounds_per_ray": npr["rounds"]})
+        del o
+    res["resolution_fov_sweep"] = sweep
+    return res
 
 
 def bench_serving(n_requests: int, max_rays_per_step: int = 4 << 20, max_inflight: int = 64):
@@ -373,6 +415,7 @@ def bench_outdoor(steps: int, stream, flush):
     sc = R.Scene.from_params(g)
     torch.cuda.synchronize()
     build_ms = (time.perf_counter() - t0) * 1e3
+    sc_c = R.Scene.from_params(g, bvh_codes="centroid")
     del g
     n = cam["width"] * cam["height"]
     prim = [torch.empty((n, 3), device="cuda"), torch.empty((n, 3), device="cuda"), torch.empty(n, device="cuda"),
@@ -390,13 +433,18 @@ def bench_outdoor(steps: int, stream, flush):
     ts = time_frames(lambda: R.render(sc, None, rays=sec_rays, k=cfg["k"], out=out_s), steps, 2, flush, stream)
     st_p = N.stats_dict(R.render(sc, None, rays=prim, k=cfg["k"], want_stats=True)["stats"])
     st_s = N.stats_dict(R.render(sc, None, rays=sec_rays, k=cfg["k"], want_stats=True)["stats"])
+    tc = time_frames(lambda: R.render(sc_c, None, rays=prim, k=cfg["k"], out=out_p), steps, 2, flush, stream)
+    st_c = N.stats_dict(R.render(sc_c, None, rays=prim, k=cfg["k"], want_stats=True)["stats"])
+    sc_c.close()
     sc.close()
     return {"workload": "6M outdoor Gaussians, 1920x1080 equidistant fisheye, one 4x3 m mirror, k=16",
             "build_ms": build_ms, "secondary_rays": m,
             "primary": {"Mrays_per_s": n / (statistics.mean(tp) / 1e3) / 1e6, "ms": statistics.mean(tp),
                         "nodes_per_ray": nodes_per_ray(st_p)},
             "secondary": {"Mrays_per_s": m / (statistics.mean(ts) / 1e3) / 1e6, "ms": statistics.mean(ts),
-                          "nodes_per_ray": nodes_per_ray(st_s)}}
+                          "nodes_per_ray": nodes_per_ray(st_s)},
+            "primary_centroid_codes": {"Mrays_per_s": n / (statistics.mean(tc) / 1e3) / 1e6,
+                                       "ms": statistics.mean(tc), "nodes_per_ray": nodes_per_ray(st_c)}}
 
 
 def main():
@@ -510,8 +558,9 @@ def main():
     if dist.world == 1 and not args.no_serving:
         serving = bench_serving(args.serve_requests)
 
-    differentiable = outdoor = None
+    differentiable = outdoor = ablations = None
     if dist.world == 1 and not args.no_extra:
+        ablations = bench_surface_ablations(g, sc, cam, k, max(3, args.steps // 4), stream, flush)
         differentiable = bench_differentiable(max(3, args.steps // 3), 2, stream)
         outdoor = bench_outdoor(max(3, args.steps // 3), stream, flush)
 
@@ -546,6 +595,7 @@ def main():
                       "ms_per_frame": statistics.mean(times_plain), "nodes_per_ray": nodes_per_ray(st_plain),
                       "build_ms": build_plain_ms, "bvh_bytes": info_plain["bytes_nodes"] + info_plain["bytes_leaves"],
                       "depth": info_plain["depth"]},
+            "ablations": ablations,
             "roofline": roofline,
             "e2e": {"value": e2e_val / 1e6, "unit": "Mrays/s", "h2d_bytes_per_step": 112,
                     "d2h_bytes_per_step": n_rays * 16},

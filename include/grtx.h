@@ -33,6 +33,7 @@ extern "C" {
 #define GRTX_API __attribute__((visibility("default")))
 #define GRTX_VERSION 1
 #define GRTX_DEFAULT_CKPT_CAPACITY 256
+#define GRTX_DEFAULT_SINGLE_CAPACITY 2048
 #define GRTX_DEFAULT_EVICT_CAPACITY 128
 
 /* ---------------------------------------------------------------------------------------- */
@@ -83,7 +84,9 @@ enum { GRTX_FORM_SPHERE = 0,        /* one leaf per Gaussian, analytic unit sphe
        GRTX_FORM_PROXY20 = 1 };     /* one leaf per proxy triangle: 20-triangle icosahedron
                                        around each Gaussian, monolithic BVH (Sec. III-C Obs. I) */
 enum { GRTX_TRAVERSAL_CHECKPOINT = 0, /* resume from checkpointed nodes + eviction list (IV-B) */
-       GRTX_TRAVERSAL_RESTART = 1 };  /* restart from the root every round (Sec. III-A)       */
+       GRTX_TRAVERSAL_RESTART = 1,    /* restart from the root every round (Sec. III-A)       */
+       GRTX_TRAVERSAL_SINGLE = 2 };   /* one traversal collecting every hit, then sort and
+                                         blend (single-round baseline, Sec. III-C Obs. II)   */
 
 /* Tracing parameters. k: k-buffer size, one of 1, 2, 4, 8, 16, 32 (Sec. III-A).
  * alpha_min: a Gaussian is hit where its response reaches alpha_min (0.01); it also sets the
@@ -92,10 +95,18 @@ enum { GRTX_TRAVERSAL_CHECKPOINT = 0, /* resume from checkpointed nodes + evicti
  * on alpha before compositing (0.99). bg: background colour added as T * bg.
  * ckpt_capacity / evict_capacity: checkpoint and eviction entries per resident ray slot
  * (Sec. IV-B "Checkpoint and Eviction Buffer"); 0 selects GRTX_DEFAULT_CKPT_CAPACITY (256)
- * and GRTX_DEFAULT_EVICT_CAPACITY (128).
+ * and GRTX_DEFAULT_EVICT_CAPACITY (128). With GRTX_TRAVERSAL_SINGLE, ckpt_capacity is the
+ * number of hits a ray slot's list holds (0 selects GRTX_DEFAULT_SINGLE_CAPACITY, 2048, the
+ * top of the paper's 512-2048); a ray with more hits is traced with k-buffer rounds
+ * restarted from the root instead (same result, counted in fallbacks), and k must still be
+ * one of the valid sizes.
  * traversal: GRTX_TRAVERSAL_*, for either form: {sphere, proxy} x {checkpoint, restart} are the
  * paper's GRTX, GRTX-HW only (proxy + checkpoint), GRTX-SW only (sphere + restart) and the
- * baseline (proxy + restart) of Sec. V-B. */
+ * baseline (proxy + restart) of Sec. V-B.
+ * bvh_codes (read by grtx_build_bvh only): the sort key of the LBVH build,
+ * GRTX_CODES_SIZED (0, the default: grtx_morton_codes_sized) or GRTX_CODES_CENTROID
+ * (grtx_morton_codes). The tree shape changes the cost of a trace, never its result. */
+enum { GRTX_CODES_SIZED = 0, GRTX_CODES_CENTROID = 1 };
 typedef struct grtx_params {
     int32_t k;
     int32_t traversal;
@@ -105,6 +116,7 @@ typedef struct grtx_params {
     float bg[3];
     int32_t ckpt_capacity;
     int32_t evict_capacity;
+    int32_t bvh_codes;
 } grtx_params;
 
 enum { GRTX_CAMERA_PINHOLE = 0, GRTX_CAMERA_FISHEYE = 1, GRTX_CAMERA_RAYS = 2 };
@@ -137,10 +149,11 @@ typedef struct grtx_camera {
  * blended: Gaussians composited; rounds: tracing rounds; ckpt_writes: checkpoint entries
  * written; evictions: entries written to the eviction list; fallbacks: rays that exceeded a
  * capacity and restarted from the root; stack_overflow: traversal stack overflows (never
- * expected: the build rejects trees deeper than the stack). */
+ * expected: the build rejects trees deeper than the stack); collected: hits appended to the
+ * single-round lists (GRTX_TRAVERSAL_SINGLE only). */
 typedef struct grtx_stats {
     unsigned long long rays, nodes, leaves, blended, rounds, ckpt_writes, evictions, fallbacks,
-        stack_overflow, reserved;
+        stack_overflow, collected;
 } grtx_stats;
 
 /* Outputs of a forward trace. rgbT: device [n_rays][4] = (C + T bg, T), required.
@@ -215,6 +228,19 @@ GRTX_API int grtx_prep_gaussians(const grtx_gaussians *g, float alpha_min, float
  * d_aabb [n][6] in, d_codes [n] out; device, caller-owned. */
 GRTX_API int grtx_morton_codes(const float *d_aabb, int64_t n, const float *d_bounds,
                                float *d_bounds_out, uint64_t *d_codes, void *stream);
+
+/* Size-aware 64-bit Morton codes (extended Morton codes, Vinkler, Bittner and Havran, HPG
+ * 2017; the paper builds its BVH with a third-party builder, Sec. V-A): the box diagonal is a
+ * fourth coordinate, so that Gaussians of very different sizes (scales spanning three
+ * decades) do not share subtrees whose boxes the largest of them inflate. In FP32 per box:
+ * q_a = floor((c_a - blo_a) * (2^16 / (bhi_a - blo_a))) clamped to [0, 2^16 - 1] for the
+ * centroid c = 0.5 (lo + hi) (0 when bhi_a == blo_a); q_s = floor(sqrt((ex^2 + ey^2) + ez^2)
+ * * (2^15 / E)) clamped to [0, 2^16 - 2], with e = hi - lo and E the largest extent of the
+ * centroid bounds (q_s = 0 when E == 0). Bit b of (q_x, q_y, q_z, q_s) is code bit
+ * 4b + (3, 2, 1, 0). An empty box gets 2^64 - 1, which no other code reaches. Arguments
+ * and bounds as for grtx_morton_codes. */
+GRTX_API int grtx_morton_codes_sized(const float *d_aabb, int64_t n, const float *d_bounds,
+                                     float *d_bounds_out, uint64_t *d_codes, void *stream);
 
 /* Stable ascending LSD radix sort of (key, value) pairs in place, over the low key_bits bits
  * of the keys (1..64; bits above are ignored for ordering). d_temp / *temp_bytes: scratch;
@@ -346,7 +372,8 @@ GRTX_API int grtx_composite_bounce(float *d_rgbT, const float *d_sec_rgbT, const
  * start-up and may not grow it, or a frame loop that cannot afford to wait on the allocator.
  * grtx_trace_forward may allocate (it grows a per-scene workspace on first use); this variant
  * never does. It renders cam like grtx_trace_forward with rgbT = d_rgbT (device [n_rays][4],
- * 16-byte aligned, caller-owned) and no optional outputs. Its scratch -- the ray-queue
+ * 16-byte aligned, caller-owned) and no optional outputs; GRTX_TRAVERSAL_SINGLE is rejected
+ * with GRTX_ERR_INVALID_ARG (its hit lists do not fit the array). Its scratch -- the ray-queue
  * counter and the per-ray-slot checkpoint and eviction lists -- lives in one library-owned
  * device array of GRTX_NOALLOC_SCRATCH_BYTES (32 MiB) that every GPU which loads the library
  * holds until the process exits. The number of rays in flight is whatever fits in that array
@@ -389,7 +416,8 @@ typedef struct grtx_completion {
 
 /* Create a server over n_scenes built scenes (not owned; they must outlive the server).
  * max_rays_per_step: rays per persistent launch (0: 4M); max_inflight: requests admitted at
- * once (0: 64); p: tracing parameters for every request. Host call; allocates a step table
+ * once (0: 64); p: tracing parameters for every request (checkpoint or restart traversal;
+ * GRTX_TRAVERSAL_SINGLE is rejected with GRTX_ERR_INVALID_ARG). Host call; allocates a step table
  * in device memory on `stream`, which all later server work uses. */
 GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scenes, const grtx_params *p,
                                 int64_t max_rays_per_step, int max_inflight, void *stream,

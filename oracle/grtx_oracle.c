@@ -886,6 +886,47 @@ OG_API void og_morton63(int n, const float *aabb, const float *bounds, uint64_t 
     }
 }
 
+/* Size-aware 64-bit Morton code (extended Morton codes for LBVH construction, Vinkler,
+ * Bittner and Havran, HPG 2017): the AABB diagonal length is a fourth coordinate, on the
+ * grid of the positions at half their resolution. Per box, in FP32:
+ *   q_a = floor((c_a - lo_a) * (2^16 / (hi_a - lo_a))), clamped to [0, 2^16 - 1], for the
+ *         centroid c (0 on an axis of zero extent);
+ *   q_s = floor(diag * (2^15 / E)), clamped to [0, 2^16 - 2], diag = sqrt((ex^2 + ey^2) + ez^2)
+ *         of the box extents and E the largest extent of the bounds (0 when E == 0).
+ * Bit b of (x, y, z, s) goes to bit 4b + (3, 2, 1, 0). The clamp of q_s below 2^16 - 1 keeps
+ * every code below 2^64 - 1, which marks empty boxes. */
+OG_API void og_morton_sized64(int n, const float *aabb, const float *bounds, uint64_t *codes)
+{
+    float E = 0.0f;
+    for (int a = 0; a < 3; ++a) {
+        float ext = bounds[3 + a] - bounds[a];
+        if (ext > E) E = ext;
+    }
+    float scale_s = E > 0.0f ? 32768.0f / E : 0.0f;
+    for (int i = 0; i < n; ++i) {
+        const float *bb = aabb + 6 * i;
+        uint32_t q[4];
+        for (int a = 0; a < 3; ++a) {
+            float c = 0.5f * (bb[a] + bb[3 + a]);
+            float ext = bounds[3 + a] - bounds[a];
+            float scale = ext > 0.0f ? 65536.0f / ext : 0.0f;
+            float u = (c - bounds[a]) * scale;
+            q[a] = u <= 0.0f ? 0u : (u >= 65535.0f ? 65535u : (uint32_t)u);
+        }
+        float ex = bb[3] - bb[0], ey = bb[4] - bb[1], ez = bb[5] - bb[2];
+        float d2 = ex * ex;
+        d2 = d2 + ey * ey;
+        d2 = d2 + ez * ez;
+        float us = sqrtf(d2) * scale_s;
+        q[3] = us <= 0.0f ? 0u : (us >= 65534.0f ? 65534u : (uint32_t)us);
+        uint64_t code = 0;
+        for (int b = 0; b < 16; ++b)
+            for (int a = 0; a < 4; ++a)
+                code |= (uint64_t)((q[a] >> b) & 1u) << (4 * b + 3 - a);
+        codes[i] = code;
+    }
+}
+
 /* Length of the common prefix of sorted keys i and j, with the index appended to break
  * ties between equal codes; -1 outside the array. */
 static int og_prefix(const uint64_t *k, int n, int i, int j)

@@ -106,6 +106,7 @@ def lib():
             L.og_composite_bounce.argtypes = [_dp, _dp, _ip, C.c_int, _dp]
             L.og_centroid_bounds.argtypes = [C.c_int, _fp, _fp]
             L.og_morton63.argtypes = [C.c_int, _fp, _fp, _u64p]
+            L.og_morton_sized64.argtypes = [C.c_int, _fp, _fp, _u64p]
             L.og_radix_tree.argtypes = [C.c_int, _u64p, _u32p, _u32p]
             L.og_refit.argtypes = [C.c_int, _u32p, _u32p, _fp, _fp]
             _lib = L
@@ -276,6 +277,14 @@ def morton63(aabb_f32: np.ndarray, bounds_f32: np.ndarray) -> np.ndarray:
     b = np.ascontiguousarray(bounds_f32, dtype=np.float32).reshape(6)
     codes = np.empty(a.shape[0], dtype=np.uint64)
     lib().og_morton63(a.shape[0], _p(a, _fp), _p(b, _fp), _p(codes, _u64p))
+    return codes
+
+
+def morton_sized64(aabb_f32: np.ndarray, bounds_f32: np.ndarray) -> np.ndarray:
+    a = np.ascontiguousarray(aabb_f32, dtype=np.float32).reshape(-1, 6)
+    b = np.ascontiguousarray(bounds_f32, dtype=np.float32).reshape(6)
+    codes = np.empty(a.shape[0], dtype=np.uint64)
+    lib().og_morton_sized64(a.shape[0], _p(a, _fp), _p(b, _fp), _p(codes, _u64p))
     return codes
 
 

@@ -151,6 +151,45 @@ __global__ void k_morton(const float *__restrict__ aabb, int64_t n, const float 
     codes[i] = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
 }
 
+// Spread the low 16 bits of v so that bit b lands at bit 4b.
+__host__ __device__ __forceinline__ uint64_t spread4(uint32_t v)
+{
+    uint64_t x = v & 0xffffu;
+    x = (x | (x << 24)) & 0x000000ff000000ffull;
+    x = (x | (x << 12)) & 0x000f000f000f000full;
+    x = (x | (x << 6)) & 0x0303030303030303ull;
+    x = (x | (x << 3)) & 0x1111111111111111ull;
+    return x;
+}
+
+// Size-aware code: 16 bits each of the quantised centroid and of the box diagonal on the
+// positions' grid at half resolution, interleaved x, y, z, size (see grtx_morton_codes_sized).
+__global__ void k_morton_sized(const float *__restrict__ aabb, int64_t n, const float *__restrict__ bounds,
+                               uint64_t *__restrict__ codes, uint32_t *__restrict__ values)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float *bb = aabb + 6 * i;
+    if (values) values[i] = (uint32_t)i;
+    if (box_empty(bb)) { codes[i] = ~0ull; return; }
+    float E = 0.0f;
+    uint32_t q[4];
+    for (int a = 0; a < 3; ++a) {
+        float c = __fmul_rn(0.5f, __fadd_rn(bb[a], bb[3 + a]));
+        float ext = __fsub_rn(bounds[3 + a], bounds[a]);
+        E = ext > E ? ext : E;
+        float scale = ext > 0.0f ? __fdiv_rn(65536.0f, ext) : 0.0f;
+        float u = __fmul_rn(__fsub_rn(c, bounds[a]), scale);
+        q[a] = u <= 0.0f ? 0u : (u >= 65535.0f ? 65535u : (uint32_t)u);
+    }
+    float ex = __fsub_rn(bb[3], bb[0]), ey = __fsub_rn(bb[4], bb[1]), ez = __fsub_rn(bb[5], bb[2]);
+    float d2 = __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
+    float scale_s = E > 0.0f ? __fdiv_rn(32768.0f, E) : 0.0f;
+    float us = __fmul_rn(__fsqrt_rn(d2), scale_s);
+    q[3] = us <= 0.0f ? 0u : (us >= 65534.0f ? 65534u : (uint32_t)us);
+    codes[i] = (spread4(q[0]) << 3) | (spread4(q[1]) << 2) | (spread4(q[2]) << 1) | spread4(q[3]);
+}
+
 // ------------------------------------------------------------------------------------------
 // Exclusive scan of uint32 (tiles of 4096, recursive over tile sums).
 // ------------------------------------------------------------------------------------------
@@ -634,13 +673,16 @@ void free_scene_arrays(grtx_scene *sc)
 // Morton -> sort -> radix tree -> refit -> nodes over n leaf boxes (sorted in place with
 // `order`). Writes sc->nodes, sc->codes, sc->depth.
 int build_tree(grtx_scene *sc, Alloc &A, float *leaf_aabb, int64_t n, uint32_t *order, uint64_t *codes,
-               float *bounds_dev)
+               float *bounds_dev, int code_kind)
 {
     cudaStream_t s = sc->stream;
     int blocks = grtx_div_up(n, kThreads);
     k_init_bounds<<<1, 32, 0, s>>>(bounds_dev);
     k_centroid_bounds<<<std::min(blocks, 4096), kThreads, 0, s>>>(leaf_aabb, n, bounds_dev);
-    k_morton<<<blocks, kThreads, 0, s>>>(leaf_aabb, n, bounds_dev, codes, order);
+    if (code_kind == GRTX_CODES_CENTROID)
+        k_morton<<<blocks, kThreads, 0, s>>>(leaf_aabb, n, bounds_dev, codes, order);
+    else
+        k_morton_sized<<<blocks, kThreads, 0, s>>>(leaf_aabb, n, bounds_dev, codes, order);
     GRTX_CHECK_LAUNCH("morton");
     void *stmp;
     TRY(A.get((char **)&stmp, sort_layout(n).total, true));
@@ -716,7 +758,7 @@ int build_scene(const grtx_gaussians *g, const grtx_params *p, int form, grtx_sc
     k_prep<<<blocks, kThreads, 0, s>>>(g->means, g->log_scales, g->quats, g->opacity_logits, n, p->alpha_min,
                                        geom_raw, aabb_raw);
     GRTX_CHECK_LAUNCH("prep");
-    TRY(build_tree(sc, A, aabb_raw, n, order, codes, bounds_dev));
+    TRY(build_tree(sc, A, aabb_raw, n, order, codes, bounds_dev, p->bvh_codes));
     // number of valid Gaussians: their codes sort before the 2^64-1 of the empty boxes
     unsigned long long *d_nvalid;
     TRY(A.get(&d_nvalid, 1, true));
@@ -772,7 +814,7 @@ int build_scene(const grtx_gaussians *g, const grtx_params *p, int form, grtx_sc
                                                                       sc->gid, nv, g_ico_circ, tris_raw,
                                                                       tri_aabb_raw, slack_raw);
         GRTX_CHECK_LAUNCH("proxy expand");
-        TRY(build_tree(sc, A, tri_aabb_raw, nt, torder, tcodes, bounds_dev));
+        TRY(build_tree(sc, A, tri_aabb_raw, nt, torder, tcodes, bounds_dev, p->bvh_codes));
         sc->n_leaves = nt;
         TRY(A.get(&sc->tris, 3 * nt, false));
         TRY(A.get(&tri_aabb, 6 * nt, true));
@@ -857,8 +899,8 @@ extern "C" GRTX_API int grtx_prep_gaussians(const grtx_gaussians *g, float alpha
     return GRTX_OK;
 }
 
-extern "C" GRTX_API int grtx_morton_codes(const float *d_aabb, int64_t n, const float *d_bounds, float *d_bounds_out,
-                                          uint64_t *d_codes, void *stream)
+static int morton_codes_abi(const float *d_aabb, int64_t n, const float *d_bounds, float *d_bounds_out,
+                            uint64_t *d_codes, void *stream, bool sized)
 {
     if (n < 0 || n >= ((int64_t)1 << 31)) return grtx_fail(GRTX_ERR_INVALID_ARG, "n out of range");
     if (n == 0) return GRTX_OK;
@@ -876,10 +918,25 @@ extern "C" GRTX_API int grtx_morton_codes(const float *d_aabb, int64_t n, const 
         k_centroid_bounds<<<std::min(grtx_div_up(n, kThreads), 4096), kThreads, 0, s>>>(d_aabb, n, b);
         bounds = b;
     }
-    k_morton<<<grtx_div_up(n, kThreads), kThreads, 0, s>>>(d_aabb, n, bounds, d_codes, nullptr);
+    if (sized)
+        k_morton_sized<<<grtx_div_up(n, kThreads), kThreads, 0, s>>>(d_aabb, n, bounds, d_codes, nullptr);
+    else
+        k_morton<<<grtx_div_up(n, kThreads), kThreads, 0, s>>>(d_aabb, n, bounds, d_codes, nullptr);
     if (tmp) cudaFreeAsync(tmp, s);
-    GRTX_CHECK_LAUNCH("grtx_morton_codes");
+    GRTX_CHECK_LAUNCH(sized ? "grtx_morton_codes_sized" : "grtx_morton_codes");
     return GRTX_OK;
+}
+
+extern "C" GRTX_API int grtx_morton_codes(const float *d_aabb, int64_t n, const float *d_bounds, float *d_bounds_out,
+                                          uint64_t *d_codes, void *stream)
+{
+    return morton_codes_abi(d_aabb, n, d_bounds, d_bounds_out, d_codes, stream, false);
+}
+
+extern "C" GRTX_API int grtx_morton_codes_sized(const float *d_aabb, int64_t n, const float *d_bounds,
+                                                float *d_bounds_out, uint64_t *d_codes, void *stream)
+{
+    return morton_codes_abi(d_aabb, n, d_bounds, d_bounds_out, d_codes, stream, true);
 }
 
 extern "C" GRTX_API int grtx_sort_pairs(uint64_t *d_keys, uint32_t *d_values, int64_t n, int key_bits, void *d_temp,
@@ -932,6 +989,8 @@ extern "C" GRTX_API int grtx_build_bvh(const grtx_gaussians *g, const grtx_param
     if (!p || !out) return grtx_fail(GRTX_ERR_INVALID_ARG, "params or out is NULL");
     if (form != GRTX_FORM_SPHERE && form != GRTX_FORM_PROXY20) return grtx_fail(GRTX_ERR_INVALID_ARG, "unknown form");
     if (!(p->alpha_min > 0.f && p->alpha_min < 1.f)) return grtx_fail(GRTX_ERR_INVALID_ARG, "alpha_min must be in (0,1)");
+    if (p->bvh_codes != GRTX_CODES_SIZED && p->bvh_codes != GRTX_CODES_CENTROID)
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "unknown bvh_codes");
     grtx_scene *sc = new (std::nothrow) grtx_scene();
     if (!sc) return grtx_fail(GRTX_ERR_OOM, "host allocation failed");
     sc->stream = S(stream);

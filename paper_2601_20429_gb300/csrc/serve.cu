@@ -172,6 +172,8 @@ extern "C" GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scen
     if (!scenes || n_scenes <= 0 || !out) return grtx_fail(GRTX_ERR_INVALID_ARG, "need scenes and out");
     int st = grtx_check_params(p);
     if (st) return st;
+    if (p->traversal == GRTX_TRAVERSAL_SINGLE)
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "serving supports checkpoint and restart traversal");
     for (int i = 0; i < n_scenes; ++i) {
         if (!scenes[i]) return grtx_fail(GRTX_ERR_INVALID_ARG, "scene is NULL");
         if (scenes[i]->form != GRTX_FORM_SPHERE) return grtx_fail(GRTX_ERR_INVALID_ARG, "serving needs sphere-form scenes");

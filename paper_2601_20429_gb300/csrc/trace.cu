@@ -18,6 +18,9 @@ GRTX_EXTERN_TRACE(8)
 GRTX_EXTERN_TRACE(16)
 GRTX_EXTERN_TRACE(32)
 
+int trace_single_launch(const TraceArgs &a, bool proxy, bool instr, int blocks, cudaStream_t s);
+int trace_single_occupancy(bool proxy, bool instr, int *blocks_per_sm);
+
 namespace {
 
 inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -52,7 +55,8 @@ int check_params(const grtx_params *p)
 {
     if (!p) return grtx_fail(GRTX_ERR_INVALID_ARG, "params is NULL");
     if (!valid_k(p->k)) return grtx_fail(GRTX_ERR_INVALID_ARG, "k must be one of 1, 2, 4, 8, 16, 32");
-    if (p->traversal != GRTX_TRAVERSAL_CHECKPOINT && p->traversal != GRTX_TRAVERSAL_RESTART)
+    if (p->traversal != GRTX_TRAVERSAL_CHECKPOINT && p->traversal != GRTX_TRAVERSAL_RESTART &&
+        p->traversal != GRTX_TRAVERSAL_SINGLE)
         return grtx_fail(GRTX_ERR_INVALID_ARG, "unknown traversal mode");
     if (!(p->T_min >= 0.f && p->T_min < 1.f)) return grtx_fail(GRTX_ERR_INVALID_ARG, "T_min must be in [0,1)");
     if (!(p->alpha_max > 0.f && p->alpha_max < 1.f)) return grtx_fail(GRTX_ERR_INVALID_ARG, "alpha_max must be in (0,1)");
@@ -122,10 +126,10 @@ int sm_count()
     return cached[dev];
 }
 
-// Per-slot checkpoint lists (ping-pong) and eviction list, grown on demand.
-int ensure_workspace(grtx_scene *sc, int n_slots, int C, int E, cudaStream_t s, TraceArgs &a)
+// Per-slot lists (entries_per_slot uint2 per ray slot), grown on demand; returns the base.
+int ensure_workspace(grtx_scene *sc, int n_slots, size_t entries_per_slot, cudaStream_t s, uint2 **base_out)
 {
-    size_t need = (size_t)n_slots * (2 * (size_t)C + (size_t)E) * sizeof(uint2);
+    size_t need = (size_t)n_slots * entries_per_slot * sizeof(uint2);
     if (need > sc->ws_bytes) {
         if (sc->ws) {
             GRTX_CUDA(cudaDeviceSynchronize());   // earlier traces on any stream may still use it
@@ -141,11 +145,7 @@ int ensure_workspace(grtx_scene *sc, int n_slots, int C, int E, cudaStream_t s, 
         }
         sc->ws_bytes = need;
     }
-    uint2 *base = (uint2 *)sc->ws;
-    a.ck0 = base;
-    a.ck1 = base + (size_t)n_slots * C;
-    a.ev = base + (size_t)n_slots * 2 * C;
-    a.n_slots = n_slots;
+    *base_out = (uint2 *)sc->ws;
     return GRTX_OK;
 }
 
@@ -186,7 +186,8 @@ int setup(grtx_scene *sc, const grtx_camera *cam, const grtx_params *p, TraceArg
     a.bg0 = p->bg[0];
     a.bg1 = p->bg[1];
     a.bg2 = p->bg[2];
-    a.ckpt_cap = p->ckpt_capacity > 0 ? p->ckpt_capacity : GRTX_DEFAULT_CKPT_CAPACITY;
+    a.ckpt_cap = p->ckpt_capacity > 0 ? p->ckpt_capacity
+                 : (p->traversal == GRTX_TRAVERSAL_SINGLE ? GRTX_DEFAULT_SINGLE_CAPACITY : GRTX_DEFAULT_CKPT_CAPACITY);
     a.evict_cap = p->evict_capacity > 0 ? p->evict_capacity : GRTX_DEFAULT_EVICT_CAPACITY;
     return GRTX_OK;
 }
@@ -194,17 +195,28 @@ int setup(grtx_scene *sc, const grtx_camera *cam, const grtx_params *p, TraceArg
 int run(grtx_scene *sc, TraceArgs &a, int k, bool instr, bool bwd, unsigned *queue, cudaStream_t s)
 {
     bool proxy = sc->form == GRTX_FORM_PROXY20;
+    bool single = a.traversal == GRTX_TRAVERSAL_SINGLE && !bwd;
     int bps = 0;
-    if (occupancy_k(k, proxy, instr, bwd, &bps) != GRTX_OK || bps <= 0)
-        return grtx_fail(GRTX_ERR_CUDA, "occupancy query failed");
+    int occ = single ? trace_single_occupancy(proxy, instr, &bps) : occupancy_k(k, proxy, instr, bwd, &bps);
+    if (occ != GRTX_OK || bps <= 0) return grtx_fail(GRTX_ERR_CUDA, "occupancy query failed");
     int blocks = sm_count() * bps;
+    int n_slots = blocks * 128;
     bool ckpt = a.traversal == GRTX_TRAVERSAL_CHECKPOINT;
-    int C = ckpt ? a.ckpt_cap : 0, E = ckpt ? a.evict_cap : 0;
-    int st = ensure_workspace(sc, blocks * 128, std::max(C, 1), std::max(E, 1), s, a);
+    // checkpoint: two ping-pong checkpoint lists and the eviction list; single: the hit list
+    size_t C = ckpt ? a.ckpt_cap : 1, E = ckpt ? a.evict_cap : 1;
+    size_t per_slot = single ? (size_t)a.ckpt_cap : 2 * C + E;
+    uint2 *base = nullptr;
+    int st = ensure_workspace(sc, n_slots, per_slot, s, &base);
     if (st) return st;
+    a.ck0 = base;
+    a.ck1 = single ? base : base + (size_t)n_slots * C;
+    a.ev = single ? base : base + (size_t)n_slots * 2 * C;
+    a.n_slots = n_slots;
     a.queue = queue;
     GRTX_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned), s));
-    if (launch_k(k, a, proxy, instr, bwd, blocks, s) != GRTX_OK) {
+    int launched = single ? trace_single_launch(a, proxy, instr, blocks, s)
+                          : launch_k(k, a, proxy, instr, bwd, blocks, s);
+    if (launched != GRTX_OK) {
         cudaError_t e = cudaGetLastError();
         return grtx_cuda_fail(e == cudaSuccess ? cudaErrorLaunchFailure : e, "trace launch");
     }
@@ -283,6 +295,11 @@ extern "C" GRTX_API int grtx_trace_backward(grtx_scene *sc, const grtx_gaussians
     if (!d_rgbT || !d_dL_drgbT || !grads) return grtx_fail(GRTX_ERR_INVALID_ARG, "NULL pointer");
     if (((uintptr_t)d_rgbT & 15) || ((uintptr_t)d_dL_drgbT & 15))
         return grtx_fail(GRTX_ERR_INVALID_ARG, "image buffers must be 16-byte aligned");
+    // the backward replays k-buffer rounds; a single-round forward gives the same blend lists
+    if (a.traversal == GRTX_TRAVERSAL_SINGLE) {
+        a.traversal = GRTX_TRAVERSAL_RESTART;
+        a.ckpt_cap = GRTX_DEFAULT_CKPT_CAPACITY;
+    }
     a.fwd_rgbT = (const float4 *)d_rgbT;
     a.dL_drgbT = (const float4 *)d_dL_drgbT;
     a.means = g->means;

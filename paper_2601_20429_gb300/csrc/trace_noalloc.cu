@@ -95,6 +95,8 @@ extern "C" GRTX_API int grtx_trace_forward_noalloc(grtx_scene *sc, const grtx_ca
     if (st) return st;
     if (p->alpha_min != sc->alpha_min)
         return grtx_fail(GRTX_ERR_INVALID_ARG, "alpha_min differs from the one the scene was built with");
+    if (p->traversal == GRTX_TRAVERSAL_SINGLE)
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "the fixed-scratch trace supports checkpoint and restart traversal");
     if (!d_rgbT || ((uintptr_t)d_rgbT & 15)) return grtx_fail(GRTX_ERR_INVALID_ARG, "rgbT must be a 16-byte aligned pointer");
     TraceArgs a = {};
     st = grtx_fill_camera(a.cam, a.n_items, cam);

@@ -1,0 +1,219 @@
+// Single-round traversal: the baseline of Sec. III-C (Observation II) that collects every
+// intersected Gaussian in one traversal, then sorts and blends after it, instead of k-buffer
+// rounds with early termination between them.
+//
+// Per ray: one stack traversal of the whole BVH over (t_near, t_far] appends every hit key
+// (t, leaf index) to the ray slot's list in the trace workspace (capacity ckpt_capacity,
+// interleaved [entry][slot] like the checkpoint lists). The list is then made a binary
+// min-heap and popped in key order while blending front to back, stopping right after the
+// Gaussian that takes T below T_min: the sort stops where termination does, so its cost is
+// O(n + b log n) for n hits and b blended. A ray with more hits than the capacity is traced
+// again with k-buffer rounds restarted from the root (k = 16), which gives the same result.
+#include "trace_impl.cuh"
+
+namespace {
+
+constexpr int kFallbackK = 16;
+
+// Orderable 64-bit key of (t, leaf index): float bits mapped so that unsigned order is
+// numeric order for either sign, then the index.
+__device__ __forceinline__ uint64_t single_key(uint2 v)
+{
+    uint32_t b = v.x;
+    b ^= (b & 0x80000000u) ? 0xffffffffu : 0x80000000u;
+    return ((uint64_t)b << 32) | v.y;
+}
+
+__device__ __forceinline__ void heap_sift_down(uint2 *__restrict__ h, size_t S, int i, int n)
+{
+    uint2 v = h[(size_t)i * S];
+    uint64_t kv = single_key(v);
+    for (;;) {
+        int c = 2 * i + 1;
+        if (c >= n) break;
+        uint2 cv = h[(size_t)c * S];
+        uint64_t kc = single_key(cv);
+        if (c + 1 < n) {
+            uint2 rv = h[(size_t)(c + 1) * S];
+            uint64_t kr = single_key(rv);
+            if (kr < kc) {
+                ++c;
+                cv = rv;
+                kc = kr;
+            }
+        }
+        if (kv <= kc) break;
+        h[(size_t)i * S] = cv;
+        i = c;
+    }
+    h[(size_t)i * S] = v;
+}
+
+// Every hit of the ray, appended to list (stride S). Returns the count, or -1 when the
+// capacity is exceeded.
+template <bool PROXY, bool INSTR>
+__device__ __forceinline__ int collect_hits(const TraceArgs &a, const SceneRef &sc, float3 o, float3 d, float3 inv,
+                                            float tn, float tf, uint2 *__restrict__ list, Counters &cnt,
+                                            unsigned &collected)
+{
+    const size_t S = (size_t)a.n_slots;
+    uint32_t stack[GRTX_STACK];
+    int sp = 0, n = 0;
+    uint32_t ref = 0u;
+    for (;;) {
+        if (ref & GRTX_LEAF) {
+            uint32_t idx = ref & ~GRTX_LEAF;
+            if (INSTR) cnt.leaves++;
+            uint32_t gi;
+            bool touch = true;
+            if (PROXY) {
+                const float4 *tr = sc.tris + 3 * (size_t)idx;
+                float4 v0 = __ldg(tr), v1 = __ldg(tr + 1), v2 = __ldg(tr + 2);
+                gi = __float_as_uint(v0.w);
+                touch = tri_hit(v0, v1, v2, o, d) > tn;
+            } else {
+                gi = idx;
+            }
+            float t, D2, w[3];
+            if (touch && sphere_test(sc.geom + 4 * (size_t)gi, o, d, t, D2, w) && D2 <= 1.0f && t > tn && t <= tf) {
+                if (n >= a.ckpt_cap) return -1;
+                list[(size_t)n * S] = make_uint2(__float_as_uint(t), gi);
+                ++n;
+                if (INSTR) collected++;
+            }
+        } else {
+            if (INSTR) cnt.nodes++;
+            const float4 *nd = sc.nodes + 4 * (size_t)ref;
+            float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+            uint32_t c0 = __float_as_uint(n3.x), c1 = __float_as_uint(n3.y);
+            float e0, x0, e1, x1;
+            slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, o, inv, tn, tf, e0, x0);
+            slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, o, inv, tn, tf, e1, x1);
+            bool h0 = e0 <= x0;
+            bool h1 = e1 <= x1 && c1 != GRTX_NONE;
+            if (h0 && h1) {
+                bool near0 = e0 <= e1;
+                ref = near0 ? c0 : c1;
+                if (sp < GRTX_STACK) stack[sp++] = near0 ? c1 : c0;
+                else if (INSTR) cnt.overflow++;
+                continue;
+            }
+            if (h0 || h1) {
+                ref = h0 ? c0 : c1;
+                continue;
+            }
+        }
+        if (sp == 0) break;
+        ref = stack[--sp];
+    }
+    return n;
+}
+
+template <bool PROXY, bool INSTR>
+__device__ __forceinline__ void single_ray(const TraceArgs &a, const SceneRef &sc, int slot, int64_t pix, float3 o,
+                                           float3 d, float tn, float tf, KBuf<kFallbackK> &kb, Counters &cnt,
+                                           unsigned &collected)
+{
+    const size_t S = (size_t)a.n_slots;
+    float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+    float nrm = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+    float3 dn = make_float3(d.x * nrm, d.y * nrm, d.z * nrm);
+    uint2 *list = a.ck0 + slot;
+    int n = 0;
+    if (sc.has_tree) {
+        if (INSTR) cnt.rounds++;
+        n = collect_hits<PROXY, INSTR>(a, sc, o, d, inv, tn, tf, list, cnt, collected);
+        if (n < 0) {                  // more hits than the list holds: k-buffer rounds instead
+            if (INSTR) cnt.fallbacks++;
+            trace_ray<kFallbackK, PROXY, INSTR, false>(a, sc, a.rgbT, slot, pix, o, d, tn, tf, kb, cnt);
+            return;
+        }
+    }
+    BlendState st;
+    st.C[0] = st.C[1] = st.C[2] = 0.f;
+    st.T = 1.f;
+    for (int i = n / 2 - 1; i >= 0; --i) heap_sift_down(list, S, i, n);
+    uint64_t prev = ~0ull;
+    int nb = 0;
+    while (n > 0) {
+        uint2 top = list[0];
+        --n;
+        if (n > 0) {
+            list[0] = list[(size_t)n * S];
+            heap_sift_down(list, S, 0, n);
+        }
+        uint64_t key = single_key(top);
+        if (PROXY && key == prev) continue;     // one Gaussian found through several triangles
+        prev = key;
+        uint32_t idx = top.y;
+        blend_one<false>(a, sc, st, idx, o, d, dn);
+        if (INSTR) {
+            if (a.ids && nb < a.ids_cap) a.ids[(size_t)pix * a.ids_cap + nb] = sc.gid[idx];
+            cnt.blended++;
+        }
+        ++nb;
+        if (st.T < a.T_min) break;
+    }
+    a.rgbT[pix] = make_float4(st.C[0] + st.T * a.bg0, st.C[1] + st.T * a.bg1, st.C[2] + st.T * a.bg2, st.T);
+    if (INSTR && a.n_blended) a.n_blended[pix] = nb;
+}
+
+template <bool PROXY, bool INSTR>
+__global__ void __launch_bounds__(kBlock, 8) k_trace_single(TraceArgs a)
+{
+    __shared__ float s_kt[kFallbackK * kBlock];
+    __shared__ uint32_t s_ki[kFallbackK * kBlock];
+    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    KBuf<kFallbackK> kb;
+    kb.t = s_kt + threadIdx.x;
+    kb.id = s_ki + threadIdx.x;
+    Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
+    unsigned rays = 0, collected = 0;
+    for (;;) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(a.queue, 32u);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= a.n_items) break;
+        int64_t pix;
+        float3 o, d;
+        float tn, tf;
+        if (make_ray(a.cam, base + lane, pix, o, d, tn, tf)) {
+            ++rays;
+            single_ray<PROXY, INSTR>(a, a.sc, slot, pix, o, d, tn, tf, kb, cnt, collected);
+        }
+        __syncwarp();
+    }
+    if (INSTR && a.stats) {
+        unsigned long long v[10] = {rays, cnt.nodes, cnt.leaves, cnt.blended, cnt.rounds, cnt.ckpt, cnt.evictions,
+                                    cnt.fallbacks, cnt.overflow, collected};
+#pragma unroll
+        for (int q = 0; q < 10; ++q) {
+            unsigned long long x = v[q];
+            for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+            if (lane == 0 && x) atomicAdd((&a.stats->rays) + q, x);
+        }
+    }
+}
+
+}  // namespace
+
+int trace_single_launch(const TraceArgs &a, bool proxy, bool instr, int blocks, cudaStream_t s)
+{
+    dim3 g(blocks), b(kBlock);
+    if (proxy && instr) k_trace_single<true, true><<<g, b, 0, s>>>(a);
+    else if (proxy) k_trace_single<true, false><<<g, b, 0, s>>>(a);
+    else if (instr) k_trace_single<false, true><<<g, b, 0, s>>>(a);
+    else k_trace_single<false, false><<<g, b, 0, s>>>(a);
+    return cudaGetLastError() == cudaSuccess ? GRTX_OK : GRTX_ERR_CUDA;
+}
+
+int trace_single_occupancy(bool proxy, bool instr, int *blocks_per_sm)
+{
+    cudaError_t e;
+    if (proxy && instr) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace_single<true, true>, kBlock, 0);
+    else if (proxy) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace_single<true, false>, kBlock, 0);
+    else if (instr) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace_single<false, true>, kBlock, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace_single<false, false>, kBlock, 0);
+    return e == cudaSuccess ? GRTX_OK : GRTX_ERR_CUDA;
+}

@@ -98,7 +98,7 @@ class grtx_grads(C.Structure):
 class grtx_params(C.Structure):
     _fields_ = [("k", C.c_int32), ("traversal", C.c_int32), ("alpha_min", C.c_float), ("T_min", C.c_float),
                 ("alpha_max", C.c_float), ("bg", C.c_float * 3), ("ckpt_capacity", C.c_int32),
-                ("evict_capacity", C.c_int32)]
+                ("evict_capacity", C.c_int32), ("bvh_codes", C.c_int32)]
 
 
 class grtx_camera(C.Structure):
@@ -110,7 +110,7 @@ class grtx_camera(C.Structure):
 
 class grtx_stats(C.Structure):
     _fields_ = [(n, C.c_ulonglong) for n in ("rays", "nodes", "leaves", "blended", "rounds", "ckpt_writes",
-                                             "evictions", "fallbacks", "stack_overflow", "reserved")]
+                                             "evictions", "fallbacks", "stack_overflow", "collected")]
 
 
 class grtx_trace_outputs(C.Structure):
@@ -148,6 +148,7 @@ _SIGS = {
     "grtx_last_error": (C.c_char_p, []),
     "grtx_prep_gaussians": (C.c_int, [C.POINTER(grtx_gaussians), C.c_float, _fp, _fp, _fp]),
     "grtx_morton_codes": (C.c_int, [_fp, C.c_int64, _fp, _fp, _fp, _fp]),
+    "grtx_morton_codes_sized": (C.c_int, [_fp, C.c_int64, _fp, _fp, _fp, _fp]),
     "grtx_sort_pairs": (C.c_int, [_fp, _fp, C.c_int64, C.c_int, _fp, C.POINTER(C.c_size_t), _fp]),
     "grtx_radix_tree": (C.c_int, [_fp, C.c_int64, _fp, _fp, _fp, _fp]),
     "grtx_refit": (C.c_int, [_fp, _fp, _fp, _fp, C.c_int64, _fp, _fp, _fp]),
@@ -223,9 +224,13 @@ def stream_handle(stream=None):
     return C.c_void_p(s.cuda_stream)
 
 
+BVH_CODES = {"sized": 0, "centroid": 1}
+
+
 def make_params(k=16, traversal=0, alpha_min=0.01, T_min=1e-3, alpha_max=0.99, bg=(0.0, 0.0, 0.0),
-                ckpt_capacity=0, evict_capacity=0) -> grtx_params:
+                ckpt_capacity=0, evict_capacity=0, bvh_codes=0) -> grtx_params:
     p = grtx_params()
+    p.bvh_codes = BVH_CODES[bvh_codes] if isinstance(bvh_codes, str) else int(bvh_codes)
     p.k, p.traversal = int(k), int(traversal)
     p.alpha_min, p.T_min, p.alpha_max = alpha_min, T_min, alpha_max
     for i in range(3):
@@ -279,6 +284,11 @@ def grtx_prep_gaussians(g: grtx_gaussians, alpha_min: float, geom, aabb, stream=
 def grtx_morton_codes(aabb, bounds, codes, bounds_out=None, stream=None):
     check(lib().grtx_morton_codes(ptr(aabb), int(aabb.shape[0]), ptr(bounds), ptr(bounds_out), ptr(codes),
                                   stream_handle(stream)), "grtx_morton_codes")
+
+
+def grtx_morton_codes_sized(aabb, bounds, codes, bounds_out=None, stream=None):
+    check(lib().grtx_morton_codes_sized(ptr(aabb), int(aabb.shape[0]), ptr(bounds), ptr(bounds_out), ptr(codes),
+                                        stream_handle(stream)), "grtx_morton_codes_sized")
 
 
 def grtx_sort_pairs(keys, values, key_bits=64, stream=None):
@@ -378,7 +388,7 @@ def grtx_trace_backward(scene: int, g: grtx_gaussians, cam: grtx_camera, p: grtx
                                     ptr(dL_drgbT), C.byref(gr), stream_handle(stream)), "grtx_trace_backward")
 
 
-STATS_FIELDS = tuple(n for n, _ in grtx_stats._fields_ if n != "reserved")
+STATS_FIELDS = tuple(n for n, _ in grtx_stats._fields_)
 
 
 def stats_tensor(device="cuda"):

@@ -10,7 +10,7 @@ import torch
 from . import native as N
 
 FORMS = {"sphere": 0, "proxy20": 1}
-TRAVERSALS = {"checkpoint": 0, "restart": 1}
+TRAVERSALS = {"checkpoint": 0, "restart": 1, "single": 2}
 
 
 def _cuda_f32(a, device) -> torch.Tensor:
@@ -31,19 +31,20 @@ class Scene:
     triangles per Gaussian in one monolithic BVH, the baseline of Sec. III-C)."""
 
     def __init__(self, means, log_scales, quats, logits, sh, sh_degree: int, form: str = "sphere",
-                 alpha_min: float = 0.01, stream=None):
+                 alpha_min: float = 0.01, stream=None, bvh_codes: str = "sized"):
         dev = torch.device("cuda", torch.cuda.current_device())
         self.tensors = tuple(_cuda_f32(a, dev) for a in (means, log_scales, quats, logits, sh))
         self.sh_degree = int(sh_degree)
         self.form = form
         self.alpha_min = float(alpha_min)
         self._g = N.make_gaussians(*self.tensors, self.sh_degree)
-        p = N.make_params(alpha_min=alpha_min)
+        self.bvh_codes = bvh_codes
+        p = N.make_params(alpha_min=alpha_min, bvh_codes=bvh_codes)
         self.handle = N.grtx_build_bvh(self._g, p, FORMS[form], stream)
 
     @classmethod
-    def from_params(cls, g, form="sphere", alpha_min=0.01, stream=None):
-        return cls(g.means, g.log_scales, g.quats, g.logits, g.sh, g.sh_degree, form, alpha_min, stream)
+    def from_params(cls, g, form="sphere", alpha_min=0.01, stream=None, bvh_codes="sized"):
+        return cls(g.means, g.log_scales, g.quats, g.logits, g.sh, g.sh_degree, form, alpha_min, stream, bvh_codes)
 
     @property
     def n(self) -> int:

@@ -85,21 +85,26 @@ def _random_boxes(n, seed, dups=False):
     return np.concatenate([c - e, c + e], 1).astype(np.float32)
 
 
+@pytest.mark.parametrize("kind", ["centroid", "sized"])
 @pytest.mark.parametrize("n,dups", [(1, False), (2, False), (1000, False), (4097, True), (300_001, False)])
-def test_morton_bit_exact(n, dups):
+def test_morton_bit_exact(n, dups, kind):
     boxes = _random_boxes(n, n, dups)
     boxes[::97] = [np.inf, np.inf, np.inf, -np.inf, -np.inf, -np.inf]     # empty boxes
+    if n > 10:
+        boxes[5] = [-40, -40, -40, 40, 40, 40]                             # size clamps
+        boxes[7, 3:] = boxes[7, :3]                                        # a point
     d = torch.from_numpy(boxes).cuda()
     codes = torch.empty(n, dtype=torch.int64, device="cuda")
     bounds = torch.empty(6, dtype=torch.float32, device="cuda")
-    N.grtx_morton_codes(d, None, codes, bounds_out=bounds)
+    fn = N.grtx_morton_codes if kind == "centroid" else N.grtx_morton_codes_sized
+    fn(d, None, codes, bounds_out=bounds)
     torch.cuda.synchronize()
     valid = np.all(boxes[:, :3] <= boxes[:, 3:], axis=1)
     ob = O.centroid_bounds(boxes[valid]) if valid.any() else np.zeros(6, np.float32)
     np.testing.assert_array_equal(bounds.cpu().numpy()[: 6] if valid.any() else ob, ob)
     oc = np.full(n, np.iinfo(np.uint64).max, dtype=np.uint64)
     if valid.any():
-        oc[valid] = O.morton63(boxes[valid], ob)
+        oc[valid] = (O.morton63 if kind == "centroid" else O.morton_sized64)(boxes[valid], ob)
     assert np.array_equal(codes.cpu().numpy().view(np.uint64), oc)
 
 
@@ -147,9 +152,10 @@ def test_radix_tree_and_refit_bit_exact(n, dups):
             assert par[j] == i
 
 
-def test_scene_tree_is_valid_lbvh():
+@pytest.mark.parametrize("bvh_codes", ["sized", "centroid"])
+def test_scene_tree_is_valid_lbvh(bvh_codes):
     g = scenes.surface_scene(n=20000, seed=9)
-    sc = R.Scene.from_params(g)
+    sc = R.Scene.from_params(g, bvh_codes=bvh_codes)
     info = sc.info()
     nodes, ids, codes = sc.export()
     nodes = nodes.cpu().numpy()
@@ -257,6 +263,61 @@ def test_forward_dense_parity_both_traversals(dense, k):
     assert (ref["n_blend"] < ref["n_hits"]).sum() > 100       # early termination is exercised
 
 
+# ------------------------------------------------------------------ single-round traversal
+
+
+@pytest.mark.parametrize("form", ["sphere", "proxy20"])
+def test_single_round_parity(dense, form):
+    """Collect every hit, then sort and blend (Sec. III-C Obs. II): the definition of the
+    image, so it matches the oracle, blends exactly the k-buffer rounds' lists and collects
+    every hit of every ray, past the termination point too."""
+    g, cam, S, rays, ref = dense
+    res = _gpu_render(g, cam, form=form, traversal="single", ids_cap=256)
+    _check_image(res, ref, S, rays)
+    st = res["stats"]
+    assert st["rounds"] == st["rays"] and st["fallbacks"] == 0
+    assert st["ckpt_writes"] == 0 and st["evictions"] == 0
+    assert st["blended"] == int(ref["n_blend"].sum())
+    if form == "sphere":
+        # every hit is collected once (up to the alpha_min boundary flips of FP32)
+        assert abs(st["collected"] - int(ref["n_hits"].sum())) <= 1e-4 * int(ref["n_hits"].sum()) + 2
+    else:
+        assert st["collected"] >= int(ref["n_hits"].sum())       # duplicates through triangles
+    # same blend lists; the colour may differ in the last bit where the compiler contracted
+    # the SH polynomial differently in the two kernels
+    rounds = _gpu_render(g, cam, form=form, k=8, traversal="checkpoint", ids_cap=256)
+    np.testing.assert_array_equal(res["ids"], rounds["ids"])
+    np.testing.assert_array_equal(res["n_blended"], rounds["n_blended"])
+    np.testing.assert_allclose(res["rgbT"], rounds["rgbT"], rtol=0, atol=1e-6)
+
+
+@pytest.mark.parametrize("form", ["sphere", "proxy20"])
+def test_single_round_overflow_falls_back_exactly(dense, form):
+    g, cam, S, rays, ref = dense
+    res = _gpu_render(g, cam, form=form, traversal="single", ckpt_capacity=5, ids_cap=256)
+    assert res["stats"]["fallbacks"] > 0
+    _check_image(res, ref, S, rays)
+    full = _gpu_render(g, cam, form=form, traversal="single", ids_cap=256)
+    np.testing.assert_array_equal(res["ids"], full["ids"])
+    np.testing.assert_allclose(res["rgbT"], full["rgbT"], rtol=0, atol=1e-6)
+
+
+def test_single_round_rejected_where_unsupported(dense):
+    g = dense[0]
+    sc = R.Scene.from_params(g)
+    cam = scenes.pinhole_camera(16, 16, (0.0, 0.0, -3.0), (0, 0, 0), 60.0)
+    out = torch.empty((256, 4), device="cuda")
+    p = N.make_params(traversal=2)
+    with pytest.raises(N.GrtxError, match="traversal") as e:
+        N.grtx_trace_forward_noalloc(sc.handle, N.make_camera(cam), p, out)
+    assert e.value.status == 1
+    from paper_2601_20429_gb300.serve import Server
+    with pytest.raises(N.GrtxError, match="traversal") as e:
+        Server([sc], traversal="single")
+    assert e.value.status == 1
+    sc.close()
+
+
 @pytest.mark.parametrize("caps", [(2, 0), (0, 1), (3, 3)])
 def test_forward_capacity_fallback_is_exact(dense, caps):
     g, cam, S, rays, ref = dense
@@ -272,6 +333,25 @@ def test_forward_proxy_form_parity(dense, k, traversal):
     res = _gpu_render(g, cam, form="proxy20", k=k, traversal=traversal, ids_cap=256)
     _check_image(res, ref, S, rays)
     assert res["stats"]["blended"] == int(ref["n_blend"].sum())
+
+
+@pytest.mark.parametrize("form", ["sphere", "proxy20"])
+def test_image_independent_of_bvh_codes(form):
+    """The tree shape changes the cost, never the result: the same Gaussians in the same
+    (t, id) order are blended with the same arithmetic, so the images are bitwise equal."""
+    g = scenes.outdoor_scene(n=30000, seed=12, size=16.0, n_clusters=30)
+    cam = scenes.fisheye_camera(72, 40, (0.0, 1.7, 0.0), (1.0, 0.0, 0.0), 90.0)
+    out, nodes = {}, {}
+    for codes in ("sized", "centroid"):
+        sc = R.Scene.from_params(g, form=form, bvh_codes=codes)
+        r = R.render(sc, cam, k=8, want_n_blended=True, want_stats=True)
+        torch.cuda.synchronize()
+        out[codes] = (r["rgbT"].cpu().numpy(), r["n_blended"].cpu().numpy())
+        nodes[codes] = N.stats_dict(r["stats"])["nodes"]
+        sc.close()
+    np.testing.assert_array_equal(out["sized"][0], out["centroid"][0])
+    np.testing.assert_array_equal(out["sized"][1], out["centroid"][1])
+    assert out["sized"][1].sum() > 0 and nodes["sized"] != nodes["centroid"]
 
 
 def test_forward_proxy_checkpoint_fallback_is_exact(dense):

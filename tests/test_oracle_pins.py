@@ -426,6 +426,60 @@ def test_morton_known_codes():
     assert [int(c) for c in codes] == expect
 
 
+def _pt_boxes(pts):
+    pts = np.asarray(pts, np.float32)
+    return np.concatenate([pts, pts], 1)
+
+
+def test_morton_sized_known_codes():
+    """Hand-computed size-aware codes: a point box has size 0; the diagonal of a 3-4-0 box is
+    exactly 5; a box larger than twice the bounds clamps the size to 2^16 - 2."""
+    unit = np.array([0, 0, 0, 1, 1, 1], np.float32)
+    codes = O.morton_sized64(_pt_boxes([[0, 0, 0], [0.5, 0, 0], [0, 0.5, 0], [0, 0, 0.5], [1, 1, 1]]), unit)
+    all_xyz = sum(0xE << (4 * b) for b in range(16))
+    assert [int(c) for c in codes] == [0, 2 ** 63, 2 ** 62, 2 ** 61, all_xyz]
+    boxes = np.array([[0, 0, 0, 1, 0, 0], [-5, -5, -5, 5, 5, 5]], np.float32)
+    codes = O.morton_sized64(boxes, unit)
+    assert int(codes[0]) == 2 ** 63 + 2 ** 60                        # centroid x 0.5, diagonal 1
+    assert int(codes[1]) == sum(1 << (4 * b) for b in range(1, 16))  # centroid 0, size 65534
+    eight = np.array([0, 0, 0, 8, 8, 8], np.float32)
+    codes = O.morton_sized64(np.array([[0, 0, 0, 3, 4, 0]], np.float32), eight)
+    # centroid (1.5, 2, 0) -> q = (12288, 16384, 0); diagonal 5 -> q_s = 5 * 2^15 / 8 = 20480
+    assert int(codes[0]) == 2 ** 58 + 2 ** 56 + 2 ** 55 + 2 ** 51 + 2 ** 48
+
+
+def test_morton_sized_position_bits_are_the_63bit_code_prefix():
+    """For point boxes the x, y, z bits of the sized code are the top 16 of the 21-bit
+    quantisation (the power-of-two grids nest exactly in FP32)."""
+    rng = np.random.default_rng(21)
+    pts = rng.uniform(-3, 7, (5000, 3)).astype(np.float32)
+    pts[:10] = pts[:10].min(0)
+    pts[10:20] = pts[10:20].max(0)
+    boxes = _pt_boxes(pts)
+    bounds = O.centroid_bounds(boxes)
+    sized = O.morton_sized64(boxes, bounds)
+    m63 = O.morton63(boxes, bounds)
+    for c, m in zip(sized[:2000], m63[:2000]):
+        c = int(c)
+        assert c & sum(1 << (4 * b) for b in range(16)) == 0          # size 0
+        xyz = 0
+        for b in range(16):
+            xyz |= ((c >> (4 * b + 1)) & 7) << (3 * b)
+        assert xyz == int(m) >> 15
+
+
+def test_morton_sized_monotone_in_size_and_below_empty_marker():
+    c = np.array([0.25, 0.5, 0.75], np.float32)
+    h = (np.arange(1001) / 4096.0).astype(np.float32)     # exact: the centroid stays c
+    boxes = np.concatenate([c - h[:, None], c + h[:, None]], 1).astype(np.float32)
+    codes = O.morton_sized64(boxes, np.array([0, 0, 0, 1, 1, 1], np.float32))
+    assert np.all(np.diff(codes.astype(object)) > 0)
+    big = np.array([[1, 1, 1, 1, 1, 1], [-1e30, -1e30, -1e30, 1e30, 1e30, 1e30]], np.float32)
+    big[0, :3] -= 1e6; big[0, 3:] += 1e6 + 2
+    codes = O.morton_sized64(big, np.array([0, 0, 0, 1, 1, 1], np.float32))
+    assert all(int(x) < 2 ** 64 - 1 for x in codes)
+
+
 def test_centroid_bounds():
     rng = np.random.default_rng(8)
     a = rng.uniform(-5, 5, (100, 6)).astype(np.float32)
