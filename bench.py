@@ -271,9 +271,10 @@ def mrays(n_rays: int, times_ms) -> float:
 
 
 def bench_surface_ablations(g, sc, cam, k: int, steps: int, stream, flush) -> dict:
-    """On the surface scene: single-round traversal (Sec. III-C Obs. II), the centroid-only
-    LBVH codes against the size-aware default, and the resolution / field-of-view sweep
-    (Sec. V-E)."""
+    """On the surface scene: single-round traversal (Sec. III-C Obs. II), the instance BVH over
+    a shared 20- / 80-triangle icosphere template (Sec. IV-A, second option), the
+    centroid-only LBVH codes against the size-aware default, and the resolution /
+    field-of-view sweep (Sec. V-E)."""
     import torch
     from paper_2601_20429_gb300 import native as N
     from paper_2601_20429_gb300 import render as R
@@ -285,6 +286,13 @@ def bench_surface_ablations(g, sc, cam, k: int, steps: int, stream, flush) -> di
     t = time_frames(lambda: R.render(sc, cam, k=k, traversal="single", out=out), steps, 2, flush, stream)
     res["single_round"] = {"Mrays_per_s": mrays(n_rays, t), "ms_per_frame": statistics.mean(t),
                            "nodes_per_ray": nodes_per_ray(st), "list_capacity": 2048}
+    for form in ("ico20", "ico80"):
+        sc_i = R.Scene.from_params(g, form=form)
+        st = N.stats_dict(R.render(sc_i, cam, k=k, out=out, want_stats=True)["stats"])
+        t = time_frames(lambda: R.render(sc_i, cam, k=k, out=out), steps, 2, flush, stream)
+        res[form] = {"Mrays_per_s": mrays(n_rays, t), "ms_per_frame": statistics.mean(t),
+                     "nodes_per_ray": nodes_per_ray(st), "template_triangles": 20 if form == "ico20" else 80}
+        sc_i.close()
     sc_c = R.Scene.from_params(g, bvh_codes="centroid")
     st = N.stats_dict(R.render(sc_c, cam, k=k, out=out, want_stats=True)["stats"])
     t = time_frames(lambda: R.render(sc_c, cam, k=k, out=out), steps, 2, flush, stream)
@@ -404,8 +412,8 @@ def bench_differentiable(steps: int, warmup: int, stream):
 
 
 def bench_outdoor(steps: int, stream, flush):
-    """6M-Gaussian outdoor scene, 1920x1080 fisheye plus one mirror bounce: primary and
-    secondary rays timed separately (explicit ray lists), k = 16."""
+    """6M-Gaussian outdoor scene, 1920x1080 fisheye plus one bounce off a mirror or through a
+    glass ball: primary and secondary rays timed separately (explicit ray lists), k = 16."""
     import torch
     from paper_2601_20429_gb300 import native as N
     from paper_2601_20429_gb300 import render as R
@@ -424,7 +432,8 @@ def bench_outdoor(steps: int, stream, flush):
            torch.empty(n, device="cuda")]
     spix = torch.empty(n, dtype=torch.int32, device="cuda")
     ns = torch.zeros(1, dtype=torch.int32, device="cuda")
-    N.grtx_mirror_rays(N.make_camera(cam), N.make_mirror(mirror), prim, sec, spix, ns)
+    glass = scenes.outdoor_glass()
+    N.grtx_secondary_rays(N.make_camera(cam), [N.make_mirror(mirror)], [N.make_glass(glass)], prim, sec, spix, ns)
     m = int(ns.item())
     sec_rays = [t[:m] for t in sec]
     out_p = torch.empty((n, 4), device="cuda")
@@ -437,7 +446,8 @@ def bench_outdoor(steps: int, stream, flush):
     st_c = N.stats_dict(R.render(sc_c, None, rays=prim, k=cfg["k"], want_stats=True)["stats"])
     sc_c.close()
     sc.close()
-    return {"workload": "6M outdoor Gaussians, 1920x1080 equidistant fisheye, one 4x3 m mirror, k=16",
+    return {"workload": "6M outdoor Gaussians, 1920x1080 equidistant fisheye, one 4x3 m mirror and one glass "
+                        "ball (index 1.5), k=16",
             "build_ms": build_ms, "secondary_rays": m,
             "primary": {"Mrays_per_s": n / (statistics.mean(tp) / 1e3) / 1e6, "ms": statistics.mean(tp),
                         "nodes_per_ray": nodes_per_ray(st_p)},

@@ -81,8 +81,12 @@ typedef struct grtx_grads {
 } grtx_grads;
 
 enum { GRTX_FORM_SPHERE = 0,        /* one leaf per Gaussian, analytic unit sphere (Sec. IV-A) */
-       GRTX_FORM_PROXY20 = 1 };     /* one leaf per proxy triangle: 20-triangle icosahedron
+       GRTX_FORM_PROXY20 = 1,       /* one leaf per proxy triangle: 20-triangle icosahedron
                                        around each Gaussian, monolithic BVH (Sec. III-C Obs. I) */
+       GRTX_FORM_ICO20 = 2,         /* two-level: the sphere form's BVH over Gaussian instances,
+                                       and one shared template BVH of a 20-triangle icosahedron
+                                       around the unit sphere (Sec. IV-A, second option) */
+       GRTX_FORM_ICO80 = 3 };       /* as ICO20 with the 80-triangle icosphere */
 enum { GRTX_TRAVERSAL_CHECKPOINT = 0, /* resume from checkpointed nodes + eviction list (IV-B) */
        GRTX_TRAVERSAL_RESTART = 1,    /* restart from the root every round (Sec. III-A)       */
        GRTX_TRAVERSAL_SINGLE = 2 };   /* one traversal collecting every hit, then sort and
@@ -272,7 +276,9 @@ GRTX_API int grtx_refit(const uint32_t *d_left, const uint32_t *d_right, const u
 
 /* Build the acceleration structure for one set of Gaussians (Sec. IV-A "Bounding
  * Primitives": form GRTX_FORM_SPHERE keeps one instance per Gaussian over a shared analytic
- * unit sphere; GRTX_FORM_PROXY20 is the 20-triangle monolithic baseline of Sec. III-C).
+ * unit sphere; GRTX_FORM_ICO20 / GRTX_FORM_ICO80 build the same instance BVH and refer to a
+ * shared template mesh BVH (grtx_template_mesh), uploaded once per device; GRTX_FORM_PROXY20
+ * is the 20-triangle monolithic baseline of Sec. III-C).
  * Steps: grtx_prep_gaussians -> (proxy: expand 20 triangles per Gaussian) -> Morton codes ->
  * radix sort -> radix tree -> refit -> node compaction. p->alpha_min fixes the ellipsoid
  * radius; later traces must use the same alpha_min. The library allocates (stream-ordered)
@@ -283,6 +289,18 @@ GRTX_API int grtx_refit(const uint32_t *d_left, const uint32_t *d_right, const u
  * tree is deeper than the traversal stack (64). */
 GRTX_API int grtx_build_bvh(const grtx_gaussians *g, const grtx_params *p, int form, void *stream,
                             grtx_scene **out);
+
+/* The shared template mesh of GRTX_FORM_ICO20 / GRTX_FORM_ICO80 (host only, no device work):
+ * a regular icosahedron (20 triangles), or for ICO80 the icosphere made by splitting each of
+ * its faces into four at the edge midpoints pushed out to the sphere, with every face oriented
+ * outwards and the mesh scaled so that its nearest face plane is at 1 + 1e-3 from the centre
+ * (it encloses the unit sphere). Writes *n_tris and, if h_tris is not NULL, the triangles as
+ * h_tris[n_tris][9] (three vertices x, y, z) into caller host memory of 9 * n_tris floats.
+ * At a top-level leaf the trace maps the ray into the Gaussian's unit-sphere space (scaled by
+ * 1 / (1 + 1e-5 + 4e-6 |o_l|) against FP32 rounding, which leaves t unchanged), traverses a
+ * BVH over these triangles, and on a triangle hit at t > t_near runs the exact unit-sphere
+ * test for the Gaussian, so the image equals the sphere form's. */
+GRTX_API int grtx_template_mesh(int form, float *h_tris, int *n_tris);
 
 /* Fill *info (host) for a built scene. Host-only, no stream work. */
 GRTX_API int grtx_scene_info_get(const grtx_scene *scene, grtx_scene_info *info);
@@ -353,6 +371,38 @@ GRTX_API int grtx_mirror_rays(const grtx_camera *cam, const grtx_mirror *m, floa
                               float *d_sec_origins, float *d_sec_dirs, float *d_sec_tnear,
                               float *d_sec_tfar, int32_t *d_sec_pixel, int32_t *d_n_sec,
                               void *stream);
+
+/* A solid glass ball for refraction secondary rays (Sec. VI "GRTX-HW on Secondary Rays": a
+ * spherical glass object placed in the scene). center, radius > 0; ior: index of refraction
+ * (> 0) against the surrounding air of index 1; t_near_secondary: t_near of its rays. */
+typedef struct grtx_glass {
+    float center[3];
+    float radius;
+    float ior;
+    float t_near_secondary;
+    float reserved[2];
+} grtx_glass;
+
+#define GRTX_MAX_BOUNCE_OBJECTS 16
+
+/* Rays of a camera with one bounce off the nearest of n_mirrors mirrors and n_glass glass
+ * balls (host arrays, each count in [0, GRTX_MAX_BOUNCE_OBJECTS], copied at the call). Every
+ * primary ray (width*height, pixel order) is written to d_prim_* with t_far clipped to the
+ * nearest object it meets in (t_near, t_far). Each such primary spawns one secondary ray with
+ * t_near = the object's t_near_secondary and t_far = +inf:
+ *  - mirror: as grtx_mirror_rays (origin at the hit, direction reflected about the normal);
+ *  - glass: the unit direction is refracted into the ball at the entry point (Snell's law,
+ *    index 1 outside), carried straight across the ball to the far side, and refracted out;
+ *    the secondary starts on the far side with that unit direction. The inside of a ball is
+ *    empty (nothing is rendered along the chord), there is no Fresnel reflection, and a ray
+ *    that starts inside a ball or only grazes it does not meet it.
+ * Output layout, compaction and *d_n_sec as for grtx_mirror_rays. */
+GRTX_API int grtx_secondary_rays(const grtx_camera *cam, const grtx_mirror *mirrors, int n_mirrors,
+                                 const grtx_glass *glass, int n_glass, float *d_prim_origins,
+                                 float *d_prim_dirs, float *d_prim_tnear, float *d_prim_tfar,
+                                 float *d_sec_origins, float *d_sec_dirs, float *d_sec_tnear,
+                                 float *d_sec_tfar, int32_t *d_sec_pixel, int32_t *d_n_sec,
+                                 void *stream);
 
 /* Composite the secondary image behind the primary one: for each of the *d_n_sec secondary
  * rays j (at most max_sec) with pixel p = d_sec_pixel[j], the primary pixel (C + T bg, T)

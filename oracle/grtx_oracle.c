@@ -1036,6 +1036,125 @@ OG_API int og_mirror_rays(const og_camera *cam, const og_mirror *m, double *po, 
     return ns;
 }
 
+/* A solid glass ball (Sec. VI "GRTX-HW on Secondary Rays": a spherical glass object placed in
+ * the scene for refractions): centre, radius, index of refraction, t_near of its rays. */
+typedef struct og_glass {
+    double center[3], radius, ior, t_near_secondary;
+} og_glass;
+
+/* Snell refraction of unit direction I at a surface with unit normal N facing against I
+ * (N.I < 0) from index n1 into n2, eta = n1 / n2: T = eta I + (eta cos_i - cos_t) N with
+ * cos_i = -N.I and cos_t = sqrt(1 - eta^2 (1 - cos_i^2)) (clamped at 0). */
+static void og_refract(const double I[3], const double Nf[3], double eta, double T[3])
+{
+    double ci = -(I[0] * Nf[0] + I[1] * Nf[1] + I[2] * Nf[2]);
+    double k = 1.0 - eta * eta * (1.0 - ci * ci);
+    double ct = k > 0.0 ? sqrt(k) : 0.0;
+    for (int a = 0; a < 3; ++a) T[a] = eta * I[a] + (eta * ci - ct) * Nf[a];
+}
+
+/* Entry distance of the ray o + t d into the ball (t in units of |d|), or -1 when the ray
+ * misses it, only grazes it, or starts inside it. */
+static double og_glass_entry(const og_glass *gl, const double *o, const double *d)
+{
+    double oc[3], a = 0, b = 0, cc = 0;
+    for (int q = 0; q < 3; ++q) {
+        oc[q] = o[q] - gl->center[q];
+        a += d[q] * d[q];
+        b += oc[q] * d[q];
+        cc += oc[q] * oc[q];
+    }
+    cc -= gl->radius * gl->radius;
+    if (cc <= 0.0 || a == 0.0) return -1.0;
+    double disc = b * b - a * cc;
+    if (disc <= 0.0) return -1.0;
+    return (-b - sqrt(disc)) / a;
+}
+
+/* The nearest of n_mirrors mirrors and n_glass glass balls along each primary ray of cam
+ * (within its (t_near, t_far)) clips the primary there and spawns one secondary ray:
+ *  - a mirror reflects it as in og_mirror_rays;
+ *  - a glass ball refracts it into the ball at the entry point p1 (air index 1), carries it
+ *    straight to the far side p2 = p1 + t2 v, t2 = -2 v.(p1 - c), refracts it out into the
+ *    air, and the secondary starts at p2 with that direction. The ball's inside is empty
+ *    space (nothing is rendered along the chord), there is no Fresnel reflection, and a
+ *    camera inside a ball sees no ball.
+ * Secondaries are listed in pixel order; returns their number. */
+OG_API int og_secondary_rays(const og_camera *cam, const og_mirror *mirrors, int n_mirrors, const og_glass *glass,
+                             int n_glass, double *po, double *pd, double *ptn, double *ptf, double *so, double *sd,
+                             double *stn, double *stf, int *spix)
+{
+    og_camera_rays(cam, po, pd, ptn, ptf);
+    int n = cam->width * cam->height, ns = 0;
+    for (int p = 0; p < n; ++p) {
+        const double *o = po + 3 * p, *d = pd + 3 * p;
+        double t_best = ptf[p];
+        int kind = 0, which = -1;
+        for (int i = 0; i < n_mirrors; ++i) {
+            const og_mirror *m = mirrors + i;
+            double den = 0, num = 0;
+            for (int a = 0; a < 3; ++a) { den += d[a] * m->normal[a]; num += (m->center[a] - o[a]) * m->normal[a]; }
+            if (den == 0.0) continue;
+            double t = num / den;
+            if (!(t > ptn[p] && t < t_best)) continue;
+            double du = 0, dv = 0;
+            for (int a = 0; a < 3; ++a) {
+                double qa = o[a] + t * d[a] - m->center[a];
+                du += qa * m->axis_u[a];
+                dv += qa * m->axis_v[a];
+            }
+            if (fabs(du) > m->half_u || fabs(dv) > m->half_v) continue;
+            t_best = t; kind = 1; which = i;
+        }
+        for (int i = 0; i < n_glass; ++i) {
+            double t = og_glass_entry(glass + i, o, d);
+            if (!(t > ptn[p] && t < t_best)) continue;
+            t_best = t; kind = 2; which = i;
+        }
+        if (kind == 0) continue;
+        ptf[p] = t_best;
+        double q[3];
+        for (int a = 0; a < 3; ++a) q[a] = o[a] + t_best * d[a];
+        if (kind == 1) {
+            const og_mirror *m = mirrors + which;
+            double den = 0;
+            for (int a = 0; a < 3; ++a) den += d[a] * m->normal[a];
+            for (int a = 0; a < 3; ++a) {
+                so[3 * ns + a] = q[a];
+                sd[3 * ns + a] = d[a] - 2.0 * den * m->normal[a];
+            }
+            stn[ns] = m->t_near_secondary;
+        } else {
+            const og_glass *gl = glass + which;
+            double len = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            double u[3], n1[3], v[3], p2[3], n2[3], w[3];
+            for (int a = 0; a < 3; ++a) {
+                u[a] = d[a] / len;
+                n1[a] = (q[a] - gl->center[a]) / gl->radius;
+            }
+            og_refract(u, n1, 1.0 / gl->ior, v);
+            double vl = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]), vp = 0;
+            for (int a = 0; a < 3; ++a) { v[a] /= vl; vp += v[a] * (q[a] - gl->center[a]); }
+            double t2 = -2.0 * vp;
+            for (int a = 0; a < 3; ++a) {
+                p2[a] = q[a] + t2 * v[a];
+                n2[a] = -(p2[a] - gl->center[a]) / gl->radius;     /* inward: faces against v */
+            }
+            og_refract(v, n2, gl->ior, w);
+            double wl = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+            for (int a = 0; a < 3; ++a) {
+                so[3 * ns + a] = p2[a];
+                sd[3 * ns + a] = w[a] / wl;
+            }
+            stn[ns] = gl->t_near_secondary;
+        }
+        stf[ns] = INFINITY;
+        spix[ns] = p;
+        ++ns;
+    }
+    return ns;
+}
+
 /* Continue Eq. volume-render past the mirror: the primary pixel (C + T bg, T) becomes
  * (C + T C2, T T2) with (C2, T2) the secondary ray's pixel rendered against the same bg. */
 OG_API void og_composite_bounce(double *rgbT, const double *sec_rgbT, const int *spix, int n_sec, const double bg[3])

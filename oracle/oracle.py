@@ -62,6 +62,11 @@ class OgMirror(C.Structure):
                 ("t_near_secondary", C.c_double)]
 
 
+class OgGlass(C.Structure):
+    _fields_ = [("center", C.c_double * 3), ("radius", C.c_double), ("ior", C.c_double),
+                ("t_near_secondary", C.c_double)]
+
+
 class OgGrads(C.Structure):
     _fields_ = [(n, C.POINTER(C.c_double)) for n in ("means", "log_scales", "quats", "logits", "sh")]
 
@@ -104,6 +109,9 @@ def lib():
             L.og_mirror_rays.restype = C.c_int
             L.og_mirror_rays.argtypes = [C.POINTER(OgCamera), C.POINTER(OgMirror)] + [_dp] * 8 + [_ip]
             L.og_composite_bounce.argtypes = [_dp, _dp, _ip, C.c_int, _dp]
+            L.og_secondary_rays.restype = C.c_int
+            L.og_secondary_rays.argtypes = ([C.POINTER(OgCamera), C.POINTER(OgMirror), C.c_int, C.POINTER(OgGlass),
+                                             C.c_int] + [_dp] * 8 + [_ip])
             L.og_centroid_bounds.argtypes = [C.c_int, _fp, _fp]
             L.og_morton63.argtypes = [C.c_int, _fp, _fp, _u64p]
             L.og_morton_sized64.argtypes = [C.c_int, _fp, _fp, _u64p]
@@ -331,6 +339,31 @@ def mirror_rays(cam: dict, mirror: dict):
     ns = lib().og_mirror_rays(C.byref(c), C.byref(make_mirror(mirror)), *[_p(a) for a in prim],
                               *[_p(a) for a in sec], _p(spix, _ip))
     return tuple(prim), tuple(a[:ns] for a in sec), spix[:ns].copy()
+
+
+def make_glass(gl: dict) -> OgGlass:
+    g = OgGlass()
+    for i in range(3):
+        g.center[i] = gl["center"][i]
+    g.radius, g.ior, g.t_near_secondary = gl["radius"], gl["ior"], gl["t_near_secondary"]
+    return g
+
+
+def secondary_rays(cam: dict, mirrors=(), glass=()):
+    """Primary rays clipped at the nearest mirror or glass ball, and one reflected or refracted
+    secondary ray per such primary (pixel order); returns (prim, sec, spix)."""
+    n = cam["width"] * cam["height"]
+    po, pd = np.empty((n, 3)), np.empty((n, 3))
+    ptn, ptf = np.empty(n), np.empty(n)
+    so, sd = np.empty((n, 3)), np.empty((n, 3))
+    stn, stf = np.empty(n), np.empty(n)
+    spix = np.empty(n, dtype=np.int32)
+    ma = (OgMirror * max(len(mirrors), 1))(*[make_mirror(m) for m in mirrors])
+    ga = (OgGlass * max(len(glass), 1))(*[make_glass(g) for g in glass])
+    c = make_camera(cam)
+    ns = lib().og_secondary_rays(C.byref(c), ma, len(mirrors), ga, len(glass), _p(po), _p(pd), _p(ptn), _p(ptf),
+                                 _p(so), _p(sd), _p(stn), _p(stf), _p(spix, _ip))
+    return (po, pd, ptn, ptf), (so[:ns], sd[:ns], stn[:ns], stf[:ns]), spix[:ns]
 
 
 def composite_bounce(rgbT: np.ndarray, sec_rgbT: np.ndarray, spix: np.ndarray, bg=(0.0, 0.0, 0.0)) -> np.ndarray:

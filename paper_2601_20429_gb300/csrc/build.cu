@@ -783,7 +783,8 @@ int build_scene(const grtx_gaussians *g, const grtx_params *p, int form, grtx_sc
                                                                       sc->app_stride, sc->geom, leaf_aabb,
                                                                       sc->app, sc->gid);
     GRTX_CHECK_LAUNCH("gather");
-    if (form == GRTX_FORM_SPHERE) {
+    if (form != GRTX_FORM_PROXY20) {       // sphere and icosphere forms: one leaf per Gaussian
+        if (form != GRTX_FORM_SPHERE) TRY(grtx_template_blas(form, &sc->tpl_nodes, &sc->tpl_tris));
         sc->n_leaves = nv;
         TRY(A.get(&sc->codes, nv, false));
         GRTX_CUDA(cudaMemcpyAsync(sc->codes, codes, (size_t)nv * 8, cudaMemcpyDeviceToDevice, s));
@@ -987,7 +988,8 @@ extern "C" GRTX_API int grtx_build_bvh(const grtx_gaussians *g, const grtx_param
     int st = check_gaussians(g);
     if (st) return st;
     if (!p || !out) return grtx_fail(GRTX_ERR_INVALID_ARG, "params or out is NULL");
-    if (form != GRTX_FORM_SPHERE && form != GRTX_FORM_PROXY20) return grtx_fail(GRTX_ERR_INVALID_ARG, "unknown form");
+    if (form != GRTX_FORM_SPHERE && form != GRTX_FORM_PROXY20 && form != GRTX_FORM_ICO20 && form != GRTX_FORM_ICO80)
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "unknown form");
     if (!(p->alpha_min > 0.f && p->alpha_min < 1.f)) return grtx_fail(GRTX_ERR_INVALID_ARG, "alpha_min must be in (0,1)");
     if (p->bvh_codes != GRTX_CODES_SIZED && p->bvh_codes != GRTX_CODES_CENTROID)
         return grtx_fail(GRTX_ERR_INVALID_ARG, "unknown bvh_codes");
@@ -1017,7 +1019,7 @@ extern "C" GRTX_API int grtx_scene_info_get(const grtx_scene *sc, grtx_scene_inf
     info->form = sc->form;
     info->sh_degree = sc->sh_degree;
     info->bytes_nodes = sc->n_nodes * 64;
-    info->bytes_leaves = sc->form == GRTX_FORM_SPHERE ? sc->n_valid * 64 : sc->n_leaves * 48 + sc->n_valid * 64;
+    info->bytes_leaves = sc->form != GRTX_FORM_PROXY20 ? sc->n_valid * 64 : sc->n_leaves * 48 + sc->n_valid * 64;
     info->bytes_appearance = sc->n_valid * sc->app_stride * 4;
     info->bytes_workspace = (int64_t)sc->ws_bytes;
     for (int c = 0; c < 6; ++c) info->bounds[c] = sc->bounds[c];

@@ -45,12 +45,17 @@ struct grtx_scene {
     uint32_t *gid = nullptr;     // [n_valid] Gaussian id of each sorted Gaussian
     uint32_t *leaf_ids = nullptr;// [n_leaves] Gaussian id of each leaf
     uint64_t *codes = nullptr;   // [n_leaves] sorted Morton codes
+    const float4 *tpl_nodes = nullptr;   // icosphere forms: shared template BVH (not owned)
+    const float4 *tpl_tris = nullptr;
     cudaStream_t stream = nullptr;
     // trace workspace (per resident ray slot checkpoint / eviction lists), grown on demand
     void *ws = nullptr;
     size_t ws_bytes = 0;
     unsigned int *d_counter = nullptr;   // ray-queue counters (2 per launch kind)
 };
+
+// Device template BVH and triangles of an icosphere form on the current device (built once).
+int grtx_template_blas(int form, const float4 **nodes, const float4 **tris);
 
 // Persistent-launch geometry of the trace kernels (filled by the trace unit).
 int grtx_trace_slots(int kind, int k, int *blocks, int *threads);

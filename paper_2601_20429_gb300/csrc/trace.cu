@@ -9,8 +9,8 @@
 #include "trace_impl.cuh"
 
 #define GRTX_EXTERN_TRACE(K)                                                                     \
-    extern template int trace_launch<K>(const TraceArgs &, bool, bool, bool, int, cudaStream_t); \
-    extern template int trace_occupancy<K>(bool, bool, bool, int *);
+    extern template int trace_launch<K>(const TraceArgs &, int, bool, bool, int, cudaStream_t); \
+    extern template int trace_occupancy<K>(int, bool, bool, int *);
 GRTX_EXTERN_TRACE(1)
 GRTX_EXTERN_TRACE(2)
 GRTX_EXTERN_TRACE(4)
@@ -18,8 +18,8 @@ GRTX_EXTERN_TRACE(8)
 GRTX_EXTERN_TRACE(16)
 GRTX_EXTERN_TRACE(32)
 
-int trace_single_launch(const TraceArgs &a, bool proxy, bool instr, int blocks, cudaStream_t s);
-int trace_single_occupancy(bool proxy, bool instr, int *blocks_per_sm);
+int trace_single_launch(const TraceArgs &a, int form, bool instr, int blocks, cudaStream_t s);
+int trace_single_occupancy(int form, bool instr, int *blocks_per_sm);
 
 namespace {
 
@@ -27,27 +27,27 @@ inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
 bool valid_k(int k) { return k == 1 || k == 2 || k == 4 || k == 8 || k == 16 || k == 32; }
 
-int launch_k(int k, const TraceArgs &a, bool proxy, bool instr, bool bwd, int blocks, cudaStream_t s)
+int launch_k(int k, const TraceArgs &a, int form, bool instr, bool bwd, int blocks, cudaStream_t s)
 {
     switch (k) {
-    case 1: return trace_launch<1>(a, proxy, instr, bwd, blocks, s);
-    case 2: return trace_launch<2>(a, proxy, instr, bwd, blocks, s);
-    case 4: return trace_launch<4>(a, proxy, instr, bwd, blocks, s);
-    case 8: return trace_launch<8>(a, proxy, instr, bwd, blocks, s);
-    case 16: return trace_launch<16>(a, proxy, instr, bwd, blocks, s);
-    default: return trace_launch<32>(a, proxy, instr, bwd, blocks, s);
+    case 1: return trace_launch<1>(a, form, instr, bwd, blocks, s);
+    case 2: return trace_launch<2>(a, form, instr, bwd, blocks, s);
+    case 4: return trace_launch<4>(a, form, instr, bwd, blocks, s);
+    case 8: return trace_launch<8>(a, form, instr, bwd, blocks, s);
+    case 16: return trace_launch<16>(a, form, instr, bwd, blocks, s);
+    default: return trace_launch<32>(a, form, instr, bwd, blocks, s);
     }
 }
 
-int occupancy_k(int k, bool proxy, bool instr, bool bwd, int *bps)
+int occupancy_k(int k, int form, bool instr, bool bwd, int *bps)
 {
     switch (k) {
-    case 1: return trace_occupancy<1>(proxy, instr, bwd, bps);
-    case 2: return trace_occupancy<2>(proxy, instr, bwd, bps);
-    case 4: return trace_occupancy<4>(proxy, instr, bwd, bps);
-    case 8: return trace_occupancy<8>(proxy, instr, bwd, bps);
-    case 16: return trace_occupancy<16>(proxy, instr, bwd, bps);
-    default: return trace_occupancy<32>(proxy, instr, bwd, bps);
+    case 1: return trace_occupancy<1>(form, instr, bwd, bps);
+    case 2: return trace_occupancy<2>(form, instr, bwd, bps);
+    case 4: return trace_occupancy<4>(form, instr, bwd, bps);
+    case 8: return trace_occupancy<8>(form, instr, bwd, bps);
+    case 16: return trace_occupancy<16>(form, instr, bwd, bps);
+    default: return trace_occupancy<32>(form, instr, bwd, bps);
     }
 }
 
@@ -159,6 +159,8 @@ SceneRef grtx_scene_ref(const grtx_scene *sc)
     r.tris = sc->tris;
     r.app = sc->app;
     r.gid = sc->gid;
+    r.tpl_nodes = sc->tpl_nodes;
+    r.tpl_tris = sc->tpl_tris;
     r.app_stride = sc->app_stride;
     r.sh_degree = sc->sh_degree;
     r.has_tree = sc->n_valid > 0;
@@ -194,10 +196,10 @@ int setup(grtx_scene *sc, const grtx_camera *cam, const grtx_params *p, TraceArg
 
 int run(grtx_scene *sc, TraceArgs &a, int k, bool instr, bool bwd, unsigned *queue, cudaStream_t s)
 {
-    bool proxy = sc->form == GRTX_FORM_PROXY20;
+    int form = kernel_form(sc->form);
     bool single = a.traversal == GRTX_TRAVERSAL_SINGLE && !bwd;
     int bps = 0;
-    int occ = single ? trace_single_occupancy(proxy, instr, &bps) : occupancy_k(k, proxy, instr, bwd, &bps);
+    int occ = single ? trace_single_occupancy(form, instr, &bps) : occupancy_k(k, form, instr, bwd, &bps);
     if (occ != GRTX_OK || bps <= 0) return grtx_fail(GRTX_ERR_CUDA, "occupancy query failed");
     int blocks = sm_count() * bps;
     int n_slots = blocks * 128;
@@ -214,8 +216,8 @@ int run(grtx_scene *sc, TraceArgs &a, int k, bool instr, bool bwd, unsigned *que
     a.n_slots = n_slots;
     a.queue = queue;
     GRTX_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned), s));
-    int launched = single ? trace_single_launch(a, proxy, instr, blocks, s)
-                          : launch_k(k, a, proxy, instr, bwd, blocks, s);
+    int launched = single ? trace_single_launch(a, form, instr, blocks, s)
+                          : launch_k(k, a, form, instr, bwd, blocks, s);
     if (launched != GRTX_OK) {
         cudaError_t e = cudaGetLastError();
         return grtx_cuda_fail(e == cudaSuccess ? cudaErrorLaunchFailure : e, "trace launch");
@@ -287,7 +289,7 @@ extern "C" GRTX_API int grtx_trace_backward(grtx_scene *sc, const grtx_gaussians
     TraceArgs a = {};
     int st = setup(sc, cam, p, a);
     if (st) return st;
-    if (sc->form != GRTX_FORM_SPHERE) return grtx_fail(GRTX_ERR_INVALID_ARG, "backward needs a sphere-form scene");
+    if (sc->form == GRTX_FORM_PROXY20) return grtx_fail(GRTX_ERR_INVALID_ARG, "backward needs a sphere or icosphere scene");
     if (!g || g->n != sc->n || g->sh_degree != sc->sh_degree)
         return grtx_fail(GRTX_ERR_INVALID_ARG, "gaussians do not match the scene");
     if (sc->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits))

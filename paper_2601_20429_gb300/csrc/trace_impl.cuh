@@ -17,8 +17,14 @@ struct SceneRef {
     const float4 *tris;
     const float *app;
     const uint32_t *gid;
+    const float4 *tpl_nodes, *tpl_tris;   // icosphere forms: shared template BVH and triangles
     int app_stride, sh_degree, has_tree, pad;
 };
+
+// Leaf kinds of the trace kernels: one analytic unit sphere per Gaussian; one world-space
+// proxy triangle per leaf (monolithic); one Gaussian instance whose leaf test traverses the
+// shared icosphere template in unit-sphere space before the exact test.
+enum : int { FORM_SPHERE = 0, FORM_PROXY = 1, FORM_ICO = 2 };
 
 // A camera (rays generated in-kernel) or an explicit ray list.
 struct CamRef {
@@ -351,13 +357,65 @@ __device__ __forceinline__ float tri_hit(float4 v0, float4 v1, float4 v2, float3
     return (e2x * qx + e2y * qy + e2z * qz) * id;
 }
 
+// Leaf test of the instanced-icosphere forms (Sec. IV-A, second option): the ray in Gaussian
+// gi's unit-sphere space (o_l = A (o - mu), d_l = A d, so t is the world t) traverses the
+// shared template BVH; true at the first template triangle hit beyond t_near. The local ray
+// is scaled by 1 / (1 + 1e-5 + 4e-6 |o_l|), which inflates the template against the FP32
+// error of o_l without changing t, so that no exact hit is lost.
+template <bool INSTR>
+__device__ __forceinline__ bool template_touch(const SceneRef &sc, uint32_t gi, float3 o, float3 d, float tn,
+                                               Counters &cnt)
+{
+    const float4 *g = sc.geom + 4 * (size_t)gi;
+    float4 r0 = __ldg(g), r1 = __ldg(g + 1), r2 = __ldg(g + 2);
+    float rx = o.x - r0.w, ry = o.y - r1.w, rz = o.z - r2.w;
+    float3 ol = make_float3(r0.x * rx + r0.y * ry + r0.z * rz, r1.x * rx + r1.y * ry + r1.z * rz,
+                            r2.x * rx + r2.y * ry + r2.z * rz);
+    float sc_l = 1.0f / (1.0f + 1e-5f + 4e-6f * sqrtf(ol.x * ol.x + ol.y * ol.y + ol.z * ol.z));
+    ol = make_float3(ol.x * sc_l, ol.y * sc_l, ol.z * sc_l);
+    float3 dl = make_float3((r0.x * d.x + r0.y * d.y + r0.z * d.z) * sc_l, (r1.x * d.x + r1.y * d.y + r1.z * d.z) * sc_l,
+                            (r2.x * d.x + r2.y * d.y + r2.z * d.z) * sc_l);
+    float3 inv = make_float3(safe_rcp(dl.x), safe_rcp(dl.y), safe_rcp(dl.z));
+    uint32_t stack[16];
+    int sp = 0;
+    uint32_t ref = 0u;
+    for (;;) {
+        if (ref & GRTX_LEAF) {
+            if (INSTR) cnt.leaves++;
+            const float4 *tr = sc.tpl_tris + 3 * (size_t)(ref & ~GRTX_LEAF);
+            if (tri_hit(__ldg(tr), __ldg(tr + 1), __ldg(tr + 2), ol, dl) > tn) return true;
+        } else {
+            if (INSTR) cnt.nodes++;
+            const float4 *nd = sc.tpl_nodes + 4 * (size_t)ref;
+            float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+            float e0, x0, e1, x1;
+            slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, ol, inv, tn, GRTX_INF, e0, x0);
+            slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, ol, inv, tn, GRTX_INF, e1, x1);
+            bool h0 = e0 <= x0, h1 = e1 <= x1;
+            uint32_t c0 = __float_as_uint(n3.x), c1 = __float_as_uint(n3.y);
+            if (h0 && h1) {
+                bool near0 = e0 <= e1;
+                ref = near0 ? c0 : c1;
+                if (sp < 16) stack[sp++] = near0 ? c1 : c0;
+                continue;
+            }
+            if (h0 || h1) {
+                ref = h0 ? c0 : c1;
+                continue;
+            }
+        }
+        if (sp == 0) return false;
+        ref = stack[--sp];
+    }
+}
+
 // ------------------------------------------------------------------------------------------
 // One traversal round over keys in (L, t_max] (Sec. III-A). With ckpt, it starts from the
 // checkpoint source list (or the root in the first round), writes nodes failing the t_max
 // test to the destination list and rejected hits to the eviction list (Sec. IV-B);
 // otherwise it starts at the root and culls. Returns false when a capacity is exceeded.
 // ------------------------------------------------------------------------------------------
-template <int K, bool PROXY, bool INSTR>
+template <int K, int FORM, bool INSTR>
 __device__ __forceinline__ bool trace_round(const TraceArgs &a, const SceneRef &sc, float3 o, float3 d, float3 inv,
                                             float inv_len, float tn, float tf,
                                             float Lt, uint32_t Li, bool ckpt, bool from_root,
@@ -396,18 +454,19 @@ __device__ __forceinline__ bool trace_round(const TraceArgs &a, const SceneRef &
             if (INSTR) cnt.leaves++;
             uint32_t gi;
             bool touch = true;
-            if (PROXY) {
+            if (FORM == FORM_PROXY) {
                 const float4 *tr = sc.tris + 3 * (size_t)idx;
                 float4 v0 = __ldg(tr), v1 = __ldg(tr + 1), v2 = __ldg(tr + 2);
                 gi = __float_as_uint(v0.w);
                 touch = tri_hit(v0, v1, v2, o, d) > tn;
             } else {
                 gi = idx;
+                if (FORM == FORM_ICO) touch = template_touch<INSTR>(sc, gi, o, d, tn, cnt);
             }
             float t, D2, w[3];
             if (touch && sphere_test(sc.geom + 4 * (size_t)gi, o, d, t, D2, w)) {
                 if (D2 <= 1.0f && t > tn && t <= tf && key_after(t, gi, Lt, Li)) {
-                    if (!PROXY || !kb.contains(t, gi)) {
+                    if (FORM != FORM_PROXY || !kb.contains(t, gi)) {
                         float ct = t;
                         uint32_t ci = gi;
                         if (kb.insert(ct, ci) && ckpt) {       // any-hit: rejected -> eviction list
@@ -431,7 +490,7 @@ __device__ __forceinline__ bool trace_round(const TraceArgs &a, const SceneRef &
             bool h0 = e0 <= x0 && !(x0 < Lt);
             bool h1 = e1 <= x1 && !(x1 < Lt) && c1 != GRTX_NONE;
             bool near0 = e0 <= e1;
-            if (PROXY) {
+            if (FORM == FORM_PROXY) {
                 // a proxy face can lie up to one proxy diameter beyond the Gaussian's key, so
                 // the t_max test of a proxy subtree is taken at entry - (its largest diameter)
                 e0 = fmaf(-n3.z, inv_len, e0);
@@ -617,7 +676,7 @@ __device__ __forceinline__ void blend_one(const TraceArgs &a, const SceneRef &sc
 // ------------------------------------------------------------------------------------------
 // One ray: the round loop of Listing 1's raygen shader.
 // ------------------------------------------------------------------------------------------
-template <int K, bool PROXY, bool INSTR, bool BWD>
+template <int K, int FORM, bool INSTR, bool BWD>
 __device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc, float4 *__restrict__ out, int slot,
                                           int64_t pix, float3 o, float3 d, float tn, float tf, KBuf<K> &kb,
                                           Counters &cnt)
@@ -657,7 +716,7 @@ __device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc
                 uint32_t ci = v.y;
                 // the proxy form can find one Gaussian through several triangles, so an evicted
                 // copy may already be blended (key <= L) or already be in the buffer
-                if (PROXY && (!key_after(ct, ci, Lt, Li) || kb.contains(ct, ci))) continue;
+                if (FORM == FORM_PROXY && (!key_after(ct, ci, Lt, Li) || kb.contains(ct, ci))) continue;
                 if (kb.insert(ct, ci)) {
                     ev[(size_t)w * S] = make_uint2(__float_as_uint(ct), ci);
                     ++w;
@@ -666,7 +725,7 @@ __device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc
             n_ev = w;
         }
         int n_dst = 0;
-        if (!trace_round<K, PROXY, INSTR>(a, sc, o, d, inv, inv_len, tn, tf, Lt, Li, ckpt, from_root, src, n_src, dst, n_dst,
+        if (!trace_round<K, FORM, INSTR>(a, sc, o, d, inv, inv_len, tn, tf, Lt, Li, ckpt, from_root, src, n_src, dst, n_dst,
                                           ev, n_ev, kb, cnt)) {
             // a capacity was exceeded: redo this round from the root and stay in restart mode
             if (INSTR) cnt.fallbacks++;
@@ -675,7 +734,7 @@ __device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc
             n_src = 0;
             n_ev = 0;
             kb.clear();
-            trace_round<K, PROXY, INSTR>(a, sc, o, d, inv, inv_len, tn, tf, Lt, Li, false, true, src, 0, dst, n_dst, ev, n_ev,
+            trace_round<K, FORM, INSTR>(a, sc, o, d, inv, inv_len, tn, tf, Lt, Li, false, true, src, 0, dst, n_dst, ev, n_ev,
                                          kb, cnt);
         }
         for (int j = 0; j < kb.n; ++j) {
@@ -707,7 +766,7 @@ __device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc
 // memory per block allows 6; the backward keeps more live state and prefers 7).
 __host__ __device__ constexpr int trace_min_blocks(int k, bool bwd) { return k >= 32 ? 6 : (bwd ? 7 : 8); }
 
-template <int K, bool PROXY, bool INSTR, bool BWD>
+template <int K, int FORM, bool INSTR, bool BWD>
 __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, BWD)) k_trace(TraceArgs a)
 {
     __shared__ float s_kt[K * kBlock];
@@ -729,7 +788,7 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, BWD)) k_trace(Trac
         float tn, tf;
         if (make_ray(a.cam, base + lane, pix, o, d, tn, tf)) {
             ++rays;
-            trace_ray<K, PROXY, INSTR, BWD>(a, a.sc, a.rgbT, slot, pix, o, d, tn, tf, kb, cnt);
+            trace_ray<K, FORM, INSTR, BWD>(a, a.sc, a.rgbT, slot, pix, o, d, tn, tf, kb, cnt);
         }
         __syncwarp();
     }
@@ -776,34 +835,47 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, false)) k_serve(Tr
         float3 o, d;
         float tn, tf;
         if (make_ray(cam, item, pix, o, d, tn, tf))
-            trace_ray<K, false, false, false>(a, sc, sg.out, slot, pix, o, d, tn, tf, kb, cnt);
+            trace_ray<K, FORM_SPHERE, false, false>(a, sc, sg.out, slot, pix, o, d, tn, tf, kb, cnt);
         __syncwarp();
     }
 }
 
 // Launch helpers, instantiated per k in the trace_k*.cu units.
+// form: FORM_* of the scene. The backward always runs the sphere leaf test: the icosphere
+// forms hit exactly the Gaussians the sphere form hits, and the proxy form has no backward.
 template <int K>
-int trace_launch(const TraceArgs &a, bool proxy, bool instr, bool bwd, int blocks, cudaStream_t s)
+int trace_launch(const TraceArgs &a, int form, bool instr, bool bwd, int blocks, cudaStream_t s)
 {
     dim3 g(blocks), b(128);
-    if (bwd) k_trace<K, false, false, true><<<g, b, 0, s>>>(a);
-    else if (proxy && instr) k_trace<K, true, true, false><<<g, b, 0, s>>>(a);
-    else if (proxy) k_trace<K, true, false, false><<<g, b, 0, s>>>(a);
-    else if (instr) k_trace<K, false, true, false><<<g, b, 0, s>>>(a);
-    else k_trace<K, false, false, false><<<g, b, 0, s>>>(a);
+    if (bwd) k_trace<K, FORM_SPHERE, false, true><<<g, b, 0, s>>>(a);
+    else if (form == FORM_PROXY && instr) k_trace<K, FORM_PROXY, true, false><<<g, b, 0, s>>>(a);
+    else if (form == FORM_PROXY) k_trace<K, FORM_PROXY, false, false><<<g, b, 0, s>>>(a);
+    else if (form == FORM_ICO && instr) k_trace<K, FORM_ICO, true, false><<<g, b, 0, s>>>(a);
+    else if (form == FORM_ICO) k_trace<K, FORM_ICO, false, false><<<g, b, 0, s>>>(a);
+    else if (instr) k_trace<K, FORM_SPHERE, true, false><<<g, b, 0, s>>>(a);
+    else k_trace<K, FORM_SPHERE, false, false><<<g, b, 0, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? GRTX_OK : GRTX_ERR_CUDA;
 }
 
 template <int K>
-int trace_occupancy(bool proxy, bool instr, bool bwd, int *blocks_per_sm)
+int trace_occupancy(int form, bool instr, bool bwd, int *blocks_per_sm)
 {
     cudaError_t e;
-    if (bwd) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, false, false, true>, 128, 0);
-    else if (proxy && instr) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, true, true, false>, 128, 0);
-    else if (proxy) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, true, false, false>, 128, 0);
-    else if (instr) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, false, true, false>, 128, 0);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, false, false, false>, 128, 0);
+    if (bwd) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_SPHERE, false, true>, 128, 0);
+    else if (form == FORM_PROXY && instr) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_PROXY, true, false>, 128, 0);
+    else if (form == FORM_PROXY) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_PROXY, false, false>, 128, 0);
+    else if (form == FORM_ICO && instr) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_ICO, true, false>, 128, 0);
+    else if (form == FORM_ICO) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_ICO, false, false>, 128, 0);
+    else if (instr) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_SPHERE, true, false>, 128, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_SPHERE, false, false>, 128, 0);
     return e == cudaSuccess ? GRTX_OK : GRTX_ERR_CUDA;
+}
+
+// Kernel leaf kind of a scene form.
+inline int kernel_form(int scene_form)
+{
+    return scene_form == GRTX_FORM_PROXY20 ? FORM_PROXY
+           : (scene_form == GRTX_FORM_ICO20 || scene_form == GRTX_FORM_ICO80) ? FORM_ICO : FORM_SPHERE;
 }
 
 template <int K>
@@ -821,7 +893,7 @@ int serve_occupancy(int *blocks_per_sm)
 }
 
 #define GRTX_INSTANTIATE_TRACE(K)                                                                  \
-    template int trace_launch<K>(const TraceArgs &, bool, bool, bool, int, cudaStream_t);         \
-    template int trace_occupancy<K>(bool, bool, bool, int *);                                       \
+    template int trace_launch<K>(const TraceArgs &, int, bool, bool, int, cudaStream_t);          \
+    template int trace_occupancy<K>(int, bool, bool, int *);                                        \
     template int serve_launch<K>(const TraceArgs &, const ServeSeg *, int, int, cudaStream_t);     \
     template int serve_occupancy<K>(int *);

@@ -15,8 +15,8 @@
 #include "trace_impl.cuh"
 
 #define GRTX_EXTERN_NOALLOC(K)                                                                   \
-    extern template int trace_launch<K>(const TraceArgs &, bool, bool, bool, int, cudaStream_t); \
-    extern template int trace_occupancy<K>(bool, bool, bool, int *);
+    extern template int trace_launch<K>(const TraceArgs &, int, bool, bool, int, cudaStream_t); \
+    extern template int trace_occupancy<K>(int, bool, bool, int *);
 GRTX_EXTERN_NOALLOC(1)
 GRTX_EXTERN_NOALLOC(2)
 GRTX_EXTERN_NOALLOC(4)
@@ -61,27 +61,27 @@ int scratch_for_current_device(unsigned char **out, int *sms)
     return GRTX_OK;
 }
 
-int launch_noalloc(int k, const TraceArgs &a, bool proxy, int blocks, cudaStream_t s)
+int launch_noalloc(int k, const TraceArgs &a, int form, int blocks, cudaStream_t s)
 {
     switch (k) {
-    case 1: return trace_launch<1>(a, proxy, false, false, blocks, s);
-    case 2: return trace_launch<2>(a, proxy, false, false, blocks, s);
-    case 4: return trace_launch<4>(a, proxy, false, false, blocks, s);
-    case 8: return trace_launch<8>(a, proxy, false, false, blocks, s);
-    case 16: return trace_launch<16>(a, proxy, false, false, blocks, s);
-    default: return trace_launch<32>(a, proxy, false, false, blocks, s);
+    case 1: return trace_launch<1>(a, form, false, false, blocks, s);
+    case 2: return trace_launch<2>(a, form, false, false, blocks, s);
+    case 4: return trace_launch<4>(a, form, false, false, blocks, s);
+    case 8: return trace_launch<8>(a, form, false, false, blocks, s);
+    case 16: return trace_launch<16>(a, form, false, false, blocks, s);
+    default: return trace_launch<32>(a, form, false, false, blocks, s);
     }
 }
 
-int occupancy_noalloc(int k, bool proxy, int *bps)
+int occupancy_noalloc(int k, int form, int *bps)
 {
     switch (k) {
-    case 1: return trace_occupancy<1>(proxy, false, false, bps);
-    case 2: return trace_occupancy<2>(proxy, false, false, bps);
-    case 4: return trace_occupancy<4>(proxy, false, false, bps);
-    case 8: return trace_occupancy<8>(proxy, false, false, bps);
-    case 16: return trace_occupancy<16>(proxy, false, false, bps);
-    default: return trace_occupancy<32>(proxy, false, false, bps);
+    case 1: return trace_occupancy<1>(form, false, false, bps);
+    case 2: return trace_occupancy<2>(form, false, false, bps);
+    case 4: return trace_occupancy<4>(form, false, false, bps);
+    case 8: return trace_occupancy<8>(form, false, false, bps);
+    case 16: return trace_occupancy<16>(form, false, false, bps);
+    default: return trace_occupancy<32>(form, false, false, bps);
     }
 }
 
@@ -101,7 +101,7 @@ extern "C" GRTX_API int grtx_trace_forward_noalloc(grtx_scene *sc, const grtx_ca
     TraceArgs a = {};
     st = grtx_fill_camera(a.cam, a.n_items, cam);
     if (st) return st;
-    bool proxy = sc->form == GRTX_FORM_PROXY20;
+    int form = kernel_form(sc->form);
     a.sc = grtx_scene_ref(sc);
     a.traversal = p->traversal;
     a.T_min = p->T_min;
@@ -126,7 +126,7 @@ extern "C" GRTX_API int grtx_trace_forward_noalloc(grtx_scene *sc, const grtx_ca
     st = scratch_for_current_device(&base, &sms);
     if (st) return st;
     int bps = 0;
-    if (occupancy_noalloc(p->k, proxy, &bps) != GRTX_OK || bps <= 0)
+    if (occupancy_noalloc(p->k, form, &bps) != GRTX_OK || bps <= 0)
         return grtx_fail(GRTX_ERR_CUDA, "occupancy query failed");
     int blocks = (int)std::min<size_t>((size_t)sms * bps, room / per_block);
     int n_slots = blocks * 128;
@@ -139,7 +139,7 @@ extern "C" GRTX_API int grtx_trace_forward_noalloc(grtx_scene *sc, const grtx_ca
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     // the counter must start at zero; the lists are always written before they are read
     GRTX_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned), s));
-    if (launch_noalloc(p->k, a, proxy, blocks, s) != GRTX_OK) {
+    if (launch_noalloc(p->k, a, form, blocks, s) != GRTX_OK) {
         cudaError_t e = cudaGetLastError();
         return grtx_cuda_fail(e == cudaSuccess ? cudaErrorLaunchFailure : e, "trace launch");
     }

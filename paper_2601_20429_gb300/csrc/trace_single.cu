@@ -51,7 +51,7 @@ __device__ __forceinline__ void heap_sift_down(uint2 *__restrict__ h, size_t S, 
 
 // Every hit of the ray, appended to list (stride S). Returns the count, or -1 when the
 // capacity is exceeded.
-template <bool PROXY, bool INSTR>
+template <int FORM, bool INSTR>
 __device__ __forceinline__ int collect_hits(const TraceArgs &a, const SceneRef &sc, float3 o, float3 d, float3 inv,
                                             float tn, float tf, uint2 *__restrict__ list, Counters &cnt,
                                             unsigned &collected)
@@ -66,13 +66,14 @@ __device__ __forceinline__ int collect_hits(const TraceArgs &a, const SceneRef &
             if (INSTR) cnt.leaves++;
             uint32_t gi;
             bool touch = true;
-            if (PROXY) {
+            if (FORM == FORM_PROXY) {
                 const float4 *tr = sc.tris + 3 * (size_t)idx;
                 float4 v0 = __ldg(tr), v1 = __ldg(tr + 1), v2 = __ldg(tr + 2);
                 gi = __float_as_uint(v0.w);
                 touch = tri_hit(v0, v1, v2, o, d) > tn;
             } else {
                 gi = idx;
+                if (FORM == FORM_ICO) touch = template_touch<INSTR>(sc, gi, o, d, tn, cnt);
             }
             float t, D2, w[3];
             if (touch && sphere_test(sc.geom + 4 * (size_t)gi, o, d, t, D2, w) && D2 <= 1.0f && t > tn && t <= tf) {
@@ -109,7 +110,7 @@ __device__ __forceinline__ int collect_hits(const TraceArgs &a, const SceneRef &
     return n;
 }
 
-template <bool PROXY, bool INSTR>
+template <int FORM, bool INSTR>
 __device__ __forceinline__ void single_ray(const TraceArgs &a, const SceneRef &sc, int slot, int64_t pix, float3 o,
                                            float3 d, float tn, float tf, KBuf<kFallbackK> &kb, Counters &cnt,
                                            unsigned &collected)
@@ -122,10 +123,10 @@ __device__ __forceinline__ void single_ray(const TraceArgs &a, const SceneRef &s
     int n = 0;
     if (sc.has_tree) {
         if (INSTR) cnt.rounds++;
-        n = collect_hits<PROXY, INSTR>(a, sc, o, d, inv, tn, tf, list, cnt, collected);
+        n = collect_hits<FORM, INSTR>(a, sc, o, d, inv, tn, tf, list, cnt, collected);
         if (n < 0) {                  // more hits than the list holds: k-buffer rounds instead
             if (INSTR) cnt.fallbacks++;
-            trace_ray<kFallbackK, PROXY, INSTR, false>(a, sc, a.rgbT, slot, pix, o, d, tn, tf, kb, cnt);
+            trace_ray<kFallbackK, FORM, INSTR, false>(a, sc, a.rgbT, slot, pix, o, d, tn, tf, kb, cnt);
             return;
         }
     }
@@ -143,7 +144,7 @@ __device__ __forceinline__ void single_ray(const TraceArgs &a, const SceneRef &s
             heap_sift_down(list, S, 0, n);
         }
         uint64_t key = single_key(top);
-        if (PROXY && key == prev) continue;     // one Gaussian found through several triangles
+        if (FORM == FORM_PROXY && key == prev) continue;   // one Gaussian found through several triangles
         prev = key;
         uint32_t idx = top.y;
         blend_one<false>(a, sc, st, idx, o, d, dn);
@@ -158,7 +159,7 @@ __device__ __forceinline__ void single_ray(const TraceArgs &a, const SceneRef &s
     if (INSTR && a.n_blended) a.n_blended[pix] = nb;
 }
 
-template <bool PROXY, bool INSTR>
+template <int FORM, bool INSTR>
 __global__ void __launch_bounds__(kBlock, 8) k_trace_single(TraceArgs a)
 {
     __shared__ float s_kt[kFallbackK * kBlock];
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(kBlock, 8) k_trace_single(TraceArgs a)
         float tn, tf;
         if (make_ray(a.cam, base + lane, pix, o, d, tn, tf)) {
             ++rays;
-            single_ray<PROXY, INSTR>(a, a.sc, slot, pix, o, d, tn, tf, kb, cnt, collected);
+            single_ray<FORM, INSTR>(a, a.sc, slot, pix, o, d, tn, tf, kb, cnt, collected);
         }
         __syncwarp();
     }
@@ -198,22 +199,28 @@ __global__ void __launch_bounds__(kBlock, 8) k_trace_single(TraceArgs a)
 
 }  // namespace
 
-int trace_single_launch(const TraceArgs &a, bool proxy, bool instr, int blocks, cudaStream_t s)
+int trace_single_launch(const TraceArgs &a, int form, bool instr, int blocks, cudaStream_t s)
 {
     dim3 g(blocks), b(kBlock);
-    if (proxy && instr) k_trace_single<true, true><<<g, b, 0, s>>>(a);
-    else if (proxy) k_trace_single<true, false><<<g, b, 0, s>>>(a);
-    else if (instr) k_trace_single<false, true><<<g, b, 0, s>>>(a);
-    else k_trace_single<false, false><<<g, b, 0, s>>>(a);
+    if (form == FORM_PROXY && instr) k_trace_single<FORM_PROXY, true><<<g, b, 0, s>>>(a);
+    else if (form == FORM_PROXY) k_trace_single<FORM_PROXY, false><<<g, b, 0, s>>>(a);
+    else if (form == FORM_ICO && instr) k_trace_single<FORM_ICO, true><<<g, b, 0, s>>>(a);
+    else if (form == FORM_ICO) k_trace_single<FORM_ICO, false><<<g, b, 0, s>>>(a);
+    else if (instr) k_trace_single<FORM_SPHERE, true><<<g, b, 0, s>>>(a);
+    else k_trace_single<FORM_SPHERE, false><<<g, b, 0, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? GRTX_OK : GRTX_ERR_CUDA;
 }
 
-int trace_single_occupancy(bool proxy, bool instr, int *blocks_per_sm)
+template <int FORM, bool INSTR>
+static int single_occ(int *bps)
 {
-    cudaError_t e;
-    if (proxy && instr) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace_single<true, true>, kBlock, 0);
-    else if (proxy) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace_single<true, false>, kBlock, 0);
-    else if (instr) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace_single<false, true>, kBlock, 0);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace_single<false, false>, kBlock, 0);
-    return e == cudaSuccess ? GRTX_OK : GRTX_ERR_CUDA;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_trace_single<FORM, INSTR>, kBlock, 0) == cudaSuccess
+               ? GRTX_OK : GRTX_ERR_CUDA;
+}
+
+int trace_single_occupancy(int form, bool instr, int *blocks_per_sm)
+{
+    if (form == FORM_PROXY) return instr ? single_occ<FORM_PROXY, true>(blocks_per_sm) : single_occ<FORM_PROXY, false>(blocks_per_sm);
+    if (form == FORM_ICO) return instr ? single_occ<FORM_ICO, true>(blocks_per_sm) : single_occ<FORM_ICO, false>(blocks_per_sm);
+    return instr ? single_occ<FORM_SPHERE, true>(blocks_per_sm) : single_occ<FORM_SPHERE, false>(blocks_per_sm);
 }

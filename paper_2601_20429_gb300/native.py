@@ -131,6 +131,11 @@ class grtx_mirror(C.Structure):
                 ("t_near_secondary", C.c_float), ("reserved", C.c_float)]
 
 
+class grtx_glass(C.Structure):
+    _fields_ = [("center", C.c_float * 3), ("radius", C.c_float), ("ior", C.c_float),
+                ("t_near_secondary", C.c_float), ("reserved", C.c_float * 2)]
+
+
 class grtx_request(C.Structure):
     _fields_ = [("scene_id", C.c_int32), ("reserved", C.c_int32), ("cam", grtx_camera), ("d_rgbT", _fp),
                 ("tag", C.c_uint64)]
@@ -162,6 +167,9 @@ _SIGS = {
     "grtx_trace_backward": (C.c_int, [_fp, C.POINTER(grtx_gaussians), C.POINTER(grtx_camera), C.POINTER(grtx_params),
                                       _fp, _fp, C.POINTER(grtx_grads), _fp]),
     "grtx_mirror_rays": (C.c_int, [C.POINTER(grtx_camera), C.POINTER(grtx_mirror)] + [_fp] * 11),
+    "grtx_template_mesh": (C.c_int, [C.c_int, _fp, C.POINTER(C.c_int)]),
+    "grtx_secondary_rays": (C.c_int, [C.POINTER(grtx_camera), C.POINTER(grtx_mirror), C.c_int, C.POINTER(grtx_glass),
+                                      C.c_int] + [_fp] * 11),
     "grtx_composite_bounce": (C.c_int, [_fp, _fp, _fp, _fp, C.c_int64, C.POINTER(C.c_float * 3), _fp]),
     "grtx_trace_forward_noalloc": (C.c_int, [_fp, C.POINTER(grtx_camera), C.POINTER(grtx_params), _fp, _fp]),
     "grtx_server_create": (C.c_int, [C.POINTER(_fp), C.c_int, C.POINTER(grtx_params), C.c_int64, C.c_int, _fp,
@@ -360,6 +368,33 @@ def make_mirror(m: dict) -> grtx_mirror:
             arr[i] = float(m[name][i])
     g.half_u, g.half_v, g.t_near_secondary = float(m["half_u"]), float(m["half_v"]), float(m["t_near_secondary"])
     return g
+
+
+def template_mesh(form: int):
+    """Triangles [n][3][3] of the shared icosphere template of form 2 (ICO20) or 3 (ICO80)."""
+    import numpy as np
+    n = C.c_int(0)
+    check(lib().grtx_template_mesh(int(form), None, C.byref(n)), "grtx_template_mesh")
+    out = np.empty((n.value, 3, 3), dtype=np.float32)
+    check(lib().grtx_template_mesh(int(form), out.ctypes.data, C.byref(n)), "grtx_template_mesh")
+    return out
+
+
+def make_glass(gl: dict) -> grtx_glass:
+    g = grtx_glass()
+    for i in range(3):
+        g.center[i] = gl["center"][i]
+    g.radius, g.ior, g.t_near_secondary = gl["radius"], gl["ior"], gl["t_near_secondary"]
+    return g
+
+
+def grtx_secondary_rays(cam: grtx_camera, mirrors, glass, prim, sec, sec_pixel, n_sec, stream=None):
+    """mirrors / glass: lists of grtx_mirror / grtx_glass; prim, sec: (origins, dirs, tnear, tfar)."""
+    ma = (grtx_mirror * max(len(mirrors), 1))(*mirrors)
+    ga = (grtx_glass * max(len(glass), 1))(*glass)
+    check(lib().grtx_secondary_rays(C.byref(cam), ma, len(mirrors), ga, len(glass), *[ptr(t) for t in prim],
+                                    *[ptr(t) for t in sec], ptr(sec_pixel), ptr(n_sec), stream_handle(stream)),
+          "grtx_secondary_rays")
 
 
 def grtx_mirror_rays(cam: grtx_camera, mirror: grtx_mirror, prim, sec, sec_pixel, n_sec, stream=None):

@@ -9,7 +9,7 @@ import torch
 
 from . import native as N
 
-FORMS = {"sphere": 0, "proxy20": 1}
+FORMS = {"sphere": 0, "proxy20": 1, "ico20": 2, "ico80": 3}
 TRAVERSALS = {"checkpoint": 0, "restart": 1, "single": 2}
 
 
@@ -27,8 +27,10 @@ def params_to_device(g, device="cuda"):
 class Scene:
     """A built acceleration structure (library-owned) for one set of Gaussians.
 
-    form: "sphere" (one unit-sphere instance per Gaussian, Sec. IV-A) or "proxy20" (20
-    triangles per Gaussian in one monolithic BVH, the baseline of Sec. III-C)."""
+    form: "sphere" (one unit-sphere instance per Gaussian, Sec. IV-A), "ico20" / "ico80" (the
+    same instances over a shared 20- / 80-triangle icosphere template, Sec. IV-A's second
+    option) or "proxy20" (20 triangles per Gaussian in one monolithic BVH, the baseline of
+    Sec. III-C)."""
 
     def __init__(self, means, log_scales, quats, logits, sh, sh_degree: int, form: str = "sphere",
                  alpha_min: float = 0.01, stream=None, bvh_codes: str = "sized"):

@@ -322,6 +322,21 @@ def outdoor_mirror(seed: int = 2, cam_pos=(0.0, 1.7, 0.0), view=(1.0, 0.0, 0.0))
                 half_v=1.5, t_near_secondary=1e-3)
 
 
+def outdoor_glass(seed: int = 2, cam_pos=(0.0, 1.7, 0.0), view=(1.0, 0.0, 0.0)) -> dict:
+    """A glass ball (index 1.5) at a seeded place in front of the camera: radius 0.5-1.5 m,
+    centre 6-12 m away within +-30 degrees of the view direction, resting 0-0.5 m above the
+    ground."""
+    rng = np.random.default_rng(seed + 2000)
+    yaw = math.radians(rng.uniform(-30.0, 30.0))
+    dist = rng.uniform(6.0, 12.0)
+    radius = rng.uniform(0.5, 1.5)
+    v = np.asarray(view, dtype=np.float64)
+    side = np.cross(v, [0.0, 1.0, 0.0])
+    center = np.asarray(cam_pos, dtype=np.float64) + dist * (math.cos(yaw) * v + math.sin(yaw) * side)
+    center[1] = radius + rng.uniform(0.0, 0.5)
+    return dict(center=tuple(float(x) for x in center), radius=float(radius), ior=1.5, t_near_secondary=1e-3)
+
+
 def config_outdoor(n: int = 6_000_000, width: int = 1920, height: int = 1080):
     """6M-Gaussian outdoor-like scene (seed 2), equidistant fisheye at (0, 1.7, 0) looking
     along +x with 90 degrees at half the width, one mirror bounce; k = 16 and 32."""

@@ -263,6 +263,41 @@ def test_forward_dense_parity_both_traversals(dense, k):
     assert (ref["n_blend"] < ref["n_hits"]).sum() > 100       # early termination is exercised
 
 
+# ------------------------------------------------------------------ instanced icosphere forms
+
+
+@pytest.mark.parametrize("form", ["ico20", "ico80"])
+@pytest.mark.parametrize("traversal", ["checkpoint", "restart", "single"])
+def test_icosphere_forms_parity(dense, form, traversal):
+    """Sec. IV-A's second option: the instance BVH over a shared template mesh. The template
+    only filters, the exact test decides, so the image is the definition's (oracle) and the
+    sphere form's blend lists; the template traversal adds node and triangle fetches."""
+    g, cam, S, rays, ref = dense
+    res = _gpu_render(g, cam, form=form, k=8, traversal=traversal, ids_cap=256)
+    _check_image(res, ref, S, rays)
+    sph = _gpu_render(g, cam, form="sphere", k=8, traversal=traversal, ids_cap=256)
+    np.testing.assert_array_equal(res["ids"], sph["ids"])
+    np.testing.assert_allclose(res["rgbT"], sph["rgbT"], rtol=0, atol=1e-6)
+    assert res["stats"]["rounds"] == sph["stats"]["rounds"]
+    assert res["stats"]["nodes"] > sph["stats"]["nodes"] and res["stats"]["leaves"] > sph["stats"]["leaves"]
+    assert res["stats"]["fallbacks"] == 0
+
+
+def test_icosphere_scene_backward_equals_sphere_scene():
+    g, _ = _dense()
+    g = g.subset(np.arange(2000))
+    cam = scenes.pinhole_camera(16, 16, (0.0, 0.0, -3.0), (0, 0, 0), 45.0)
+    w = torch.from_numpy(np.random.default_rng(3).normal(0, 1, (256, 4)).astype(np.float32)).cuda()
+    out = {}
+    for form in ("sphere", "ico80"):
+        sc = R.Scene.from_params(g, form=form)
+        fwd = R.render(sc, cam, k=8)["rgbT"]
+        out[form] = {k: v.cpu().numpy() for k, v in R.backward(sc, cam, fwd, w, k=8).items()}
+        sc.close()
+    for name in out["sphere"]:
+        np.testing.assert_allclose(out["ico80"][name], out["sphere"][name], rtol=1e-5, atol=1e-6)
+
+
 # ------------------------------------------------------------------ single-round traversal
 
 

@@ -618,3 +618,92 @@ def test_mirror_misses_outside_the_rectangle_and_keeps_background():
     out = O.composite_bounce(rgbT, sec_rgbT, spix, bg=(0.2, 0.2, 0.2))
     np.testing.assert_allclose(out[12], [0.1 - 0.1 + 0.2, 0.2 - 0.1 + 0.2, 0.3 - 0.1 + 0.2, 0.125])
     np.testing.assert_array_equal(out[:12], rgbT[:12])
+
+
+# ---------------------------------------------------------------- glass-ball refraction
+
+
+def _ball(r=1.0, ior=1.5, center=(0.0, 0.0, 0.0)):
+    return dict(center=center, radius=r, ior=ior, t_near_secondary=1e-4)
+
+
+def test_glass_axis_ray_passes_undeviated():
+    cam = scenes.pinhole_camera(1, 1, (0.0, 0.0, -5.0), (0, 0, 0), 10.0)
+    prim, sec, spix = O.secondary_rays(cam, glass=[_ball()])
+    assert list(spix) == [0]
+    assert prim[3][0] == pytest.approx(4.0, abs=1e-12)
+    np.testing.assert_allclose(sec[0][0], [0, 0, 1], atol=1e-12)
+    np.testing.assert_allclose(sec[1][0], [0, 0, 1], atol=1e-12)
+    assert sec[2][0] == 1e-4 and np.isinf(sec[3][0])
+
+
+def test_glass_deviation_is_the_ball_lens_formula():
+    """A ray at impact parameter b leaves the ball turned by 2 (theta_i - theta_t) with
+    sin theta_i = b / R and sin theta_i = n sin theta_t, in the plane of the ray and the
+    centre, from a point on the sphere."""
+    R, n = 1.3, 1.52
+    cam = scenes.pinhole_camera(15, 15, (0.2, -0.1, -6.0), (0, 0, 0), 30.0)
+    prim, sec, spix = O.secondary_rays(cam, glass=[_ball(R, n)])
+    assert len(spix) > 50
+    c = np.zeros(3)
+    for j, p in enumerate(spix):
+        o, u = prim[0][p], prim[1][p] / np.linalg.norm(prim[1][p])
+        b = np.linalg.norm(np.cross(c - o, u))
+        ti = math.asin(b / R)
+        tt = math.asin(math.sin(ti) / n)
+        w = sec[1][j]
+        assert np.linalg.norm(w) == pytest.approx(1.0, abs=1e-12)
+        dev = math.acos(min(1.0, float(np.dot(u, w))))
+        assert dev == pytest.approx(2 * (ti - tt), abs=1e-9)
+        assert abs(np.dot(w, np.cross(c - o, u))) <= 1e-9                 # coplanar
+        assert np.linalg.norm(sec[0][j] - c) == pytest.approx(R, abs=1e-12)
+        # the primary stops on the near surface
+        hit = o + prim[3][p] * prim[1][p]
+        assert np.linalg.norm(hit - c) == pytest.approx(R, abs=1e-12)
+
+
+def test_glass_of_index_one_continues_the_ray():
+    cam = scenes.pinhole_camera(7, 7, (0.0, 0.3, -4.0), (0, 0, 0), 25.0)
+    prim, sec, spix = O.secondary_rays(cam, glass=[_ball(1.0, 1.0)])
+    assert len(spix) > 10
+    for j, p in enumerate(spix):
+        o, d = prim[0][p], prim[1][p]
+        u = d / np.linalg.norm(d)
+        np.testing.assert_allclose(sec[1][j], u, atol=1e-12)
+        # the exit is the far root of |o + t u| = 1
+        b = np.dot(o, u)
+        t_far = -b + math.sqrt(b * b - (np.dot(o, o) - 1.0))
+        np.testing.assert_allclose(sec[0][j], o + t_far * u, atol=1e-12)
+
+
+def test_secondary_takes_the_nearest_object_and_none_from_inside():
+    cam = scenes.pinhole_camera(9, 9, (0.0, 0.0, -5.0), (0, 0, 0), 20.0)
+    front = dict(_facing_mirror(), center=(0.0, 0.0, -2.0), half_u=10.0, half_v=10.0)
+    prim, sec, spix = O.secondary_rays(cam, mirrors=[front], glass=[_ball()])
+    assert len(spix) == 81                                              # the mirror hides the ball
+    np.testing.assert_allclose(prim[3], 3.0 / prim[1][:, 2], rtol=1e-12)
+    np.testing.assert_allclose(sec[1][:, 2], -prim[1][:, 2])
+    back = dict(front, center=(0.0, 0.0, 3.0))
+    prim, sec, spix = O.secondary_rays(cam, mirrors=[back], glass=[_ball()])
+    assert len(spix) == 81
+    through = prim[3] < 6.0                                             # stopped on the ball
+    assert 0 < through.sum() < 81
+    assert np.all(np.abs(prim[3][~through] - 8.0 / prim[1][~through, 2]) < 1e-9)
+    inside = scenes.pinhole_camera(5, 5, (0.0, 0.0, 0.2), (0, 0, 1.0), 40.0)
+    prim, sec, spix = O.secondary_rays(inside, glass=[_ball()])
+    assert len(spix) == 0 and np.isinf(prim[3]).all()
+
+
+def test_glass_shows_the_gaussian_behind_it():
+    """A Gaussian on the axis behind the ball is seen through it along the undeviated axis
+    ray: the pixel is the Gaussian's alpha times its colour."""
+    a, col = 0.7, np.array([0.2, 0.8, 0.4])
+    S = make_scene([[0, 0, 3.0]], 0.05, [1, 0, 0, 0], a, col)
+    cam = scenes.pinhole_camera(1, 1, (0.0, 0.0, -5.0), (0, 0, 0), 10.0)
+    prim, sec, spix = O.secondary_rays(cam, glass=[_ball()])
+    p = S.render(prim)["out"]
+    s = S.render(sec)["out"]
+    assert p[0, 3] == 1.0                                  # nothing before the ball
+    out = O.composite_bounce(p, s, spix)
+    np.testing.assert_allclose(out[0, :3], a * col, rtol=1e-12)
+    assert out[0, 3] == pytest.approx(1 - a, rel=1e-12)
