@@ -411,6 +411,74 @@ def bench_differentiable(steps: int, warmup: int, stream):
             "step": "BVH build + forward + backward (atomics into all five parameter tensors)"}
 
 
+def _quat_mul(a, b):
+    w1, x1, y1, z1 = a
+    w2, x2, y2, z2 = b.T
+    return np.stack([w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2, w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+                     w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2, w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2], 1)
+
+
+def bench_world(steps: int, stream, flush):
+    """Multi-level instancing (Sec. VI): two surface objects (0.5M and 1M Gaussians) placed
+    four times each around a ring (rotation, uniform scale, translation), 1920x1080, k = 16,
+    against the same 6M Gaussians baked into one flat scene (colours aside: the SH are not
+    rotated in the baked copy, which leaves the traversal work unchanged)."""
+    import math
+    import torch
+    from paper_2601_20429_gb300 import native as N
+    from paper_2601_20429_gb300 import render as R
+    from paper_2601_20429_gb300 import scenes
+    objs = [scenes.surface_scene(n=500_000, seed=20, extent=1.0), scenes.surface_scene(n=1_000_000, seed=21, extent=1.0)]
+    gsc = [R.Scene.from_params(g) for g in objs]
+    rng = np.random.default_rng(22)
+    placements, flat = [], []
+    for j in range(8):
+        ang = 2 * math.pi * j / 8
+        ax = rng.normal(size=3)
+        ax /= np.linalg.norm(ax)
+        th = rng.uniform(0, math.pi)
+        q = np.array([math.cos(th / 2), *(math.sin(th / 2) * ax)])
+        w, x, y, z = q
+        Rm = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                       [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                       [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+        sc_ = rng.uniform(0.8, 1.2)
+        c = np.array([3.0 * math.cos(ang), 0.3 * rng.normal(), 3.0 * math.sin(ang)])
+        i = j % 2
+        placements.append((gsc[i], np.concatenate([sc_ * Rm, c[:, None]], 1)))
+        g = objs[i]
+        flat.append(scenes.GaussianParams((g.means @ (sc_ * Rm).T + c).astype(np.float32),
+                                          (g.log_scales + math.log(sc_)).astype(np.float32),
+                                          _quat_mul(q, g.quats.astype(np.float64)).astype(np.float32),
+                                          g.logits, g.sh, g.sh_degree, {}))
+    world = R.World(placements)
+    cat = lambda name: np.concatenate([getattr(f, name) for f in flat])
+    gflat = scenes.GaussianParams(cat("means"), cat("log_scales"), cat("quats"), cat("logits"), cat("sh"), 3, {})
+    del flat
+    t0 = time.perf_counter()
+    scflat = R.Scene.from_params(gflat)
+    torch.cuda.synchronize()
+    flat_build_ms = (time.perf_counter() - t0) * 1e3
+    cam = scenes.pinhole_camera(1920, 1080, (0.0, 2.5, -9.0), (0.0, 0.0, 0.0), 50.0)
+    n = 1920 * 1080
+    out = torch.empty((n, 4), device="cuda")
+    st_w = N.stats_dict(R.render_world(world, cam, k=16, out=out, want_stats=True)["stats"])
+    tw = time_frames(lambda: R.render_world(world, cam, k=16, out=out), steps, 2, flush, stream)
+    st_f = N.stats_dict(R.render(scflat, cam, k=16, out=out, want_stats=True)["stats"])
+    tf = time_frames(lambda: R.render(scflat, cam, k=16, out=out), steps, 2, flush, stream)
+    res = {"workload": "8 placements of two surface objects (0.5M + 1M Gaussians stored, 6M placed), "
+                       "1920x1080 pinhole, k=16",
+           "world": {"Mrays_per_s": mrays(n, tw), "ms_per_frame": statistics.mean(tw),
+                     "nodes_per_ray": nodes_per_ray(st_w), "gaussians_stored": sum(g.n for g in objs)},
+           "flat": {"Mrays_per_s": mrays(n, tf), "ms_per_frame": statistics.mean(tf),
+                    "nodes_per_ray": nodes_per_ray(st_f), "gaussians_stored": gflat.n, "build_ms": flat_build_ms}}
+    world.close()
+    scflat.close()
+    for s_ in gsc:
+        s_.close()
+    return res
+
+
 def bench_outdoor(steps: int, stream, flush):
     """6M-Gaussian outdoor scene, 1920x1080 fisheye plus one bounce off a mirror or through a
     glass ball: primary and secondary rays timed separately (explicit ray lists), k = 16."""
@@ -571,6 +639,7 @@ def main():
     differentiable = outdoor = ablations = None
     if dist.world == 1 and not args.no_extra:
         ablations = bench_surface_ablations(g, sc, cam, k, max(3, args.steps // 4), stream, flush)
+        ablations["instancing"] = bench_world(max(3, args.steps // 4), stream, flush)
         differentiable = bench_differentiable(max(3, args.steps // 3), 2, stream)
         outdoor = bench_outdoor(max(3, args.steps // 3), stream, flush)
 

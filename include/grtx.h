@@ -208,8 +208,8 @@ GRTX_API const char *grtx_last_error(void);
 /* Building blocks of the BVH build (each also runs inside grtx_build_bvh)                  */
 /* ---------------------------------------------------------------------------------------- */
 
-/* Parameter activation and instance transform (Sec. II-B; Sec. IV-A "the ray is
- * transformed to the local coordinate system ... derived from its rotation and scaling").
+/* Parameter activation and instance transform (Sec. II-B; Sec. IV-A: the per-Gaussian
+ * transform, built from its rotation and scales, that takes a ray into unit-sphere space).
  * For each Gaussian i: o = sigmoid(logit); s = exp(log_scale); R from the normalised
  * quaternion; kappa = sqrt(2 ln(o/alpha_min)). If o > alpha_min, writes
  *   d_geom[i] (16 floats): the rows of A = diag(1/(kappa s)) R^T with the mean, as three float4
@@ -437,6 +437,53 @@ GRTX_API int grtx_composite_bounce(float *d_rgbT, const float *d_sec_rgbT, const
 #define GRTX_NOALLOC_SCRATCH_BYTES (32u << 20)
 GRTX_API int grtx_trace_forward_noalloc(grtx_scene *scene, const grtx_camera *cam,
                                         const grtx_params *p, float *d_rgbT, void *stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Multi-level instancing (Sec. VI "Support for Dynamic and Multi-Object Scenes"): a shared  */
+/* primitive (the unit sphere), per-object instance BVHs (built scenes), a scene-level TLAS. */
+/* ---------------------------------------------------------------------------------------- */
+
+/* One placement of a built sphere-form scene: x_world = L x_object + c with object_to_world
+ * = rows (L_r0 | c_0), (L_r1 | c_1), (L_r2 | c_2) (row-major 3x4, L invertible). The scene
+ * is not owned and must outlive every world that refers to it; one scene may be placed many
+ * times. */
+typedef struct grtx_instance {
+    const grtx_scene *scene;
+    float object_to_world[12];
+    int32_t reserved[2];
+} grtx_instance;
+
+typedef struct grtx_world grtx_world;
+
+/* Build a world over n >= 1 instances (host array, copied). All scenes must be of
+ * GRTX_FORM_SPHERE and built with the same alpha_min. The host computes each instance's
+ * world-to-object map (in double, stored as FP32) and world box (the object's bounds through
+ * the map, widened by 1e-5 of its extent + 1e-6 of its coordinates against FP32 rounding)
+ * and builds the scene-level BVH over the boxes of the non-empty instances; the instance
+ * table and the TLAS go to device memory on `stream`. World Gaussian ids: the instance's
+ * base (the sum of the n of the scenes of the instances before it) plus the Gaussian's id
+ * in its scene. Fails with GRTX_ERR_INVALID_ARG on a NULL or non-sphere scene, mixed
+ * alpha_min, a non-invertible or non-finite map, more than 2^32 - 2 leaves in all, or a
+ * TLAS deeper than 32. */
+GRTX_API int grtx_world_create(const grtx_instance *inst, int n, void *stream, grtx_world **out);
+
+/* Replace the instance list (objects moved, added or removed): rebuilds the TLAS and the
+ * instance table, as grtx_world_create. Waits for the world's earlier work on `stream`. */
+GRTX_API int grtx_world_update(grtx_world *world, const grtx_instance *inst, int n, void *stream);
+
+/* Render cam through the world: k-buffer rounds (k = 8, 16 or 32) with checkpointed resume
+ * or restart (GRTX_TRAVERSAL_CHECKPOINT / RESTART) over the two-level structure. At a TLAS
+ * leaf the ray is mapped into the object's frame (t is unchanged by the affine map) and
+ * descends that scene's BVH; checkpoint entries carry the instance of object-level nodes
+ * (Sec. IV-B's checkpoint entry with its TLAS-leaf field). Keys are (t, world leaf index)
+ * and colours are evaluated along the object-frame direction. Outputs as
+ * grtx_trace_forward, with blended_ids in world Gaussian ids. p->alpha_min must be the
+ * scenes'. The world's trace workspace is grown on demand (stream-ordered allocation). */
+GRTX_API int grtx_world_trace_forward(grtx_world *world, const grtx_camera *cam, const grtx_params *p,
+                                      const grtx_trace_outputs *out, void *stream);
+
+/* Release a world (waits for its work on the last stream it used; NULL is a no-op). */
+GRTX_API void grtx_world_destroy(grtx_world *world);
 
 /* ---------------------------------------------------------------------------------------- */
 /* Serving: several resident scenes, camera requests batched into persistent launches.      */

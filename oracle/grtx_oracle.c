@@ -389,6 +389,113 @@ OG_API void og_render(const og_scene *S, const og_params *p, int n_rays, const d
     }
 }
 
+/* ------------------------------------------------------------------------------------ */
+/* Multi-level instancing (Sec. VI "Support for Dynamic and Multi-Object Scenes"): a     */
+/* world of placed objects, each a Gaussian scene under an affine object-to-world map.   */
+/* ------------------------------------------------------------------------------------ */
+
+typedef struct og_whit { double t; int id; double alpha; int inst, g; } og_whit;
+
+static int og_whit_cmp(const void *a, const void *b)
+{
+    const og_whit *x = (const og_whit *)a, *y = (const og_whit *)b;
+    if (x->t < y->t) return -1;
+    if (x->t > y->t) return 1;
+    return (x->id > y->id) - (x->id < y->id);
+}
+
+/* Inverse of the 3x3 matrix m (row-major) by cofactors; returns the determinant. */
+static double og_inv3(const double m[9], double inv[9])
+{
+    double c00 = m[4] * m[8] - m[5] * m[7], c01 = m[5] * m[6] - m[3] * m[8], c02 = m[3] * m[7] - m[4] * m[6];
+    double det = m[0] * c00 + m[1] * c01 + m[2] * c02;
+    inv[0] = c00 / det;
+    inv[1] = (m[2] * m[7] - m[1] * m[8]) / det;
+    inv[2] = (m[1] * m[5] - m[2] * m[4]) / det;
+    inv[3] = c01 / det;
+    inv[4] = (m[0] * m[8] - m[2] * m[6]) / det;
+    inv[5] = (m[2] * m[3] - m[0] * m[5]) / det;
+    inv[6] = c02 / det;
+    inv[7] = (m[1] * m[6] - m[0] * m[7]) / det;
+    inv[8] = (m[0] * m[4] - m[1] * m[3]) / det;
+    return det;
+}
+
+/* Render through a world of n_inst instances: instance i places scenes[inst_scene[i]] with
+ * the object-to-world map x_w = L x_o + c, M[12 i ..] = rows (L_r0 | c_0), (L_r1 | c_1),
+ * (L_r2 | c_2). Per ray, by the definition: every Gaussian g of every instance is met along
+ * the ray mapped into the object's frame, o_o = L^-1 (o - c), d_o = L^-1 d (an affine map, so
+ * t is the world t); it is hit when its response reaches alpha_min with t_near < t <= t_far.
+ * Hits are ordered by (t, world id), world id = (the n of the scenes of instances 0..i-1) +
+ * g, and composited front to back with the colour seen along the object-frame direction
+ * d_o / |d_o|. Outputs as og_render, ids in world ids. */
+OG_API void og_world_render(og_scene *const *scenes, int n_inst, const int *inst_scene, const double *M,
+                            const og_params *p, int n_rays, const double *origins, const double *dirs,
+                            const double *tnear, const double *tfar, double *out, int *n_blend, int *ids,
+                            int ids_cap, int *n_hits_total)
+{
+    double *Li = (double *)malloc(sizeof(double) * 9 * (n_inst > 0 ? n_inst : 1));
+    int *id_base = (int *)malloc(sizeof(int) * (n_inst > 0 ? n_inst : 1));
+    int base = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        const double *m = M + 12 * i;
+        double L[9] = {m[0], m[1], m[2], m[4], m[5], m[6], m[8], m[9], m[10]};
+        og_inv3(L, Li + 9 * i);
+        id_base[i] = base;
+        base += scenes[inst_scene[i]]->n;
+    }
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int r = 0; r < n_rays; ++r) {
+        const double *ro = origins + 3 * r, *rd = dirs + 3 * r;
+        int cap = 64, nh = 0;
+        og_whit *hits = (og_whit *)malloc(cap * sizeof(og_whit));
+        double *dob = (double *)malloc(sizeof(double) * 3 * (n_inst > 0 ? n_inst : 1));
+        for (int i = 0; i < n_inst; ++i) {
+            const og_scene *S = scenes[inst_scene[i]];
+            const double *m = M + 12 * i, *A = Li + 9 * i;
+            double v[3] = {ro[0] - m[3], ro[1] - m[7], ro[2] - m[11]}, oo[3], od[3];
+            for (int a = 0; a < 3; ++a) {
+                oo[a] = A[3 * a] * v[0] + A[3 * a + 1] * v[1] + A[3 * a + 2] * v[2];
+                od[a] = A[3 * a] * rd[0] + A[3 * a + 1] * rd[1] + A[3 * a + 2] * rd[2];
+            }
+            double nd = sqrt(od[0] * od[0] + od[1] * od[1] + od[2] * od[2]);
+            for (int a = 0; a < 3; ++a) dob[3 * i + a] = od[a] / nd;
+            for (int g = 0; g < S->n; ++g) {
+                if (!S->valid[g]) continue;
+                double t, d2, al;
+                og_response(S, g, oo, od, &t, &d2, &al);
+                if (al >= p->alpha_min && t > tnear[r] && t <= tfar[r]) {
+                    if (nh == cap) { cap *= 2; hits = (og_whit *)realloc(hits, cap * sizeof(og_whit)); }
+                    hits[nh].t = t; hits[nh].id = id_base[i] + g; hits[nh].alpha = al;
+                    hits[nh].inst = i; hits[nh].g = g;
+                    ++nh;
+                }
+            }
+        }
+        qsort(hits, nh, sizeof(og_whit), og_whit_cmp);
+        double C[3] = {0, 0, 0}, T = 1.0;
+        int nb = 0;
+        for (int h = 0; h < nh; ++h) {
+            double a = hits[h].alpha < p->alpha_max ? hits[h].alpha : p->alpha_max;
+            double c[3], raw[3];
+            og_color(scenes[inst_scene[hits[h].inst]], hits[h].g, dob + 3 * hits[h].inst, c, raw);
+            for (int ch = 0; ch < 3; ++ch) C[ch] += T * a * c[ch];
+            T *= (1.0 - a);
+            if (ids && nb < ids_cap) ids[(size_t)r * ids_cap + nb] = hits[h].id;
+            ++nb;
+            if (T < p->T_min) break;
+        }
+        for (int ch = 0; ch < 3; ++ch) out[4 * r + ch] = C[ch] + T * p->bg[ch];
+        out[4 * r + 3] = T;
+        if (n_blend) n_blend[r] = nb;
+        if (n_hits_total) n_hits_total[r] = nh;
+        free(dob);
+        free(hits);
+    }
+    free(Li);
+    free(id_base);
+}
+
 OG_API int og_num_threads(void)
 {
 #ifdef _OPENMP

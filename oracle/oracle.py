@@ -109,6 +109,8 @@ def lib():
             L.og_mirror_rays.restype = C.c_int
             L.og_mirror_rays.argtypes = [C.POINTER(OgCamera), C.POINTER(OgMirror)] + [_dp] * 8 + [_ip]
             L.og_composite_bounce.argtypes = [_dp, _dp, _ip, C.c_int, _dp]
+            L.og_world_render.argtypes = [C.POINTER(C.c_void_p), C.c_int, _ip, _dp, C.POINTER(OgParams), C.c_int,
+                                          _dp, _dp, _dp, _dp, _dp, _ip, _ip, C.c_int, _ip]
             L.og_secondary_rays.restype = C.c_int
             L.og_secondary_rays.argtypes = ([C.POINTER(OgCamera), C.POINTER(OgMirror), C.c_int, C.POINTER(OgGlass),
                                              C.c_int] + [_dp] * 8 + [_ip])
@@ -271,6 +273,26 @@ class Scene:
         G = OgGrads(*[_p(g[k]) for k in ("means", "log_scales", "quats", "logits", "sh")])
         lib().og_backward(self._h, C.byref(params), n, _p(o), _p(d), _p(tn), _p(tf), _p(gL), C.byref(G))
         return g
+
+
+def world_render(scenes, inst_scene, object_to_world, rays, params: OgParams | None = None, ids_cap: int = 0):
+    """Render rays through a world: instance i places scenes[inst_scene[i]] with the 3x4
+    object-to-world map object_to_world[i] (row-major); ids are world ids."""
+    o, d, tn, tf = [_f64(a) for a in rays]
+    n = tn.shape[0]
+    params = params or make_params()
+    M = np.ascontiguousarray(np.asarray(object_to_world, dtype=np.float64).reshape(-1, 12))
+    inst = np.ascontiguousarray(np.asarray(inst_scene, dtype=np.int32))
+    handles = (C.c_void_p * max(len(scenes), 1))(*[s._h for s in scenes])
+    out = np.empty((n, 4)); nb = np.empty(n, dtype=np.int32); nh = np.empty(n, dtype=np.int32)
+    ids = np.full((n, max(ids_cap, 1)), -1, dtype=np.int32)
+    lib().og_world_render(handles, len(inst), _p(inst, _ip), _p(M), C.byref(params), n, _p(o), _p(d), _p(tn),
+                          _p(tf), _p(out), _p(nb, _ip), _p(ids, _ip) if ids_cap > 0 else None, int(ids_cap),
+                          _p(nh, _ip))
+    res = dict(out=out, n_blend=nb, n_hits=nh)
+    if ids_cap > 0:
+        res["ids"] = ids
+    return res
 
 
 def centroid_bounds(aabb_f32: np.ndarray) -> np.ndarray:

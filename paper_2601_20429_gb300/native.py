@@ -136,6 +136,10 @@ class grtx_glass(C.Structure):
                 ("t_near_secondary", C.c_float), ("reserved", C.c_float * 2)]
 
 
+class grtx_instance(C.Structure):
+    _fields_ = [("scene", _fp), ("object_to_world", C.c_float * 12), ("reserved", C.c_int32 * 2)]
+
+
 class grtx_request(C.Structure):
     _fields_ = [("scene_id", C.c_int32), ("reserved", C.c_int32), ("cam", grtx_camera), ("d_rgbT", _fp),
                 ("tag", C.c_uint64)]
@@ -168,6 +172,11 @@ _SIGS = {
                                       _fp, _fp, C.POINTER(grtx_grads), _fp]),
     "grtx_mirror_rays": (C.c_int, [C.POINTER(grtx_camera), C.POINTER(grtx_mirror)] + [_fp] * 11),
     "grtx_template_mesh": (C.c_int, [C.c_int, _fp, C.POINTER(C.c_int)]),
+    "grtx_world_create": (C.c_int, [C.POINTER(grtx_instance), C.c_int, _fp, C.POINTER(_fp)]),
+    "grtx_world_update": (C.c_int, [_fp, C.POINTER(grtx_instance), C.c_int, _fp]),
+    "grtx_world_trace_forward": (C.c_int, [_fp, C.POINTER(grtx_camera), C.POINTER(grtx_params),
+                                           C.POINTER(grtx_trace_outputs), _fp]),
+    "grtx_world_destroy": (None, [_fp]),
     "grtx_secondary_rays": (C.c_int, [C.POINTER(grtx_camera), C.POINTER(grtx_mirror), C.c_int, C.POINTER(grtx_glass),
                                       C.c_int] + [_fp] * 11),
     "grtx_composite_bounce": (C.c_int, [_fp, _fp, _fp, _fp, C.c_int64, C.POINTER(C.c_float * 3), _fp]),
@@ -358,6 +367,43 @@ def grtx_trace_forward(scene: int, cam: grtx_camera, p: grtx_params, rgbT, n_ble
     out.stats = ptr(stats)
     check(lib().grtx_trace_forward(C.c_void_p(scene), C.byref(cam), C.byref(p), C.byref(out), stream_handle(stream)),
           "grtx_trace_forward")
+
+
+def make_instances(placements) -> C.Array:
+    """placements: iterable of (scene handle, 3x4 object-to-world matrix, row-major)."""
+    import numpy as np
+    pl = list(placements)
+    arr = (grtx_instance * max(len(pl), 1))()
+    for i, (h, M) in enumerate(pl):
+        arr[i].scene = h
+        m = np.asarray(M, dtype=np.float64).reshape(12)
+        for k in range(12):
+            arr[i].object_to_world[k] = float(m[k])
+    return arr
+
+
+def grtx_world_create(placements, stream=None) -> int:
+    arr = make_instances(placements)
+    out = C.c_void_p()
+    check(lib().grtx_world_create(arr, len(list(placements)), stream_handle(stream), C.byref(out)),
+          "grtx_world_create")
+    return out.value
+
+
+def grtx_world_update(world: int, placements, stream=None):
+    arr = make_instances(placements)
+    check(lib().grtx_world_update(C.c_void_p(world), arr, len(list(placements)), stream_handle(stream)),
+          "grtx_world_update")
+
+
+def grtx_world_trace_forward(world: int, cam: grtx_camera, p: grtx_params, rgbT, n_blended=None, blended_ids=None,
+                             stats=None, stream=None):
+    out = grtx_trace_outputs()
+    out.rgbT, out.n_blended, out.blended_ids = ptr(rgbT), ptr(n_blended), ptr(blended_ids)
+    out.ids_cap = int(blended_ids.shape[-1]) if blended_ids is not None else 0
+    out.stats = ptr(stats)
+    check(lib().grtx_world_trace_forward(C.c_void_p(world), C.byref(cam), C.byref(p), C.byref(out),
+                                         stream_handle(stream)), "grtx_world_trace_forward")
 
 
 def make_mirror(m: dict) -> grtx_mirror:

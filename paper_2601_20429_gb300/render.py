@@ -76,6 +76,53 @@ class Scene:
             pass
 
 
+class World:
+    """Placed objects (Sec. VI multi-level instancing): each placement is (Scene, 3x4
+    object-to-world matrix). The scenes are not owned and must outlive the world."""
+
+    def __init__(self, placements, stream=None):
+        self.placements = [(sc, np.asarray(M, dtype=np.float64).reshape(3, 4)) for sc, M in placements]
+        self.alpha_min = self.placements[0][0].alpha_min
+        self.handle = N.grtx_world_create([(sc.handle, M) for sc, M in self.placements], stream)
+
+    def update(self, placements, stream=None):
+        self.placements = [(sc, np.asarray(M, dtype=np.float64).reshape(3, 4)) for sc, M in placements]
+        N.grtx_world_update(self.handle, [(sc.handle, M) for sc, M in self.placements], stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            N.lib().grtx_world_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def render_world(world: World, cam: dict | None, rays=None, out=None, ids_cap: int = 0, want_n_blended=False,
+                 want_stats=False, stream=None, **params):
+    """Forward trace through a world. Returns dict(rgbT, n_blended?, ids? (world ids), stats?)."""
+    p = trace_params(alpha_min=world.alpha_min, **params)
+    c = N.make_camera(cam, rays)
+    n = n_rays_of(cam, rays)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rgbT = out if out is not None else torch.empty((n, 4), dtype=torch.float32, device=dev)
+    nb = torch.empty(n, dtype=torch.int32, device=dev) if want_n_blended else None
+    ids = torch.empty((n, ids_cap), dtype=torch.int32, device=dev) if ids_cap > 0 else None
+    st = N.stats_tensor(dev) if want_stats else None
+    N.grtx_world_trace_forward(world.handle, c, p, rgbT, nb, ids, st, stream)
+    res = {"rgbT": rgbT}
+    if nb is not None:
+        res["n_blended"] = nb
+    if ids is not None:
+        res["ids"] = ids
+    if st is not None:
+        res["stats"] = st
+    return res
+
+
 def trace_params(k=16, traversal="checkpoint", alpha_min=0.01, T_min=1e-3, alpha_max=0.99, bg=(0.0, 0.0, 0.0),
                  ckpt_capacity=0, evict_capacity=0):
     return N.make_params(k, TRAVERSALS[traversal] if isinstance(traversal, str) else traversal, alpha_min, T_min,

@@ -707,3 +707,85 @@ def test_glass_shows_the_gaussian_behind_it():
     out = O.composite_bounce(p, s, spix)
     np.testing.assert_allclose(out[0, :3], a * col, rtol=1e-12)
     assert out[0, 3] == pytest.approx(1 - a, rel=1e-12)
+
+
+# ---------------------------------------------------------------- multi-level instancing
+
+
+def _world_scene(n=3000, seed=31):
+    g = scenes.surface_scene(n=n, seed=seed, n_spheres=2, n_patches=2, extent=0.4)   # SH degree 3
+    return g, O.Scene.from_params(g)
+
+
+def _affine(R, c):
+    return np.concatenate([np.asarray(R, float), np.asarray(c, float)[:, None]], 1).reshape(12)
+
+
+def _rot(axis, ang):
+    axis = np.asarray(axis, float) / np.linalg.norm(axis)
+    K = np.array([[0, -axis[2], axis[1]], [axis[2], 0, -axis[0]], [-axis[1], axis[0], 0]])
+    return np.eye(3) + math.sin(ang) * K + (1 - math.cos(ang)) * K @ K
+
+
+def test_world_identity_instance_is_the_scene():
+    g, S = _world_scene()
+    rays = O.camera_rays(scenes.pinhole_camera(20, 16, (0.0, 0.3, -3.0), (0, 0, 0), 20.0))
+    ref = S.render(rays, ids_cap=64)
+    w = O.world_render([S], [0], [_affine(np.eye(3), [0, 0, 0])], rays, ids_cap=64)
+    np.testing.assert_array_equal(w["out"], ref["out"])
+    np.testing.assert_array_equal(w["ids"], ref["ids"])
+    assert ref["n_blend"].sum() > 100
+
+
+def test_world_moves_with_its_camera():
+    """Moving the object and the camera by the same rigid motion leaves the image unchanged
+    (the colour is evaluated along the object-frame direction)."""
+    g, S = _world_scene()
+    o, d, tn, tf = O.camera_rays(scenes.pinhole_camera(18, 14, (0.2, 0.1, -3.0), (0, 0, 0), 20.0))
+    ref = S.render((o, d, tn, tf), ids_cap=64)
+    R, c = _rot([1.0, 2.0, -0.5], 0.9), np.array([3.0, -1.0, 7.5])
+    moved = (o @ R.T + c, d @ R.T, tn, tf)
+    w = O.world_render([S], [0], [_affine(R, c)], moved, ids_cap=64)
+    np.testing.assert_allclose(w["out"], ref["out"], atol=1e-10)
+    np.testing.assert_array_equal(w["n_blend"], ref["n_blend"])
+
+
+def test_world_scaled_isotropic_gaussian_closed_form():
+    """An isotropic Gaussian (sigma, opacity a) placed with uniform scale s is the Gaussian of
+    width s sigma: alpha = a exp(-b^2 / (2 s^2 sigma^2)) at impact parameter b, at the foot of
+    the perpendicular."""
+    a, col, sig, s = 0.8, np.array([0.3, 0.6, 0.9]), 0.1, 2.5
+    S = make_scene([[0, 0, 0.0]], sig, [1, 0, 0, 0], a, col)
+    b = np.array([0.0, 0.1, 0.3, 0.8])                  # the hit boundary is at 0.74
+    o = np.stack([b, np.zeros(4), np.full(4, -5.0)], 1)
+    d = np.tile([0.0, 0.0, 1.0], (4, 1))
+    w = O.world_render([S], [0], [_affine(s * np.eye(3), [0, 0, 2.0])], (o, d, np.zeros(4), np.full(4, np.inf)))
+    alpha = a * np.exp(-b ** 2 / (2 * (s * sig) ** 2))
+    hit = alpha >= 0.01
+    np.testing.assert_allclose(w["out"][hit, :3], alpha[hit, None] * col, rtol=1e-12)
+    np.testing.assert_allclose(w["out"][:, 3], np.where(hit, 1 - alpha, 1.0), rtol=1e-12)
+    assert hit.sum() == 3
+
+
+def test_world_overlapping_copies_blend_twice_in_id_order():
+    a, col = 0.6, np.array([0.9, 0.3, 0.1])
+    S = make_scene([[0, 0, 0.0]], 0.05, [1, 0, 0, 0], a, col)
+    ray = (np.array([[0.0, 0.0, -3.0]]), np.array([[0.0, 0.0, 1.0]]), np.zeros(1), np.full(1, np.inf))
+    I = _affine(np.eye(3), [0, 0, 0])
+    w = O.world_render([S], [0, 0], [I, I], ray, ids_cap=4)
+    np.testing.assert_allclose(w["out"][0, :3], a * col + (1 - a) * a * col, rtol=1e-12)
+    assert w["out"][0, 3] == pytest.approx((1 - a) ** 2, rel=1e-12)
+    assert list(w["ids"][0, :2]) == [0, 1]
+
+
+def test_world_ids_and_images_of_separate_instances():
+    g, S = _world_scene()
+    g2 = scenes.tiny_scene(n=120, seed=5)
+    S2 = O.Scene.from_params(g2)
+    o, d, tn, tf = O.camera_rays(scenes.pinhole_camera(16, 12, (0.0, 0.0, -3.0), (0, 0, 0), 50.0))
+    far = _affine(np.eye(3), [100.0, 0, 0])
+    w = O.world_render([S2, S], [0, 1], [far, _affine(np.eye(3), [0, 0, 0])], (o, d, tn, tf), ids_cap=64)
+    ref = S.render((o, d, tn, tf), ids_cap=64)
+    np.testing.assert_array_equal(w["out"], ref["out"])
+    m = ref["ids"] >= 0
+    np.testing.assert_array_equal(w["ids"][m], ref["ids"][m] + 120)     # after the first instance's ids
