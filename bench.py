@@ -272,9 +272,9 @@ def mrays(n_rays: int, times_ms) -> float:
 
 def bench_surface_ablations(g, sc, cam, k: int, steps: int, stream, flush) -> dict:
     """On the surface scene: single-round traversal (Sec. III-C Obs. II), the instance BVH over
-    a shared 20- / 80-triangle icosphere template (Sec. IV-A, second option), the
-    centroid-only LBVH codes against the size-aware default, and the resolution /
-    field-of-view sweep (Sec. V-E)."""
+    a shared 20- / 80-triangle icosphere template (Sec. IV-A, second option), the LBVH (radix
+    tree) with size-aware and centroid codes against the default clustering builder, and the
+    resolution / field-of-view sweep (Sec. V-E)."""
     import torch
     from paper_2601_20429_gb300 import native as N
     from paper_2601_20429_gb300 import render as R
@@ -293,12 +293,16 @@ def bench_surface_ablations(g, sc, cam, k: int, steps: int, stream, flush) -> di
         res[form] = {"Mrays_per_s": mrays(n_rays, t), "ms_per_frame": statistics.mean(t),
                      "nodes_per_ray": nodes_per_ray(st), "template_triangles": 20 if form == "ico20" else 80}
         sc_i.close()
-    sc_c = R.Scene.from_params(g, bvh_codes="centroid")
-    st = N.stats_dict(R.render(sc_c, cam, k=k, out=out, want_stats=True)["stats"])
-    t = time_frames(lambda: R.render(sc_c, cam, k=k, out=out), steps, 2, flush, stream)
-    res["centroid_codes"] = {"Mrays_per_s": mrays(n_rays, t), "ms_per_frame": statistics.mean(t),
-                             "nodes_per_ray": nodes_per_ray(st)}
-    sc_c.close()
+    for name, codes, builder in (("lbvh_sized_codes", "sized", "lbvh"), ("lbvh_centroid_codes", "centroid", "lbvh")):
+        t0 = time.perf_counter()
+        sc_c = R.Scene.from_params(g, bvh_codes=codes, bvh_builder=builder)
+        torch.cuda.synchronize()
+        build_ms = (time.perf_counter() - t0) * 1e3
+        st = N.stats_dict(R.render(sc_c, cam, k=k, out=out, want_stats=True)["stats"])
+        t = time_frames(lambda: R.render(sc_c, cam, k=k, out=out), steps, 2, flush, stream)
+        res[name] = {"Mrays_per_s": mrays(n_rays, t), "ms_per_frame": statistics.mean(t),
+                     "nodes_per_ray": nodes_per_ray(st), "build_ms": build_ms, "depth": sc_c.info()["depth"]}
+        sc_c.close()
     sweep = []
     for (w, h, fov) in ((640, 360, 60.0), (1280, 720, 60.0), (1920, 1080, 60.0), (3840, 2160, 60.0),
                         (1920, 1080, 30.0), (1920, 1080, 90.0)):
@@ -491,7 +495,8 @@ def bench_outdoor(steps: int, stream, flush):
     sc = R.Scene.from_params(g)
     torch.cuda.synchronize()
     build_ms = (time.perf_counter() - t0) * 1e3
-    sc_c = R.Scene.from_params(g, bvh_codes="centroid")
+    sc_c = R.Scene.from_params(g, bvh_codes="centroid", bvh_builder="lbvh")
+    sc_l = R.Scene.from_params(g, bvh_builder="lbvh")
     del g
     n = cam["width"] * cam["height"]
     prim = [torch.empty((n, 3), device="cuda"), torch.empty((n, 3), device="cuda"), torch.empty(n, device="cuda"),
@@ -512,7 +517,11 @@ def bench_outdoor(steps: int, stream, flush):
     st_s = N.stats_dict(R.render(sc, None, rays=sec_rays, k=cfg["k"], want_stats=True)["stats"])
     tc = time_frames(lambda: R.render(sc_c, None, rays=prim, k=cfg["k"], out=out_p), steps, 2, flush, stream)
     st_c = N.stats_dict(R.render(sc_c, None, rays=prim, k=cfg["k"], want_stats=True)["stats"])
+    tl = time_frames(lambda: R.render(sc_l, None, rays=prim, k=cfg["k"], out=out_p), steps, 2, flush, stream)
+    st_l = N.stats_dict(R.render(sc_l, None, rays=prim, k=cfg["k"], want_stats=True)["stats"])
+    depth = sc.info()["depth"]
     sc_c.close()
+    sc_l.close()
     sc.close()
     return {"workload": "6M outdoor Gaussians, 1920x1080 equidistant fisheye, one 4x3 m mirror and one glass "
                         "ball (index 1.5), k=16",
@@ -521,8 +530,11 @@ def bench_outdoor(steps: int, stream, flush):
                         "nodes_per_ray": nodes_per_ray(st_p)},
             "secondary": {"Mrays_per_s": m / (statistics.mean(ts) / 1e3) / 1e6, "ms": statistics.mean(ts),
                           "nodes_per_ray": nodes_per_ray(st_s)},
-            "primary_centroid_codes": {"Mrays_per_s": n / (statistics.mean(tc) / 1e3) / 1e6,
-                                       "ms": statistics.mean(tc), "nodes_per_ray": nodes_per_ray(st_c)}}
+            "depth": depth,
+            "primary_lbvh_sized_codes": {"Mrays_per_s": n / (statistics.mean(tl) / 1e3) / 1e6,
+                                         "ms": statistics.mean(tl), "nodes_per_ray": nodes_per_ray(st_l)},
+            "primary_lbvh_centroid_codes": {"Mrays_per_s": n / (statistics.mean(tc) / 1e3) / 1e6,
+                                            "ms": statistics.mean(tc), "nodes_per_ray": nodes_per_ray(st_c)}}
 
 
 def main():

@@ -107,10 +107,14 @@ enum { GRTX_TRAVERSAL_CHECKPOINT = 0, /* resume from checkpointed nodes + evicti
  * traversal: GRTX_TRAVERSAL_*, for either form: {sphere, proxy} x {checkpoint, restart} are the
  * paper's GRTX, GRTX-HW only (proxy + checkpoint), GRTX-SW only (sphere + restart) and the
  * baseline (proxy + restart) of Sec. V-B.
- * bvh_codes (read by grtx_build_bvh only): the sort key of the LBVH build,
- * GRTX_CODES_SIZED (0, the default: grtx_morton_codes_sized) or GRTX_CODES_CENTROID
- * (grtx_morton_codes). The tree shape changes the cost of a trace, never its result. */
+ * bvh_codes (read by grtx_build_bvh only): the sort key of the build, GRTX_CODES_SIZED (0,
+ * the default: grtx_morton_codes_sized) or GRTX_CODES_CENTROID (grtx_morton_codes).
+ * bvh_builder (read by grtx_build_bvh only): GRTX_BUILDER_PLOC (0, the default: clustering
+ * of the sorted leaves, grtx_ploc_tree) or GRTX_BUILDER_LBVH (the binary radix tree of the
+ * codes, grtx_radix_tree). The tree shape changes the cost of a trace, never its result. */
 enum { GRTX_CODES_SIZED = 0, GRTX_CODES_CENTROID = 1 };
+enum { GRTX_BUILDER_PLOC = 0, GRTX_BUILDER_LBVH = 1 };
+#define GRTX_PLOC_RADIUS 16
 typedef struct grtx_params {
     int32_t k;
     int32_t traversal;
@@ -121,6 +125,7 @@ typedef struct grtx_params {
     int32_t ckpt_capacity;
     int32_t evict_capacity;
     int32_t bvh_codes;
+    int32_t bvh_builder;
 } grtx_params;
 
 enum { GRTX_CAMERA_PINHOLE = 0, GRTX_CAMERA_FISHEYE = 1, GRTX_CAMERA_RAYS = 2 };
@@ -262,6 +267,20 @@ GRTX_API int grtx_sort_pairs(uint64_t *d_keys, uint32_t *d_values, int64_t n, in
 GRTX_API int grtx_radix_tree(const uint64_t *d_sorted_keys, int64_t n, uint32_t *d_left,
                              uint32_t *d_right, uint32_t *d_parent, void *stream);
 
+/* Locally-ordered clustering (PLOC: Meister and Bittner, IEEE TVCG 2018; the paper builds its
+ * BVH with a third-party SAH builder, Sec. V-A) over n >= 2 leaf boxes in Morton order
+ * (d_leaf_aabb [n][6]). Iterate until one cluster is left: every cluster i picks the cluster
+ * j in [i - GRTX_PLOC_RADIUS, i + GRTX_PLOC_RADIUS] whose union box has the smallest surface
+ * area 2 (ex ey + ey ez + ez ex) (FP32, rounded in that order), ties to the lower j; each
+ * mutual pair i < j merges into a new node (left = cluster i, right = cluster j) in cluster
+ * i's place, new nodes numbered in creation order by increasing i; the clusters are
+ * compacted in order. The node created k-th becomes internal node n - 2 - k (the root is 0).
+ * Writes d_left / d_right [n-1] and d_parent [2n-1] in grtx_radix_tree's layout and, if not
+ * NULL, *iterations (host). Allocates scratch stream-ordered and synchronises the stream
+ * once per iteration (to read how many clusters are left). Device, caller-owned. */
+GRTX_API int grtx_ploc_tree(const float *d_leaf_aabb, int64_t n, uint32_t *d_left, uint32_t *d_right,
+                            uint32_t *d_parent, int *iterations, void *stream);
+
 /* Bottom-up bounds: box of every internal node = union of its children's boxes, leaves'
  * boxes given in sorted order (d_leaf_aabb [n][6]); FP32 min/max, hence exact. Uses the tree
  * of grtx_radix_tree. d_node_aabb [n-1][6] out; d_counters: device scratch of n-1 uint32
@@ -286,7 +305,7 @@ GRTX_API int grtx_refit(const uint32_t *d_left, const uint32_t *d_right, const u
  * per-slot trace workspace grown on demand; the caller's arrays may be freed once the
  * stream passes the call. Synchronises the stream once at the end (to read the node count
  * and tree depth). *out is set only on success. Fails with GRTX_ERR_OVERFLOW_FATAL if the
- * tree is deeper than the traversal stack (64). */
+ * tree is deeper than the traversal stack (128). */
 GRTX_API int grtx_build_bvh(const grtx_gaussians *g, const grtx_params *p, int form, void *stream,
                             grtx_scene **out);
 

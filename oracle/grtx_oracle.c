@@ -1099,6 +1099,81 @@ OG_API void og_refit(int n, const uint32_t *left, const uint32_t *right, const f
     if (n >= 2) og_refit_rec(0u, left, right, leaf_aabb, node_aabb, root);
 }
 
+/* Locally-ordered clustering (PLOC: Meister and Bittner, "Parallel Locally-Ordered
+ * Clustering for Bounding Volume Hierarchy Construction", IEEE TVCG 2018) over n >= 2 boxes in
+ * Morton order. Clusters start as the leaves. Each iteration, every cluster i picks its
+ * nearest neighbour among clusters i-r..i+r: the one whose union with it has the smallest
+ * surface area 2 (ex ey + ey ez + ez ex) (FP32, in that order), ties to the lower index;
+ * every mutual pair (i, j), i < j, merges into a new internal node (left = cluster i,
+ * right = cluster j) that takes cluster i's place, nodes numbered in order of creation by
+ * increasing i; the surviving clusters keep their order. Iterations repeat until one cluster
+ * remains (the globally closest pair is always mutual, so every iteration merges). Output:
+ * internal node created k-th is numbered n - 2 - k (the root is 0); left/right hold
+ * internal numbers or (0x80000000 | leaf index). Returns the number of iterations. */
+static float og_ploc_area(const float *a, const float *b)
+{
+    float e0 = fmaxf(a[3], b[3]) - fminf(a[0], b[0]);
+    float e1 = fmaxf(a[4], b[4]) - fminf(a[1], b[1]);
+    float e2 = fmaxf(a[5], b[5]) - fminf(a[2], b[2]);
+    float s = e0 * e1;
+    s = s + e1 * e2;
+    s = s + e2 * e0;
+    return 2.0f * s;
+}
+
+OG_API int og_ploc(int n, const float *aabb, int radius, uint32_t *left, uint32_t *right)
+{
+    float *cb = (float *)malloc(sizeof(float) * 6 * n), *cb2 = (float *)malloc(sizeof(float) * 6 * n);
+    uint32_t *id = (uint32_t *)malloc(sizeof(uint32_t) * n), *id2 = (uint32_t *)malloc(sizeof(uint32_t) * n);
+    uint32_t *lc = (uint32_t *)malloc(sizeof(uint32_t) * n), *rc = (uint32_t *)malloc(sizeof(uint32_t) * n);
+    int *nn = (int *)malloc(sizeof(int) * n);
+    memcpy(cb, aabb, sizeof(float) * 6 * n);
+    for (int i = 0; i < n; ++i) id[i] = OG_LEAF | (uint32_t)i;
+    int m = n, created = 0, iters = 0;
+    while (m > 1) {
+        ++iters;
+        for (int i = 0; i < m; ++i) {
+            float best = INFINITY;
+            int bj = -1;
+            int lo = i - radius < 0 ? 0 : i - radius, hi = i + radius > m - 1 ? m - 1 : i + radius;
+            for (int j = lo; j <= hi; ++j) {
+                if (j == i) continue;
+                float a = og_ploc_area(cb + 6 * i, cb + 6 * j);
+                if (a < best) { best = a; bj = j; }           /* ascending j: ties keep the lower */
+            }
+            nn[i] = bj;
+        }
+        int w = 0;
+        for (int i = 0; i < m; ++i) {
+            int j = nn[i];
+            if (nn[j] == i && j < i) continue;                /* merged into cluster j */
+            if (nn[j] == i) {
+                lc[created] = id[i];
+                rc[created] = id[j];
+                for (int c = 0; c < 3; ++c) {
+                    cb2[6 * w + c] = fminf(cb[6 * i + c], cb[6 * j + c]);
+                    cb2[6 * w + 3 + c] = fmaxf(cb[6 * i + 3 + c], cb[6 * j + 3 + c]);
+                }
+                id2[w] = (uint32_t)created++;
+            } else {
+                memcpy(cb2 + 6 * w, cb + 6 * i, sizeof(float) * 6);
+                id2[w] = id[i];
+            }
+            ++w;
+        }
+        float *tf = cb; cb = cb2; cb2 = tf;
+        uint32_t *ti = id; id = id2; id2 = ti;
+        m = w;
+    }
+    for (int k = 0; k < n - 1; ++k) {
+        uint32_t L = lc[k], R = rc[k];
+        left[n - 2 - k] = (L & OG_LEAF) ? L : (uint32_t)(n - 2) - L;
+        right[n - 2 - k] = (R & OG_LEAF) ? R : (uint32_t)(n - 2) - R;
+    }
+    free(cb); free(cb2); free(id); free(id2); free(lc); free(rc); free(nn);
+    return iters;
+}
+
 /* ------------------------------------------------------------------------------------ */
 /* One bounce off a rectangular planar mirror (Sec. VI "GRTX-HW on Secondary Rays").     */
 /* ------------------------------------------------------------------------------------ */

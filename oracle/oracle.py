@@ -119,6 +119,8 @@ def lib():
             L.og_morton_sized64.argtypes = [C.c_int, _fp, _fp, _u64p]
             L.og_radix_tree.argtypes = [C.c_int, _u64p, _u32p, _u32p]
             L.og_refit.argtypes = [C.c_int, _u32p, _u32p, _fp, _fp]
+            L.og_ploc.restype = C.c_int
+            L.og_ploc.argtypes = [C.c_int, _fp, C.c_int, _u32p, _u32p]
             _lib = L
     return _lib
 
@@ -329,6 +331,16 @@ def radix_tree(sorted_codes: np.ndarray):
     if n >= 2:
         lib().og_radix_tree(n, _p(k, _u64p), _p(left, _u32p), _p(right, _u32p))
     return left, right
+
+
+def ploc(leaf_aabb_f32: np.ndarray, radius: int = 16):
+    """(left, right, iterations) of the locally-ordered clustering tree over boxes in order."""
+    a = np.ascontiguousarray(leaf_aabb_f32, dtype=np.float32).reshape(-1, 6)
+    n = a.shape[0]
+    left = np.zeros(max(n - 1, 0), dtype=np.uint32)
+    right = np.zeros(max(n - 1, 0), dtype=np.uint32)
+    it = lib().og_ploc(n, _p(a, _fp), int(radius), _p(left, _u32p), _p(right, _u32p)) if n >= 2 else 0
+    return left, right, it
 
 
 def refit(left: np.ndarray, right: np.ndarray, leaf_aabb_f32: np.ndarray) -> np.ndarray:

@@ -481,6 +481,186 @@ __global__ void k_emit_nodes(const uint32_t *__restrict__ left, const uint32_t *
     nodes[4 * (size_t)i + 3] = make_float4(__uint_as_float(L), __uint_as_float(R), s0, s1);
 }
 
+// ------------------------------------------------------------------------------------------
+// Locally-ordered clustering (PLOC; Meister and Bittner, IEEE TVCG 2018) over boxes in Morton
+// order: each iteration every cluster finds its nearest neighbour (smallest union surface
+// area, ties to the lower index) within kPlocRadius places, mutual pairs merge into a new
+// node, and the clusters are compacted. The globally closest pair is always mutual, so every
+// iteration merges at least one pair.
+// ------------------------------------------------------------------------------------------
+constexpr int kPlocBlock = 256;
+constexpr int kPlocRadius = GRTX_PLOC_RADIUS;
+
+// Surface area of the union of two boxes, 2 (ex ey + ey ez + ez ex) with every operation
+// rounded as written (no contraction), so that both members of a pair see the same value.
+__device__ __forceinline__ float ploc_area(const float *a, const float *b)
+{
+    float e0 = __fsub_rn(fmaxf(a[3], b[3]), fminf(a[0], b[0]));
+    float e1 = __fsub_rn(fmaxf(a[4], b[4]), fminf(a[1], b[1]));
+    float e2 = __fsub_rn(fmaxf(a[5], b[5]), fminf(a[2], b[2]));
+    float s = __fmul_rn(e0, e1);
+    s = __fadd_rn(s, __fmul_rn(e1, e2));
+    s = __fadd_rn(s, __fmul_rn(e2, e0));
+    return __fmul_rn(2.0f, s);
+}
+
+__global__ void k_ploc_init(uint32_t *__restrict__ id, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) id[i] = GRTX_LEAF | (uint32_t)i;
+}
+
+__global__ void __launch_bounds__(kPlocBlock) k_ploc_nn(const float *__restrict__ cb, int m, int *__restrict__ nn)
+{
+    __shared__ float sb[(kPlocBlock + 2 * kPlocRadius) * 6];
+    const int b0 = blockIdx.x * kPlocBlock;
+    for (int t = threadIdx.x; t < (kPlocBlock + 2 * kPlocRadius) * 6; t += blockDim.x) {
+        int g = b0 - kPlocRadius + t / 6;
+        sb[t] = (g >= 0 && g < m) ? cb[6 * (size_t)g + t % 6] : 0.f;
+    }
+    __syncthreads();
+    int i = b0 + threadIdx.x;
+    if (i >= m) return;
+    const float *me = sb + 6 * (threadIdx.x + kPlocRadius);
+    int lo = max(i - kPlocRadius, 0), hi = min(i + kPlocRadius, m - 1);
+    float best = INFINITY;
+    int bj = -1;
+    for (int j = lo; j <= hi; ++j) {
+        if (j == i) continue;
+        float a = ploc_area(me, sb + 6 * (j - b0 + kPlocRadius));
+        if (a < best) {                       // ascending j: a tie keeps the lower index
+            best = a;
+            bj = j;
+        }
+    }
+    nn[i] = bj;
+}
+
+// create[i]: cluster i starts a merge (mutual pair, i the lower); keep[i]: cluster i survives
+// (as itself or as the merged node); tail: the two flags of the last cluster.
+__global__ void k_ploc_flags(const int *__restrict__ nn, int m, uint32_t *__restrict__ create,
+                             uint32_t *__restrict__ keep, uint32_t *__restrict__ tail)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int j = nn[i];
+    bool mutual = j >= 0 && nn[j] == i;
+    uint32_t c = mutual && i < j, k = !(mutual && j < i);
+    create[i] = c;
+    keep[i] = k;
+    if (i == m - 1) {
+        tail[0] = c;
+        tail[1] = k;
+    }
+}
+
+__global__ void k_ploc_totals(const uint32_t *__restrict__ create_off, const uint32_t *__restrict__ keep_off, int m,
+                              const uint32_t *__restrict__ tail, uint32_t *__restrict__ totals)
+{
+    totals[0] = create_off[m - 1] + tail[0];
+    totals[1] = keep_off[m - 1] + tail[1];
+}
+
+__global__ void k_ploc_merge(const float *__restrict__ cb, const uint32_t *__restrict__ id, const int *__restrict__ nn,
+                             const uint32_t *__restrict__ create_off, const uint32_t *__restrict__ keep_off, int m,
+                             uint32_t node_base, float *__restrict__ cb_out, uint32_t *__restrict__ id_out,
+                             uint32_t *__restrict__ lc, uint32_t *__restrict__ rc)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int j = nn[i];
+    bool mutual = j >= 0 && nn[j] == i;
+    if (mutual && j < i) return;              // merged into cluster j
+    size_t w = keep_off[i];
+    if (mutual) {
+        uint32_t k = node_base + create_off[i];
+        lc[k] = id[i];
+        rc[k] = id[j];
+        for (int c = 0; c < 3; ++c) {
+            cb_out[6 * w + c] = fminf(cb[6 * (size_t)i + c], cb[6 * (size_t)j + c]);
+            cb_out[6 * w + 3 + c] = fmaxf(cb[6 * (size_t)i + 3 + c], cb[6 * (size_t)j + 3 + c]);
+        }
+        id_out[w] = k;
+    } else {
+        for (int c = 0; c < 6; ++c) cb_out[6 * w + c] = cb[6 * (size_t)i + c];
+        id_out[w] = id[i];
+    }
+}
+
+// Node created k-th -> internal node n - 2 - k (the root, created last, is 0), with parents.
+__global__ void k_ploc_finish(const uint32_t *__restrict__ lc, const uint32_t *__restrict__ rc, int n,
+                              uint32_t *__restrict__ left, uint32_t *__restrict__ right, uint32_t *__restrict__ parent)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n - 1) return;
+    uint32_t dst = (uint32_t)(n - 2 - k);
+    uint32_t L = lc[k], R = rc[k];
+    L = (L & GRTX_LEAF) ? L : (uint32_t)(n - 2) - L;
+    R = (R & GRTX_LEAF) ? R : (uint32_t)(n - 2) - R;
+    left[dst] = L;
+    right[dst] = R;
+    parent[(L & GRTX_LEAF) ? (n - 1 + (L & ~GRTX_LEAF)) : L] = dst;
+    parent[(R & GRTX_LEAF) ? (n - 1 + (R & ~GRTX_LEAF)) : R] = dst;
+    if (dst == 0) parent[0] = GRTX_NONE;
+}
+
+// ------------------------------------------------------------------------------------------
+// Depth-first renumbering of a tree's internal nodes (pre-order: a node, then its left
+// subtree, then its right subtree), so that every subtree occupies a contiguous range of the
+// node array and a parent sits next to its left child.
+// ------------------------------------------------------------------------------------------
+__global__ void k_subtree_sizes(const uint32_t *__restrict__ left, const uint32_t *__restrict__ right,
+                                const uint32_t *__restrict__ parent, int n, uint32_t *size, uint32_t *counters)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    uint32_t node = parent[n - 1 + j];
+    while (node != GRTX_NONE) {
+        __threadfence();
+        if (atomicAdd(&counters[node], 1u) == 0u) return;   // the sibling subtree is not done yet
+        __threadfence();
+        uint32_t L = left[node], R = right[node];
+        uint32_t sl = (L & GRTX_LEAF) ? 0u : __ldcg(size + L);
+        uint32_t sr = (R & GRTX_LEAF) ? 0u : __ldcg(size + R);
+        __stcg(size + node, 1u + sl + sr);
+        node = parent[node];
+    }
+}
+
+// max_depth bounds the walk to the root (a clustering tree is no deeper than its rounds).
+__global__ void k_preorder(const uint32_t *__restrict__ left, const uint32_t *__restrict__ parent,
+                           const uint32_t *__restrict__ size, int n, int max_depth, uint32_t *__restrict__ pre)
+{
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n - 1) return;
+    uint32_t idx = 0, c = (uint32_t)v;
+    for (int guard = 0; guard <= max_depth; ++guard) {
+        uint32_t p = parent[c];
+        if (p == GRTX_NONE) break;
+        uint32_t L = left[p];
+        idx += 1u + ((L == c) ? 0u : ((L & GRTX_LEAF) ? 0u : size[L]));
+        c = p;
+    }
+    pre[v] = idx;
+}
+
+__global__ void k_permute_tree(const uint32_t *__restrict__ left, const uint32_t *__restrict__ right,
+                               const uint32_t *__restrict__ pre, int n, uint32_t *__restrict__ left_out,
+                               uint32_t *__restrict__ right_out, uint32_t *__restrict__ parent_out)
+{
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n - 1) return;
+    uint32_t d = pre[v];
+    uint32_t L = left[v], R = right[v];
+    L = (L & GRTX_LEAF) ? L : pre[L];
+    R = (R & GRTX_LEAF) ? R : pre[R];
+    left_out[d] = L;
+    right_out[d] = R;
+    parent_out[(L & GRTX_LEAF) ? (n - 1 + (L & ~GRTX_LEAF)) : L] = d;
+    parent_out[(R & GRTX_LEAF) ? (n - 1 + (R & ~GRTX_LEAF)) : R] = d;
+    if (d == 0) parent_out[0] = GRTX_NONE;
+}
+
 // One-leaf scene: a root whose second child is an empty box that no ray hits.
 __global__ void k_emit_single(const float *__restrict__ leaf_aabb, float4 *__restrict__ nodes)
 {
@@ -690,7 +870,59 @@ int build_tree(grtx_scene *sc, Alloc &A, float *leaf_aabb, int64_t n, uint32_t *
     return GRTX_OK;
 }
 
-int finish_tree(grtx_scene *sc, Alloc &A, const float *leaf_aabb_sorted, int64_t n, const float *leaf_slack = nullptr)
+// PLOC tree over n >= 2 boxes in order: left/right/parent in the radix tree's layout. One
+// host round trip per iteration reads the number of clusters left; at most n - 1 iterations
+// can happen (each merges at least one pair), and more fail the build.
+int ploc_tree(Alloc &A, const float *leaf_aabb, int64_t n, uint32_t *left, uint32_t *right, uint32_t *parent,
+              cudaStream_t s, int *iterations)
+{
+    float *cb[2];
+    uint32_t *id[2], *create, *keep, *lc, *rc, *small;
+    int *nn;
+    void *scan_tmp;
+    TRY(A.get(&cb[0], 6 * (size_t)n, true));
+    TRY(A.get(&cb[1], 6 * (size_t)n, true));
+    TRY(A.get(&id[0], n, true));
+    TRY(A.get(&id[1], n, true));
+    TRY(A.get(&nn, n, true));
+    TRY(A.get(&create, n, true));
+    TRY(A.get(&keep, n, true));
+    TRY(A.get(&lc, n - 1, true));
+    TRY(A.get(&rc, n - 1, true));
+    TRY(A.get(&small, 4, true));
+    TRY(A.get((char **)&scan_tmp, grtx_scan_temp_bytes(n), true));
+    GRTX_CUDA(cudaMemcpyAsync(cb[0], leaf_aabb, sizeof(float) * 6 * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    k_ploc_init<<<grtx_div_up(n, kThreads), kThreads, 0, s>>>(id[0], (int)n);
+    int64_t m = n, made = 0;
+    int cur = 0, it = 0;
+    while (m > 1) {
+        if (++it > n) return grtx_fail(GRTX_ERR_OVERFLOW_FATAL, "clustering did not converge");
+        int blocks = grtx_div_up(m, kPlocBlock);
+        k_ploc_nn<<<blocks, kPlocBlock, 0, s>>>(cb[cur], (int)m, nn);
+        k_ploc_flags<<<blocks, kPlocBlock, 0, s>>>(nn, (int)m, create, keep, small);
+        TRY(grtx_scan_exclusive(create, m, scan_tmp, s));
+        TRY(grtx_scan_exclusive(keep, m, scan_tmp, s));
+        k_ploc_totals<<<1, 1, 0, s>>>(create, keep, (int)m, small, small + 2);
+        k_ploc_merge<<<blocks, kPlocBlock, 0, s>>>(cb[cur], id[cur], nn, create, keep, (int)m, (uint32_t)made,
+                                                   cb[cur ^ 1], id[cur ^ 1], lc, rc);
+        GRTX_CHECK_LAUNCH("clustering");
+        uint32_t tot[2] = {0, 0};
+        GRTX_CUDA(cudaMemcpyAsync(tot, small + 2, sizeof(tot), cudaMemcpyDeviceToHost, s));
+        GRTX_CUDA(cudaStreamSynchronize(s));
+        if (tot[0] == 0 || (int64_t)tot[1] != m - (int64_t)tot[0] || made + tot[0] > n - 1)
+            return grtx_fail(GRTX_ERR_OVERFLOW_FATAL, "clustering made no progress");
+        made += tot[0];
+        m = tot[1];
+        cur ^= 1;
+    }
+    k_ploc_finish<<<grtx_div_up(n - 1, kThreads), kThreads, 0, s>>>(lc, rc, (int)n, left, right, parent);
+    GRTX_CHECK_LAUNCH("clustering finish");
+    if (iterations) *iterations = it;
+    return GRTX_OK;
+}
+
+int finish_tree(grtx_scene *sc, Alloc &A, const float *leaf_aabb_sorted, int64_t n, int builder,
+                const float *leaf_slack = nullptr)
 {
     cudaStream_t s = sc->stream;
     int64_t n_nodes = std::max<int64_t>(n - 1, 1);
@@ -711,7 +943,25 @@ int finish_tree(grtx_scene *sc, Alloc &A, const float *leaf_aabb_sorted, int64_t
         TRY(A.get(&cnt, n - 1, true));
         TRY(A.get(&node_aabb, 6 * (n - 1), true));
         GRTX_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (n - 1), s));
-        k_radix_tree<<<grtx_div_up(n - 1, kThreads), kThreads, 0, s>>>(sc->codes, (int)n, left, right, parent);
+        if (builder == GRTX_BUILDER_PLOC) {
+            // clustering numbers nodes by creation round, scattering subtrees over the array:
+            // renumber them depth-first for locality
+            uint32_t *l0, *r0, *p0, *sz, *pre;
+            TRY(A.get(&l0, n - 1, true));
+            TRY(A.get(&r0, n - 1, true));
+            TRY(A.get(&p0, 2 * n - 1, true));
+            TRY(A.get(&sz, n - 1, true));
+            TRY(A.get(&pre, n - 1, true));
+            int rounds = 0;
+            TRY(ploc_tree(A, leaf_aabb_sorted, n, l0, r0, p0, s, &rounds));
+            k_subtree_sizes<<<grtx_div_up(n, kThreads), kThreads, 0, s>>>(l0, r0, p0, (int)n, sz, cnt);
+            k_preorder<<<grtx_div_up(n - 1, kThreads), kThreads, 0, s>>>(l0, p0, sz, (int)n, rounds, pre);
+            k_permute_tree<<<grtx_div_up(n - 1, kThreads), kThreads, 0, s>>>(l0, r0, pre, (int)n, left, right, parent);
+            GRTX_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (n - 1), s));
+            GRTX_CHECK_LAUNCH("depth-first renumbering");
+        } else {
+            k_radix_tree<<<grtx_div_up(n - 1, kThreads), kThreads, 0, s>>>(sc->codes, (int)n, left, right, parent);
+        }
         k_refit<<<grtx_div_up(n, kThreads), kThreads, 0, s>>>(left, right, parent, leaf_aabb_sorted, (int)n,
                                                               node_aabb, cnt, leaf_slack, node_slack);
         k_depth<<<grtx_div_up(n, kThreads), kThreads, 0, s>>>(parent, (int)n, d_depth);
@@ -790,7 +1040,7 @@ int build_scene(const grtx_gaussians *g, const grtx_params *p, int form, grtx_sc
         GRTX_CUDA(cudaMemcpyAsync(sc->codes, codes, (size_t)nv * 8, cudaMemcpyDeviceToDevice, s));
         TRY(A.get(&sc->leaf_ids, nv, false));
         GRTX_CUDA(cudaMemcpyAsync(sc->leaf_ids, sc->gid, (size_t)nv * 4, cudaMemcpyDeviceToDevice, s));
-        TRY(finish_tree(sc, A, leaf_aabb, nv));
+        TRY(finish_tree(sc, A, leaf_aabb, nv, p->bvh_builder));
     } else {
         int dev = 0;
         GRTX_CUDA(cudaGetDevice(&dev));
@@ -825,7 +1075,7 @@ int build_scene(const grtx_gaussians *g, const grtx_params *p, int form, grtx_sc
         GRTX_CHECK_LAUNCH("gather triangles");
         TRY(A.get(&sc->codes, nt, false));
         GRTX_CUDA(cudaMemcpyAsync(sc->codes, tcodes, (size_t)nt * 8, cudaMemcpyDeviceToDevice, s));
-        TRY(finish_tree(sc, A, tri_aabb, nt, slack));
+        TRY(finish_tree(sc, A, tri_aabb, nt, p->bvh_builder, slack));
     }
     // world bounds of all leaves = union of the root's two child boxes
     float h_root[16];
@@ -940,6 +1190,15 @@ extern "C" GRTX_API int grtx_morton_codes_sized(const float *d_aabb, int64_t n, 
     return morton_codes_abi(d_aabb, n, d_bounds, d_bounds_out, d_codes, stream, true);
 }
 
+extern "C" GRTX_API int grtx_ploc_tree(const float *d_leaf_aabb, int64_t n, uint32_t *d_left, uint32_t *d_right,
+                                       uint32_t *d_parent, int *iterations, void *stream)
+{
+    if (n < 2 || n >= ((int64_t)1 << 30)) return grtx_fail(GRTX_ERR_INVALID_ARG, "n must be in [2, 2^30)");
+    if (!d_leaf_aabb || !d_left || !d_right || !d_parent) return grtx_fail(GRTX_ERR_INVALID_ARG, "NULL pointer");
+    Alloc A(S(stream));
+    return ploc_tree(A, d_leaf_aabb, n, d_left, d_right, d_parent, S(stream), iterations);
+}
+
 extern "C" GRTX_API int grtx_sort_pairs(uint64_t *d_keys, uint32_t *d_values, int64_t n, int key_bits, void *d_temp,
                                         size_t *temp_bytes, void *stream)
 {
@@ -993,6 +1252,8 @@ extern "C" GRTX_API int grtx_build_bvh(const grtx_gaussians *g, const grtx_param
     if (!(p->alpha_min > 0.f && p->alpha_min < 1.f)) return grtx_fail(GRTX_ERR_INVALID_ARG, "alpha_min must be in (0,1)");
     if (p->bvh_codes != GRTX_CODES_SIZED && p->bvh_codes != GRTX_CODES_CENTROID)
         return grtx_fail(GRTX_ERR_INVALID_ARG, "unknown bvh_codes");
+    if (p->bvh_builder != GRTX_BUILDER_PLOC && p->bvh_builder != GRTX_BUILDER_LBVH)
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "unknown bvh_builder");
     grtx_scene *sc = new (std::nothrow) grtx_scene();
     if (!sc) return grtx_fail(GRTX_ERR_OOM, "host allocation failed");
     sc->stream = S(stream);

@@ -10,7 +10,7 @@
 
 #define GRTX_LEAF 0x80000000u
 #define GRTX_NONE 0xFFFFFFFFu
-#define GRTX_STACK 64          // traversal stack entries per ray; the build rejects deeper trees
+#define GRTX_STACK 128         // traversal stack entries per ray; the build rejects deeper trees
 
 // Record the host-side text of an error for grtx_last_error() and return the status.
 int grtx_fail(int status, const std::string &msg);

@@ -22,7 +22,7 @@ int grtx_check_params(const grtx_params *p);
 
 namespace {
 
-constexpr int kWorldStack = 96;           // TLAS depth (<= 32) + object depth (<= 64)
+constexpr int kWorldStack = 32 + GRTX_STACK;   // TLAS depth (<= 32) + object depth (< GRTX_STACK)
 constexpr int kMaxTlasDepth = 32;
 
 struct InstRec {

@@ -98,7 +98,7 @@ class grtx_grads(C.Structure):
 class grtx_params(C.Structure):
     _fields_ = [("k", C.c_int32), ("traversal", C.c_int32), ("alpha_min", C.c_float), ("T_min", C.c_float),
                 ("alpha_max", C.c_float), ("bg", C.c_float * 3), ("ckpt_capacity", C.c_int32),
-                ("evict_capacity", C.c_int32), ("bvh_codes", C.c_int32)]
+                ("evict_capacity", C.c_int32), ("bvh_codes", C.c_int32), ("bvh_builder", C.c_int32)]
 
 
 class grtx_camera(C.Structure):
@@ -160,6 +160,7 @@ _SIGS = {
     "grtx_morton_codes_sized": (C.c_int, [_fp, C.c_int64, _fp, _fp, _fp, _fp]),
     "grtx_sort_pairs": (C.c_int, [_fp, _fp, C.c_int64, C.c_int, _fp, C.POINTER(C.c_size_t), _fp]),
     "grtx_radix_tree": (C.c_int, [_fp, C.c_int64, _fp, _fp, _fp, _fp]),
+    "grtx_ploc_tree": (C.c_int, [_fp, C.c_int64, _fp, _fp, _fp, C.POINTER(C.c_int), _fp]),
     "grtx_refit": (C.c_int, [_fp, _fp, _fp, _fp, C.c_int64, _fp, _fp, _fp]),
     "grtx_build_bvh": (C.c_int, [C.POINTER(grtx_gaussians), C.POINTER(grtx_params), C.c_int, _fp, C.POINTER(_fp)]),
     "grtx_scene_info_get": (C.c_int, [_fp, C.POINTER(grtx_scene_info)]),
@@ -242,12 +243,14 @@ def stream_handle(stream=None):
 
 
 BVH_CODES = {"sized": 0, "centroid": 1}
+BVH_BUILDERS = {"ploc": 0, "lbvh": 1}
 
 
 def make_params(k=16, traversal=0, alpha_min=0.01, T_min=1e-3, alpha_max=0.99, bg=(0.0, 0.0, 0.0),
-                ckpt_capacity=0, evict_capacity=0, bvh_codes=0) -> grtx_params:
+                ckpt_capacity=0, evict_capacity=0, bvh_codes=0, bvh_builder=0) -> grtx_params:
     p = grtx_params()
     p.bvh_codes = BVH_CODES[bvh_codes] if isinstance(bvh_codes, str) else int(bvh_codes)
+    p.bvh_builder = BVH_BUILDERS[bvh_builder] if isinstance(bvh_builder, str) else int(bvh_builder)
     p.k, p.traversal = int(k), int(traversal)
     p.alpha_min, p.T_min, p.alpha_max = alpha_min, T_min, alpha_max
     for i in range(3):
@@ -306,6 +309,13 @@ def grtx_morton_codes(aabb, bounds, codes, bounds_out=None, stream=None):
 def grtx_morton_codes_sized(aabb, bounds, codes, bounds_out=None, stream=None):
     check(lib().grtx_morton_codes_sized(ptr(aabb), int(aabb.shape[0]), ptr(bounds), ptr(bounds_out), ptr(codes),
                                         stream_handle(stream)), "grtx_morton_codes_sized")
+
+
+def grtx_ploc_tree(leaf_aabb, left, right, parent, stream=None) -> int:
+    it = C.c_int(0)
+    check(lib().grtx_ploc_tree(ptr(leaf_aabb), int(leaf_aabb.shape[0]), ptr(left), ptr(right), ptr(parent),
+                               C.byref(it), stream_handle(stream)), "grtx_ploc_tree")
+    return it.value
 
 
 def grtx_sort_pairs(keys, values, key_bits=64, stream=None):

@@ -33,7 +33,7 @@ class Scene:
     Sec. III-C)."""
 
     def __init__(self, means, log_scales, quats, logits, sh, sh_degree: int, form: str = "sphere",
-                 alpha_min: float = 0.01, stream=None, bvh_codes: str = "sized"):
+                 alpha_min: float = 0.01, stream=None, bvh_codes: str = "sized", bvh_builder: str = "ploc"):
         dev = torch.device("cuda", torch.cuda.current_device())
         self.tensors = tuple(_cuda_f32(a, dev) for a in (means, log_scales, quats, logits, sh))
         self.sh_degree = int(sh_degree)
@@ -41,12 +41,14 @@ class Scene:
         self.alpha_min = float(alpha_min)
         self._g = N.make_gaussians(*self.tensors, self.sh_degree)
         self.bvh_codes = bvh_codes
-        p = N.make_params(alpha_min=alpha_min, bvh_codes=bvh_codes)
+        self.bvh_builder = bvh_builder
+        p = N.make_params(alpha_min=alpha_min, bvh_codes=bvh_codes, bvh_builder=bvh_builder)
         self.handle = N.grtx_build_bvh(self._g, p, FORMS[form], stream)
 
     @classmethod
-    def from_params(cls, g, form="sphere", alpha_min=0.01, stream=None, bvh_codes="sized"):
-        return cls(g.means, g.log_scales, g.quats, g.logits, g.sh, g.sh_degree, form, alpha_min, stream, bvh_codes)
+    def from_params(cls, g, form="sphere", alpha_min=0.01, stream=None, bvh_codes="sized", bvh_builder="ploc"):
+        return cls(g.means, g.log_scales, g.quats, g.logits, g.sh, g.sh_degree, form, alpha_min, stream, bvh_codes,
+                   bvh_builder)
 
     @property
     def n(self) -> int:
@@ -167,14 +169,16 @@ def backward(scene: Scene, cam: dict | None, rgbT, dL_drgbT, rays=None, stream=N
 
 class RenderFunction(torch.autograd.Function):
     """Differentiable render: builds the BVH from the current parameters, traces forward,
-    and in backward re-traverses the same rounds to accumulate parameter gradients."""
+    and in backward re-traverses the same rounds to accumulate parameter gradients. The BVH
+    is rebuilt at every step, so the faster-to-build radix tree ("lbvh") is the default
+    here; opts may set bvh_builder / bvh_codes."""
 
     @staticmethod
     def forward(ctx, means, log_scales, quats, logits, sh, sh_degree, cam, opts):
-        scene = Scene(means.detach(), log_scales.detach(), quats.detach(), logits.detach(), sh.detach(), sh_degree,
-                      "sphere", opts.get("alpha_min", 0.01))
         o = dict(opts)
-        o.pop("alpha_min", None)
+        scene = Scene(means.detach(), log_scales.detach(), quats.detach(), logits.detach(), sh.detach(), sh_degree,
+                      "sphere", o.pop("alpha_min", 0.01), bvh_codes=o.pop("bvh_codes", "sized"),
+                      bvh_builder=o.pop("bvh_builder", "lbvh"))
         rgbT = render(scene, cam, **o)["rgbT"]
         ctx.scene, ctx.cam, ctx.opts = scene, cam, o
         ctx.save_for_backward(rgbT)

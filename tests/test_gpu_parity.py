@@ -152,10 +152,42 @@ def test_radix_tree_and_refit_bit_exact(n, dups):
             assert par[j] == i
 
 
+@pytest.mark.parametrize("n,dups", [(2, False), (3, True), (1000, False), (65_537, True), (400_001, False)])
+def test_ploc_tree_bit_exact(n, dups):
+    """The clustering tree (topology and node numbering) equals the oracle's, and refit over
+    it gives the oracle's boxes."""
+    boxes = _random_boxes(n, n + 5, dups)
+    order = np.argsort(O.morton_sized64(boxes, O.centroid_bounds(boxes)), kind="stable")
+    boxes = np.ascontiguousarray(boxes[order])
+    d = torch.from_numpy(boxes).cuda()
+    left = torch.empty(n - 1, dtype=torch.int32, device="cuda")
+    right = torch.empty(n - 1, dtype=torch.int32, device="cuda")
+    parent = torch.empty(2 * n - 1, dtype=torch.int32, device="cuda")
+    it = N.grtx_ploc_tree(d, left, right, parent)
+    torch.cuda.synchronize()
+    ol, orr, oit = O.ploc(boxes, radius=16)
+    assert it == oit
+    np.testing.assert_array_equal(left.cpu().numpy().view(np.uint32), ol)
+    np.testing.assert_array_equal(right.cpu().numpy().view(np.uint32), orr)
+    par = parent.cpu().numpy().view(np.uint32)
+    assert par[0] == 0xFFFFFFFF
+    for i in range(0, n - 1, max(1, (n - 1) // 2000)):
+        for c in (ol[i], orr[i]):
+            j = (n - 1 + (int(c) & 0x7FFFFFFF)) if c & 0x80000000 else int(c)
+            assert par[j] == i
+    if n >= 1000:
+        node_aabb = torch.empty((n - 1, 6), dtype=torch.float32, device="cuda")
+        cnt = torch.empty(n - 1, dtype=torch.int32, device="cuda")
+        N.grtx_refit(left, right, parent, d, node_aabb, cnt)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(node_aabb.cpu().numpy(), O.refit(ol, orr, boxes))
+
+
+@pytest.mark.parametrize("bvh_builder", ["ploc", "lbvh"])
 @pytest.mark.parametrize("bvh_codes", ["sized", "centroid"])
-def test_scene_tree_is_valid_lbvh(bvh_codes):
+def test_scene_tree_is_valid_lbvh(bvh_codes, bvh_builder):
     g = scenes.surface_scene(n=20000, seed=9)
-    sc = R.Scene.from_params(g, bvh_codes=bvh_codes)
+    sc = R.Scene.from_params(g, bvh_codes=bvh_codes, bvh_builder=bvh_builder)
     info = sc.info()
     nodes, ids, codes = sc.export()
     nodes = nodes.cpu().numpy()
@@ -372,21 +404,25 @@ def test_forward_proxy_form_parity(dense, k, traversal):
 
 @pytest.mark.parametrize("form", ["sphere", "proxy20"])
 def test_image_independent_of_bvh_codes(form):
-    """The tree shape changes the cost, never the result: the same Gaussians in the same
-    (t, id) order are blended with the same arithmetic, so the images are bitwise equal."""
+    """The tree shape (sort key and builder) changes the cost, never the result: the same
+    Gaussians in the same (t, id) order are blended with the same arithmetic, so the images are
+    bitwise equal."""
     g = scenes.outdoor_scene(n=30000, seed=12, size=16.0, n_clusters=30)
     cam = scenes.fisheye_camera(72, 40, (0.0, 1.7, 0.0), (1.0, 0.0, 0.0), 90.0)
     out, nodes = {}, {}
-    for codes in ("sized", "centroid"):
-        sc = R.Scene.from_params(g, form=form, bvh_codes=codes)
+    for codes, builder in (("sized", "ploc"), ("centroid", "ploc"), ("sized", "lbvh"), ("centroid", "lbvh")):
+        sc = R.Scene.from_params(g, form=form, bvh_codes=codes, bvh_builder=builder)
         r = R.render(sc, cam, k=8, want_n_blended=True, want_stats=True)
         torch.cuda.synchronize()
-        out[codes] = (r["rgbT"].cpu().numpy(), r["n_blended"].cpu().numpy())
-        nodes[codes] = N.stats_dict(r["stats"])["nodes"]
+        out[codes, builder] = (r["rgbT"].cpu().numpy(), r["n_blended"].cpu().numpy())
+        nodes[codes, builder] = N.stats_dict(r["stats"])["nodes"]
+        assert 0 < sc.info()["depth"] < 128
         sc.close()
-    np.testing.assert_array_equal(out["sized"][0], out["centroid"][0])
-    np.testing.assert_array_equal(out["sized"][1], out["centroid"][1])
-    assert out["sized"][1].sum() > 0 and nodes["sized"] != nodes["centroid"]
+    ref = out["sized", "ploc"]
+    for key, v in out.items():
+        np.testing.assert_array_equal(v[0], ref[0])
+        np.testing.assert_array_equal(v[1], ref[1])
+    assert ref[1].sum() > 0 and len(set(nodes.values())) == 4
 
 
 def test_forward_proxy_checkpoint_fallback_is_exact(dense):

@@ -789,3 +789,58 @@ def test_world_ids_and_images_of_separate_instances():
     np.testing.assert_array_equal(w["out"], ref["out"])
     m = ref["ids"] >= 0
     np.testing.assert_array_equal(w["ids"][m], ref["ids"][m] + 120)     # after the first instance's ids
+
+
+# ---------------------------------------------------------------- locally-ordered clustering
+
+
+def _cubes(xs):
+    xs = np.asarray(xs, np.float32)
+    return np.stack([xs, np.zeros_like(xs), np.zeros_like(xs), xs + 1, np.ones_like(xs), np.ones_like(xs)], 1)
+
+
+def test_ploc_merges_mutual_nearest_pairs_first():
+    """Unit cubes at x = 0, 1, 10, 11: the union of two cubes d apart has area 4 (d + 1) + 2,
+    so (0, 1) and (2, 3) are mutual nearest neighbours and merge first (nodes created in that
+    order), then the two pairs merge into the root."""
+    left, right, it = O.ploc(_cubes([0, 1, 10, 11]), radius=3)
+    L = O.LEAF
+    assert it == 2
+    assert list(left) == [2, L | 2, L | 0] and list(right) == [1, L | 3, L | 1]
+
+
+def test_ploc_breaks_ties_to_the_lower_index():
+    """Cubes at 0, 2, 4: cube 1 is equally near both others and picks cube 0; cube 2 is left
+    alone for one iteration."""
+    left, right, it = O.ploc(_cubes([0, 2, 4]), radius=2)
+    L = O.LEAF
+    assert it == 2 and list(left) == [1, L | 0] and list(right) == [L | 2, L | 1]
+
+
+def test_ploc_radius_limits_the_search():
+    """With radius 1 only neighbours in order are seen: cubes at 0, 9, 10, 19 with r = 1 pair
+    (1, 2) first; with r = 3 as well (the nearest pair anywhere)."""
+    L = O.LEAF
+    for r in (1, 3):
+        left, right, it = O.ploc(_cubes([0, 9, 10, 19]), radius=r)
+        assert [left[2], right[2]] == [L | 1, L | 2]       # the first node created
+
+
+@pytest.mark.parametrize("n,dups", [(2, False), (3, True), (50, False), (777, True)])
+def test_ploc_builds_a_valid_binary_tree(n, dups):
+    rng = np.random.default_rng(n)
+    c = rng.uniform(-1, 1, (n, 3)).astype(np.float32)
+    if dups:
+        c[n // 2:] = c[: n - n // 2]
+    e = rng.uniform(0, 0.1, (n, 3)).astype(np.float32)
+    boxes = np.concatenate([c - e, c + e], 1)
+    left, right, it = O.ploc(boxes, radius=4)
+    seen_leaf = np.zeros(n, int)
+    seen_node = np.zeros(n - 1, int)
+    for ch in np.concatenate([left, right]):
+        if ch & O.LEAF:
+            seen_leaf[int(ch) & 0x7FFFFFFF] += 1
+        else:
+            seen_node[ch] += 1
+    assert np.all(seen_leaf == 1) and seen_node[0] == 0 and np.all(seen_node[1:] == 1)
+    assert 1 <= it <= n - 1
