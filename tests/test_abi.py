@@ -60,3 +60,35 @@ def test_host_side_argument_errors(lib):
     assert lib.grtx_radix_tree(None, 1, None, None, None, None) == 1
     assert lib.grtx_server_submit(None, None, 0) == 1
     assert lib.grtx_server_create(None, 0, None, 0, 0, None, None) == 1
+
+
+def test_host_side_errors_of_the_extensions(lib):
+    """Argument checks of the builder, world, template and secondary-ray entry points return
+    GRTX_ERR_INVALID_ARG before any device work."""
+    it = C.c_int(0)
+    assert lib.grtx_ploc_tree(None, 1, None, None, None, C.byref(it), None) == 1       # n < 2
+    assert lib.grtx_ploc_tree(None, 10, None, None, None, C.byref(it), None) == 1      # NULL arrays
+    assert lib.grtx_morton_codes_sized(None, -1, None, None, None, None) == 1
+    n = C.c_int(0)
+    assert lib.grtx_template_mesh(0, None, C.byref(n)) == 1                            # not an icosphere form
+    assert lib.grtx_template_mesh(2, None, C.byref(n)) == 0 and n.value == 20
+    assert lib.grtx_template_mesh(3, None, C.byref(n)) == 0 and n.value == 80
+    w = C.c_void_p()
+    assert lib.grtx_world_create(None, 0, None, C.byref(w)) == 1 and not w.value
+    inst = (N.grtx_instance * 1)()
+    assert lib.grtx_world_create(inst, 1, None, C.byref(w)) == 1                        # NULL scene
+    assert b"scene is NULL" in lib.grtx_last_error()
+    assert lib.grtx_world_update(None, inst, 1, None) == 1
+    assert lib.grtx_world_trace_forward(None, None, None, None, None) == 1
+    lib.grtx_world_destroy(None)
+    cam = N.grtx_camera()
+    cam.type, cam.width, cam.height, cam.fov, cam.t_far = 0, 4, 4, 1.0, 1e30
+    mirrors = (N.grtx_mirror * 1)()
+    glass = (N.grtx_glass * 1)()
+    nulls = [None] * 10
+    assert lib.grtx_secondary_rays(C.byref(cam), mirrors, 17, glass, 0, *nulls, None) == 1   # too many objects
+    assert lib.grtx_secondary_rays(C.byref(cam), mirrors, 0, glass, 1, *nulls, None) == 1    # radius 0
+    assert b"glass" in lib.grtx_last_error()
+    p = N.make_params(bvh_builder=7)
+    g = N.grtx_gaussians()
+    assert lib.grtx_build_bvh(C.byref(g), C.byref(p), 0, None, C.byref(C.c_void_p())) == 1
