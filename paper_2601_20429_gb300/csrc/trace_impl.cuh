@@ -538,6 +538,166 @@ __device__ __forceinline__ bool trace_round(const TraceArgs &a, const SceneRef &
 }
 
 // ------------------------------------------------------------------------------------------
+// Round 1 of a warp's rays as one packet. Every ray of a warp starts its first round at the
+// root (Sec. III-A), and the rays of an 8x4 pixel tile need nearly the same nodes, so the warp
+// walks one node sequence -- the union of what its rays need -- loading each node once for all
+// lanes instead of once per lane, with no divergence between node and leaf steps. Each lane
+// keeps its own entry test against its t_max, its k-buffer, checkpoint and eviction lists,
+// exactly as in trace_round, so every ray's round ends with the same k-buffer (the traversal
+// order, hence the checkpoint lists, may differ). The warp's stack (kPacketStack entries of
+// (node, parent << 1 | child slot, lane mask), in shared memory) holds far children with the
+// lanes that want them; a popped node's entry distance is recomputed per lane from its box in
+// the parent. Every lane of the warp must call this together (full-mask ballots); lanes
+// without a ray pass valid = false. lane_ok is false for a lane whose lists overflowed, and for
+// every lane if the warp's stack would overflow (returns false then): such a lane redoes the
+// round from the root on its own, as after any capacity overflow in trace_ray.
+// ------------------------------------------------------------------------------------------
+constexpr int kPacketStack = 64;
+
+template <int K, int FORM, bool INSTR>
+__device__ __forceinline__ bool packet_round(const TraceArgs &a, const SceneRef &sc, bool valid, uint4 *pst, float3 o,
+                                             float3 d, float3 inv, float inv_len, float tn, float tf, bool ckpt,
+                                             uint2 *__restrict__ dst, int &n_dst, uint2 *__restrict__ ev, int &n_ev,
+                                             KBuf<K> &kb, Counters &cnt, bool &lane_ok)
+{
+    const unsigned full = 0xffffffffu;
+    const size_t S = (size_t)a.n_slots;
+    const int lane = threadIdx.x & 31;
+    const float Lt = tn;
+    const uint32_t Li = GRTX_NONE;
+    float tmax = kb.tmax;
+    n_dst = 0;
+    n_ev = 0;
+    lane_ok = true;
+    if (!sc.has_tree) return true;                      // nothing to traverse (uniform)
+    int sp = 0;
+    uint32_t ref = 0u, parent = GRTX_NONE, slot = 0u;
+    unsigned m = __ballot_sync(full, valid);
+    float te = tn;
+    bool have_te = true;
+    for (;;) {
+        bool in = (m >> lane) & 1u;
+        if (!have_te && in) {                           // a popped node: entry from the parent's box
+            const float4 *pn = sc.nodes + 4 * (size_t)parent;
+            float x;
+            if (slot == 0u) {
+                float4 n0 = __ldg(pn), n1 = __ldg(pn + 1);
+                slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, o, inv, tn, tf, te, x);
+            } else {
+                float4 n1 = __ldg(pn + 1), n2 = __ldg(pn + 2);
+                slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, o, inv, tn, tf, te, x);
+            }
+            if (FORM == FORM_PROXY) te = fmaf(-(slot == 0u ? __ldg(pn + 3).z : __ldg(pn + 3).w), inv_len, te);
+        }
+        bool go = in && lane_ok && !(te > tmax);
+        if (in && lane_ok && te > tmax && ckpt) {       // fails the t_max test: checkpoint it
+            if (n_dst >= a.ckpt_cap) {
+                lane_ok = false;
+            } else {
+                dst[(size_t)n_dst * S] = make_uint2(ref, __float_as_uint(te));
+                ++n_dst;
+                if (INSTR) cnt.ckpt++;
+            }
+        }
+        m = __ballot_sync(full, go);
+        bool pop = true;
+        if (m) {
+            if (ref & GRTX_LEAF) {
+                if (go) {
+                    uint32_t idx = ref & ~GRTX_LEAF;
+                    if (INSTR) cnt.leaves++;
+                    uint32_t gi;
+                    bool touch = true;
+                    if (FORM == FORM_PROXY) {
+                        const float4 *tr = sc.tris + 3 * (size_t)idx;
+                        float4 v0 = __ldg(tr), v1 = __ldg(tr + 1), v2 = __ldg(tr + 2);
+                        gi = __float_as_uint(v0.w);
+                        touch = tri_hit(v0, v1, v2, o, d) > tn;
+                    } else {
+                        gi = idx;
+                        if (FORM == FORM_ICO) touch = template_touch<INSTR>(sc, gi, o, d, tn, cnt);
+                    }
+                    float t, D2, w[3];
+                    if (touch && sphere_test(sc.geom + 4 * (size_t)gi, o, d, t, D2, w) && D2 <= 1.0f && t > tn &&
+                        t <= tf && key_after(t, gi, Lt, Li) && (FORM != FORM_PROXY || !kb.contains(t, gi))) {
+                        float ct = t;
+                        uint32_t ci = gi;
+                        if (kb.insert(ct, ci) && ckpt) {
+                            if (n_ev >= a.evict_cap) {
+                                lane_ok = false;
+                            } else {
+                                ev[(size_t)n_ev * S] = make_uint2(__float_as_uint(ct), ci);
+                                ++n_ev;
+                                if (INSTR) cnt.evictions++;
+                            }
+                        }
+                        tmax = kb.tmax;
+                    }
+                }
+            } else {
+                const float4 *nd = sc.nodes + 4 * (size_t)ref;
+                float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+                uint32_t c0 = __float_as_uint(n3.x), c1 = __float_as_uint(n3.y);
+                bool h0 = false, h1 = false, near0 = true;
+                float e0 = 0.f, e1 = 0.f;
+                if (go) {
+                    if (INSTR) cnt.nodes++;
+                    float x0, x1;
+                    slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, o, inv, tn, tf, e0, x0);
+                    slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, o, inv, tn, tf, e1, x1);
+                    h0 = e0 <= x0 && !(x0 < Lt);
+                    h1 = e1 <= x1 && !(x1 < Lt) && c1 != GRTX_NONE;
+                    near0 = e0 <= e1;
+                    if (FORM == FORM_PROXY) {             // t_max tests at entry - slack (see trace_round)
+                        e0 = fmaf(-n3.z, inv_len, e0);
+                        e1 = fmaf(-n3.w, inv_len, e1);
+                    }
+                }
+                unsigned m0 = __ballot_sync(full, h0), m1 = __ballot_sync(full, h1);
+                if (m0 && m1) {
+                    unsigned both = m0 & m1, vote = __ballot_sync(full, h0 && h1 && near0);
+                    bool n0first = both ? (2 * __popc(vote) >= __popc(both)) : (__popc(m0) >= __popc(m1));
+                    if (sp == kPacketStack) {                 // too deep for the warp's stack
+                        lane_ok = false;
+                        return false;
+                    }
+                    if (lane == 0)
+                        pst[sp] = make_uint4(n0first ? c1 : c0, (ref << 1) | (n0first ? 1u : 0u), n0first ? m1 : m0, 0u);
+                    ++sp;
+                    __syncwarp(full);
+                    parent = ref;
+                    slot = n0first ? 0u : 1u;
+                    m = n0first ? m0 : m1;
+                    te = n0first ? e0 : e1;
+                    ref = n0first ? c0 : c1;
+                    have_te = true;
+                    pop = false;
+                } else if (m0 || m1) {
+                    parent = ref;
+                    slot = m0 ? 0u : 1u;
+                    m = m0 ? m0 : m1;
+                    te = m0 ? e0 : e1;
+                    ref = m0 ? c0 : c1;
+                    have_te = true;
+                    pop = false;
+                }
+            }
+        }
+        if (pop) {
+            if (sp == 0) break;
+            --sp;
+            uint4 v = pst[sp];
+            ref = v.x;
+            parent = v.y >> 1;
+            slot = v.y & 1u;
+            m = v.z;
+            have_te = false;
+        }
+    }
+    return true;
+}
+
+// ------------------------------------------------------------------------------------------
 // Blending (Sec. II-B Eq. volume-render) and its derivative.
 // ------------------------------------------------------------------------------------------
 struct BlendState {
@@ -679,7 +839,8 @@ __device__ __forceinline__ void blend_one(const TraceArgs &a, const SceneRef &sc
 template <int K, int FORM, bool INSTR, bool BWD>
 __device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc, float4 *__restrict__ out, int slot,
                                           int64_t pix, float3 o, float3 d, float tn, float tf, KBuf<K> &kb,
-                                          Counters &cnt)
+                                          Counters &cnt, bool r1_done = false, bool r1_ok = true, int r1_n_dst = 0,
+                                          int r1_n_ev = 0)
 {
     const size_t S = (size_t)a.n_slots;
     float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
@@ -705,9 +866,10 @@ __device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc
     int n_src = 0, n_ev = 0, nb = 0;
     uint2 *src = a.ck0 + slot, *dst = a.ck1 + slot, *ev = a.ev + slot;
     bool done = !sc.has_tree;
+    bool first_round = true;
     while (!done) {
         if (INSTR) cnt.rounds++;
-        kb.clear();
+        if (!(r1_done && first_round)) kb.clear();
         if (ckpt && n_ev > 0) {            // raygen: closest evicted hits -> k-buffer
             int w = 0;
             for (int e = 0; e < n_ev; ++e) {
@@ -725,8 +887,16 @@ __device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc
             n_ev = w;
         }
         int n_dst = 0;
-        if (!trace_round<K, FORM, INSTR>(a, sc, o, d, inv, inv_len, tn, tf, Lt, Li, ckpt, from_root, src, n_src, dst, n_dst,
-                                          ev, n_ev, kb, cnt)) {
+        bool round_ok;
+        if (r1_done && first_round) {                  // round 1 was traced as the warp's packet
+            round_ok = r1_ok;
+            n_dst = r1_n_dst;
+            n_ev = r1_n_ev;
+        } else {
+            round_ok = trace_round<K, FORM, INSTR>(a, sc, o, d, inv, inv_len, tn, tf, Lt, Li, ckpt, from_root, src, n_src,
+                                                   dst, n_dst, ev, n_ev, kb, cnt);
+        }
+        if (!round_ok) {
             // a capacity was exceeded: redo this round from the root and stay in restart mode
             if (INSTR) cnt.fallbacks++;
             ckpt = false;
@@ -747,6 +917,7 @@ __device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc
             ++nb;
             if (st.T < a.T_min) { done = true; break; }
         }
+        first_round = false;
         if (done || kb.n < K) break;
         Lt = kb.T(K - 1);
         Li = kb.I(K - 1);
@@ -760,6 +931,30 @@ __device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc
     if (INSTR && a.n_blended) a.n_blended[pix] = nb;
 }
 
+// The rays of one warp: round 1 as the warp's packet, then each ray's later rounds on its
+// own. Every lane of the warp calls this together; lanes without a ray pass valid = false.
+template <int K, int FORM, bool INSTR, bool BWD>
+__device__ __forceinline__ void trace_warp(const TraceArgs &a, const SceneRef &sc, float4 *__restrict__ out, int slot,
+                                           bool valid, int64_t pix, float3 o, float3 d, float tn, float tf, KBuf<K> &kb,
+                                           Counters &cnt, uint4 *pst)
+{
+    if (!valid) {
+        o = make_float3(0.f, 0.f, 0.f);
+        d = make_float3(0.f, 0.f, 1.f);
+        tn = tf = 0.f;
+    }
+    float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+    float inv_len = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+    kb.clear();
+    int n_dst = 0, n_ev = 0;
+    bool lane_ok = true;
+    packet_round<K, FORM, INSTR>(a, sc, valid, pst, o, d, inv, inv_len, tn, tf, a.traversal == GRTX_TRAVERSAL_CHECKPOINT,
+                                 a.ck1 + slot, n_dst, a.ev + slot, n_ev, kb, cnt, lane_ok);
+    // a lane whose packet could not finish (lists or the warp's stack overflowed) redoes round 1
+    // from the root on its own, as after any capacity overflow
+    if (valid) trace_ray<K, FORM, INSTR, BWD>(a, sc, out, slot, pix, o, d, tn, tf, kb, cnt, true, lane_ok, n_dst, n_ev);
+}
+
 // Resident blocks per SM the trace kernels are compiled for. The traversal is latency-bound,
 // so occupancy pays even at the cost of a few spilled registers (measured on GB300: 8 blocks of
 // 128 threads is the best forward setting for k <= 16; the k = 32 k-buffer's 32 KB of shared
@@ -771,6 +966,7 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, BWD)) k_trace(Trac
 {
     __shared__ float s_kt[K * kBlock];
     __shared__ uint32_t s_ki[K * kBlock];
+    __shared__ uint4 s_pst[kBlock / 32][kPacketStack];
     const int slot = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     KBuf<K> kb;
@@ -786,10 +982,9 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, BWD)) k_trace(Trac
         int64_t pix;
         float3 o, d;
         float tn, tf;
-        if (make_ray(a.cam, base + lane, pix, o, d, tn, tf)) {
-            ++rays;
-            trace_ray<K, FORM, INSTR, BWD>(a, a.sc, a.rgbT, slot, pix, o, d, tn, tf, kb, cnt);
-        }
+        bool valid = make_ray(a.cam, base + lane, pix, o, d, tn, tf);
+        rays += valid;
+        trace_warp<K, FORM, INSTR, BWD>(a, a.sc, a.rgbT, slot, valid, pix, o, d, tn, tf, kb, cnt, s_pst[threadIdx.x >> 5]);
         __syncwarp();
     }
     if (INSTR && a.stats) {
@@ -811,6 +1006,7 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, false)) k_serve(Tr
 {
     __shared__ float s_kt[K * kBlock];
     __shared__ uint32_t s_ki[K * kBlock];
+    __shared__ uint4 s_pst[kBlock / 32][kPacketStack];
     const int slot = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     KBuf<K> kb;
@@ -834,8 +1030,9 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, false)) k_serve(Tr
         int64_t pix;
         float3 o, d;
         float tn, tf;
-        if (make_ray(cam, item, pix, o, d, tn, tf))
-            trace_ray<K, FORM_SPHERE, false, false>(a, sc, sg.out, slot, pix, o, d, tn, tf, kb, cnt);
+        bool valid = make_ray(cam, item, pix, o, d, tn, tf);
+        trace_warp<K, FORM_SPHERE, false, false>(a, sc, sg.out, slot, valid, pix, o, d, tn, tf, kb, cnt,
+                                                 s_pst[threadIdx.x >> 5]);
         __syncwarp();
     }
 }
