@@ -196,11 +196,168 @@ __device__ __forceinline__ bool world_round(const WorldArgs &W, float3 o, float3
     return true;
 }
 
+// Round 1 of a warp's rays through the world as one packet (see packet_round): the warp walks
+// one sequence of TLAS and object nodes, each lane with its own ray in the current object's
+// frame, entry tests, k-buffer and lists. Stack entries carry the instance of object-level
+// nodes. Every lane of the warp calls this together; lanes without a ray pass valid = false.
+template <int K, bool INSTR>
+__device__ __forceinline__ void world_packet_round(const WorldArgs &W, bool valid, uint4 *pst, float3 o, float3 d,
+                                                   float3 inv, float tn, float tf, bool ckpt, uint4 *__restrict__ dst,
+                                                   int &n_dst, uint2 *__restrict__ ev, int &n_ev, KBuf<K> &kb,
+                                                   Counters &cnt, bool &lane_ok)
+{
+    const unsigned full = 0xffffffffu;
+    const size_t S = (size_t)W.a.n_slots;
+    const int lane = threadIdx.x & 31;
+    const float Lt = tn;
+    const uint32_t Li = GRTX_NONE;
+    float tmax = kb.tmax;
+    n_dst = 0;
+    n_ev = 0;
+    lane_ok = true;
+    if (W.n_inst == 0) return;
+    int sp = 0;
+    uint32_t ref = 0u, parent = GRTX_NONE, slot = 0u, inst = GRTX_NONE, cur = GRTX_NONE;
+    unsigned m = __ballot_sync(full, valid);
+    float te = tn;
+    bool have_te = true;
+    float3 ob = o, db = d, ib = inv;
+    const float4 *nodes = W.tl_nodes, *geom = nullptr;
+    uint32_t base = 0;
+    for (;;) {
+        if (inst != cur) {                                  // another level: map each lane's ray
+            cur = inst;
+            if (inst == GRTX_NONE) {
+                ob = o;
+                db = d;
+                ib = inv;
+                nodes = W.tl_nodes;
+            } else {
+                const InstRec &I = W.inst[inst];
+                to_object(I, o, d, ob, db);
+                ib = make_float3(safe_rcp(db.x), safe_rcp(db.y), safe_rcp(db.z));
+                nodes = I.sc.nodes;
+                geom = I.sc.geom;
+                base = I.leaf_base;
+            }
+        }
+        bool in = (m >> lane) & 1u;
+        if (!have_te && in) {                               // a popped node: entry from the parent's box
+            const float4 *pn = nodes + 4 * (size_t)parent;
+            float x;
+            if (slot == 0u) {
+                float4 n0 = __ldg(pn), n1 = __ldg(pn + 1);
+                slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, ob, ib, tn, tf, te, x);
+            } else {
+                float4 n1 = __ldg(pn + 1), n2 = __ldg(pn + 2);
+                slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, ob, ib, tn, tf, te, x);
+            }
+        }
+        bool go = in && lane_ok && !(te > tmax);
+        if (in && lane_ok && te > tmax && ckpt) {
+            if (n_dst >= W.a.ckpt_cap) {
+                lane_ok = false;
+            } else {
+                dst[(size_t)n_dst * S] = make_uint4(ref, __float_as_uint(te), inst, 0u);
+                ++n_dst;
+                if (INSTR) cnt.ckpt++;
+            }
+        }
+        m = __ballot_sync(full, go);
+        bool pop = true;
+        if (m) {
+            if (ref & GRTX_LEAF) {
+                if (inst == GRTX_NONE) {                    // TLAS leaf: descend into the object's root
+                    inst = ref & ~GRTX_LEAF;
+                    ref = 0u;
+                    have_te = true;
+                    continue;
+                }
+                if (go) {
+                    uint32_t gi = ref & ~GRTX_LEAF;
+                    if (INSTR) cnt.leaves++;
+                    float t, D2, w[3];
+                    uint32_t key = base + gi;
+                    if (sphere_test(geom + 4 * (size_t)gi, ob, db, t, D2, w) && D2 <= 1.0f && t > tn && t <= tf &&
+                        key_after(t, key, Lt, Li)) {
+                        float ct = t;
+                        uint32_t ci = key;
+                        if (kb.insert(ct, ci) && ckpt) {
+                            if (n_ev >= W.a.evict_cap) {
+                                lane_ok = false;
+                            } else {
+                                ev[(size_t)n_ev * S] = make_uint2(__float_as_uint(ct), ci);
+                                ++n_ev;
+                                if (INSTR) cnt.evictions++;
+                            }
+                        }
+                        tmax = kb.tmax;
+                    }
+                }
+            } else {
+                const float4 *nd = nodes + 4 * (size_t)ref;
+                float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+                uint32_t c0 = __float_as_uint(n3.x), c1 = __float_as_uint(n3.y);
+                bool h0 = false, h1 = false, near0 = true;
+                float e0 = 0.f, e1 = 0.f;
+                if (go) {
+                    if (INSTR) cnt.nodes++;
+                    float x0, x1;
+                    slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, ob, ib, tn, tf, e0, x0);
+                    slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, ob, ib, tn, tf, e1, x1);
+                    h0 = e0 <= x0 && !(x0 < Lt);
+                    h1 = e1 <= x1 && !(x1 < Lt) && c1 != GRTX_NONE;
+                    near0 = e0 <= e1;
+                }
+                unsigned m0 = __ballot_sync(full, h0), m1 = __ballot_sync(full, h1);
+                if (m0 && m1) {
+                    unsigned both = m0 & m1, vote = __ballot_sync(full, h0 && h1 && near0);
+                    bool n0first = both ? (2 * __popc(vote) >= __popc(both)) : (__popc(m0) >= __popc(m1));
+                    if (sp == kPacketStack) {                 // too deep for the warp's stack
+                        lane_ok = false;
+                        return;
+                    }
+                    if (lane == 0)
+                        pst[sp] = make_uint4(n0first ? c1 : c0, (ref << 1) | (n0first ? 1u : 0u), n0first ? m1 : m0, inst);
+                    ++sp;
+                    __syncwarp(full);
+                    parent = ref;
+                    slot = n0first ? 0u : 1u;
+                    m = n0first ? m0 : m1;
+                    te = n0first ? e0 : e1;
+                    ref = n0first ? c0 : c1;
+                    have_te = true;
+                    pop = false;
+                } else if (m0 || m1) {
+                    parent = ref;
+                    slot = m0 ? 0u : 1u;
+                    m = m0 ? m0 : m1;
+                    te = m0 ? e0 : e1;
+                    ref = m0 ? c0 : c1;
+                    have_te = true;
+                    pop = false;
+                }
+            }
+        }
+        if (pop) {
+            if (sp == 0) break;
+            --sp;
+            uint4 v = pst[sp];
+            ref = v.x;
+            parent = v.y >> 1;
+            slot = v.y & 1u;
+            m = v.z;
+            inst = v.w;
+            have_te = false;
+        }
+    }
+}
+
 // One ray through the world: the round loop of trace_ray with world_round and blending in
 // the frame of each Gaussian's object.
 template <int K, bool INSTR>
 __device__ __forceinline__ void world_ray(const WorldArgs &W, int slot, int64_t pix, float3 o, float3 d, float tn,
-                                          float tf, KBuf<K> &kb, Counters &cnt)
+                                          float tf, KBuf<K> &kb, Counters &cnt, bool r1_ok, int r1_n_dst, int r1_n_ev)
 {
     const TraceArgs &a = W.a;
     const size_t S = (size_t)a.n_slots;
@@ -216,9 +373,10 @@ __device__ __forceinline__ void world_ray(const WorldArgs &W, int slot, int64_t 
     uint4 *src = W.wck0 + slot, *dst = W.wck1 + slot;
     uint2 *ev = a.ev + slot;
     bool done = W.n_inst == 0;
+    bool first_round = true;
     while (!done) {
         if (INSTR) cnt.rounds++;
-        kb.clear();
+        if (!first_round) kb.clear();
         if (ckpt && n_ev > 0) {
             int w = 0;
             for (int e = 0; e < n_ev; ++e) {
@@ -233,8 +391,16 @@ __device__ __forceinline__ void world_ray(const WorldArgs &W, int slot, int64_t 
             n_ev = w;
         }
         int n_dst = 0;
-        if (!world_round<K, INSTR>(W, o, d, inv, tn, tf, Lt, Li, ckpt, from_root, src, n_src, dst, n_dst, ev, n_ev,
-                                   kb, cnt)) {
+        bool round_ok;
+        if (first_round) {                             // round 1 was traced as the warp's packet
+            round_ok = r1_ok;
+            n_dst = r1_n_dst;
+            n_ev = r1_n_ev;
+        } else {
+            round_ok = world_round<K, INSTR>(W, o, d, inv, tn, tf, Lt, Li, ckpt, from_root, src, n_src, dst, n_dst, ev,
+                                             n_ev, kb, cnt);
+        }
+        if (!round_ok) {
             if (INSTR) cnt.fallbacks++;
             ckpt = false;
             from_root = true;
@@ -262,6 +428,7 @@ __device__ __forceinline__ void world_ray(const WorldArgs &W, int slot, int64_t 
                 break;
             }
         }
+        first_round = false;
         if (done || kb.n < K) break;
         Lt = kb.T(K - 1);
         Li = kb.I(K - 1);
@@ -282,6 +449,7 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, false)) k_trace_wo
 {
     __shared__ float s_kt[K * kBlock];
     __shared__ uint32_t s_ki[K * kBlock];
+    __shared__ uint4 s_pst[kBlock / 32][kPacketStack];
     const int slot = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     KBuf<K> kb;
@@ -297,9 +465,23 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, false)) k_trace_wo
         int64_t pix;
         float3 o, d;
         float tn, tf;
-        if (make_ray(W.a.cam, b + lane, pix, o, d, tn, tf)) {
+        bool valid = make_ray(W.a.cam, b + lane, pix, o, d, tn, tf);
+        if (!valid) {
+            o = make_float3(0.f, 0.f, 0.f);
+            d = make_float3(0.f, 0.f, 1.f);
+            tn = tf = 0.f;
+        }
+        // round 1 of the warp's rays as one packet (every lane takes part), later rounds per ray
+        float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+        kb.clear();
+        int n_dst = 0, n_ev = 0;
+        bool lane_ok = true;
+        world_packet_round<K, INSTR>(W, valid, s_pst[threadIdx.x >> 5], o, d, inv, tn, tf,
+                                     W.a.traversal == GRTX_TRAVERSAL_CHECKPOINT, W.wck1 + slot, n_dst, W.a.ev + slot,
+                                     n_ev, kb, cnt, lane_ok);
+        if (valid) {
             ++rays;
-            world_ray<K, INSTR>(W, slot, pix, o, d, tn, tf, kb, cnt);
+            world_ray<K, INSTR>(W, slot, pix, o, d, tn, tf, kb, cnt, lane_ok, n_dst, n_ev);
         }
         __syncwarp();
     }
