@@ -538,8 +538,9 @@ __device__ __forceinline__ bool trace_round(const TraceArgs &a, const SceneRef &
 }
 
 // ------------------------------------------------------------------------------------------
-// Round 1 of a warp's rays as one packet. Every ray of a warp starts its first round at the
-// root (Sec. III-A), and the rays of an 8x4 pixel tile need nearly the same nodes, so the warp
+// A round of a warp's rays from the root as one packet (round 1, and every round when
+// restarting). Every ray of a warp starts its first round at the root (Sec. III-A), and the
+// rays of an 8x4 pixel tile need nearly the same nodes, so the warp
 // walks one node sequence -- the union of what its rays need -- loading each node once for all
 // lanes instead of once per lane, with no divergence between node and leaf steps. Each lane
 // keeps its own entry test against its t_max, its k-buffer, checkpoint and eviction lists,
@@ -556,15 +557,14 @@ constexpr int kPacketStack = 64;
 
 template <int K, int FORM, bool INSTR>
 __device__ __forceinline__ bool packet_round(const TraceArgs &a, const SceneRef &sc, bool valid, uint4 *pst, float3 o,
-                                             float3 d, float3 inv, float inv_len, float tn, float tf, bool ckpt,
-                                             uint2 *__restrict__ dst, int &n_dst, uint2 *__restrict__ ev, int &n_ev,
-                                             KBuf<K> &kb, Counters &cnt, bool &lane_ok)
+                                             float3 d, float3 inv, float inv_len, float tn, float tf, float Lt,
+                                             uint32_t Li, bool ckpt, uint2 *__restrict__ dst, int &n_dst,
+                                             uint2 *__restrict__ ev, int &n_ev, KBuf<K> &kb, Counters &cnt,
+                                             bool &lane_ok)
 {
     const unsigned full = 0xffffffffu;
     const size_t S = (size_t)a.n_slots;
     const int lane = threadIdx.x & 31;
-    const float Lt = tn;
-    const uint32_t Li = GRTX_NONE;
     float tmax = kb.tmax;
     n_dst = 0;
     n_ev = 0;
@@ -931,6 +931,72 @@ __device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc
     if (INSTR && a.n_blended) a.n_blended[pix] = nb;
 }
 
+// The rays of one warp with restart traversal (Sec. III-A): every round from the root as the
+// warp's packet over the lanes still tracing, each lane culling with its own last key L. Once
+// rays travel as packets, the upper levels a restart revisits cost one broadcast load per warp,
+// which is what makes this the faster restart on the SMs. A lane whose packet could not finish
+// (the warp's stack would overflow) traces that round on its own. Every lane calls this
+// together; lanes without a ray pass valid = false.
+template <int K, int FORM, bool INSTR>
+__device__ __forceinline__ void trace_warp_restart(const TraceArgs &a, const SceneRef &sc, float4 *__restrict__ out,
+                                                   int slot, bool valid, int64_t pix, float3 o, float3 d, float tn,
+                                                   float tf, KBuf<K> &kb, Counters &cnt, uint4 *pst)
+{
+    if (!valid) {
+        o = make_float3(0.f, 0.f, 0.f);
+        d = make_float3(0.f, 0.f, 1.f);
+        tn = tf = 0.f;
+    }
+    float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+    float nrm = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+    float3 dn = make_float3(d.x * nrm, d.y * nrm, d.z * nrm);
+    BlendState st;
+    st.C[0] = st.C[1] = st.C[2] = 0.f;
+    st.T = 1.f;
+    float Lt = tn;
+    uint32_t Li = GRTX_NONE;
+    int nb = 0;
+    bool done = !valid || !sc.has_tree;
+    while (__any_sync(0xffffffffu, !done)) {
+        if (!done) {
+            if (INSTR) cnt.rounds++;
+            kb.clear();
+        }
+        int n_dst = 0, n_ev = 0;
+        bool lane_ok = true;
+        packet_round<K, FORM, INSTR>(a, sc, !done, pst, o, d, inv, nrm, tn, tf, Lt, Li, false, nullptr, n_dst, nullptr,
+                                     n_ev, kb, cnt, lane_ok);
+        if (done) continue;
+        if (!lane_ok) {
+            kb.clear();
+            trace_round<K, FORM, INSTR>(a, sc, o, d, inv, nrm, tn, tf, Lt, Li, false, true, nullptr, 0, nullptr, n_dst,
+                                        nullptr, n_ev, kb, cnt);
+        }
+        for (int j = 0; j < kb.n; ++j) {
+            uint32_t idx = kb.I(j);
+            blend_one<false>(a, sc, st, idx, o, d, dn);
+            if (INSTR) {
+                if (a.ids && nb < a.ids_cap) a.ids[(size_t)pix * a.ids_cap + nb] = sc.gid[idx];
+                cnt.blended++;
+            }
+            ++nb;
+            if (st.T < a.T_min) {
+                done = true;
+                break;
+            }
+        }
+        if (!done && kb.n < K) done = true;
+        if (!done) {
+            Lt = kb.T(K - 1);
+            Li = kb.I(K - 1);
+        }
+    }
+    if (valid) {
+        out[pix] = make_float4(st.C[0] + st.T * a.bg0, st.C[1] + st.T * a.bg1, st.C[2] + st.T * a.bg2, st.T);
+        if (INSTR && a.n_blended) a.n_blended[pix] = nb;
+    }
+}
+
 // The rays of one warp: round 1 as the warp's packet, then each ray's later rounds on its
 // own. Every lane of the warp calls this together; lanes without a ray pass valid = false.
 template <int K, int FORM, bool INSTR, bool BWD>
@@ -948,8 +1014,9 @@ __device__ __forceinline__ void trace_warp(const TraceArgs &a, const SceneRef &s
     kb.clear();
     int n_dst = 0, n_ev = 0;
     bool lane_ok = true;
-    packet_round<K, FORM, INSTR>(a, sc, valid, pst, o, d, inv, inv_len, tn, tf, a.traversal == GRTX_TRAVERSAL_CHECKPOINT,
-                                 a.ck1 + slot, n_dst, a.ev + slot, n_ev, kb, cnt, lane_ok);
+    packet_round<K, FORM, INSTR>(a, sc, valid, pst, o, d, inv, inv_len, tn, tf, tn, GRTX_NONE,
+                                 a.traversal == GRTX_TRAVERSAL_CHECKPOINT, a.ck1 + slot, n_dst, a.ev + slot, n_ev, kb,
+                                 cnt, lane_ok);
     // a lane whose packet could not finish (lists or the warp's stack overflowed) redoes round 1
     // from the root on its own, as after any capacity overflow
     if (valid) trace_ray<K, FORM, INSTR, BWD>(a, sc, out, slot, pix, o, d, tn, tf, kb, cnt, true, lane_ok, n_dst, n_ev);
@@ -984,7 +1051,12 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, BWD)) k_trace(Trac
         float tn, tf;
         bool valid = make_ray(a.cam, base + lane, pix, o, d, tn, tf);
         rays += valid;
-        trace_warp<K, FORM, INSTR, BWD>(a, a.sc, a.rgbT, slot, valid, pix, o, d, tn, tf, kb, cnt, s_pst[threadIdx.x >> 5]);
+        if (!BWD && a.traversal == GRTX_TRAVERSAL_RESTART)
+            trace_warp_restart<K, FORM, INSTR>(a, a.sc, a.rgbT, slot, valid, pix, o, d, tn, tf, kb, cnt,
+                                               s_pst[threadIdx.x >> 5]);
+        else
+            trace_warp<K, FORM, INSTR, BWD>(a, a.sc, a.rgbT, slot, valid, pix, o, d, tn, tf, kb, cnt,
+                                            s_pst[threadIdx.x >> 5]);
         __syncwarp();
     }
     if (INSTR && a.stats) {
