@@ -2,9 +2,10 @@
 // intersected Gaussian in one traversal, then sorts and blends after it, instead of k-buffer
 // rounds with early termination between them.
 //
-// Per ray: one stack traversal of the whole BVH over (t_near, t_far] appends every hit key
-// (t, leaf index) to the ray slot's list in the trace workspace (capacity ckpt_capacity,
-// interleaved [entry][slot] like the checkpoint lists). The list is then made a binary
+// Per ray: one traversal of the whole BVH over (t_near, t_far] (as the warp's packet, like
+// round 1 of the k-buffer kernels) appends every hit key (t, leaf index) to the ray slot's list
+// in the trace workspace (capacity ckpt_capacity, interleaved [entry][slot] like the
+// checkpoint lists). The list is then made a binary
 // min-heap and popped in key order while blending front to back, stopping right after the
 // Gaussian that takes T below T_min: the sort stops where termination does, so its cost is
 // O(n + b log n) for n hits and b blended. A ray with more hits than the capacity is traced
@@ -49,81 +50,116 @@ __device__ __forceinline__ void heap_sift_down(uint2 *__restrict__ h, size_t S, 
     h[(size_t)i * S] = v;
 }
 
-// Every hit of the ray, appended to list (stride S). Returns the count, or -1 when the
-// capacity is exceeded.
+// Every hit of the warp's rays, collected as one packet: the warp walks the union of the nodes
+// its rays need (one broadcast load per node, see packet_round), each lane appending its own
+// hits to its list (stride S).
+// Every lane calls this together; lanes without a ray pass valid = false. Returns each lane's
+// count, or -1 for a lane whose list overflowed or, for every lane, when the warp's stack would.
 template <int FORM, bool INSTR>
-__device__ __forceinline__ int collect_hits(const TraceArgs &a, const SceneRef &sc, float3 o, float3 d, float3 inv,
-                                            float tn, float tf, uint2 *__restrict__ list, Counters &cnt,
-                                            unsigned &collected)
+__device__ __forceinline__ int packet_collect(const TraceArgs &a, const SceneRef &sc, bool valid, uint4 *pst, float3 o,
+                                              float3 d, float3 inv, float tn, float tf, uint2 *__restrict__ list,
+                                              Counters &cnt, unsigned &collected)
 {
+    const unsigned full = 0xffffffffu;
     const size_t S = (size_t)a.n_slots;
-    uint32_t stack[GRTX_STACK];
-    int sp = 0, n = 0;
+    const int lane = threadIdx.x & 31;
+    int n = 0;
+    bool ok = true;
+    if (!sc.has_tree) return 0;
+    int sp = 0;
     uint32_t ref = 0u;
+    unsigned m = __ballot_sync(full, valid);
     for (;;) {
-        if (ref & GRTX_LEAF) {
-            uint32_t idx = ref & ~GRTX_LEAF;
-            if (INSTR) cnt.leaves++;
-            uint32_t gi;
-            bool touch = true;
-            if (FORM == FORM_PROXY) {
-                const float4 *tr = sc.tris + 3 * (size_t)idx;
-                float4 v0 = __ldg(tr), v1 = __ldg(tr + 1), v2 = __ldg(tr + 2);
-                gi = __float_as_uint(v0.w);
-                touch = tri_hit(v0, v1, v2, o, d) > tn;
+        bool go = ((m >> lane) & 1u) && ok;
+        if (__ballot_sync(full, go)) {
+            if (ref & GRTX_LEAF) {
+                if (go) {
+                    uint32_t idx = ref & ~GRTX_LEAF;
+                    if (INSTR) cnt.leaves++;
+                    uint32_t gi;
+                    bool touch = true;
+                    if (FORM == FORM_PROXY) {
+                        const float4 *tr = sc.tris + 3 * (size_t)idx;
+                        float4 v0 = __ldg(tr), v1 = __ldg(tr + 1), v2 = __ldg(tr + 2);
+                        gi = __float_as_uint(v0.w);
+                        touch = tri_hit(v0, v1, v2, o, d) > tn;
+                    } else {
+                        gi = idx;
+                        if (FORM == FORM_ICO) touch = template_touch<INSTR>(sc, gi, o, d, tn, cnt);
+                    }
+                    float t, D2, w[3];
+                    if (touch && sphere_test(sc.geom + 4 * (size_t)gi, o, d, t, D2, w) && D2 <= 1.0f && t > tn &&
+                        t <= tf) {
+                        if (n >= a.ckpt_cap) {
+                            ok = false;
+                        } else {
+                            list[(size_t)n * S] = make_uint2(__float_as_uint(t), gi);
+                            ++n;
+                            if (INSTR) collected++;
+                        }
+                    }
+                }
             } else {
-                gi = idx;
-                if (FORM == FORM_ICO) touch = template_touch<INSTR>(sc, gi, o, d, tn, cnt);
-            }
-            float t, D2, w[3];
-            if (touch && sphere_test(sc.geom + 4 * (size_t)gi, o, d, t, D2, w) && D2 <= 1.0f && t > tn && t <= tf) {
-                if (n >= a.ckpt_cap) return -1;
-                list[(size_t)n * S] = make_uint2(__float_as_uint(t), gi);
-                ++n;
-                if (INSTR) collected++;
-            }
-        } else {
-            if (INSTR) cnt.nodes++;
-            const float4 *nd = sc.nodes + 4 * (size_t)ref;
-            float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
-            uint32_t c0 = __float_as_uint(n3.x), c1 = __float_as_uint(n3.y);
-            float e0, x0, e1, x1;
-            slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, o, inv, tn, tf, e0, x0);
-            slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, o, inv, tn, tf, e1, x1);
-            bool h0 = e0 <= x0;
-            bool h1 = e1 <= x1 && c1 != GRTX_NONE;
-            if (h0 && h1) {
-                bool near0 = e0 <= e1;
-                ref = near0 ? c0 : c1;
-                if (sp < GRTX_STACK) stack[sp++] = near0 ? c1 : c0;
-                else if (INSTR) cnt.overflow++;
-                continue;
-            }
-            if (h0 || h1) {
-                ref = h0 ? c0 : c1;
-                continue;
+                const float4 *nd = sc.nodes + 4 * (size_t)ref;
+                float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+                uint32_t c0 = __float_as_uint(n3.x), c1 = __float_as_uint(n3.y);
+                bool h0 = false, h1 = false, near0 = true;
+                if (go) {
+                    if (INSTR) cnt.nodes++;
+                    float e0, x0, e1, x1;
+                    slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, o, inv, tn, tf, e0, x0);
+                    slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, o, inv, tn, tf, e1, x1);
+                    h0 = e0 <= x0;
+                    h1 = e1 <= x1 && c1 != GRTX_NONE;
+                    near0 = e0 <= e1;
+                }
+                unsigned m0 = __ballot_sync(full, h0), m1 = __ballot_sync(full, h1);
+                if (m0 && m1) {
+                    unsigned both = m0 & m1, vote = __ballot_sync(full, h0 && h1 && near0);
+                    bool n0first = both ? (2 * __popc(vote) >= __popc(both)) : (__popc(m0) >= __popc(m1));
+                    if (sp == kPacketStack) return -1;          // too deep for the warp's stack
+                    if (lane == 0) pst[sp] = make_uint4(n0first ? c1 : c0, 0u, n0first ? m1 : m0, 0u);
+                    ++sp;
+                    __syncwarp(full);
+                    m = n0first ? m0 : m1;
+                    ref = n0first ? c0 : c1;
+                    continue;
+                }
+                if (m0 || m1) {
+                    m = m0 ? m0 : m1;
+                    ref = m0 ? c0 : c1;
+                    continue;
+                }
             }
         }
         if (sp == 0) break;
-        ref = stack[--sp];
+        --sp;
+        uint4 v = pst[sp];
+        ref = v.x;
+        m = v.z;
     }
-    return n;
+    return ok ? n : -1;
 }
 
 template <int FORM, bool INSTR>
-__device__ __forceinline__ void single_ray(const TraceArgs &a, const SceneRef &sc, int slot, int64_t pix, float3 o,
-                                           float3 d, float tn, float tf, KBuf<kFallbackK> &kb, Counters &cnt,
-                                           unsigned &collected)
+__device__ __forceinline__ void single_ray(const TraceArgs &a, const SceneRef &sc, int slot, bool valid, int64_t pix,
+                                           float3 o, float3 d, float tn, float tf, KBuf<kFallbackK> &kb, Counters &cnt,
+                                           unsigned &collected, uint4 *pst)
 {
     const size_t S = (size_t)a.n_slots;
+    if (!valid) {
+        o = make_float3(0.f, 0.f, 0.f);
+        d = make_float3(0.f, 0.f, 1.f);
+        tn = tf = 0.f;
+    }
     float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
     float nrm = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
     float3 dn = make_float3(d.x * nrm, d.y * nrm, d.z * nrm);
     uint2 *list = a.ck0 + slot;
-    int n = 0;
+    int n = packet_collect<FORM, INSTR>(a, sc, valid, pst, o, d, inv, tn, tf, list, cnt, collected);
+    if (!valid) return;
     if (sc.has_tree) {
         if (INSTR) cnt.rounds++;
-        n = collect_hits<FORM, INSTR>(a, sc, o, d, inv, tn, tf, list, cnt, collected);
         if (n < 0) {                  // more hits than the list holds: k-buffer rounds instead
             if (INSTR) cnt.fallbacks++;
             trace_ray<kFallbackK, FORM, INSTR, false>(a, sc, a.rgbT, slot, pix, o, d, tn, tf, kb, cnt);
@@ -164,6 +200,7 @@ __global__ void __launch_bounds__(kBlock, 8) k_trace_single(TraceArgs a)
 {
     __shared__ float s_kt[kFallbackK * kBlock];
     __shared__ uint32_t s_ki[kFallbackK * kBlock];
+    __shared__ uint4 s_pst[kBlock / 32][kPacketStack];
     const int slot = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     KBuf<kFallbackK> kb;
@@ -179,10 +216,9 @@ __global__ void __launch_bounds__(kBlock, 8) k_trace_single(TraceArgs a)
         int64_t pix;
         float3 o, d;
         float tn, tf;
-        if (make_ray(a.cam, base + lane, pix, o, d, tn, tf)) {
-            ++rays;
-            single_ray<FORM, INSTR>(a, a.sc, slot, pix, o, d, tn, tf, kb, cnt, collected);
-        }
+        bool valid = make_ray(a.cam, base + lane, pix, o, d, tn, tf);
+        rays += valid;
+        single_ray<FORM, INSTR>(a, a.sc, slot, valid, pix, o, d, tn, tf, kb, cnt, collected, s_pst[threadIdx.x >> 5]);
         __syncwarp();
     }
     if (INSTR && a.stats) {
