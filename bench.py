@@ -319,7 +319,8 @@ def bench_surface_ablations(g, sc, cam, k: int, steps: int, stream, flush) -> di
     return res
 
 
-def bench_serving(n_requests: int, max_rays_per_step: int = 4 << 20, max_inflight: int = 64):
+def bench_serving(n_requests: int, max_rays_per_step: int = 4 << 20, max_inflight: int = 64,
+                  traversal: str = "checkpoint"):
     import torch
     from paper_2601_20429_gb300 import render as R
     from paper_2601_20429_gb300 import scenes
@@ -327,7 +328,8 @@ def bench_serving(n_requests: int, max_rays_per_step: int = 4 << 20, max_infligh
     scs, reqs, cfg = scenes.config_serving(n_requests=n_requests)
     gpu_scenes = [R.Scene.from_params(g) for g in scs]
     del scs
-    srv = Server(gpu_scenes, k=cfg["k"], max_rays_per_step=max_rays_per_step, max_inflight=max_inflight)
+    srv = Server(gpu_scenes, k=cfg["k"], traversal=traversal, max_rays_per_step=max_rays_per_step,
+                 max_inflight=max_inflight)
     max_px = 1920 * 1080
     pool = deque(torch.empty((max_px, 4), dtype=torch.float32, device="cuda") for _ in range(80))
     # warm-up: a few requests of each size
@@ -375,7 +377,7 @@ def bench_serving(n_requests: int, max_rays_per_step: int = 4 << 20, max_infligh
             "p99_ms": float(np.percentile(lat_ms, 99)), "mean_ms": float(lat_ms.mean()),
             "Mrays_per_s": rays / makespan / 1e6, "makespan_s": makespan,
             "offered_Mrays_per_s": rays / (reqs[-1]["arrival"] - reqs[0]["arrival"]) / 1e6,
-            "max_rays_per_step": max_rays_per_step, "max_inflight": max_inflight}
+            "max_rays_per_step": max_rays_per_step, "max_inflight": max_inflight, "traversal": traversal}
 
 
 def bench_differentiable(steps: int, warmup: int, stream):
@@ -647,6 +649,8 @@ def main():
     serving = None
     if dist.world == 1 and not args.no_serving:
         serving = bench_serving(args.serve_requests)
+        if not args.no_extra:
+            serving["restart_traversal"] = bench_serving(args.serve_requests, traversal="restart")
 
     differentiable = outdoor = ablations = None
     if dist.world == 1 and not args.no_extra:

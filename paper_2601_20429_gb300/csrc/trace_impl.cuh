@@ -1103,8 +1103,12 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, false)) k_serve(Tr
         float3 o, d;
         float tn, tf;
         bool valid = make_ray(cam, item, pix, o, d, tn, tf);
-        trace_warp<K, FORM_SPHERE, false, false>(a, sc, sg.out, slot, valid, pix, o, d, tn, tf, kb, cnt,
-                                                 s_pst[threadIdx.x >> 5]);
+        if (a.traversal == GRTX_TRAVERSAL_RESTART)
+            trace_warp_restart<K, FORM_SPHERE, false>(a, sc, sg.out, slot, valid, pix, o, d, tn, tf, kb, cnt,
+                                                      s_pst[threadIdx.x >> 5]);
+        else
+            trace_warp<K, FORM_SPHERE, false, false>(a, sc, sg.out, slot, valid, pix, o, d, tn, tf, kb, cnt,
+                                                     s_pst[threadIdx.x >> 5]);
         __syncwarp();
     }
 }

@@ -54,6 +54,20 @@ def test_alone_equals_mix(world):
     srv.close()
 
 
+def test_restart_traversal_serves_the_same_images(world):
+    """The server with restart traversal (every round a warp packet) gives every request the
+    image of a lone checkpointed render."""
+    sc, reqs, alone = world
+    srv = Server(sc, k=16, traversal="restart", max_rays_per_step=20_000, max_inflight=8)
+    bufs = _bufs(reqs)
+    done = srv.render_requests([(r["scene"], r["camera"], b, i) for i, (r, b) in enumerate(zip(reqs, bufs))])
+    torch.cuda.synchronize()
+    assert sorted(d["tag"] for d in done) == list(range(len(reqs)))
+    worst = max(_same(a, b) for a, b in zip(alone, bufs))
+    assert worst <= 1e-5
+    srv.close()
+
+
 def test_requests_admitted_while_others_run(world):
     sc, reqs, alone = world
     srv = Server(sc, k=16, max_rays_per_step=5_000, max_inflight=3)
