@@ -111,7 +111,11 @@ enum { GRTX_TRAVERSAL_CHECKPOINT = 0, /* resume from checkpointed nodes + evicti
  * the default: grtx_morton_codes_sized) or GRTX_CODES_CENTROID (grtx_morton_codes).
  * bvh_builder (read by grtx_build_bvh only): GRTX_BUILDER_PLOC (0, the default: clustering
  * of the sorted leaves, grtx_ploc_tree) or GRTX_BUILDER_LBVH (the binary radix tree of the
- * codes, grtx_radix_tree). The tree shape changes the cost of a trace, never its result. */
+ * codes, grtx_radix_tree). The tree shape changes the cost of a trace, never its result.
+ * packet_stack: entries of the per-warp stack that a warp-packet traversal may use (0: all
+ * GRTX_PACKET_STACK); a packet that would need more falls back to tracing its rays one by
+ * one, with the same result. Smaller values exist to exercise that fallback. */
+#define GRTX_PACKET_STACK 64
 enum { GRTX_CODES_SIZED = 0, GRTX_CODES_CENTROID = 1 };
 enum { GRTX_BUILDER_PLOC = 0, GRTX_BUILDER_LBVH = 1 };
 #define GRTX_PLOC_RADIUS 16
@@ -126,6 +130,7 @@ typedef struct grtx_params {
     int32_t evict_capacity;
     int32_t bvh_codes;
     int32_t bvh_builder;
+    int32_t packet_stack;
 } grtx_params;
 
 enum { GRTX_CAMERA_PINHOLE = 0, GRTX_CAMERA_FISHEYE = 1, GRTX_CAMERA_RAYS = 2 };

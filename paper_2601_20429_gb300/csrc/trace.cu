@@ -62,6 +62,7 @@ int check_params(const grtx_params *p)
     if (!(p->alpha_max > 0.f && p->alpha_max < 1.f)) return grtx_fail(GRTX_ERR_INVALID_ARG, "alpha_max must be in (0,1)");
     if (p->ckpt_capacity < 0 || p->evict_capacity < 0 || p->ckpt_capacity > 65536 || p->evict_capacity > 65536)
         return grtx_fail(GRTX_ERR_INVALID_ARG, "capacities must be in [0, 65536]");
+    if (p->packet_stack < 0) return grtx_fail(GRTX_ERR_INVALID_ARG, "packet_stack must be >= 0");
     return GRTX_OK;
 }
 
@@ -191,6 +192,7 @@ int setup(grtx_scene *sc, const grtx_camera *cam, const grtx_params *p, TraceArg
     a.ckpt_cap = p->ckpt_capacity > 0 ? p->ckpt_capacity
                  : (p->traversal == GRTX_TRAVERSAL_SINGLE ? GRTX_DEFAULT_SINGLE_CAPACITY : GRTX_DEFAULT_CKPT_CAPACITY);
     a.evict_cap = p->evict_capacity > 0 ? p->evict_capacity : GRTX_DEFAULT_EVICT_CAPACITY;
+    a.packet_stack = p->packet_stack > 0 ? std::min(p->packet_stack, kPacketStack) : kPacketStack;
     return GRTX_OK;
 }
 

@@ -44,6 +44,7 @@ struct TraceArgs {
     float T_min, alpha_max;
     float bg0, bg1, bg2;
     int ckpt_cap, evict_cap;
+    int packet_stack;            // warp-stack entries a packet may use (1..kPacketStack)
     // per-slot workspace, interleaved [entry][slot]
     uint2 *ck0, *ck1, *ev;
     int n_slots;
@@ -553,7 +554,7 @@ __device__ __forceinline__ bool trace_round(const TraceArgs &a, const SceneRef &
 // every lane if the warp's stack would overflow (returns false then): such a lane redoes the
 // round from the root on its own, as after any capacity overflow in trace_ray.
 // ------------------------------------------------------------------------------------------
-constexpr int kPacketStack = 64;
+constexpr int kPacketStack = GRTX_PACKET_STACK;
 
 template <int K, int FORM, bool INSTR>
 __device__ __forceinline__ bool packet_round(const TraceArgs &a, const SceneRef &sc, bool valid, uint4 *pst, float3 o,
@@ -657,7 +658,7 @@ __device__ __forceinline__ bool packet_round(const TraceArgs &a, const SceneRef 
                 if (m0 && m1) {
                     unsigned both = m0 & m1, vote = __ballot_sync(full, h0 && h1 && near0);
                     bool n0first = both ? (2 * __popc(vote) >= __popc(both)) : (__popc(m0) >= __popc(m1));
-                    if (sp == kPacketStack) {                 // too deep for the warp's stack
+                    if (sp >= a.packet_stack) {               // too deep for the warp's stack
                         lane_ok = false;
                         return false;
                     }

@@ -111,6 +111,7 @@ extern "C" GRTX_API int grtx_trace_forward_noalloc(grtx_scene *sc, const grtx_ca
     a.bg2 = p->bg[2];
     a.ckpt_cap = p->ckpt_capacity > 0 ? p->ckpt_capacity : GRTX_DEFAULT_CKPT_CAPACITY;
     a.evict_cap = p->evict_capacity > 0 ? p->evict_capacity : GRTX_DEFAULT_EVICT_CAPACITY;
+    a.packet_stack = p->packet_stack > 0 ? std::min(p->packet_stack, kPacketStack) : kPacketStack;
     a.rgbT = (float4 *)d_rgbT;
     bool ckpt = a.traversal == GRTX_TRAVERSAL_CHECKPOINT;
     size_t C = ckpt ? (size_t)a.ckpt_cap : 1, E = ckpt ? (size_t)a.evict_cap : 1;

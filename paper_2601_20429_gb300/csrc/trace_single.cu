@@ -117,7 +117,7 @@ __device__ __forceinline__ int packet_collect(const TraceArgs &a, const SceneRef
                 if (m0 && m1) {
                     unsigned both = m0 & m1, vote = __ballot_sync(full, h0 && h1 && near0);
                     bool n0first = both ? (2 * __popc(vote) >= __popc(both)) : (__popc(m0) >= __popc(m1));
-                    if (sp == kPacketStack) return -1;          // too deep for the warp's stack
+                    if (sp >= a.packet_stack) return -1;        // too deep for the warp's stack
                     if (lane == 0) pst[sp] = make_uint4(n0first ? c1 : c0, 0u, n0first ? m1 : m0, 0u);
                     ++sp;
                     __syncwarp(full);

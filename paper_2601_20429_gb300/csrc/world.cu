@@ -313,7 +313,7 @@ __device__ __forceinline__ void world_packet_round(const WorldArgs &W, bool vali
                 if (m0 && m1) {
                     unsigned both = m0 & m1, vote = __ballot_sync(full, h0 && h1 && near0);
                     bool n0first = both ? (2 * __popc(vote) >= __popc(both)) : (__popc(m0) >= __popc(m1));
-                    if (sp == kPacketStack) {                 // too deep for the warp's stack
+                    if (sp >= W.a.packet_stack) {             // too deep for the warp's stack
                         lane_ok = false;
                         return;
                     }
@@ -694,6 +694,7 @@ extern "C" GRTX_API int grtx_world_trace_forward(grtx_world *w, const grtx_camer
     a.bg2 = p->bg[2];
     a.ckpt_cap = p->ckpt_capacity > 0 ? p->ckpt_capacity : GRTX_DEFAULT_CKPT_CAPACITY;
     a.evict_cap = p->evict_capacity > 0 ? p->evict_capacity : GRTX_DEFAULT_EVICT_CAPACITY;
+    a.packet_stack = p->packet_stack > 0 ? std::min(p->packet_stack, kPacketStack) : kPacketStack;
     a.rgbT = (float4 *)out->rgbT;
     a.n_blended = out->n_blended;
     a.ids = out->blended_ids;

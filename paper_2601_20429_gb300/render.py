@@ -126,9 +126,9 @@ def render_world(world: World, cam: dict | None, rays=None, out=None, ids_cap: i
 
 
 def trace_params(k=16, traversal="checkpoint", alpha_min=0.01, T_min=1e-3, alpha_max=0.99, bg=(0.0, 0.0, 0.0),
-                 ckpt_capacity=0, evict_capacity=0):
+                 ckpt_capacity=0, evict_capacity=0, packet_stack=0):
     return N.make_params(k, TRAVERSALS[traversal] if isinstance(traversal, str) else traversal, alpha_min, T_min,
-                         alpha_max, bg, ckpt_capacity, evict_capacity)
+                         alpha_max, bg, ckpt_capacity, evict_capacity, packet_stack=packet_stack)
 
 
 def n_rays_of(cam: dict, rays=None) -> int:

@@ -330,6 +330,24 @@ def test_icosphere_scene_backward_equals_sphere_scene():
         np.testing.assert_allclose(out["ico80"][name], out["sphere"][name], rtol=1e-5, atol=1e-6)
 
 
+# ------------------------------------------------------------------ warp-packet fallback
+
+
+@pytest.mark.parametrize("form,traversal", [("sphere", "checkpoint"), ("sphere", "restart"), ("sphere", "single"),
+                                            ("proxy20", "checkpoint"), ("ico20", "restart")])
+def test_packet_stack_overflow_falls_back_exactly(dense, form, traversal):
+    """A warp whose packet would outgrow its stack traces its rays one by one: forcing that
+    with a one-entry stack leaves every blend list unchanged."""
+    g, cam, S, rays, ref = dense
+    full = _gpu_render(g, cam, form=form, k=8, traversal=traversal, ids_cap=256)
+    tiny = _gpu_render(g, cam, form=form, k=8, traversal=traversal, ids_cap=256, packet_stack=1)
+    np.testing.assert_array_equal(tiny["ids"], full["ids"])
+    np.testing.assert_allclose(tiny["rgbT"], full["rgbT"], rtol=0, atol=1e-6)
+    if traversal != "restart":
+        assert tiny["stats"]["fallbacks"] > 0
+    _check_image(tiny, ref, S, rays)
+
+
 # ------------------------------------------------------------------ single-round traversal
 
 

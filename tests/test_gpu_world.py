@@ -139,6 +139,19 @@ def test_world_checkpoints_save_revisits_and_fall_back_exactly(objects):
     world.close()
 
 
+def test_world_packet_stack_overflow_falls_back_exactly(objects):
+    gs, oscenes, gscenes = objects
+    pl = _placements()
+    world = R.World([(gscenes[i], M) for i, M in pl])
+    cam = _cam()
+    a = _gpu_world(world, cam, k=16)
+    b = _gpu_world(world, cam, k=16, packet_stack=1)
+    np.testing.assert_array_equal(a["ids"], b["ids"])
+    np.testing.assert_allclose(a["rgbT"], b["rgbT"], rtol=0, atol=1e-6)
+    assert b["stats"]["fallbacks"] > 0
+    world.close()
+
+
 def test_world_update_moves_an_object(objects):
     gs, oscenes, gscenes = objects
     pl = _placements()
