@@ -319,8 +319,35 @@ def bench_surface_ablations(g, sc, cam, k: int, steps: int, stream, flush) -> di
     return res
 
 
+def traversal_modes_on_views(gpu_scenes, reqs, per_scene: int = 20) -> dict:
+    """Mrays/s of checkpoint, restart and single-round traversal on each serving scene, over
+    the first per_scene request views of that scene (one launch each, CUDA events)."""
+    import torch
+    from paper_2601_20429_gb300 import render as R
+    res = {}
+    for si, sc in enumerate(gpu_scenes):
+        views = [r["camera"] for r in reqs if r["scene"] == si][:per_scene]
+        row = {}
+        for trav in ("checkpoint", "restart", "single"):
+            ms, rays = 0.0, 0
+            for cam in views:
+                n = cam["width"] * cam["height"]
+                out = torch.empty((n, 4), device="cuda")
+                R.render(sc, cam, k=16, traversal=trav, out=out)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                R.render(sc, cam, k=16, traversal=trav, out=out)
+                e1.record()
+                torch.cuda.synchronize()
+                ms += e0.elapsed_time(e1)
+                rays += n
+            row[trav] = rays / ms / 1e3
+        res[str(sc.n)] = row
+    return res
+
+
 def bench_serving(n_requests: int, max_rays_per_step: int = 4 << 20, max_inflight: int = 64,
-                  traversal: str = "checkpoint"):
+                  traversal: str = "checkpoint", modes: bool = False):
     import torch
     from paper_2601_20429_gb300 import render as R
     from paper_2601_20429_gb300 import scenes
@@ -371,9 +398,11 @@ def bench_serving(n_requests: int, max_rays_per_step: int = 4 << 20, max_infligh
     makespan = t_last - reqs[0]["arrival"]
     lat_ms = np.array(lat) * 1e3
     srv.close()
+    mode_rates = traversal_modes_on_views(gpu_scenes, reqs) if modes else None
     for s in gpu_scenes:
         s.close()
     return {"requests": n, "rate_hz": 200.0, "p50_ms": float(np.percentile(lat_ms, 50)),
+            "traversal_modes_Mrays_per_s": mode_rates,
             "p99_ms": float(np.percentile(lat_ms, 99)), "mean_ms": float(lat_ms.mean()),
             "Mrays_per_s": rays / makespan / 1e6, "makespan_s": makespan,
             "offered_Mrays_per_s": rays / (reqs[-1]["arrival"] - reqs[0]["arrival"]) / 1e6,
@@ -514,6 +543,8 @@ def bench_outdoor(steps: int, stream, flush):
     out_p = torch.empty((n, 4), device="cuda")
     out_s = torch.empty((max(m, 1), 4), device="cuda")
     tp = time_frames(lambda: R.render(sc, None, rays=prim, k=cfg["k"], out=out_p), steps, 2, flush, stream)
+    tp32 = time_frames(lambda: R.render(sc, None, rays=prim, k=32, out=out_p), steps, 2, flush, stream)
+    st_p32 = N.stats_dict(R.render(sc, None, rays=prim, k=32, want_stats=True)["stats"])
     ts = time_frames(lambda: R.render(sc, None, rays=sec_rays, k=cfg["k"], out=out_s), steps, 2, flush, stream)
     st_p = N.stats_dict(R.render(sc, None, rays=prim, k=cfg["k"], want_stats=True)["stats"])
     st_s = N.stats_dict(R.render(sc, None, rays=sec_rays, k=cfg["k"], want_stats=True)["stats"])
@@ -526,13 +557,15 @@ def bench_outdoor(steps: int, stream, flush):
     sc_l.close()
     sc.close()
     return {"workload": "6M outdoor Gaussians, 1920x1080 equidistant fisheye, one 4x3 m mirror and one glass "
-                        "ball (index 1.5), k=16",
+                        "ball (index 1.5), k=16 (primary also at k=32)",
             "build_ms": build_ms, "secondary_rays": m,
             "primary": {"Mrays_per_s": n / (statistics.mean(tp) / 1e3) / 1e6, "ms": statistics.mean(tp),
                         "nodes_per_ray": nodes_per_ray(st_p)},
             "secondary": {"Mrays_per_s": m / (statistics.mean(ts) / 1e3) / 1e6, "ms": statistics.mean(ts),
                           "nodes_per_ray": nodes_per_ray(st_s)},
             "depth": depth,
+            "primary_k32": {"Mrays_per_s": n / (statistics.mean(tp32) / 1e3) / 1e6, "ms": statistics.mean(tp32),
+                            "nodes_per_ray": nodes_per_ray(st_p32)},
             "primary_lbvh_sized_codes": {"Mrays_per_s": n / (statistics.mean(tl) / 1e3) / 1e6,
                                          "ms": statistics.mean(tl), "nodes_per_ray": nodes_per_ray(st_l)},
             "primary_lbvh_centroid_codes": {"Mrays_per_s": n / (statistics.mean(tc) / 1e3) / 1e6,
@@ -648,7 +681,7 @@ def main():
 
     serving = None
     if dist.world == 1 and not args.no_serving:
-        serving = bench_serving(args.serve_requests)
+        serving = bench_serving(args.serve_requests, modes=not args.no_extra)
         if not args.no_extra:
             serving["restart_traversal"] = bench_serving(args.serve_requests, traversal="restart")
 
