@@ -817,6 +817,26 @@ def test_ploc_breaks_ties_to_the_lower_index():
     assert it == 2 and list(left) == [1, L | 0] and list(right) == [L | 2, L | 1]
 
 
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_ploc_distance_is_the_full_surface_area(axis):
+    """Each of the three face terms decides a merge. A unit cube (cluster 1) sits between
+    cube A, moved 2 along `axis`, and cube B, moved 1 along both other axes. The union with A
+    has extents 3 along `axis` and 1 elsewhere, area 2 (3 + 3 + 1) = 14; the union with B has
+    extents 2, 2 and 1, area 2 (2 + 2 + 4) = 16; A with B is larger still. So clusters 0 and 1
+    are mutual nearest and merge first. Dropping the face term of B's two moved axes (4 for B,
+    1 for A) would pair B with the middle cube instead."""
+    A = np.array([0, 0, 0, 1, 1, 1], np.float32)
+    C = A.copy()
+    B = A.copy()
+    A[[axis, axis + 3]] += 2
+    for a in range(3):
+        if a != axis:
+            B[[a, a + 3]] += 1
+    left, right, it = O.ploc(np.stack([A, C, B]), radius=2)
+    L = O.LEAF
+    assert it == 2 and list(left) == [1, L | 0] and list(right) == [L | 2, L | 1]
+
+
 def test_ploc_radius_limits_the_search():
     """With radius 1 only neighbours in order are seen: cubes at 0, 9, 10, 19 with r = 1 pair
     (1, 2) first; with r = 3 as well (the nearest pair anywhere)."""
