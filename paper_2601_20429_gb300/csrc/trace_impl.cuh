@@ -201,7 +201,9 @@ __device__ __forceinline__ bool key_after(float t, uint32_t i, float Lt, uint32_
 // D2 = |o_l + t d_l|^2. t is the max-response depth of Sec. III-A Eq. t-max-resp, and D2 <= 1
 // iff alpha >= alpha_min. Stage 1 runs for every leaf and only filters: in FP32 its absolute
 // error in D2 grows like |o_l| (the ray origin measured in Gaussian widths), so the threshold
-// is widened accordingly.
+// is widened to 1 + 1e-5 + 4e-6 |o_l|, tested in squared form (no square root). Its t only
+// seeds stage 2, whose Newton step lands on the minimiser from any nearby start, so the
+// quotient is the fast approximate one.
 __device__ __forceinline__ bool sphere_candidate(float4 r0, float4 r1, float4 r2, float3 o, float3 d, float &t)
 {
     float vx = o.x - r0.w, vy = o.y - r1.w, vz = o.z - r2.w;
@@ -213,11 +215,12 @@ __device__ __forceinline__ bool sphere_candidate(float4 r0, float4 r1, float4 r2
     float dlz = fmaf(r2.x, d.x, fmaf(r2.y, d.y, r2.z * d.z));
     float aa = fmaf(dlx, dlx, fmaf(dly, dly, dlz * dlz));
     float bb = fmaf(olx, dlx, fmaf(oly, dly, olz * dlz));
-    t = -bb / aa;
+    t = __fdividef(-bb, aa);
     float px = fmaf(t, dlx, olx), py = fmaf(t, dly, oly), pz = fmaf(t, dlz, olz);
     float D2 = fmaf(px, px, fmaf(py, py, pz * pz));
     float oo = fmaf(olx, olx, fmaf(oly, oly, olz * olz));
-    return D2 <= 1.0f + 1e-5f + 4e-6f * sqrtf(oo);
+    float ex = D2 - (1.0f + 1e-5f);
+    return ex <= 0.0f || ex * ex <= 1.6e-11f * oo;    // ex <= 4e-6 sqrt(oo)
 }
 
 // Error-free a + b = s + e (Knuth's two-sum).
@@ -257,7 +260,10 @@ __device__ __forceinline__ void sphere_refine(float4 r0, float4 r1, float4 r2, f
         p[j] = fmaf(R[j].x, wh[0], fmaf(R[j].y, wh[1], fmaf(R[j].z, wh[2], lo)));
         dl[j] = fmaf(R[j].x, d.x, fmaf(R[j].y, d.y, R[j].z * d.z));
     }
-    float delta = fmaf(p[0], dl[0], fmaf(p[1], dl[1], p[2] * dl[2])) / fmaf(dl[0], dl[0], fmaf(dl[1], dl[1], dl[2] * dl[2]));
+    // the step only corrects t, so the fast quotient's few-ulp relative error in it stays far
+    // below one ulp of t
+    float delta = __fdividef(fmaf(p[0], dl[0], fmaf(p[1], dl[1], p[2] * dl[2])),
+                             fmaf(dl[0], dl[0], fmaf(dl[1], dl[1], dl[2] * dl[2])));
     t -= delta;
 #pragma unroll
     for (int j = 0; j < 3; ++j) p[j] = fmaf(-delta, dl[j], p[j]);
@@ -769,7 +775,7 @@ __device__ __forceinline__ void blend_one(const TraceArgs &a, const SceneRef &sc
     st.C[0] = fmaf(w, c[0], st.C[0]);
     st.C[1] = fmaf(w, c[1], st.C[1]);
     st.C[2] = fmaf(w, c[2], st.C[2]);
-    float inv1m = 1.0f / (1.0f - al);
+    float inv1m = __fdividef(1.0f, 1.0f - al);           // 1 - al >= 1 - alpha_max > 0
     float dLda = -st.dLdT * st.Tf * inv1m;
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) dLda += st.G[ch] * (st.T * c[ch] - (st.Cf[ch] - st.C[ch]) * inv1m);
@@ -777,14 +783,14 @@ __device__ __forceinline__ void blend_one(const TraceArgs &a, const SceneRef &sc
     if (clamped || dLda == 0.f) return;
     // alpha = o exp(-d2/2), d2 = |S^-1 R^T (x* - mu)|^2 at x* = o + t d (t fixed: envelope)
     float lam = a.logits[gi];
-    float op = 1.0f / (1.0f + expf(-lam));
+    float op = __fdividef(1.0f, 1.0f + expf(-lam));
     if (a.g_logits) atomic_add_f(a.g_logits + gi, dLda * al_raw * (1.0f - op));
     float dLdd2 = -0.5f * dLda * al_raw;
     float mu[3] = {a.means[3 * gi], a.means[3 * gi + 1], a.means[3 * gi + 2]};
-    float s[3] = {expf(a.log_scales[3 * gi]), expf(a.log_scales[3 * gi + 1]), expf(a.log_scales[3 * gi + 2])};
+    // inverse scales 1/s_j = exp(-log s_j)
+    float is[3] = {expf(-a.log_scales[3 * gi]), expf(-a.log_scales[3 * gi + 1]), expf(-a.log_scales[3 * gi + 2])};
     float qw = a.quats[4 * gi], qx = a.quats[4 * gi + 1], qy = a.quats[4 * gi + 2], qz = a.quats[4 * gi + 3];
-    float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
-    float iq = 1.0f / qn;
+    float iq = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
     float w_ = qw * iq, x = qx * iq, y = qy * iq, z = qz * iq;
     float R[3][3] = {{1.f - 2.f * (y * y + z * z), 2.f * (x * y - w_ * z), 2.f * (x * z + w_ * y)},
                      {2.f * (x * y + w_ * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w_ * x)},
@@ -793,8 +799,8 @@ __device__ __forceinline__ void blend_one(const TraceArgs &a, const SceneRef &sc
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         float u = R[0][j] * e[0] + R[1][j] * e[1] + R[2][j] * e[2];
-        v[j] = u / s[j];
-        vs[j] = v[j] / s[j];
+        v[j] = u * is[j];
+        vs[j] = v[j] * is[j];
     }
     if (a.g_means) {
 #pragma unroll
