@@ -410,8 +410,10 @@ def bench_serving(n_requests: int, max_rays_per_step: int = 4 << 20, max_infligh
 
 
 def bench_differentiable(steps: int, warmup: int, stream):
-    """Training-style step on the 256K-Gaussian scene at 800x800: rebuild the BVH from the
-    current parameters, render, L2 loss against the target image, backward."""
+    """Training-style step on the 256K-Gaussian scene at 800x800: bring the BVH up to the
+    current parameters, render, L2 loss against the target image, backward. Two forms: a
+    scene kept across steps and refitted in place each step (built once by clustering), and a
+    scene built anew each step (radix tree) and freed after backward."""
     import torch
     from paper_2601_20429_gb300 import render as R
     from paper_2601_20429_gb300 import scenes
@@ -420,30 +422,37 @@ def bench_differentiable(steps: int, warmup: int, stream):
     target = R.render(tsc, cam, k=cfg["k"])["rgbT"].clone()
     tsc.close()
     params = [t.requires_grad_(True) for t in R.params_to_device(g)]
+    kept = R.Scene(*[t.detach() for t in params], g.sh_degree)
 
-    def step():
+    def step(opts):
         for t in params:
             t.grad = None
-        out = R.render_differentiable(*params, g.sh_degree, cam, k=cfg["k"])
+        out = R.render_differentiable(*params, g.sh_degree, cam, k=cfg["k"], **opts)
         loss = ((out[:, :3] - target[:, :3]) ** 2).mean()
         loss.backward()
         return loss
 
-    for _ in range(warmup):
-        step()
-    torch.cuda.synchronize()
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(steps):
-        loss = step()
-    b.record(stream)
-    torch.cuda.synchronize()
-    ms = a.elapsed_time(b) / steps
     rays = cam["width"] * cam["height"]
+    res = {}
+    for name, opts in (("refit", {"scene": kept}), ("rebuild", {})):
+        for _ in range(warmup):
+            step(opts)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            loss = step(opts)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        res[name] = {"ms_per_step": ms, "Mrays_per_s": rays / (ms / 1e3) / 1e6, "loss": float(loss.item())}
+    kept.close()
     return {"workload": "256K surface Gaussians, 800x800, L2 loss vs perturbed-parameter target, k=16",
-            "ms_per_step": ms, "Mrays_per_s": rays / (ms / 1e3) / 1e6, "loss": float(loss.item()),
-            "step": "BVH build + forward + backward (atomics into all five parameter tensors)"}
+            "ms_per_step": res["refit"]["ms_per_step"], "Mrays_per_s": res["refit"]["Mrays_per_s"],
+            "loss": res["refit"]["loss"],
+            "step": "BVH refit in place + forward + backward (atomics into all five parameter tensors)",
+            "rebuild": dict(res["rebuild"], step="BVH built anew (radix tree) + forward + backward")}
 
 
 def _quat_mul(a, b):

@@ -314,6 +314,33 @@ GRTX_API int grtx_refit(const uint32_t *d_left, const uint32_t *d_right, const u
 GRTX_API int grtx_build_bvh(const grtx_gaussians *g, const grtx_params *p, int form, void *stream,
                             grtx_scene **out);
 
+/* Update modes of grtx_scene_update. */
+#define GRTX_UPDATE_REFIT 0
+#define GRTX_UPDATE_REBUILD 1
+
+/* Update a built scene in place for new parameters of the same Gaussians, as a training loop
+ * needs after each optimiser step. g must have the scene's n and sh_degree; the scene keeps its
+ * form, alpha_min, Morton code kind and builder.
+ * GRTX_UPDATE_REFIT (sphere and icosphere forms) keeps the tree's topology and leaf order. It
+ * recomputes every leaf's record, appearance and box from g (Sec. IV-A's per-Gaussian
+ * bounds), then refits the node boxes bottom-up, the last step of the LBVH build. A leaf whose
+ * Gaussian is now at or below alpha_min gets an empty box and a record that never hits. A
+ * Gaussian culled at the last build cannot be added by a refit: if one is now above alpha_min,
+ * the scene is rebuilt instead, and *rebuilt (may be NULL) is set to 1.
+ * GRTX_UPDATE_REBUILD always runs the full build of grtx_build_bvh (any form) and sets
+ * *rebuilt to 1. A refit leaves every array in place; a rebuild replaces them, freeing the old
+ * ones stream-ordered on `stream`, and keeps the trace workspace.
+ * Images do not depend on which happened: the tree only sets the traversal cost. Earlier work
+ * on the scene must be ordered before `stream`, which becomes the scene's stream. A world
+ * placing the scene needs grtx_world_update afterwards (its object bounds moved), and a
+ * server must not hold a scene while it is rebuilt. Synchronises the stream once (refit: to
+ * read the revival flag and the root box).
+ * Errors: GRTX_ERR_INVALID_ARG for a NULL scene, bad arrays, another n or sh_degree, an
+ * unknown mode, or a refit of the proxy form (the scene is unchanged then); after a CUDA or
+ * build error the scene may only be updated again or destroyed. */
+GRTX_API int grtx_scene_update(grtx_scene *scene, const grtx_gaussians *g, int mode, void *stream,
+                               int *rebuilt);
+
 /* The shared template mesh of GRTX_FORM_ICO20 / GRTX_FORM_ICO80 (host only, no device work):
  * a regular icosahedron (20 triangles), or for ICO80 the icosphere made by splitting each of
  * its faces into four at the edge midpoints pushed out to the sphere, with every face oriented

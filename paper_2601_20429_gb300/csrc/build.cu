@@ -25,16 +25,23 @@ inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 // ------------------------------------------------------------------------------------------
 // Activation and instance transform (Sec. II-B parameters; Sec. IV-A unit sphere).
 // ------------------------------------------------------------------------------------------
-__global__ void k_prep(const float *__restrict__ means, const float *__restrict__ log_scales,
-                       const float *__restrict__ quats, const float *__restrict__ logits, int64_t n,
-                       float alpha_min, float4 *__restrict__ geom, float *__restrict__ aabb)
+// Opacity of Gaussian i (sigmoid of its logit); it has a record and a box iff o > alpha_min.
+__device__ __forceinline__ float gaussian_opacity(const float *__restrict__ logits, int64_t i)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float o = 1.0f / (1.0f + expf(-logits[i]));
-    float *bb = aabb + 6 * i;
+    return 1.0f / (1.0f + expf(-logits[i]));
+}
+
+// Record (rows (A_j | mu_j), then (o, -kappa^2 log2(e) / 2, i, 0)) and world box of Gaussian i,
+// written to geom[0..3] and bb[0..5]. A Gaussian at or below alpha_min gets a zero record
+// (its test never passes) and an empty box.
+__device__ __forceinline__ void prep_one(const float *__restrict__ means, const float *__restrict__ log_scales,
+                                         const float *__restrict__ quats, const float *__restrict__ logits,
+                                         int64_t i, float alpha_min, float4 *__restrict__ geom,
+                                         float *__restrict__ bb)
+{
+    float o = gaussian_opacity(logits, i);
     if (!(o > alpha_min)) {
-        geom[4 * i + 0] = geom[4 * i + 1] = geom[4 * i + 2] = geom[4 * i + 3] = make_float4(0, 0, 0, 0);
+        geom[0] = geom[1] = geom[2] = geom[3] = make_float4(0, 0, 0, 0);
         bb[0] = bb[1] = bb[2] = INFINITY;
         bb[3] = bb[4] = bb[5] = -INFINITY;
         return;
@@ -54,10 +61,10 @@ __global__ void k_prep(const float *__restrict__ means, const float *__restrict_
         float f = 1.0f / (kap * s[j]);
         rows[j] = make_float4(R[0][j] * f, R[1][j] * f, R[2][j] * f, mu[j]);
     }
-    geom[4 * i + 0] = rows[0];
-    geom[4 * i + 1] = rows[1];
-    geom[4 * i + 2] = rows[2];
-    geom[4 * i + 3] = make_float4(o, -0.5f * kap * kap * 1.4426950408889634f, __int_as_float((int)i), 0.f);
+    geom[0] = rows[0];
+    geom[1] = rows[1];
+    geom[2] = rows[2];
+    geom[3] = make_float4(o, -0.5f * kap * kap * 1.4426950408889634f, __int_as_float((int)i), 0.f);
     for (int a = 0; a < 3; ++a) {
         float var = R[a][0] * R[a][0] * s[0] * s[0] + R[a][1] * R[a][1] * s[1] * s[1] +
                     R[a][2] * R[a][2] * s[2] * s[2];
@@ -66,6 +73,15 @@ __global__ void k_prep(const float *__restrict__ means, const float *__restrict_
         bb[a] = mu[a] - h;
         bb[3 + a] = mu[a] + h;
     }
+}
+
+__global__ void k_prep(const float *__restrict__ means, const float *__restrict__ log_scales,
+                       const float *__restrict__ quats, const float *__restrict__ logits, int64_t n,
+                       float alpha_min, float4 *__restrict__ geom, float *__restrict__ aabb)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    prep_one(means, log_scales, quats, logits, i, alpha_min, geom + 4 * i, aabb + 6 * i);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -479,6 +495,48 @@ __global__ void k_emit_nodes(const uint32_t *__restrict__ left, const uint32_t *
         s1 = load_slack(R, leaf_slack, node_slack);
     }
     nodes[4 * (size_t)i + 3] = make_float4(__uint_as_float(L), __uint_as_float(R), s0, s1);
+}
+
+// Refit for new parameters of the same Gaussians: the record, appearance and box of the
+// Gaussian gid[s] at every leaf slot s < n_valid are recomputed in place; the Gaussians culled
+// at build time (gid[n_valid..n)) only set *revived when one of them is now above alpha_min.
+__global__ void k_refit_records(const float *__restrict__ means, const float *__restrict__ log_scales,
+                                const float *__restrict__ quats, const float *__restrict__ logits,
+                                const float *__restrict__ sh, int n_sh, int app_stride,
+                                const uint32_t *__restrict__ gid, int64_t n_valid, int64_t n, float alpha_min,
+                                float4 *__restrict__ geom, float *__restrict__ leaf_aabb, float *__restrict__ app,
+                                unsigned *__restrict__ revived)
+{
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    uint32_t j = gid[s];
+    if (s < n_valid) {
+        prep_one(means, log_scales, quats, logits, j, alpha_min, geom + 4 * s, leaf_aabb + 6 * s);
+        const float *src = sh + (size_t)j * n_sh;
+        float *dst = app + (size_t)s * app_stride;
+        for (int c = 0; c < app_stride; ++c) dst[c] = c < n_sh ? src[c] : 0.f;
+    } else if (gaussian_opacity(logits, j) > alpha_min) {
+        atomicOr(revived, 1u);
+    }
+}
+
+// Left / right / parent arrays in the radix tree's layout (internal nodes 0..n-2, leaf j at
+// n - 1 + j, the root's parent GRTX_NONE) read back from the compacted nodes of a tree over
+// n >= 2 leaves.
+__global__ void k_unpack_tree(const float4 *__restrict__ nodes, int n, uint32_t *__restrict__ left,
+                              uint32_t *__restrict__ right, uint32_t *__restrict__ parent)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    float4 r = nodes[4 * (size_t)i + 3];
+    uint32_t L = __float_as_uint(r.x), R = __float_as_uint(r.y);
+    left[i] = L;
+    right[i] = R;
+    uint32_t pl = (L & GRTX_LEAF) ? (uint32_t)(n - 1) + (L & ~GRTX_LEAF) : L;
+    uint32_t pr = (R & GRTX_LEAF) ? (uint32_t)(n - 1) + (R & ~GRTX_LEAF) : R;
+    if (pl < (uint32_t)(2 * n - 1)) parent[pl] = (uint32_t)i;
+    if (pr < (uint32_t)(2 * n - 1)) parent[pr] = (uint32_t)i;
+    if (i == 0) parent[0] = GRTX_NONE;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -976,6 +1034,15 @@ int finish_tree(grtx_scene *sc, Alloc &A, const float *leaf_aabb_sorted, int64_t
     return GRTX_OK;
 }
 
+// World bounds of all leaves = union of the root's two child boxes (h_root: the root node).
+void set_bounds(grtx_scene *sc, const float *h_root)
+{
+    for (int c = 0; c < 3; ++c) {
+        sc->bounds[c] = std::min(h_root[c], h_root[6 + c]);
+        sc->bounds[3 + c] = std::max(h_root[3 + c], h_root[9 + c]);
+    }
+}
+
 int build_scene(const grtx_gaussians *g, const grtx_params *p, int form, grtx_scene *sc)
 {
     cudaStream_t s = sc->stream;
@@ -988,6 +1055,8 @@ int build_scene(const grtx_gaussians *g, const grtx_params *p, int form, grtx_sc
     int n_sh = sc->n_coef * 3;
     sc->app_stride = (n_sh + 3) & ~3;
     sc->alpha_min = p->alpha_min;
+    sc->bvh_codes = p->bvh_codes;
+    sc->bvh_builder = p->bvh_builder;
     TRY(A.get(&sc->d_counter, 8, false));
     GRTX_CUDA(cudaMemsetAsync(sc->d_counter, 0, 8 * sizeof(unsigned), s));
     if (n == 0) {
@@ -1027,12 +1096,14 @@ int build_scene(const grtx_gaussians *g, const grtx_params *p, int form, grtx_sc
     float *leaf_aabb;
     TRY(A.get(&sc->geom, 4 * nv, false));
     TRY(A.get(&sc->app, (size_t)sc->app_stride * nv, false));
-    TRY(A.get(&sc->gid, nv, false));
+    TRY(A.get(&sc->gid, n, false));                 // leaf slots, then the culled Gaussians
     TRY(A.get(&leaf_aabb, 6 * nv, true));
     k_gather_gaussians<<<grtx_div_up(nv, kThreads), kThreads, 0, s>>>(order, nv, geom_raw, aabb_raw, g->sh, n_sh,
                                                                       sc->app_stride, sc->geom, leaf_aabb,
                                                                       sc->app, sc->gid);
     GRTX_CHECK_LAUNCH("gather");
+    if (n > nv)
+        GRTX_CUDA(cudaMemcpyAsync(sc->gid + nv, order + nv, (size_t)(n - nv) * 4, cudaMemcpyDeviceToDevice, s));
     if (form != GRTX_FORM_PROXY20) {       // sphere and icosphere forms: one leaf per Gaussian
         if (form != GRTX_FORM_SPHERE) TRY(grtx_template_blas(form, &sc->tpl_nodes, &sc->tpl_tris));
         sc->n_leaves = nv;
@@ -1077,19 +1148,90 @@ int build_scene(const grtx_gaussians *g, const grtx_params *p, int form, grtx_sc
         GRTX_CUDA(cudaMemcpyAsync(sc->codes, tcodes, (size_t)nt * 8, cudaMemcpyDeviceToDevice, s));
         TRY(finish_tree(sc, A, tri_aabb, nt, p->bvh_builder, slack));
     }
-    // world bounds of all leaves = union of the root's two child boxes
     float h_root[16];
     GRTX_CUDA(cudaMemcpyAsync(h_root, sc->nodes, sizeof(h_root), cudaMemcpyDeviceToHost, s));
     GRTX_CUDA(cudaStreamSynchronize(s));
-    float a[6] = {h_root[0], h_root[1], h_root[2], h_root[3], h_root[4], h_root[5]};
-    float b[6] = {h_root[6], h_root[7], h_root[8], h_root[9], h_root[10], h_root[11]};
-    for (int c = 0; c < 3; ++c) {
-        sc->bounds[c] = std::min(a[c], b[c]);
-        sc->bounds[3 + c] = std::max(a[3 + c], b[3 + c]);
-    }
+    set_bounds(sc, h_root);
     if (sc->depth >= GRTX_STACK)
         return grtx_fail(GRTX_ERR_OVERFLOW_FATAL, "BVH depth " + std::to_string(sc->depth) +
                                                       " exceeds the traversal stack");
+    return GRTX_OK;
+}
+
+// Refit of a sphere- or icosphere-form scene with n_valid >= 1 for new parameters of the same
+// Gaussians: topology and leaf order kept, records / appearance / leaf boxes recomputed, node
+// boxes refitted bottom-up. *revived reports a build-time-culled Gaussian that is now valid
+// (the caller then rebuilds). One host round trip (flag and root box).
+int refit_scene(const grtx_gaussians *g, grtx_scene *sc, cudaStream_t s, bool *revived)
+{
+    Alloc A(s);
+    int64_t n = sc->n, nv = sc->n_valid;
+    unsigned *d_flag;
+    float *leaf_aabb;
+    TRY(A.get(&d_flag, 1, true));
+    TRY(A.get(&leaf_aabb, 6 * nv, true));
+    uint32_t *left = nullptr, *right = nullptr, *parent = nullptr, *cnt = nullptr;
+    float *node_aabb = nullptr;
+    if (nv >= 2) {
+        TRY(A.get(&left, nv - 1, true));
+        TRY(A.get(&right, nv - 1, true));
+        TRY(A.get(&parent, 2 * nv - 1, true));
+        TRY(A.get(&cnt, nv - 1, true));
+        TRY(A.get(&node_aabb, 6 * (nv - 1), true));
+    }
+    GRTX_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(unsigned), s));
+    k_refit_records<<<grtx_div_up(n, kThreads), kThreads, 0, s>>>(
+        g->means, g->log_scales, g->quats, g->opacity_logits, g->sh, sc->n_coef * 3, sc->app_stride, sc->gid, nv, n,
+        sc->alpha_min, sc->geom, leaf_aabb, sc->app, d_flag);
+    if (nv == 1) {
+        k_emit_single<<<1, 1, 0, s>>>(leaf_aabb, sc->nodes);
+    } else {
+        k_unpack_tree<<<grtx_div_up(nv - 1, kThreads), kThreads, 0, s>>>(sc->nodes, (int)nv, left, right, parent);
+        GRTX_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (nv - 1), s));
+        k_refit<<<grtx_div_up(nv, kThreads), kThreads, 0, s>>>(left, right, parent, leaf_aabb, (int)nv, node_aabb,
+                                                               cnt);
+        k_emit_nodes<<<grtx_div_up(nv - 1, kThreads), kThreads, 0, s>>>(left, right, leaf_aabb, node_aabb, (int)nv,
+                                                                        sc->nodes, nullptr, nullptr);
+    }
+    GRTX_CHECK_LAUNCH("refit");
+    unsigned h_flag = 0;
+    float h_root[16];
+    GRTX_CUDA(cudaMemcpyAsync(&h_flag, d_flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    GRTX_CUDA(cudaMemcpyAsync(h_root, sc->nodes, sizeof(h_root), cudaMemcpyDeviceToHost, s));
+    GRTX_CUDA(cudaStreamSynchronize(s));
+    *revived = h_flag != 0;
+    set_bounds(sc, h_root);
+    return GRTX_OK;
+}
+
+// Full rebuild with the scene's form, alpha_min, codes and builder; the new arrays replace the
+// old ones (freed stream-ordered on s), the trace workspace is kept.
+int rebuild_scene(const grtx_gaussians *g, grtx_scene *sc, cudaStream_t s)
+{
+    grtx_params p;
+    std::memset(&p, 0, sizeof(p));
+    p.alpha_min = sc->alpha_min;
+    p.bvh_codes = sc->bvh_codes;
+    p.bvh_builder = sc->bvh_builder;
+    grtx_scene *ns = new (std::nothrow) grtx_scene();
+    if (!ns) return grtx_fail(GRTX_ERR_OOM, "host allocation failed");
+    ns->stream = s;
+    int st = build_scene(g, &p, sc->form, ns);
+    if (st != GRTX_OK) {
+        free_scene_arrays(ns);
+        cudaStreamSynchronize(s);
+        delete ns;
+        return st;
+    }
+    void *ws = sc->ws;
+    size_t ws_bytes = sc->ws_bytes;
+    sc->ws = nullptr;
+    sc->stream = s;
+    free_scene_arrays(sc);
+    *sc = *ns;
+    sc->ws = ws;
+    sc->ws_bytes = ws_bytes;
+    delete ns;
     return GRTX_OK;
 }
 
@@ -1266,6 +1408,31 @@ extern "C" GRTX_API int grtx_build_bvh(const grtx_gaussians *g, const grtx_param
     }
     *out = sc;
     return GRTX_OK;
+}
+
+extern "C" GRTX_API int grtx_scene_update(grtx_scene *sc, const grtx_gaussians *g, int mode, void *stream,
+                                          int *rebuilt)
+{
+    if (rebuilt) *rebuilt = 0;
+    if (!sc) return grtx_fail(GRTX_ERR_INVALID_ARG, "scene is NULL");
+    int st = check_gaussians(g);
+    if (st) return st;
+    if (g->n != sc->n) return grtx_fail(GRTX_ERR_INVALID_ARG, "update needs the scene's number of Gaussians");
+    if (g->sh_degree != sc->sh_degree) return grtx_fail(GRTX_ERR_INVALID_ARG, "update needs the scene's SH degree");
+    if (mode != GRTX_UPDATE_REFIT && mode != GRTX_UPDATE_REBUILD)
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "unknown update mode");
+    if (mode == GRTX_UPDATE_REFIT && sc->form == GRTX_FORM_PROXY20)
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "refit needs the sphere or an icosphere form (rebuild the proxy form)");
+    cudaStream_t s = S(stream);
+    sc->stream = s;
+    if (mode == GRTX_UPDATE_REFIT && sc->n_valid > 0) {
+        bool revived = false;
+        st = refit_scene(g, sc, s, &revived);
+        if (st != GRTX_OK || !revived) return st;
+    }
+    st = rebuild_scene(g, sc, s);
+    if (st == GRTX_OK && rebuilt) *rebuilt = 1;
+    return st;
 }
 
 extern "C" GRTX_API int grtx_scene_info_get(const grtx_scene *sc, grtx_scene_info *info)

@@ -36,13 +36,14 @@ struct grtx_scene {
     int app_stride = 4;          // floats per appearance record (SH coefficients, padded to 4)
     int depth = 0;
     float alpha_min = 0.01f;
+    int bvh_codes = GRTX_CODES_SIZED, bvh_builder = GRTX_BUILDER_PLOC;   // as built (for rebuilds)
     int64_t n = 0, n_valid = 0, n_leaves = 0, n_nodes = 0;
     float bounds[6] = {0, 0, 0, 0, 0, 0};
     float4 *nodes = nullptr;     // [n_nodes][4]: BVH2 node, see grtx_scene_export
     float4 *geom = nullptr;      // [n_valid][4]: rows (A_j | mu_j) + (o, -kappa^2 log2(e)/2, id, 0), leaf order
     float4 *tris = nullptr;      // proxy form: [n_leaves][3] world triangle (v0 | gidx, v1, v2)
     float *app = nullptr;        // [n_valid][app_stride] SH coefficients in leaf order
-    uint32_t *gid = nullptr;     // [n_valid] Gaussian id of each sorted Gaussian
+    uint32_t *gid = nullptr;     // [n] Gaussian id of each sorted Gaussian, then of each culled one
     uint32_t *leaf_ids = nullptr;// [n_leaves] Gaussian id of each leaf
     uint64_t *codes = nullptr;   // [n_leaves] sorted Morton codes
     const float4 *tpl_nodes = nullptr;   // icosphere forms: shared template BVH (not owned)

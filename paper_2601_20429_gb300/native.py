@@ -164,6 +164,7 @@ _SIGS = {
     "grtx_ploc_tree": (C.c_int, [_fp, C.c_int64, _fp, _fp, _fp, C.POINTER(C.c_int), _fp]),
     "grtx_refit": (C.c_int, [_fp, _fp, _fp, _fp, C.c_int64, _fp, _fp, _fp]),
     "grtx_build_bvh": (C.c_int, [C.POINTER(grtx_gaussians), C.POINTER(grtx_params), C.c_int, _fp, C.POINTER(_fp)]),
+    "grtx_scene_update": (C.c_int, [_fp, C.POINTER(grtx_gaussians), C.c_int, _fp, C.POINTER(C.c_int)]),
     "grtx_scene_info_get": (C.c_int, [_fp, C.POINTER(grtx_scene_info)]),
     "grtx_scene_export": (C.c_int, [_fp, _fp, _fp, _fp, _fp]),
     "grtx_scene_destroy": (None, [_fp]),
@@ -346,6 +347,17 @@ def grtx_build_bvh(g: grtx_gaussians, p: grtx_params, form: int, stream=None) ->
     check(lib().grtx_build_bvh(C.byref(g), C.byref(p), int(form), stream_handle(stream), C.byref(out)),
           "grtx_build_bvh")
     return out.value
+
+
+UPDATE_MODES = {"refit": 0, "rebuild": 1}
+
+
+def grtx_scene_update(scene: int, g: grtx_gaussians, mode: int, stream=None) -> bool:
+    """Update a scene in place for new parameters; True when it was rebuilt."""
+    rebuilt = C.c_int(0)
+    check(lib().grtx_scene_update(C.c_void_p(scene), C.byref(g), int(mode), stream_handle(stream), C.byref(rebuilt)),
+          "grtx_scene_update")
+    return bool(rebuilt.value)
 
 
 def grtx_scene_info_get(scene: int) -> dict:

@@ -50,6 +50,18 @@ class Scene:
         return cls(g.means, g.log_scales, g.quats, g.logits, g.sh, g.sh_degree, form, alpha_min, stream, bvh_codes,
                    bvh_builder)
 
+    def update(self, means, log_scales, quats, logits, sh, mode: str = "refit", stream=None) -> bool:
+        """New parameters for the same Gaussians (same n and SH degree), in place: "refit" keeps
+        the tree and refits its boxes (sphere and icosphere forms), "rebuild" builds it anew.
+        A refit falls back to a rebuild when a Gaussian culled at the last build is now above
+        alpha_min. Returns True when the tree was rebuilt. The image does not depend on which."""
+        dev = self.tensors[0].device
+        tensors = tuple(_cuda_f32(a, dev) for a in (means, log_scales, quats, logits, sh))
+        g = N.make_gaussians(*tensors, self.sh_degree)
+        rebuilt = N.grtx_scene_update(self.handle, g, N.UPDATE_MODES[mode], stream)
+        self.tensors, self._g = tensors, g
+        return rebuilt
+
     @property
     def n(self) -> int:
         return int(self.tensors[3].shape[0])
@@ -168,17 +180,30 @@ def backward(scene: Scene, cam: dict | None, rgbT, dL_drgbT, rays=None, stream=N
 
 
 class RenderFunction(torch.autograd.Function):
-    """Differentiable render: builds the BVH from the current parameters, traces forward,
-    and in backward re-traverses the same rounds to accumulate parameter gradients. The BVH
-    is rebuilt at every step, so the faster-to-build radix tree ("lbvh") is the default
-    here; opts may set bvh_builder / bvh_codes."""
+    """Differentiable render: brings the BVH up to the current parameters, traces forward,
+    and in backward re-traverses the same rounds to accumulate parameter gradients. Without a
+    scene in opts the BVH is built anew at every call (the faster-to-build radix tree "lbvh"
+    by default; opts may set bvh_builder / bvh_codes) and freed after backward. With
+    opts["scene"] (a sphere- or icosphere-form Scene of the same Gaussians, kept by the caller
+    across steps) it is updated in place, by opts["update"] = "refit" (default) or
+    "rebuild"."""
 
     @staticmethod
     def forward(ctx, means, log_scales, quats, logits, sh, sh_degree, cam, opts):
         o = dict(opts)
-        scene = Scene(means.detach(), log_scales.detach(), quats.detach(), logits.detach(), sh.detach(), sh_degree,
-                      "sphere", o.pop("alpha_min", 0.01), bvh_codes=o.pop("bvh_codes", "sized"),
-                      bvh_builder=o.pop("bvh_builder", "lbvh"))
+        params = (means.detach(), log_scales.detach(), quats.detach(), logits.detach(), sh.detach())
+        scene = o.pop("scene", None)
+        mode = o.pop("update", "refit")
+        ctx.owned = scene is None
+        if scene is None:
+            scene = Scene(*params, sh_degree, "sphere", o.pop("alpha_min", 0.01), bvh_codes=o.pop("bvh_codes", "sized"),
+                          bvh_builder=o.pop("bvh_builder", "lbvh"))
+        else:
+            if scene.sh_degree != int(sh_degree):
+                raise ValueError("the scene's SH degree differs from sh_degree")
+            for key in ("alpha_min", "bvh_codes", "bvh_builder"):
+                o.pop(key, None)
+            scene.update(*params, mode=mode)
         rgbT = render(scene, cam, **o)["rgbT"]
         ctx.scene, ctx.cam, ctx.opts = scene, cam, o
         ctx.save_for_backward(rgbT)
@@ -188,7 +213,8 @@ class RenderFunction(torch.autograd.Function):
     def backward(ctx, grad_rgbT):
         (rgbT,) = ctx.saved_tensors
         g = backward(ctx.scene, ctx.cam, rgbT, grad_rgbT.float().contiguous(), **ctx.opts)
-        ctx.scene.close()
+        if ctx.owned:
+            ctx.scene.close()
         return g["means"], g["log_scales"], g["quats"], g["opacity_logits"], g["sh"], None, None, None
 
 

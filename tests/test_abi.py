@@ -79,6 +79,9 @@ def test_host_side_errors_of_the_extensions(lib):
     assert lib.grtx_world_create(inst, 1, None, C.byref(w)) == 1                        # NULL scene
     assert b"scene is NULL" in lib.grtx_last_error()
     assert lib.grtx_world_update(None, inst, 1, None) == 1
+    rebuilt = C.c_int(5)
+    assert lib.grtx_scene_update(None, None, 0, None, C.byref(rebuilt)) == 1 and rebuilt.value == 0
+    assert b"scene is NULL" in lib.grtx_last_error()
     assert lib.grtx_world_trace_forward(None, None, None, None, None) == 1
     lib.grtx_world_destroy(None)
     cam = N.grtx_camera()
