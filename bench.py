@@ -624,6 +624,16 @@ def main():
     st_plain_ckpt = N.stats_dict(R.render(sc_plain, cam, k=k, traversal="checkpoint", out=out,
                                           want_stats=True)["stats"])
 
+    # total against distinct node fetches per ray (Sec. III-C's revisits): the fetches of every
+    # 1009th ray logged in order (instrumented run, not timed)
+    def fetch_log(scene, traversal, cap):
+        r = R.render(scene, cam, k=k, traversal=traversal, out=out, visit_log=(1009, n_rays // 1009 + 1, cap))
+        return R.visit_counts(r["visits"], r["visits_n"])
+
+    revisits = {"grtx": fetch_log(sc, "checkpoint", 4096), "grtx_restart": fetch_log(sc, "restart", 4096),
+                "plain": fetch_log(sc_plain, "restart", 8192),
+                "plain_checkpoint": fetch_log(sc_plain, "checkpoint", 8192)}
+
     def frame():
         R.render(sc, cam, k=k, out=out)
 
@@ -720,16 +730,20 @@ def main():
                        "parallelism": f"replicas x{dist.world}"},
             "gpu_launches": args.steps,
             "grtx": {"Mrays_per_s": value, "ms_per_frame": ms, "nodes_per_ray": nodes_per_ray(st_grtx),
+                     "fetches_vs_distinct": revisits["grtx"],
                      "build_ms": build_sphere_ms, "bvh_bytes": info["bytes_nodes"] + info["bytes_leaves"],
                      "depth": info["depth"], "workspace_bytes": info["bytes_workspace"]},
             "grtx_restart": {"Mrays_per_s": n_rays / (statistics.mean(times_restart) / 1e3) / 1e6,
-                             "ms_per_frame": statistics.mean(times_restart), "nodes_per_ray": nodes_per_ray(st_restart)},
+                             "ms_per_frame": statistics.mean(times_restart), "nodes_per_ray": nodes_per_ray(st_restart),
+                             "fetches_vs_distinct": revisits["grtx_restart"]},
             "plain_checkpoint": {"Mrays_per_s": n_rays / (statistics.mean(times_plain_ckpt) / 1e3) / 1e6,
                                  "ms_per_frame": statistics.mean(times_plain_ckpt),
-                                 "nodes_per_ray": nodes_per_ray(st_plain_ckpt)},
+                                 "nodes_per_ray": nodes_per_ray(st_plain_ckpt),
+                                 "fetches_vs_distinct": revisits["plain_checkpoint"]},
             "k_sweep_Mrays_per_s": k_sweep,
             "plain": {"Mrays_per_s": n_rays / (statistics.mean(times_plain) / 1e3) / 1e6,
                       "ms_per_frame": statistics.mean(times_plain), "nodes_per_ray": nodes_per_ray(st_plain),
+                      "fetches_vs_distinct": revisits["plain"],
                       "build_ms": build_plain_ms, "bvh_bytes": info_plain["bytes_nodes"] + info_plain["bytes_leaves"],
                       "depth": info_plain["depth"]},
             "ablations": ablations,

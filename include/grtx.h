@@ -174,6 +174,15 @@ typedef struct grtx_stats {
  * n_blended: optional device [n_rays], Gaussians composited per ray. blended_ids: optional
  * device [n_rays][ids_cap], the first ids_cap composited Gaussian ids per ray in blend order
  * (unused tail entries are 0xFFFFFFFF). stats: optional device grtx_stats (accumulated).
+ * visits / visits_n: optional node-visit log of sampled rays, for counting total against
+ * distinct node fetches (a revisit is a fetch of a node the ray fetched before, the work
+ * checkpointing removes, Sec. III-C). A ray with output index p is logged when
+ * p % visits_stride == 0 and p / visits_stride < visits_rows: row r = p / visits_stride of
+ * device [visits_rows][visits_cap] receives its fetches in order (internal node index, or
+ * GRTX_LEAF | leaf index for a leaf record; the nodes of an icosphere template are not
+ * logged), and visits_n[r] their number, which may exceed visits_cap (the row then holds the
+ * first visits_cap). Rows of rays that are not traced keep their contents; visits_n is
+ * zeroed by the call. Both pointers or neither; cap, stride and rows >= 1 when given.
  * With any optional output requested the kernel takes a slower instrumented path. */
 typedef struct grtx_trace_outputs {
     float *rgbT;
@@ -182,6 +191,9 @@ typedef struct grtx_trace_outputs {
     int32_t ids_cap;
     int32_t reserved;
     grtx_stats *stats;
+    uint32_t *visits;
+    uint32_t *visits_n;
+    int32_t visits_cap, visits_stride, visits_rows, reserved2;
 } grtx_trace_outputs;
 
 /* Host-readable description of a built scene. */

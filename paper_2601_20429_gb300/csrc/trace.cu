@@ -272,13 +272,23 @@ extern "C" GRTX_API int grtx_trace_forward(grtx_scene *sc, const grtx_camera *ca
     if (!out || !out->rgbT) return grtx_fail(GRTX_ERR_INVALID_ARG, "rgbT output is NULL");
     if (((uintptr_t)out->rgbT & 15) != 0) return grtx_fail(GRTX_ERR_INVALID_ARG, "rgbT must be 16-byte aligned");
     if (out->blended_ids && out->ids_cap <= 0) return grtx_fail(GRTX_ERR_INVALID_ARG, "ids_cap must be positive");
+    if ((out->visits != nullptr) != (out->visits_n != nullptr))
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "visits and visits_n go together");
+    if (out->visits && (out->visits_cap <= 0 || out->visits_stride <= 0 || out->visits_rows <= 0))
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "visits_cap, visits_stride and visits_rows must be positive");
     a.rgbT = (float4 *)out->rgbT;
     a.n_blended = out->n_blended;
     a.ids = out->blended_ids;
     a.ids_cap = out->ids_cap;
     a.stats = out->stats;
+    a.visits = out->visits;
+    a.visits_n = out->visits_n;
+    a.visits_cap = out->visits_cap;
+    a.visits_stride = out->visits_stride;
+    a.visits_rows = out->visits_rows;
     cudaStream_t s = S(stream);
-    bool instr = out->n_blended || out->blended_ids || out->stats;
+    bool instr = out->n_blended || out->blended_ids || out->stats || out->visits;
+    if (out->visits) GRTX_CUDA(cudaMemsetAsync(out->visits_n, 0, (size_t)out->visits_rows * 4, s));
     if (out->blended_ids)
         GRTX_CUDA(cudaMemsetAsync(out->blended_ids, 0xff, (size_t)cam->width * cam->height * out->ids_cap * 4, s));
     return run(sc, a, p->k, instr, false, sc->d_counter, s);

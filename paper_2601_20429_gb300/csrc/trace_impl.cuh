@@ -54,6 +54,8 @@ struct TraceArgs {
     int32_t *n_blended;
     uint32_t *ids;
     int ids_cap;
+    uint32_t *visits, *visits_n;   // visit log of sampled rays (see grtx_trace_outputs)
+    int visits_cap, visits_stride, visits_rows;
     grtx_stats *stats;
     // backward
     const float4 *fwd_rgbT, *dL_drgbT;
@@ -75,9 +77,36 @@ struct ServeSeg {
 
 struct Counters {
     unsigned nodes, leaves, blended, rounds, ckpt, evictions, fallbacks, overflow;
+    uint32_t *vlog;    // the current ray's row of the visit log, or NULL (instrumented path only)
+    unsigned vn, vcap;
 };
 
+// One node or leaf-record fetch of the current ray into its visit-log row (if it has one).
+__device__ __forceinline__ void log_visit(Counters &c, uint32_t ref)
+{
+    if (c.vlog) {
+        if (c.vn < c.vcap) c.vlog[c.vn] = ref;
+        ++c.vn;
+    }
+}
+
 #define GRTX_INF __int_as_float(0x7f800000)
+
+// Start / finish the visit log of one ray (valid: the lane holds a ray with output index pix).
+__device__ __forceinline__ void visits_begin(const TraceArgs &a, Counters &c, bool valid, int64_t pix)
+{
+    c.vlog = nullptr;
+    c.vn = 0;
+    if (a.visits && valid && pix % a.visits_stride == 0 && pix / a.visits_stride < a.visits_rows) {
+        c.vlog = a.visits + (size_t)(pix / a.visits_stride) * a.visits_cap;
+        c.vcap = (unsigned)a.visits_cap;
+    }
+}
+__device__ __forceinline__ void visits_end(const TraceArgs &a, Counters &c, int64_t pix)
+{
+    if (c.vlog) a.visits_n[pix / a.visits_stride] = c.vn;
+    c.vlog = nullptr;
+}
 
 // ------------------------------------------------------------------------------------------
 // Rays
@@ -458,7 +487,10 @@ __device__ __forceinline__ bool trace_round(const TraceArgs &a, const SceneRef &
             }
         } else if (ref & GRTX_LEAF) {
             uint32_t idx = ref & ~GRTX_LEAF;
-            if (INSTR) cnt.leaves++;
+            if (INSTR) {
+                cnt.leaves++;
+                log_visit(cnt, ref);
+            }
             uint32_t gi;
             bool touch = true;
             if (FORM == FORM_PROXY) {
@@ -487,7 +519,10 @@ __device__ __forceinline__ bool trace_round(const TraceArgs &a, const SceneRef &
                 }
             }
         } else {
-            if (INSTR) cnt.nodes++;
+            if (INSTR) {
+                cnt.nodes++;
+                log_visit(cnt, ref);
+            }
             const float4 *nd = sc.nodes + 4 * (size_t)ref;
             float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
             uint32_t c0 = __float_as_uint(n3.x), c1 = __float_as_uint(n3.y);
@@ -612,7 +647,10 @@ __device__ __forceinline__ bool packet_round(const TraceArgs &a, const SceneRef 
             if (ref & GRTX_LEAF) {
                 if (go) {
                     uint32_t idx = ref & ~GRTX_LEAF;
-                    if (INSTR) cnt.leaves++;
+                    if (INSTR) {
+                        cnt.leaves++;
+                        log_visit(cnt, ref);
+                    }
                     uint32_t gi;
                     bool touch = true;
                     if (FORM == FORM_PROXY) {
@@ -648,7 +686,10 @@ __device__ __forceinline__ bool packet_round(const TraceArgs &a, const SceneRef 
                 bool h0 = false, h1 = false, near0 = true;
                 float e0 = 0.f, e1 = 0.f;
                 if (go) {
-                    if (INSTR) cnt.nodes++;
+                    if (INSTR) {
+                        cnt.nodes++;
+                        log_visit(cnt, ref);
+                    }
                     float x0, x1;
                     slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, o, inv, tn, tf, e0, x0);
                     slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, o, inv, tn, tf, e1, x1);
@@ -1046,7 +1087,7 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, BWD)) k_trace(Trac
     KBuf<K> kb;
     kb.t = s_kt + threadIdx.x;
     kb.id = s_ki + threadIdx.x;
-    Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
+    Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0, nullptr, 0, 0};
     unsigned rays = 0;
     for (;;) {
         unsigned base = 0;
@@ -1058,12 +1099,14 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, BWD)) k_trace(Trac
         float tn, tf;
         bool valid = make_ray(a.cam, base + lane, pix, o, d, tn, tf);
         rays += valid;
+        if (INSTR) visits_begin(a, cnt, valid, pix);
         if (!BWD && a.traversal == GRTX_TRAVERSAL_RESTART)
             trace_warp_restart<K, FORM, INSTR>(a, a.sc, a.rgbT, slot, valid, pix, o, d, tn, tf, kb, cnt,
                                                s_pst[threadIdx.x >> 5]);
         else
             trace_warp<K, FORM, INSTR, BWD>(a, a.sc, a.rgbT, slot, valid, pix, o, d, tn, tf, kb, cnt,
                                             s_pst[threadIdx.x >> 5]);
+        if (INSTR) visits_end(a, cnt, pix);
         __syncwarp();
     }
     if (INSTR && a.stats) {
@@ -1091,7 +1134,7 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, false)) k_serve(Tr
     KBuf<K> kb;
     kb.t = s_kt + threadIdx.x;
     kb.id = s_ki + threadIdx.x;
-    Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
+    Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0, nullptr, 0, 0};
     for (;;) {
         unsigned base = 0;
         if (lane == 0) base = atomicAdd(a.queue, 32u);

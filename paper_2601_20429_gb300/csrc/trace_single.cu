@@ -75,7 +75,10 @@ __device__ __forceinline__ int packet_collect(const TraceArgs &a, const SceneRef
             if (ref & GRTX_LEAF) {
                 if (go) {
                     uint32_t idx = ref & ~GRTX_LEAF;
-                    if (INSTR) cnt.leaves++;
+                    if (INSTR) {
+                        cnt.leaves++;
+                        log_visit(cnt, ref);
+                    }
                     uint32_t gi;
                     bool touch = true;
                     if (FORM == FORM_PROXY) {
@@ -105,7 +108,10 @@ __device__ __forceinline__ int packet_collect(const TraceArgs &a, const SceneRef
                 uint32_t c0 = __float_as_uint(n3.x), c1 = __float_as_uint(n3.y);
                 bool h0 = false, h1 = false, near0 = true;
                 if (go) {
-                    if (INSTR) cnt.nodes++;
+                    if (INSTR) {
+                        cnt.nodes++;
+                        log_visit(cnt, ref);
+                    }
                     float e0, x0, e1, x1;
                     slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, o, inv, tn, tf, e0, x0);
                     slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, o, inv, tn, tf, e1, x1);
@@ -206,7 +212,7 @@ __global__ void __launch_bounds__(kBlock, 8) k_trace_single(TraceArgs a)
     KBuf<kFallbackK> kb;
     kb.t = s_kt + threadIdx.x;
     kb.id = s_ki + threadIdx.x;
-    Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
+    Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0, nullptr, 0, 0};
     unsigned rays = 0, collected = 0;
     for (;;) {
         unsigned base = 0;
@@ -218,7 +224,9 @@ __global__ void __launch_bounds__(kBlock, 8) k_trace_single(TraceArgs a)
         float tn, tf;
         bool valid = make_ray(a.cam, base + lane, pix, o, d, tn, tf);
         rays += valid;
+        if (INSTR) visits_begin(a, cnt, valid, pix);
         single_ray<FORM, INSTR>(a, a.sc, slot, valid, pix, o, d, tn, tf, kb, cnt, collected, s_pst[threadIdx.x >> 5]);
+        if (INSTR) visits_end(a, cnt, pix);
         __syncwarp();
     }
     if (INSTR && a.stats) {

@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, false)) k_trace_wo
     KBuf<K> kb;
     kb.t = s_kt + threadIdx.x;
     kb.id = s_ki + threadIdx.x;
-    Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0};
+    Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0, nullptr, 0, 0};
     unsigned rays = 0;
     for (;;) {
         unsigned b = 0;
@@ -682,6 +682,8 @@ extern "C" GRTX_API int grtx_world_trace_forward(grtx_world *w, const grtx_camer
     if (!out || !out->rgbT || ((uintptr_t)out->rgbT & 15))
         return grtx_fail(GRTX_ERR_INVALID_ARG, "rgbT must be a 16-byte aligned device pointer");
     if (out->blended_ids && out->ids_cap <= 0) return grtx_fail(GRTX_ERR_INVALID_ARG, "ids_cap must be positive");
+    if (out->visits || out->visits_n)
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "visit logs are not available for worlds (node indices of the levels collide)");
     WorldArgs W = {};
     TraceArgs &a = W.a;
     st = grtx_fill_camera(a.cam, a.n_items, cam);

@@ -116,7 +116,9 @@ class grtx_stats(C.Structure):
 
 class grtx_trace_outputs(C.Structure):
     _fields_ = [("rgbT", _fp), ("n_blended", _fp), ("blended_ids", _fp), ("ids_cap", C.c_int32),
-                ("reserved", C.c_int32), ("stats", _fp)]
+                ("reserved", C.c_int32), ("stats", _fp), ("visits", _fp), ("visits_n", _fp),
+                ("visits_cap", C.c_int32), ("visits_stride", C.c_int32), ("visits_rows", C.c_int32),
+                ("reserved2", C.c_int32)]
 
 
 class grtx_scene_info(C.Structure):
@@ -384,11 +386,17 @@ def grtx_generate_rays(cam: grtx_camera, origins, dirs, tnear=None, tfar=None, s
 
 
 def grtx_trace_forward(scene: int, cam: grtx_camera, p: grtx_params, rgbT, n_blended=None, blended_ids=None,
-                       stats=None, stream=None):
+                       stats=None, stream=None, visits=None, visits_n=None, visits_stride: int = 1):
+    """visits: optional [rows, cap] uint32/int32 device log of every visits_stride-th ray's node
+    fetches, visits_n: [rows] their counts (see grtx_trace_outputs)."""
     out = grtx_trace_outputs()
     out.rgbT, out.n_blended, out.blended_ids = ptr(rgbT), ptr(n_blended), ptr(blended_ids)
     out.ids_cap = int(blended_ids.shape[-1]) if blended_ids is not None else 0
     out.stats = ptr(stats)
+    if visits is not None:
+        out.visits, out.visits_n = ptr(visits), ptr(visits_n)
+        out.visits_rows, out.visits_cap = int(visits.shape[0]), int(visits.shape[1])
+        out.visits_stride = int(visits_stride)
     check(lib().grtx_trace_forward(C.c_void_p(scene), C.byref(cam), C.byref(p), C.byref(out), stream_handle(stream)),
           "grtx_trace_forward")
 

@@ -148,8 +148,10 @@ def n_rays_of(cam: dict, rays=None) -> int:
 
 
 def render(scene: Scene, cam: dict | None, rays=None, out=None, ids_cap: int = 0, want_n_blended=False,
-           want_stats=False, stream=None, **params):
-    """Forward trace. Returns dict(rgbT [n_rays, 4], n_blended?, ids?, stats?)."""
+           want_stats=False, stream=None, visit_log=None, **params):
+    """Forward trace. Returns dict(rgbT [n_rays, 4], n_blended?, ids?, stats?, visits?,
+    visits_n?). visit_log = (stride, rows, cap) logs the node fetches of every stride-th ray
+    (output index), up to rows rays and cap fetches each."""
     p = trace_params(alpha_min=scene.alpha_min, **params)
     c = N.make_camera(cam, rays)
     n = n_rays_of(cam, rays)
@@ -158,7 +160,13 @@ def render(scene: Scene, cam: dict | None, rays=None, out=None, ids_cap: int = 0
     nb = torch.empty(n, dtype=torch.int32, device=dev) if want_n_blended else None
     ids = torch.empty((n, ids_cap), dtype=torch.int32, device=dev) if ids_cap > 0 else None
     st = N.stats_tensor(dev) if want_stats else None
-    N.grtx_trace_forward(scene.handle, c, p, rgbT, nb, ids, st, stream)
+    vis = vis_n = None
+    stride = 1
+    if visit_log is not None:
+        stride, rows, cap = (int(v) for v in visit_log)
+        vis = torch.empty((rows, cap), dtype=torch.int32, device=dev)
+        vis_n = torch.empty(rows, dtype=torch.int32, device=dev)
+    N.grtx_trace_forward(scene.handle, c, p, rgbT, nb, ids, st, stream, vis, vis_n, stride)
     res = {"rgbT": rgbT}
     if nb is not None:
         res["n_blended"] = nb
@@ -166,7 +174,24 @@ def render(scene: Scene, cam: dict | None, rays=None, out=None, ids_cap: int = 0
         res["ids"] = ids
     if st is not None:
         res["stats"] = st
+    if vis is not None:
+        res["visits"], res["visits_n"] = vis, vis_n
     return res
+
+
+def visit_counts(visits, visits_n) -> dict:
+    """Per logged ray: node and leaf fetches, total and distinct, from a visit log
+    (numpy or torch; rows whose count exceeds the log's width are left out)."""
+    import numpy as np
+    V = visits.cpu().numpy() if hasattr(visits, "cpu") else np.asarray(visits)
+    n = visits_n.cpu().numpy() if hasattr(visits_n, "cpu") else np.asarray(visits_n)
+    V = V.view(np.uint32)
+    rows = [r for r in range(V.shape[0]) if 0 < n[r] <= V.shape[1]]
+    tot = np.array([n[r] for r in rows], dtype=np.int64)
+    uniq = np.array([len(np.unique(V[r, : n[r]])) for r in rows], dtype=np.int64)
+    return {"rays": len(rows), "truncated": int((n > V.shape[1]).sum()), "fetches_per_ray": float(tot.mean()) if rows else 0.0,
+            "distinct_per_ray": float(uniq.mean()) if rows else 0.0,
+            "revisit_fraction": float(1.0 - uniq.sum() / tot.sum()) if rows and tot.sum() else 0.0}
 
 
 def backward(scene: Scene, cam: dict | None, rgbT, dL_drgbT, rays=None, stream=None, **params):

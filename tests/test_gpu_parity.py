@@ -648,3 +648,63 @@ def _compare_gradients_with_oracle(S, sc, cam, rays_dev, rays_np, w, ref_g, k):
     for kg, ko in names.items():
         e = rel_err(grads[kg].cpu().numpy()[keep], ref_g[ko][keep])
         assert e <= 1e-3, (kg, e, len(differ))
+
+
+# ------------------------------------------------------------------ visit log (total vs distinct fetches)
+
+
+def _logged(sc, cam, stride=1, cap=4096, **kw):
+    n = cam["width"] * cam["height"]
+    rows = (n + stride - 1) // stride
+    r = R.render(sc, cam, want_stats=True, want_n_blended=True, visit_log=(stride, rows, cap), **kw)
+    torch.cuda.synchronize()
+    return r, r["visits"].cpu().numpy().view(np.uint32), r["visits_n"].cpu().numpy(), N.stats_dict(r["stats"])
+
+
+@pytest.mark.parametrize("form", ["sphere", "proxy20"])
+def test_visit_log_counts_every_fetch_and_checkpoints_revisit_nothing(dense, form):
+    """The log of every ray sums to the fetch counters. With checkpointed rounds (and no
+    capacity fallback) no ray fetches a node or leaf twice (Sec. III-C); restarting from the
+    root re-fetches the upper levels every round."""
+    g, cam, S, rays, ref = dense
+    sc = R.Scene.from_params(g, form=form)
+    out = {}
+    for trav in ("checkpoint", "restart"):
+        r, V, n, st = _logged(sc, cam, cap=16384, k=4, traversal=trav)
+        assert int(n.sum()) == st["nodes"] + st["leaves"]
+        for row in range(V.shape[0]):                      # logged ids are real nodes / leaves
+            ids = V[row, : min(n[row], V.shape[1])]        # (a longer trace keeps its first cap)
+            inner = ids < np.uint32(0x80000000)
+            assert (ids[inner] < sc.info()["n_nodes"]).all()
+            assert ((ids[~inner] & 0x7FFFFFFF) < sc.info()["n_leaves"]).all()
+        out[trav] = (R.visit_counts(r["visits"], r["visits_n"]), st, r["rgbT"].cpu().numpy())
+    ck, rs = out["checkpoint"], out["restart"]
+    np.testing.assert_allclose(ck[2], rs[2], rtol=0, atol=1e-6)
+    assert rs[0]["revisit_fraction"] > 0.1
+    if ck[1]["fallbacks"] == 0:
+        assert ck[0]["revisit_fraction"] == 0.0 and ck[0]["fetches_per_ray"] == ck[0]["distinct_per_ray"]
+    if form == "sphere":                                   # (proxy rays overflow their lists here
+        assert ck[1]["fallbacks"] == 0                     #  and restart from the root)
+        assert ck[0]["truncated"] == 0 and ck[0]["rays"] == cam["width"] * cam["height"]
+        assert rs[1]["nodes"] + rs[1]["leaves"] > ck[1]["nodes"] + ck[1]["leaves"]
+    sc.close()
+
+
+def test_visit_log_samples_every_stride_th_ray(dense):
+    g, cam, S, rays, ref = dense
+    sc = R.Scene.from_params(g)
+    _, V1, n1, _ = _logged(sc, cam, stride=1, k=8)
+    _, V7, n7, _ = _logged(sc, cam, stride=7, cap=64, k=8)           # truncated rows keep the count
+    np.testing.assert_array_equal(n7, n1[::7])
+    for row in range(len(n7)):
+        m = min(n7[row], 64)
+        np.testing.assert_array_equal(V7[row, :m], V1[7 * row, :m])
+    # the single-round packet path logs too: it fetches each needed node once
+    r, V, n, st = _logged(sc, cam, k=8, traversal="single")
+    assert int(n.sum()) == st["nodes"] + st["leaves"]
+    assert R.visit_counts(r["visits"], r["visits_n"])["revisit_fraction"] == 0.0
+    with pytest.raises(N.GrtxError, match="visits and visits_n"):
+        rgbT = torch.empty((cam["width"] * cam["height"], 4), device="cuda")
+        N.grtx_trace_forward(sc.handle, N.make_camera(cam, None), R.trace_params(), rgbT,
+                             visits=torch.empty((4, 4), dtype=torch.int32, device="cuda"), visits_n=None)
+    sc.close()
