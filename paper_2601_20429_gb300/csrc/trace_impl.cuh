@@ -362,13 +362,18 @@ __device__ __forceinline__ void sh_color(const float *__restrict__ f, int deg, i
     c[0] = fmaxf(acc[0], 0.f); c[1] = fmaxf(acc[1], 0.f); c[2] = fmaxf(acc[2], 0.f);
 }
 
-// Slab test of one child box against the ray over [tn, tf]: entry / exit distances.
+// Slab test of one child box against the ray over [tn, tf]: entry / exit distances, each
+// plane distance as one FMA, l * inv - o * inv. Its rounding error is an ulp of the origin's
+// plane distance, far inside the margin between a box's entry and the depth of any Gaussian hit
+// in it, except for grazing hits at alpha_min; an axis-parallel ray (inv = 1e30) lying exactly
+// in a face plane may lose that box, which it could only touch tangentially.
 __device__ __forceinline__ void slab(float lx, float ly, float lz, float hx, float hy, float hz, float3 o, float3 inv,
                                      float tn, float tf, float &t0, float &t1)
 {
-    float ax = (lx - o.x) * inv.x, bx = (hx - o.x) * inv.x;
-    float ay = (ly - o.y) * inv.y, by = (hy - o.y) * inv.y;
-    float az = (lz - o.z) * inv.z, bz = (hz - o.z) * inv.z;
+    const float px = -o.x * inv.x, py = -o.y * inv.y, pz = -o.z * inv.z;
+    float ax = fmaf(lx, inv.x, px), bx = fmaf(hx, inv.x, px);
+    float ay = fmaf(ly, inv.y, py), by = fmaf(hy, inv.y, py);
+    float az = fmaf(lz, inv.z, pz), bz = fmaf(hz, inv.z, pz);
     t0 = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fmaxf(fminf(az, bz), tn));
     t1 = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fminf(fmaxf(az, bz), tf));
 }
