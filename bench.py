@@ -525,7 +525,8 @@ def bench_world(steps: int, stream, flush):
 
 def bench_outdoor(steps: int, stream, flush):
     """6M-Gaussian outdoor scene, 1920x1080 fisheye plus one bounce off a mirror or through a
-    glass ball: primary and secondary rays timed separately (explicit ray lists), k = 16."""
+    glass ball: primary and secondary rays timed separately (explicit ray lists; the primary
+    list is the camera's image of rays, traced in pixel tiles), k = 16."""
     import torch
     from paper_2601_20429_gb300 import native as N
     from paper_2601_20429_gb300 import render as R
@@ -551,16 +552,16 @@ def bench_outdoor(steps: int, stream, flush):
     sec_rays = [t[:m] for t in sec]
     out_p = torch.empty((n, 4), device="cuda")
     out_s = torch.empty((max(m, 1), 4), device="cuda")
-    tp = time_frames(lambda: R.render(sc, None, rays=prim, k=cfg["k"], out=out_p), steps, 2, flush, stream)
-    tp32 = time_frames(lambda: R.render(sc, None, rays=prim, k=32, out=out_p), steps, 2, flush, stream)
-    st_p32 = N.stats_dict(R.render(sc, None, rays=prim, k=32, want_stats=True)["stats"])
+    tp = time_frames(lambda: R.render(sc, cam, rays=prim, k=cfg["k"], out=out_p), steps, 2, flush, stream)
+    tp32 = time_frames(lambda: R.render(sc, cam, rays=prim, k=32, out=out_p), steps, 2, flush, stream)
+    st_p32 = N.stats_dict(R.render(sc, cam, rays=prim, k=32, want_stats=True)["stats"])
     ts = time_frames(lambda: R.render(sc, None, rays=sec_rays, k=cfg["k"], out=out_s), steps, 2, flush, stream)
-    st_p = N.stats_dict(R.render(sc, None, rays=prim, k=cfg["k"], want_stats=True)["stats"])
+    st_p = N.stats_dict(R.render(sc, cam, rays=prim, k=cfg["k"], want_stats=True)["stats"])
     st_s = N.stats_dict(R.render(sc, None, rays=sec_rays, k=cfg["k"], want_stats=True)["stats"])
-    tc = time_frames(lambda: R.render(sc_c, None, rays=prim, k=cfg["k"], out=out_p), steps, 2, flush, stream)
-    st_c = N.stats_dict(R.render(sc_c, None, rays=prim, k=cfg["k"], want_stats=True)["stats"])
-    tl = time_frames(lambda: R.render(sc_l, None, rays=prim, k=cfg["k"], out=out_p), steps, 2, flush, stream)
-    st_l = N.stats_dict(R.render(sc_l, None, rays=prim, k=cfg["k"], want_stats=True)["stats"])
+    tc = time_frames(lambda: R.render(sc_c, cam, rays=prim, k=cfg["k"], out=out_p), steps, 2, flush, stream)
+    st_c = N.stats_dict(R.render(sc_c, cam, rays=prim, k=cfg["k"], want_stats=True)["stats"])
+    tl = time_frames(lambda: R.render(sc_l, cam, rays=prim, k=cfg["k"], out=out_p), steps, 2, flush, stream)
+    st_l = N.stats_dict(R.render(sc_l, cam, rays=prim, k=cfg["k"], want_stats=True)["stats"])
     depth = sc.info()["depth"]
     sc_c.close()
     sc_l.close()

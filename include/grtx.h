@@ -144,7 +144,9 @@ enum { GRTX_CAMERA_PINHOLE = 0, GRTX_CAMERA_FISHEYE = 1, GRTX_CAMERA_RAYS = 2 };
  *   reached at half the image width.
  * Rays: width*height rays (height may be 1) from device arrays ray_origins [n][3],
  *   ray_dirs [n][3] (any non-zero length; t is measured in units of |dir|), and optional
- *   ray_tnear / ray_tfar [n] (NULL: the scalar t_near / t_far below).
+ *   ray_tnear / ray_tfar [n] (NULL: the scalar t_near / t_far below). A list of at least
+ *   four rows is taken as an image and traced in 8x4 tiles, like a camera, so that a warp's
+ *   rays are neighbours; the output order is the same either way.
  * Every ray accepts hits with t_near < t <= t_far. Output pixel index = y * width + x. */
 typedef struct grtx_camera {
     int32_t type;

@@ -22,13 +22,7 @@ __global__ void k_mirror_rays(CamRef cam, grtx_mirror m, float *__restrict__ po,
     float3 o = make_float3(0.f, 0.f, 0.f), d = o, q = o, r = o;
     int64_t pix = -1;
     if (p < n) {
-        unsigned item;
-        if (cam.cam_type == GRTX_CAMERA_RAYS) {
-            item = (unsigned)p;
-        } else {
-            int x = (int)(p % cam.width), y = (int)(p / cam.width);
-            item = (unsigned)(((y / 4) * cam.tiles_x + (x / 8)) * 32 + (y % 4) * 8 + (x % 8));
-        }
+        unsigned item = item_of_pixel(cam, p);
         float tn, tf;
         if (make_ray(cam, item, pix, o, d, tn, tf)) {
             const float3 c = make_float3(m.center[0], m.center[1], m.center[2]);
@@ -109,13 +103,7 @@ __global__ void k_secondary_rays(CamRef cam, BounceObjects ob, float *__restrict
     float s_tn = 0.f;
     int64_t pix = -1;
     if (p < n) {
-        unsigned item;
-        if (cam.cam_type == GRTX_CAMERA_RAYS) {
-            item = (unsigned)p;
-        } else {
-            int x = (int)(p % cam.width), y = (int)(p / cam.width);
-            item = (unsigned)(((y / 4) * cam.tiles_x + (x / 8)) * 32 + (y % 4) * 8 + (x % 8));
-        }
+        unsigned item = item_of_pixel(cam, p);
         float3 o, d;
         float tn, tf;
         if (make_ray(cam, item, pix, o, d, tn, tf)) {

@@ -86,7 +86,13 @@ int grtx_fill_camera(CamRef &a, unsigned &n_items_out, const grtx_camera *cam)
         a.ray_d = cam->ray_dirs;
         a.ray_tn = cam->ray_tnear;
         a.ray_tf = cam->ray_tfar;
-        n_items = ((int64_t)cam->width * cam->height + 31) / 32 * 32;
+        if (cam->height >= 4) {                 // an image of rays: traced in 8x4 tiles
+            a.tiles_x = (cam->width + 7) / 8;
+            n_items = (int64_t)a.tiles_x * ((cam->height + 3) / 4) * 32;
+        } else {
+            a.tiles_x = 0;
+            n_items = ((int64_t)cam->width * cam->height + 31) / 32 * 32;
+        }
     } else if (cam->type == GRTX_CAMERA_PINHOLE || cam->type == GRTX_CAMERA_FISHEYE) {
         if (!(cam->fov > 0.f) || (cam->type == GRTX_CAMERA_PINHOLE && !(cam->fov < 3.14159f)))
             return grtx_fail(GRTX_ERR_INVALID_ARG, "bad field of view");
@@ -231,13 +237,7 @@ __global__ void k_gen_rays(CamRef a, float *o, float *d, float *tn, float *tf)
 {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= (int64_t)a.width * a.height) return;
-    unsigned item;
-    if (a.cam_type == GRTX_CAMERA_RAYS) {
-        item = (unsigned)p;
-    } else {
-        int x = (int)(p % a.width), y = (int)(p / a.width);
-        item = (unsigned)(((y / 4) * a.tiles_x + (x / 8)) * 32 + (y % 4) * 8 + (x % 8));
-    }
+    unsigned item = item_of_pixel(a, p);
     int64_t pix;
     float3 ro, rd;
     float a0, a1;

@@ -111,23 +111,37 @@ __device__ __forceinline__ void visits_end(const TraceArgs &a, Counters &c, int6
 // ------------------------------------------------------------------------------------------
 // Rays
 // ------------------------------------------------------------------------------------------
+// Queue items: a warp's 32 items are an 8x4 pixel tile (tiles_x > 0: cameras, and ray lists
+// laid out as an image of at least four rows, so that a warp's rays are neighbours), or 32
+// consecutive rays of a list (tiles_x = 0). Output index pix = y * width + x either way.
+__device__ __forceinline__ unsigned item_of_pixel(const CamRef &a, int64_t p)
+{
+    if (!a.tiles_x) return (unsigned)p;
+    int x = (int)(p % a.width), y = (int)(p / a.width);
+    return (unsigned)(((y / 4) * a.tiles_x + (x / 8)) * 32 + (y % 4) * 8 + (x % 8));
+}
+
 __device__ __forceinline__ bool make_ray(const CamRef &a, unsigned item, int64_t &pix, float3 &o, float3 &d,
                                          float &tn, float &tf)
 {
-    if (a.cam_type == GRTX_CAMERA_RAYS) {
+    int px = 0, py = 0;
+    if (a.tiles_x) {
+        unsigned tile = item >> 5, l = item & 31u;
+        px = (int)(tile % (unsigned)a.tiles_x) * 8 + (int)(l & 7u);
+        py = (int)(tile / (unsigned)a.tiles_x) * 4 + (int)(l >> 3);
+        if (px >= a.width || py >= a.height) return false;
+        pix = (int64_t)py * a.width + px;
+    } else {
         if ((int64_t)item >= (int64_t)a.width * a.height) return false;
         pix = item;
+    }
+    if (a.cam_type == GRTX_CAMERA_RAYS) {
         o = make_float3(a.ray_o[3 * pix], a.ray_o[3 * pix + 1], a.ray_o[3 * pix + 2]);
         d = make_float3(a.ray_d[3 * pix], a.ray_d[3 * pix + 1], a.ray_d[3 * pix + 2]);
         tn = a.ray_tn ? a.ray_tn[pix] : a.t_near;
         tf = a.ray_tf ? a.ray_tf[pix] : a.t_far;
         return true;
     }
-    unsigned tile = item >> 5, l = item & 31u;
-    int px = (int)(tile % (unsigned)a.tiles_x) * 8 + (int)(l & 7u);
-    int py = (int)(tile / (unsigned)a.tiles_x) * 4 + (int)(l >> 3);
-    if (px >= a.width || py >= a.height) return false;
-    pix = (int64_t)py * a.width + px;
     float dx, dy, dz;
     if (a.cam_type == GRTX_CAMERA_PINHOLE) {
         float u = (2.0f * (px + 0.5f) / a.width - 1.0f) * a.tan_half * a.aspect;

@@ -266,12 +266,18 @@ def make_params(k=16, traversal=0, alpha_min=0.01, T_min=1e-3, alpha_max=0.99, b
 
 def make_camera(cam: dict, rays=None) -> grtx_camera:
     """A grtx_camera from a scenes.* camera dict, or (rays given) an explicit ray list:
-    rays = (origins [n,3], dirs [n,3], t_near [n] or None, t_far [n] or None) CUDA tensors."""
+    rays = (origins [n,3], dirs [n,3], t_near [n] or None, t_far [n] or None) CUDA tensors.
+    With both, and the camera's width * height equal to n, the list is the camera's image of
+    rays (row-major) and is traced in pixel tiles."""
     c = grtx_camera()
     if rays is not None:
         o, d, tn, tf = rays
         c.type = 2
-        c.width, c.height = int(o.shape[0]), 1
+        n = int(o.shape[0])
+        if cam and "width" in cam and "height" in cam and int(cam["width"]) * int(cam["height"]) == n:
+            c.width, c.height = int(cam["width"]), int(cam["height"])
+        else:
+            c.width, c.height = n, 1
         c.t_near = float(cam.get("t_near", 0.0)) if cam else 0.0
         c.t_far = float(cam.get("t_far", float("inf"))) if cam else float("inf")
         c.ray_origins, c.ray_dirs = ptr(o), ptr(d)

@@ -708,3 +708,27 @@ def test_visit_log_samples_every_stride_th_ray(dense):
         N.grtx_trace_forward(sc.handle, N.make_camera(cam, None), R.trace_params(), rgbT,
                              visits=torch.empty((4, 4), dtype=torch.int32, device="cuda"), visits_n=None)
     sc.close()
+
+
+def test_image_shaped_ray_list_traces_in_tiles(dense):
+    """A ray list with the camera's width x height is traced in the camera's 8x4 pixel tiles:
+    the same image and blend lists as the camera (whose rays it holds) and as the same list
+    traced as one row, and the camera's exact node counts (the same rays share each warp)."""
+    g, cam, S, rays, ref = dense
+    sc = R.Scene.from_params(g)
+    n = cam["width"] * cam["height"]
+    o, d = torch.empty((n, 3), device="cuda"), torch.empty((n, 3), device="cuda")
+    tn, tf = torch.empty(n, device="cuda"), torch.empty(n, device="cuda")
+    N.grtx_generate_rays(N.make_camera(cam), o, d, tn, tf)
+    res = {}
+    for name, c, rr in (("camera", cam, None), ("tiled", cam, (o, d, tn, tf)), ("row", None, (o, d, tn, tf))):
+        r = R.render(sc, c, rays=rr, k=8, ids_cap=256, want_n_blended=True, want_stats=True)
+        torch.cuda.synchronize()
+        res[name] = ({key: v.cpu().numpy() for key, v in r.items() if key != "stats"}, N.stats_dict(r["stats"]))
+    for name in ("tiled", "row"):
+        for key in ("rgbT", "ids", "n_blended"):
+            np.testing.assert_array_equal(res[name][0][key], res["camera"][0][key])
+    for key in ("nodes", "leaves", "blended", "rounds", "ckpt_writes", "evictions"):
+        assert res["tiled"][1][key] == res["camera"][1][key]
+    assert res["row"][1]["nodes"] != res["camera"][1]["nodes"]          # other warps, other packets
+    sc.close()
