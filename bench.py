@@ -526,7 +526,8 @@ def bench_world(steps: int, stream, flush):
 def bench_outdoor(steps: int, stream, flush):
     """6M-Gaussian outdoor scene, 1920x1080 fisheye plus one bounce off a mirror or through a
     glass ball: primary and secondary rays timed separately (explicit ray lists; the primary
-    list is the camera's image of rays, traced in pixel tiles), k = 16."""
+    list is the camera's image of rays, traced in pixel tiles), and the whole frame as one
+    batched launch, k = 16."""
     import torch
     from paper_2601_20429_gb300 import native as N
     from paper_2601_20429_gb300 import render as R
@@ -556,6 +557,9 @@ def bench_outdoor(steps: int, stream, flush):
     tp32 = time_frames(lambda: R.render(sc, cam, rays=prim, k=32, out=out_p), steps, 2, flush, stream)
     st_p32 = N.stats_dict(R.render(sc, cam, rays=prim, k=32, want_stats=True)["stats"])
     ts = time_frames(lambda: R.render(sc, None, rays=sec_rays, k=cfg["k"], out=out_s), steps, 2, flush, stream)
+    # the whole frame (primary image and bounce list) as one batched launch
+    tf = time_frames(lambda: R.render_batch(sc, [(cam, prim), (None, sec_rays)], k=cfg["k"]), steps, 2, flush,
+                     stream)
     st_p = N.stats_dict(R.render(sc, cam, rays=prim, k=cfg["k"], want_stats=True)["stats"])
     st_s = N.stats_dict(R.render(sc, None, rays=sec_rays, k=cfg["k"], want_stats=True)["stats"])
     tc = time_frames(lambda: R.render(sc_c, cam, rays=prim, k=cfg["k"], out=out_p), steps, 2, flush, stream)
@@ -573,6 +577,9 @@ def bench_outdoor(steps: int, stream, flush):
                         "nodes_per_ray": nodes_per_ray(st_p)},
             "secondary": {"Mrays_per_s": m / (statistics.mean(ts) / 1e3) / 1e6, "ms": statistics.mean(ts),
                           "nodes_per_ray": nodes_per_ray(st_s)},
+            "frame_one_launch": {"Mrays_per_s": (n + m) / (statistics.mean(tf) / 1e3) / 1e6,
+                                 "ms": statistics.mean(tf),
+                                 "ms_as_two_launches": statistics.mean(tp) + statistics.mean(ts)},
             "depth": depth,
             "primary_k32": {"Mrays_per_s": n / (statistics.mean(tp32) / 1e3) / 1e6, "ms": statistics.mean(tp32),
                             "nodes_per_ray": nodes_per_ray(st_p32)},

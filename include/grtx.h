@@ -400,6 +400,20 @@ GRTX_API int grtx_generate_rays(const grtx_camera *cam, float *d_origins, float 
 GRTX_API int grtx_trace_forward(grtx_scene *scene, const grtx_camera *cam, const grtx_params *p,
                                 const grtx_trace_outputs *out, void *stream);
 
+#define GRTX_MAX_BATCH 64
+
+/* Trace several cameras or ray lists of one scene in one persistent launch (the segments of
+ * the serving kernel): cams[i] is traced into rgbT[i] (device [width*height][4], 16-byte
+ * aligned, as grtx_trace_forward's rgbT), with the same parameters for all. The warps of
+ * every item share the GPU, so a small list (a frame's bounce rays) overlaps a large image
+ * instead of running after it with most of the GPU idle. Results equal grtx_trace_forward's
+ * for each camera alone, to the last bit of rounding (the batch runs in the serving kernel).
+ * Sphere-form scenes, checkpoint or restart traversal, no optional outputs; n_cams in
+ * [1, GRTX_MAX_BATCH].
+ * Errors: GRTX_ERR_INVALID_ARG for bad arguments (checked before any device work). */
+GRTX_API int grtx_trace_forward_batch(grtx_scene *scene, const grtx_camera *cams, int n_cams,
+                                      const grtx_params *p, float *const *rgbT, void *stream);
+
 /* Gradients of a loss L w.r.t. the raw Gaussian parameters for the image of
  * grtx_trace_forward. g must hold the parameters the scene was built from; d_rgbT is the
  * forward output [n_rays][4] and d_dL_drgbT the upstream gradient [n_rays][4]. The kernel

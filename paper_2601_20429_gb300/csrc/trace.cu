@@ -18,6 +18,16 @@ GRTX_EXTERN_TRACE(8)
 GRTX_EXTERN_TRACE(16)
 GRTX_EXTERN_TRACE(32)
 
+#define GRTX_EXTERN_SEGMENTS(K)                                                                          \
+    extern template int serve_launch<K>(const TraceArgs &, const ServeSeg *, int, int, cudaStream_t);     \
+    extern template int serve_occupancy<K>(int *);
+GRTX_EXTERN_SEGMENTS(1)
+GRTX_EXTERN_SEGMENTS(2)
+GRTX_EXTERN_SEGMENTS(4)
+GRTX_EXTERN_SEGMENTS(8)
+GRTX_EXTERN_SEGMENTS(16)
+GRTX_EXTERN_SEGMENTS(32)
+
 int trace_single_launch(const TraceArgs &a, int form, bool instr, int blocks, cudaStream_t s);
 int trace_single_occupancy(int form, bool instr, int *blocks_per_sm);
 
@@ -292,6 +302,94 @@ extern "C" GRTX_API int grtx_trace_forward(grtx_scene *sc, const grtx_camera *ca
     if (out->blended_ids)
         GRTX_CUDA(cudaMemsetAsync(out->blended_ids, 0xff, (size_t)cam->width * cam->height * out->ids_cap * 4, s));
     return run(sc, a, p->k, instr, false, sc->d_counter, s);
+}
+
+namespace {
+
+int segments_launch_k(int k, const TraceArgs &a, const ServeSeg *segs, int n, int blocks, cudaStream_t s)
+{
+    switch (k) {
+    case 1: return serve_launch<1>(a, segs, n, blocks, s);
+    case 2: return serve_launch<2>(a, segs, n, blocks, s);
+    case 4: return serve_launch<4>(a, segs, n, blocks, s);
+    case 8: return serve_launch<8>(a, segs, n, blocks, s);
+    case 16: return serve_launch<16>(a, segs, n, blocks, s);
+    default: return serve_launch<32>(a, segs, n, blocks, s);
+    }
+}
+
+int segments_occupancy_k(int k, int *bps)
+{
+    switch (k) {
+    case 1: return serve_occupancy<1>(bps);
+    case 2: return serve_occupancy<2>(bps);
+    case 4: return serve_occupancy<4>(bps);
+    case 8: return serve_occupancy<8>(bps);
+    case 16: return serve_occupancy<16>(bps);
+    default: return serve_occupancy<32>(bps);
+    }
+}
+
+}  // namespace
+
+extern "C" GRTX_API int grtx_trace_forward_batch(grtx_scene *sc, const grtx_camera *cams, int n_cams,
+                                                 const grtx_params *p, float *const *rgbT, void *stream)
+{
+    if (!cams || !rgbT) return grtx_fail(GRTX_ERR_INVALID_ARG, "NULL pointer");
+    if (n_cams < 1 || n_cams > GRTX_MAX_BATCH) return grtx_fail(GRTX_ERR_INVALID_ARG, "n_cams must be in [1, 64]");
+    TraceArgs a = {};
+    int st = setup(sc, &cams[0], p, a);
+    if (st) return st;
+    if (sc->form != GRTX_FORM_SPHERE) return grtx_fail(GRTX_ERR_INVALID_ARG, "batched traces need the sphere form");
+    if (a.traversal == GRTX_TRAVERSAL_SINGLE)
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "batched traces take checkpoint or restart traversal");
+    ServeSeg h[GRTX_MAX_BATCH];
+    unsigned total = 0;
+    for (int i = 0; i < n_cams; ++i) {
+        if (!rgbT[i] || ((uintptr_t)rgbT[i] & 15))
+            return grtx_fail(GRTX_ERR_INVALID_ARG, "every rgbT output must be non-NULL and 16-byte aligned");
+        unsigned items = 0;
+        st = grtx_fill_camera(h[i].cam, items, &cams[i]);
+        if (st) return st;
+        if ((uint64_t)total + items >= (1ull << 31)) return grtx_fail(GRTX_ERR_INVALID_ARG, "too many rays");
+        h[i].sc = grtx_scene_ref(sc);
+        h[i].out = (float4 *)rgbT[i];
+        h[i].item_begin = 0;
+        h[i].step_begin = total;
+        h[i].count = items;
+        h[i].pad = 0;
+        total += items;
+    }
+    int bps = 0;
+    if (segments_occupancy_k(p->k, &bps) != GRTX_OK || bps <= 0) return grtx_fail(GRTX_ERR_CUDA, "occupancy query failed");
+    int blocks = sm_count() * bps;
+    int n_slots = blocks * 128;
+    bool ckpt = a.traversal == GRTX_TRAVERSAL_CHECKPOINT;
+    size_t C = ckpt ? a.ckpt_cap : 1, E = ckpt ? a.evict_cap : 1;
+    uint2 *base = nullptr;
+    cudaStream_t s = S(stream);
+    st = ensure_workspace(sc, n_slots, 2 * C + E, s, &base);
+    if (st) return st;
+    a.ck0 = base;
+    a.ck1 = base + (size_t)n_slots * C;
+    a.ev = base + (size_t)n_slots * 2 * C;
+    a.n_slots = n_slots;
+    a.queue = sc->d_counter + 2;
+    a.n_items = total;
+    ServeSeg *d = nullptr;
+    if (cudaMallocAsync((void **)&d, sizeof(ServeSeg) * n_cams, s) != cudaSuccess) {
+        cudaGetLastError();
+        return grtx_fail(GRTX_ERR_OOM, "segment table allocation failed");
+    }
+    GRTX_CUDA(cudaMemcpyAsync(d, h, sizeof(ServeSeg) * n_cams, cudaMemcpyHostToDevice, s));
+    GRTX_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned), s));
+    int launched = segments_launch_k(p->k, a, d, n_cams, blocks, s);
+    cudaFreeAsync(d, s);
+    if (launched != GRTX_OK) {
+        cudaError_t e = cudaGetLastError();
+        return grtx_cuda_fail(e == cudaSuccess ? cudaErrorLaunchFailure : e, "batched trace launch");
+    }
+    return GRTX_OK;
 }
 
 extern "C" GRTX_API int grtx_trace_backward(grtx_scene *sc, const grtx_gaussians *g, const grtx_camera *cam,

@@ -173,6 +173,8 @@ _SIGS = {
     "grtx_generate_rays": (C.c_int, [C.POINTER(grtx_camera), _fp, _fp, _fp, _fp, _fp]),
     "grtx_trace_forward": (C.c_int, [_fp, C.POINTER(grtx_camera), C.POINTER(grtx_params),
                                      C.POINTER(grtx_trace_outputs), _fp]),
+    "grtx_trace_forward_batch": (C.c_int, [_fp, C.POINTER(grtx_camera), C.c_int, C.POINTER(grtx_params),
+                                           C.POINTER(_fp), _fp]),
     "grtx_trace_backward": (C.c_int, [_fp, C.POINTER(grtx_gaussians), C.POINTER(grtx_camera), C.POINTER(grtx_params),
                                       _fp, _fp, C.POINTER(grtx_grads), _fp]),
     "grtx_mirror_rays": (C.c_int, [C.POINTER(grtx_camera), C.POINTER(grtx_mirror)] + [_fp] * 11),
@@ -405,6 +407,15 @@ def grtx_trace_forward(scene: int, cam: grtx_camera, p: grtx_params, rgbT, n_ble
         out.visits_stride = int(visits_stride)
     check(lib().grtx_trace_forward(C.c_void_p(scene), C.byref(cam), C.byref(p), C.byref(out), stream_handle(stream)),
           "grtx_trace_forward")
+
+
+def grtx_trace_forward_batch(scene: int, cams, p: grtx_params, outs, stream=None):
+    """cams: list of grtx_camera; outs: matching list of rgbT tensors."""
+    n = len(cams)
+    arr = (grtx_camera * max(n, 1))(*cams)
+    ptrs = (_fp * max(n, 1))(*[ptr(o) for o in outs])
+    check(lib().grtx_trace_forward_batch(C.c_void_p(scene), arr, n, C.byref(p), ptrs, stream_handle(stream)),
+          "grtx_trace_forward_batch")
 
 
 def make_instances(placements) -> C.Array:

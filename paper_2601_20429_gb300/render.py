@@ -179,6 +179,19 @@ def render(scene: Scene, cam: dict | None, rays=None, out=None, ids_cap: int = 0
     return res
 
 
+def render_batch(scene: Scene, views, stream=None, **params) -> list:
+    """Several views of one scene in one launch: views = [(cam, rays)] with cam a camera dict
+    or None and rays an explicit ray list or None (as in render). Returns the rgbT of each."""
+    p = trace_params(alpha_min=scene.alpha_min, **params)
+    dev = scene.tensors[0].device
+    cams, outs = [], []
+    for cam, rays in views:
+        cams.append(N.make_camera(cam, rays))
+        outs.append(torch.empty((n_rays_of(cam, rays), 4), dtype=torch.float32, device=dev))
+    N.grtx_trace_forward_batch(scene.handle, cams, p, outs, stream)
+    return outs
+
+
 def visit_counts(visits, visits_n) -> dict:
     """Per logged ray: node and leaf fetches, total and distinct, from a visit log
     (numpy or torch; rows whose count exceeds the log's width are left out)."""

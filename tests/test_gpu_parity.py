@@ -732,3 +732,36 @@ def test_image_shaped_ray_list_traces_in_tiles(dense):
         assert res["tiled"][1][key] == res["camera"][1][key]
     assert res["row"][1]["nodes"] != res["camera"][1]["nodes"]          # other warps, other packets
     sc.close()
+
+
+def test_batched_views_equal_separate_traces(dense):
+    """Several views in one launch (grtx_trace_forward_batch): a camera, the same camera's
+    rays as an image-shaped list, a ragged list of 777 of its rays in scrambled order and a
+    second camera give, each, what grtx_trace_forward gives for it alone (to the last bit:
+    the batch runs in the serving kernel, where the compiler may contract the colour
+    arithmetic differently)."""
+    g, cam, S, rays, ref = dense
+    sc = R.Scene.from_params(g)
+    n = cam["width"] * cam["height"]
+    o, d = torch.empty((n, 3), device="cuda"), torch.empty((n, 3), device="cuda")
+    tn, tf = torch.empty(n, device="cuda"), torch.empty(n, device="cuda")
+    N.grtx_generate_rays(N.make_camera(cam), o, d, tn, tf)
+    pick = torch.from_numpy(np.random.default_rng(3).permutation(n)[:777]).cuda()
+    sub = (o[pick].contiguous(), d[pick].contiguous(), tn[pick].contiguous(), tf[pick].contiguous())
+    cam2 = scenes.fisheye_camera(37, 23, (0.0, 0.0, -3.0), (0.0, 0.0, 1.0), 40.0)
+    views = [(cam, None), (cam, (o, d, tn, tf)), (None, sub), (cam2, None)]
+    for trav in ("checkpoint", "restart"):
+        outs = R.render_batch(sc, views, k=8, traversal=trav)
+        torch.cuda.synchronize()
+        for (c, rr), got in zip(views, outs):
+            alone = R.render(sc, c, rays=rr, k=8, traversal=trav)["rgbT"]
+            np.testing.assert_allclose(got.cpu().numpy(), alone.cpu().numpy(), rtol=0, atol=1e-6)
+    proxy = R.Scene.from_params(g.subset(np.arange(500)), form="proxy20")
+    with pytest.raises(N.GrtxError, match="sphere form"):
+        R.render_batch(proxy, views[:1], k=8)
+    with pytest.raises(N.GrtxError, match="checkpoint or restart"):
+        R.render_batch(sc, views[:1], k=8, traversal="single")
+    with pytest.raises(N.GrtxError, match="n_cams"):
+        R.render_batch(sc, [(cam, None)] * 65, k=8)
+    proxy.close()
+    sc.close()
