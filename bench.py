@@ -434,7 +434,7 @@ def bench_differentiable(steps: int, warmup: int, stream):
 
     rays = cam["width"] * cam["height"]
     res = {}
-    for name, opts in (("refit", {"scene": kept}), ("rebuild", {})):
+    for name, opts in (("refit", {"scene": kept}), ("rebuild", {}), ("refit_saved_lists", {"scene": kept, "save_cap": 64})):
         for _ in range(warmup):
             step(opts)
         torch.cuda.synchronize()
@@ -452,7 +452,10 @@ def bench_differentiable(steps: int, warmup: int, stream):
             "ms_per_step": res["refit"]["ms_per_step"], "Mrays_per_s": res["refit"]["Mrays_per_s"],
             "loss": res["refit"]["loss"],
             "step": "BVH refit in place + forward + backward (atomics into all five parameter tensors)",
-            "rebuild": dict(res["rebuild"], step="BVH built anew (radix tree) + forward + backward")}
+            "rebuild": dict(res["rebuild"], step="BVH built anew (radix tree) + forward + backward"),
+            "refit_saved_lists": dict(res["refit_saved_lists"],
+                                      step="BVH refit + forward saving blend lists (64 per ray) + backward "
+                                           "from the lists (rounds replayed for overflowed rays)")}
 
 
 def _quat_mul(a, b):

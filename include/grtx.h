@@ -172,6 +172,18 @@ typedef struct grtx_stats {
         stack_overflow, collected;
 } grtx_stats;
 
+/* Blend lists a forward trace saves for its backward (grtx_trace_backward_saved): for each
+ * ray, the leaf slots it blended, in blend order. leaves: device [n_rays][cap]; n: device
+ * [n_rays], the number blended; a count above cap means the list is incomplete, and the
+ * backward replays that ray's rounds. Leaf slots index the scene's leaf order: the lists
+ * hold while the scene is not updated. Caller-owned device memory. */
+typedef struct grtx_saved {
+    uint32_t *leaves;
+    int32_t *n;
+    int32_t cap;
+    int32_t reserved;
+} grtx_saved;
+
 /* Outputs of a forward trace. rgbT: device [n_rays][4] = (C + T bg, T), required.
  * n_blended: optional device [n_rays], Gaussians composited per ray. blended_ids: optional
  * device [n_rays][ids_cap], the first ids_cap composited Gaussian ids per ray in blend order
@@ -185,7 +197,10 @@ typedef struct grtx_stats {
  * logged), and visits_n[r] their number, which may exceed visits_cap (the row then holds the
  * first visits_cap). Rows of rays that are not traced keep their contents; visits_n is
  * zeroed by the call. Both pointers or neither; cap, stride and rows >= 1 when given.
- * With any optional output requested the kernel takes a slower instrumented path. */
+ * saved: optional blend lists for the backward (sphere form, checkpoint or restart
+ * traversal, with no other optional output: the saving forward is its own uninstrumented
+ * kernel). With any other optional output requested the kernel takes a slower instrumented
+ * path. */
 typedef struct grtx_trace_outputs {
     float *rgbT;
     int32_t *n_blended;
@@ -196,6 +211,7 @@ typedef struct grtx_trace_outputs {
     uint32_t *visits;
     uint32_t *visits_n;
     int32_t visits_cap, visits_stride, visits_rows, reserved2;
+    const grtx_saved *saved;
 } grtx_trace_outputs;
 
 /* Host-readable description of a built scene. */
@@ -425,6 +441,17 @@ GRTX_API int grtx_trace_backward(grtx_scene *scene, const grtx_gaussians *g,
                                  const grtx_camera *cam, const grtx_params *p,
                                  const float *d_rgbT, const float *d_dL_drgbT,
                                  const grtx_grads *grads, void *stream);
+
+/* grtx_trace_backward for a forward that saved its blend lists (grtx_trace_outputs.saved,
+ * same scene, camera and parameters): a ray with a complete list (n <= cap) computes its
+ * gradients from the list, in blend order, without traversing the BVH; the others replay
+ * their rounds as in grtx_trace_backward. The gradients are the same (up to the order of the
+ * atomic additions). Sphere form. */
+GRTX_API int grtx_trace_backward_saved(grtx_scene *scene, const grtx_gaussians *g,
+                                       const grtx_camera *cam, const grtx_params *p,
+                                       const float *d_rgbT, const float *d_dL_drgbT,
+                                       const grtx_saved *saved, const grtx_grads *grads,
+                                       void *stream);
 
 /* A rectangular planar mirror for secondary rays (Sec. VI "GRTX-HW on Secondary Rays").
  * center: a point of the mirror; normal: unit normal; axis_u / axis_v: unit in-plane axes;

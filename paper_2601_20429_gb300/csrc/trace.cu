@@ -9,8 +9,8 @@
 #include "trace_impl.cuh"
 
 #define GRTX_EXTERN_TRACE(K)                                                                     \
-    extern template int trace_launch<K>(const TraceArgs &, int, bool, bool, int, cudaStream_t); \
-    extern template int trace_occupancy<K>(int, bool, bool, int *);
+    extern template int trace_launch<K>(const TraceArgs &, int, bool, int, int, cudaStream_t); \
+    extern template int trace_occupancy<K>(int, bool, int, int *);
 GRTX_EXTERN_TRACE(1)
 GRTX_EXTERN_TRACE(2)
 GRTX_EXTERN_TRACE(4)
@@ -37,27 +37,27 @@ inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
 bool valid_k(int k) { return k == 1 || k == 2 || k == 4 || k == 8 || k == 16 || k == 32; }
 
-int launch_k(int k, const TraceArgs &a, int form, bool instr, bool bwd, int blocks, cudaStream_t s)
+int launch_k(int k, const TraceArgs &a, int form, bool instr, int pass, int blocks, cudaStream_t s)
 {
     switch (k) {
-    case 1: return trace_launch<1>(a, form, instr, bwd, blocks, s);
-    case 2: return trace_launch<2>(a, form, instr, bwd, blocks, s);
-    case 4: return trace_launch<4>(a, form, instr, bwd, blocks, s);
-    case 8: return trace_launch<8>(a, form, instr, bwd, blocks, s);
-    case 16: return trace_launch<16>(a, form, instr, bwd, blocks, s);
-    default: return trace_launch<32>(a, form, instr, bwd, blocks, s);
+    case 1: return trace_launch<1>(a, form, instr, pass, blocks, s);
+    case 2: return trace_launch<2>(a, form, instr, pass, blocks, s);
+    case 4: return trace_launch<4>(a, form, instr, pass, blocks, s);
+    case 8: return trace_launch<8>(a, form, instr, pass, blocks, s);
+    case 16: return trace_launch<16>(a, form, instr, pass, blocks, s);
+    default: return trace_launch<32>(a, form, instr, pass, blocks, s);
     }
 }
 
-int occupancy_k(int k, int form, bool instr, bool bwd, int *bps)
+int occupancy_k(int k, int form, bool instr, int pass, int *bps)
 {
     switch (k) {
-    case 1: return trace_occupancy<1>(form, instr, bwd, bps);
-    case 2: return trace_occupancy<2>(form, instr, bwd, bps);
-    case 4: return trace_occupancy<4>(form, instr, bwd, bps);
-    case 8: return trace_occupancy<8>(form, instr, bwd, bps);
-    case 16: return trace_occupancy<16>(form, instr, bwd, bps);
-    default: return trace_occupancy<32>(form, instr, bwd, bps);
+    case 1: return trace_occupancy<1>(form, instr, pass, bps);
+    case 2: return trace_occupancy<2>(form, instr, pass, bps);
+    case 4: return trace_occupancy<4>(form, instr, pass, bps);
+    case 8: return trace_occupancy<8>(form, instr, pass, bps);
+    case 16: return trace_occupancy<16>(form, instr, pass, bps);
+    default: return trace_occupancy<32>(form, instr, pass, bps);
     }
 }
 
@@ -212,12 +212,12 @@ int setup(grtx_scene *sc, const grtx_camera *cam, const grtx_params *p, TraceArg
     return GRTX_OK;
 }
 
-int run(grtx_scene *sc, TraceArgs &a, int k, bool instr, bool bwd, unsigned *queue, cudaStream_t s)
+int run(grtx_scene *sc, TraceArgs &a, int k, bool instr, int pass, unsigned *queue, cudaStream_t s)
 {
     int form = kernel_form(sc->form);
-    bool single = a.traversal == GRTX_TRAVERSAL_SINGLE && !bwd;
+    bool single = a.traversal == GRTX_TRAVERSAL_SINGLE && pass == PASS_FWD;
     int bps = 0;
-    int occ = single ? trace_single_occupancy(form, instr, &bps) : occupancy_k(k, form, instr, bwd, &bps);
+    int occ = single ? trace_single_occupancy(form, instr, &bps) : occupancy_k(k, form, instr, pass, &bps);
     if (occ != GRTX_OK || bps <= 0) return grtx_fail(GRTX_ERR_CUDA, "occupancy query failed");
     int blocks = sm_count() * bps;
     int n_slots = blocks * 128;
@@ -235,7 +235,7 @@ int run(grtx_scene *sc, TraceArgs &a, int k, bool instr, bool bwd, unsigned *que
     a.queue = queue;
     GRTX_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned), s));
     int launched = single ? trace_single_launch(a, form, instr, blocks, s)
-                          : launch_k(k, a, form, instr, bwd, blocks, s);
+                          : launch_k(k, a, form, instr, pass, blocks, s);
     if (launched != GRTX_OK) {
         cudaError_t e = cudaGetLastError();
         return grtx_cuda_fail(e == cudaSuccess ? cudaErrorLaunchFailure : e, "trace launch");
@@ -298,10 +298,24 @@ extern "C" GRTX_API int grtx_trace_forward(grtx_scene *sc, const grtx_camera *ca
     a.visits_rows = out->visits_rows;
     cudaStream_t s = S(stream);
     bool instr = out->n_blended || out->blended_ids || out->stats || out->visits;
+    int pass = PASS_FWD;
+    if (out->saved) {
+        const grtx_saved *sv = out->saved;
+        if (!sv->leaves || !sv->n || sv->cap <= 0)
+            return grtx_fail(GRTX_ERR_INVALID_ARG, "saved lists need leaves, n and a positive cap");
+        if (sc->form != GRTX_FORM_SPHERE) return grtx_fail(GRTX_ERR_INVALID_ARG, "saved lists need the sphere form");
+        if (instr || a.traversal == GRTX_TRAVERSAL_SINGLE)
+            return grtx_fail(GRTX_ERR_INVALID_ARG,
+                             "saved lists take checkpoint or restart traversal and no other optional output");
+        a.save_leaves = sv->leaves;
+        a.save_n = sv->n;
+        a.save_cap = sv->cap;
+        pass = PASS_SAVE;
+    }
     if (out->visits) GRTX_CUDA(cudaMemsetAsync(out->visits_n, 0, (size_t)out->visits_rows * 4, s));
     if (out->blended_ids)
         GRTX_CUDA(cudaMemsetAsync(out->blended_ids, 0xff, (size_t)cam->width * cam->height * out->ids_cap * 4, s));
-    return run(sc, a, p->k, instr, false, sc->d_counter, s);
+    return run(sc, a, p->k, instr, pass, sc->d_counter, s);
 }
 
 namespace {
@@ -392,9 +406,11 @@ extern "C" GRTX_API int grtx_trace_forward_batch(grtx_scene *sc, const grtx_came
     return GRTX_OK;
 }
 
-extern "C" GRTX_API int grtx_trace_backward(grtx_scene *sc, const grtx_gaussians *g, const grtx_camera *cam,
-                                            const grtx_params *p, const float *d_rgbT, const float *d_dL_drgbT,
-                                            const grtx_grads *grads, void *stream)
+namespace {
+
+int backward(grtx_scene *sc, const grtx_gaussians *g, const grtx_camera *cam, const grtx_params *p,
+             const float *d_rgbT, const float *d_dL_drgbT, const grtx_saved *saved, const grtx_grads *grads,
+             cudaStream_t s)
 {
     TraceArgs a = {};
     int st = setup(sc, cam, p, a);
@@ -426,5 +442,31 @@ extern "C" GRTX_API int grtx_trace_backward(grtx_scene *sc, const grtx_gaussians
     a.n_sh = sc->n_coef * 3;
     a.vec_sh = a.n_sh == 48 && ((uintptr_t)grads->sh & 15) == 0;
     a.vec_q = ((uintptr_t)grads->quats & 15) == 0;
-    return run(sc, a, p->k, false, true, sc->d_counter + 1, S(stream));
+    if (saved) {
+        if (!saved->leaves || !saved->n || saved->cap <= 0)
+            return grtx_fail(GRTX_ERR_INVALID_ARG, "saved lists need leaves, n and a positive cap");
+        if (sc->form != GRTX_FORM_SPHERE) return grtx_fail(GRTX_ERR_INVALID_ARG, "saved lists need the sphere form");
+        a.save_leaves = saved->leaves;
+        a.save_n = saved->n;
+        a.save_cap = saved->cap;
+    }
+    return run(sc, a, p->k, false, PASS_BWD, sc->d_counter + 1, s);
+}
+
+}  // namespace
+
+extern "C" GRTX_API int grtx_trace_backward(grtx_scene *sc, const grtx_gaussians *g, const grtx_camera *cam,
+                                            const grtx_params *p, const float *d_rgbT, const float *d_dL_drgbT,
+                                            const grtx_grads *grads, void *stream)
+{
+    return backward(sc, g, cam, p, d_rgbT, d_dL_drgbT, nullptr, grads, S(stream));
+}
+
+extern "C" GRTX_API int grtx_trace_backward_saved(grtx_scene *sc, const grtx_gaussians *g, const grtx_camera *cam,
+                                                  const grtx_params *p, const float *d_rgbT,
+                                                  const float *d_dL_drgbT, const grtx_saved *saved,
+                                                  const grtx_grads *grads, void *stream)
+{
+    if (!saved) return grtx_fail(GRTX_ERR_INVALID_ARG, "saved is NULL");
+    return backward(sc, g, cam, p, d_rgbT, d_dL_drgbT, saved, grads, S(stream));
 }

@@ -56,6 +56,9 @@ struct TraceArgs {
     int ids_cap;
     uint32_t *visits, *visits_n;   // visit log of sampled rays (see grtx_trace_outputs)
     int visits_cap, visits_stride, visits_rows;
+    uint32_t *save_leaves;         // blend lists saved by a forward for its backward (grtx_saved)
+    int32_t *save_n;
+    int save_cap;
     grtx_stats *stats;
     // backward
     const float4 *fwd_rgbT, *dL_drgbT;
@@ -901,14 +904,24 @@ __device__ __forceinline__ void blend_one(const TraceArgs &a, const SceneRef &sc
 }
 
 // ------------------------------------------------------------------------------------------
-// One ray: the round loop of Listing 1's raygen shader.
+// One ray: the round loop of Listing 1's raygen shader. PASS: the forward, the backward (same
+// rounds, gradients while blending), or the forward that also saves each ray's blend list.
 // ------------------------------------------------------------------------------------------
-template <int K, int FORM, bool INSTR, bool BWD>
+enum { PASS_FWD = 0, PASS_BWD = 1, PASS_SAVE = 2 };
+
+// Blend-list entry j of a ray whose forward saved its list, and the end of its list.
+__device__ __forceinline__ void save_blended(const TraceArgs &a, int64_t pix, int j, uint32_t idx)
+{
+    if (j < a.save_cap) a.save_leaves[(size_t)pix * a.save_cap + j] = idx;
+}
+
+template <int K, int FORM, bool INSTR, int PASS>
 __device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc, float4 *__restrict__ out, int slot,
                                           int64_t pix, float3 o, float3 d, float tn, float tf, KBuf<K> &kb,
                                           Counters &cnt, bool r1_done = false, bool r1_ok = true, int r1_n_dst = 0,
                                           int r1_n_ev = 0)
 {
+    constexpr bool BWD = PASS == PASS_BWD;
     const size_t S = (size_t)a.n_slots;
     float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
     float nrm = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
@@ -981,6 +994,7 @@ __device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc
                 if (a.ids && nb < a.ids_cap) a.ids[(size_t)pix * a.ids_cap + nb] = sc.gid[idx];
                 cnt.blended++;
             }
+            if (PASS == PASS_SAVE) save_blended(a, pix, nb, idx);
             ++nb;
             if (st.T < a.T_min) { done = true; break; }
         }
@@ -996,6 +1010,28 @@ __device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc
     }
     if (!BWD) out[pix] = make_float4(st.C[0] + st.T * a.bg0, st.C[1] + st.T * a.bg1, st.C[2] + st.T * a.bg2, st.T);
     if (INSTR && a.n_blended) a.n_blended[pix] = nb;
+    if (PASS == PASS_SAVE) a.save_n[pix] = nb;
+}
+
+// The backward of a ray from the blend list its forward saved (n <= save_cap entries): the
+// same blends, gradients and order as replaying the rounds, without the traversal.
+__device__ __forceinline__ void backward_from_list(const TraceArgs &a, const SceneRef &sc, int64_t pix, float3 o,
+                                                   float3 d, int n)
+{
+    float nrm = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
+    float3 dn = make_float3(d.x * nrm, d.y * nrm, d.z * nrm);
+    BlendState st;
+    st.C[0] = st.C[1] = st.C[2] = 0.f;
+    st.T = 1.f;
+    float4 F = a.fwd_rgbT[pix], G = a.dL_drgbT[pix];
+    st.G[0] = G.x; st.G[1] = G.y; st.G[2] = G.z; st.G[3] = G.w;
+    st.Tf = F.w;
+    st.Cf[0] = F.x - F.w * a.bg0;
+    st.Cf[1] = F.y - F.w * a.bg1;
+    st.Cf[2] = F.z - F.w * a.bg2;
+    st.dLdT = G.w + a.bg0 * G.x + a.bg1 * G.y + a.bg2 * G.z;
+    const uint32_t *list = a.save_leaves + (size_t)pix * a.save_cap;
+    for (int j = 0; j < n; ++j) blend_one<true>(a, sc, st, list[j], o, d, dn);
 }
 
 // The rays of one warp with restart traversal (Sec. III-A): every round from the root as the
@@ -1004,7 +1040,7 @@ __device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc
 // which is what makes this the faster restart on the SMs. A lane whose packet could not finish
 // (the warp's stack would overflow) traces that round on its own. Every lane calls this
 // together; lanes without a ray pass valid = false.
-template <int K, int FORM, bool INSTR>
+template <int K, int FORM, bool INSTR, bool SAVE>
 __device__ __forceinline__ void trace_warp_restart(const TraceArgs &a, const SceneRef &sc, float4 *__restrict__ out,
                                                    int slot, bool valid, int64_t pix, float3 o, float3 d, float tn,
                                                    float tf, KBuf<K> &kb, Counters &cnt, uint4 *pst)
@@ -1046,6 +1082,7 @@ __device__ __forceinline__ void trace_warp_restart(const TraceArgs &a, const Sce
                 if (a.ids && nb < a.ids_cap) a.ids[(size_t)pix * a.ids_cap + nb] = sc.gid[idx];
                 cnt.blended++;
             }
+            if (SAVE) save_blended(a, pix, nb, idx);
             ++nb;
             if (st.T < a.T_min) {
                 done = true;
@@ -1061,16 +1098,26 @@ __device__ __forceinline__ void trace_warp_restart(const TraceArgs &a, const Sce
     if (valid) {
         out[pix] = make_float4(st.C[0] + st.T * a.bg0, st.C[1] + st.T * a.bg1, st.C[2] + st.T * a.bg2, st.T);
         if (INSTR && a.n_blended) a.n_blended[pix] = nb;
+        if (SAVE) a.save_n[pix] = nb;
     }
 }
 
 // The rays of one warp: round 1 as the warp's packet, then each ray's later rounds on its
-// own. Every lane of the warp calls this together; lanes without a ray pass valid = false.
-template <int K, int FORM, bool INSTR, bool BWD>
+// own. Every lane of the warp calls this together; lanes without a ray pass valid = false. In
+// the backward, a ray whose forward saved its whole blend list takes it from there and leaves
+// the traversal to the others.
+template <int K, int FORM, bool INSTR, int PASS>
 __device__ __forceinline__ void trace_warp(const TraceArgs &a, const SceneRef &sc, float4 *__restrict__ out, int slot,
                                            bool valid, int64_t pix, float3 o, float3 d, float tn, float tf, KBuf<K> &kb,
                                            Counters &cnt, uint4 *pst)
 {
+    if (PASS == PASS_BWD && valid && a.save_n) {
+        int n = a.save_n[pix];
+        if (n <= a.save_cap) {
+            backward_from_list(a, sc, pix, o, d, n);
+            valid = false;
+        }
+    }
     if (!valid) {
         o = make_float3(0.f, 0.f, 0.f);
         d = make_float3(0.f, 0.f, 1.f);
@@ -1086,7 +1133,7 @@ __device__ __forceinline__ void trace_warp(const TraceArgs &a, const SceneRef &s
                                  cnt, lane_ok);
     // a lane whose packet could not finish (lists or the warp's stack overflowed) redoes round 1
     // from the root on its own, as after any capacity overflow
-    if (valid) trace_ray<K, FORM, INSTR, BWD>(a, sc, out, slot, pix, o, d, tn, tf, kb, cnt, true, lane_ok, n_dst, n_ev);
+    if (valid) trace_ray<K, FORM, INSTR, PASS>(a, sc, out, slot, pix, o, d, tn, tf, kb, cnt, true, lane_ok, n_dst, n_ev);
 }
 
 // Resident blocks per SM the trace kernels are compiled for. The traversal is latency-bound,
@@ -1095,8 +1142,8 @@ __device__ __forceinline__ void trace_warp(const TraceArgs &a, const SceneRef &s
 // memory per block allows 6; the backward keeps more live state and prefers 7).
 __host__ __device__ constexpr int trace_min_blocks(int k, bool bwd) { return k >= 32 ? 6 : (bwd ? 7 : 8); }
 
-template <int K, int FORM, bool INSTR, bool BWD>
-__global__ void __launch_bounds__(kBlock, trace_min_blocks(K, BWD)) k_trace(TraceArgs a)
+template <int K, int FORM, bool INSTR, int PASS>
+__global__ void __launch_bounds__(kBlock, trace_min_blocks(K, PASS == PASS_BWD)) k_trace(TraceArgs a)
 {
     __shared__ float s_kt[K * kBlock];
     __shared__ uint32_t s_ki[K * kBlock];
@@ -1119,12 +1166,12 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, BWD)) k_trace(Trac
         bool valid = make_ray(a.cam, base + lane, pix, o, d, tn, tf);
         rays += valid;
         if (INSTR) visits_begin(a, cnt, valid, pix);
-        if (!BWD && a.traversal == GRTX_TRAVERSAL_RESTART)
-            trace_warp_restart<K, FORM, INSTR>(a, a.sc, a.rgbT, slot, valid, pix, o, d, tn, tf, kb, cnt,
-                                               s_pst[threadIdx.x >> 5]);
+        if (PASS != PASS_BWD && a.traversal == GRTX_TRAVERSAL_RESTART)
+            trace_warp_restart<K, FORM, INSTR, PASS == PASS_SAVE>(a, a.sc, a.rgbT, slot, valid, pix, o, d, tn, tf,
+                                                                  kb, cnt, s_pst[threadIdx.x >> 5]);
         else
-            trace_warp<K, FORM, INSTR, BWD>(a, a.sc, a.rgbT, slot, valid, pix, o, d, tn, tf, kb, cnt,
-                                            s_pst[threadIdx.x >> 5]);
+            trace_warp<K, FORM, INSTR, PASS>(a, a.sc, a.rgbT, slot, valid, pix, o, d, tn, tf, kb, cnt,
+                                             s_pst[threadIdx.x >> 5]);
         if (INSTR) visits_end(a, cnt, pix);
         __syncwarp();
     }
@@ -1173,10 +1220,10 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, false)) k_serve(Tr
         float tn, tf;
         bool valid = make_ray(cam, item, pix, o, d, tn, tf);
         if (a.traversal == GRTX_TRAVERSAL_RESTART)
-            trace_warp_restart<K, FORM_SPHERE, false>(a, sc, sg.out, slot, valid, pix, o, d, tn, tf, kb, cnt,
+            trace_warp_restart<K, FORM_SPHERE, false, false>(a, sc, sg.out, slot, valid, pix, o, d, tn, tf, kb, cnt,
                                                       s_pst[threadIdx.x >> 5]);
         else
-            trace_warp<K, FORM_SPHERE, false, false>(a, sc, sg.out, slot, valid, pix, o, d, tn, tf, kb, cnt,
+            trace_warp<K, FORM_SPHERE, false, PASS_FWD>(a, sc, sg.out, slot, valid, pix, o, d, tn, tf, kb, cnt,
                                                      s_pst[threadIdx.x >> 5]);
         __syncwarp();
     }
@@ -1185,31 +1232,34 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, false)) k_serve(Tr
 // Launch helpers, instantiated per k in the trace_k*.cu units.
 // form: FORM_* of the scene. The backward always runs the sphere leaf test: the icosphere
 // forms hit exactly the Gaussians the sphere form hits, and the proxy form has no backward.
+// pass: PASS_FWD, PASS_BWD or PASS_SAVE (the saving forward exists for the sphere form only).
 template <int K>
-int trace_launch(const TraceArgs &a, int form, bool instr, bool bwd, int blocks, cudaStream_t s)
+int trace_launch(const TraceArgs &a, int form, bool instr, int pass, int blocks, cudaStream_t s)
 {
     dim3 g(blocks), b(128);
-    if (bwd) k_trace<K, FORM_SPHERE, false, true><<<g, b, 0, s>>>(a);
-    else if (form == FORM_PROXY && instr) k_trace<K, FORM_PROXY, true, false><<<g, b, 0, s>>>(a);
-    else if (form == FORM_PROXY) k_trace<K, FORM_PROXY, false, false><<<g, b, 0, s>>>(a);
-    else if (form == FORM_ICO && instr) k_trace<K, FORM_ICO, true, false><<<g, b, 0, s>>>(a);
-    else if (form == FORM_ICO) k_trace<K, FORM_ICO, false, false><<<g, b, 0, s>>>(a);
-    else if (instr) k_trace<K, FORM_SPHERE, true, false><<<g, b, 0, s>>>(a);
-    else k_trace<K, FORM_SPHERE, false, false><<<g, b, 0, s>>>(a);
+    if (pass == PASS_BWD) k_trace<K, FORM_SPHERE, false, PASS_BWD><<<g, b, 0, s>>>(a);
+    else if (pass == PASS_SAVE) k_trace<K, FORM_SPHERE, false, PASS_SAVE><<<g, b, 0, s>>>(a);
+    else if (form == FORM_PROXY && instr) k_trace<K, FORM_PROXY, true, PASS_FWD><<<g, b, 0, s>>>(a);
+    else if (form == FORM_PROXY) k_trace<K, FORM_PROXY, false, PASS_FWD><<<g, b, 0, s>>>(a);
+    else if (form == FORM_ICO && instr) k_trace<K, FORM_ICO, true, PASS_FWD><<<g, b, 0, s>>>(a);
+    else if (form == FORM_ICO) k_trace<K, FORM_ICO, false, PASS_FWD><<<g, b, 0, s>>>(a);
+    else if (instr) k_trace<K, FORM_SPHERE, true, PASS_FWD><<<g, b, 0, s>>>(a);
+    else k_trace<K, FORM_SPHERE, false, PASS_FWD><<<g, b, 0, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? GRTX_OK : GRTX_ERR_CUDA;
 }
 
 template <int K>
-int trace_occupancy(int form, bool instr, bool bwd, int *blocks_per_sm)
+int trace_occupancy(int form, bool instr, int pass, int *blocks_per_sm)
 {
     cudaError_t e;
-    if (bwd) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_SPHERE, false, true>, 128, 0);
-    else if (form == FORM_PROXY && instr) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_PROXY, true, false>, 128, 0);
-    else if (form == FORM_PROXY) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_PROXY, false, false>, 128, 0);
-    else if (form == FORM_ICO && instr) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_ICO, true, false>, 128, 0);
-    else if (form == FORM_ICO) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_ICO, false, false>, 128, 0);
-    else if (instr) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_SPHERE, true, false>, 128, 0);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_SPHERE, false, false>, 128, 0);
+    if (pass == PASS_BWD) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_SPHERE, false, PASS_BWD>, 128, 0);
+    else if (pass == PASS_SAVE) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_SPHERE, false, PASS_SAVE>, 128, 0);
+    else if (form == FORM_PROXY && instr) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_PROXY, true, PASS_FWD>, 128, 0);
+    else if (form == FORM_PROXY) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_PROXY, false, PASS_FWD>, 128, 0);
+    else if (form == FORM_ICO && instr) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_ICO, true, PASS_FWD>, 128, 0);
+    else if (form == FORM_ICO) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_ICO, false, PASS_FWD>, 128, 0);
+    else if (instr) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_SPHERE, true, PASS_FWD>, 128, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_SPHERE, false, PASS_FWD>, 128, 0);
     return e == cudaSuccess ? GRTX_OK : GRTX_ERR_CUDA;
 }
 
@@ -1235,7 +1285,7 @@ int serve_occupancy(int *blocks_per_sm)
 }
 
 #define GRTX_INSTANTIATE_TRACE(K)                                                                  \
-    template int trace_launch<K>(const TraceArgs &, int, bool, bool, int, cudaStream_t);          \
-    template int trace_occupancy<K>(int, bool, bool, int *);                                        \
+    template int trace_launch<K>(const TraceArgs &, int, bool, int, int, cudaStream_t);           \
+    template int trace_occupancy<K>(int, bool, int, int *);                                         \
     template int serve_launch<K>(const TraceArgs &, const ServeSeg *, int, int, cudaStream_t);     \
     template int serve_occupancy<K>(int *);

@@ -15,8 +15,8 @@
 #include "trace_impl.cuh"
 
 #define GRTX_EXTERN_NOALLOC(K)                                                                   \
-    extern template int trace_launch<K>(const TraceArgs &, int, bool, bool, int, cudaStream_t); \
-    extern template int trace_occupancy<K>(int, bool, bool, int *);
+    extern template int trace_launch<K>(const TraceArgs &, int, bool, int, int, cudaStream_t); \
+    extern template int trace_occupancy<K>(int, bool, int, int *);
 GRTX_EXTERN_NOALLOC(1)
 GRTX_EXTERN_NOALLOC(2)
 GRTX_EXTERN_NOALLOC(4)

@@ -682,6 +682,7 @@ extern "C" GRTX_API int grtx_world_trace_forward(grtx_world *w, const grtx_camer
     if (!out || !out->rgbT || ((uintptr_t)out->rgbT & 15))
         return grtx_fail(GRTX_ERR_INVALID_ARG, "rgbT must be a 16-byte aligned device pointer");
     if (out->blended_ids && out->ids_cap <= 0) return grtx_fail(GRTX_ERR_INVALID_ARG, "ids_cap must be positive");
+    if (out->saved) return grtx_fail(GRTX_ERR_INVALID_ARG, "saved blend lists are not available for worlds");
     if (out->visits || out->visits_n)
         return grtx_fail(GRTX_ERR_INVALID_ARG, "visit logs are not available for worlds (node indices of the levels collide)");
     WorldArgs W = {};

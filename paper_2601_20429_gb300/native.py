@@ -114,11 +114,15 @@ class grtx_stats(C.Structure):
                                              "evictions", "fallbacks", "stack_overflow", "collected")]
 
 
+class grtx_saved(C.Structure):
+    _fields_ = [("leaves", _fp), ("n", _fp), ("cap", C.c_int32), ("reserved", C.c_int32)]
+
+
 class grtx_trace_outputs(C.Structure):
     _fields_ = [("rgbT", _fp), ("n_blended", _fp), ("blended_ids", _fp), ("ids_cap", C.c_int32),
                 ("reserved", C.c_int32), ("stats", _fp), ("visits", _fp), ("visits_n", _fp),
                 ("visits_cap", C.c_int32), ("visits_stride", C.c_int32), ("visits_rows", C.c_int32),
-                ("reserved2", C.c_int32)]
+                ("reserved2", C.c_int32), ("saved", _fp)]
 
 
 class grtx_scene_info(C.Structure):
@@ -177,6 +181,9 @@ _SIGS = {
                                            C.POINTER(_fp), _fp]),
     "grtx_trace_backward": (C.c_int, [_fp, C.POINTER(grtx_gaussians), C.POINTER(grtx_camera), C.POINTER(grtx_params),
                                       _fp, _fp, C.POINTER(grtx_grads), _fp]),
+    "grtx_trace_backward_saved": (C.c_int, [_fp, C.POINTER(grtx_gaussians), C.POINTER(grtx_camera),
+                                            C.POINTER(grtx_params), _fp, _fp, C.POINTER(grtx_saved),
+                                            C.POINTER(grtx_grads), _fp]),
     "grtx_mirror_rays": (C.c_int, [C.POINTER(grtx_camera), C.POINTER(grtx_mirror)] + [_fp] * 11),
     "grtx_template_mesh": (C.c_int, [C.c_int, _fp, C.POINTER(C.c_int)]),
     "grtx_world_create": (C.c_int, [C.POINTER(grtx_instance), C.c_int, _fp, C.POINTER(_fp)]),
@@ -393,11 +400,21 @@ def grtx_generate_rays(cam: grtx_camera, origins, dirs, tnear=None, tfar=None, s
                                    stream_handle(stream)), "grtx_generate_rays")
 
 
+def make_saved(leaves, n) -> grtx_saved:
+    """Saved blend lists: leaves [n_rays, cap] int32 and n [n_rays] int32 CUDA tensors."""
+    sv = grtx_saved()
+    sv.leaves, sv.n, sv.cap = ptr(leaves), ptr(n), int(leaves.shape[1])
+    return sv
+
+
 def grtx_trace_forward(scene: int, cam: grtx_camera, p: grtx_params, rgbT, n_blended=None, blended_ids=None,
-                       stats=None, stream=None, visits=None, visits_n=None, visits_stride: int = 1):
+                       stats=None, stream=None, visits=None, visits_n=None, visits_stride: int = 1, saved=None):
     """visits: optional [rows, cap] uint32/int32 device log of every visits_stride-th ray's node
-    fetches, visits_n: [rows] their counts (see grtx_trace_outputs)."""
+    fetches, visits_n: [rows] their counts (see grtx_trace_outputs). saved: optional grtx_saved
+    that receives the blend lists."""
     out = grtx_trace_outputs()
+    if saved is not None:
+        out.saved = C.addressof(saved)
     out.rgbT, out.n_blended, out.blended_ids = ptr(rgbT), ptr(n_blended), ptr(blended_ids)
     out.ids_cap = int(blended_ids.shape[-1]) if blended_ids is not None else 0
     out.stats = ptr(stats)
@@ -516,6 +533,16 @@ def grtx_trace_backward(scene: int, g: grtx_gaussians, cam: grtx_camera, p: grtx
         setattr(gr, name, ptr(grads.get(name)))
     check(lib().grtx_trace_backward(C.c_void_p(scene), C.byref(g), C.byref(cam), C.byref(p), ptr(rgbT),
                                     ptr(dL_drgbT), C.byref(gr), stream_handle(stream)), "grtx_trace_backward")
+
+
+def grtx_trace_backward_saved(scene: int, g: grtx_gaussians, cam: grtx_camera, p: grtx_params, rgbT, dL_drgbT,
+                              saved: grtx_saved, grads: dict, stream=None):
+    gr = grtx_grads()
+    for name in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        setattr(gr, name, ptr(grads.get(name)))
+    check(lib().grtx_trace_backward_saved(C.c_void_p(scene), C.byref(g), C.byref(cam), C.byref(p), ptr(rgbT),
+                                          ptr(dL_drgbT), C.byref(saved), C.byref(gr), stream_handle(stream)),
+          "grtx_trace_backward_saved")
 
 
 STATS_FIELDS = tuple(n for n, _ in grtx_stats._fields_)

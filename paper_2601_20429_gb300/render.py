@@ -148,10 +148,11 @@ def n_rays_of(cam: dict, rays=None) -> int:
 
 
 def render(scene: Scene, cam: dict | None, rays=None, out=None, ids_cap: int = 0, want_n_blended=False,
-           want_stats=False, stream=None, visit_log=None, **params):
+           want_stats=False, stream=None, visit_log=None, save_cap: int = 0, **params):
     """Forward trace. Returns dict(rgbT [n_rays, 4], n_blended?, ids?, stats?, visits?,
-    visits_n?). visit_log = (stride, rows, cap) logs the node fetches of every stride-th ray
-    (output index), up to rows rays and cap fetches each."""
+    visits_n?, saved?). visit_log = (stride, rows, cap) logs the node fetches of every
+    stride-th ray (output index), up to rows rays and cap fetches each. save_cap > 0 saves each
+    ray's blend list (up to save_cap entries) for backward(saved=...)."""
     p = trace_params(alpha_min=scene.alpha_min, **params)
     c = N.make_camera(cam, rays)
     n = n_rays_of(cam, rays)
@@ -166,8 +167,15 @@ def render(scene: Scene, cam: dict | None, rays=None, out=None, ids_cap: int = 0
         stride, rows, cap = (int(v) for v in visit_log)
         vis = torch.empty((rows, cap), dtype=torch.int32, device=dev)
         vis_n = torch.empty(rows, dtype=torch.int32, device=dev)
-    N.grtx_trace_forward(scene.handle, c, p, rgbT, nb, ids, st, stream, vis, vis_n, stride)
+    saved = sv = None
+    if save_cap > 0:
+        saved = (torch.empty((n, int(save_cap)), dtype=torch.int32, device=dev),
+                 torch.empty(n, dtype=torch.int32, device=dev))
+        sv = N.make_saved(*saved)
+    N.grtx_trace_forward(scene.handle, c, p, rgbT, nb, ids, st, stream, vis, vis_n, stride, saved=sv)
     res = {"rgbT": rgbT}
+    if saved is not None:
+        res["saved"] = saved
     if nb is not None:
         res["n_blended"] = nb
     if ids is not None:
@@ -207,13 +215,19 @@ def visit_counts(visits, visits_n) -> dict:
             "revisit_fraction": float(1.0 - uniq.sum() / tot.sum()) if rows and tot.sum() else 0.0}
 
 
-def backward(scene: Scene, cam: dict | None, rgbT, dL_drgbT, rays=None, stream=None, **params):
-    """Gradients of the raw parameters the scene was built from, given dL/d(rgbT)."""
+def backward(scene: Scene, cam: dict | None, rgbT, dL_drgbT, rays=None, stream=None, saved=None, **params):
+    """Gradients of the raw parameters the scene was built from, given dL/d(rgbT). saved: the
+    blend lists of render(save_cap=...) for this view: rays with a complete list skip the
+    traversal."""
     p = trace_params(alpha_min=scene.alpha_min, **params)
     c = N.make_camera(cam, rays)
     grads = {name: torch.zeros_like(t) for name, t in
              zip(("means", "log_scales", "quats", "opacity_logits", "sh"), scene.tensors)}
-    N.grtx_trace_backward(scene.handle, scene._g, c, p, rgbT.contiguous(), dL_drgbT.contiguous(), grads, stream)
+    if saved is None:
+        N.grtx_trace_backward(scene.handle, scene._g, c, p, rgbT.contiguous(), dL_drgbT.contiguous(), grads, stream)
+    else:
+        N.grtx_trace_backward_saved(scene.handle, scene._g, c, p, rgbT.contiguous(), dL_drgbT.contiguous(),
+                                    N.make_saved(*saved), grads, stream)
     return grads
 
 
@@ -224,7 +238,9 @@ class RenderFunction(torch.autograd.Function):
     by default; opts may set bvh_builder / bvh_codes) and freed after backward. With
     opts["scene"] (a sphere- or icosphere-form Scene of the same Gaussians, kept by the caller
     across steps) it is updated in place, by opts["update"] = "refit" (default) or
-    "rebuild"."""
+    "rebuild". With opts["save_cap"] > 0 the forward saves each ray's blend list (up to that
+    many entries) and the backward reads it instead of re-traversing, replaying only the rays
+    whose list overflowed."""
 
     @staticmethod
     def forward(ctx, means, log_scales, quats, logits, sh, sh_degree, cam, opts):
@@ -242,15 +258,18 @@ class RenderFunction(torch.autograd.Function):
             for key in ("alpha_min", "bvh_codes", "bvh_builder"):
                 o.pop(key, None)
             scene.update(*params, mode=mode)
-        rgbT = render(scene, cam, **o)["rgbT"]
-        ctx.scene, ctx.cam, ctx.opts = scene, cam, o
+        save_cap = int(o.pop("save_cap", 0))
+        res = render(scene, cam, save_cap=save_cap, **o)
+        rgbT = res["rgbT"]
+        ctx.scene, ctx.cam, ctx.opts, ctx.saved = scene, cam, o, res.get("saved")
         ctx.save_for_backward(rgbT)
         return rgbT
 
     @staticmethod
     def backward(ctx, grad_rgbT):
         (rgbT,) = ctx.saved_tensors
-        g = backward(ctx.scene, ctx.cam, rgbT, grad_rgbT.float().contiguous(), **ctx.opts)
+        g = backward(ctx.scene, ctx.cam, rgbT, grad_rgbT.float().contiguous(), saved=ctx.saved, **ctx.opts)
+        ctx.saved = None
         if ctx.owned:
             ctx.scene.close()
         return g["means"], g["log_scales"], g["quats"], g["opacity_logits"], g["sh"], None, None, None

@@ -765,3 +765,64 @@ def test_batched_views_equal_separate_traces(dense):
         R.render_batch(sc, [(cam, None)] * 65, k=8)
     proxy.close()
     sc.close()
+
+
+# ------------------------------------------------------------------ saved blend lists for the backward
+
+
+@pytest.mark.parametrize("traversal", ["checkpoint", "restart"])
+def test_saved_blend_lists_give_the_replay_gradients(dense, traversal):
+    """A forward that saves each ray's blend list gives the same image, lists that are the
+    blend order of the instrumented trace, and a backward that reads them (complete lists)
+    or replays the rounds (overflowed lists, cap 3 here) with the same gradients as the
+    plain replay, up to the order of the atomic additions."""
+    g, cam, S, rays, ref = dense
+    g = g.subset(np.arange(6000))
+    sc = R.Scene.from_params(g)
+    inst = R.render(sc, cam, k=8, traversal=traversal, ids_cap=256, want_n_blended=True)
+    plain = R.render(sc, cam, k=8, traversal=traversal)["rgbT"]
+    w = torch.from_numpy(np.random.default_rng(4).normal(0, 1, (cam["width"] * cam["height"], 4))
+                         .astype(np.float32)).cuda()
+    replay = {key: v.cpu().numpy() for key, v in R.backward(sc, cam, plain, w, k=8, traversal=traversal).items()}
+    nb = inst["n_blended"].cpu().numpy()
+    leaf_ids = sc.export()[1].cpu().numpy()                     # Gaussian id of each leaf slot
+    for cap in (256, 3):
+        res = R.render(sc, cam, k=8, traversal=traversal, save_cap=cap)
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(res["rgbT"].cpu().numpy(), plain.cpu().numpy(), rtol=0, atol=1e-6)
+        leaves, n = (t.cpu().numpy() for t in res["saved"])
+        np.testing.assert_array_equal(n, nb)
+        ids = inst["ids"].cpu().numpy()
+        for r in range(len(n)):
+            m = min(n[r], cap)
+            np.testing.assert_array_equal(leaf_ids[leaves[r, :m]], ids[r, :m])
+        if cap == 3:
+            assert (n > cap).mean() > 0.02 and (n <= cap).mean() > 0.02   # both paths exercised
+        got = R.backward(sc, cam, res["rgbT"], w, k=8, traversal=traversal, saved=res["saved"])
+        for key, v in got.items():
+            np.testing.assert_allclose(v.cpu().numpy(), replay[key], rtol=1e-4, atol=1e-6)
+    sc.close()
+
+
+def test_saved_blend_lists_in_autograd_and_errors(dense):
+    g, cam, S, rays, ref = dense
+    g = g.subset(np.arange(3000))
+    target = torch.rand(cam["width"] * cam["height"], 4, device="cuda")
+    grads = {}
+    for save_cap in (0, 64):
+        params = [t.requires_grad_(True) for t in R.params_to_device(g)]
+        out = R.render_differentiable(*params, g.sh_degree, cam, k=8, save_cap=save_cap)
+        ((out - target) ** 2).mean().backward()
+        grads[save_cap] = [p.grad.cpu().numpy() for p in params]
+    for a, b in zip(grads[64], grads[0]):
+        np.testing.assert_allclose(a, b, rtol=1e-4, atol=1e-7)
+    sc = R.Scene.from_params(g)
+    proxy = R.Scene.from_params(g, form="proxy20")
+    with pytest.raises(N.GrtxError, match="sphere form"):
+        R.render(proxy, cam, k=8, save_cap=8)
+    with pytest.raises(N.GrtxError, match="no other optional output"):
+        R.render(sc, cam, k=8, save_cap=8, want_stats=True)
+    with pytest.raises(N.GrtxError, match="no other optional output"):
+        R.render(sc, cam, k=8, save_cap=8, traversal="single")
+    sc.close()
+    proxy.close()
