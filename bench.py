@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-extra", action="store_true", help="skip the differentiable and outdoor measurements")
+    ap.add_argument("--section", choices=["differentiable", "outdoor"], default=None,
+                    help="run one measurement section alone and print its JSON (for profiling; 1 GPU)")
     return ap.parse_args()
 
 
@@ -606,6 +608,17 @@ def main():
 
     torch.cuda.set_device(dist.local)
     N.lib()
+    if args.section is not None:
+        stream = torch.cuda.current_stream()
+        if args.section == "differentiable":
+            res = bench_differentiable(args.steps, args.warmup, stream)
+        else:
+            flush_buf = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
+            res = bench_outdoor(args.steps, stream, lambda: flush_buf.fill_(1))
+        if dist.rank == 0:
+            print(json.dumps({"section": args.section, **res}))
+        dist.close()
+        return
     peaks = load_peaks()
     g, cam, cfg = scenes.config_surface()
     k = cfg["k"]
