@@ -225,7 +225,8 @@ typedef struct grtx_scene_info {
     int32_t sh_degree;
     int32_t reserved;
     int64_t bytes_nodes;       /* device bytes of BVH nodes                                */
-    int64_t bytes_leaves;      /* device bytes of leaf records (geometry / triangles)      */
+    int64_t bytes_leaves;      /* device bytes of leaf records (geometry / triangles, and   */
+                               /* the raw parameters in leaf order that the backward reads) */
     int64_t bytes_appearance;  /* device bytes of the appearance (SH) records              */
     int64_t bytes_workspace;   /* device bytes of the per-slot checkpoint/eviction buffers */
     float bounds[6];           /* world AABB of all leaves                                 */
@@ -436,7 +437,10 @@ GRTX_API int grtx_trace_forward_batch(grtx_scene *scene, const grtx_camera *cams
  * re-traverses the same rounds and accumulates, front to back, the derivative of Eq.
  * volume-render and of alpha = o G(r_o + t_alpha r_d) through the unit-sphere transform
  * (the hit set, order and termination index are piecewise constant and not differentiated).
- * Accumulates with atomics into *grads (caller zeroes). */
+ * Accumulates into *grads (caller zeroes): SH gradients with vector atomics, the others with
+ * vector atomics into a per-leaf stage that a second kernel adds into *grads. The gradient
+ * reads the scene's own copy of the raw parameters (packed in leaf order at build and
+ * update), so g must be the parameters the scene was built or last updated from. */
 GRTX_API int grtx_trace_backward(grtx_scene *scene, const grtx_gaussians *g,
                                  const grtx_camera *cam, const grtx_params *p,
                                  const float *d_rgbT, const float *d_dL_drgbT,

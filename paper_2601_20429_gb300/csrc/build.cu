@@ -75,6 +75,16 @@ __device__ __forceinline__ void prep_one(const float *__restrict__ means, const 
     }
 }
 
+// Raw parameters of Gaussian i packed for the backward: (mu, logit), (log-scales, 0), q.
+__device__ __forceinline__ void pack_raw(const float *__restrict__ means, const float *__restrict__ log_scales,
+                                         const float *__restrict__ quats, const float *__restrict__ logits,
+                                         int64_t i, float4 *__restrict__ raw)
+{
+    raw[0] = make_float4(means[3 * i], means[3 * i + 1], means[3 * i + 2], logits[i]);
+    raw[1] = make_float4(log_scales[3 * i], log_scales[3 * i + 1], log_scales[3 * i + 2], 0.f);
+    raw[2] = make_float4(quats[4 * i], quats[4 * i + 1], quats[4 * i + 2], quats[4 * i + 3]);
+}
+
 __global__ void k_prep(const float *__restrict__ means, const float *__restrict__ log_scales,
                        const float *__restrict__ quats, const float *__restrict__ logits, int64_t n,
                        float alpha_min, float4 *__restrict__ geom, float *__restrict__ aabb)
@@ -505,13 +515,14 @@ __global__ void k_refit_records(const float *__restrict__ means, const float *__
                                 const float *__restrict__ sh, int n_sh, int app_stride,
                                 const uint32_t *__restrict__ gid, int64_t n_valid, int64_t n, float alpha_min,
                                 float4 *__restrict__ geom, float *__restrict__ leaf_aabb, float *__restrict__ app,
-                                unsigned *__restrict__ revived)
+                                float4 *__restrict__ raw, unsigned *__restrict__ revived)
 {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     uint32_t j = gid[s];
     if (s < n_valid) {
         prep_one(means, log_scales, quats, logits, j, alpha_min, geom + 4 * s, leaf_aabb + 6 * s);
+        pack_raw(means, log_scales, quats, logits, j, raw + 3 * s);
         const float *src = sh + (size_t)j * n_sh;
         float *dst = app + (size_t)s * app_stride;
         for (int c = 0; c < app_stride; ++c) dst[c] = c < n_sh ? src[c] : 0.f;
@@ -744,8 +755,10 @@ __global__ void k_count_valid(const uint64_t *codes, int64_t n, unsigned long lo
 __global__ void k_gather_gaussians(const uint32_t *__restrict__ order, int64_t n_valid,
                                    const float4 *__restrict__ geom_in, const float *__restrict__ aabb_in,
                                    const float *__restrict__ sh, int n_sh, int app_stride,
+                                   const float *__restrict__ means, const float *__restrict__ log_scales,
+                                   const float *__restrict__ quats, const float *__restrict__ logits,
                                    float4 *__restrict__ geom, float *__restrict__ aabb,
-                                   float *__restrict__ app, uint32_t *__restrict__ gid)
+                                   float *__restrict__ app, uint32_t *__restrict__ gid, float4 *__restrict__ raw)
 {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_valid) return;
@@ -756,6 +769,7 @@ __global__ void k_gather_gaussians(const uint32_t *__restrict__ order, int64_t n
     float *dst = app + (size_t)s * app_stride;
     for (int c = 0; c < app_stride; ++c) dst[c] = c < n_sh ? src[c] : 0.f;
     gid[s] = i;
+    pack_raw(means, log_scales, quats, logits, i, raw + 3 * s);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -903,7 +917,8 @@ struct Alloc {
 void free_scene_arrays(grtx_scene *sc)
 {
     cudaStream_t s = sc->stream;
-    void *ptrs[] = {sc->nodes, sc->geom, sc->tris, sc->app, sc->gid, sc->leaf_ids, sc->codes, sc->ws, sc->d_counter};
+    void *ptrs[] = {sc->nodes, sc->geom, sc->tris, sc->app, sc->raw, sc->gid, sc->leaf_ids, sc->codes, sc->ws,
+                    sc->d_counter};
     for (void *p : ptrs)
         if (p) cudaFreeAsync(p, s);
 }
@@ -1097,10 +1112,12 @@ int build_scene(const grtx_gaussians *g, const grtx_params *p, int form, grtx_sc
     TRY(A.get(&sc->geom, 4 * nv, false));
     TRY(A.get(&sc->app, (size_t)sc->app_stride * nv, false));
     TRY(A.get(&sc->gid, n, false));                 // leaf slots, then the culled Gaussians
+    TRY(A.get(&sc->raw, 3 * nv, false));
     TRY(A.get(&leaf_aabb, 6 * nv, true));
     k_gather_gaussians<<<grtx_div_up(nv, kThreads), kThreads, 0, s>>>(order, nv, geom_raw, aabb_raw, g->sh, n_sh,
-                                                                      sc->app_stride, sc->geom, leaf_aabb,
-                                                                      sc->app, sc->gid);
+                                                                      sc->app_stride, g->means, g->log_scales,
+                                                                      g->quats, g->opacity_logits, sc->geom,
+                                                                      leaf_aabb, sc->app, sc->gid, sc->raw);
     GRTX_CHECK_LAUNCH("gather");
     if (n > nv)
         GRTX_CUDA(cudaMemcpyAsync(sc->gid + nv, order + nv, (size_t)(n - nv) * 4, cudaMemcpyDeviceToDevice, s));
@@ -1182,7 +1199,7 @@ int refit_scene(const grtx_gaussians *g, grtx_scene *sc, cudaStream_t s, bool *r
     GRTX_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(unsigned), s));
     k_refit_records<<<grtx_div_up(n, kThreads), kThreads, 0, s>>>(
         g->means, g->log_scales, g->quats, g->opacity_logits, g->sh, sc->n_coef * 3, sc->app_stride, sc->gid, nv, n,
-        sc->alpha_min, sc->geom, leaf_aabb, sc->app, d_flag);
+        sc->alpha_min, sc->geom, leaf_aabb, sc->app, sc->raw, d_flag);
     if (nv == 1) {
         k_emit_single<<<1, 1, 0, s>>>(leaf_aabb, sc->nodes);
     } else {
@@ -1447,7 +1464,8 @@ extern "C" GRTX_API int grtx_scene_info_get(const grtx_scene *sc, grtx_scene_inf
     info->form = sc->form;
     info->sh_degree = sc->sh_degree;
     info->bytes_nodes = sc->n_nodes * 64;
-    info->bytes_leaves = sc->form != GRTX_FORM_PROXY20 ? sc->n_valid * 64 : sc->n_leaves * 48 + sc->n_valid * 64;
+    info->bytes_leaves = (sc->form != GRTX_FORM_PROXY20 ? sc->n_valid * 64 : sc->n_leaves * 48 + sc->n_valid * 64) +
+                         sc->n_valid * 48;      // + the raw parameters in leaf order
     info->bytes_appearance = sc->n_valid * sc->app_stride * 4;
     info->bytes_workspace = (int64_t)sc->ws_bytes;
     for (int c = 0; c < 6; ++c) info->bounds[c] = sc->bounds[c];

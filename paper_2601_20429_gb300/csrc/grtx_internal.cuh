@@ -43,6 +43,7 @@ struct grtx_scene {
     float4 *geom = nullptr;      // [n_valid][4]: rows (A_j | mu_j) + (o, -kappa^2 log2(e)/2, id, 0), leaf order
     float4 *tris = nullptr;      // proxy form: [n_leaves][3] world triangle (v0 | gidx, v1, v2)
     float *app = nullptr;        // [n_valid][app_stride] SH coefficients in leaf order
+    float4 *raw = nullptr;       // [n_valid][3] raw parameters in leaf order: (mu, logit), (log-scales, 0), q
     uint32_t *gid = nullptr;     // [n] Gaussian id of each sorted Gaussian, then of each culled one
     uint32_t *leaf_ids = nullptr;// [n_leaves] Gaussian id of each leaf
     uint64_t *codes = nullptr;   // [n_leaves] sorted Morton codes

@@ -178,6 +178,7 @@ SceneRef grtx_scene_ref(const grtx_scene *sc)
     r.gid = sc->gid;
     r.tpl_nodes = sc->tpl_nodes;
     r.tpl_tris = sc->tpl_tris;
+    r.raw = sc->raw;
     r.app_stride = sc->app_stride;
     r.sh_degree = sc->sh_degree;
     r.has_tree = sc->n_valid > 0;
@@ -241,6 +242,34 @@ int run(grtx_scene *sc, TraceArgs &a, int k, bool instr, int pass, unsigned *que
         return grtx_cuda_fail(e == cudaSuccess ? cudaErrorLaunchFailure : e, "trace launch");
     }
     return GRTX_OK;
+}
+
+// Add the per-leaf staged gradients into the caller's arrays (one thread per leaf, so plain
+// additions; the caller zeroed or holds earlier sums).
+__global__ void k_scatter_grads(const float4 *__restrict__ stage, const uint32_t *__restrict__ gid, int64_t n,
+                                float *g_means, float *g_log_scales, float *g_quats, float *g_logits)
+{
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const size_t i = gid[s];
+    const float4 a = stage[3 * s], b = stage[3 * s + 1], c = stage[3 * s + 2];
+    if (g_means) {
+        g_means[3 * i] += a.x;
+        g_means[3 * i + 1] += a.y;
+        g_means[3 * i + 2] += a.z;
+    }
+    if (g_logits) g_logits[i] += a.w;
+    if (g_log_scales) {
+        g_log_scales[3 * i] += b.x;
+        g_log_scales[3 * i + 1] += b.y;
+        g_log_scales[3 * i + 2] += b.z;
+    }
+    if (g_quats) {
+        g_quats[4 * i] += c.x;
+        g_quats[4 * i + 1] += c.y;
+        g_quats[4 * i + 2] += c.z;
+        g_quats[4 * i + 3] += c.w;
+    }
 }
 
 __global__ void k_gen_rays(CamRef a, float *o, float *d, float *tn, float *tf)
@@ -441,7 +470,6 @@ int backward(grtx_scene *sc, const grtx_gaussians *g, const grtx_camera *cam, co
     a.g_sh = grads->sh;
     a.n_sh = sc->n_coef * 3;
     a.vec_sh = a.n_sh == 48 && ((uintptr_t)grads->sh & 15) == 0;
-    a.vec_q = ((uintptr_t)grads->quats & 15) == 0;
     if (saved) {
         if (!saved->leaves || !saved->n || saved->cap <= 0)
             return grtx_fail(GRTX_ERR_INVALID_ARG, "saved lists need leaves, n and a positive cap");
@@ -450,7 +478,26 @@ int backward(grtx_scene *sc, const grtx_gaussians *g, const grtx_camera *cam, co
         a.save_n = saved->n;
         a.save_cap = saved->cap;
     }
-    return run(sc, a, p->k, false, PASS_BWD, sc->d_counter + 1, s);
+    // gradients of means, logits, log-scales and quaternions are staged per leaf (vector
+    // atomics in the kernel), then added into the caller's arrays
+    const bool staged = sc->n_valid > 0 && (grads->means || grads->log_scales || grads->quats || grads->opacity_logits);
+    if (staged) {
+        if (cudaMallocAsync((void **)&a.g_stage, (size_t)sc->n_valid * 48, s) != cudaSuccess) {
+            cudaGetLastError();
+            return grtx_fail(GRTX_ERR_OOM, "gradient staging allocation failed");
+        }
+        GRTX_CUDA(cudaMemsetAsync(a.g_stage, 0, (size_t)sc->n_valid * 48, s));
+    }
+    st = run(sc, a, p->k, false, PASS_BWD, sc->d_counter + 1, s);
+    if (staged) {
+        if (st == GRTX_OK)
+            k_scatter_grads<<<grtx_div_up(sc->n_valid, 256), 256, 0, s>>>(a.g_stage, sc->gid, sc->n_valid, grads->means,
+                                                                         grads->log_scales, grads->quats,
+                                                                         grads->opacity_logits);
+        cudaFreeAsync(a.g_stage, s);
+        if (st == GRTX_OK) GRTX_CHECK_LAUNCH("gradient scatter");
+    }
+    return st;
 }
 
 }  // namespace

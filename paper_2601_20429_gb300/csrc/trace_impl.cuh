@@ -18,6 +18,7 @@ struct SceneRef {
     const float *app;
     const uint32_t *gid;
     const float4 *tpl_nodes, *tpl_tris;   // icosphere forms: shared template BVH and triangles
+    const float4 *raw;                    // [n_valid][3] raw parameters in leaf order (backward)
     int app_stride, sh_degree, has_tree, pad;
 };
 
@@ -64,8 +65,9 @@ struct TraceArgs {
     const float4 *fwd_rgbT, *dL_drgbT;
     const float *means, *log_scales, *quats, *logits;
     float *g_means, *g_log_scales, *g_quats, *g_logits, *g_sh;
+    float4 *g_stage;             // [n_valid][3] per-leaf gradients of (mu, logit), log-scales, q
     int n_sh;
-    int vec_sh, vec_q;           // gradients of SH (48 floats) / quaternions may use float4 atomics
+    int vec_sh;                  // gradients of SH (48 floats) may use float4 atomics
 };
 
 // One request of a serving step: its scene, camera, output, and which of its queue items
@@ -844,15 +846,17 @@ __device__ __forceinline__ void blend_one(const TraceArgs &a, const SceneRef &sc
     for (int ch = 0; ch < 3; ++ch) dLda += st.G[ch] * (st.T * c[ch] - (st.Cf[ch] - st.C[ch]) * inv1m);
     st.T *= (1.0f - al);
     if (clamped || dLda == 0.f) return;
-    // alpha = o exp(-d2/2), d2 = |S^-1 R^T (x* - mu)|^2 at x* = o + t d (t fixed: envelope)
-    float lam = a.logits[gi];
-    float op = __fdividef(1.0f, 1.0f + expf(-lam));
-    if (a.g_logits) atomic_add_f(a.g_logits + gi, dLda * al_raw * (1.0f - op));
+    if (!a.g_stage) return;
+    // alpha = o exp(-d2/2), d2 = |S^-1 R^T (x* - mu)|^2 at x* = o + t d (t fixed: envelope).
+    // The raw parameters come packed in leaf order, (mu, logit), (log-scales, 0), q.
+    const float4 *rw = sc.raw + 3 * (size_t)idx;
+    const float4 r_ml = __ldg(rw), r_ls = __ldg(rw + 1), r_q = __ldg(rw + 2);
+    float op = __fdividef(1.0f, 1.0f + expf(-r_ml.w));
+    const float g_logit = dLda * al_raw * (1.0f - op);
     float dLdd2 = -0.5f * dLda * al_raw;
-    float mu[3] = {a.means[3 * gi], a.means[3 * gi + 1], a.means[3 * gi + 2]};
     // inverse scales 1/s_j = exp(-log s_j)
-    float is[3] = {expf(-a.log_scales[3 * gi]), expf(-a.log_scales[3 * gi + 1]), expf(-a.log_scales[3 * gi + 2])};
-    float qw = a.quats[4 * gi], qx = a.quats[4 * gi + 1], qy = a.quats[4 * gi + 2], qz = a.quats[4 * gi + 3];
+    float is[3] = {expf(-r_ls.x), expf(-r_ls.y), expf(-r_ls.z)};
+    float qw = r_q.x, qx = r_q.y, qy = r_q.z, qz = r_q.w;
     float iq = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
     float w_ = qw * iq, x = qx * iq, y = qy * iq, z = qz * iq;
     float R[3][3] = {{1.f - 2.f * (y * y + z * z), 2.f * (x * y - w_ * z), 2.f * (x * z + w_ * y)},
@@ -865,18 +869,15 @@ __device__ __forceinline__ void blend_one(const TraceArgs &a, const SceneRef &sc
         v[j] = u * is[j];
         vs[j] = v[j] * is[j];
     }
-    if (a.g_means) {
+    float gm[3];
 #pragma unroll
-        for (int c2 = 0; c2 < 3; ++c2) {
-            float gm = R[c2][0] * vs[0] + R[c2][1] * vs[1] + R[c2][2] * vs[2];
-            atomic_add_f(a.g_means + 3 * gi + c2, -2.0f * dLdd2 * gm);
-        }
-    }
-    if (a.g_log_scales) {
-#pragma unroll
-        for (int j = 0; j < 3; ++j) atomic_add_f(a.g_log_scales + 3 * gi + j, -2.0f * dLdd2 * v[j] * v[j]);
-    }
-    if (a.g_quats) {
+    for (int c2 = 0; c2 < 3; ++c2) gm[c2] = -2.0f * dLdd2 * (R[c2][0] * vs[0] + R[c2][1] * vs[1] + R[c2][2] * vs[2]);
+    // staged per leaf (three vector atomics); added into the caller's arrays after the kernel
+    float4 *stage = a.g_stage + 3 * (size_t)idx;
+    atomicAdd(stage, make_float4(gm[0], gm[1], gm[2], g_logit));
+    atomicAdd(stage + 1, make_float4(-2.0f * dLdd2 * v[0] * v[0], -2.0f * dLdd2 * v[1] * v[1],
+                                     -2.0f * dLdd2 * v[2] * v[2], 0.f));
+    {
         float Gr[3][3];
 #pragma unroll
         for (int r = 0; r < 3; ++r)
@@ -890,16 +891,8 @@ __device__ __forceinline__ void blend_one(const TraceArgs &a, const SceneRef &sc
         float gz = 2.f * (-2.f * z * Gr[0][0] - w_ * Gr[0][1] + x * Gr[0][2] + w_ * Gr[1][0] - 2.f * z * Gr[1][1] +
                           y * Gr[1][2] + x * Gr[2][0] + y * Gr[2][1]);
         float dot = w_ * gw + x * gx + y * gy + z * gz;
-        const float4 gq = make_float4((gw - w_ * dot) * iq, (gx - x * dot) * iq, (gy - y * dot) * iq,
-                                      (gz - z * dot) * iq);
-        if (a.vec_q) {
-            atomicAdd(reinterpret_cast<float4 *>(a.g_quats) + gi, gq);
-        } else {
-            atomic_add_f(a.g_quats + 4 * gi + 0, gq.x);
-            atomic_add_f(a.g_quats + 4 * gi + 1, gq.y);
-            atomic_add_f(a.g_quats + 4 * gi + 2, gq.z);
-            atomic_add_f(a.g_quats + 4 * gi + 3, gq.w);
-        }
+        atomicAdd(stage + 2, make_float4((gw - w_ * dot) * iq, (gx - x * dot) * iq, (gy - y * dot) * iq,
+                                         (gz - z * dot) * iq));
     }
 }
 
