@@ -59,9 +59,9 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(name: str):
-    """DRAM bytes per launch recorded in profiles/<name>.md by an ncu capture, if the trace
-    kernel's source is unchanged since (its hash is recorded beside the figure)."""
+def profiled_figure(name: str, key: str):
+    """A figure recorded in profiles/<name>.md from an ncu capture (a "- key: `value`" line),
+    if the trace kernel's source is unchanged since (its hash is recorded beside it)."""
     path = os.path.join(ROOT, "profiles", name + ".md")
     try:
         text = open(path).read()
@@ -71,13 +71,21 @@ def profiled_traffic(name: str):
     for line in text.splitlines():
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
-            vals[k.strip()] = v.strip().strip("`")
+            v = v.strip()
+            if v.startswith("`") and v.count("`") >= 2:
+                v = v[1:v.index("`", 1)]              # the first `value`; a note may follow
+            vals[k.strip()] = v
     if vals.get("kernel_source_hash") != kernel_source_hash():
         return None
     try:
-        return float(vals["dram_bytes_per_launch"])
+        return float(vals[key])
     except (KeyError, ValueError):
         return None
+
+
+def profiled_traffic(name: str):
+    """DRAM bytes per launch of the profiled kernel (see profiled_figure)."""
+    return profiled_figure(name, "dram_bytes_per_launch")
 
 
 def load_peaks():
@@ -719,6 +727,7 @@ def main():
                 "traffic": traffic, "kernel": "k_trace<16, sphere>",
                 "bytes_per_ray": logical / max(st["rays"], 1),
                 "dram_frac": (traffic / (ms / 1e3) / 1e9 / peak) if traffic else None,
+                "issue_active_frac": profiled_figure("k_trace16_surface1M_1080p", "issue_active_frac"),
                 "kernel_source_hash": kernel_source_hash(),
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
 
