@@ -18,7 +18,10 @@
  *     overflows are never fatal: the affected ray falls back to restarting from the root
  *     (always correct) and the event is counted in grtx_stats.
  *   - Floating point is IEEE FP32 throughout; arrays are C-contiguous structure-of-arrays.
- *   - A scene or server may be used from one host thread at a time.
+ *   - A scene or server may be used from one host thread at a time. The traces of one scene
+ *     share its per-slot workspace and queue counters, so they must be ordered: issue them
+ *     on one stream, or synchronise between streams. Different scenes may trace
+ *     concurrently.
  */
 #ifndef GRTX_H
 #define GRTX_H
