@@ -179,7 +179,9 @@ def test_update_rejects_bad_input():
 
 def test_training_steps_with_a_kept_scene_give_the_same_gradients():
     """Autograd with a scene kept across steps (refit each step) against a scene built anew
-    each step: same images and, up to the order of the gradient atomics, the same gradients."""
+    each step: same images and, up to the order of the gradient atomics, the same gradients.
+    Also with the kept scene and blend lists saved for the backward (a small cap, so that
+    some rays overflow theirs and replay)."""
     g0 = _base(n=4000)
     cam = scenes.pinhole_camera(24, 24, (0.0, 0.0, -3.0), (0, 0, 0), 50.0)
     target = torch.rand(24 * 24, 4, device="cuda")
@@ -187,7 +189,7 @@ def test_training_steps_with_a_kept_scene_give_the_same_gradients():
     for step in range(3):
         g = _moved(g0, seed=40 + step, sigma=0.02)
         res = {}
-        for name, opts in (("fresh", {}), ("kept", {"scene": kept})):
+        for name, opts in (("fresh", {}), ("kept", {"scene": kept}), ("saved", {"scene": kept, "save_cap": 6})):
             params = [t.requires_grad_(True) for t in R.params_to_device(g)]
             out = R.render_differentiable(*params, g.sh_degree, cam, k=8, **opts)
             loss = ((out - target) ** 2).mean()
@@ -196,4 +198,7 @@ def test_training_steps_with_a_kept_scene_give_the_same_gradients():
         np.testing.assert_array_equal(res["kept"][0], res["fresh"][0])
         for a, b in zip(res["kept"][1], res["fresh"][1]):
             np.testing.assert_allclose(a, b, rtol=1e-5, atol=1e-7)
+        np.testing.assert_allclose(res["saved"][0], res["fresh"][0], rtol=0, atol=1e-6)
+        for a, b in zip(res["saved"][1], res["fresh"][1]):
+            np.testing.assert_allclose(a, b, rtol=1e-4, atol=1e-7)
     kept.close()
