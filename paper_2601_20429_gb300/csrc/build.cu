@@ -559,6 +559,8 @@ __global__ void k_unpack_tree(const float4 *__restrict__ nodes, int n, uint32_t 
 // ------------------------------------------------------------------------------------------
 constexpr int kPlocBlock = 256;
 constexpr int kPlocRadius = GRTX_PLOC_RADIUS;
+constexpr int kPlocBatch = 8;              // rounds between host checks once few clusters are left
+constexpr int kPlocBatchBelow = 65536;     // "few": below this many clusters
 
 // Surface area of the union of two boxes, 2 (ex ey + ey ez + ez ex) with every operation
 // rounded as written (no contraction), so that both members of a pair see the same value.
@@ -573,16 +575,31 @@ __device__ __forceinline__ float ploc_area(const float *a, const float *b)
     return __fmul_rn(2.0f, s);
 }
 
-__global__ void k_ploc_init(uint32_t *__restrict__ id, int n)
+// Device loop state of the clustering: [0] clusters left m, [1] nodes made, [2] rounds run,
+// [3] error (a round that made no progress or made too many nodes). A round with m <= 1 does
+// nothing, so several rounds can be enqueued between host checks.
+enum { kPlocM = 0, kPlocMade = 1, kPlocRounds = 2, kPlocErr = 3 };
+
+__global__ void k_ploc_init(uint32_t *__restrict__ id, int n, int *__restrict__ st)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) id[i] = GRTX_LEAF | (uint32_t)i;
+    if (i == 0) {
+        st[kPlocM] = n;
+        st[kPlocMade] = 0;
+        st[kPlocRounds] = 0;
+        st[kPlocErr] = 0;
+    }
 }
 
-__global__ void __launch_bounds__(kPlocBlock) k_ploc_nn(const float *__restrict__ cb, int m, int *__restrict__ nn)
+__global__ void __launch_bounds__(kPlocBlock) k_ploc_nn(const float *__restrict__ cb, const int *__restrict__ st,
+                                                        int *__restrict__ nn)
 {
     __shared__ float sb[(kPlocBlock + 2 * kPlocRadius) * 6];
+    const int m = st[kPlocM];
+    if (m <= 1) return;
     const int b0 = blockIdx.x * kPlocBlock;
+    if (b0 >= m) return;
     for (int t = threadIdx.x; t < (kPlocBlock + 2 * kPlocRadius) * 6; t += blockDim.x) {
         int g = b0 - kPlocRadius + t / 6;
         sb[t] = (g >= 0 && g < m) ? cb[6 * (size_t)g + t % 6] : 0.f;
@@ -607,11 +624,12 @@ __global__ void __launch_bounds__(kPlocBlock) k_ploc_nn(const float *__restrict_
 
 // create[i]: cluster i starts a merge (mutual pair, i the lower); keep[i]: cluster i survives
 // (as itself or as the merged node); tail: the two flags of the last cluster.
-__global__ void k_ploc_flags(const int *__restrict__ nn, int m, uint32_t *__restrict__ create,
+__global__ void k_ploc_flags(const int *__restrict__ nn, const int *__restrict__ st, uint32_t *__restrict__ create,
                              uint32_t *__restrict__ keep, uint32_t *__restrict__ tail)
 {
+    const int m = st[kPlocM];
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
+    if (m <= 1 || i >= m) return;
     int j = nn[i];
     bool mutual = j >= 0 && nn[j] == i;
     uint32_t c = mutual && i < j, k = !(mutual && j < i);
@@ -623,20 +641,35 @@ __global__ void k_ploc_flags(const int *__restrict__ nn, int m, uint32_t *__rest
     }
 }
 
-__global__ void k_ploc_totals(const uint32_t *__restrict__ create_off, const uint32_t *__restrict__ keep_off, int m,
-                              const uint32_t *__restrict__ tail, uint32_t *__restrict__ totals)
+// The round's totals (nodes created, clusters kept) and the next loop state, with the progress
+// checks: every round must merge at least one pair and keep exactly m - created clusters.
+__global__ void k_ploc_advance(const uint32_t *__restrict__ create_off, const uint32_t *__restrict__ keep_off,
+                               const uint32_t *__restrict__ tail, int n, int *__restrict__ st)
 {
-    totals[0] = create_off[m - 1] + tail[0];
-    totals[1] = keep_off[m - 1] + tail[1];
+    const int m = st[kPlocM];
+    if (m <= 1 || st[kPlocErr]) return;
+    const uint32_t created = create_off[m - 1] + tail[0];
+    const uint32_t kept = keep_off[m - 1] + tail[1];
+    const int made = st[kPlocMade];
+    if (created == 0 || (int64_t)kept != (int64_t)m - created || (int64_t)made + created > n - 1) {
+        st[kPlocErr] = 1;
+        st[kPlocM] = 1;                       // stop the enqueued rounds
+        return;
+    }
+    st[kPlocMade] = made + (int)created;
+    st[kPlocM] = (int)kept;
+    st[kPlocRounds] += 1;
 }
 
 __global__ void k_ploc_merge(const float *__restrict__ cb, const uint32_t *__restrict__ id, const int *__restrict__ nn,
-                             const uint32_t *__restrict__ create_off, const uint32_t *__restrict__ keep_off, int m,
-                             uint32_t node_base, float *__restrict__ cb_out, uint32_t *__restrict__ id_out,
+                             const uint32_t *__restrict__ create_off, const uint32_t *__restrict__ keep_off,
+                             const int *__restrict__ st, float *__restrict__ cb_out, uint32_t *__restrict__ id_out,
                              uint32_t *__restrict__ lc, uint32_t *__restrict__ rc)
 {
+    const int m = st[kPlocM];
+    const uint32_t node_base = (uint32_t)st[kPlocMade];
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
+    if (m <= 1 || i >= m) return;
     int j = nn[i];
     bool mutual = j >= 0 && nn[j] == i;
     if (mutual && j < i) return;              // merged into cluster j
@@ -943,15 +976,18 @@ int build_tree(grtx_scene *sc, Alloc &A, float *leaf_aabb, int64_t n, uint32_t *
     return GRTX_OK;
 }
 
-// PLOC tree over n >= 2 boxes in order: left/right/parent in the radix tree's layout. One
-// host round trip per iteration reads the number of clusters left; at most n - 1 iterations
-// can happen (each merges at least one pair), and more fail the build.
+// PLOC tree over n >= 2 boxes in order: left/right/parent in the radix tree's layout. The loop
+// state lives on the device (k_ploc_advance). The host reads it after every round while many
+// clusters are left (a round then costs far more than the round trip), and after every
+// kPlocBatch rounds once few are left, each launch sized by the last count it read (an upper
+// bound; rounds after the last do nothing). Every round merges at least one pair, so at most
+// n - 1 rounds make progress; a round that does not fails the build.
 int ploc_tree(Alloc &A, const float *leaf_aabb, int64_t n, uint32_t *left, uint32_t *right, uint32_t *parent,
               cudaStream_t s, int *iterations)
 {
     float *cb[2];
     uint32_t *id[2], *create, *keep, *lc, *rc, *small;
-    int *nn;
+    int *nn, *st;
     void *scan_tmp;
     TRY(A.get(&cb[0], 6 * (size_t)n, true));
     TRY(A.get(&cb[1], 6 * (size_t)n, true));
@@ -963,34 +999,38 @@ int ploc_tree(Alloc &A, const float *leaf_aabb, int64_t n, uint32_t *left, uint3
     TRY(A.get(&lc, n - 1, true));
     TRY(A.get(&rc, n - 1, true));
     TRY(A.get(&small, 4, true));
+    TRY(A.get(&st, 4, true));
     TRY(A.get((char **)&scan_tmp, grtx_scan_temp_bytes(n), true));
     GRTX_CUDA(cudaMemcpyAsync(cb[0], leaf_aabb, sizeof(float) * 6 * (size_t)n, cudaMemcpyDeviceToDevice, s));
-    k_ploc_init<<<grtx_div_up(n, kThreads), kThreads, 0, s>>>(id[0], (int)n);
-    int64_t m = n, made = 0;
-    int cur = 0, it = 0;
+    k_ploc_init<<<grtx_div_up(n, kThreads), kThreads, 0, s>>>(id[0], (int)n, st);
+    int64_t m = n;                            // clusters left as last read by the host
+    int cur = 0, checks = 0;
+    int h[4] = {(int)n, 0, 0, 0};
     while (m > 1) {
-        if (++it > n) return grtx_fail(GRTX_ERR_OVERFLOW_FATAL, "clustering did not converge");
-        int blocks = grtx_div_up(m, kPlocBlock);
-        k_ploc_nn<<<blocks, kPlocBlock, 0, s>>>(cb[cur], (int)m, nn);
-        k_ploc_flags<<<blocks, kPlocBlock, 0, s>>>(nn, (int)m, create, keep, small);
-        TRY(grtx_scan_exclusive(create, m, scan_tmp, s));
-        TRY(grtx_scan_exclusive(keep, m, scan_tmp, s));
-        k_ploc_totals<<<1, 1, 0, s>>>(create, keep, (int)m, small, small + 2);
-        k_ploc_merge<<<blocks, kPlocBlock, 0, s>>>(cb[cur], id[cur], nn, create, keep, (int)m, (uint32_t)made,
-                                                   cb[cur ^ 1], id[cur ^ 1], lc, rc);
+        if (++checks > n) return grtx_fail(GRTX_ERR_OVERFLOW_FATAL, "clustering did not converge");
+        const int rounds = m > kPlocBatchBelow ? 1 : kPlocBatch;
+        const int blocks = grtx_div_up(m, kPlocBlock);
+        for (int r = 0; r < rounds; ++r) {
+            k_ploc_nn<<<blocks, kPlocBlock, 0, s>>>(cb[cur], st, nn);
+            k_ploc_flags<<<blocks, kPlocBlock, 0, s>>>(nn, st, create, keep, small);
+            TRY(grtx_scan_exclusive(create, m, scan_tmp, s));
+            TRY(grtx_scan_exclusive(keep, m, scan_tmp, s));
+            k_ploc_merge<<<blocks, kPlocBlock, 0, s>>>(cb[cur], id[cur], nn, create, keep, st, cb[cur ^ 1],
+                                                       id[cur ^ 1], lc, rc);
+            k_ploc_advance<<<1, 1, 0, s>>>(create, keep, small, (int)n, st);
+            cur ^= 1;
+        }
         GRTX_CHECK_LAUNCH("clustering");
-        uint32_t tot[2] = {0, 0};
-        GRTX_CUDA(cudaMemcpyAsync(tot, small + 2, sizeof(tot), cudaMemcpyDeviceToHost, s));
+        GRTX_CUDA(cudaMemcpyAsync(h, st, sizeof(h), cudaMemcpyDeviceToHost, s));
         GRTX_CUDA(cudaStreamSynchronize(s));
-        if (tot[0] == 0 || (int64_t)tot[1] != m - (int64_t)tot[0] || made + tot[0] > n - 1)
-            return grtx_fail(GRTX_ERR_OVERFLOW_FATAL, "clustering made no progress");
-        made += tot[0];
-        m = tot[1];
-        cur ^= 1;
+        if (h[kPlocErr]) return grtx_fail(GRTX_ERR_OVERFLOW_FATAL, "clustering made no progress");
+        if ((int64_t)h[kPlocM] >= m) return grtx_fail(GRTX_ERR_OVERFLOW_FATAL, "clustering made no progress");
+        m = h[kPlocM];
     }
+    if (h[kPlocMade] != n - 1) return grtx_fail(GRTX_ERR_OVERFLOW_FATAL, "clustering made a wrong number of nodes");
     k_ploc_finish<<<grtx_div_up(n - 1, kThreads), kThreads, 0, s>>>(lc, rc, (int)n, left, right, parent);
     GRTX_CHECK_LAUNCH("clustering finish");
-    if (iterations) *iterations = it;
+    if (iterations) *iterations = h[kPlocRounds];
     return GRTX_OK;
 }
 
