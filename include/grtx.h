@@ -248,6 +248,13 @@ GRTX_API int grtx_version(void);
 /* Host-side text of the last error detected in this thread (never NULL; "" if none). */
 GRTX_API const char *grtx_last_error(void);
 
+/* The library allocates its device memory (scene arrays, build temporaries, trace
+ * workspaces) stream-ordered from a pool of its own on each device, which keeps freed memory
+ * mapped for the next build or trace. grtx_memory_trim synchronises the current device and
+ * returns the pool's unused memory to the driver beyond keep_bytes (>= 0). Memory of live
+ * scenes, worlds and servers is not affected. */
+GRTX_API int grtx_memory_trim(int64_t keep_bytes);
+
 /* ---------------------------------------------------------------------------------------- */
 /* Building blocks of the BVH build (each also runs inside grtx_build_bvh)                  */
 /* ---------------------------------------------------------------------------------------- */

@@ -926,12 +926,8 @@ struct Alloc {
     int get(T **p, size_t count, bool temp)
     {
         size_t bytes = std::max<size_t>(count * sizeof(T), 16);
-        cudaError_t e = cudaMallocAsync((void **)p, bytes, s);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            *p = nullptr;
-            return grtx_fail(GRTX_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
-        }
+        int st = grtx_malloc_async((void **)p, bytes, s);
+        if (st) return st;
         if (temp) tmp.push_back(*p);
         return GRTX_OK;
     }
@@ -1361,7 +1357,8 @@ static int morton_codes_abi(const float *d_aabb, int64_t n, const float *d_bound
     if (!bounds) {
         float *b = d_bounds_out;
         if (!b) {
-            GRTX_CUDA(cudaMallocAsync((void **)&tmp, 6 * sizeof(float), s));
+            int st = grtx_malloc_async((void **)&tmp, 6 * sizeof(float), s);
+            if (st) return st;
             b = tmp;
         }
         k_init_bounds<<<1, 32, 0, s>>>(b);

@@ -15,6 +15,9 @@
 // Record the host-side text of an error for grtx_last_error() and return the status.
 int grtx_fail(int status, const std::string &msg);
 int grtx_cuda_fail(cudaError_t e, const char *what);
+// Stream-ordered allocation from the library's per-device pool (freed with cudaFreeAsync);
+// GRTX_ERR_OOM with a message on failure, *p = NULL then.
+int grtx_malloc_async(void **p, size_t bytes, cudaStream_t s);
 
 #define GRTX_CUDA(call)                                                  \
     do {                                                                 \

@@ -150,16 +150,12 @@ int ensure_workspace(grtx_scene *sc, int n_slots, size_t entries_per_slot, cudaS
     if (need > sc->ws_bytes) {
         if (sc->ws) {
             GRTX_CUDA(cudaDeviceSynchronize());   // earlier traces on any stream may still use it
-            GRTX_CUDA(cudaFree(sc->ws));
+            GRTX_CUDA(cudaFreeAsync(sc->ws, s));
             sc->ws = nullptr;
             sc->ws_bytes = 0;
         }
-        cudaError_t e = cudaMallocAsync(&sc->ws, need, s);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            sc->ws = nullptr;
-            return grtx_fail(GRTX_ERR_OOM, "trace workspace allocation failed");
-        }
+        int st = grtx_malloc_async(&sc->ws, need, s);
+        if (st) return st;
         sc->ws_bytes = need;
     }
     *base_out = (uint2 *)sc->ws;
@@ -420,10 +416,8 @@ extern "C" GRTX_API int grtx_trace_forward_batch(grtx_scene *sc, const grtx_came
     a.queue = sc->d_counter + 2;
     a.n_items = total;
     ServeSeg *d = nullptr;
-    if (cudaMallocAsync((void **)&d, sizeof(ServeSeg) * n_cams, s) != cudaSuccess) {
-        cudaGetLastError();
-        return grtx_fail(GRTX_ERR_OOM, "segment table allocation failed");
-    }
+    st = grtx_malloc_async((void **)&d, sizeof(ServeSeg) * n_cams, s);
+    if (st) return st;
     GRTX_CUDA(cudaMemcpyAsync(d, h, sizeof(ServeSeg) * n_cams, cudaMemcpyHostToDevice, s));
     GRTX_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned), s));
     int launched = segments_launch_k(p->k, a, d, n_cams, blocks, s);
@@ -482,10 +476,8 @@ int backward(grtx_scene *sc, const grtx_gaussians *g, const grtx_camera *cam, co
     // atomics in the kernel), then added into the caller's arrays
     const bool staged = sc->n_valid > 0 && (grads->means || grads->log_scales || grads->quats || grads->opacity_logits);
     if (staged) {
-        if (cudaMallocAsync((void **)&a.g_stage, (size_t)sc->n_valid * 48, s) != cudaSuccess) {
-            cudaGetLastError();
-            return grtx_fail(GRTX_ERR_OOM, "gradient staging allocation failed");
-        }
+        st = grtx_malloc_async((void **)&a.g_stage, (size_t)sc->n_valid * 48, s);
+        if (st) return st;
         GRTX_CUDA(cudaMemsetAsync(a.g_stage, 0, (size_t)sc->n_valid * 48, s));
     }
     st = run(sc, a, p->k, false, PASS_BWD, sc->d_counter + 1, s);

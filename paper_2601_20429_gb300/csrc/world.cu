@@ -718,17 +718,13 @@ extern "C" GRTX_API int grtx_world_trace_forward(grtx_world *w, const grtx_camer
     size_t need = n_slots * (2 * C * sizeof(uint4) + E * sizeof(uint2));
     if (need > w->ws_bytes) {
         if (w->ws) {
-            GRTX_CUDA(cudaDeviceSynchronize());
-            GRTX_CUDA(cudaFree(w->ws));
+            GRTX_CUDA(cudaDeviceSynchronize());          // earlier traces on any stream may use it
+            GRTX_CUDA(cudaFreeAsync(w->ws, s));
             w->ws = nullptr;
             w->ws_bytes = 0;
         }
-        cudaError_t e = cudaMallocAsync(&w->ws, need, s);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            w->ws = nullptr;
-            return grtx_fail(GRTX_ERR_OOM, "world trace workspace allocation failed");
-        }
+        st = grtx_malloc_async(&w->ws, need, s);
+        if (st) return st;
         w->ws_bytes = need;
     }
     W.wck0 = (uint4 *)w->ws;
@@ -755,8 +751,9 @@ extern "C" GRTX_API void grtx_world_destroy(grtx_world *w)
 {
     if (!w) return;
     world_free_tables(w);
+    if (w->ws) cudaFreeAsync(w->ws, w->stream);
     if (w->stream) cudaStreamSynchronize(w->stream);
-    cudaFree(w->ws);
+    else cudaDeviceSynchronize();
     cudaFree(w->counter);
     delete w;
 }

@@ -162,6 +162,7 @@ _SIGS = {
     "grtx_status_string": (C.c_char_p, [C.c_int]),
     "grtx_version": (C.c_int, []),
     "grtx_last_error": (C.c_char_p, []),
+    "grtx_memory_trim": (C.c_int, [C.c_int64]),
     "grtx_prep_gaussians": (C.c_int, [C.POINTER(grtx_gaussians), C.c_float, _fp, _fp, _fp]),
     "grtx_morton_codes": (C.c_int, [_fp, C.c_int64, _fp, _fp, _fp, _fp]),
     "grtx_morton_codes_sized": (C.c_int, [_fp, C.c_int64, _fp, _fp, _fp, _fp]),
@@ -375,6 +376,11 @@ def grtx_scene_update(scene: int, g: grtx_gaussians, mode: int, stream=None) -> 
     check(lib().grtx_scene_update(C.c_void_p(scene), C.byref(g), int(mode), stream_handle(stream), C.byref(rebuilt)),
           "grtx_scene_update")
     return bool(rebuilt.value)
+
+
+def grtx_memory_trim(keep_bytes: int = 0):
+    """Return the library pool's unused device memory beyond keep_bytes to the driver."""
+    check(lib().grtx_memory_trim(int(keep_bytes)), "grtx_memory_trim")
 
 
 def grtx_scene_info_get(scene: int) -> dict:

@@ -79,6 +79,7 @@ def test_host_side_errors_of_the_extensions(lib):
     assert lib.grtx_world_create(inst, 1, None, C.byref(w)) == 1                        # NULL scene
     assert b"scene is NULL" in lib.grtx_last_error()
     assert lib.grtx_world_update(None, inst, 1, None) == 1
+    assert lib.grtx_memory_trim(-1) == 1                                                 # no device work
     assert lib.grtx_trace_forward_batch(None, None, 1, None, None, None) == 1
     assert lib.grtx_trace_forward_batch(None, N.grtx_camera(), 0, None, (N._fp * 1)(), None) == 1
     rebuilt = C.c_int(5)

@@ -202,3 +202,15 @@ def test_training_steps_with_a_kept_scene_give_the_same_gradients():
         for a, b in zip(res["saved"][1], res["fresh"][1]):
             np.testing.assert_allclose(a, b, rtol=1e-4, atol=1e-7)
     kept.close()
+
+
+def test_memory_trim_between_scenes():
+    """The library's pool keeps freed memory for the next build; trimming hands it back and
+    later builds and traces work as before."""
+    g0 = _base(n=6000)
+    first = _fresh(g0)
+    N.grtx_memory_trim(0)
+    _same(_fresh(g0), first)
+    N.grtx_memory_trim(1 << 30)
+    with pytest.raises(N.GrtxError, match="keep_bytes"):
+        N.grtx_memory_trim(-5)
