@@ -826,3 +826,53 @@ def test_saved_blend_lists_in_autograd_and_errors(dense):
         R.render(sc, cam, k=8, save_cap=8, traversal="single")
     sc.close()
     proxy.close()
+
+
+# ------------------------------------------------------------------ zero sizes and empty windows
+
+
+def test_zero_gaussians_through_every_entry_point():
+    """A scene of no Gaussians: background everywhere through the plain and instrumented
+    forward, saved lists, batched views and both backward paths (zero gradients), and an
+    update of it; a ray list of no rays is an argument error."""
+    g = scenes.tiny_scene(seed=1, n=0)
+    assert g.n == 0
+    cam = scenes.pinhole_camera(12, 9, (0.0, 0.0, -3.0), (0, 0, 0), 60.0)
+    bg = (0.1, 0.2, 0.3)
+    sc = R.Scene.from_params(g)
+    assert sc.info()["n_valid"] == 0 and sc.info()["n_nodes"] == 0
+    want = np.tile([0.1, 0.2, 0.3, 1.0], (cam["width"] * cam["height"], 1)).astype(np.float32)
+    for kw in ({}, {"traversal": "restart"}, {"traversal": "single"}, {"ids_cap": 8, "want_stats": True}):
+        r = R.render(sc, cam, k=4, bg=bg, **kw)
+        np.testing.assert_allclose(r["rgbT"].cpu().numpy(), want, atol=0)
+    r = R.render(sc, cam, k=4, bg=bg, save_cap=4)
+    assert int(r["saved"][1].abs().sum()) == 0
+    np.testing.assert_allclose(R.render_batch(sc, [(cam, None), (cam, None)], k=4, bg=bg)[1].cpu().numpy(), want, atol=0)
+    dl = torch.ones((cam["width"] * cam["height"], 4), device="cuda")
+    for saved in (None, r["saved"]):
+        grads = R.backward(sc, cam, r["rgbT"], dl, k=4, bg=bg, saved=saved)
+        assert all(v.numel() == 0 for v in grads.values())
+    assert sc.update(g.means, g.log_scales, g.quats, g.logits, g.sh) is True    # nothing to refit: rebuilt
+    empty = tuple(torch.empty(s, device="cuda") for s in ((0, 3), (0, 3), (0,), (0,)))
+    with pytest.raises(N.GrtxError, match="camera size"):
+        R.render(sc, None, rays=empty, k=4)
+    sc.close()
+
+
+def test_empty_and_inverted_ray_windows(dense):
+    """Rays whose window (t_near, t_far] is empty or inverted see nothing, on every path."""
+    g, cam, S, rays, ref = dense
+    sc = R.Scene.from_params(g)
+    n = cam["width"] * cam["height"]
+    o, d = torch.empty((n, 3), device="cuda"), torch.empty((n, 3), device="cuda")
+    tn, tf = torch.empty(n, device="cuda"), torch.empty(n, device="cuda")
+    N.grtx_generate_rays(N.make_camera(cam), o, d, tn, tf)
+    tn = torch.full((n,), 3.0, device="cuda")
+    tf = torch.where(torch.arange(n, device="cuda") % 2 == 0, tn, tn - 1.0)   # empty, inverted
+    for kw in ({}, {"traversal": "restart"}, {"traversal": "single"}, {"ids_cap": 8, "want_n_blended": True}):
+        out = R.render(sc, cam, rays=(o, d, tn, tf), k=8, **kw)
+        rgbT = out["rgbT"].cpu().numpy()
+        np.testing.assert_array_equal(rgbT, np.tile([0.0, 0.0, 0.0, 1.0], (n, 1)).astype(np.float32))
+        if "n_blended" in out:
+            assert int(out["n_blended"].sum()) == 0
+    sc.close()
