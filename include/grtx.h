@@ -169,17 +169,21 @@ typedef struct grtx_camera {
  * written; evictions: entries written to the eviction list; fallbacks: rays that exceeded a
  * capacity and restarted from the root; stack_overflow: traversal stack overflows (never
  * expected: the build rejects trees deeper than the stack); collected: hits appended to the
- * single-round lists (GRTX_TRAVERSAL_SINGLE only). */
+ * single-round lists (GRTX_TRAVERSAL_SINGLE only); bounds_errors: node, leaf-record or
+ * Gaussian indices that the traversal met outside the scene's arrays. The kernels that fill
+ * these counters compare each such index with its array's size before the fetch, count one
+ * outside and skip it (never expected: every index comes from the scene's own build). */
 typedef struct grtx_stats {
     unsigned long long rays, nodes, leaves, blended, rounds, ckpt_writes, evictions, fallbacks,
-        stack_overflow, collected;
+        stack_overflow, collected, bounds_errors;
 } grtx_stats;
 
 /* Blend lists a forward trace saves for its backward (grtx_trace_backward_saved): for each
  * ray, the leaf slots it blended, in blend order. leaves: device [n_rays][cap]; n: device
  * [n_rays], the number blended; a count above cap means the list is incomplete, and the
  * backward replays that ray's rounds. Leaf slots index the scene's leaf order: the lists
- * hold while the scene is not updated. Caller-owned device memory. */
+ * hold while the scene is not updated; an entry at or past the scene's number of valid
+ * Gaussians (a list from another scene) is skipped, never read. Caller-owned device memory. */
 typedef struct grtx_saved {
     uint32_t *leaves;
     int32_t *n;

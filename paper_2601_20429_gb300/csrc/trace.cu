@@ -178,7 +178,9 @@ SceneRef grtx_scene_ref(const grtx_scene *sc)
     r.app_stride = sc->app_stride;
     r.sh_degree = sc->sh_degree;
     r.has_tree = sc->n_valid > 0;
-    r.pad = 0;
+    r.n_nodes = (uint32_t)sc->n_nodes;
+    r.n_leaves = (uint32_t)sc->n_leaves;
+    r.n_geom = (uint32_t)sc->n_valid;
     return r;
 }
 

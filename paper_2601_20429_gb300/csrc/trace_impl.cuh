@@ -19,7 +19,8 @@ struct SceneRef {
     const uint32_t *gid;
     const float4 *tpl_nodes, *tpl_tris;   // icosphere forms: shared template BVH and triangles
     const float4 *raw;                    // [n_valid][3] raw parameters in leaf order (backward)
-    int app_stride, sh_degree, has_tree, pad;
+    int app_stride, sh_degree, has_tree;
+    uint32_t n_nodes, n_leaves, n_geom;   // internal nodes, leaf records, Gaussian records
 };
 
 // Leaf kinds of the trace kernels: one analytic unit sphere per Gaussian; one world-space
@@ -82,6 +83,7 @@ struct ServeSeg {
 
 struct Counters {
     unsigned nodes, leaves, blended, rounds, ckpt, evictions, fallbacks, overflow;
+    unsigned oob;      // fetch indices found outside their arrays (instrumented path only)
     uint32_t *vlog;    // the current ray's row of the visit log, or NULL (instrumented path only)
     unsigned vn, vcap;
 };
@@ -93,6 +95,25 @@ __device__ __forceinline__ void log_visit(Counters &c, uint32_t ref)
         if (c.vn < c.vcap) c.vlog[c.vn] = ref;
         ++c.vn;
     }
+}
+
+// Self-check of the instrumented kernels (the ones that fill grtx_stats): before a node or
+// leaf record is fetched its index is compared with the size of its array, and so is the
+// Gaussian index a proxy triangle names. An index outside is counted (grtx_stats.bounds_errors)
+// and not fetched; the traversal treats it as a miss. Every parity render runs these kernels,
+// so every parity case is also a check that the traversal never leaves the scene's arrays.
+__device__ __forceinline__ bool ref_ok(const SceneRef &sc, uint32_t ref, Counters &c, bool count = true)
+{
+    bool ok = (ref & GRTX_LEAF) ? (ref & ~GRTX_LEAF) < sc.n_leaves : ref < sc.n_nodes;
+    if (!ok && count) ++c.oob;
+    return ok;
+}
+
+__device__ __forceinline__ bool gauss_ok(const SceneRef &sc, uint32_t gi, Counters &c)
+{
+    if (gi < sc.n_geom) return true;
+    ++c.oob;
+    return false;
 }
 
 #define GRTX_INF __int_as_float(0x7f800000)
@@ -509,6 +530,7 @@ __device__ __forceinline__ bool trace_round(const TraceArgs &a, const SceneRef &
                 ++n_dst;
                 if (INSTR) cnt.ckpt++;
             }
+        } else if (INSTR && !ref_ok(sc, ref, cnt)) {  // not fetched (self-check)
         } else if (ref & GRTX_LEAF) {
             uint32_t idx = ref & ~GRTX_LEAF;
             if (INSTR) {
@@ -521,7 +543,7 @@ __device__ __forceinline__ bool trace_round(const TraceArgs &a, const SceneRef &
                 const float4 *tr = sc.tris + 3 * (size_t)idx;
                 float4 v0 = __ldg(tr), v1 = __ldg(tr + 1), v2 = __ldg(tr + 2);
                 gi = __float_as_uint(v0.w);
-                touch = tri_hit(v0, v1, v2, o, d) > tn;
+                touch = (!INSTR || gauss_ok(sc, gi, cnt)) && tri_hit(v0, v1, v2, o, d) > tn;
             } else {
                 gi = idx;
                 if (FORM == FORM_ICO) touch = template_touch<INSTR>(sc, gi, o, d, tn, cnt);
@@ -667,7 +689,7 @@ __device__ __forceinline__ bool packet_round(const TraceArgs &a, const SceneRef 
         }
         m = __ballot_sync(full, go);
         bool pop = true;
-        if (m) {
+        if (m && (!INSTR || ref_ok(sc, ref, cnt, go))) {   // ref is the warp's: all lanes agree
             if (ref & GRTX_LEAF) {
                 if (go) {
                     uint32_t idx = ref & ~GRTX_LEAF;
@@ -681,7 +703,7 @@ __device__ __forceinline__ bool packet_round(const TraceArgs &a, const SceneRef 
                         const float4 *tr = sc.tris + 3 * (size_t)idx;
                         float4 v0 = __ldg(tr), v1 = __ldg(tr + 1), v2 = __ldg(tr + 2);
                         gi = __float_as_uint(v0.w);
-                        touch = tri_hit(v0, v1, v2, o, d) > tn;
+                        touch = (!INSTR || gauss_ok(sc, gi, cnt)) && tri_hit(v0, v1, v2, o, d) > tn;
                     } else {
                         gi = idx;
                         if (FORM == FORM_ICO) touch = template_touch<INSTR>(sc, gi, o, d, tn, cnt);
@@ -1024,7 +1046,10 @@ __device__ __forceinline__ void backward_from_list(const TraceArgs &a, const Sce
     st.Cf[2] = F.z - F.w * a.bg2;
     st.dLdT = G.w + a.bg0 * G.x + a.bg1 * G.y + a.bg2 * G.z;
     const uint32_t *list = a.save_leaves + (size_t)pix * a.save_cap;
-    for (int j = 0; j < n; ++j) blend_one<true>(a, sc, st, list[j], o, d, dn);
+    for (int j = 0; j < n; ++j) {
+        uint32_t idx = list[j];
+        if (idx < sc.n_geom) blend_one<true>(a, sc, st, idx, o, d, dn);   // never read outside the scene
+    }
 }
 
 // The rays of one warp with restart traversal (Sec. III-A): every round from the root as the
@@ -1146,7 +1171,7 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, PASS == PASS_BWD))
     KBuf<K> kb;
     kb.t = s_kt + threadIdx.x;
     kb.id = s_ki + threadIdx.x;
-    Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0, nullptr, 0, 0};
+    Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr, 0, 0};
     unsigned rays = 0;
     for (;;) {
         unsigned base = 0;
@@ -1169,10 +1194,10 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, PASS == PASS_BWD))
         __syncwarp();
     }
     if (INSTR && a.stats) {
-        unsigned long long v[9] = {rays, cnt.nodes, cnt.leaves, cnt.blended, cnt.rounds, cnt.ckpt, cnt.evictions,
-                                   cnt.fallbacks, cnt.overflow};
+        unsigned long long v[11] = {rays, cnt.nodes, cnt.leaves, cnt.blended, cnt.rounds, cnt.ckpt, cnt.evictions,
+                                    cnt.fallbacks, cnt.overflow, 0ull, cnt.oob};
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {
+        for (int q = 0; q < 11; ++q) {
             unsigned long long x = v[q];
             for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
             if (lane == 0 && x) atomicAdd((&a.stats->rays) + q, x);
@@ -1193,7 +1218,7 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, false)) k_serve(Tr
     KBuf<K> kb;
     kb.t = s_kt + threadIdx.x;
     kb.id = s_ki + threadIdx.x;
-    Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0, nullptr, 0, 0};
+    Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr, 0, 0};
     for (;;) {
         unsigned base = 0;
         if (lane == 0) base = atomicAdd(a.queue, 32u);

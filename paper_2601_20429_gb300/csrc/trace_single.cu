@@ -71,7 +71,7 @@ __device__ __forceinline__ int packet_collect(const TraceArgs &a, const SceneRef
     unsigned m = __ballot_sync(full, valid);
     for (;;) {
         bool go = ((m >> lane) & 1u) && ok;
-        if (__ballot_sync(full, go)) {
+        if (__ballot_sync(full, go) && (!INSTR || ref_ok(sc, ref, cnt, go))) {   // ref is the warp's
             if (ref & GRTX_LEAF) {
                 if (go) {
                     uint32_t idx = ref & ~GRTX_LEAF;
@@ -85,7 +85,7 @@ __device__ __forceinline__ int packet_collect(const TraceArgs &a, const SceneRef
                         const float4 *tr = sc.tris + 3 * (size_t)idx;
                         float4 v0 = __ldg(tr), v1 = __ldg(tr + 1), v2 = __ldg(tr + 2);
                         gi = __float_as_uint(v0.w);
-                        touch = tri_hit(v0, v1, v2, o, d) > tn;
+                        touch = (!INSTR || gauss_ok(sc, gi, cnt)) && tri_hit(v0, v1, v2, o, d) > tn;
                     } else {
                         gi = idx;
                         if (FORM == FORM_ICO) touch = template_touch<INSTR>(sc, gi, o, d, tn, cnt);
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(kBlock, 8) k_trace_single(TraceArgs a)
     KBuf<kFallbackK> kb;
     kb.t = s_kt + threadIdx.x;
     kb.id = s_ki + threadIdx.x;
-    Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0, nullptr, 0, 0};
+    Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr, 0, 0};
     unsigned rays = 0, collected = 0;
     for (;;) {
         unsigned base = 0;
@@ -230,10 +230,10 @@ __global__ void __launch_bounds__(kBlock, 8) k_trace_single(TraceArgs a)
         __syncwarp();
     }
     if (INSTR && a.stats) {
-        unsigned long long v[10] = {rays, cnt.nodes, cnt.leaves, cnt.blended, cnt.rounds, cnt.ckpt, cnt.evictions,
-                                    cnt.fallbacks, cnt.overflow, collected};
+        unsigned long long v[11] = {rays, cnt.nodes, cnt.leaves, cnt.blended, cnt.rounds, cnt.ckpt, cnt.evictions,
+                                    cnt.fallbacks, cnt.overflow, collected, cnt.oob};
 #pragma unroll
-        for (int q = 0; q < 10; ++q) {
+        for (int q = 0; q < 11; ++q) {
             unsigned long long x = v[q];
             for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
             if (lane == 0 && x) atomicAdd((&a.stats->rays) + q, x);

@@ -38,9 +38,19 @@ struct WorldArgs {
     const float4 *tl_nodes;   // scene-level BVH, leaf ref = row of inst
     const InstRec *inst;      // non-empty instances
     const uint32_t *leaf_base;// inst[i].leaf_base, ascending
-    int n_inst;
+    int n_inst, n_tl_nodes;
     uint4 *wck0, *wck1;       // checkpoint lists of (ref, t bits, instance, 0), [entry][slot]
 };
+
+// The self-check of the instrumented kernels (see ref_ok) at either level of the world.
+__device__ __forceinline__ bool world_ref_ok(const WorldArgs &W, uint32_t inst, uint32_t ref, Counters &c,
+                                             bool count = true)
+{
+    if (inst != GRTX_NONE) return ref_ok(W.inst[inst].sc, ref, c, count);
+    bool ok = (ref & GRTX_LEAF) ? (ref & ~GRTX_LEAF) < (uint32_t)W.n_inst : ref < (uint32_t)W.n_tl_nodes;
+    if (!ok && count) ++c.oob;
+    return ok;
+}
 
 __device__ __forceinline__ void to_object(const InstRec &I, float3 o, float3 d, float3 &oo, float3 &od)
 {
@@ -119,6 +129,7 @@ __device__ __forceinline__ bool world_round(const WorldArgs &W, float3 o, float3
                 ++n_dst;
                 if (INSTR) cnt.ckpt++;
             }
+        } else if (INSTR && !world_ref_ok(W, inst, ref, cnt)) {   // not fetched (self-check)
         } else if (ref & GRTX_LEAF) {
             if (inst == GRTX_NONE) {                  // TLAS leaf: descend into the object's root
                 inst = ref & ~GRTX_LEAF;
@@ -265,7 +276,7 @@ __device__ __forceinline__ void world_packet_round(const WorldArgs &W, bool vali
         }
         m = __ballot_sync(full, go);
         bool pop = true;
-        if (m) {
+        if (m && (!INSTR || world_ref_ok(W, inst, ref, cnt, go))) {   // ref is the warp's
             if (ref & GRTX_LEAF) {
                 if (inst == GRTX_NONE) {                    // TLAS leaf: descend into the object's root
                     inst = ref & ~GRTX_LEAF;
@@ -455,7 +466,7 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, false)) k_trace_wo
     KBuf<K> kb;
     kb.t = s_kt + threadIdx.x;
     kb.id = s_ki + threadIdx.x;
-    Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0, nullptr, 0, 0};
+    Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr, 0, 0};
     unsigned rays = 0;
     for (;;) {
         unsigned b = 0;
@@ -486,10 +497,10 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, false)) k_trace_wo
         __syncwarp();
     }
     if (INSTR && W.a.stats) {
-        unsigned long long v[9] = {rays, cnt.nodes, cnt.leaves, cnt.blended, cnt.rounds, cnt.ckpt, cnt.evictions,
-                                   cnt.fallbacks, cnt.overflow};
+        unsigned long long v[11] = {rays, cnt.nodes, cnt.leaves, cnt.blended, cnt.rounds, cnt.ckpt, cnt.evictions,
+                                    cnt.fallbacks, cnt.overflow, 0ull, cnt.oob};
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {
+        for (int q = 0; q < 11; ++q) {
             unsigned long long x = v[q];
             for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
             if (lane == 0 && x) atomicAdd((&W.a.stats->rays) + q, x);
@@ -518,6 +529,7 @@ int world_occupancy(bool instr, int *bps)
 struct grtx_world {
     float alpha_min = 0.f;
     int n_inst = 0;            // non-empty instances (rows of the table and TLAS leaves)
+    int n_tl_nodes = 0;
     int tl_depth = 0;
     float4 *tl_nodes = nullptr;
     InstRec *inst = nullptr;
@@ -540,6 +552,7 @@ void world_free_tables(grtx_world *w)
     w->inst = nullptr;
     w->leaf_base = nullptr;
     w->n_inst = 0;
+    w->n_tl_nodes = 0;
 }
 
 int world_set(grtx_world *w, const grtx_instance *inst, int n, cudaStream_t s)
@@ -629,6 +642,7 @@ int world_set(grtx_world *w, const grtx_instance *inst, int n, cudaStream_t s)
         return grtx_cuda_fail(e, "world table upload");
     }
     w->n_inst = (int)rows.size();
+    w->n_tl_nodes = (int)nodes.size();
     return GRTX_OK;
 }
 
@@ -736,6 +750,7 @@ extern "C" GRTX_API int grtx_world_trace_forward(grtx_world *w, const grtx_camer
     W.inst = w->inst;
     W.leaf_base = w->leaf_base;
     W.n_inst = w->n_inst;
+    W.n_tl_nodes = w->n_tl_nodes;
     w->stream = s;
     GRTX_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned), s));
     int launched = p->k == 8 ? world_launch<8>(W, instr, blocks, s)

@@ -111,7 +111,8 @@ class grtx_camera(C.Structure):
 
 class grtx_stats(C.Structure):
     _fields_ = [(n, C.c_ulonglong) for n in ("rays", "nodes", "leaves", "blended", "rounds", "ckpt_writes",
-                                             "evictions", "fallbacks", "stack_overflow", "collected")]
+                                             "evictions", "fallbacks", "stack_overflow", "collected",
+                                             "bounds_errors")]
 
 
 class grtx_saved(C.Structure):
@@ -556,7 +557,7 @@ STATS_FIELDS = tuple(n for n, _ in grtx_stats._fields_)
 
 def stats_tensor(device="cuda"):
     import torch
-    return torch.zeros(10, dtype=torch.int64, device=device)
+    return torch.zeros(len(STATS_FIELDS), dtype=torch.int64, device=device)
 
 
 def stats_dict(t) -> dict:

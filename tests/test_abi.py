@@ -98,3 +98,37 @@ def test_host_side_errors_of_the_extensions(lib):
     p = N.make_params(bvh_builder=7)
     g = N.grtx_gaussians()
     assert lib.grtx_build_bvh(C.byref(g), C.byref(p), 0, None, C.byref(C.c_void_p())) == 1
+
+
+def header_structs():
+    """Field names of every `typedef struct name { ... } name;` in the header, in order."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    out = {}
+    for name, body in re.findall(r"typedef\s+struct\s+(\w+)\s*\{(.*?)\}\s*\1\s*;", src, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            first, *more = decl.split(",")
+            fields.append(re.findall(r"(\w+)\s*(?:\[[^\]]*\])?\s*$", first)[0])
+            fields += [re.findall(r"(\w+)", m)[0] for m in more]
+        out[name] = fields
+    return out
+
+
+def test_binding_structs_match_the_header():
+    """The binding's ctypes mirrors name the header's fields in the header's order (a field
+    added on one side only would shift every later one)."""
+    structs = header_structs()
+    assert {"grtx_stats", "grtx_params", "grtx_trace_outputs", "grtx_saved"} <= set(structs)
+    checked = 0
+    for name, fields in structs.items():
+        mirror = getattr(N, name, None)
+        if mirror is None:
+            continue
+        assert [f for f, *_ in mirror._fields_] == fields, name
+        checked += 1
+    assert checked >= 6
+    assert N.STATS_FIELDS[-1] == "bounds_errors"

@@ -250,6 +250,7 @@ def _gpu_render(g, cam, form="sphere", rays=None, **kw):
     torch.cuda.synchronize()
     res = {k: v.cpu().numpy() for k, v in out.items()}
     res["stats"] = N.stats_dict(out["stats"])
+    assert res["stats"]["bounds_errors"] == 0         # the kernels' own index checks
     sc.close()
     return res
 

@@ -43,6 +43,7 @@ def _image(sc, k=16, **kw):
     torch.cuda.synchronize()
     res = {key: v.cpu().numpy() for key, v in r.items()}
     res["stats"] = N.stats_dict(r["stats"])
+    assert res["stats"]["bounds_errors"] == 0         # the kernels' own index checks
     return res
 
 

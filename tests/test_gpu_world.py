@@ -85,6 +85,7 @@ def _gpu_world(world, cam, **kw):
     torch.cuda.synchronize()
     res = {k: v.cpu().numpy() for k, v in out.items()}
     res["stats"] = N.stats_dict(out["stats"])
+    assert res["stats"]["bounds_errors"] == 0         # the kernels' own index checks
     return res
 
 
