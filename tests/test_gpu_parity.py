@@ -829,6 +829,38 @@ def test_saved_blend_lists_in_autograd_and_errors(dense):
     proxy.close()
 
 
+def test_saved_list_entries_outside_the_scene_are_skipped(dense):
+    """Blend lists are caller memory: an entry at or past the scene's number of valid
+    Gaussians (here n_valid itself, 2^31 - 1 and 0xFFFFFFFF, as from a larger scene) is
+    skipped by the backward, never read, so the gradients equal those of the same lists with
+    those entries removed."""
+    g, cam, S, rays, ref = dense
+    g = g.subset(np.arange(4000))
+    sc = R.Scene.from_params(g)
+    nv = sc.info()["n_valid"]
+    res = R.render(sc, cam, k=8, save_cap=128)
+    leaves, n = (t.clone() for t in res["saved"])
+    lv, nn = leaves.cpu().numpy(), n.cpu().numpy()
+    rows = np.nonzero((nn >= 3) & (nn <= 128))[0][::3]
+    assert len(rows) > 20
+    bad_lv, cut_lv, cut_n = lv.copy(), lv.copy(), nn.copy()
+    for q, r in enumerate(rows):
+        j = q % 3                                              # first, second or third entry
+        bad_lv[r, j] = (nv, 0x7FFFFFFF, -1)[q % 3]             # -1 is 0xFFFFFFFF as uint32
+        cut_lv[r, j:-1] = lv[r, j + 1:]
+        cut_n[r] -= 1
+    w = torch.from_numpy(np.random.default_rng(9).normal(0, 1, (cam["width"] * cam["height"], 4))
+                         .astype(np.float32)).cuda()
+    got = {}
+    for name, (a, b) in (("bad", (bad_lv, nn)), ("cut", (cut_lv, cut_n))):
+        saved = (torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda())
+        got[name] = {key: v.cpu().numpy() for key, v in
+                     R.backward(sc, cam, res["rgbT"], w, k=8, saved=saved).items()}
+    for key in got["cut"]:
+        np.testing.assert_allclose(got["bad"][key], got["cut"][key], rtol=1e-5, atol=1e-7)
+    sc.close()
+
+
 # ------------------------------------------------------------------ zero sizes and empty windows
 
 
