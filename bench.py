@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-extra", action="store_true", help="skip the differentiable and outdoor measurements")
-    ap.add_argument("--section", choices=["differentiable", "outdoor"], default=None,
+    ap.add_argument("--section", choices=["differentiable", "outdoor", "serving"], default=None,
                     help="run one measurement section alone and print its JSON (for profiling; 1 GPU)")
     return ap.parse_args()
 
@@ -368,7 +368,8 @@ def bench_serving(n_requests: int, max_rays_per_step: int = 4 << 20, max_infligh
     srv = Server(gpu_scenes, k=cfg["k"], traversal=traversal, max_rays_per_step=max_rays_per_step,
                  max_inflight=max_inflight)
     max_px = 1920 * 1080
-    pool = deque(torch.empty((max_px, 4), dtype=torch.float32, device="cuda") for _ in range(80))
+    n_buffers = min(80, max(16, n_requests // 4))          # output buffers in flight
+    pool = deque(torch.empty((max_px, 4), dtype=torch.float32, device="cuda") for _ in range(n_buffers))
     # warm-up: a few requests of each size
     warm = [(j % 4, reqs[j]["camera"], pool[j], 10 ** 9 + j) for j in range(8)]
     srv.render_requests(warm)
@@ -620,6 +621,8 @@ def main():
         stream = torch.cuda.current_stream()
         if args.section == "differentiable":
             res = bench_differentiable(args.steps, args.warmup, stream)
+        elif args.section == "serving":
+            res = bench_serving(args.serve_requests)
         else:
             flush_buf = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
             res = bench_outdoor(args.steps, stream, lambda: flush_buf.fill_(1))

@@ -638,8 +638,12 @@ typedef struct grtx_completion {
 /* Create a server over n_scenes built scenes (not owned; they must outlive the server).
  * max_rays_per_step: rays per persistent launch (0: 4M); max_inflight: requests admitted at
  * once (0: 64); p: tracing parameters for every request (checkpoint or restart traversal;
- * GRTX_TRAVERSAL_SINGLE is rejected with GRTX_ERR_INVALID_ARG). Host call; allocates a step table
- * in device memory on `stream`, which all later server work uses. */
+ * GRTX_TRAVERSAL_SINGLE is rejected with GRTX_ERR_INVALID_ARG). Host call; waits for the
+ * device once (the scenes' builds), then allocates 4 step slots, each with its own stream
+ * (slot 0 uses `stream`, the others streams the server creates) and its own
+ * checkpoint/eviction lists, so that a step's launch fills the SMs its predecessors' last
+ * warps leave. A request's output is complete when its completion is reported (steps are
+ * reported in the order they were enqueued). */
 GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scenes, const grtx_params *p,
                                 int64_t max_rays_per_step, int max_inflight, void *stream,
                                 grtx_server **out);
@@ -649,7 +653,7 @@ GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scenes, const g
 GRTX_API int grtx_server_submit(grtx_server *srv, const grtx_request *reqs, int n);
 
 /* Advance the server: admit pending requests into free slots (continuous batching), enqueue
- * one step if there is work and fewer than 2 steps are in flight, and report requests whose
+ * steps while there is work and fewer than 4 steps are in flight, and report requests whose
  * last step has completed. Writes at most max_done completions to done (host) and their
  * count to *n_done. Non-blocking unless wait != 0, in which case it blocks until at least one
  * request completes or nothing is in flight. */

@@ -31,7 +31,8 @@ int grtx_check_params(const grtx_params *p);
 namespace {
 
 constexpr int kMaxPending = 65536;
-constexpr int kSteps = 2;
+constexpr int kSteps = 4;         // step slots (streams) in flight
+constexpr int kQueueStride = 32;   // the slots' queue counters on separate 128-byte lines
 
 double now_s()
 {
@@ -72,8 +73,13 @@ struct SrvReq {
     double t_admit = 0;
 };
 
+// A step slot: each has its own stream, per-slot lists and queue counter, so that the next
+// step's blocks take the SMs the previous step's blocks leave while its slowest warps finish.
 struct SrvStep {
     cudaEvent_t ev = nullptr;
+    cudaStream_t s = nullptr;  // slot 0: the server's stream; the others: created by the server
+    bool own_stream = false;
+    void *ws = nullptr;        // checkpoint and eviction lists of this slot's launches
     ServeSeg *h = nullptr;     // pinned host copy of the segment table
     ServeSeg *d = nullptr;     // device segment table
     std::vector<SrvReq *> finishing;
@@ -95,21 +101,22 @@ struct grtx_server {
     std::deque<grtx_completion> backlog;
     TraceArgs a;
     int blocks = 0;
-    void *ws = nullptr;
-    unsigned *queue = nullptr;
+    unsigned *queue = nullptr;  // one ray-queue counter per step slot
 };
 
 namespace {
 
 void server_free(grtx_server *v)
 {
-    if (v->s) cudaStreamSynchronize(v->s);
+    for (auto &st : v->steps)
+        if (st.ev) cudaStreamSynchronize(st.s);
     for (auto &st : v->steps) {
         if (st.ev) cudaEventDestroy(st.ev);
         if (st.h) cudaFreeHost(st.h);
         if (st.d) cudaFree(st.d);
+        if (st.ws) cudaFree(st.ws);
+        if (st.own_stream) cudaStreamDestroy(st.s);
     }
-    if (v->ws) cudaFree(v->ws);
     if (v->queue) cudaFree(v->queue);
     for (auto *r : v->pending) delete r;
     for (auto *r : v->active) delete r;
@@ -142,15 +149,20 @@ int schedule_step(grtx_server *v, int si)
         if (r->next >= r->n_items) st.finishing.push_back(r);
     }
     if (n == 0) return GRTX_OK;
-    GRTX_CUDA(cudaMemcpyAsync(st.d, st.h, sizeof(ServeSeg) * n, cudaMemcpyHostToDevice, v->s));
-    GRTX_CUDA(cudaMemsetAsync(v->queue, 0, sizeof(unsigned), v->s));
     TraceArgs a = v->a;
+    const size_t S = (size_t)a.n_slots;
+    a.ck0 = (uint2 *)st.ws;
+    a.ck1 = a.ck0 + S * a.ckpt_cap;
+    a.ev = a.ck0 + S * 2 * a.ckpt_cap;
+    a.queue = v->queue + kQueueStride * si;
     a.n_items = total;
-    if (serve_launch_k(v->p.k, a, st.d, n, v->blocks, v->s) != GRTX_OK) {
+    GRTX_CUDA(cudaMemcpyAsync(st.d, st.h, sizeof(ServeSeg) * n, cudaMemcpyHostToDevice, st.s));
+    GRTX_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned), st.s));
+    if (serve_launch_k(v->p.k, a, st.d, n, v->blocks, st.s) != GRTX_OK) {
         cudaError_t e = cudaGetLastError();
         return grtx_cuda_fail(e == cudaSuccess ? cudaErrorLaunchFailure : e, "serve step launch");
     }
-    GRTX_CUDA(cudaEventRecord(st.ev, v->s));
+    GRTX_CUDA(cudaEventRecord(st.ev, st.s));
     st.busy = true;
     v->inflight.push_back(si);
     return GRTX_OK;
@@ -209,24 +221,29 @@ extern "C" GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scen
     v->blocks = sms * bps;
     int n_slots = v->blocks * 128;
     size_t ws = (size_t)n_slots * (2 * (size_t)a.ckpt_cap + (size_t)a.evict_cap) * sizeof(uint2);
-    cudaError_t e = cudaMalloc(&v->ws, ws);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&v->queue, 4 * sizeof(unsigned));
+    // earlier work on any stream (the scenes' builds) completes before steps run on the
+    // server's own streams
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMalloc((void **)&v->queue, kSteps * kQueueStride * sizeof(unsigned));
     for (int i = 0; i < kSteps && e == cudaSuccess; ++i) {
-        e = cudaEventCreateWithFlags(&v->steps[i].ev, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaMallocHost((void **)&v->steps[i].h, sizeof(ServeSeg) * v->max_inflight);
-        if (e == cudaSuccess) e = cudaMalloc((void **)&v->steps[i].d, sizeof(ServeSeg) * v->max_inflight);
+        SrvStep &st = v->steps[i];
+        if (i == 0) {
+            st.s = v->s;
+        } else {
+            e = cudaStreamCreateWithFlags(&st.s, cudaStreamNonBlocking);
+            st.own_stream = e == cudaSuccess;
+        }
+        if (e == cudaSuccess) e = cudaMalloc(&st.ws, ws);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st.ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&st.h, sizeof(ServeSeg) * v->max_inflight);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&st.d, sizeof(ServeSeg) * v->max_inflight);
     }
     if (e != cudaSuccess) {
         cudaGetLastError();
         server_free(v);
         return grtx_fail(GRTX_ERR_OOM, "server allocation failed");
     }
-    uint2 *base = (uint2 *)v->ws;
-    a.ck0 = base;
-    a.ck1 = base + (size_t)n_slots * a.ckpt_cap;
-    a.ev = base + (size_t)n_slots * 2 * a.ckpt_cap;
     a.n_slots = n_slots;
-    a.queue = v->queue;
     *out = v;
     return GRTX_OK;
 }
@@ -297,7 +314,7 @@ extern "C" GRTX_API int grtx_server_poll(grtx_server *v, grtx_completion *done, 
             r->t_admit = now_s();
             v->active.push_back(r);
         }
-        // keep up to two steps enqueued
+        // keep up to kSteps steps enqueued, one per slot
         while ((int)v->inflight.size() < kSteps && has_unscheduled(v)) {
             int si = -1;
             for (int i = 0; i < kSteps; ++i)
