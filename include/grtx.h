@@ -642,8 +642,10 @@ typedef struct grtx_completion {
  * device once (the scenes' builds), then allocates 4 step slots, each with its own stream
  * (slot 0 uses `stream`, the others streams the server creates) and its own
  * checkpoint/eviction lists, so that a step's launch fills the SMs its predecessors' last
- * warps leave. A request's output is complete when its completion is reported (steps are
- * reported in the order they were enqueued). */
+ * warps leave. Each slot's lists take (resident ray slots) x (2 ckpt_capacity +
+ * evict_capacity) x 8 bytes: about 0.8 GB with the default capacities on 152 SMs; an
+ * allocation that fails returns GRTX_ERR_OOM. A request's output is complete when its
+ * completion is reported (steps are reported in the order they were enqueued). */
 GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scenes, const grtx_params *p,
                                 int64_t max_rays_per_step, int max_inflight, void *stream,
                                 grtx_server **out);
