@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-extra", action="store_true", help="skip the differentiable and outdoor measurements")
-    ap.add_argument("--section", choices=["differentiable", "outdoor", "serving"], default=None,
+    ap.add_argument("--section", choices=["differentiable", "outdoor", "outdoor-primary", "serving"], default=None,
                     help="run one measurement section alone and print its JSON (for profiling; 1 GPU)")
     return ap.parse_args()
 
@@ -537,11 +537,12 @@ def bench_world(steps: int, stream, flush):
     return res
 
 
-def bench_outdoor(steps: int, stream, flush):
+def bench_outdoor(steps: int, stream, flush, primary_only: bool = False):
     """6M-Gaussian outdoor scene, 1920x1080 fisheye plus one bounce off a mirror or through a
     glass ball: primary and secondary rays timed separately (explicit ray lists; the primary
     list is the camera's image of rays, traced in pixel tiles), and the whole frame as one
-    batched launch, k = 16."""
+    batched launch, k = 16. primary_only: the one scene and its primary frames alone (a
+    smaller device footprint, for profiling)."""
     import torch
     from paper_2601_20429_gb300 import native as N
     from paper_2601_20429_gb300 import render as R
@@ -551,8 +552,8 @@ def bench_outdoor(steps: int, stream, flush):
     sc = R.Scene.from_params(g)
     torch.cuda.synchronize()
     build_ms = (time.perf_counter() - t0) * 1e3
-    sc_c = R.Scene.from_params(g, bvh_codes="centroid", bvh_builder="lbvh")
-    sc_l = R.Scene.from_params(g, bvh_builder="lbvh")
+    sc_c = None if primary_only else R.Scene.from_params(g, bvh_codes="centroid", bvh_builder="lbvh")
+    sc_l = None if primary_only else R.Scene.from_params(g, bvh_builder="lbvh")
     del g
     n = cam["width"] * cam["height"]
     prim = [torch.empty((n, 3), device="cuda"), torch.empty((n, 3), device="cuda"), torch.empty(n, device="cuda"),
@@ -568,6 +569,14 @@ def bench_outdoor(steps: int, stream, flush):
     out_p = torch.empty((n, 4), device="cuda")
     out_s = torch.empty((max(m, 1), 4), device="cuda")
     tp = time_frames(lambda: R.render(sc, cam, rays=prim, k=cfg["k"], out=out_p), steps, 2, flush, stream)
+    if primary_only:
+        st_p = N.stats_dict(R.render(sc, cam, rays=prim, k=cfg["k"], want_stats=True)["stats"])
+        depth = sc.info()["depth"]
+        sc.close()
+        return {"workload": "6M outdoor Gaussians, 1920x1080 equidistant fisheye primary rays, k=16",
+                "build_ms": build_ms, "depth": depth,
+                "primary": {"Mrays_per_s": n / (statistics.mean(tp) / 1e3) / 1e6, "ms": statistics.mean(tp),
+                            "nodes_per_ray": nodes_per_ray(st_p)}}
     tp32 = time_frames(lambda: R.render(sc, cam, rays=prim, k=32, out=out_p), steps, 2, flush, stream)
     st_p32 = N.stats_dict(R.render(sc, cam, rays=prim, k=32, want_stats=True)["stats"])
     ts = time_frames(lambda: R.render(sc, None, rays=sec_rays, k=cfg["k"], out=out_s), steps, 2, flush, stream)
@@ -625,7 +634,8 @@ def main():
             res = bench_serving(args.serve_requests)
         else:
             flush_buf = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
-            res = bench_outdoor(args.steps, stream, lambda: flush_buf.fill_(1))
+            res = bench_outdoor(args.steps, stream, lambda: flush_buf.fill_(1),
+                                primary_only=args.section == "outdoor-primary")
         if dist.rank == 0:
             print(json.dumps({"section": args.section, **res}))
         dist.close()

@@ -37,7 +37,7 @@ extern "C" {
 #define GRTX_VERSION 1
 #define GRTX_DEFAULT_CKPT_CAPACITY 256
 #define GRTX_DEFAULT_SINGLE_CAPACITY 2048
-#define GRTX_DEFAULT_EVICT_CAPACITY 128
+#define GRTX_DEFAULT_EVICT_CAPACITY 512
 
 /* ---------------------------------------------------------------------------------------- */
 /* Status codes                                                                             */
@@ -102,7 +102,11 @@ enum { GRTX_TRAVERSAL_CHECKPOINT = 0, /* resume from checkpointed nodes + evicti
  * on alpha before compositing (0.99). bg: background colour added as T * bg.
  * ckpt_capacity / evict_capacity: checkpoint and eviction entries per resident ray slot
  * (Sec. IV-B "Checkpoint and Eviction Buffer"); 0 selects GRTX_DEFAULT_CKPT_CAPACITY (256)
- * and GRTX_DEFAULT_EVICT_CAPACITY (128). With GRTX_TRAVERSAL_SINGLE, ckpt_capacity is the
+ * and GRTX_DEFAULT_EVICT_CAPACITY (512). A ray whose list overflows redoes that round from
+ * the root and restarts from then on (exact; counted in fallbacks); on deep scenes such rays
+ * hold their launch long after the others finish, so the defaults leave room for the deep
+ * views of the configurations (a 6M-Gaussian outdoor frame had 24,610 such rays with 128
+ * eviction entries, none with 512). With GRTX_TRAVERSAL_SINGLE, ckpt_capacity is the
  * number of hits a ray slot's list holds (0 selects GRTX_DEFAULT_SINGLE_CAPACITY, 2048, the
  * top of the paper's 512-2048); a ray with more hits is traced with k-buffer rounds
  * restarted from the root instead (same result, counted in fallbacks), and k must still be
@@ -643,7 +647,7 @@ typedef struct grtx_completion {
  * (slot 0 uses `stream`, the others streams the server creates) and its own
  * checkpoint/eviction lists, so that a step's launch fills the SMs its predecessors' last
  * warps leave. Each slot's lists take (resident ray slots) x (2 ckpt_capacity +
- * evict_capacity) x 8 bytes: about 0.8 GB with the default capacities on 152 SMs; an
+ * evict_capacity) x 8 bytes: about 1.3 GB with the default capacities on 152 SMs; an
  * allocation that fails returns GRTX_ERR_OOM. A request's output is complete when its
  * completion is reported (steps are reported in the order they were enqueued). */
 GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scenes, const grtx_params *p,

@@ -856,8 +856,8 @@ def test_saved_list_entries_outside_the_scene_are_skipped(dense):
         saved = (torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda())
         got[name] = {key: v.cpu().numpy() for key, v in
                      R.backward(sc, cam, res["rgbT"], w, k=8, saved=saved).items()}
-    for key in got["cut"]:
-        np.testing.assert_allclose(got["bad"][key], got["cut"][key], rtol=1e-5, atol=1e-7)
+    for key in got["cut"]:                                     # sums of float atomics in any order
+        np.testing.assert_allclose(got["bad"][key], got["cut"][key], rtol=1e-4, atol=1e-6)
     sc.close()
 
 
