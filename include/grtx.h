@@ -441,7 +441,9 @@ GRTX_API int grtx_trace_forward(grtx_scene *scene, const grtx_camera *cam, const
  * the serving kernel): cams[i] is traced into rgbT[i] (device [width*height][4], 16-byte
  * aligned, as grtx_trace_forward's rgbT), with the same parameters for all. The warps of
  * every item share the GPU, so a small list (a frame's bounce rays) overlaps a large image
- * instead of running after it with most of the GPU idle. Results equal grtx_trace_forward's
+ * instead of running after it with most of the GPU idle. The launch's queue hands out the
+ * views smallest first, whatever their order in cams, so that a small view of long rays runs
+ * beside the large ones rather than after them. Results equal grtx_trace_forward's
  * for each camera alone, to the last bit of rounding (the batch runs in the serving kernel).
  * Sphere-form scenes, checkpoint or restart traversal, no optional outputs; n_cams in
  * [1, GRTX_MAX_BATCH].

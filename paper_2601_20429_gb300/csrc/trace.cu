@@ -384,22 +384,35 @@ extern "C" GRTX_API int grtx_trace_forward_batch(grtx_scene *sc, const grtx_came
     if (sc->form != GRTX_FORM_SPHERE) return grtx_fail(GRTX_ERR_INVALID_ARG, "batched traces need the sphere form");
     if (a.traversal == GRTX_TRAVERSAL_SINGLE)
         return grtx_fail(GRTX_ERR_INVALID_ARG, "batched traces take checkpoint or restart traversal");
-    ServeSeg h[GRTX_MAX_BATCH];
-    unsigned total = 0;
+    ServeSeg v[GRTX_MAX_BATCH], h[GRTX_MAX_BATCH];
+    unsigned items[GRTX_MAX_BATCH];
+    uint64_t all = 0;
     for (int i = 0; i < n_cams; ++i) {
         if (!rgbT[i] || ((uintptr_t)rgbT[i] & 15))
             return grtx_fail(GRTX_ERR_INVALID_ARG, "every rgbT output must be non-NULL and 16-byte aligned");
-        unsigned items = 0;
-        st = grtx_fill_camera(h[i].cam, items, &cams[i]);
+        items[i] = 0;
+        st = grtx_fill_camera(v[i].cam, items[i], &cams[i]);
         if (st) return st;
-        if ((uint64_t)total + items >= (1ull << 31)) return grtx_fail(GRTX_ERR_INVALID_ARG, "too many rays");
-        h[i].sc = grtx_scene_ref(sc);
-        h[i].out = (float4 *)rgbT[i];
-        h[i].item_begin = 0;
-        h[i].step_begin = total;
-        h[i].count = items;
-        h[i].pad = 0;
-        total += items;
+        all += items[i];
+        if (all >= (1ull << 31)) return grtx_fail(GRTX_ERR_INVALID_ARG, "too many rays");
+        v[i].sc = grtx_scene_ref(sc);
+        v[i].out = (float4 *)rgbT[i];
+        v[i].item_begin = 0;
+        v[i].pad = 0;
+    }
+    // The queue hands out the smallest views first: a small view cannot fill the GPU alone and
+    // often holds the longest rays (bounce rays), so queued last its warps would run on after
+    // the large views finish; queued first they run beside them (identical outputs). The
+    // table stays sorted by step_begin for the kernel's search.
+    int order[GRTX_MAX_BATCH];
+    for (int i = 0; i < n_cams; ++i) order[i] = i;
+    std::stable_sort(order, order + n_cams, [&](int x, int y) { return items[x] < items[y]; });
+    unsigned total = 0;
+    for (int j = 0; j < n_cams; ++j) {
+        h[j] = v[order[j]];
+        h[j].step_begin = total;
+        h[j].count = items[order[j]];
+        total += items[order[j]];
     }
     int bps = 0;
     if (segments_occupancy_k(p->k, &bps) != GRTX_OK || bps <= 0) return grtx_fail(GRTX_ERR_CUDA, "occupancy query failed");
