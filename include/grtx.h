@@ -556,9 +556,12 @@ GRTX_API int grtx_composite_bounce(float *d_rgbT, const float *d_sec_rgbT, const
  * with GRTX_ERR_INVALID_ARG (its hit lists do not fit the array). Its scratch -- the ray-queue
  * counter and the per-ray-slot checkpoint and eviction lists -- lives in one library-owned
  * device array of GRTX_NOALLOC_SCRATCH_BYTES (32 MiB) that every GPU which loads the library
- * holds until the process exits. The number of rays in flight is whatever fits in that array
- * (about 6,500 with the default capacities 256 / 128, against 155,648 for
- * grtx_trace_forward at k = 16 on 152 SMs), so a frame may take longer. If one block of 128 ray slots
+ * holds until the process exits. The number of rays in flight is whatever fits in that array:
+ * floor((GRTX_NOALLOC_SCRATCH_BYTES - 256) / (128 * (2 C + E) * 8)) blocks of 128 ray slots
+ * (C, E the checkpoint and eviction capacities; C = E = 1 for restart traversal), at most the
+ * resident blocks of the GPU. With the default capacities 256 / 512 that is 31 blocks, 3,968
+ * rays, against 155,648 for grtx_trace_forward at k = 16 on 152 SMs, so a frame may take
+ * longer; restart traversal fills the GPU. If one block of 128 ray slots
  * does not fit (large ckpt_capacity / evict_capacity) it returns GRTX_ERR_INVALID_ARG and says
  * so in grtx_last_error(). The first call on a device looks up the array's device address
  * with that device current; make that first call before any stream capture begins. Every

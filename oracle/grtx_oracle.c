@@ -863,10 +863,21 @@ static void og_atomic_add(double *p, double v)
 }
 
 /* dL_drgbT: n_rays*4 upstream gradient w.r.t. (r, g, b, T) of each output pixel.
- * Gradients are accumulated (+=) into g, which the caller zeroes. */
+ * Gradients are accumulated (+=) into g, which the caller zeroes.
+ * gabs (may be NULL): the same shapes, receiving for every gradient element the sum of the
+ * magnitudes of the terms that element is summed from, each term taken with the magnitudes
+ * of the quantities it is formed from (|dL/dC|, T, alpha, colours, the partial composites
+ * C_<=j and C_final that the opacity derivative subtracts, |dL/dT|). It is the scale of a
+ * first-order rounding-error bound for a lower-precision evaluation of the same sums: an
+ * element whose terms cancel can only be known to about eps * gabs, not eps * |g|.
+ * A term decided at a kink -- a colour channel whose SH sum + 0.5 lies within OG_KINK_MARGIN
+ * of the clamp at 0, or an alpha within OG_KINK_MARGIN of alpha_max -- may be present in a
+ * lower-precision evaluation and absent here (or the reverse); gabs is +inf for every
+ * element such a term feeds, whether or not this evaluation includes it. */
+#define OG_KINK_MARGIN 1e-5
 OG_API void og_backward(const og_scene *S, const og_params *p, int n_rays, const double *origins,
                         const double *dirs, const double *tnear, const double *tfar,
-                        const double *dL_drgbT, const og_grads *g)
+                        const double *dL_drgbT, const og_grads *g, const og_grads *gabs)
 {
     int K = S->n_coef;
 #pragma omp parallel for schedule(dynamic, 4)
@@ -904,16 +915,36 @@ OG_API void og_backward(const og_scene *S, const og_params *p, int n_rays, const
             double Y[16];
             og_sh_basis(S->sh_degree, dir, Y);
             for (int ch = 0; ch < 3; ++ch) {
+                if (gabs && fabs(raw[3 * h + ch]) < OG_KINK_MARGIN)
+                    for (int kk = 0; kk < K; ++kk) og_atomic_add(&gabs->sh[((size_t)i * K + kk) * 3 + ch], INFINITY);
                 if (!(raw[3 * h + ch] > 0)) continue;
                 double dc = gout[ch] * Tb[h] * a;
-                for (int kk = 0; kk < K; ++kk)
+                for (int kk = 0; kk < K; ++kk) {
                     og_atomic_add(&g->sh[((size_t)i * K + kk) * 3 + ch], dc * Y[kk]);
+                    if (gabs) og_atomic_add(&gabs->sh[((size_t)i * K + kk) * 3 + ch], fabs(dc * Y[kk]));
+                }
             }
             /* opacity of this hit */
             double dLda = -dLdT * T / (1.0 - a);
             for (int ch = 0; ch < 3; ++ch)
                 dLda += gout[ch] * (Tb[h] * col[3 * h + ch] - Sacc[ch] / (1.0 - a));
+            /* magnitude of the same expression's pieces: the colour behind this hit is formed
+             * as C_final - C_<=h, so its scale is |C_final| + |C_<=h| */
+            double dLda_abs = fabs(dLdT) * T / (1.0 - a);
+            for (int ch = 0; ch < 3; ++ch) {
+                double upto = C[ch] - Sacc[ch];                  /* C_<=h */
+                dLda_abs += fabs(gout[ch]) * (Tb[h] * fabs(col[3 * h + ch]) +
+                                              (fabs(C[ch]) + fabs(upto)) / (1.0 - a));
+            }
             for (int ch = 0; ch < 3; ++ch) Sacc[ch] += Tb[h] * a * col[3 * h + ch];
+            if (gabs && fabs(al - p->alpha_max) < OG_KINK_MARGIN) {
+                og_atomic_add(&gabs->logits[i], INFINITY);
+                for (int a2 = 0; a2 < 3; ++a2) {
+                    og_atomic_add(&gabs->means[3 * i + a2], INFINITY);
+                    og_atomic_add(&gabs->log_scales[3 * i + a2], INFINITY);
+                }
+                for (int mm = 0; mm < 4; ++mm) og_atomic_add(&gabs->quats[4 * i + mm], INFINITY);
+            }
             if (clamped) continue;
             /* alpha = o exp(-d2/2), d2 = min_t (x(t)-mu)^T Sigma^-1 (x(t)-mu); by the
              * envelope theorem d(d2) = partial derivative at fixed t = t_alpha. */
@@ -948,6 +979,33 @@ OG_API void og_backward(const og_scene *S, const og_params *p, int n_rays, const
             double dot = qn[0] * dqn[0] + qn[1] * dqn[1] + qn[2] * dqn[2] + qn[3] * dqn[3];
             for (int mm = 0; mm < 4; ++mm)
                 og_atomic_add(&g->quats[4 * i + mm], (dqn[mm] - qn[mm] * dot) / S->qnorm[i]);
+            if (gabs) {
+                /* the same chain with every factor and partial sum taken by magnitude */
+                double sc = dLda_abs * 0.5 * al2;                /* |dL/d d2| scale */
+                og_atomic_add(&gabs->logits[i], dLda_abs * G * o * (1.0 - o));
+                double ae[3];
+                for (int a2 = 0; a2 < 3; ++a2) ae[a2] = fabs(e[a2]);
+                for (int a2 = 0; a2 < 3; ++a2) {
+                    double Pa = fabs(P[3 * a2]) * ae[0] + fabs(P[3 * a2 + 1]) * ae[1] + fabs(P[3 * a2 + 2]) * ae[2];
+                    og_atomic_add(&gabs->means[3 * i + a2], 2.0 * sc * Pa);
+                }
+                double aRm[9];
+                for (int j = 0; j < 3; ++j) {
+                    double pa = fabs(R[j]) * ae[0] + fabs(R[3 + j]) * ae[1] + fabs(R[6 + j]) * ae[2];
+                    double inv2 = 1.0 / (s[j] * s[j]);
+                    og_atomic_add(&gabs->log_scales[3 * i + j], 2.0 * sc * pa * pa * inv2);
+                    for (int a2 = 0; a2 < 3; ++a2) aRm[3 * a2 + j] = 2.0 * sc * pa * ae[a2] * inv2;
+                }
+                double aq[4], adot = 0;
+                for (int mm = 0; mm < 4; ++mm) {
+                    double acc = 0;
+                    for (int ee = 0; ee < 9; ++ee) acc += fabs(dR[mm][ee]) * aRm[ee];
+                    aq[mm] = acc;
+                    adot += fabs(qn[mm]) * acc;
+                }
+                for (int mm = 0; mm < 4; ++mm)
+                    og_atomic_add(&gabs->quats[4 * i + mm], (aq[mm] + fabs(qn[mm]) * adot) / S->qnorm[i]);
+            }
         }
         free(Tb); free(col); free(raw); free(hits);
     }

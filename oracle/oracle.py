@@ -105,7 +105,7 @@ def lib():
                                            C.POINTER(OgRoundCfg), C.c_int, _dp, _dp, _dp, _dp, _dp,
                                            _ip, C.POINTER(OgRoundStats), C.c_int]
             L.og_backward.argtypes = [C.c_void_p, C.POINTER(OgParams), C.c_int, _dp, _dp, _dp, _dp, _dp,
-                                      C.POINTER(OgGrads)]
+                                      C.POINTER(OgGrads), C.POINTER(OgGrads)]
             L.og_mirror_rays.restype = C.c_int
             L.og_mirror_rays.argtypes = [C.POINTER(OgCamera), C.POINTER(OgMirror)] + [_dp] * 8 + [_ip]
             L.og_composite_bounce.argtypes = [_dp, _dp, _ip, C.c_int, _dp]
@@ -265,15 +265,28 @@ class Scene:
         stats = {name: int(getattr(st, name)) for name, _ in OgRoundStats._fields_}
         return dict(out=out, n_blend=nb, stats=stats)
 
-    def backward(self, rays, dL_drgbT, params: OgParams | None = None) -> dict:
+    def backward(self, rays, dL_drgbT, params: OgParams | None = None, term_scale: bool = False) -> dict:
+        """Analytic gradient of sum(dL_drgbT * image) w.r.t. the raw parameters. With
+        term_scale, the result also holds "<name>_scale": per element, the summed magnitudes
+        of the terms the element is formed from (see og_backward), the scale of its rounding
+        error in a lower-precision evaluation."""
         o, d, tn, tf = [_f64(a) for a in rays]
         n = tn.shape[0]
         params = params or make_params()
         gL = _f64(dL_drgbT).reshape(n, 4)
-        g = dict(means=np.zeros((self.n, 3)), log_scales=np.zeros((self.n, 3)), quats=np.zeros((self.n, 4)),
-                 logits=np.zeros(self.n), sh=np.zeros((self.n, self.n_coef, 3)))
-        G = OgGrads(*[_p(g[k]) for k in ("means", "log_scales", "quats", "logits", "sh")])
-        lib().og_backward(self._h, C.byref(params), n, _p(o), _p(d), _p(tn), _p(tf), _p(gL), C.byref(G))
+        names = ("means", "log_scales", "quats", "logits", "sh")
+
+        def zeros():
+            return dict(means=np.zeros((self.n, 3)), log_scales=np.zeros((self.n, 3)), quats=np.zeros((self.n, 4)),
+                        logits=np.zeros(self.n), sh=np.zeros((self.n, self.n_coef, 3)))
+        g = zeros()
+        G = OgGrads(*[_p(g[k]) for k in names])
+        ga = zeros() if term_scale else None
+        GA = OgGrads(*[_p(ga[k]) for k in names]) if term_scale else None
+        lib().og_backward(self._h, C.byref(params), n, _p(o), _p(d), _p(tn), _p(tf), _p(gL), C.byref(G),
+                          C.byref(GA) if term_scale else None)
+        if term_scale:
+            g.update({k + "_scale": ga[k] for k in names})
         return g
 
 

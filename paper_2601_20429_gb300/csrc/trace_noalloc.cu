@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 
 #include "trace_impl.cuh"
@@ -37,51 +38,59 @@ namespace {
 constexpr size_t kCounterBytes = 256;
 constexpr int kMaxDevices = 64;
 
-// Device address of g_noalloc_scratch per device (host code only sees a stand-in for the
-// symbol; the address is looked up once per device, with that device current).
-unsigned char *g_scratch_addr[kMaxDevices] = {};
-int g_sms[kMaxDevices] = {};
+// Device address of g_noalloc_scratch and SM count per device. Host code only sees a
+// stand-in for the symbol, so the address is looked up once per device, with that device
+// current; the once-flag makes concurrent first calls from several host threads safe.
+struct DeviceScratch {
+    std::once_flag once;
+    cudaError_t err = cudaSuccess;
+    unsigned char *addr = nullptr;
+    int sms = 1;
+};
+DeviceScratch g_dev[kMaxDevices];
 
 int scratch_for_current_device(unsigned char **out, int *sms)
 {
     int dev = 0;
     GRTX_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return grtx_fail(GRTX_ERR_INVALID_ARG, "device ordinal out of range");
-    if (!g_scratch_addr[dev]) {
+    DeviceScratch &d = g_dev[dev];
+    std::call_once(d.once, [&d, dev]() {
         void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return grtx_cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        d.err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (d.err != cudaSuccess) return;
         int n = 0;
-        GRTX_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
-        g_sms[dev] = n > 0 ? n : 1;
-        g_scratch_addr[dev] = (unsigned char *)p;
-    }
-    *out = g_scratch_addr[dev];
-    *sms = g_sms[dev];
+        d.err = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        d.sms = n > 0 ? n : 1;
+        d.addr = (unsigned char *)p;
+    });
+    if (d.err != cudaSuccess) return grtx_cuda_fail(d.err, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    *out = d.addr;
+    *sms = d.sms;
     return GRTX_OK;
 }
 
 int launch_noalloc(int k, const TraceArgs &a, int form, int blocks, cudaStream_t s)
 {
     switch (k) {
-    case 1: return trace_launch<1>(a, form, false, false, blocks, s);
-    case 2: return trace_launch<2>(a, form, false, false, blocks, s);
-    case 4: return trace_launch<4>(a, form, false, false, blocks, s);
-    case 8: return trace_launch<8>(a, form, false, false, blocks, s);
-    case 16: return trace_launch<16>(a, form, false, false, blocks, s);
-    default: return trace_launch<32>(a, form, false, false, blocks, s);
+    case 1: return trace_launch<1>(a, form, false, PASS_FWD, blocks, s);
+    case 2: return trace_launch<2>(a, form, false, PASS_FWD, blocks, s);
+    case 4: return trace_launch<4>(a, form, false, PASS_FWD, blocks, s);
+    case 8: return trace_launch<8>(a, form, false, PASS_FWD, blocks, s);
+    case 16: return trace_launch<16>(a, form, false, PASS_FWD, blocks, s);
+    default: return trace_launch<32>(a, form, false, PASS_FWD, blocks, s);
     }
 }
 
 int occupancy_noalloc(int k, int form, int *bps)
 {
     switch (k) {
-    case 1: return trace_occupancy<1>(form, false, false, bps);
-    case 2: return trace_occupancy<2>(form, false, false, bps);
-    case 4: return trace_occupancy<4>(form, false, false, bps);
-    case 8: return trace_occupancy<8>(form, false, false, bps);
-    case 16: return trace_occupancy<16>(form, false, false, bps);
-    default: return trace_occupancy<32>(form, false, false, bps);
+    case 1: return trace_occupancy<1>(form, false, PASS_FWD, bps);
+    case 2: return trace_occupancy<2>(form, false, PASS_FWD, bps);
+    case 4: return trace_occupancy<4>(form, false, PASS_FWD, bps);
+    case 8: return trace_occupancy<8>(form, false, PASS_FWD, bps);
+    case 16: return trace_occupancy<16>(form, false, PASS_FWD, bps);
+    default: return trace_occupancy<32>(form, false, PASS_FWD, bps);
     }
 }
 

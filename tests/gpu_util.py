@@ -6,6 +6,12 @@ import numpy as np
 ALPHA_MIN = 0.01
 T_MIN = 1e-3
 RGB_TOL = 2e-4          # max abs per RGB channel (and on T)
+# Per-element gradient tolerance, in units of the oracle's term scale of the element (the
+# summed magnitudes of its terms): about 840 FP32 unit roundoffs (2^-24). The kernel forms
+# each term from FP32 values that carry a few roundoffs each, except the opacity derivative's
+# colour behind a hit, a difference of two FP32 composites of up to ~100 terms, and the
+# backward sums the terms with FP32 atomics.
+GRAD_TERM_TOL = 5e-5
 
 
 def oracle_rays_subset(rays, idx):

@@ -413,6 +413,53 @@ def test_backward_matches_central_differences():
     assert compared > 0.9 * sum(a.size for a in params)
 
 
+def test_backward_term_scale_bounds_and_single_terms():
+    """The term scale of og_backward (the magnitudes an element's terms are summed from) is an
+    upper bound of |g| on every element (triangle inequality), zero exactly where no term
+    reaches the element, and equal to |g| for SH coefficients of a Gaussian that one ray
+    blends once (one term). It is the same gradient with or without the scale."""
+    params = _fd_scene()
+    cam = scenes.pinhole_camera(10, 10, (0.0, 0.0, -2.5), (0, 0, 0), 40.0)
+    rays = O.camera_rays(cam)
+    w = np.random.default_rng(7).normal(0, 1, (rays[0].shape[0], 4))
+    S = O.Scene(*params, sh_degree=3)
+    g = S.backward(rays, w, term_scale=True)
+    g0 = S.backward(rays, w)
+    for name in ("means", "log_scales", "quats", "logits", "sh"):
+        a, sc = np.abs(g[name]), g[name + "_scale"]
+        np.testing.assert_allclose(g[name], g0[name], rtol=1e-9, atol=1e-12 * a.max())
+        assert np.all(np.isfinite(sc))                       # alphas < 0.99, colours away from 0
+        assert np.all(sc >= a * (1 - 1e-12))
+        assert np.all((sc > 0) == (a > 0))
+        assert sc.max() > a.max()
+    one = one_ray([0.01, 0.0, -3.0], [0, 0, 1])
+    S1 = make_scene([[0, 0, 0]], 0.05, [1, 0, 0, 0], 0.6, sh=np.random.default_rng(3).normal(0, 0.1, (1, 16, 3)),
+                    sh_degree=3)
+    g1 = S1.backward(one, np.array([[0.7, -0.4, 0.2, 0.3]]), term_scale=True)
+    np.testing.assert_allclose(g1["sh_scale"], np.abs(g1["sh"]), rtol=1e-14, atol=0)
+    assert np.abs(g1["sh"]).max() > 0
+
+
+@pytest.mark.parametrize("offset,kink", [(0.0, True), (3e-6, True), (-3e-6, True), (1e-3, False)])
+def test_backward_term_scale_marks_kinks(offset, kink):
+    """A colour channel whose SH sum + 0.5 sits within 1e-5 of the clamp at 0, or an alpha
+    within 1e-5 of the 0.99 clamp, marks the elements it feeds with an infinite scale: a
+    lower-precision evaluation may take the other side of the kink."""
+    one = one_ray([0.0, 0.0, -3.0], [0, 0, 1])
+    w = np.array([[0.7, -0.4, 0.2, 0.3]])
+    # colour channel 1 at raw = offset (on axis: alpha = o, colour = degree-0 coefficient)
+    S = make_scene([[0, 0, 0]], 0.05, [1, 0, 0, 0], 0.6, [0.3, offset, 0.8])
+    g = S.backward(one, w, term_scale=True)
+    assert np.isinf(g["sh_scale"][0, 0, 1]) == kink
+    assert np.isfinite(g["sh_scale"][0, 0, [0, 2]]).all() and np.isfinite(g["means_scale"]).all()
+    # alpha at 0.99 + offset on the axis (alpha = o there)
+    S = make_scene([[0, 0, 0]], 0.05, [1, 0, 0, 0], 0.99 + offset, [0.3, 0.5, 0.8])
+    g = S.backward(one, w, term_scale=True)
+    for name in ("means", "log_scales", "quats", "logits"):
+        assert np.isinf(g[name + "_scale"]).all() == kink
+    assert np.isfinite(g["sh_scale"]).all()
+
+
 # ---------------------------------------------------------------- LBVH building blocks
 
 

@@ -32,6 +32,35 @@ def test_noalloc_matches_regular_entry_point_twice(form, k):
     sc.close()
 
 
+@pytest.mark.parametrize("traversal", ["checkpoint", "restart"])
+def test_noalloc_on_a_fresh_scene_allocates_nothing(traversal):
+    """On a scene that no regular trace has touched, the allocation-free trace leaves the
+    scene's own workspace unallocated and the device's free memory unchanged across a call
+    (the first call on a device may still load the library's device code, so it comes
+    first), and gives the regular entry point's image in both traversal modes."""
+    g = scenes.surface_scene(n=60_000, seed=22)
+    cam = scenes.pinhole_camera(256, 160, (0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 60.0)
+    sc = R.Scene.from_params(g)
+    p = R.trace_params(k=16, traversal=traversal, alpha_min=sc.alpha_min)
+    c = N.make_camera(cam)
+    n = cam["width"] * cam["height"]
+    outs = [torch.full((n, 4), -1.0, device="cuda") for _ in range(2)]
+    torch.cuda.synchronize()
+    N.grtx_trace_forward_noalloc(sc.handle, c, p, outs[0])
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    N.grtx_trace_forward_noalloc(sc.handle, c, p, outs[1])
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free_before
+    assert sc.info()["bytes_workspace"] == 0
+    ref = R.render(sc, cam, k=16, traversal=traversal)["rgbT"]
+    torch.cuda.synchronize()
+    for out in outs:
+        assert float((out - ref).abs().max()) <= TOL
+    assert float(ref[:, 3].min()) < 0.5
+    sc.close()
+
+
 def test_noalloc_rejects_capacities_beyond_its_scratch():
     g = scenes.tiny_scene(seed=0, n=500)
     cam = scenes.pinhole_camera(16, 16, (0.0, 0.0, -3.0), (0.0, 0.0, 0.0), 60.0)
