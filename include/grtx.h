@@ -624,8 +624,11 @@ GRTX_API void grtx_world_destroy(grtx_world *world);
 
 typedef struct grtx_server grtx_server;
 
-/* A camera request: render cam on scene scene_id into d_rgbT (device [W*H][4], caller-owned,
- * must stay valid until the request completes). tag is returned with the completion. */
+/* A camera request: render cam on scene scene_id into d_rgbT (device [W*H][4], 16-byte
+ * aligned, caller-owned, valid until the request completes), or, with d_rgbT = NULL, into an
+ * output the server allocates from its memory budget when it admits the request (see
+ * grtx_server_create; returned in the completion, given back with grtx_server_release).
+ * tag is returned with the completion. */
 typedef struct grtx_request {
     int32_t scene_id;
     int32_t reserved;
@@ -634,33 +637,70 @@ typedef struct grtx_request {
     uint64_t tag;
 } grtx_request;
 
-/* A finished request: tag, status, and host wall-clock times in seconds (CLOCK_MONOTONIC)
- * of admission (work first enqueued) and completion (its last step observed complete). */
+/* A finished request: tag, status, host wall-clock times in seconds (CLOCK_MONOTONIC) of
+ * admission (work first enqueued) and completion (its last step observed complete), and the
+ * device image [W*H][4] it was rendered into (the request's own buffer or a server-owned one). */
 typedef struct grtx_completion {
     uint64_t tag;
     int32_t status;
     int32_t reserved;
     double t_admit;
     double t_done;
+    float *d_rgbT;
 } grtx_completion;
 
 /* Create a server over n_scenes built scenes (not owned; they must outlive the server).
  * max_rays_per_step: rays per persistent launch (0: 4M); max_inflight: requests admitted at
  * once (0: 64); p: tracing parameters for every request (checkpoint or restart traversal;
  * GRTX_TRAVERSAL_SINGLE is rejected with GRTX_ERR_INVALID_ARG). Host call; waits for the
- * device once (the scenes' builds), then allocates 4 step slots, each with its own stream
- * (slot 0 uses `stream`, the others streams the server creates) and its own
+ * device once (the scenes' builds). A request's output is complete when its completion is
+ * reported (steps are reported in the order they were enqueued).
+ *
+ * Memory (the paper sizes its checkpoint and eviction buffers per resident ray slot and
+ * reports their total, Sec. V-E). The server runs up to 4 step slots, each with its own
+ * stream (slot 0 uses `stream`, the others streams the server creates), queue counter and
  * checkpoint/eviction lists, so that a step's launch fills the SMs its predecessors' last
- * warps leave. Each slot's lists take (resident ray slots) x (2 ckpt_capacity +
- * evict_capacity) x 8 bytes: about 1.3 GB with the default capacities on 152 SMs; an
- * allocation that fails returns GRTX_ERR_OOM. A request's output is complete when its
- * completion is reported (steps are reported in the order they were enqueued). */
+ * warps leave. One step slot's lists take (resident ray slots) x (2 ckpt_capacity +
+ * evict_capacity) x 8 bytes: about 1.3 GB with the default capacities at full residency on
+ * 152 SMs.
+ *   - mem_budget_bytes = 0: no cap. 4 step slots at full residency; requests must bring their
+ *     own output (d_rgbT = NULL is rejected with GRTX_ERR_INVALID_ARG).
+ *   - mem_budget_bytes > 0: the server's device memory never exceeds it. The step slots' lists
+ *     take at most half of it: as many full-residency step slots as fit (1 to 4), or one slot
+ *     with as many 128-ray blocks as fit; GRTX_ERR_INVALID_ARG if not even one block of lists
+ *     fits. The rest (less the small segment tables) is reserved as an output arena. A request
+ *     with d_rgbT = NULL needs W*H*16 bytes of it: requests are admitted in submission order,
+ *     and admission stops at the first one whose output does not fit until grtx_server_release
+ *     returns memory (so a large request is never overtaken). A request whose output exceeds
+ *     the whole arena is rejected by grtx_server_submit with GRTX_ERR_OOM.
+ * An allocation that fails returns GRTX_ERR_OOM. */
 GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scenes, const grtx_params *p,
-                                int64_t max_rays_per_step, int max_inflight, void *stream,
-                                grtx_server **out);
+                                int64_t mem_budget_bytes, int64_t max_rays_per_step, int max_inflight,
+                                void *stream, grtx_server **out);
 
-/* Queue n requests (host array, copied). Returns GRTX_ERR_BUSY, queueing none of them, if
- * the pending queue would exceed 65536 entries. Non-blocking. */
+/* Give a server-owned output (a completion's d_rgbT of a request submitted with d_rgbT =
+ * NULL) back to the server's arena. Call it once every read of the image has completed
+ * (the server may render the next admitted request into the same memory). Host call.
+ * GRTX_ERR_NOT_FOUND if d_rgbT is not a live server-owned output. */
+GRTX_API int grtx_server_release(grtx_server *srv, float *d_rgbT);
+
+/* Sizes chosen at creation and current use (host call). */
+typedef struct grtx_server_info {
+    int32_t n_step_slots;        /* step slots (streams) the server runs, 1..4             */
+    int32_t blocks_per_step;     /* 128-ray blocks of one step's persistent launch          */
+    int64_t list_bytes;          /* checkpoint/eviction lists of all step slots             */
+    int64_t arena_bytes;         /* output arena reserved for server-owned outputs          */
+    int64_t arena_used;          /* bytes of the arena held by admitted, unreleased outputs */
+    int64_t device_bytes;        /* all device memory the server holds                      */
+    int32_t n_inflight;          /* admitted, not yet completed                            */
+    int32_t n_pending;           /* submitted, not yet admitted                            */
+} grtx_server_info;
+GRTX_API int grtx_server_get_info(const grtx_server *srv, grtx_server_info *info);
+
+/* Queue n requests (host array, copied). Non-blocking. None of them is queued if one fails:
+ * GRTX_ERR_BUSY if the pending queue would exceed 65536 entries; GRTX_ERR_OOM for a request
+ * with d_rgbT = NULL whose output exceeds the server's whole output arena (or with no budget,
+ * GRTX_ERR_INVALID_ARG); GRTX_ERR_NOT_FOUND for an unknown scene id. */
 GRTX_API int grtx_server_submit(grtx_server *srv, const grtx_request *reqs, int n);
 
 /* Advance the server: admit pending requests into free slots (continuous batching), enqueue

@@ -1,13 +1,16 @@
 // Serving: several resident scenes and a stream of camera requests. Requests are admitted
-// into a bounded set of slots as earlier ones finish (continuous batching); each step is one
+// into a bounded set of slots as earlier ones finish (continuous batching), and, under a
+// memory budget, only while their outputs fit the server's output arena; each step is one
 // persistent launch whose queue concatenates pieces of every admitted request (mixed scenes
-// and resolutions), so rays of new and old requests share the device. Two steps may be in
-// flight: the host prepares and enqueues the next while the current one runs.
+// and resolutions), so rays of new and old requests share the device. Up to four steps are
+// in flight, each on its own stream: the host prepares and enqueues the next while the
+// others run.
 #include <cuda_runtime.h>
 #include <time.h>
 
 #include <algorithm>
 #include <deque>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -71,6 +74,62 @@ struct SrvReq {
     unsigned n_items = 0;      // queue items of the whole request (32 per warp tile)
     unsigned next = 0;         // first item not yet scheduled
     double t_admit = 0;
+    size_t out_bytes = 0;      // > 0: the server allocates the output from its arena at admission
+};
+
+// First-fit allocator over the output arena (offsets on the host, 256-byte granules).
+struct Arena {
+    char *base = nullptr;
+    size_t bytes = 0, used = 0;
+    std::map<size_t, size_t> free_;     // offset -> size, coalesced
+    std::map<size_t, size_t> live;      // offset -> size of outputs handed out
+    void reset(char *b, size_t n)
+    {
+        base = b;
+        bytes = n;
+        used = 0;
+        free_.clear();
+        live.clear();
+        if (n) free_[0] = n;
+    }
+    static size_t round(size_t n) { return (n + 255) / 256 * 256; }
+    char *alloc(size_t n)
+    {
+        n = round(n);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < n) continue;
+            size_t off = it->first, sz = it->second;
+            free_.erase(it);
+            if (sz > n) free_[off + n] = sz - n;
+            live[off] = n;
+            used += n;
+            return base + off;
+        }
+        return nullptr;
+    }
+    bool release(char *p)
+    {
+        if (!base || p < base || p >= base + bytes) return false;
+        auto it = live.find((size_t)(p - base));
+        if (it == live.end()) return false;
+        size_t off = it->first, n = it->second;
+        live.erase(it);
+        used -= n;
+        auto nx = free_.lower_bound(off);
+        if (nx != free_.end() && off + n == nx->first) {      // merge with the next free block
+            n += nx->second;
+            nx = free_.erase(nx);
+        }
+        if (nx != free_.begin()) {                              // and with the previous one
+            auto pv = std::prev(nx);
+            if (pv->first + pv->second == off) {
+                pv->second += n;
+                return true;
+            }
+        }
+        free_[off] = n;
+        return true;
+    }
 };
 
 // A step slot: each has its own stream, per-slot lists and queue counter, so that the next
@@ -93,15 +152,20 @@ struct grtx_server {
     grtx_params p;
     int64_t max_rays = 0;
     int max_inflight = 0;
+    int64_t budget = 0;         // device bytes the server may hold (0: no cap)
     cudaStream_t s = nullptr;
     std::deque<SrvReq *> pending;
     std::deque<SrvReq *> active;
     SrvStep steps[kSteps];
+    int n_steps = kSteps;       // step slots in use (fewer under a small budget)
     std::deque<int> inflight;
     std::deque<grtx_completion> backlog;
     TraceArgs a;
     int blocks = 0;
+    size_t list_bytes = 0;      // lists of all step slots
+    size_t device_bytes = 0;    // everything the server allocated on the device
     unsigned *queue = nullptr;  // one ray-queue counter per step slot
+    Arena arena;                // server-owned outputs (budget > 0)
 };
 
 namespace {
@@ -109,7 +173,7 @@ namespace {
 void server_free(grtx_server *v)
 {
     for (auto &st : v->steps)
-        if (st.ev) cudaStreamSynchronize(st.s);
+        if (st.ev) cudaStreamSynchronize(st.s);     // (unused slots have no event)
     for (auto &st : v->steps) {
         if (st.ev) cudaEventDestroy(st.ev);
         if (st.h) cudaFreeHost(st.h);
@@ -118,6 +182,7 @@ void server_free(grtx_server *v)
         if (st.own_stream) cudaStreamDestroy(st.s);
     }
     if (v->queue) cudaFree(v->queue);
+    if (v->arena.base) cudaFree(v->arena.base);
     for (auto *r : v->pending) delete r;
     for (auto *r : v->active) delete r;
     delete v;
@@ -178,8 +243,8 @@ bool has_unscheduled(const grtx_server *v)
 }  // namespace
 
 extern "C" GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scenes, const grtx_params *p,
-                                           int64_t max_rays_per_step, int max_inflight, void *stream,
-                                           grtx_server **out)
+                                           int64_t mem_budget_bytes, int64_t max_rays_per_step, int max_inflight,
+                                           void *stream, grtx_server **out)
 {
     if (!scenes || n_scenes <= 0 || !out) return grtx_fail(GRTX_ERR_INVALID_ARG, "need scenes and out");
     int st = grtx_check_params(p);
@@ -191,14 +256,47 @@ extern "C" GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scen
         if (scenes[i]->form != GRTX_FORM_SPHERE) return grtx_fail(GRTX_ERR_INVALID_ARG, "serving needs sphere-form scenes");
         if (scenes[i]->alpha_min != p->alpha_min) return grtx_fail(GRTX_ERR_INVALID_ARG, "alpha_min mismatch");
     }
-    if (max_rays_per_step < 0 || max_inflight < 0 || max_inflight > 4096)
+    if (max_rays_per_step < 0 || max_inflight < 0 || max_inflight > 4096 || mem_budget_bytes < 0)
         return grtx_fail(GRTX_ERR_INVALID_ARG, "bad server limits");
+    const int64_t max_rays = max_rays_per_step > 0 ? max_rays_per_step : (int64_t)4 << 20;
+    const int inflight_cap = max_inflight > 0 ? max_inflight : 64;
+    const size_t C = p->ckpt_capacity > 0 ? p->ckpt_capacity : GRTX_DEFAULT_CKPT_CAPACITY;
+    const size_t E = p->evict_capacity > 0 ? p->evict_capacity : GRTX_DEFAULT_EVICT_CAPACITY;
+    int bps = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (serve_occupancy_k(p->k, &bps) != GRTX_OK || bps <= 0 || sms <= 0)
+        return grtx_fail(GRTX_ERR_CUDA, "occupancy query failed");
+    // sizes: the lists of n_steps step slots of `blocks` 128-ray blocks each, the segment
+    // tables and queue counters, and (under a budget) the output arena
+    const size_t per_block = 128 * (2 * C + E) * sizeof(uint2);
+    const int blocks_full = sms * bps;
+    const size_t tables = kSteps * kQueueStride * sizeof(unsigned) + (size_t)kSteps * sizeof(ServeSeg) * inflight_cap;
+    int n_steps = kSteps, blocks = blocks_full;
+    size_t arena = 0;
+    if (mem_budget_bytes > 0) {
+        const size_t budget = (size_t)mem_budget_bytes;
+        const size_t list_cap = budget / 2;
+        const size_t full_step = (size_t)blocks_full * per_block;
+        n_steps = (int)std::min<size_t>(kSteps, std::max<size_t>(1, list_cap / full_step));
+        blocks = (int)std::min<size_t>((size_t)blocks_full, list_cap / ((size_t)n_steps * per_block));
+        if (blocks < 1)
+            return grtx_fail(GRTX_ERR_INVALID_ARG, "memory budget of " + std::to_string(budget) +
+                                                       " bytes is below twice one block of lists (" +
+                                                       std::to_string(per_block) + " bytes)");
+        size_t lists = (size_t)n_steps * blocks * per_block;
+        if (lists + tables > budget) return grtx_fail(GRTX_ERR_INVALID_ARG, "memory budget too small");
+        arena = (budget - lists - tables) / 256 * 256;
+    }
     grtx_server *v = new (std::nothrow) grtx_server();
     if (!v) return grtx_fail(GRTX_ERR_OOM, "host allocation failed");
     v->scenes.assign(scenes, scenes + n_scenes);
     v->p = *p;
-    v->max_rays = max_rays_per_step > 0 ? max_rays_per_step : (int64_t)4 << 20;
-    v->max_inflight = max_inflight > 0 ? max_inflight : 64;
+    v->max_rays = max_rays;
+    v->max_inflight = inflight_cap;
+    v->budget = mem_budget_bytes;
+    v->n_steps = n_steps;
+    v->blocks = blocks;
     v->s = reinterpret_cast<cudaStream_t>(stream);
     TraceArgs &a = v->a;
     a = TraceArgs{};
@@ -208,41 +306,39 @@ extern "C" GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scen
     a.bg0 = p->bg[0];
     a.bg1 = p->bg[1];
     a.bg2 = p->bg[2];
-    a.ckpt_cap = p->ckpt_capacity > 0 ? p->ckpt_capacity : GRTX_DEFAULT_CKPT_CAPACITY;
-    a.evict_cap = p->evict_capacity > 0 ? p->evict_capacity : GRTX_DEFAULT_EVICT_CAPACITY;
+    a.ckpt_cap = (int)C;
+    a.evict_cap = (int)E;
     a.packet_stack = p->packet_stack > 0 ? std::min(p->packet_stack, kPacketStack) : kPacketStack;
-    int bps = 0, dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (serve_occupancy_k(p->k, &bps) != GRTX_OK || bps <= 0 || sms <= 0) {
-        server_free(v);
-        return grtx_fail(GRTX_ERR_CUDA, "occupancy query failed");
-    }
-    v->blocks = sms * bps;
     int n_slots = v->blocks * 128;
-    size_t ws = (size_t)n_slots * (2 * (size_t)a.ckpt_cap + (size_t)a.evict_cap) * sizeof(uint2);
+    size_t ws = (size_t)blocks * per_block;
     // earlier work on any stream (the scenes' builds) completes before steps run on the
     // server's own streams
     cudaError_t e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaMalloc((void **)&v->queue, kSteps * kQueueStride * sizeof(unsigned));
-    for (int i = 0; i < kSteps && e == cudaSuccess; ++i) {
-        SrvStep &st = v->steps[i];
+    for (int i = 0; i < n_steps && e == cudaSuccess; ++i) {
+        SrvStep &sst = v->steps[i];
         if (i == 0) {
-            st.s = v->s;
+            sst.s = v->s;
         } else {
-            e = cudaStreamCreateWithFlags(&st.s, cudaStreamNonBlocking);
-            st.own_stream = e == cudaSuccess;
+            e = cudaStreamCreateWithFlags(&sst.s, cudaStreamNonBlocking);
+            sst.own_stream = e == cudaSuccess;
         }
-        if (e == cudaSuccess) e = cudaMalloc(&st.ws, ws);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st.ev, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaMallocHost((void **)&st.h, sizeof(ServeSeg) * v->max_inflight);
-        if (e == cudaSuccess) e = cudaMalloc((void **)&st.d, sizeof(ServeSeg) * v->max_inflight);
+        if (e == cudaSuccess) e = cudaMalloc(&sst.ws, ws);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sst.ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&sst.h, sizeof(ServeSeg) * v->max_inflight);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&sst.d, sizeof(ServeSeg) * v->max_inflight);
     }
+    char *arena_base = nullptr;
+    if (e == cudaSuccess && arena > 0) e = cudaMalloc((void **)&arena_base, arena);
     if (e != cudaSuccess) {
         cudaGetLastError();
         server_free(v);
         return grtx_fail(GRTX_ERR_OOM, "server allocation failed");
     }
+    v->arena.reset(arena_base, arena);
+    v->list_bytes = (size_t)n_steps * ws;
+    v->device_bytes = v->list_bytes + arena + kSteps * kQueueStride * sizeof(unsigned) +
+                      (size_t)n_steps * sizeof(ServeSeg) * v->max_inflight;
     a.n_slots = n_slots;
     *out = v;
     return GRTX_OK;
@@ -256,8 +352,17 @@ extern "C" GRTX_API int grtx_server_submit(grtx_server *v, const grtx_request *r
     for (int i = 0; i < n; ++i) {
         const grtx_request &q = reqs[i];
         int st = GRTX_OK;
+        size_t out_bytes = 0;
+        if (!q.d_rgbT && q.cam.width > 0 && q.cam.height > 0)
+            out_bytes = Arena::round((size_t)q.cam.width * (size_t)q.cam.height * 16);
         if (q.scene_id < 0 || q.scene_id >= (int)v->scenes.size()) st = grtx_fail(GRTX_ERR_NOT_FOUND, "unknown scene id");
-        else if (!q.d_rgbT || ((uintptr_t)q.d_rgbT & 15)) st = grtx_fail(GRTX_ERR_INVALID_ARG, "bad output buffer");
+        else if (!q.d_rgbT && v->arena.bytes == 0)
+            st = grtx_fail(GRTX_ERR_INVALID_ARG, "a server-owned output (d_rgbT = NULL) needs a server memory budget");
+        else if (!q.d_rgbT && out_bytes > v->arena.bytes)
+            st = grtx_fail(GRTX_ERR_OOM, "the request's output (" + std::to_string(out_bytes) +
+                                             " bytes) exceeds the server's output arena (" +
+                                             std::to_string(v->arena.bytes) + " bytes)");
+        else if ((uintptr_t)q.d_rgbT & 15) st = grtx_fail(GRTX_ERR_INVALID_ARG, "bad output buffer");
         SrvReq *r = nullptr;
         if (st == GRTX_OK) {
             r = new (std::nothrow) SrvReq();
@@ -265,6 +370,7 @@ extern "C" GRTX_API int grtx_server_submit(grtx_server *v, const grtx_request *r
         }
         if (st == GRTX_OK) {
             r->r = q;
+            r->out_bytes = out_bytes;
             st = grtx_fill_camera(r->cam, r->n_items, &q.cam);
         }
         if (st != GRTX_OK) {
@@ -298,6 +404,7 @@ extern "C" GRTX_API int grtx_server_poll(grtx_server *v, grtx_completion *done, 
                 c.reserved = 0;
                 c.t_admit = r->t_admit;
                 c.t_done = t;
+                c.d_rgbT = r->r.d_rgbT;
                 v->backlog.push_back(c);
                 v->active.erase(std::find(v->active.begin(), v->active.end(), r));
                 delete r;
@@ -307,17 +414,23 @@ extern "C" GRTX_API int grtx_server_poll(grtx_server *v, grtx_completion *done, 
             st.busy = false;
             v->inflight.pop_front();
         }
-        // admission of pending requests into free slots
+        // admission of pending requests into free slots, in submission order; a request
+        // whose server-owned output does not fit the arena holds the ones behind it
         while ((int)v->active.size() < v->max_inflight && !v->pending.empty()) {
             SrvReq *r = v->pending.front();
+            if (r->out_bytes) {
+                char *o = v->arena.alloc(r->out_bytes);
+                if (!o) break;
+                r->r.d_rgbT = (float *)o;
+            }
             v->pending.pop_front();
             r->t_admit = now_s();
             v->active.push_back(r);
         }
-        // keep up to kSteps steps enqueued, one per slot
-        while ((int)v->inflight.size() < kSteps && has_unscheduled(v)) {
+        // keep up to n_steps steps enqueued, one per slot
+        while ((int)v->inflight.size() < v->n_steps && has_unscheduled(v)) {
             int si = -1;
-            for (int i = 0; i < kSteps; ++i)
+            for (int i = 0; i < v->n_steps; ++i)
                 if (!v->steps[i].busy) { si = i; break; }
             if (si < 0) break;
             int st = schedule_step(v, si);
@@ -347,7 +460,11 @@ extern "C" GRTX_API int grtx_render_requests(grtx_server *v, const grtx_request 
         st = grtx_server_poll(v, done + *n_done, n - *n_done, &got, 1);
         if (st) return st;
         *n_done += got;
-        if (got == 0 && v->inflight.empty() && v->active.empty() && v->pending.empty() && v->backlog.empty()) break;
+        if (got == 0 && v->inflight.empty() && v->active.empty() && v->backlog.empty()) {
+            if (!v->pending.empty())          // held until outputs are released, which cannot happen here
+                return grtx_fail(GRTX_ERR_BUSY, "requests are held: the output arena is full until outputs are released");
+            break;
+        }
     }
     return GRTX_OK;
 }
@@ -357,6 +474,27 @@ extern "C" GRTX_API int grtx_server_load(const grtx_server *v, int *n_inflight, 
     if (!v) return grtx_fail(GRTX_ERR_INVALID_ARG, "server is NULL");
     if (n_inflight) *n_inflight = (int)v->active.size();
     if (n_pending) *n_pending = (int)v->pending.size();
+    return GRTX_OK;
+}
+
+extern "C" GRTX_API int grtx_server_release(grtx_server *v, float *d_rgbT)
+{
+    if (!v) return grtx_fail(GRTX_ERR_INVALID_ARG, "server is NULL");
+    if (!v->arena.release((char *)d_rgbT)) return grtx_fail(GRTX_ERR_NOT_FOUND, "not a live server-owned output");
+    return GRTX_OK;
+}
+
+extern "C" GRTX_API int grtx_server_get_info(const grtx_server *v, grtx_server_info *info)
+{
+    if (!v || !info) return grtx_fail(GRTX_ERR_INVALID_ARG, "NULL argument");
+    info->n_step_slots = v->n_steps;
+    info->blocks_per_step = v->blocks;
+    info->list_bytes = (int64_t)v->list_bytes;
+    info->arena_bytes = (int64_t)v->arena.bytes;
+    info->arena_used = (int64_t)v->arena.used;
+    info->device_bytes = (int64_t)v->device_bytes;
+    info->n_inflight = (int32_t)v->active.size();
+    info->n_pending = (int32_t)v->pending.size();
     return GRTX_OK;
 }
 

@@ -155,7 +155,13 @@ class grtx_request(C.Structure):
 
 class grtx_completion(C.Structure):
     _fields_ = [("tag", C.c_uint64), ("status", C.c_int32), ("reserved", C.c_int32), ("t_admit", C.c_double),
-                ("t_done", C.c_double)]
+                ("t_done", C.c_double), ("d_rgbT", _fp)]
+
+
+class grtx_server_info(C.Structure):
+    _fields_ = [("n_step_slots", C.c_int32), ("blocks_per_step", C.c_int32), ("list_bytes", C.c_int64),
+                ("arena_bytes", C.c_int64), ("arena_used", C.c_int64), ("device_bytes", C.c_int64),
+                ("n_inflight", C.c_int32), ("n_pending", C.c_int32)]
 
 
 # every symbol declared in include/grtx.h with its ctypes signature
@@ -197,8 +203,10 @@ _SIGS = {
                                       C.c_int] + [_fp] * 11),
     "grtx_composite_bounce": (C.c_int, [_fp, _fp, _fp, _fp, C.c_int64, C.POINTER(C.c_float * 3), _fp]),
     "grtx_trace_forward_noalloc": (C.c_int, [_fp, C.POINTER(grtx_camera), C.POINTER(grtx_params), _fp, _fp]),
-    "grtx_server_create": (C.c_int, [C.POINTER(_fp), C.c_int, C.POINTER(grtx_params), C.c_int64, C.c_int, _fp,
-                                     C.POINTER(_fp)]),
+    "grtx_server_create": (C.c_int, [C.POINTER(_fp), C.c_int, C.POINTER(grtx_params), C.c_int64, C.c_int64, C.c_int,
+                                     _fp, C.POINTER(_fp)]),
+    "grtx_server_release": (C.c_int, [_fp, _fp]),
+    "grtx_server_get_info": (C.c_int, [_fp, C.POINTER(grtx_server_info)]),
     "grtx_server_submit": (C.c_int, [_fp, C.POINTER(grtx_request), C.c_int]),
     "grtx_server_poll": (C.c_int, [_fp, C.POINTER(grtx_completion), C.c_int, C.POINTER(C.c_int), C.c_int]),
     "grtx_render_requests": (C.c_int, [_fp, C.POINTER(grtx_request), C.c_int, C.POINTER(grtx_completion),
@@ -249,6 +257,21 @@ def ptr(t) -> int | None:
     if t is None:
         return None
     return t.data_ptr()
+
+
+class _DeviceArray:
+    """A float32 device array the library owns, exposed through __cuda_array_interface__."""
+
+    def __init__(self, address: int, shape):
+        self.__cuda_array_interface__ = {"shape": tuple(int(x) for x in shape), "typestr": "<f4",
+                                         "data": (int(address), False), "version": 3, "strides": None}
+
+
+def device_view(address: int, shape):
+    """A torch tensor viewing float32 device memory owned by the library (no copy; valid as
+    long as the library keeps the memory)."""
+    import torch
+    return torch.as_tensor(_DeviceArray(address, shape), device="cuda")
 
 
 def stream_handle(stream=None):

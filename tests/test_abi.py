@@ -59,7 +59,9 @@ def test_host_side_argument_errors(lib):
     assert lib.grtx_sort_pairs(None, None, 10, 65, None, C.byref(nb), None) == 1
     assert lib.grtx_radix_tree(None, 1, None, None, None, None) == 1
     assert lib.grtx_server_submit(None, None, 0) == 1
-    assert lib.grtx_server_create(None, 0, None, 0, 0, None, None) == 1
+    assert lib.grtx_server_create(None, 0, None, 0, 0, 0, None, None) == 1
+    assert lib.grtx_server_release(None, None) == 1
+    assert lib.grtx_server_get_info(None, None) == 1
 
 
 def test_host_side_errors_of_the_extensions(lib):

@@ -107,6 +107,102 @@ def test_server_errors(world):
         Server([plain], k=16)
 
 
+# Small list capacities for the budget tests: one 128-ray block of lists is then
+# 128 * (2 * 16 + 32) * 8 = 64 KiB, the size of one 64x64 output (capacity overflows fall back
+# to exact restarts, so the images do not change).
+CAPS = dict(ckpt_capacity=16, evict_capacity=32)
+PER_BLOCK = 128 * (2 * 16 + 32) * 8
+OUT64 = 64 * 64 * 16
+
+
+def _budget_for(n_outputs):
+    """A budget of one block of lists (its half for lists holds one block, not two) and an
+    output arena of n 64x64 outputs plus less than one more (the segment tables of 8 requests
+    take under 8 KiB)."""
+    return PER_BLOCK + n_outputs * OUT64 + 8192
+
+
+def test_memory_budget_holds_requests_until_outputs_are_released(world):
+    """Under a budget whose output arena holds one 64x64 image, server-owned requests are
+    admitted one at a time: the others stay pending while an output is held, and the next is
+    admitted only after release. Every image equals the lone render; the server's device
+    memory never exceeds the budget."""
+    sc, reqs, alone = world
+    budget = _budget_for(1)
+    srv = Server(sc, k=16, mem_budget_bytes=budget, max_inflight=8, **CAPS)
+    inf = srv.info()
+    assert inf["device_bytes"] <= budget and inf["n_step_slots"] == 1 and inf["blocks_per_step"] == 1
+    assert inf["list_bytes"] == PER_BLOCK
+    assert OUT64 <= inf["arena_bytes"] < 2 * OUT64
+    small = [j for j, r in enumerate(reqs) if (r["camera"]["width"], r["camera"]["height"]) == (64, 64)][:4]
+    assert len(small) >= 3
+    srv.submit([(reqs[j]["scene"], reqs[j]["camera"], None, j) for j in small])
+    seen = []
+    while len(seen) < len(small):
+        got = srv.poll(wait=True)
+        inf = srv.info()
+        assert inf["arena_used"] <= inf["arena_bytes"] and inf["n_inflight"] <= 1
+        for c in got:
+            assert c["status"] == 0 and c["d_rgbT"]
+            torch.cuda.synchronize()
+            # held: nothing else is admitted while this output is not released
+            assert srv.poll() == []
+            i2 = srv.info()
+            assert i2["n_inflight"] == 0 and i2["n_pending"] == len(small) - len(seen) - 1
+            _same(alone[c["tag"]], c["rgbT"])
+            seen.append(c["tag"])
+            srv.release(c)
+    assert sorted(seen) == sorted(small)
+    assert srv.info()["arena_used"] == 0
+    srv.close()
+
+
+def test_memory_budget_mixes_owned_and_caller_outputs_and_rejects_oversize(world):
+    """Under a budget whose arena holds two 64x64 outputs: a request larger than the arena is
+    rejected at submission with GRTX_ERR_OOM (nothing queued); requests that bring their own
+    buffer need no arena; owned and caller outputs mixed all give the lone images. Without a
+    budget a server-owned output is an argument error; a budget below one block of lists is
+    rejected at creation."""
+    sc, reqs, alone = world
+    srv = Server(sc, k=16, mem_budget_bytes=_budget_for(2), max_inflight=8, **CAPS)
+    assert 2 * OUT64 <= srv.info()["arena_bytes"] < 3 * OUT64
+    big = next(r for r in reqs if r["camera"]["width"] * r["camera"]["height"] > 3 * 64 * 64)
+    with pytest.raises(N.GrtxError) as e:
+        srv.submit([(big["scene"], big["camera"], None, 99)])
+    assert e.value.status == 2                    # GRTX_ERR_OOM
+    assert srv.load() == (0, 0)
+    bufs = _bufs(reqs)
+    small = {j for j, r in enumerate(reqs) if (r["camera"]["width"], r["camera"]["height"]) == (64, 64)}
+    batch = [(r["scene"], r["camera"], None if j in small else bufs[j], j) for j, r in enumerate(reqs)]
+    srv.submit(batch)
+    done = 0
+    while done < len(reqs):
+        for c in srv.poll(wait=True):
+            assert c["status"] == 0
+            j = c["tag"]
+            torch.cuda.synchronize()
+            _same(alone[j], c["rgbT"] if j in small else bufs[j])
+            if j in small:
+                srv.release(c)
+            done += 1
+    with pytest.raises(N.GrtxError):
+        srv.release(12345)                        # not a live server-owned output
+    srv.close()
+    plain = Server(sc, k=16)
+    with pytest.raises(N.GrtxError) as e:
+        plain.submit([(0, reqs[0]["camera"], None, 0)])
+    assert e.value.status == 1
+    assert plain.info()["n_step_slots"] == 4 and plain.info()["arena_bytes"] == 0
+    plain.close()
+    with pytest.raises(N.GrtxError) as e:
+        Server(sc, k=16, mem_budget_bytes=PER_BLOCK, max_inflight=8, **CAPS)   # half is below a block
+    assert e.value.status == 1
+    big_budget = Server(sc, k=16, mem_budget_bytes=16 << 30)                  # lists of full step slots
+    inf = big_budget.info()
+    assert inf["n_step_slots"] >= 2 and inf["device_bytes"] <= 16 << 30 and inf["arena_bytes"] >= (8 << 30) - (1 << 20)
+    big_budget.close()
+
+
 @pytest.mark.slow
 def test_serving_full_size_sampled_against_oracle():
     """The serving configuration at full size (four resident scenes of 0.5/1/2/3 M Gaussians)
