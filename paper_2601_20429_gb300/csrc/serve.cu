@@ -221,6 +221,7 @@ int schedule_step(grtx_server *v, int si)
     a.ev = a.ck0 + S * 2 * a.ckpt_cap;
     a.queue = v->queue + kQueueStride * si;
     a.n_items = total;
+    a.discard = lists_discardable(a);
     GRTX_CUDA(cudaMemcpyAsync(st.d, st.h, sizeof(ServeSeg) * n, cudaMemcpyHostToDevice, st.s));
     GRTX_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned), st.s));
     if (serve_launch_k(v->p.k, a, st.d, n, v->blocks, st.s) != GRTX_OK) {

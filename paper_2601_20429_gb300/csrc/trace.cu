@@ -232,6 +232,7 @@ int run(grtx_scene *sc, TraceArgs &a, int k, bool instr, int pass, unsigned *que
     a.ev = single ? base : base + (size_t)n_slots * 2 * C;
     a.n_slots = n_slots;
     a.queue = queue;
+    a.discard = single ? 0 : lists_discardable(a);
     GRTX_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned), s));
     int launched = single ? trace_single_launch(a, form, instr, blocks, s)
                           : launch_k(k, a, form, instr, pass, blocks, s);
@@ -430,6 +431,7 @@ extern "C" GRTX_API int grtx_trace_forward_batch(grtx_scene *sc, const grtx_came
     a.n_slots = n_slots;
     a.queue = sc->d_counter + 2;
     a.n_items = total;
+    a.discard = lists_discardable(a);
     ServeSeg *d = nullptr;
     st = grtx_malloc_async((void **)&d, sizeof(ServeSeg) * n_cams, s);
     if (st) return st;

@@ -50,6 +50,7 @@ struct TraceArgs {
     // per-slot workspace, interleaved [entry][slot]
     uint2 *ck0, *ck1, *ev;
     int n_slots;
+    int discard;                 // drop dead list lines from L2 after each tile (lists 256-byte aligned)
     unsigned *queue;
     // outputs
     float4 *rgbT;
@@ -505,7 +506,9 @@ __device__ __forceinline__ bool trace_round(const TraceArgs &a, const SceneRef &
                                             Counters &cnt)
 {
     const size_t S = (size_t)a.n_slots;
-    uint2 stack[GRTX_STACK];
+    // far children deferred within this round: node refs only (4 bytes each); a popped entry
+    // is visited without re-testing its entry depth, since its children meet the t_max test
+    uint32_t stack[GRTX_STACK];
     int sp = 0, si = 0;
     float tmax = kb.tmax;
     uint32_t ref;
@@ -597,7 +600,7 @@ __device__ __forceinline__ bool trace_round(const TraceArgs &a, const SceneRef &
                         if (INSTR) cnt.ckpt++;
                     }
                 } else if (sp < GRTX_STACK) {
-                    stack[sp++] = make_uint2(far_ref, __float_as_uint(far_t));
+                    stack[sp++] = far_ref;
                 } else if (INSTR) {
                     cnt.overflow++;
                 }
@@ -610,9 +613,8 @@ __device__ __forceinline__ bool trace_round(const TraceArgs &a, const SceneRef &
             }
         }
         if (sp > 0) {
-            --sp;
-            ref = stack[sp].x;
-            te = __uint_as_float(stack[sp].y);
+            ref = stack[--sp];
+            te = -GRTX_INF;
         } else if (si < n_src) {
             uint2 v = src[(size_t)si * S];
             ++si;
@@ -811,8 +813,10 @@ __device__ __forceinline__ float atomic_add_f(float *p, float v)
 
 template <bool BWD>
 __device__ __forceinline__ void blend_one(const TraceArgs &a, const SceneRef &sc, BlendState &st, uint32_t idx,
-                                          float3 o, float3 d, float3 dn)
+                                          float3 o, float3 d)
 {
+    const float nrm = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);     // colour along the unit direction
+    const float3 dn = make_float3(d.x * nrm, d.y * nrm, d.z * nrm);
     const float4 *g = sc.geom + 4 * (size_t)idx;
     float t, D2, e[3];
     {
@@ -939,9 +943,7 @@ __device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc
     constexpr bool BWD = PASS == PASS_BWD;
     const size_t S = (size_t)a.n_slots;
     float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
-    float nrm = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
-    float3 dn = make_float3(d.x * nrm, d.y * nrm, d.z * nrm);
-    const float inv_len = nrm;
+    const float inv_len = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
     BlendState st;
     st.C[0] = st.C[1] = st.C[2] = 0.f;
     st.T = 1.f;
@@ -1004,7 +1006,7 @@ __device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc
         }
         for (int j = 0; j < kb.n; ++j) {
             uint32_t idx = kb.I(j);
-            blend_one<BWD>(a, sc, st, idx, o, d, dn);
+            blend_one<BWD>(a, sc, st, idx, o, d);
             if (INSTR) {
                 if (a.ids && nb < a.ids_cap) a.ids[(size_t)pix * a.ids_cap + nb] = sc.gid[idx];
                 cnt.blended++;
@@ -1033,8 +1035,6 @@ __device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc
 __device__ __forceinline__ void backward_from_list(const TraceArgs &a, const SceneRef &sc, int64_t pix, float3 o,
                                                    float3 d, int n)
 {
-    float nrm = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
-    float3 dn = make_float3(d.x * nrm, d.y * nrm, d.z * nrm);
     BlendState st;
     st.C[0] = st.C[1] = st.C[2] = 0.f;
     st.T = 1.f;
@@ -1048,7 +1048,7 @@ __device__ __forceinline__ void backward_from_list(const TraceArgs &a, const Sce
     const uint32_t *list = a.save_leaves + (size_t)pix * a.save_cap;
     for (int j = 0; j < n; ++j) {
         uint32_t idx = list[j];
-        if (idx < sc.n_geom) blend_one<true>(a, sc, st, idx, o, d, dn);   // never read outside the scene
+        if (idx < sc.n_geom) blend_one<true>(a, sc, st, idx, o, d);   // never read outside the scene
     }
 }
 
@@ -1070,7 +1070,6 @@ __device__ __forceinline__ void trace_warp_restart(const TraceArgs &a, const Sce
     }
     float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
     float nrm = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
-    float3 dn = make_float3(d.x * nrm, d.y * nrm, d.z * nrm);
     BlendState st;
     st.C[0] = st.C[1] = st.C[2] = 0.f;
     st.T = 1.f;
@@ -1095,7 +1094,7 @@ __device__ __forceinline__ void trace_warp_restart(const TraceArgs &a, const Sce
         }
         for (int j = 0; j < kb.n; ++j) {
             uint32_t idx = kb.I(j);
-            blend_one<false>(a, sc, st, idx, o, d, dn);
+            blend_one<false>(a, sc, st, idx, o, d);
             if (INSTR) {
                 if (a.ids && nb < a.ids_cap) a.ids[(size_t)pix * a.ids_cap + nb] = sc.gid[idx];
                 cnt.blended++;
@@ -1154,6 +1153,33 @@ __device__ __forceinline__ void trace_warp(const TraceArgs &a, const SceneRef &s
     if (valid) trace_ray<K, FORM, INSTR, PASS>(a, sc, out, slot, pix, o, d, tn, tf, kb, cnt, true, lane_ok, n_dst, n_ev);
 }
 
+// After a tile, every checkpoint and eviction list entry of the warp's 32 ray slots is dead:
+// the next tile writes each entry before it reads it. The lines holding them are dropped from
+// L2 without being written back, so that the lists, written and read once per round, cost no
+// DRAM writes. An entry row of the warp's slots is 32 x 8 = 256 contiguous bytes, two 128-byte
+// lines, aligned because slot counts are multiples of 128 and list bases are 256-byte aligned.
+// The first kDiscardRows rows of each list are dropped (a ray rarely writes more entries per
+// round; a row past that is only written back as before); rows past a list's capacity would
+// belong to the next list or lie past the workspace, and are skipped.
+constexpr int kDiscardRows = 32;
+
+__device__ __forceinline__ void discard_dead_lists(const TraceArgs &a, int warp_slot0)
+{
+    const size_t S = (size_t)a.n_slots;
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < (3 * kDiscardRows * 2) / 32; ++q) {
+        const int l = q * 32 + lane;
+        const int list = l / (2 * kDiscardRows), row = (l % (2 * kDiscardRows)) >> 1, half = l & 1;
+        const uint2 *base = list == 0 ? a.ck0 : (list == 1 ? a.ck1 : a.ev);
+        const int cap = list == 2 ? a.evict_cap : a.ckpt_cap;
+        if (row < cap) {
+            const char *p = reinterpret_cast<const char *>(base + (size_t)row * S + warp_slot0) + 128 * half;
+            asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+        }
+    }
+}
+
 // Resident blocks per SM the trace kernels are compiled for. The traversal is latency-bound,
 // so occupancy pays even at the cost of a few spilled registers (measured on GB300: 8 blocks of
 // 128 threads is the best forward setting for k <= 16; the k = 32 k-buffer's 32 KB of shared
@@ -1192,6 +1218,7 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, PASS == PASS_BWD))
                                              s_pst[threadIdx.x >> 5]);
         if (INSTR) visits_end(a, cnt, pix);
         __syncwarp();
+        if (a.discard) discard_dead_lists(a, slot & ~31);
     }
     if (INSTR && a.stats) {
         unsigned long long v[11] = {rays, cnt.nodes, cnt.leaves, cnt.blended, cnt.rounds, cnt.ckpt, cnt.evictions,
@@ -1244,7 +1271,17 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, false)) k_serve(Tr
             trace_warp<K, FORM_SPHERE, false, PASS_FWD>(a, sc, sg.out, slot, valid, pix, o, d, tn, tf, kb, cnt,
                                                      s_pst[threadIdx.x >> 5]);
         __syncwarp();
+        if (a.discard) discard_dead_lists(a, slot & ~31);
     }
+}
+
+// Whether the lists of a launch may be dropped from L2 per tile (see discard_dead_lists): the
+// checkpointed traversal writes lists, and each list row must start on a 256-byte boundary.
+inline int lists_discardable(const TraceArgs &a)
+{
+    if (a.traversal != GRTX_TRAVERSAL_CHECKPOINT || !a.ck0 || !a.ck1 || !a.ev) return 0;
+    const uintptr_t m = (uintptr_t)a.ck0 | (uintptr_t)a.ck1 | (uintptr_t)a.ev;
+    return (m & 255u) == 0 && (a.n_slots % 32) == 0 && ((size_t)a.n_slots * sizeof(uint2)) % 256 == 0;
 }
 
 // Launch helpers, instantiated per k in the trace_k*.cu units.

@@ -146,6 +146,7 @@ extern "C" GRTX_API int grtx_trace_forward_noalloc(grtx_scene *sc, const grtx_ca
     a.ev = ws + (size_t)n_slots * 2 * C;
     a.n_slots = n_slots;
     a.queue = (unsigned *)base;
+    a.discard = lists_discardable(a);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     // the counter must start at zero; the lists are always written before they are read
     GRTX_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned), s));

@@ -159,8 +159,6 @@ __device__ __forceinline__ void single_ray(const TraceArgs &a, const SceneRef &s
         tn = tf = 0.f;
     }
     float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
-    float nrm = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
-    float3 dn = make_float3(d.x * nrm, d.y * nrm, d.z * nrm);
     uint2 *list = a.ck0 + slot;
     int n = packet_collect<FORM, INSTR>(a, sc, valid, pst, o, d, inv, tn, tf, list, cnt, collected);
     if (!valid) return;
@@ -189,7 +187,7 @@ __device__ __forceinline__ void single_ray(const TraceArgs &a, const SceneRef &s
         if (FORM == FORM_PROXY && key == prev) continue;   // one Gaussian found through several triangles
         prev = key;
         uint32_t idx = top.y;
-        blend_one<false>(a, sc, st, idx, o, d, dn);
+        blend_one<false>(a, sc, st, idx, o, d);
         if (INSTR) {
             if (a.ids && nb < a.ids_cap) a.ids[(size_t)pix * a.ids_cap + nb] = sc.gid[idx];
             cnt.blended++;

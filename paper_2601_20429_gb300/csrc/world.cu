@@ -426,9 +426,7 @@ __device__ __forceinline__ void world_ray(const WorldArgs &W, int slot, int64_t 
             uint32_t gi = key - I.leaf_base;
             float3 oo, od;
             to_object(I, o, d, oo, od);
-            float nrm = rsqrtf(od.x * od.x + od.y * od.y + od.z * od.z);
-            float3 dn = make_float3(od.x * nrm, od.y * nrm, od.z * nrm);
-            blend_one<false>(a, I.sc, st, gi, oo, od, dn);
+            blend_one<false>(a, I.sc, st, gi, oo, od);      // colour along the object-frame direction
             if (INSTR) {
                 if (a.ids && nb < a.ids_cap) a.ids[(size_t)pix * a.ids_cap + nb] = I.id_base + I.sc.gid[gi];
                 cnt.blended++;
