@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-extra", action="store_true", help="skip the differentiable and outdoor measurements")
-    ap.add_argument("--section", choices=["differentiable", "outdoor", "outdoor-primary", "serving"], default=None,
+    ap.add_argument("--section", choices=["differentiable", "outdoor", "outdoor-primary", "serving", "serving-capacity"],
+                    default=None,
                     help="run one measurement section alone and print its JSON (for profiling; 1 GPU)")
     return ap.parse_args()
 
@@ -363,24 +364,14 @@ def traversal_modes_on_views(gpu_scenes, reqs, per_scene: int = 20) -> dict:
     return res
 
 
-def bench_serving(n_requests: int, max_rays_per_step: int = 4 << 20, max_inflight: int = 64,
-                  traversal: str = "checkpoint", modes: bool = False):
+def run_stream(srv, reqs, rate_hz: float) -> dict:
+    """Replay a request stream against a server in real time: each request is submitted at its
+    arrival time (or as soon as an output buffer is free), completions are polled without
+    blocking. Latency = completion - arrival."""
     import torch
-    from paper_2601_20429_gb300 import render as R
-    from paper_2601_20429_gb300 import scenes
-    from paper_2601_20429_gb300.serve import Server
-    scs, reqs, cfg = scenes.config_serving(n_requests=n_requests)
-    gpu_scenes = [R.Scene.from_params(g) for g in scs]
-    del scs
-    srv = Server(gpu_scenes, k=cfg["k"], traversal=traversal, max_rays_per_step=max_rays_per_step,
-                 max_inflight=max_inflight)
     max_px = 1920 * 1080
-    n_buffers = min(80, max(16, n_requests // 4))          # output buffers in flight
+    n_buffers = min(80, max(16, len(reqs) // 4))          # output buffers in flight
     pool = deque(torch.empty((max_px, 4), dtype=torch.float32, device="cuda") for _ in range(n_buffers))
-    # warm-up: a few requests of each size
-    warm = [(j % 4, reqs[j]["camera"], pool[j], 10 ** 9 + j) for j in range(8)]
-    srv.render_requests(warm)
-    torch.cuda.synchronize()
     n = len(reqs)
     lat = [None] * n
     busy = {}
@@ -388,7 +379,6 @@ def bench_serving(n_requests: int, max_rays_per_step: int = 4 << 20, max_infligh
     i = 0
     waiting = deque()
     done_n = 0
-    t_first = None
     t_last = 0.0
     while done_n < n:
         now = time.monotonic() - t0
@@ -412,19 +402,59 @@ def bench_serving(n_requests: int, max_rays_per_step: int = 4 << 20, max_infligh
             done_n += 1
         if not got and not batch:
             time.sleep(0.0002)
-    rays = sum(reqs[j]["camera"]["width"] * reqs[j]["camera"]["height"] for j in range(n))
+    rays = sum(r["camera"]["width"] * r["camera"]["height"] for r in reqs)
     makespan = t_last - reqs[0]["arrival"]
     lat_ms = np.array(lat) * 1e3
-    srv.close()
-    mode_rates = traversal_modes_on_views(gpu_scenes, reqs) if modes else None
-    for s in gpu_scenes:
-        s.close()
-    return {"requests": n, "rate_hz": 200.0, "p50_ms": float(np.percentile(lat_ms, 50)),
-            "traversal_modes_Mrays_per_s": mode_rates,
+    return {"requests": n, "rate_hz": rate_hz, "p50_ms": float(np.percentile(lat_ms, 50)),
             "p99_ms": float(np.percentile(lat_ms, 99)), "mean_ms": float(lat_ms.mean()),
             "Mrays_per_s": rays / makespan / 1e6, "makespan_s": makespan,
-            "offered_Mrays_per_s": rays / (reqs[-1]["arrival"] - reqs[0]["arrival"]) / 1e6,
-            "max_rays_per_step": max_rays_per_step, "max_inflight": max_inflight, "traversal": traversal}
+            "offered_Mrays_per_s": rays / (reqs[-1]["arrival"] - reqs[0]["arrival"]) / 1e6}
+
+
+def bench_serving(n_requests: int, max_rays_per_step: int = 4 << 20, max_inflight: int = 64,
+                  modes: bool = False, restart: bool = False, capacity_rates=(), capacity_requests: int = 1000):
+    """The serving configuration: four resident scenes, the 200 req/s stream through the
+    server (checkpointed rounds); optionally the same stream with restart traversal, the
+    traversal modes on the requests' views, and a capacity sweep: the same views arriving
+    at higher rates (capacity_requests of them per rate)."""
+    import torch
+    from paper_2601_20429_gb300 import render as R
+    from paper_2601_20429_gb300 import scenes
+    from paper_2601_20429_gb300.serve import Server
+    scs, reqs, cfg = scenes.config_serving(n_requests=n_requests)
+    gpu_scenes = [R.Scene.from_params(g) for g in scs]
+    del scs
+
+    def server(traversal):
+        srv = Server(gpu_scenes, k=cfg["k"], traversal=traversal, max_rays_per_step=max_rays_per_step,
+                     max_inflight=max_inflight)
+        # warm-up: a few requests of each size
+        warm = [torch.empty((1920 * 1080, 4), dtype=torch.float32, device="cuda") for _ in range(8)]
+        srv.render_requests([(j % 4, reqs[j]["camera"], warm[j], 10 ** 9 + j) for j in range(8)])
+        torch.cuda.synchronize()
+        return srv
+
+    srv = server("checkpoint")
+    res = run_stream(srv, reqs, 200.0)
+    res.update(max_rays_per_step=max_rays_per_step, max_inflight=max_inflight, traversal="checkpoint")
+    if capacity_rates:
+        sweep = []
+        for rate in capacity_rates:
+            r = run_stream(srv, scenes.serving_stream_at(rate, n_requests=capacity_requests), rate)
+            sweep.append(r)
+        res["capacity_sweep"] = sweep
+        ok = [r["rate_hz"] for r in [res] + sweep
+              if r["Mrays_per_s"] >= 0.98 * r["offered_Mrays_per_s"] and r["p99_ms"] <= 100.0]
+        res["capacity_rate_hz"] = max(ok) if ok else None
+    srv.close()
+    if restart:
+        srv = server("restart")
+        res["restart_traversal"] = dict(run_stream(srv, reqs, 200.0), traversal="restart")
+        srv.close()
+    res["traversal_modes_Mrays_per_s"] = traversal_modes_on_views(gpu_scenes, reqs) if modes else None
+    for s in gpu_scenes:
+        s.close()
+    return res
 
 
 def bench_differentiable(steps: int, warmup: int, stream):
@@ -639,6 +669,8 @@ def main():
             res = bench_differentiable(args.steps, args.warmup, stream)
         elif args.section == "serving":
             res = bench_serving(args.serve_requests)
+        elif args.section == "serving-capacity":
+            res = bench_serving(args.serve_requests, capacity_rates=(250.0, 300.0, 350.0, 400.0, 450.0, 500.0))
         else:
             flush_buf = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
             res = bench_outdoor(args.steps, stream, lambda: flush_buf.fill_(1),
@@ -759,9 +791,8 @@ def main():
 
     serving = None
     if dist.world == 1 and not args.no_serving:
-        serving = bench_serving(args.serve_requests, modes=not args.no_extra)
-        if not args.no_extra:
-            serving["restart_traversal"] = bench_serving(args.serve_requests, traversal="restart")
+        serving = bench_serving(args.serve_requests, modes=not args.no_extra, restart=not args.no_extra,
+                                capacity_rates=() if args.no_extra else (250.0, 300.0, 350.0, 400.0))
 
     differentiable = outdoor = ablations = None
     if dist.world == 1 and not args.no_extra:
@@ -789,6 +820,7 @@ def main():
             "plain_nodes_per_ray": nodes_per_ray(st_plain)["total"],
             "serving_p50_ms": serving["p50_ms"] if serving else None,
             "serving_p99_ms": serving["p99_ms"] if serving else None,
+            "serving_capacity_rate_hz": serving.get("capacity_rate_hz") if serving else None,
             "config": {"workload": "surface-like scene: 1M Gaussians on 200 spheres/patches, SH degree 3; "
                                    "1920x1080 pinhole at (0,0,-4); k=16, alpha_min=0.01, T_min=1e-3",
                        "step": "one frame traced on the resident scene (BVH built once, timed separately)",

@@ -298,6 +298,16 @@ def config_serving(sizes=(500_000, 1_000_000, 2_000_000, 3_000_000), n_requests:
     return scenes, reqs, dict(k=16, alpha_min=0.01, T_min=1e-3)
 
 
+def serving_stream_at(rate_hz: float, n_requests: int = 2000, n_scenes: int = 4):
+    """The serving configuration's request stream (same seed, resolutions and poses) with
+    Poisson arrivals at another rate: the views are those of the 200 req/s stream, only the
+    gaps between arrivals scale by 200 / rate_hz."""
+    reqs = request_stream(n_requests=n_requests, rate_hz=200.0, n_scenes=n_scenes, seed=4)
+    for r in reqs:
+        r["arrival"] *= 200.0 / rate_hz
+    return reqs
+
+
 def outdoor_mirror(seed: int = 2, cam_pos=(0.0, 1.7, 0.0), view=(1.0, 0.0, 0.0)) -> dict:
     """A 4 x 3 m rectangular mirror at a seeded pose in front of the camera: centre 5-15 m away
     within +-30 degrees of the view direction at a height of 1.5-2.5 m, facing back towards
