@@ -221,6 +221,7 @@ int schedule_step(grtx_server *v, int si)
     a.ev = a.ck0 + S * 2 * a.ckpt_cap;
     a.queue = v->queue + kQueueStride * si;
     a.n_items = total;
+    set_list_offsets(a, 2 * (size_t)a.ckpt_cap + (size_t)a.evict_cap);   // size checked at creation
     a.discard = lists_discardable(a);
     GRTX_CUDA(cudaMemcpyAsync(st.d, st.h, sizeof(ServeSeg) * n, cudaMemcpyHostToDevice, st.s));
     GRTX_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned), st.s));
@@ -272,6 +273,8 @@ extern "C" GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scen
     // tables and queue counters, and (under a budget) the output arena
     const size_t per_block = 128 * (2 * C + E) * sizeof(uint2);
     const int blocks_full = sms * bps;
+    if ((size_t)blocks_full * 128 * (2 * C + E) >= ((size_t)1 << 31))
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "checkpoint/eviction capacities too large for the resident ray slots");
     const size_t tables = kSteps * kQueueStride * sizeof(unsigned) + (size_t)kSteps * sizeof(ServeSeg) * inflight_cap;
     int n_steps = kSteps, blocks = blocks_full;
     size_t arena = 0;

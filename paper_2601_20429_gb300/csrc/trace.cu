@@ -232,6 +232,8 @@ int run(grtx_scene *sc, TraceArgs &a, int k, bool instr, int pass, unsigned *que
     a.ev = single ? base : base + (size_t)n_slots * 2 * C;
     a.n_slots = n_slots;
     a.queue = queue;
+    if (!set_list_offsets(a, per_slot))
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "checkpoint/eviction capacities too large for the resident ray slots");
     a.discard = single ? 0 : lists_discardable(a);
     GRTX_CUDA(cudaMemsetAsync(queue, 0, sizeof(unsigned), s));
     int launched = single ? trace_single_launch(a, form, instr, blocks, s)
@@ -431,6 +433,8 @@ extern "C" GRTX_API int grtx_trace_forward_batch(grtx_scene *sc, const grtx_came
     a.n_slots = n_slots;
     a.queue = sc->d_counter + 2;
     a.n_items = total;
+    if (!set_list_offsets(a, 2 * C + E))
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "checkpoint/eviction capacities too large for the resident ray slots");
     a.discard = lists_discardable(a);
     ServeSeg *d = nullptr;
     st = grtx_malloc_async((void **)&d, sizeof(ServeSeg) * n_cams, s);

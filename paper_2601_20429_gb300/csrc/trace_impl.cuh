@@ -47,8 +47,11 @@ struct TraceArgs {
     float bg0, bg1, bg2;
     int ckpt_cap, evict_cap;
     int packet_stack;            // warp-stack entries a packet may use (1..kPacketStack)
-    // per-slot workspace, interleaved [entry][slot]
+    // per-slot workspace, interleaved [entry][slot]; the kernels address every list entry as
+    // ck0[offset] with a 32-bit offset (ck1 = ck0 + ck1_off, ev = ck0 + ev_off; the host checks
+    // that the whole workspace has fewer than 2^31 entries)
     uint2 *ck0, *ck1, *ev;
+    uint32_t ck1_off, ev_off;
     int n_slots;
     int discard;                 // drop dead list lines from L2 after each tile (lists 256-byte aligned)
     unsigned *queue;
@@ -501,11 +504,11 @@ template <int K, int FORM, bool INSTR>
 __device__ __forceinline__ bool trace_round(const TraceArgs &a, const SceneRef &sc, float3 o, float3 d, float3 inv,
                                             float inv_len, float tn, float tf,
                                             float Lt, uint32_t Li, bool ckpt, bool from_root,
-                                            const uint2 *__restrict__ src, int n_src, uint2 *__restrict__ dst,
-                                            int &n_dst, uint2 *__restrict__ ev, int &n_ev, KBuf<K> &kb,
-                                            Counters &cnt)
+                                            uint32_t src, int n_src, uint32_t dst, int &n_dst, uint32_t ev,
+                                            int &n_ev, KBuf<K> &kb, Counters &cnt)
 {
-    const size_t S = (size_t)a.n_slots;
+    const uint32_t S = (uint32_t)a.n_slots;
+    uint2 *__restrict__ const L = a.ck0;      // lists: src, dst and ev are entry offsets into L
     // far children deferred within this round: node refs only (4 bytes each); a popped entry
     // is visited without re-testing its entry depth, since its children meet the t_max test
     uint32_t stack[GRTX_STACK];
@@ -520,7 +523,7 @@ __device__ __forceinline__ bool trace_round(const TraceArgs &a, const SceneRef &
         te = tn;
     } else {
         if (n_src == 0) return true;
-        uint2 v = src[0];
+        uint2 v = L[src];
         ref = v.x;
         te = __uint_as_float(v.y);
         si = 1;
@@ -529,7 +532,7 @@ __device__ __forceinline__ bool trace_round(const TraceArgs &a, const SceneRef &
         if (te > tmax) {                              // fails the t_max test
             if (ckpt) {
                 if (n_dst >= a.ckpt_cap) return false;
-                dst[(size_t)n_dst * S] = make_uint2(ref, __float_as_uint(te));
+                L[dst + (uint32_t)n_dst * S] = make_uint2(ref, __float_as_uint(te));
                 ++n_dst;
                 if (INSTR) cnt.ckpt++;
             }
@@ -559,7 +562,7 @@ __device__ __forceinline__ bool trace_round(const TraceArgs &a, const SceneRef &
                         uint32_t ci = gi;
                         if (kb.insert(ct, ci) && ckpt) {       // any-hit: rejected -> eviction list
                             if (n_ev >= a.evict_cap) return false;
-                            ev[(size_t)n_ev * S] = make_uint2(__float_as_uint(ct), ci);
+                            L[ev + (uint32_t)n_ev * S] = make_uint2(__float_as_uint(ct), ci);
                             ++n_ev;
                             if (INSTR) cnt.evictions++;
                         }
@@ -595,7 +598,7 @@ __device__ __forceinline__ bool trace_round(const TraceArgs &a, const SceneRef &
                 if (far_t > tmax) {
                     if (ckpt) {
                         if (n_dst >= a.ckpt_cap) return false;
-                        dst[(size_t)n_dst * S] = make_uint2(far_ref, __float_as_uint(far_t));
+                        L[dst + (uint32_t)n_dst * S] = make_uint2(far_ref, __float_as_uint(far_t));
                         ++n_dst;
                         if (INSTR) cnt.ckpt++;
                     }
@@ -616,7 +619,7 @@ __device__ __forceinline__ bool trace_round(const TraceArgs &a, const SceneRef &
             ref = stack[--sp];
             te = -GRTX_INF;
         } else if (si < n_src) {
-            uint2 v = src[(size_t)si * S];
+            uint2 v = L[src + (uint32_t)si * S];
             ++si;
             ref = v.x;
             te = __uint_as_float(v.y);
@@ -648,12 +651,13 @@ constexpr int kPacketStack = GRTX_PACKET_STACK;
 template <int K, int FORM, bool INSTR>
 __device__ __forceinline__ bool packet_round(const TraceArgs &a, const SceneRef &sc, bool valid, uint4 *pst, float3 o,
                                              float3 d, float3 inv, float inv_len, float tn, float tf, float Lt,
-                                             uint32_t Li, bool ckpt, uint2 *__restrict__ dst, int &n_dst,
-                                             uint2 *__restrict__ ev, int &n_ev, KBuf<K> &kb, Counters &cnt,
+                                             uint32_t Li, bool ckpt, uint32_t dst, int &n_dst,
+                                             uint32_t ev, int &n_ev, KBuf<K> &kb, Counters &cnt,
                                              bool &lane_ok)
 {
     const unsigned full = 0xffffffffu;
-    const size_t S = (size_t)a.n_slots;
+    const uint32_t S = (uint32_t)a.n_slots;
+    uint2 *__restrict__ const L = a.ck0;      // lists: dst and ev are entry offsets into L
     const int lane = threadIdx.x & 31;
     float tmax = kb.tmax;
     n_dst = 0;
@@ -684,7 +688,7 @@ __device__ __forceinline__ bool packet_round(const TraceArgs &a, const SceneRef 
             if (n_dst >= a.ckpt_cap) {
                 lane_ok = false;
             } else {
-                dst[(size_t)n_dst * S] = make_uint2(ref, __float_as_uint(te));
+                L[dst + (uint32_t)n_dst * S] = make_uint2(ref, __float_as_uint(te));
                 ++n_dst;
                 if (INSTR) cnt.ckpt++;
             }
@@ -719,7 +723,7 @@ __device__ __forceinline__ bool packet_round(const TraceArgs &a, const SceneRef 
                             if (n_ev >= a.evict_cap) {
                                 lane_ok = false;
                             } else {
-                                ev[(size_t)n_ev * S] = make_uint2(__float_as_uint(ct), ci);
+                                L[ev + (uint32_t)n_ev * S] = make_uint2(__float_as_uint(ct), ci);
                                 ++n_ev;
                                 if (INSTR) cnt.evictions++;
                             }
@@ -941,7 +945,7 @@ __device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc
                                           int r1_n_ev = 0)
 {
     constexpr bool BWD = PASS == PASS_BWD;
-    const size_t S = (size_t)a.n_slots;
+    const uint32_t S = (uint32_t)a.n_slots;
     float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
     const float inv_len = rsqrtf(d.x * d.x + d.y * d.y + d.z * d.z);
     BlendState st;
@@ -961,7 +965,8 @@ __device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc
     bool ckpt = a.traversal == GRTX_TRAVERSAL_CHECKPOINT;
     bool from_root = true;
     int n_src = 0, n_ev = 0, nb = 0;
-    uint2 *src = a.ck0 + slot, *dst = a.ck1 + slot, *ev = a.ev + slot;
+    uint32_t src = (uint32_t)slot, dst = a.ck1_off + (uint32_t)slot;      // entry offsets into a.ck0
+    const uint32_t ev = a.ev_off + (uint32_t)slot;
     bool done = !sc.has_tree;
     bool first_round = true;
     while (!done) {
@@ -970,14 +975,14 @@ __device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc
         if (ckpt && n_ev > 0) {            // raygen: closest evicted hits -> k-buffer
             int w = 0;
             for (int e = 0; e < n_ev; ++e) {
-                uint2 v = ev[(size_t)e * S];
+                uint2 v = a.ck0[ev + (uint32_t)e * S];
                 float ct = __uint_as_float(v.x);
                 uint32_t ci = v.y;
                 // the proxy form can find one Gaussian through several triangles, so an evicted
                 // copy may already be blended (key <= L) or already be in the buffer
                 if (FORM == FORM_PROXY && (!key_after(ct, ci, Lt, Li) || kb.contains(ct, ci))) continue;
                 if (kb.insert(ct, ci)) {
-                    ev[(size_t)w * S] = make_uint2(__float_as_uint(ct), ci);
+                    a.ck0[ev + (uint32_t)w * S] = make_uint2(__float_as_uint(ct), ci);
                     ++w;
                 }
             }
@@ -1020,7 +1025,7 @@ __device__ __forceinline__ void trace_ray(const TraceArgs &a, const SceneRef &sc
         Lt = kb.T(K - 1);
         Li = kb.I(K - 1);
         if (ckpt) {
-            uint2 *tmp = src; src = dst; dst = tmp;
+            uint32_t tmp = src; src = dst; dst = tmp;
             n_src = n_dst;
             from_root = false;
         }
@@ -1084,13 +1089,13 @@ __device__ __forceinline__ void trace_warp_restart(const TraceArgs &a, const Sce
         }
         int n_dst = 0, n_ev = 0;
         bool lane_ok = true;
-        packet_round<K, FORM, INSTR>(a, sc, !done, pst, o, d, inv, nrm, tn, tf, Lt, Li, false, nullptr, n_dst, nullptr,
-                                     n_ev, kb, cnt, lane_ok);
+        packet_round<K, FORM, INSTR>(a, sc, !done, pst, o, d, inv, nrm, tn, tf, Lt, Li, false, 0u, n_dst, 0u, n_ev,
+                                     kb, cnt, lane_ok);
         if (done) continue;
         if (!lane_ok) {
             kb.clear();
-            trace_round<K, FORM, INSTR>(a, sc, o, d, inv, nrm, tn, tf, Lt, Li, false, true, nullptr, 0, nullptr, n_dst,
-                                        nullptr, n_ev, kb, cnt);
+            trace_round<K, FORM, INSTR>(a, sc, o, d, inv, nrm, tn, tf, Lt, Li, false, true, 0u, 0, 0u, n_dst, 0u, n_ev,
+                                        kb, cnt);
         }
         for (int j = 0; j < kb.n; ++j) {
             uint32_t idx = kb.I(j);
@@ -1146,8 +1151,8 @@ __device__ __forceinline__ void trace_warp(const TraceArgs &a, const SceneRef &s
     int n_dst = 0, n_ev = 0;
     bool lane_ok = true;
     packet_round<K, FORM, INSTR>(a, sc, valid, pst, o, d, inv, inv_len, tn, tf, tn, GRTX_NONE,
-                                 a.traversal == GRTX_TRAVERSAL_CHECKPOINT, a.ck1 + slot, n_dst, a.ev + slot, n_ev, kb,
-                                 cnt, lane_ok);
+                                 a.traversal == GRTX_TRAVERSAL_CHECKPOINT, a.ck1_off + (uint32_t)slot, n_dst,
+                                 a.ev_off + (uint32_t)slot, n_ev, kb, cnt, lane_ok);
     // a lane whose packet could not finish (lists or the warp's stack overflowed) redoes round 1
     // from the root on its own, as after any capacity overflow
     if (valid) trace_ray<K, FORM, INSTR, PASS>(a, sc, out, slot, pix, o, d, tn, tf, kb, cnt, true, lane_ok, n_dst, n_ev);
@@ -1273,6 +1278,16 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, false)) k_serve(Tr
         __syncwarp();
         if (a.discard) discard_dead_lists(a, slot & ~31);
     }
+}
+
+// Entry offsets of the lists relative to ck0 (the kernels index every list entry with 32 bits);
+// false if the workspace is too large for that. Call after ck0, ck1, ev and n_slots are set.
+inline bool set_list_offsets(TraceArgs &a, size_t entries_per_slot)
+{
+    if ((size_t)a.n_slots * entries_per_slot >= ((size_t)1 << 31)) return false;
+    a.ck1_off = (uint32_t)(a.ck1 - a.ck0);
+    a.ev_off = (uint32_t)(a.ev - a.ck0);
+    return true;
 }
 
 // Whether the lists of a launch may be dropped from L2 per tile (see discard_dead_lists): the

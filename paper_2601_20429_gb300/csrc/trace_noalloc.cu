@@ -146,6 +146,7 @@ extern "C" GRTX_API int grtx_trace_forward_noalloc(grtx_scene *sc, const grtx_ca
     a.ev = ws + (size_t)n_slots * 2 * C;
     a.n_slots = n_slots;
     a.queue = (unsigned *)base;
+    set_list_offsets(a, 2 * C + E);          // the fixed scratch holds far fewer than 2^31 entries
     a.discard = lists_discardable(a);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     // the counter must start at zero; the lists are always written before they are read
