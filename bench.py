@@ -311,6 +311,20 @@ def bench_surface_ablations(g, sc, cam, k: int, steps: int, stream, flush) -> di
         res[form] = {"Mrays_per_s": mrays(n_rays, t), "ms_per_frame": statistics.mean(t),
                      "nodes_per_ray": nodes_per_ray(st), "template_triangles": 20 if form == "ico20" else 80}
         sc_i.close()
+    # 4-wide nodes: the clustering-built binary tree collapsed into 4-wide nodes (the paper
+    # traverses a 6-wide BVH, Sec. V-A)
+    t0 = time.perf_counter()
+    sc_w = R.Scene.from_params(g, bvh_width=4)
+    torch.cuda.synchronize()
+    build_w = (time.perf_counter() - t0) * 1e3
+    st = N.stats_dict(R.render(sc_w, cam, k=k, out=out, want_stats=True, bvh_width=4)["stats"])
+    t = time_frames(lambda: R.render(sc_w, cam, k=k, out=out, bvh_width=4), steps, 2, flush, stream)
+    tr = time_frames(lambda: R.render(sc_w, cam, k=k, out=out, bvh_width=4, traversal="restart"), steps, 2, flush,
+                     stream)
+    res["bvh4"] = {"Mrays_per_s": mrays(n_rays, t), "ms_per_frame": statistics.mean(t),
+                   "restart_Mrays_per_s": mrays(n_rays, tr), "nodes_per_ray": nodes_per_ray(st),
+                   "build_ms": build_w, "node_bytes": 128}
+    sc_w.close()
     for name, codes, builder in (("lbvh_sized_codes", "sized", "lbvh"), ("lbvh_centroid_codes", "centroid", "lbvh")):
         t0 = time.perf_counter()
         sc_c = R.Scene.from_params(g, bvh_codes=codes, bvh_builder=builder)
@@ -591,6 +605,7 @@ def bench_outdoor(steps: int, stream, flush, primary_only: bool = False):
     build_ms = (time.perf_counter() - t0) * 1e3
     sc_c = None if primary_only else R.Scene.from_params(g, bvh_codes="centroid", bvh_builder="lbvh")
     sc_l = None if primary_only else R.Scene.from_params(g, bvh_builder="lbvh")
+    sc_w = R.Scene.from_params(g, bvh_width=4)
     del g
     n = cam["width"] * cam["height"]
     prim = [torch.empty((n, 3), device="cuda"), torch.empty((n, 3), device="cuda"), torch.empty(n, device="cuda"),
@@ -606,6 +621,12 @@ def bench_outdoor(steps: int, stream, flush, primary_only: bool = False):
     out_p = torch.empty((n, 4), device="cuda")
     out_s = torch.empty((max(m, 1), 4), device="cuda")
     tp = time_frames(lambda: R.render(sc, cam, rays=prim, k=cfg["k"], out=out_p), steps, 2, flush, stream)
+    tw = time_frames(lambda: R.render(sc_w, cam, rays=prim, k=cfg["k"], out=out_p, bvh_width=4), steps, 2, flush,
+                     stream)
+    st_w = N.stats_dict(R.render(sc_w, cam, rays=prim, k=cfg["k"], want_stats=True, bvh_width=4)["stats"])
+    sc_w.close()
+    wide = {"Mrays_per_s": n / (statistics.mean(tw) / 1e3) / 1e6, "ms": statistics.mean(tw),
+            "nodes_per_ray": nodes_per_ray(st_w)}
     if primary_only:
         st_p = N.stats_dict(R.render(sc, cam, rays=prim, k=cfg["k"], want_stats=True)["stats"])
         depth = sc.info()["depth"]
@@ -613,7 +634,7 @@ def bench_outdoor(steps: int, stream, flush, primary_only: bool = False):
         return {"workload": "6M outdoor Gaussians, 1920x1080 equidistant fisheye primary rays, k=16",
                 "build_ms": build_ms, "depth": depth,
                 "primary": {"Mrays_per_s": n / (statistics.mean(tp) / 1e3) / 1e6, "ms": statistics.mean(tp),
-                            "nodes_per_ray": nodes_per_ray(st_p)}}
+                            "nodes_per_ray": nodes_per_ray(st_p)}, "primary_bvh4": wide}
     tp32 = time_frames(lambda: R.render(sc, cam, rays=prim, k=32, out=out_p), steps, 2, flush, stream)
     st_p32 = N.stats_dict(R.render(sc, cam, rays=prim, k=32, want_stats=True)["stats"])
     ts = time_frames(lambda: R.render(sc, None, rays=sec_rays, k=cfg["k"], out=out_s), steps, 2, flush, stream)
@@ -641,6 +662,7 @@ def bench_outdoor(steps: int, stream, flush, primary_only: bool = False):
                                  "ms": statistics.mean(tf),
                                  "ms_as_two_launches": statistics.mean(tp) + statistics.mean(ts)},
             "depth": depth,
+            "primary_bvh4": wide,
             "primary_k32": {"Mrays_per_s": n / (statistics.mean(tp32) / 1e3) / 1e6, "ms": statistics.mean(tp32),
                             "nodes_per_ray": nodes_per_ray(st_p32)},
             "primary_lbvh_sized_codes": {"Mrays_per_s": n / (statistics.mean(tl) / 1e3) / 1e6,

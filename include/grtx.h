@@ -121,7 +121,14 @@ enum { GRTX_TRAVERSAL_CHECKPOINT = 0, /* resume from checkpointed nodes + evicti
  * codes, grtx_radix_tree). The tree shape changes the cost of a trace, never its result.
  * packet_stack: entries of the per-warp stack that a warp-packet traversal may use (0: all
  * GRTX_PACKET_STACK); a packet that would need more falls back to tracing its rays one by
- * one, with the same result. Smaller values exist to exercise that fallback. */
+ * one, with the same result. Smaller values exist to exercise that fallback.
+ * bvh_width (the paper traverses a 6-wide BVH, Sec. V-A): 0 or 2, binary nodes; 4, the build
+ * of a sphere-form scene also collapses the binary tree into 4-wide nodes (each binary node at
+ * even depth becomes a node over its grandchildren, 128 bytes: lo x, lo y, lo z, hi x, hi y,
+ * hi z of the four children as float4 rows, then the four child refs, then padding), and
+ * grtx_trace_forward with bvh_width 4 traverses them (checkpoint or restart traversal, no
+ * saved lists; GRTX_ERR_INVALID_ARG on a scene built without them). Every other entry point
+ * traverses the binary nodes. The image does not depend on the width. */
 #define GRTX_PACKET_STACK 64
 enum { GRTX_CODES_SIZED = 0, GRTX_CODES_CENTROID = 1 };
 enum { GRTX_BUILDER_PLOC = 0, GRTX_BUILDER_LBVH = 1 };
@@ -138,6 +145,7 @@ typedef struct grtx_params {
     int32_t bvh_codes;
     int32_t bvh_builder;
     int32_t packet_stack;
+    int32_t bvh_width;
 } grtx_params;
 
 enum { GRTX_CAMERA_PINHOLE = 0, GRTX_CAMERA_FISHEYE = 1, GRTX_CAMERA_RAYS = 2 };

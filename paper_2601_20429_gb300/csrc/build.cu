@@ -507,6 +507,90 @@ __global__ void k_emit_nodes(const uint32_t *__restrict__ left, const uint32_t *
     nodes[4 * (size_t)i + 3] = make_float4(__uint_as_float(L), __uint_as_float(R), s0, s1);
 }
 
+// ------------------------------------------------------------------------------------------
+// 4-wide nodes (bvh_width 4; the paper traverses a 6-wide BVH, Sec. V-A): every binary node at
+// even depth becomes a node over its grandchildren (a child that is a leaf is kept as a leaf),
+// so the 4-wide tree has half the depth and the same leaves. Node layout, 8 float4: lo x, lo y,
+// lo z, hi x, hi y, hi z of the four children, the four child refs (bit 31: leaf slot; else a
+// 4-wide node index; GRTX_NONE: empty, with an empty box), padding.
+// ------------------------------------------------------------------------------------------
+__global__ void k_bin_parents(const float4 *__restrict__ nodes, int n_int, uint32_t *__restrict__ parent)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_int) return;
+    const float4 r = nodes[4 * (size_t)i + 3];
+    const uint32_t c[2] = {__float_as_uint(r.x), __float_as_uint(r.y)};
+    for (int j = 0; j < 2; ++j)
+        if (c[j] != GRTX_NONE && !(c[j] & GRTX_LEAF) && c[j] < (uint32_t)n_int) parent[c[j]] = (uint32_t)i;
+}
+
+__global__ void k_even_depth(const uint32_t *__restrict__ parent, int n_int, uint32_t *__restrict__ flag)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_int) return;
+    int d = 0;
+    uint32_t node = (uint32_t)i;
+    while (parent[node] != GRTX_NONE && d < (1 << 20)) {
+        node = parent[node];
+        ++d;
+    }
+    flag[i] = (d & 1) == 0;
+}
+
+__global__ void k_emit_nodes4(const float4 *__restrict__ nodes, int n_int, const uint32_t *__restrict__ flag,
+                              const uint32_t *__restrict__ idx, float4 *__restrict__ nodes4)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_int || !flag[i]) return;
+    float b[6][4];
+    uint32_t ref[4];
+    for (int j = 0; j < 4; ++j) {
+        b[0][j] = b[1][j] = b[2][j] = __int_as_float(0x7f800000);      // empty box: lo = +inf,
+        b[3][j] = b[4][j] = b[5][j] = __int_as_float(0xff800000);      // hi = -inf
+        ref[j] = GRTX_NONE;
+    }
+    int m = 0;
+    // child c of binary node nd: its box (lo xyz, hi xyz) and ref
+    auto child = [&](uint32_t nd, int c, float box[6], uint32_t &r) {
+        const float4 n0 = nodes[4 * (size_t)nd], n1 = nodes[4 * (size_t)nd + 1], n2 = nodes[4 * (size_t)nd + 2];
+        const float4 n3 = nodes[4 * (size_t)nd + 3];
+        if (c == 0) {
+            box[0] = n0.x; box[1] = n0.y; box[2] = n0.z; box[3] = n0.w; box[4] = n1.x; box[5] = n1.y;
+            r = __float_as_uint(n3.x);
+        } else {
+            box[0] = n1.z; box[1] = n1.w; box[2] = n2.x; box[3] = n2.y; box[4] = n2.z; box[5] = n2.w;
+            r = __float_as_uint(n3.y);
+        }
+    };
+    auto add = [&](const float box[6], uint32_t r) {
+        for (int k = 0; k < 6; ++k) b[k][m] = box[k];
+        ref[m] = r;
+        ++m;
+    };
+    for (int c = 0; c < 2; ++c) {
+        float box[6];
+        uint32_t r;
+        child((uint32_t)i, c, box, r);
+        if (r == GRTX_NONE) continue;
+        if (r & GRTX_LEAF) {
+            add(box, r);
+            continue;
+        }
+        for (int g = 0; g < 2; ++g) {                // grandchildren: at even depth again
+            float gb[6];
+            uint32_t gr;
+            child(r, g, gb, gr);
+            if (gr == GRTX_NONE) continue;
+            add(gb, (gr & GRTX_LEAF) ? gr : idx[gr]);
+        }
+    }
+    float4 *out = nodes4 + 8 * (size_t)idx[i];
+    for (int k = 0; k < 6; ++k) out[k] = make_float4(b[k][0], b[k][1], b[k][2], b[k][3]);
+    out[6] = make_float4(__uint_as_float(ref[0]), __uint_as_float(ref[1]), __uint_as_float(ref[2]),
+                         __uint_as_float(ref[3]));
+    out[7] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 // Refit for new parameters of the same Gaussians: the record, appearance and box of the
 // Gaussian gid[s] at every leaf slot s < n_valid are recomputed in place; the Gaussians culled
 // at build time (gid[n_valid..n)) only set *revived when one of them is now above alpha_min.
@@ -946,8 +1030,8 @@ struct Alloc {
 void free_scene_arrays(grtx_scene *sc)
 {
     cudaStream_t s = sc->stream;
-    void *ptrs[] = {sc->nodes, sc->geom, sc->tris, sc->app, sc->raw, sc->gid, sc->leaf_ids, sc->codes, sc->ws,
-                    sc->d_counter};
+    void *ptrs[] = {sc->nodes, sc->nodes4, sc->geom, sc->tris, sc->app, sc->raw, sc->gid, sc->leaf_ids, sc->codes,
+                    sc->ws, sc->d_counter};
     for (void *p : ptrs)
         if (p) cudaFreeAsync(p, s);
 }
@@ -1094,6 +1178,41 @@ void set_bounds(grtx_scene *sc, const float *h_root)
     }
 }
 
+// Build (or, after a refit, rebuild in place) the 4-wide nodes from the binary ones.
+int collapse_wide(grtx_scene *sc, cudaStream_t s)
+{
+    if (sc->n_valid == 0 || sc->n_nodes == 0) return GRTX_OK;
+    Alloc A(s);
+    const int n_int = (int)sc->n_nodes;
+    uint32_t *parent, *flag, *idx;
+    char *temp;
+    TRY(A.get(&parent, n_int, true));
+    TRY(A.get(&flag, n_int, true));
+    TRY(A.get(&idx, n_int, true));
+    TRY(A.get(&temp, grtx_scan_temp_bytes(n_int), true));
+    GRTX_CUDA(cudaMemsetAsync(parent, 0xff, sizeof(uint32_t) * n_int, s));
+    k_bin_parents<<<grtx_div_up(n_int, kThreads), kThreads, 0, s>>>(sc->nodes, n_int, parent);
+    k_even_depth<<<grtx_div_up(n_int, kThreads), kThreads, 0, s>>>(parent, n_int, flag);
+    GRTX_CHECK_LAUNCH("4-wide collapse: depth parity");
+    GRTX_CUDA(cudaMemcpyAsync(idx, flag, sizeof(uint32_t) * n_int, cudaMemcpyDeviceToDevice, s));
+    TRY(grtx_scan_exclusive(idx, n_int, temp, s));
+    uint32_t h_last[2] = {0, 0};
+    GRTX_CUDA(cudaMemcpyAsync(&h_last[0], idx + n_int - 1, 4, cudaMemcpyDeviceToHost, s));
+    GRTX_CUDA(cudaMemcpyAsync(&h_last[1], flag + n_int - 1, 4, cudaMemcpyDeviceToHost, s));
+    GRTX_CUDA(cudaStreamSynchronize(s));
+    const int64_t n4 = (int64_t)h_last[0] + h_last[1];
+    if (!sc->nodes4 || n4 != sc->n_nodes4) {
+        if (sc->nodes4) cudaFreeAsync(sc->nodes4, s);
+        sc->nodes4 = nullptr;
+        sc->n_nodes4 = 0;
+        TRY(A.get(&sc->nodes4, 8 * (size_t)n4, false));
+        sc->n_nodes4 = n4;
+    }
+    k_emit_nodes4<<<grtx_div_up(n_int, kThreads), kThreads, 0, s>>>(sc->nodes, n_int, flag, idx, sc->nodes4);
+    GRTX_CHECK_LAUNCH("4-wide collapse: nodes");
+    return GRTX_OK;
+}
+
 int build_scene(const grtx_gaussians *g, const grtx_params *p, int form, grtx_scene *sc)
 {
     cudaStream_t s = sc->stream;
@@ -1108,6 +1227,7 @@ int build_scene(const grtx_gaussians *g, const grtx_params *p, int form, grtx_sc
     sc->alpha_min = p->alpha_min;
     sc->bvh_codes = p->bvh_codes;
     sc->bvh_builder = p->bvh_builder;
+    sc->bvh_width = p->bvh_width == 4 ? 4 : 2;
     TRY(A.get(&sc->d_counter, 8, false));
     GRTX_CUDA(cudaMemsetAsync(sc->d_counter, 0, 8 * sizeof(unsigned), s));
     if (n == 0) {
@@ -1208,6 +1328,7 @@ int build_scene(const grtx_gaussians *g, const grtx_params *p, int form, grtx_sc
     if (sc->depth >= GRTX_STACK)
         return grtx_fail(GRTX_ERR_OVERFLOW_FATAL, "BVH depth " + std::to_string(sc->depth) +
                                                       " exceeds the traversal stack");
+    if (sc->bvh_width == 4) TRY(collapse_wide(sc, s));
     return GRTX_OK;
 }
 
@@ -1247,6 +1368,7 @@ int refit_scene(const grtx_gaussians *g, grtx_scene *sc, cudaStream_t s, bool *r
                                                                         sc->nodes, nullptr, nullptr);
     }
     GRTX_CHECK_LAUNCH("refit");
+    if (sc->bvh_width == 4) TRY(collapse_wide(sc, s));
     unsigned h_flag = 0;
     float h_root[16];
     GRTX_CUDA(cudaMemcpyAsync(&h_flag, d_flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
@@ -1266,6 +1388,7 @@ int rebuild_scene(const grtx_gaussians *g, grtx_scene *sc, cudaStream_t s)
     p.alpha_min = sc->alpha_min;
     p.bvh_codes = sc->bvh_codes;
     p.bvh_builder = sc->bvh_builder;
+    p.bvh_width = sc->bvh_width;
     grtx_scene *ns = new (std::nothrow) grtx_scene();
     if (!ns) return grtx_fail(GRTX_ERR_OOM, "host allocation failed");
     ns->stream = s;
@@ -1450,6 +1573,10 @@ extern "C" GRTX_API int grtx_build_bvh(const grtx_gaussians *g, const grtx_param
         return grtx_fail(GRTX_ERR_INVALID_ARG, "unknown bvh_codes");
     if (p->bvh_builder != GRTX_BUILDER_PLOC && p->bvh_builder != GRTX_BUILDER_LBVH)
         return grtx_fail(GRTX_ERR_INVALID_ARG, "unknown bvh_builder");
+    if (p->bvh_width != 0 && p->bvh_width != 2 && p->bvh_width != 4)
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "bvh_width must be 0, 2 or 4");
+    if (p->bvh_width == 4 && form != GRTX_FORM_SPHERE)
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "4-wide nodes are built for the sphere form only");
     grtx_scene *sc = new (std::nothrow) grtx_scene();
     if (!sc) return grtx_fail(GRTX_ERR_OOM, "host allocation failed");
     sc->stream = S(stream);

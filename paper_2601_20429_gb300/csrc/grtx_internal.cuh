@@ -11,6 +11,7 @@
 #define GRTX_LEAF 0x80000000u
 #define GRTX_NONE 0xFFFFFFFFu
 #define GRTX_STACK 128         // traversal stack entries per ray; the build rejects deeper trees
+#define GRTX_STACK4 192        // the same for 4-wide nodes: up to 3 per level of a tree of depth <= 64
 
 // Record the host-side text of an error for grtx_last_error() and return the status.
 int grtx_fail(int status, const std::string &msg);
@@ -40,9 +41,12 @@ struct grtx_scene {
     int depth = 0;
     float alpha_min = 0.01f;
     int bvh_codes = GRTX_CODES_SIZED, bvh_builder = GRTX_BUILDER_PLOC;   // as built (for rebuilds)
+    int bvh_width = 2;           // 4: nodes4 holds the 4-wide collapse of the binary tree
     int64_t n = 0, n_valid = 0, n_leaves = 0, n_nodes = 0;
     float bounds[6] = {0, 0, 0, 0, 0, 0};
     float4 *nodes = nullptr;     // [n_nodes][4]: BVH2 node, see grtx_scene_export
+    float4 *nodes4 = nullptr;    // [n_nodes4][8]: 4-wide nodes (bvh_width 4), see grtx_params
+    int64_t n_nodes4 = 0;
     float4 *geom = nullptr;      // [n_valid][4]: rows (A_j | mu_j) + (o, -kappa^2 log2(e)/2, id, 0), leaf order
     float4 *tris = nullptr;      // proxy form: [n_leaves][3] world triangle (v0 | gidx, v1, v2)
     float *app = nullptr;        // [n_valid][app_stride] SH coefficients in leaf order

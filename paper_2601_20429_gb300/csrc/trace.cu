@@ -73,6 +73,8 @@ int check_params(const grtx_params *p)
     if (p->ckpt_capacity < 0 || p->evict_capacity < 0 || p->ckpt_capacity > 65536 || p->evict_capacity > 65536)
         return grtx_fail(GRTX_ERR_INVALID_ARG, "capacities must be in [0, 65536]");
     if (p->packet_stack < 0) return grtx_fail(GRTX_ERR_INVALID_ARG, "packet_stack must be >= 0");
+    if (p->bvh_width != 0 && p->bvh_width != 2 && p->bvh_width != 4)
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "bvh_width must be 0, 2 or 4");
     return GRTX_OK;
 }
 
@@ -175,6 +177,8 @@ SceneRef grtx_scene_ref(const grtx_scene *sc)
     r.tpl_nodes = sc->tpl_nodes;
     r.tpl_tris = sc->tpl_tris;
     r.raw = sc->raw;
+    r.nodes4 = sc->nodes4;
+    r.n_nodes4 = (uint32_t)sc->n_nodes4;
     r.app_stride = sc->app_stride;
     r.sh_degree = sc->sh_degree;
     r.has_tree = sc->n_valid > 0;
@@ -211,9 +215,9 @@ int setup(grtx_scene *sc, const grtx_camera *cam, const grtx_params *p, TraceArg
     return GRTX_OK;
 }
 
-int run(grtx_scene *sc, TraceArgs &a, int k, bool instr, int pass, unsigned *queue, cudaStream_t s)
+int run(grtx_scene *sc, TraceArgs &a, int k, bool instr, int pass, unsigned *queue, cudaStream_t s, bool wide = false)
 {
-    int form = kernel_form(sc->form);
+    int form = kernel_form(sc->form, wide);
     bool single = a.traversal == GRTX_TRAVERSAL_SINGLE && pass == PASS_FWD;
     int bps = 0;
     int occ = single ? trace_single_occupancy(form, instr, &bps) : occupancy_k(k, form, instr, pass, &bps);
@@ -342,10 +346,17 @@ extern "C" GRTX_API int grtx_trace_forward(grtx_scene *sc, const grtx_camera *ca
         a.save_cap = sv->cap;
         pass = PASS_SAVE;
     }
+    const bool wide = p->bvh_width == 4;
+    if (wide) {
+        if (sc->bvh_width != 4 && sc->n_valid > 0)
+            return grtx_fail(GRTX_ERR_INVALID_ARG, "bvh_width 4: the scene was built without 4-wide nodes");
+        if (a.traversal == GRTX_TRAVERSAL_SINGLE || pass != PASS_FWD)
+            return grtx_fail(GRTX_ERR_INVALID_ARG, "4-wide nodes take checkpoint or restart traversal, no saved lists");
+    }
     if (out->visits) GRTX_CUDA(cudaMemsetAsync(out->visits_n, 0, (size_t)out->visits_rows * 4, s));
     if (out->blended_ids)
         GRTX_CUDA(cudaMemsetAsync(out->blended_ids, 0xff, (size_t)cam->width * cam->height * out->ids_cap * 4, s));
-    return run(sc, a, p->k, instr, pass, sc->d_counter, s);
+    return run(sc, a, p->k, instr, pass, sc->d_counter, s, wide);
 }
 
 namespace {

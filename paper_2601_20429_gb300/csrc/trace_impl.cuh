@@ -19,14 +19,16 @@ struct SceneRef {
     const uint32_t *gid;
     const float4 *tpl_nodes, *tpl_tris;   // icosphere forms: shared template BVH and triangles
     const float4 *raw;                    // [n_valid][3] raw parameters in leaf order (backward)
+    const float4 *nodes4;                 // 4-wide nodes (8 float4 each), or NULL
     int app_stride, sh_degree, has_tree;
     uint32_t n_nodes, n_leaves, n_geom;   // internal nodes, leaf records, Gaussian records
+    uint32_t n_nodes4;
 };
 
 // Leaf kinds of the trace kernels: one analytic unit sphere per Gaussian; one world-space
 // proxy triangle per leaf (monolithic); one Gaussian instance whose leaf test traverses the
 // shared icosphere template in unit-sphere space before the exact test.
-enum : int { FORM_SPHERE = 0, FORM_PROXY = 1, FORM_ICO = 2 };
+enum : int { FORM_SPHERE = 0, FORM_PROXY = 1, FORM_ICO = 2, FORM_SPHERE4 = 3 };   // 3: sphere leaves, 4-wide nodes
 
 // A camera (rays generated in-kernel) or an explicit ray list.
 struct CamRef {
@@ -109,6 +111,13 @@ __device__ __forceinline__ void log_visit(Counters &c, uint32_t ref)
 __device__ __forceinline__ bool ref_ok(const SceneRef &sc, uint32_t ref, Counters &c, bool count = true)
 {
     bool ok = (ref & GRTX_LEAF) ? (ref & ~GRTX_LEAF) < sc.n_leaves : ref < sc.n_nodes;
+    if (!ok && count) ++c.oob;
+    return ok;
+}
+
+__device__ __forceinline__ bool ref4_ok(const SceneRef &sc, uint32_t ref, Counters &c, bool count = true)
+{
+    bool ok = (ref & GRTX_LEAF) ? (ref & ~GRTX_LEAF) < sc.n_leaves : ref < sc.n_nodes4;
     if (!ok && count) ++c.oob;
     return ok;
 }
@@ -495,6 +504,299 @@ __device__ __forceinline__ bool template_touch(const SceneRef &sc, uint32_t gi, 
 }
 
 // ------------------------------------------------------------------------------------------
+// 4-wide nodes (FORM_SPHERE4; see grtx_params.bvh_width). A node holds its four children's
+// boxes as per-axis rows; empty children have empty boxes (lo = +inf, hi = -inf) and ref
+// GRTX_NONE. The rounds are those of the binary traversal: a child whose entry exceeds t_max
+// is checkpointed, the others are visited, nearest first.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ float pick4(const float v[4], int i)
+{
+    return i == 0 ? v[0] : (i == 1 ? v[1] : (i == 2 ? v[2] : v[3]));
+}
+__device__ __forceinline__ uint32_t pick4(const uint32_t v[4], int i)
+{
+    return i == 0 ? v[0] : (i == 1 ? v[1] : (i == 2 ? v[2] : v[3]));
+}
+
+// Entry and exit of the ray in each child box of a 4-wide node (e > x: missed).
+__device__ __forceinline__ void slab4(const float4 *__restrict__ nd, float3 o, float3 inv, float tn, float tf, float e[4],
+                                      float x[4], uint32_t c[4])
+{
+    const float4 lx = __ldg(nd), ly = __ldg(nd + 1), lz = __ldg(nd + 2);
+    const float4 hx = __ldg(nd + 3), hy = __ldg(nd + 4), hz = __ldg(nd + 5);
+    const float4 rf = __ldg(nd + 6);
+    slab(lx.x, ly.x, lz.x, hx.x, hy.x, hz.x, o, inv, tn, tf, e[0], x[0]);
+    slab(lx.y, ly.y, lz.y, hx.y, hy.y, hz.y, o, inv, tn, tf, e[1], x[1]);
+    slab(lx.z, ly.z, lz.z, hx.z, hy.z, hz.z, o, inv, tn, tf, e[2], x[2]);
+    slab(lx.w, ly.w, lz.w, hx.w, hy.w, hz.w, o, inv, tn, tf, e[3], x[3]);
+    c[0] = __float_as_uint(rf.x);
+    c[1] = __float_as_uint(rf.y);
+    c[2] = __float_as_uint(rf.z);
+    c[3] = __float_as_uint(rf.w);
+}
+
+// Order (key, ord) pairs ascending by key: a 5-comparator network over 4 entries.
+__device__ __forceinline__ void sort4(float k[4], int ord[4])
+{
+#define GRTX_CSWAP(i, j)                                                              \
+    if (k[j] < k[i]) {                                                                \
+        float tk = k[i]; k[i] = k[j]; k[j] = tk;                                      \
+        int to = ord[i]; ord[i] = ord[j]; ord[j] = to;                                \
+    }
+    GRTX_CSWAP(0, 1) GRTX_CSWAP(2, 3) GRTX_CSWAP(0, 2) GRTX_CSWAP(1, 3) GRTX_CSWAP(1, 2)
+#undef GRTX_CSWAP
+}
+
+// The sphere-leaf test of one leaf slot inside a round (shared by the 4-wide traversals):
+// a hit with key in (L, t_max] enters the k-buffer; a hit the full buffer rejects goes to the
+// eviction list when checkpointing. Returns false when the eviction list would overflow.
+template <int K, bool INSTR>
+__device__ __forceinline__ bool leaf4(const TraceArgs &a, const SceneRef &sc, uint32_t ref, float3 o, float3 d, float tn,
+                                      float tf, float Lt, uint32_t Li, bool ckpt, uint32_t ev, int &n_ev, KBuf<K> &kb,
+                                      float &tmax, Counters &cnt)
+{
+    const uint32_t gi = ref & ~GRTX_LEAF;
+    if (INSTR) {
+        cnt.leaves++;
+        log_visit(cnt, ref);
+    }
+    float t, D2, w[3];
+    if (sphere_test(sc.geom + 4 * (size_t)gi, o, d, t, D2, w) && D2 <= 1.0f && t > tn && t <= tf &&
+        key_after(t, gi, Lt, Li)) {
+        float ct = t;
+        uint32_t ci = gi;
+        if (kb.insert(ct, ci) && ckpt) {
+            if (n_ev >= a.evict_cap) return false;
+            a.ck0[ev + (uint32_t)n_ev * (uint32_t)a.n_slots] = make_uint2(__float_as_uint(ct), ci);
+            ++n_ev;
+            if (INSTR) cnt.evictions++;
+        }
+        tmax = kb.tmax;
+    }
+    return true;
+}
+
+// One round of one ray over 4-wide nodes (the per-ray rounds; see trace_round).
+template <int K, bool INSTR>
+__device__ __forceinline__ bool trace_round4(const TraceArgs &a, const SceneRef &sc, float3 o, float3 d, float3 inv,
+                                             float tn, float tf, float Lt, uint32_t Li, bool ckpt, bool from_root,
+                                             uint32_t src, int n_src, uint32_t dst, int &n_dst, uint32_t ev,
+                                             int &n_ev, KBuf<K> &kb, Counters &cnt)
+{
+    const uint32_t S = (uint32_t)a.n_slots;
+    uint2 *__restrict__ const L = a.ck0;
+    uint32_t stack[GRTX_STACK4];               // node refs; a popped entry is visited (see trace_round)
+    int sp = 0, si = 0;
+    float tmax = kb.tmax;
+    uint32_t ref;
+    float te;
+    n_dst = 0;
+    if (from_root) {
+        n_src = 0;
+        ref = 0u;
+        te = tn;
+    } else {
+        if (n_src == 0) return true;
+        uint2 v = L[src];
+        ref = v.x;
+        te = __uint_as_float(v.y);
+        si = 1;
+    }
+    for (;;) {
+        if (te > tmax) {
+            if (ckpt) {
+                if (n_dst >= a.ckpt_cap) return false;
+                L[dst + (uint32_t)n_dst * S] = make_uint2(ref, __float_as_uint(te));
+                ++n_dst;
+                if (INSTR) cnt.ckpt++;
+            }
+        } else if (INSTR && !ref4_ok(sc, ref, cnt)) {
+        } else if (ref & GRTX_LEAF) {
+            if (!leaf4<K, INSTR>(a, sc, ref, o, d, tn, tf, Lt, Li, ckpt, ev, n_ev, kb, tmax, cnt)) return false;
+        } else {
+            if (INSTR) {
+                cnt.nodes++;
+                log_visit(cnt, ref);
+            }
+            float e[4], x[4];
+            uint32_t c[4];
+            slab4(sc.nodes4 + 8 * (size_t)ref, o, inv, tn, tf, e, x, c);
+            int ord[4] = {0, 1, 2, 3};
+            int nh = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const bool h = e[j] <= x[j] && !(x[j] < Lt) && c[j] != GRTX_NONE;
+                nh += h;
+                if (!h) e[j] = GRTX_INF;           // misses sort last
+            }
+            if (nh > 0) {
+                sort4(e, ord);
+#pragma unroll
+                for (int j = 3; j >= 1; --j) {    // farthest first onto the stack, so the nearest pops first
+                    if (j < nh) {
+                        const uint32_t cj = pick4(c, ord[j]);
+                        if (e[j] > tmax) {
+                            if (ckpt) {
+                                if (n_dst >= a.ckpt_cap) return false;
+                                L[dst + (uint32_t)n_dst * S] = make_uint2(cj, __float_as_uint(e[j]));
+                                ++n_dst;
+                                if (INSTR) cnt.ckpt++;
+                            }
+                        } else if (sp < GRTX_STACK4) {
+                            stack[sp++] = cj;
+                        } else if (INSTR) {
+                            cnt.overflow++;
+                        }
+                    }
+                }
+                ref = pick4(c, ord[0]);
+                te = e[0];
+                continue;
+            }
+        }
+        if (sp > 0) {
+            ref = stack[--sp];
+            te = -GRTX_INF;
+        } else if (si < n_src) {
+            uint2 v = L[src + (uint32_t)si * S];
+            ++si;
+            ref = v.x;
+            te = __uint_as_float(v.y);
+        } else {
+            break;
+        }
+    }
+    return true;
+}
+
+// A round of a warp's rays from the root as one packet over 4-wide nodes (see packet_round).
+// At a node every lane tests the four children; the warp continues into the child its lowest
+// active lane enters first and keeps the others, with the lanes that want them, on the warp's
+// stack (entries: child, parent << 2 | child slot, lane mask); a popped child's entry
+// distance is recomputed per lane from its box in the parent.
+template <int K, bool INSTR>
+__device__ __forceinline__ bool packet_round4(const TraceArgs &a, const SceneRef &sc, bool valid, uint4 *pst, float3 o,
+                                              float3 d, float3 inv, float tn, float tf, float Lt, uint32_t Li,
+                                              bool ckpt, uint32_t dst, int &n_dst, uint32_t ev, int &n_ev, KBuf<K> &kb,
+                                              Counters &cnt, bool &lane_ok)
+{
+    const unsigned full = 0xffffffffu;
+    const uint32_t S = (uint32_t)a.n_slots;
+    uint2 *__restrict__ const L = a.ck0;
+    const int lane = threadIdx.x & 31;
+    float tmax = kb.tmax;
+    n_dst = 0;
+    n_ev = 0;
+    lane_ok = true;
+    if (!sc.has_tree) return true;
+    int sp = 0;
+    uint32_t ref = 0u, parent = GRTX_NONE, slot = 0u;
+    unsigned m = __ballot_sync(full, valid);
+    float te = tn;
+    bool have_te = true;
+    for (;;) {
+        const bool in = (m >> lane) & 1u;
+        if (!have_te && in) {                          // a popped child: entry from the parent's box
+            const float *pn = reinterpret_cast<const float *>(sc.nodes4 + 8 * (size_t)parent);
+            float x;
+            slab(__ldg(pn + slot), __ldg(pn + 4 + slot), __ldg(pn + 8 + slot), __ldg(pn + 12 + slot),
+                 __ldg(pn + 16 + slot), __ldg(pn + 20 + slot), o, inv, tn, tf, te, x);
+        }
+        const bool go = in && lane_ok && !(te > tmax);
+        if (in && lane_ok && te > tmax && ckpt) {
+            if (n_dst >= a.ckpt_cap) {
+                lane_ok = false;
+            } else {
+                L[dst + (uint32_t)n_dst * S] = make_uint2(ref, __float_as_uint(te));
+                ++n_dst;
+                if (INSTR) cnt.ckpt++;
+            }
+        }
+        m = __ballot_sync(full, go);
+        bool pop = true;
+        if (m && (!INSTR || ref4_ok(sc, ref, cnt, go))) {   // ref is the warp's: all lanes agree
+            if (ref & GRTX_LEAF) {
+                if (go && !leaf4<K, INSTR>(a, sc, ref, o, d, tn, tf, Lt, Li, ckpt, ev, n_ev, kb, tmax, cnt))
+                    lane_ok = false;
+            } else {
+                float e[4], x[4];
+                uint32_t c[4];
+                slab4(sc.nodes4 + 8 * (size_t)ref, o, inv, tn, tf, e, x, c);
+                bool h[4];
+                unsigned mh[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    h[j] = go && e[j] <= x[j] && !(x[j] < Lt) && c[j] != GRTX_NONE;
+                    mh[j] = __ballot_sync(full, h[j]);
+                }
+                if (INSTR && go) {
+                    cnt.nodes++;
+                    log_visit(cnt, ref);
+                }
+                // order the wanted children by the lowest active lane's entry distances (children
+                // it misses after those it enters, in child order; children nobody wants last)
+                const int leader = __ffs(m) - 1;
+                float k2[4];
+                int rk[4], ord[4] = {0, 1, 2, 3};
+                int nc = 0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float kl = __shfl_sync(full, h[j] ? e[j] : GRTX_INF, leader);
+                    rk[j] = mh[j] == 0u ? 2 : (kl < GRTX_INF ? 0 : 1);
+                    k2[j] = kl;
+                    nc += mh[j] != 0u;
+                }
+                if (nc > 0) {
+#define GRTX_CSWAP4(i, j)                                                                                 \
+    if (rk[j] < rk[i] || (rk[j] == rk[i] && rk[i] == 0 && k2[j] < k2[i])) {                            \
+        int tr = rk[i]; rk[i] = rk[j]; rk[j] = tr;                                                        \
+        float tk = k2[i]; k2[i] = k2[j]; k2[j] = tk;                                                      \
+        int to = ord[i]; ord[i] = ord[j]; ord[j] = to;                                                    \
+    }
+                    GRTX_CSWAP4(0, 1) GRTX_CSWAP4(2, 3) GRTX_CSWAP4(0, 2) GRTX_CSWAP4(1, 3) GRTX_CSWAP4(1, 2)
+#undef GRTX_CSWAP4
+                    if (sp + nc - 1 > a.packet_stack) {       // too deep for the warp's stack
+                        lane_ok = false;
+                        return false;
+                    }
+                    if (lane == 0) {
+#pragma unroll
+                        for (int j = 3; j >= 1; --j) {        // farthest first
+                            if (j < nc) {
+                                const int oj = ord[j];
+                                pst[sp + (nc - 1 - j)] = make_uint4(pick4(c, oj), (ref << 2) | (uint32_t)oj,
+                                                                    oj == 0 ? mh[0] : (oj == 1 ? mh[1] : (oj == 2 ? mh[2] : mh[3])), 0u);
+                            }
+                        }
+                    }
+                    sp += nc - 1;
+                    __syncwarp(full);
+                    const int f = ord[0];
+                    parent = ref;
+                    slot = (uint32_t)f;
+                    m = f == 0 ? mh[0] : (f == 1 ? mh[1] : (f == 2 ? mh[2] : mh[3]));
+                    te = pick4(e, f);
+                    ref = pick4(c, f);
+                    have_te = true;
+                    pop = false;
+                }
+            }
+        }
+        if (pop) {
+            if (sp == 0) break;
+            --sp;
+            const uint4 v = pst[sp];
+            ref = v.x;
+            parent = v.y >> 2;
+            slot = v.y & 3u;
+            m = v.z;
+            have_te = false;
+        }
+    }
+    return true;
+}
+
+// ------------------------------------------------------------------------------------------
 // One traversal round over keys in (L, t_max] (Sec. III-A). With ckpt, it starts from the
 // checkpoint source list (or the root in the first round), writes nodes failing the t_max
 // test to the destination list and rejected hits to the eviction list (Sec. IV-B);
@@ -507,6 +809,9 @@ __device__ __forceinline__ bool trace_round(const TraceArgs &a, const SceneRef &
                                             uint32_t src, int n_src, uint32_t dst, int &n_dst, uint32_t ev,
                                             int &n_ev, KBuf<K> &kb, Counters &cnt)
 {
+    if constexpr (FORM == FORM_SPHERE4)
+        return trace_round4<K, INSTR>(a, sc, o, d, inv, tn, tf, Lt, Li, ckpt, from_root, src, n_src, dst, n_dst, ev,
+                                      n_ev, kb, cnt);
     const uint32_t S = (uint32_t)a.n_slots;
     uint2 *__restrict__ const L = a.ck0;      // lists: src, dst and ev are entry offsets into L
     // far children deferred within this round: node refs only (4 bytes each); a popped entry
@@ -655,6 +960,9 @@ __device__ __forceinline__ bool packet_round(const TraceArgs &a, const SceneRef 
                                              uint32_t ev, int &n_ev, KBuf<K> &kb, Counters &cnt,
                                              bool &lane_ok)
 {
+    if constexpr (FORM == FORM_SPHERE4)
+        return packet_round4<K, INSTR>(a, sc, valid, pst, o, d, inv, tn, tf, Lt, Li, ckpt, dst, n_dst, ev, n_ev, kb,
+                                       cnt, lane_ok);
     const unsigned full = 0xffffffffu;
     const uint32_t S = (uint32_t)a.n_slots;
     uint2 *__restrict__ const L = a.ck0;      // lists: dst and ev are entry offsets into L
@@ -1166,7 +1474,7 @@ __device__ __forceinline__ void trace_warp(const TraceArgs &a, const SceneRef &s
 // The first kDiscardRows rows of each list are dropped (a ray rarely writes more entries per
 // round; a row past that is only written back as before); rows past a list's capacity would
 // belong to the next list or lie past the workspace, and are skipped.
-constexpr int kDiscardRows = 32;
+constexpr int kDiscardRows = 64;
 
 __device__ __forceinline__ void discard_dead_lists(const TraceArgs &a, int warp_slot0)
 {
@@ -1313,6 +1621,8 @@ int trace_launch(const TraceArgs &a, int form, bool instr, int pass, int blocks,
     else if (form == FORM_PROXY) k_trace<K, FORM_PROXY, false, PASS_FWD><<<g, b, 0, s>>>(a);
     else if (form == FORM_ICO && instr) k_trace<K, FORM_ICO, true, PASS_FWD><<<g, b, 0, s>>>(a);
     else if (form == FORM_ICO) k_trace<K, FORM_ICO, false, PASS_FWD><<<g, b, 0, s>>>(a);
+    else if (form == FORM_SPHERE4 && instr) k_trace<K, FORM_SPHERE4, true, PASS_FWD><<<g, b, 0, s>>>(a);
+    else if (form == FORM_SPHERE4) k_trace<K, FORM_SPHERE4, false, PASS_FWD><<<g, b, 0, s>>>(a);
     else if (instr) k_trace<K, FORM_SPHERE, true, PASS_FWD><<<g, b, 0, s>>>(a);
     else k_trace<K, FORM_SPHERE, false, PASS_FWD><<<g, b, 0, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? GRTX_OK : GRTX_ERR_CUDA;
@@ -1328,16 +1638,19 @@ int trace_occupancy(int form, bool instr, int pass, int *blocks_per_sm)
     else if (form == FORM_PROXY) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_PROXY, false, PASS_FWD>, 128, 0);
     else if (form == FORM_ICO && instr) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_ICO, true, PASS_FWD>, 128, 0);
     else if (form == FORM_ICO) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_ICO, false, PASS_FWD>, 128, 0);
+    else if (form == FORM_SPHERE4 && instr) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_SPHERE4, true, PASS_FWD>, 128, 0);
+    else if (form == FORM_SPHERE4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_SPHERE4, false, PASS_FWD>, 128, 0);
     else if (instr) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_SPHERE, true, PASS_FWD>, 128, 0);
     else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_SPHERE, false, PASS_FWD>, 128, 0);
     return e == cudaSuccess ? GRTX_OK : GRTX_ERR_CUDA;
 }
 
-// Kernel leaf kind of a scene form.
-inline int kernel_form(int scene_form)
+// Kernel leaf kind of a scene form (wide: the 4-wide nodes of a sphere-form scene).
+inline int kernel_form(int scene_form, bool wide = false)
 {
     return scene_form == GRTX_FORM_PROXY20 ? FORM_PROXY
-           : (scene_form == GRTX_FORM_ICO20 || scene_form == GRTX_FORM_ICO80) ? FORM_ICO : FORM_SPHERE;
+           : (scene_form == GRTX_FORM_ICO20 || scene_form == GRTX_FORM_ICO80) ? FORM_ICO
+           : wide ? FORM_SPHERE4 : FORM_SPHERE;
 }
 
 template <int K>

@@ -33,7 +33,8 @@ class Scene:
     Sec. III-C)."""
 
     def __init__(self, means, log_scales, quats, logits, sh, sh_degree: int, form: str = "sphere",
-                 alpha_min: float = 0.01, stream=None, bvh_codes: str = "sized", bvh_builder: str = "ploc"):
+                 alpha_min: float = 0.01, stream=None, bvh_codes: str = "sized", bvh_builder: str = "ploc",
+                 bvh_width: int = 2):
         dev = torch.device("cuda", torch.cuda.current_device())
         self.tensors = tuple(_cuda_f32(a, dev) for a in (means, log_scales, quats, logits, sh))
         self.sh_degree = int(sh_degree)
@@ -42,13 +43,15 @@ class Scene:
         self._g = N.make_gaussians(*self.tensors, self.sh_degree)
         self.bvh_codes = bvh_codes
         self.bvh_builder = bvh_builder
-        p = N.make_params(alpha_min=alpha_min, bvh_codes=bvh_codes, bvh_builder=bvh_builder)
+        self.bvh_width = int(bvh_width)
+        p = N.make_params(alpha_min=alpha_min, bvh_codes=bvh_codes, bvh_builder=bvh_builder, bvh_width=bvh_width)
         self.handle = N.grtx_build_bvh(self._g, p, FORMS[form], stream)
 
     @classmethod
-    def from_params(cls, g, form="sphere", alpha_min=0.01, stream=None, bvh_codes="sized", bvh_builder="ploc"):
+    def from_params(cls, g, form="sphere", alpha_min=0.01, stream=None, bvh_codes="sized", bvh_builder="ploc",
+                    bvh_width=2):
         return cls(g.means, g.log_scales, g.quats, g.logits, g.sh, g.sh_degree, form, alpha_min, stream, bvh_codes,
-                   bvh_builder)
+                   bvh_builder, bvh_width)
 
     def update(self, means, log_scales, quats, logits, sh, mode: str = "refit", stream=None) -> bool:
         """New parameters for the same Gaussians (same n and SH degree), in place: "refit" keeps
@@ -138,9 +141,9 @@ def render_world(world: World, cam: dict | None, rays=None, out=None, ids_cap: i
 
 
 def trace_params(k=16, traversal="checkpoint", alpha_min=0.01, T_min=1e-3, alpha_max=0.99, bg=(0.0, 0.0, 0.0),
-                 ckpt_capacity=0, evict_capacity=0, packet_stack=0):
+                 ckpt_capacity=0, evict_capacity=0, packet_stack=0, bvh_width=0):
     return N.make_params(k, TRAVERSALS[traversal] if isinstance(traversal, str) else traversal, alpha_min, T_min,
-                         alpha_max, bg, ckpt_capacity, evict_capacity, packet_stack=packet_stack)
+                         alpha_max, bg, ckpt_capacity, evict_capacity, packet_stack=packet_stack, bvh_width=bvh_width)
 
 
 def n_rays_of(cam: dict, rays=None) -> int:

@@ -244,8 +244,10 @@ def test_rays_match_oracle(kind):
 # ------------------------------------------------------------------ a5-a9: forward trace
 
 
-def _gpu_render(g, cam, form="sphere", rays=None, **kw):
-    sc = R.Scene.from_params(g, form=form)
+def _gpu_render(g, cam, form="sphere", rays=None, bvh_width=2, **kw):
+    sc = R.Scene.from_params(g, form=form, bvh_width=bvh_width)
+    if bvh_width == 4:
+        kw["bvh_width"] = 4
     out = R.render(sc, cam, rays=rays, ids_cap=kw.pop("ids_cap", 64), want_n_blended=True, want_stats=True, **kw)
     torch.cuda.synchronize()
     res = {k: v.cpu().numpy() for k, v in out.items()}
@@ -294,6 +296,64 @@ def test_forward_dense_parity_both_traversals(dense, k):
     assert a["stats"]["nodes"] < b["stats"]["nodes"]         # resume skips the revisits
     assert a["stats"]["rounds"] == b["stats"]["rounds"]
     assert (ref["n_blend"] < ref["n_hits"]).sum() > 100       # early termination is exercised
+
+
+# ------------------------------------------------------------------ 4-wide nodes (paper's wide BVH)
+
+
+@pytest.mark.parametrize("k", [4, 16])
+@pytest.mark.parametrize("traversal", ["checkpoint", "restart"])
+def test_wide_nodes_parity(dense, k, traversal):
+    """The 4-wide collapse of the tree (bvh_width 4) gives the oracle's image and blend lists,
+    never fetches outside the scene, and fetches fewer nodes than the binary tree."""
+    g, cam, S, rays, ref = dense
+    w = _gpu_render(g, cam, k=k, traversal=traversal, ids_cap=256, bvh_width=4)
+    _check_image(w, ref, S, rays)
+    b = _gpu_render(g, cam, k=k, traversal=traversal, ids_cap=256)
+    assert w["stats"]["fallbacks"] == 0 and w["stats"]["stack_overflow"] == 0
+    assert w["stats"]["rounds"] == b["stats"]["rounds"] and w["stats"]["blended"] == b["stats"]["blended"]
+    assert w["stats"]["nodes"] < b["stats"]["nodes"]
+    np.testing.assert_array_equal(w["n_blended"], b["n_blended"])
+    assert float(np.abs(w["rgbT"] - b["rgbT"]).max()) <= RGB_TOL
+
+
+def test_wide_nodes_tiny_every_k(tiny):
+    g, cam, S, rays, ref = tiny
+    for k in (1, 2, 8, 32):
+        res = _gpu_render(g, cam, k=k, bvh_width=4)
+        _check_image(res, ref, S, rays)
+        assert res["stats"]["blended"] == int(ref["n_blend"].sum())
+
+
+def test_wide_nodes_fallbacks_are_exact(dense):
+    """Tiny list capacities (rays redo rounds from the root) and a short warp stack (packets
+    fall back to per-ray rounds) give the same image over 4-wide nodes."""
+    g, cam, S, rays, ref = dense
+    a = _gpu_render(g, cam, k=4, ids_cap=256, bvh_width=4, ckpt_capacity=2, evict_capacity=1)
+    assert a["stats"]["fallbacks"] > 0
+    _check_image(a, ref, S, rays)
+    b = _gpu_render(g, cam, k=4, ids_cap=256, bvh_width=4, packet_stack=2)
+    _check_image(b, ref, S, rays)
+
+
+def test_wide_nodes_argument_errors(dense):
+    g, cam, S, rays, ref = dense
+    sc = R.Scene.from_params(g)                    # binary only
+    with pytest.raises(N.GrtxError) as e:
+        R.render(sc, cam, k=8, bvh_width=4)
+    assert e.value.status == 1 and "4-wide" in str(e.value)
+    sc.close()
+    with pytest.raises(N.GrtxError):
+        R.Scene.from_params(g, form="proxy20", bvh_width=4)
+    sw = R.Scene.from_params(g, bvh_width=4)
+    with pytest.raises(N.GrtxError):
+        R.render(sw, cam, k=8, bvh_width=4, traversal="single")
+    # the other entry points trace the binary nodes of a 4-wide scene
+    out = R.render(sw, cam, k=8)["rgbT"]
+    out4 = R.render(sw, cam, k=8, bvh_width=4)["rgbT"]
+    torch.cuda.synchronize()
+    assert float((out - out4).abs().max()) <= RGB_TOL
+    sw.close()
 
 
 # ------------------------------------------------------------------ instanced icosphere forms
@@ -540,6 +600,14 @@ def test_forward_surface_full_size_sampled():
     assert not bad
     # the two instantiations differ only in the compiler's contraction of the blend arithmetic
     assert float(np.abs(timed - rgbT).max()) <= RGB_TOL
+    # the same frame over the 4-wide collapse of the same tree
+    sc4 = R.Scene.from_params(g, bvh_width=4)
+    wide = R.render(sc4, cam, k=16, bvh_width=4)["rgbT"]
+    st4 = N.stats_dict(R.render(sc4, cam, k=16, bvh_width=4, want_stats=True)["stats"])
+    torch.cuda.synchronize()
+    assert float(np.abs(wide.cpu().numpy() - timed).max()) <= RGB_TOL
+    assert st4["bounds_errors"] == 0 and st4["fallbacks"] == 0
+    sc4.close()
     assert np.all(timed[:, 3] >= 0) and np.all(timed[:, 3] <= 1) and np.isfinite(timed).all()
     assert float(timed[:, 3].min()) < 0.5        # the frame hits Gaussians
     sc.close()

@@ -117,9 +117,9 @@ OUT64 = 64 * 64 * 16
 
 def _budget_for(n_outputs):
     """A budget of one block of lists (its half for lists holds one block, not two) and an
-    output arena of n 64x64 outputs plus less than one more (the segment tables of 8 requests
-    take under 8 KiB)."""
-    return PER_BLOCK + n_outputs * OUT64 + 8192
+    output arena of n 64x64 outputs plus less than one more (the queue counters and the
+    segment tables of 8 requests take under 16 KiB)."""
+    return PER_BLOCK + n_outputs * OUT64 + 16384
 
 
 def test_memory_budget_holds_requests_until_outputs_are_released(world):
