@@ -419,8 +419,15 @@ def run_stream(srv, reqs, rate_hz: float) -> dict:
     rays = sum(r["camera"]["width"] * r["camera"]["height"] for r in reqs)
     makespan = t_last - reqs[0]["arrival"]
     lat_ms = np.array(lat) * 1e3
+    px = np.array([r["camera"]["width"] * r["camera"]["height"] for r in reqs])
+    by_res = {}
+    for p_ in sorted(set(px.tolist())):
+        sel = lat_ms[px == p_]
+        by_res[str(p_)] = {"n": int(sel.size), "p50_ms": float(np.percentile(sel, 50)),
+                           "p99_ms": float(np.percentile(sel, 99))}
     return {"requests": n, "rate_hz": rate_hz, "p50_ms": float(np.percentile(lat_ms, 50)),
             "p99_ms": float(np.percentile(lat_ms, 99)), "mean_ms": float(lat_ms.mean()),
+            "latency_by_pixels": by_res,
             "Mrays_per_s": rays / makespan / 1e6, "makespan_s": makespan,
             "offered_Mrays_per_s": rays / (reqs[-1]["arrival"] - reqs[0]["arrival"]) / 1e6}
 
