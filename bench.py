@@ -325,6 +325,12 @@ def bench_surface_ablations(g, sc, cam, k: int, steps: int, stream, flush) -> di
                    "restart_Mrays_per_s": mrays(n_rays, tr), "nodes_per_ray": nodes_per_ray(st),
                    "build_ms": build_w, "node_bytes": 128}
     sc_w.close()
+    sc_q = R.Scene.from_params(g, bvh_width=4, bvh_quantize=True)
+    st = N.stats_dict(R.render(sc_q, cam, k=k, out=out, want_stats=True, bvh_width=4)["stats"])
+    t = time_frames(lambda: R.render(sc_q, cam, k=k, out=out, bvh_width=4), steps, 2, flush, stream)
+    res["bvh4_quantised"] = {"Mrays_per_s": mrays(n_rays, t), "ms_per_frame": statistics.mean(t),
+                             "nodes_per_ray": nodes_per_ray(st), "node_bytes": 64}
+    sc_q.close()
     for name, codes, builder in (("lbvh_sized_codes", "sized", "lbvh"), ("lbvh_centroid_codes", "centroid", "lbvh")):
         t0 = time.perf_counter()
         sc_c = R.Scene.from_params(g, bvh_codes=codes, bvh_builder=builder)
@@ -613,6 +619,7 @@ def bench_outdoor(steps: int, stream, flush, primary_only: bool = False):
     sc_c = None if primary_only else R.Scene.from_params(g, bvh_codes="centroid", bvh_builder="lbvh")
     sc_l = None if primary_only else R.Scene.from_params(g, bvh_builder="lbvh")
     sc_w = R.Scene.from_params(g, bvh_width=4)
+    sc_q = R.Scene.from_params(g, bvh_width=4, bvh_quantize=True)
     del g
     n = cam["width"] * cam["height"]
     prim = [torch.empty((n, 3), device="cuda"), torch.empty((n, 3), device="cuda"), torch.empty(n, device="cuda"),
@@ -632,8 +639,12 @@ def bench_outdoor(steps: int, stream, flush, primary_only: bool = False):
                      stream)
     st_w = N.stats_dict(R.render(sc_w, cam, rays=prim, k=cfg["k"], want_stats=True, bvh_width=4)["stats"])
     sc_w.close()
+    tq = time_frames(lambda: R.render(sc_q, cam, rays=prim, k=cfg["k"], out=out_p, bvh_width=4), steps, 2, flush,
+                     stream)
+    sc_q.close()
     wide = {"Mrays_per_s": n / (statistics.mean(tw) / 1e3) / 1e6, "ms": statistics.mean(tw),
-            "nodes_per_ray": nodes_per_ray(st_w)}
+            "nodes_per_ray": nodes_per_ray(st_w),
+            "quantised_Mrays_per_s": n / (statistics.mean(tq) / 1e3) / 1e6}
     if primary_only:
         st_p = N.stats_dict(R.render(sc, cam, rays=prim, k=cfg["k"], want_stats=True)["stats"])
         depth = sc.info()["depth"]

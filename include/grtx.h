@@ -128,7 +128,12 @@ enum { GRTX_TRAVERSAL_CHECKPOINT = 0, /* resume from checkpointed nodes + evicti
  * hi z of the four children as float4 rows, then the four child refs, then padding), and
  * grtx_trace_forward with bvh_width 4 traverses them (checkpoint or restart traversal, no
  * saved lists; GRTX_ERR_INVALID_ARG on a scene built without them). Every other entry point
- * traverses the binary nodes. The image does not depend on the width. */
+ * traverses the binary nodes. The image does not depend on the width.
+ * bvh_quantize (read by grtx_build_bvh with bvh_width 4): 1 stores the 4-wide nodes with
+ * quantised child boxes in 64 bytes: the node's lower corner (3 floats) and a power-of-two
+ * step per axis, then per child and axis an 8-bit lower and upper grid coordinate, rounded
+ * outwards so that the decoded box (corner + q * step, one FMA) contains the child's box;
+ * then the four child refs. A trace reads whichever format the scene was built with. */
 #define GRTX_PACKET_STACK 64
 enum { GRTX_CODES_SIZED = 0, GRTX_CODES_CENTROID = 1 };
 enum { GRTX_BUILDER_PLOC = 0, GRTX_BUILDER_LBVH = 1 };
@@ -146,6 +151,7 @@ typedef struct grtx_params {
     int32_t bvh_builder;
     int32_t packet_stack;
     int32_t bvh_width;
+    int32_t bvh_quantize;
 } grtx_params;
 
 enum { GRTX_CAMERA_PINHOLE = 0, GRTX_CAMERA_FISHEYE = 1, GRTX_CAMERA_RAYS = 2 };

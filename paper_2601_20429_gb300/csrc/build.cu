@@ -537,8 +537,60 @@ __global__ void k_even_depth(const uint32_t *__restrict__ parent, int n_int, uin
     flag[i] = (d & 1) == 0;
 }
 
+// Quantised child boxes (bvh_quantize): per axis a lower corner o and a power-of-two step
+// 2^e, and per child an 8-bit lower and upper coordinate q such that o + q * 2^e (one FMA in
+// FP32, as the trace decodes it) lies below the child's lower face and above its upper face.
+__device__ void quantise_axis(const float lo[4], const float hi[4], const bool used[4], float &o, uint32_t &eb,
+                              uint32_t &qlo, uint32_t &qhi)
+{
+    float nlo = __int_as_float(0x7f800000), nhi = __int_as_float(0xff800000);
+    for (int j = 0; j < 4; ++j)
+        if (used[j]) {
+            nlo = fminf(nlo, lo[j]);
+            nhi = fmaxf(nhi, hi[j]);
+        }
+    o = nlo;
+    int e = -126;
+    const float r = (nhi - nlo) / 250.0f;
+    if (r > 0.0f) {
+        int ex;
+        frexpf(r, &ex);                               // r < 2^ex
+        e = max(-126, min(127, ex));
+    }
+    qlo = qhi = 0;
+    for (;;) {
+        const float st = __int_as_float((e + 127) << 23);
+        bool fits = true;
+        uint32_t ql = 0, qh = 0;
+        for (int j = 0; j < 4; ++j) {
+            int a, b;
+            if (!used[j]) {                           // empty child: an empty decoded box
+                a = 255;
+                b = 0;
+            } else {
+                a = (int)floorf((lo[j] - o) / st);
+                b = (int)ceilf((hi[j] - o) / st);
+                a = max(0, min(255, a));
+                b = max(0, min(255, b));
+                while (a > 0 && fmaf((float)a, st, o) > lo[j]) --a;
+                while (b < 255 && fmaf((float)b, st, o) < hi[j]) ++b;
+                if (fmaf((float)a, st, o) > lo[j] || fmaf((float)b, st, o) < hi[j]) fits = false;
+            }
+            ql |= (uint32_t)a << (8 * j);
+            qh |= (uint32_t)b << (8 * j);
+        }
+        if (fits || e >= 127) {
+            qlo = ql;
+            qhi = qh;
+            break;
+        }
+        ++e;                                          // rounding pushed a face past 255 steps
+    }
+    eb = (uint32_t)(e + 127);
+}
+
 __global__ void k_emit_nodes4(const float4 *__restrict__ nodes, int n_int, const uint32_t *__restrict__ flag,
-                              const uint32_t *__restrict__ idx, float4 *__restrict__ nodes4)
+                              const uint32_t *__restrict__ idx, float4 *__restrict__ nodes4, int quant)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_int || !flag[i]) return;
@@ -583,6 +635,23 @@ __global__ void k_emit_nodes4(const float4 *__restrict__ nodes, int n_int, const
             if (gr == GRTX_NONE) continue;
             add(gb, (gr & GRTX_LEAF) ? gr : idx[gr]);
         }
+    }
+    if (quant) {
+        // 64 bytes: (o x, o y, o z, steps as exponent bytes), then the 8-bit coordinates
+        // (lo x, lo y, lo z, hi x | hi y, hi z) of the four children, then the four refs
+        bool used[4];
+        for (int j = 0; j < 4; ++j) used[j] = ref[j] != GRTX_NONE;
+        float o[3];
+        uint32_t eb[3], ql[3], qh[3];
+        for (int a = 0; a < 3; ++a) quantise_axis(b[a], b[3 + a], used, o[a], eb[a], ql[a], qh[a]);
+        float4 *out = nodes4 + 4 * (size_t)idx[i];
+        out[0] = make_float4(o[0], o[1], o[2], __uint_as_float(eb[0] | (eb[1] << 8) | (eb[2] << 16)));
+        out[1] = make_float4(__uint_as_float(ql[0]), __uint_as_float(ql[1]), __uint_as_float(ql[2]),
+                             __uint_as_float(qh[0]));
+        out[2] = make_float4(__uint_as_float(qh[1]), __uint_as_float(qh[2]), __uint_as_float(ref[0]),
+                             __uint_as_float(ref[1]));
+        out[3] = make_float4(__uint_as_float(ref[2]), __uint_as_float(ref[3]), 0.f, 0.f);
+        return;
     }
     float4 *out = nodes4 + 8 * (size_t)idx[i];
     for (int k = 0; k < 6; ++k) out[k] = make_float4(b[k][0], b[k][1], b[k][2], b[k][3]);
@@ -1205,10 +1274,11 @@ int collapse_wide(grtx_scene *sc, cudaStream_t s)
         if (sc->nodes4) cudaFreeAsync(sc->nodes4, s);
         sc->nodes4 = nullptr;
         sc->n_nodes4 = 0;
-        TRY(A.get(&sc->nodes4, 8 * (size_t)n4, false));
+        TRY(A.get(&sc->nodes4, (sc->bvh_quant ? 4 : 8) * (size_t)n4, false));
         sc->n_nodes4 = n4;
     }
-    k_emit_nodes4<<<grtx_div_up(n_int, kThreads), kThreads, 0, s>>>(sc->nodes, n_int, flag, idx, sc->nodes4);
+    k_emit_nodes4<<<grtx_div_up(n_int, kThreads), kThreads, 0, s>>>(sc->nodes, n_int, flag, idx, sc->nodes4,
+                                                                    sc->bvh_quant);
     GRTX_CHECK_LAUNCH("4-wide collapse: nodes");
     return GRTX_OK;
 }
@@ -1228,6 +1298,7 @@ int build_scene(const grtx_gaussians *g, const grtx_params *p, int form, grtx_sc
     sc->bvh_codes = p->bvh_codes;
     sc->bvh_builder = p->bvh_builder;
     sc->bvh_width = p->bvh_width == 4 ? 4 : 2;
+    sc->bvh_quant = sc->bvh_width == 4 && p->bvh_quantize ? 1 : 0;
     TRY(A.get(&sc->d_counter, 8, false));
     GRTX_CUDA(cudaMemsetAsync(sc->d_counter, 0, 8 * sizeof(unsigned), s));
     if (n == 0) {
@@ -1389,6 +1460,7 @@ int rebuild_scene(const grtx_gaussians *g, grtx_scene *sc, cudaStream_t s)
     p.bvh_codes = sc->bvh_codes;
     p.bvh_builder = sc->bvh_builder;
     p.bvh_width = sc->bvh_width;
+    p.bvh_quantize = sc->bvh_quant;
     grtx_scene *ns = new (std::nothrow) grtx_scene();
     if (!ns) return grtx_fail(GRTX_ERR_OOM, "host allocation failed");
     ns->stream = s;
@@ -1577,6 +1649,8 @@ extern "C" GRTX_API int grtx_build_bvh(const grtx_gaussians *g, const grtx_param
         return grtx_fail(GRTX_ERR_INVALID_ARG, "bvh_width must be 0, 2 or 4");
     if (p->bvh_width == 4 && form != GRTX_FORM_SPHERE)
         return grtx_fail(GRTX_ERR_INVALID_ARG, "4-wide nodes are built for the sphere form only");
+    if (p->bvh_quantize != 0 && (p->bvh_quantize != 1 || p->bvh_width != 4))
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "bvh_quantize is 0, or 1 with bvh_width 4");
     grtx_scene *sc = new (std::nothrow) grtx_scene();
     if (!sc) return grtx_fail(GRTX_ERR_OOM, "host allocation failed");
     sc->stream = S(stream);

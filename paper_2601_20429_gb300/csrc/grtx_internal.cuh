@@ -42,10 +42,11 @@ struct grtx_scene {
     float alpha_min = 0.01f;
     int bvh_codes = GRTX_CODES_SIZED, bvh_builder = GRTX_BUILDER_PLOC;   // as built (for rebuilds)
     int bvh_width = 2;           // 4: nodes4 holds the 4-wide collapse of the binary tree
+    int bvh_quant = 0;           // 1: the 4-wide nodes have quantised child boxes (64 bytes each)
     int64_t n = 0, n_valid = 0, n_leaves = 0, n_nodes = 0;
     float bounds[6] = {0, 0, 0, 0, 0, 0};
     float4 *nodes = nullptr;     // [n_nodes][4]: BVH2 node, see grtx_scene_export
-    float4 *nodes4 = nullptr;    // [n_nodes4][8]: 4-wide nodes (bvh_width 4), see grtx_params
+    float4 *nodes4 = nullptr;    // [n_nodes4][8] (or [4] quantised): 4-wide nodes (bvh_width 4), see grtx_params
     int64_t n_nodes4 = 0;
     float4 *geom = nullptr;      // [n_valid][4]: rows (A_j | mu_j) + (o, -kappa^2 log2(e)/2, id, 0), leaf order
     float4 *tris = nullptr;      // proxy form: [n_leaves][3] world triangle (v0 | gidx, v1, v2)

@@ -217,7 +217,7 @@ int setup(grtx_scene *sc, const grtx_camera *cam, const grtx_params *p, TraceArg
 
 int run(grtx_scene *sc, TraceArgs &a, int k, bool instr, int pass, unsigned *queue, cudaStream_t s, bool wide = false)
 {
-    int form = kernel_form(sc->form, wide);
+    int form = kernel_form(sc->form, wide, sc->bvh_quant != 0);
     bool single = a.traversal == GRTX_TRAVERSAL_SINGLE && pass == PASS_FWD;
     int bps = 0;
     int occ = single ? trace_single_occupancy(form, instr, &bps) : occupancy_k(k, form, instr, pass, &bps);

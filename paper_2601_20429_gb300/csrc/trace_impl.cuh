@@ -28,7 +28,8 @@ struct SceneRef {
 // Leaf kinds of the trace kernels: one analytic unit sphere per Gaussian; one world-space
 // proxy triangle per leaf (monolithic); one Gaussian instance whose leaf test traverses the
 // shared icosphere template in unit-sphere space before the exact test.
-enum : int { FORM_SPHERE = 0, FORM_PROXY = 1, FORM_ICO = 2, FORM_SPHERE4 = 3 };   // 3: sphere leaves, 4-wide nodes
+// 3 and 4: sphere leaves under 4-wide nodes, with float or quantised child boxes
+enum : int { FORM_SPHERE = 0, FORM_PROXY = 1, FORM_ICO = 2, FORM_SPHERE4 = 3, FORM_SPHERE4Q = 4 };
 
 // A camera (rays generated in-kernel) or an explicit ray list.
 struct CamRef {
@@ -518,10 +519,45 @@ __device__ __forceinline__ uint32_t pick4(const uint32_t v[4], int i)
     return i == 0 ? v[0] : (i == 1 ? v[1] : (i == 2 ? v[2] : v[3]));
 }
 
+// Float4 words of one 4-wide node: 8 with float child boxes, 4 with quantised ones.
+template <bool Q>
+__device__ __forceinline__ const float4 *node4(const SceneRef &sc, uint32_t ref)
+{
+    return sc.nodes4 + (Q ? 4 : 8) * (size_t)ref;
+}
+
+// Decoded quantised box coordinate: the node's corner plus q steps (one FMA, exactly as the
+// build checked it). eb: the step's biased exponent.
+__device__ __forceinline__ float dq(uint32_t q, uint32_t eb, float o)
+{
+    return fmaf(__uint2float_rn(q), __uint_as_float(eb << 23), o);
+}
+
 // Entry and exit of the ray in each child box of a 4-wide node (e > x: missed).
+template <bool Q>
 __device__ __forceinline__ void slab4(const float4 *__restrict__ nd, float3 o, float3 inv, float tn, float tf, float e[4],
                                       float x[4], uint32_t c[4])
 {
+    if (Q) {
+        const float4 h = __ldg(nd);
+        const uint4 qa = __ldg(reinterpret_cast<const uint4 *>(nd + 1));
+        const uint4 qb = __ldg(reinterpret_cast<const uint4 *>(nd + 2));
+        const uint4 qc = __ldg(reinterpret_cast<const uint4 *>(nd + 3));
+        const uint32_t eb = __float_as_uint(h.w);
+        const uint32_t ex = eb & 0xffu, ey = (eb >> 8) & 0xffu, ez = (eb >> 16) & 0xffu;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int sh = 8 * j;
+            slab(dq((qa.x >> sh) & 0xffu, ex, h.x), dq((qa.y >> sh) & 0xffu, ey, h.y), dq((qa.z >> sh) & 0xffu, ez, h.z),
+                 dq((qa.w >> sh) & 0xffu, ex, h.x), dq((qb.x >> sh) & 0xffu, ey, h.y), dq((qb.y >> sh) & 0xffu, ez, h.z),
+                 o, inv, tn, tf, e[j], x[j]);
+        }
+        c[0] = qb.z;
+        c[1] = qb.w;
+        c[2] = qc.x;
+        c[3] = qc.y;
+        return;
+    }
     const float4 lx = __ldg(nd), ly = __ldg(nd + 1), lz = __ldg(nd + 2);
     const float4 hx = __ldg(nd + 3), hy = __ldg(nd + 4), hz = __ldg(nd + 5);
     const float4 rf = __ldg(nd + 6);
@@ -576,8 +612,32 @@ __device__ __forceinline__ bool leaf4(const TraceArgs &a, const SceneRef &sc, ui
     return true;
 }
 
+// Entry distance of the ray into child `slot` of 4-wide node `parent`.
+template <bool Q>
+__device__ __forceinline__ float child_entry4(const SceneRef &sc, uint32_t parent, uint32_t slot, float3 o, float3 inv,
+                                              float tn, float tf)
+{
+    float te, x;
+    if (Q) {
+        const float4 *nd = node4<true>(sc, parent);
+        const float4 h = __ldg(nd);
+        const uint4 qa = __ldg(reinterpret_cast<const uint4 *>(nd + 1));
+        const uint4 qb = __ldg(reinterpret_cast<const uint4 *>(nd + 2));
+        const uint32_t eb = __float_as_uint(h.w), sh = 8 * slot;
+        const uint32_t ex = eb & 0xffu, ey = (eb >> 8) & 0xffu, ez = (eb >> 16) & 0xffu;
+        slab(dq((qa.x >> sh) & 0xffu, ex, h.x), dq((qa.y >> sh) & 0xffu, ey, h.y), dq((qa.z >> sh) & 0xffu, ez, h.z),
+             dq((qa.w >> sh) & 0xffu, ex, h.x), dq((qb.x >> sh) & 0xffu, ey, h.y), dq((qb.y >> sh) & 0xffu, ez, h.z), o,
+             inv, tn, tf, te, x);
+    } else {
+        const float *pn = reinterpret_cast<const float *>(node4<false>(sc, parent));
+        slab(__ldg(pn + slot), __ldg(pn + 4 + slot), __ldg(pn + 8 + slot), __ldg(pn + 12 + slot), __ldg(pn + 16 + slot),
+             __ldg(pn + 20 + slot), o, inv, tn, tf, te, x);
+    }
+    return te;
+}
+
 // One round of one ray over 4-wide nodes (the per-ray rounds; see trace_round).
-template <int K, bool INSTR>
+template <int K, bool INSTR, bool Q>
 __device__ __forceinline__ bool trace_round4(const TraceArgs &a, const SceneRef &sc, float3 o, float3 d, float3 inv,
                                              float tn, float tf, float Lt, uint32_t Li, bool ckpt, bool from_root,
                                              uint32_t src, int n_src, uint32_t dst, int &n_dst, uint32_t ev,
@@ -620,7 +680,7 @@ __device__ __forceinline__ bool trace_round4(const TraceArgs &a, const SceneRef 
             }
             float e[4], x[4];
             uint32_t c[4];
-            slab4(sc.nodes4 + 8 * (size_t)ref, o, inv, tn, tf, e, x, c);
+            slab4<Q>(node4<Q>(sc, ref), o, inv, tn, tf, e, x, c);
             int ord[4] = {0, 1, 2, 3};
             int nh = 0;
 #pragma unroll
@@ -674,7 +734,7 @@ __device__ __forceinline__ bool trace_round4(const TraceArgs &a, const SceneRef 
 // active lane enters first and keeps the others, with the lanes that want them, on the warp's
 // stack (entries: child, parent << 2 | child slot, lane mask); a popped child's entry
 // distance is recomputed per lane from its box in the parent.
-template <int K, bool INSTR>
+template <int K, bool INSTR, bool Q>
 __device__ __forceinline__ bool packet_round4(const TraceArgs &a, const SceneRef &sc, bool valid, uint4 *pst, float3 o,
                                               float3 d, float3 inv, float tn, float tf, float Lt, uint32_t Li,
                                               bool ckpt, uint32_t dst, int &n_dst, uint32_t ev, int &n_ev, KBuf<K> &kb,
@@ -696,12 +756,7 @@ __device__ __forceinline__ bool packet_round4(const TraceArgs &a, const SceneRef
     bool have_te = true;
     for (;;) {
         const bool in = (m >> lane) & 1u;
-        if (!have_te && in) {                          // a popped child: entry from the parent's box
-            const float *pn = reinterpret_cast<const float *>(sc.nodes4 + 8 * (size_t)parent);
-            float x;
-            slab(__ldg(pn + slot), __ldg(pn + 4 + slot), __ldg(pn + 8 + slot), __ldg(pn + 12 + slot),
-                 __ldg(pn + 16 + slot), __ldg(pn + 20 + slot), o, inv, tn, tf, te, x);
-        }
+        if (!have_te && in) te = child_entry4<Q>(sc, parent, slot, o, inv, tn, tf);   // a popped child
         const bool go = in && lane_ok && !(te > tmax);
         if (in && lane_ok && te > tmax && ckpt) {
             if (n_dst >= a.ckpt_cap) {
@@ -721,7 +776,7 @@ __device__ __forceinline__ bool packet_round4(const TraceArgs &a, const SceneRef
             } else {
                 float e[4], x[4];
                 uint32_t c[4];
-                slab4(sc.nodes4 + 8 * (size_t)ref, o, inv, tn, tf, e, x, c);
+                slab4<Q>(node4<Q>(sc, ref), o, inv, tn, tf, e, x, c);
                 bool h[4];
                 unsigned mh[4];
 #pragma unroll
@@ -809,9 +864,9 @@ __device__ __forceinline__ bool trace_round(const TraceArgs &a, const SceneRef &
                                             uint32_t src, int n_src, uint32_t dst, int &n_dst, uint32_t ev,
                                             int &n_ev, KBuf<K> &kb, Counters &cnt)
 {
-    if constexpr (FORM == FORM_SPHERE4)
-        return trace_round4<K, INSTR>(a, sc, o, d, inv, tn, tf, Lt, Li, ckpt, from_root, src, n_src, dst, n_dst, ev,
-                                      n_ev, kb, cnt);
+    if constexpr (FORM == FORM_SPHERE4 || FORM == FORM_SPHERE4Q)
+        return trace_round4<K, INSTR, FORM == FORM_SPHERE4Q>(a, sc, o, d, inv, tn, tf, Lt, Li, ckpt, from_root, src,
+                                                             n_src, dst, n_dst, ev, n_ev, kb, cnt);
     const uint32_t S = (uint32_t)a.n_slots;
     uint2 *__restrict__ const L = a.ck0;      // lists: src, dst and ev are entry offsets into L
     // far children deferred within this round: node refs only (4 bytes each); a popped entry
@@ -960,9 +1015,9 @@ __device__ __forceinline__ bool packet_round(const TraceArgs &a, const SceneRef 
                                              uint32_t ev, int &n_ev, KBuf<K> &kb, Counters &cnt,
                                              bool &lane_ok)
 {
-    if constexpr (FORM == FORM_SPHERE4)
-        return packet_round4<K, INSTR>(a, sc, valid, pst, o, d, inv, tn, tf, Lt, Li, ckpt, dst, n_dst, ev, n_ev, kb,
-                                       cnt, lane_ok);
+    if constexpr (FORM == FORM_SPHERE4 || FORM == FORM_SPHERE4Q)
+        return packet_round4<K, INSTR, FORM == FORM_SPHERE4Q>(a, sc, valid, pst, o, d, inv, tn, tf, Lt, Li, ckpt, dst,
+                                                              n_dst, ev, n_ev, kb, cnt, lane_ok);
     const unsigned full = 0xffffffffu;
     const uint32_t S = (uint32_t)a.n_slots;
     uint2 *__restrict__ const L = a.ck0;      // lists: dst and ev are entry offsets into L
@@ -1623,6 +1678,8 @@ int trace_launch(const TraceArgs &a, int form, bool instr, int pass, int blocks,
     else if (form == FORM_ICO) k_trace<K, FORM_ICO, false, PASS_FWD><<<g, b, 0, s>>>(a);
     else if (form == FORM_SPHERE4 && instr) k_trace<K, FORM_SPHERE4, true, PASS_FWD><<<g, b, 0, s>>>(a);
     else if (form == FORM_SPHERE4) k_trace<K, FORM_SPHERE4, false, PASS_FWD><<<g, b, 0, s>>>(a);
+    else if (form == FORM_SPHERE4Q && instr) k_trace<K, FORM_SPHERE4Q, true, PASS_FWD><<<g, b, 0, s>>>(a);
+    else if (form == FORM_SPHERE4Q) k_trace<K, FORM_SPHERE4Q, false, PASS_FWD><<<g, b, 0, s>>>(a);
     else if (instr) k_trace<K, FORM_SPHERE, true, PASS_FWD><<<g, b, 0, s>>>(a);
     else k_trace<K, FORM_SPHERE, false, PASS_FWD><<<g, b, 0, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? GRTX_OK : GRTX_ERR_CUDA;
@@ -1640,17 +1697,20 @@ int trace_occupancy(int form, bool instr, int pass, int *blocks_per_sm)
     else if (form == FORM_ICO) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_ICO, false, PASS_FWD>, 128, 0);
     else if (form == FORM_SPHERE4 && instr) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_SPHERE4, true, PASS_FWD>, 128, 0);
     else if (form == FORM_SPHERE4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_SPHERE4, false, PASS_FWD>, 128, 0);
+    else if (form == FORM_SPHERE4Q && instr) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_SPHERE4Q, true, PASS_FWD>, 128, 0);
+    else if (form == FORM_SPHERE4Q) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_SPHERE4Q, false, PASS_FWD>, 128, 0);
     else if (instr) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_SPHERE, true, PASS_FWD>, 128, 0);
     else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_SPHERE, false, PASS_FWD>, 128, 0);
     return e == cudaSuccess ? GRTX_OK : GRTX_ERR_CUDA;
 }
 
-// Kernel leaf kind of a scene form (wide: the 4-wide nodes of a sphere-form scene).
-inline int kernel_form(int scene_form, bool wide = false)
+// Kernel leaf kind of a scene form (wide: the 4-wide nodes of a sphere-form scene, quantised
+// or not).
+inline int kernel_form(int scene_form, bool wide = false, bool quant = false)
 {
     return scene_form == GRTX_FORM_PROXY20 ? FORM_PROXY
            : (scene_form == GRTX_FORM_ICO20 || scene_form == GRTX_FORM_ICO80) ? FORM_ICO
-           : wide ? FORM_SPHERE4 : FORM_SPHERE;
+           : wide ? (quant ? FORM_SPHERE4Q : FORM_SPHERE4) : FORM_SPHERE;
 }
 
 template <int K>

@@ -99,7 +99,7 @@ class grtx_params(C.Structure):
     _fields_ = [("k", C.c_int32), ("traversal", C.c_int32), ("alpha_min", C.c_float), ("T_min", C.c_float),
                 ("alpha_max", C.c_float), ("bg", C.c_float * 3), ("ckpt_capacity", C.c_int32),
                 ("evict_capacity", C.c_int32), ("bvh_codes", C.c_int32), ("bvh_builder", C.c_int32),
-                ("packet_stack", C.c_int32), ("bvh_width", C.c_int32)]
+                ("packet_stack", C.c_int32), ("bvh_width", C.c_int32), ("bvh_quantize", C.c_int32)]
 
 
 class grtx_camera(C.Structure):
@@ -286,10 +286,11 @@ BVH_BUILDERS = {"ploc": 0, "lbvh": 1}
 
 def make_params(k=16, traversal=0, alpha_min=0.01, T_min=1e-3, alpha_max=0.99, bg=(0.0, 0.0, 0.0),
                 ckpt_capacity=0, evict_capacity=0, bvh_codes=0, bvh_builder=0, packet_stack=0,
-                bvh_width=0) -> grtx_params:
+                bvh_width=0, bvh_quantize=0) -> grtx_params:
     p = grtx_params()
     p.packet_stack = int(packet_stack)
     p.bvh_width = int(bvh_width)
+    p.bvh_quantize = int(bvh_quantize)
     p.bvh_codes = BVH_CODES[bvh_codes] if isinstance(bvh_codes, str) else int(bvh_codes)
     p.bvh_builder = BVH_BUILDERS[bvh_builder] if isinstance(bvh_builder, str) else int(bvh_builder)
     p.k, p.traversal = int(k), int(traversal)

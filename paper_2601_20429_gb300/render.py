@@ -34,7 +34,7 @@ class Scene:
 
     def __init__(self, means, log_scales, quats, logits, sh, sh_degree: int, form: str = "sphere",
                  alpha_min: float = 0.01, stream=None, bvh_codes: str = "sized", bvh_builder: str = "ploc",
-                 bvh_width: int = 2):
+                 bvh_width: int = 2, bvh_quantize: bool = False):
         dev = torch.device("cuda", torch.cuda.current_device())
         self.tensors = tuple(_cuda_f32(a, dev) for a in (means, log_scales, quats, logits, sh))
         self.sh_degree = int(sh_degree)
@@ -44,14 +44,15 @@ class Scene:
         self.bvh_codes = bvh_codes
         self.bvh_builder = bvh_builder
         self.bvh_width = int(bvh_width)
-        p = N.make_params(alpha_min=alpha_min, bvh_codes=bvh_codes, bvh_builder=bvh_builder, bvh_width=bvh_width)
+        p = N.make_params(alpha_min=alpha_min, bvh_codes=bvh_codes, bvh_builder=bvh_builder, bvh_width=bvh_width,
+                          bvh_quantize=int(bool(bvh_quantize)))
         self.handle = N.grtx_build_bvh(self._g, p, FORMS[form], stream)
 
     @classmethod
     def from_params(cls, g, form="sphere", alpha_min=0.01, stream=None, bvh_codes="sized", bvh_builder="ploc",
-                    bvh_width=2):
+                    bvh_width=2, bvh_quantize=False):
         return cls(g.means, g.log_scales, g.quats, g.logits, g.sh, g.sh_degree, form, alpha_min, stream, bvh_codes,
-                   bvh_builder, bvh_width)
+                   bvh_builder, bvh_width, bvh_quantize)
 
     def update(self, means, log_scales, quats, logits, sh, mode: str = "refit", stream=None) -> bool:
         """New parameters for the same Gaussians (same n and SH degree), in place: "refit" keeps

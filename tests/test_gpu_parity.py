@@ -244,8 +244,8 @@ def test_rays_match_oracle(kind):
 # ------------------------------------------------------------------ a5-a9: forward trace
 
 
-def _gpu_render(g, cam, form="sphere", rays=None, bvh_width=2, **kw):
-    sc = R.Scene.from_params(g, form=form, bvh_width=bvh_width)
+def _gpu_render(g, cam, form="sphere", rays=None, bvh_width=2, bvh_quantize=False, **kw):
+    sc = R.Scene.from_params(g, form=form, bvh_width=bvh_width, bvh_quantize=bvh_quantize)
     if bvh_width == 4:
         kw["bvh_width"] = 4
     out = R.render(sc, cam, rays=rays, ids_cap=kw.pop("ids_cap", 64), want_n_blended=True, want_stats=True, **kw)
@@ -301,13 +301,15 @@ def test_forward_dense_parity_both_traversals(dense, k):
 # ------------------------------------------------------------------ 4-wide nodes (paper's wide BVH)
 
 
+@pytest.mark.parametrize("quant", [False, True])
 @pytest.mark.parametrize("k", [4, 16])
 @pytest.mark.parametrize("traversal", ["checkpoint", "restart"])
-def test_wide_nodes_parity(dense, k, traversal):
-    """The 4-wide collapse of the tree (bvh_width 4) gives the oracle's image and blend lists,
-    never fetches outside the scene, and fetches fewer nodes than the binary tree."""
+def test_wide_nodes_parity(dense, k, traversal, quant):
+    """The 4-wide collapse of the tree (bvh_width 4, float or quantised child boxes) gives the
+    oracle's image and blend lists, never fetches outside the scene, and fetches fewer nodes
+    than the binary tree."""
     g, cam, S, rays, ref = dense
-    w = _gpu_render(g, cam, k=k, traversal=traversal, ids_cap=256, bvh_width=4)
+    w = _gpu_render(g, cam, k=k, traversal=traversal, ids_cap=256, bvh_width=4, bvh_quantize=quant)
     _check_image(w, ref, S, rays)
     b = _gpu_render(g, cam, k=k, traversal=traversal, ids_cap=256)
     assert w["stats"]["fallbacks"] == 0 and w["stats"]["stack_overflow"] == 0
@@ -317,22 +319,24 @@ def test_wide_nodes_parity(dense, k, traversal):
     assert float(np.abs(w["rgbT"] - b["rgbT"]).max()) <= RGB_TOL
 
 
-def test_wide_nodes_tiny_every_k(tiny):
+@pytest.mark.parametrize("quant", [False, True])
+def test_wide_nodes_tiny_every_k(tiny, quant):
     g, cam, S, rays, ref = tiny
     for k in (1, 2, 8, 32):
-        res = _gpu_render(g, cam, k=k, bvh_width=4)
+        res = _gpu_render(g, cam, k=k, bvh_width=4, bvh_quantize=quant)
         _check_image(res, ref, S, rays)
         assert res["stats"]["blended"] == int(ref["n_blend"].sum())
 
 
-def test_wide_nodes_fallbacks_are_exact(dense):
+@pytest.mark.parametrize("quant", [False, True])
+def test_wide_nodes_fallbacks_are_exact(dense, quant):
     """Tiny list capacities (rays redo rounds from the root) and a short warp stack (packets
     fall back to per-ray rounds) give the same image over 4-wide nodes."""
     g, cam, S, rays, ref = dense
-    a = _gpu_render(g, cam, k=4, ids_cap=256, bvh_width=4, ckpt_capacity=2, evict_capacity=1)
+    a = _gpu_render(g, cam, k=4, ids_cap=256, bvh_width=4, bvh_quantize=quant, ckpt_capacity=2, evict_capacity=1)
     assert a["stats"]["fallbacks"] > 0
     _check_image(a, ref, S, rays)
-    b = _gpu_render(g, cam, k=4, ids_cap=256, bvh_width=4, packet_stack=2)
+    b = _gpu_render(g, cam, k=4, ids_cap=256, bvh_width=4, bvh_quantize=quant, packet_stack=2)
     _check_image(b, ref, S, rays)
 
 
@@ -345,6 +349,8 @@ def test_wide_nodes_argument_errors(dense):
     sc.close()
     with pytest.raises(N.GrtxError):
         R.Scene.from_params(g, form="proxy20", bvh_width=4)
+    with pytest.raises(N.GrtxError):
+        R.Scene.from_params(g, bvh_quantize=True)              # quantised boxes need bvh_width 4
     sw = R.Scene.from_params(g, bvh_width=4)
     with pytest.raises(N.GrtxError):
         R.render(sw, cam, k=8, bvh_width=4, traversal="single")
@@ -600,14 +606,15 @@ def test_forward_surface_full_size_sampled():
     assert not bad
     # the two instantiations differ only in the compiler's contraction of the blend arithmetic
     assert float(np.abs(timed - rgbT).max()) <= RGB_TOL
-    # the same frame over the 4-wide collapse of the same tree
-    sc4 = R.Scene.from_params(g, bvh_width=4)
-    wide = R.render(sc4, cam, k=16, bvh_width=4)["rgbT"]
-    st4 = N.stats_dict(R.render(sc4, cam, k=16, bvh_width=4, want_stats=True)["stats"])
-    torch.cuda.synchronize()
-    assert float(np.abs(wide.cpu().numpy() - timed).max()) <= RGB_TOL
-    assert st4["bounds_errors"] == 0 and st4["fallbacks"] == 0
-    sc4.close()
+    # the same frame over the 4-wide collapse of the same tree, float and quantised child boxes
+    for quant in (False, True):
+        sc4 = R.Scene.from_params(g, bvh_width=4, bvh_quantize=quant)
+        wide = R.render(sc4, cam, k=16, bvh_width=4)["rgbT"]
+        st4 = N.stats_dict(R.render(sc4, cam, k=16, bvh_width=4, want_stats=True)["stats"])
+        torch.cuda.synchronize()
+        assert float(np.abs(wide.cpu().numpy() - timed).max()) <= RGB_TOL
+        assert st4["bounds_errors"] == 0 and st4["fallbacks"] == 0
+        sc4.close()
     assert np.all(timed[:, 3] >= 0) and np.all(timed[:, 3] <= 1) and np.isfinite(timed).all()
     assert float(timed[:, 3].min()) < 0.5        # the frame hits Gaussians
     sc.close()

@@ -217,18 +217,19 @@ def test_memory_trim_between_scenes():
         N.grtx_memory_trim(-5)
 
 
+@pytest.mark.parametrize("quant", [False, True])
 @pytest.mark.parametrize("mode", ["refit", "rebuild"])
-def test_wide_nodes_follow_an_update(mode):
+def test_wide_nodes_follow_an_update(mode, quant):
     """A scene built with 4-wide nodes keeps them current through a refit (collapsed again
     from the refitted binary tree) and a rebuild: the 4-wide image after the update equals
     the image of a scene built from scratch with the new parameters."""
     g = _base()
     h = _moved(g, seed=3)
-    sc = R.Scene.from_params(g, bvh_width=4)
+    sc = R.Scene.from_params(g, bvh_width=4, bvh_quantize=quant)
     _image(sc, bvh_width=4)
     sc.update(*h.arrays(), mode=mode)
     got = _image(sc, bvh_width=4)
-    fresh = R.Scene.from_params(h, bvh_width=4)
+    fresh = R.Scene.from_params(h, bvh_width=4, bvh_quantize=quant)
     ref = _image(fresh, bvh_width=4)
     _same(got, ref)
     bin_ref = _fresh(h)
