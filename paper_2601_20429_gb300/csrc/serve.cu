@@ -9,6 +9,7 @@
 #include <time.h>
 
 #include <algorithm>
+#include <cstring>
 #include <deque>
 #include <map>
 #include <new>
@@ -18,7 +19,8 @@
 #include "trace_impl.cuh"
 
 #define GRTX_EXTERN_SERVE(K)                                                                                 \
-    extern template int serve_launch<K>(const TraceArgs &, const ServeSeg *, int, int, cudaStream_t);        \
+    extern template int serve_launch<K>(const TraceArgs &, const ServeSeg *, int, int, cudaStream_t, unsigned *,  \
+                                        unsigned *, unsigned);                                                    \
     extern template int serve_occupancy<K>(int *);
 GRTX_EXTERN_SERVE(1)
 GRTX_EXTERN_SERVE(2)
@@ -44,15 +46,16 @@ double now_s()
     return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
 }
 
-int serve_launch_k(int k, const TraceArgs &a, const ServeSeg *segs, int n, int blocks, cudaStream_t s)
+int serve_launch_k(int k, const TraceArgs &a, const ServeSeg *segs, int n, int blocks, cudaStream_t s,
+                   unsigned *seg_done, unsigned *seg_flag, unsigned seq)
 {
     switch (k) {
-    case 1: return serve_launch<1>(a, segs, n, blocks, s);
-    case 2: return serve_launch<2>(a, segs, n, blocks, s);
-    case 4: return serve_launch<4>(a, segs, n, blocks, s);
-    case 8: return serve_launch<8>(a, segs, n, blocks, s);
-    case 16: return serve_launch<16>(a, segs, n, blocks, s);
-    default: return serve_launch<32>(a, segs, n, blocks, s);
+    case 1: return serve_launch<1>(a, segs, n, blocks, s, seg_done, seg_flag, seq);
+    case 2: return serve_launch<2>(a, segs, n, blocks, s, seg_done, seg_flag, seq);
+    case 4: return serve_launch<4>(a, segs, n, blocks, s, seg_done, seg_flag, seq);
+    case 8: return serve_launch<8>(a, segs, n, blocks, s, seg_done, seg_flag, seq);
+    case 16: return serve_launch<16>(a, segs, n, blocks, s, seg_done, seg_flag, seq);
+    default: return serve_launch<32>(a, segs, n, blocks, s, seg_done, seg_flag, seq);
     }
 }
 
@@ -75,6 +78,7 @@ struct SrvReq {
     unsigned next = 0;         // first item not yet scheduled
     double t_admit = 0;
     size_t out_bytes = 0;      // > 0: the server allocates the output from its arena at admission
+    int pending_segs = 0;      // segments scheduled in steps and not yet complete
 };
 
 // First-fit allocator over the output arena (offsets on the host, 256-byte granules).
@@ -134,6 +138,9 @@ struct Arena {
 
 // A step slot: each has its own stream, per-slot lists and queue counter, so that the next
 // step's blocks take the SMs the previous step's blocks leave while its slowest warps finish.
+// Completion is per segment: the warp that finishes a segment's last tile raises the
+// segment's flag in pinned host memory, so a request is reported as soon as its own tiles are
+// done, not when the whole step ends.
 struct SrvStep {
     cudaEvent_t ev = nullptr;
     cudaStream_t s = nullptr;  // slot 0: the server's stream; the others: created by the server
@@ -141,7 +148,12 @@ struct SrvStep {
     void *ws = nullptr;        // checkpoint and eviction lists of this slot's launches
     ServeSeg *h = nullptr;     // pinned host copy of the segment table
     ServeSeg *d = nullptr;     // device segment table
-    std::vector<SrvReq *> finishing;
+    unsigned *d_done = nullptr;     // device: items finished per segment
+    unsigned *h_flag = nullptr;     // pinned, mapped: the step's sequence number once a segment is done
+    unsigned *d_flag = nullptr;     // device address of h_flag
+    unsigned seq = 0;               // this launch's sequence number
+    std::vector<SrvReq *> seg_req;  // request of each segment
+    std::vector<char> seg_seen;     // segment completion already taken into account
     bool busy = false;
 };
 
@@ -166,6 +178,7 @@ struct grtx_server {
     size_t device_bytes = 0;    // everything the server allocated on the device
     unsigned *queue = nullptr;  // one ray-queue counter per step slot
     Arena arena;                // server-owned outputs (budget > 0)
+    unsigned seq = 0;           // launches so far (segment flags carry their launch's number)
 };
 
 namespace {
@@ -178,6 +191,8 @@ void server_free(grtx_server *v)
         if (st.ev) cudaEventDestroy(st.ev);
         if (st.h) cudaFreeHost(st.h);
         if (st.d) cudaFree(st.d);
+        if (st.d_done) cudaFree(st.d_done);
+        if (st.h_flag) cudaFreeHost(st.h_flag);
         if (st.ws) cudaFree(st.ws);
         if (st.own_stream) cudaStreamDestroy(st.s);
     }
@@ -188,30 +203,45 @@ void server_free(grtx_server *v)
     delete v;
 }
 
-// Enqueue one step over the admitted requests' unscheduled items (FIFO, up to max_rays).
+// Enqueue one step over the admitted requests' unscheduled items: requests are taken in
+// admission order up to max_rays, and the step's queue hands out the smaller pieces first, so
+// that small requests, reported per segment, finish early in the step.
 int schedule_step(grtx_server *v, int si)
 {
     SrvStep &st = v->steps[si];
-    st.finishing.clear();
+    st.seg_req.clear();
+    st.seg_seen.clear();
     int64_t budget = std::max<int64_t>(32, v->max_rays / 32 * 32);
-    unsigned total = 0;
-    int n = 0;
+    struct Piece {
+        SrvReq *r;
+        unsigned begin, count;
+    };
+    std::vector<Piece> pieces;
     for (SrvReq *r : v->active) {
         if (r->next >= r->n_items) continue;
         if (budget <= 0) break;
         unsigned take = (unsigned)std::min<int64_t>((int64_t)(r->n_items - r->next), budget);
-        ServeSeg &g = st.h[n++];
-        g.sc = grtx_scene_ref(v->scenes[r->r.scene_id]);
-        g.cam = r->cam;
-        g.out = (float4 *)r->r.d_rgbT;
-        g.item_begin = r->next;
-        g.step_begin = total;
-        g.count = take;
-        g.pad = 0;
+        pieces.push_back({r, r->next, take});
         r->next += take;
-        total += take;
         budget -= take;
-        if (r->next >= r->n_items) st.finishing.push_back(r);
+    }
+    std::stable_sort(pieces.begin(), pieces.end(), [](const Piece &x, const Piece &y) { return x.count < y.count; });
+    unsigned total = 0;
+    int n = 0;
+    for (const Piece &pc : pieces) {
+        ServeSeg &g = st.h[n];
+        g.sc = grtx_scene_ref(v->scenes[pc.r->r.scene_id]);
+        g.cam = pc.r->cam;
+        g.out = (float4 *)pc.r->r.d_rgbT;
+        g.item_begin = pc.begin;
+        g.step_begin = total;
+        g.count = pc.count;
+        g.pad = 0;
+        total += pc.count;
+        st.seg_req.push_back(pc.r);
+        st.seg_seen.push_back(0);
+        pc.r->pending_segs++;
+        ++n;
     }
     if (n == 0) return GRTX_OK;
     TraceArgs a = v->a;
@@ -225,7 +255,9 @@ int schedule_step(grtx_server *v, int si)
     a.discard = lists_discardable(a);
     GRTX_CUDA(cudaMemcpyAsync(st.d, st.h, sizeof(ServeSeg) * n, cudaMemcpyHostToDevice, st.s));
     GRTX_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned), st.s));
-    if (serve_launch_k(v->p.k, a, st.d, n, v->blocks, st.s) != GRTX_OK) {
+    GRTX_CUDA(cudaMemsetAsync(st.d_done, 0, sizeof(unsigned) * n, st.s));
+    st.seq = ++v->seq;
+    if (serve_launch_k(v->p.k, a, st.d, n, v->blocks, st.s, st.d_done, st.d_flag, st.seq) != GRTX_OK) {
         cudaError_t e = cudaGetLastError();
         return grtx_cuda_fail(e == cudaSuccess ? cudaErrorLaunchFailure : e, "serve step launch");
     }
@@ -275,7 +307,8 @@ extern "C" GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scen
     const int blocks_full = sms * bps;
     if ((size_t)blocks_full * 128 * (2 * C + E) >= ((size_t)1 << 31))
         return grtx_fail(GRTX_ERR_INVALID_ARG, "checkpoint/eviction capacities too large for the resident ray slots");
-    const size_t tables = kSteps * kQueueStride * sizeof(unsigned) + (size_t)kSteps * sizeof(ServeSeg) * inflight_cap;
+    const size_t tables = kSteps * kQueueStride * sizeof(unsigned) +
+                          (size_t)kSteps * (sizeof(ServeSeg) + sizeof(unsigned)) * inflight_cap;
     int n_steps = kSteps, blocks = blocks_full;
     size_t arena = 0;
     if (mem_budget_bytes > 0) {
@@ -331,6 +364,13 @@ extern "C" GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scen
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sst.ev, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaMallocHost((void **)&sst.h, sizeof(ServeSeg) * v->max_inflight);
         if (e == cudaSuccess) e = cudaMalloc((void **)&sst.d, sizeof(ServeSeg) * v->max_inflight);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&sst.d_done, sizeof(unsigned) * v->max_inflight);
+        if (e == cudaSuccess) e = cudaHostAlloc((void **)&sst.h_flag, sizeof(unsigned) * v->max_inflight,
+                                                cudaHostAllocMapped);
+        if (e == cudaSuccess) {
+            std::memset(sst.h_flag, 0, sizeof(unsigned) * v->max_inflight);
+            e = cudaHostGetDevicePointer((void **)&sst.d_flag, sst.h_flag, 0);
+        }
     }
     char *arena_base = nullptr;
     if (e == cudaSuccess && arena > 0) e = cudaMalloc((void **)&arena_base, arena);
@@ -342,7 +382,7 @@ extern "C" GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scen
     v->arena.reset(arena_base, arena);
     v->list_bytes = (size_t)n_steps * ws;
     v->device_bytes = v->list_bytes + arena + kSteps * kQueueStride * sizeof(unsigned) +
-                      (size_t)n_steps * sizeof(ServeSeg) * v->max_inflight;
+                      (size_t)n_steps * (sizeof(ServeSeg) + sizeof(unsigned)) * v->max_inflight;
     a.n_slots = n_slots;
     *out = v;
     return GRTX_OK;
@@ -393,28 +433,44 @@ extern "C" GRTX_API int grtx_server_poll(grtx_server *v, grtx_completion *done, 
     if (!v || !n_done || max_done < 0 || (max_done > 0 && !done)) return grtx_fail(GRTX_ERR_INVALID_ARG, "bad poll arguments");
     *n_done = 0;
     int got = 0;
+    // a segment is complete: the request is reported once all of its items have been
+    // scheduled and all of its segments are complete
+    auto segment_done = [&](SrvStep &st, size_t j, double t) {
+        st.seg_seen[j] = 1;
+        SrvReq *r = st.seg_req[j];
+        if (--r->pending_segs > 0 || r->next < r->n_items) return;
+        grtx_completion c;
+        c.tag = r->r.tag;
+        c.status = GRTX_OK;
+        c.reserved = 0;
+        c.t_admit = r->t_admit;
+        c.t_done = t;
+        c.d_rgbT = r->r.d_rgbT;
+        v->backlog.push_back(c);
+        v->active.erase(std::find(v->active.begin(), v->active.end(), r));
+        delete r;
+        ++got;
+    };
     for (;;) {
-        // completions of finished steps
+        // segments finished inside running steps
+        double t = now_s();
+        for (int si : v->inflight) {
+            SrvStep &st = v->steps[si];
+            const volatile unsigned *flag = st.h_flag;
+            for (size_t j = 0; j < st.seg_req.size(); ++j)
+                if (!st.seg_seen[j] && flag[j] == st.seq) segment_done(st, j, t);
+        }
+        // finished steps free their slots (every segment is complete once the launch is)
         while (!v->inflight.empty()) {
             SrvStep &st = v->steps[v->inflight.front()];
             cudaError_t q = cudaEventQuery(st.ev);
             if (q == cudaErrorNotReady) break;
             if (q != cudaSuccess) return grtx_cuda_fail(q, "serve step");
-            double t = now_s();
-            for (SrvReq *r : st.finishing) {
-                grtx_completion c;
-                c.tag = r->r.tag;
-                c.status = GRTX_OK;
-                c.reserved = 0;
-                c.t_admit = r->t_admit;
-                c.t_done = t;
-                c.d_rgbT = r->r.d_rgbT;
-                v->backlog.push_back(c);
-                v->active.erase(std::find(v->active.begin(), v->active.end(), r));
-                delete r;
-                ++got;
-            }
-            st.finishing.clear();
+            t = now_s();
+            for (size_t j = 0; j < st.seg_req.size(); ++j)
+                if (!st.seg_seen[j]) segment_done(st, j, t);
+            st.seg_req.clear();
+            st.seg_seen.clear();
             st.busy = false;
             v->inflight.pop_front();
         }

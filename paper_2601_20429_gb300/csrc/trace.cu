@@ -19,7 +19,8 @@ GRTX_EXTERN_TRACE(16)
 GRTX_EXTERN_TRACE(32)
 
 #define GRTX_EXTERN_SEGMENTS(K)                                                                          \
-    extern template int serve_launch<K>(const TraceArgs &, const ServeSeg *, int, int, cudaStream_t);     \
+    extern template int serve_launch<K>(const TraceArgs &, const ServeSeg *, int, int, cudaStream_t, unsigned *, \
+                                        unsigned *, unsigned);                                               \
     extern template int serve_occupancy<K>(int *);
 GRTX_EXTERN_SEGMENTS(1)
 GRTX_EXTERN_SEGMENTS(2)
@@ -364,12 +365,12 @@ namespace {
 int segments_launch_k(int k, const TraceArgs &a, const ServeSeg *segs, int n, int blocks, cudaStream_t s)
 {
     switch (k) {
-    case 1: return serve_launch<1>(a, segs, n, blocks, s);
-    case 2: return serve_launch<2>(a, segs, n, blocks, s);
-    case 4: return serve_launch<4>(a, segs, n, blocks, s);
-    case 8: return serve_launch<8>(a, segs, n, blocks, s);
-    case 16: return serve_launch<16>(a, segs, n, blocks, s);
-    default: return serve_launch<32>(a, segs, n, blocks, s);
+    case 1: return serve_launch<1>(a, segs, n, blocks, s, nullptr, nullptr, 0u);
+    case 2: return serve_launch<2>(a, segs, n, blocks, s, nullptr, nullptr, 0u);
+    case 4: return serve_launch<4>(a, segs, n, blocks, s, nullptr, nullptr, 0u);
+    case 8: return serve_launch<8>(a, segs, n, blocks, s, nullptr, nullptr, 0u);
+    case 16: return serve_launch<16>(a, segs, n, blocks, s, nullptr, nullptr, 0u);
+    default: return serve_launch<32>(a, segs, n, blocks, s, nullptr, nullptr, 0u);
     }
 }
 

@@ -1603,7 +1603,9 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, PASS == PASS_BWD))
 // Serving step: one persistent launch over the queue items of several requests (each with
 // its own scene, camera and output); a warp's 32 items always belong to one request.
 template <int K>
-__global__ void __launch_bounds__(kBlock, trace_min_blocks(K, false)) k_serve(TraceArgs a, const ServeSeg *__restrict__ segs, int n_segs)
+__global__ void __launch_bounds__(kBlock, trace_min_blocks(K, false))
+    k_serve(TraceArgs a, const ServeSeg *__restrict__ segs, int n_segs, unsigned *seg_done, unsigned *seg_flag,
+            unsigned seq)
 {
     __shared__ float s_kt[K * kBlock];
     __shared__ uint32_t s_ki[K * kBlock];
@@ -1638,6 +1640,19 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, false)) k_serve(Tr
         else
             trace_warp<K, FORM_SPHERE, false, PASS_FWD>(a, sc, sg.out, slot, valid, pix, o, d, tn, tf, kb, cnt,
                                                      s_pst[threadIdx.x >> 5]);
+        if (seg_done) {
+            // the tile's pixels are written; the warp that completes the segment raises its
+            // flag in host memory (each lane's writes fenced before the count)
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) {
+                const unsigned old = atomicAdd(seg_done + lo, 32u);
+                if (old + 32u >= sg.count) {
+                    __threadfence_system();
+                    *reinterpret_cast<volatile unsigned *>(seg_flag + lo) = seq;
+                }
+            }
+        }
         __syncwarp();
         if (a.discard) discard_dead_lists(a, slot & ~31);
     }
@@ -1713,10 +1728,12 @@ inline int kernel_form(int scene_form, bool wide = false, bool quant = false)
            : wide ? (quant ? FORM_SPHERE4Q : FORM_SPHERE4) : FORM_SPHERE;
 }
 
+// seg_done / seg_flag / seq: per-segment completion (see k_serve); NULL for none.
 template <int K>
-int serve_launch(const TraceArgs &a, const ServeSeg *segs, int n_segs, int blocks, cudaStream_t s)
+int serve_launch(const TraceArgs &a, const ServeSeg *segs, int n_segs, int blocks, cudaStream_t s,
+                 unsigned *seg_done = nullptr, unsigned *seg_flag = nullptr, unsigned seq = 0)
 {
-    k_serve<K><<<blocks, 128, 0, s>>>(a, segs, n_segs);
+    k_serve<K><<<blocks, 128, 0, s>>>(a, segs, n_segs, seg_done, seg_flag, seq);
     return cudaGetLastError() == cudaSuccess ? GRTX_OK : GRTX_ERR_CUDA;
 }
 
@@ -1730,5 +1747,6 @@ int serve_occupancy(int *blocks_per_sm)
 #define GRTX_INSTANTIATE_TRACE(K)                                                                  \
     template int trace_launch<K>(const TraceArgs &, int, bool, int, int, cudaStream_t);           \
     template int trace_occupancy<K>(int, bool, int, int *);                                         \
-    template int serve_launch<K>(const TraceArgs &, const ServeSeg *, int, int, cudaStream_t);     \
+    template int serve_launch<K>(const TraceArgs &, const ServeSeg *, int, int, cudaStream_t, unsigned *,    \
+                                 unsigned *, unsigned);                                                    \
     template int serve_occupancy<K>(int *);

@@ -89,6 +89,30 @@ def test_requests_admitted_while_others_run(world):
     srv.close()
 
 
+def test_small_request_completes_before_the_large_one_in_its_step(world):
+    """A request is reported when its own tiles are done, not when its whole step is: in one
+    step holding a 333x217 view and a 64x64 view (submitted in that order), the small view's
+    tiles run first and it completes no later than the large one, with both images equal to
+    the lone renders."""
+    sc, reqs, alone = world
+    big = next(j for j, r in enumerate(reqs) if (r["camera"]["width"], r["camera"]["height"]) == (333, 217))
+    small = next(j for j, r in enumerate(reqs) if (r["camera"]["width"], r["camera"]["height"]) == (64, 64))
+    srv = Server(sc, k=16, max_rays_per_step=1 << 22, max_inflight=8)
+    bufs = _bufs(reqs)
+    done = {}
+    for _ in range(3):
+        srv.submit([(reqs[j]["scene"], reqs[j]["camera"], bufs[j], j) for j in (big, small)])
+        got = []
+        while len(got) < 2:
+            got += srv.poll(wait=True)
+        torch.cuda.synchronize()
+        done = {c["tag"]: c for c in got}
+        assert done[small]["t_done"] <= done[big]["t_done"]
+    _same(alone[big], bufs[big])
+    _same(alone[small], bufs[small])
+    srv.close()
+
+
 def test_server_errors(world):
     sc, reqs, alone = world
     srv = Server(sc, k=16)
