@@ -438,7 +438,7 @@ def run_stream(srv, reqs, rate_hz: float) -> dict:
             "offered_Mrays_per_s": rays / (reqs[-1]["arrival"] - reqs[0]["arrival"]) / 1e6}
 
 
-def bench_serving(n_requests: int, max_rays_per_step: int = 4 << 20, max_inflight: int = 64,
+def bench_serving(n_requests: int, max_rays_per_step: int = 0, max_inflight: int = 64,
                   modes: bool = False, restart: bool = False, capacity_rates=(), capacity_requests: int = 1000):
     """The serving configuration: four resident scenes, the 200 req/s stream through the
     server (checkpointed rounds); optionally the same stream with restart traversal, the
@@ -462,8 +462,14 @@ def bench_serving(n_requests: int, max_rays_per_step: int = 4 << 20, max_infligh
         return srv
 
     srv = server("checkpoint")
+    i0 = srv.info()
     res = run_stream(srv, reqs, 200.0)
-    res.update(max_rays_per_step=max_rays_per_step, max_inflight=max_inflight, traversal="checkpoint")
+    i1 = srv.info()
+    # 0: the server's default, two rounds of its launch's warps' 32-ray tiles
+    chunk = max_rays_per_step or 2 * 32 * 4 * i0["blocks_per_step"]
+    res.update(max_rays_per_step=chunk, max_inflight=max_inflight, traversal="checkpoint",
+               launches=i1["n_launches"] - i0["n_launches"], appends=i1["n_appends"] - i0["n_appends"],
+               retried_tiles=i1["n_retried_tiles"] - i0["n_retried_tiles"])
     if capacity_rates:
         sweep = []
         for rate in capacity_rates:

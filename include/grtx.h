@@ -664,16 +664,26 @@ typedef struct grtx_completion {
 } grtx_completion;
 
 /* Create a server over n_scenes built scenes (not owned; they must outlive the server).
- * max_rays_per_step: rays per persistent launch (0: 4M); max_inflight: requests admitted at
- * once (0: 64); p: tracing parameters for every request (checkpoint or restart traversal;
+ * p: tracing parameters for every request (checkpoint or restart traversal;
  * GRTX_TRAVERSAL_SINGLE is rejected with GRTX_ERR_INVALID_ARG). Host call; waits for the
  * device once (the scenes' builds). A request's output is complete when its completion is
- * reported (steps are reported in the order they were enqueued).
+ * reported.
+ *
+ * Scheduling. A step is one persistent launch of the server's trace kernel; its queue hands
+ * out 32-ray tiles of the admitted requests (mixed scenes and resolutions). The running
+ * ("live") launch is fed while it runs: the host publishes up to max_rays_per_step more rays
+ * (0: two rounds of the launch's warps, 32 rays each: 311,296 at full residency on 152 SMs)
+ * whenever less than half of that is left unclaimed, choosing the requests by deadline (see
+ * grtx_server_set_order), so that a request that arrives waits for at most about that much
+ * of others' work. Warps without work wait for more (see grtx_server_set_linger). A launch's
+ * segment table holds 4 x max_inflight pieces of requests; when it is full, or the launch has
+ * gone idle, the next work starts a new launch in a free step slot while the old one
+ * finishes. max_inflight: requests admitted at once (0: 64).
  *
  * Memory (the paper sizes its checkpoint and eviction buffers per resident ray slot and
  * reports their total, Sec. V-E). The server runs up to 4 step slots, each with its own
  * stream (slot 0 uses `stream`, the others streams the server creates), queue counter and
- * checkpoint/eviction lists, so that a step's launch fills the SMs its predecessors' last
+ * checkpoint/eviction lists, so that a new launch fills the SMs the finishing launch's last
  * warps leave. One step slot's lists take (resident ray slots) x (2 ckpt_capacity +
  * evict_capacity) x 8 bytes: about 1.3 GB with the default capacities at full residency on
  * 152 SMs.
@@ -698,6 +708,24 @@ GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scenes, const g
  * GRTX_ERR_NOT_FOUND if d_rgbT is not a live server-owned output. */
 GRTX_API int grtx_server_release(grtx_server *srv, float *d_rgbT);
 
+/* How long, in nanoseconds, the warps of a running step launch that has run out of work
+ * wait for more (default 2,000,000: 2 ms; each new publication restarts the wait). Work that
+ * arrives while a launch runs, or while its warps wait, is appended to that launch (its warps
+ * take it without a new launch); the host appends to a launch without work only while its
+ * last publication is less than linger_ns / 2 old, so that no warp stops before the append
+ * lands (a tile published to a warp that has stopped all the same is traced by a later
+ * launch). Waiting warps keep their SMs: kernels of other streams start on them once the
+ * launch ends, at most linger_ns after its last publication. 0: a launch ends as soon as its
+ * published work is taken. Applies to launches started after the call. Host call.
+ * GRTX_ERR_INVALID_ARG if linger_ns is negative or above 1 s. */
+GRTX_API int grtx_server_set_linger(grtx_server *srv, int64_t linger_ns);
+
+/* Order in which admitted requests' work is published to the running launch: by deadline,
+ * admission time + size_ns_per_ray x the request's rays (default 10 ns per ray). 0: admission
+ * order; large: the smallest request first. Host call. GRTX_ERR_INVALID_ARG unless
+ * 0 <= size_ns_per_ray <= 1e9. */
+GRTX_API int grtx_server_set_order(grtx_server *srv, double size_ns_per_ray);
+
 /* Sizes chosen at creation and current use (host call). */
 typedef struct grtx_server_info {
     int32_t n_step_slots;        /* step slots (streams) the server runs, 1..4             */
@@ -708,6 +736,9 @@ typedef struct grtx_server_info {
     int64_t device_bytes;        /* all device memory the server holds                      */
     int32_t n_inflight;          /* admitted, not yet completed                            */
     int32_t n_pending;           /* submitted, not yet admitted                            */
+    int64_t n_launches;          /* step launches so far                                    */
+    int64_t n_appends;           /* publications of new work to a running launch so far     */
+    int64_t n_retried_tiles;     /* 32-ray tiles a launch gave up and a later one traced    */
 } grtx_server_info;
 GRTX_API int grtx_server_get_info(const grtx_server *srv, grtx_server_info *info);
 
@@ -717,11 +748,13 @@ GRTX_API int grtx_server_get_info(const grtx_server *srv, grtx_server_info *info
  * GRTX_ERR_INVALID_ARG); GRTX_ERR_NOT_FOUND for an unknown scene id. */
 GRTX_API int grtx_server_submit(grtx_server *srv, const grtx_request *reqs, int n);
 
-/* Advance the server: admit pending requests into free slots (continuous batching), enqueue
- * steps while there is work and fewer than 4 steps are in flight, and report requests whose
- * last step has completed. Writes at most max_done completions to done (host) and their
- * count to *n_done. Non-blocking unless wait != 0, in which case it blocks until at least one
- * request completes or nothing is in flight. */
+/* Advance the server: admit pending requests (continuous batching), publish work to the live
+ * launch or start a launch (see grtx_server_create), and report requests whose tiles have all
+ * been traced (each piece of a request raises a flag in host memory when its last tile is
+ * written). Writes at most max_done completions to done (host) and their count to *n_done.
+ * Non-blocking unless wait != 0, in which case it blocks until at least one request
+ * completes or none is admitted. Call it often while requests are in flight: work is
+ * published only when it runs. */
 GRTX_API int grtx_server_poll(grtx_server *srv, grtx_completion *done, int max_done, int *n_done,
                               int wait);
 

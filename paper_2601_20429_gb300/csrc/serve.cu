@@ -1,10 +1,12 @@
 // Serving: several resident scenes and a stream of camera requests. Requests are admitted
-// into a bounded set of slots as earlier ones finish (continuous batching), and, under a
-// memory budget, only while their outputs fit the server's output arena; each step is one
-// persistent launch whose queue concatenates pieces of every admitted request (mixed scenes
-// and resolutions), so rays of new and old requests share the device. Up to four steps are
-// in flight, each on its own stream: the host prepares and enqueues the next while the
-// others run.
+// into a bounded set (continuous batching), and, under a memory budget, only while their
+// outputs fit the server's output arena. One persistent launch (the live launch) traces the
+// 32-ray tiles of every admitted request (mixed scenes and resolutions) from one queue; the
+// host keeps publishing work to it while it runs, a little at a time and earliest deadline
+// first, so that a request that arrives waits for little of the others' work, and the launch
+// never drains into a tail while work is waiting. Its warps wait a short while for more work
+// when there is none. A full or idle launch is closed and the next one starts in another step
+// slot (own stream and lists), taking the SMs the old one's last warps leave.
 #include <cuda_runtime.h>
 #include <time.h>
 
@@ -19,8 +21,8 @@
 #include "trace_impl.cuh"
 
 #define GRTX_EXTERN_SERVE(K)                                                                                 \
-    extern template int serve_launch<K>(const TraceArgs &, const ServeSeg *, int, int, cudaStream_t, unsigned *,  \
-                                        unsigned *, unsigned);                                                    \
+    extern template int serve_launch<K>(const TraceArgs &, const ServeSeg *, const unsigned *, int, int,            \
+                                        cudaStream_t, ServeLive);                                                    \
     extern template int serve_occupancy<K>(int *);
 GRTX_EXTERN_SERVE(1)
 GRTX_EXTERN_SERVE(2)
@@ -38,6 +40,8 @@ namespace {
 constexpr int kMaxPending = 65536;
 constexpr int kSteps = 4;         // step slots (streams) in flight
 constexpr int kQueueStride = 32;   // the slots' queue counters on separate 128-byte lines
+constexpr unsigned kLingerNs = 2000000;   // default wait of a live launch's warps for new work
+constexpr double kSizeNs = 10.0;          // default deadline weight: 10 ns per ray
 
 double now_s()
 {
@@ -46,16 +50,16 @@ double now_s()
     return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
 }
 
-int serve_launch_k(int k, const TraceArgs &a, const ServeSeg *segs, int n, int blocks, cudaStream_t s,
-                   unsigned *seg_done, unsigned *seg_flag, unsigned seq)
+int serve_launch_k(int k, const TraceArgs &a, const ServeSeg *segs, const unsigned *begins, int n, int blocks,
+                   cudaStream_t s, const ServeLive &live)
 {
     switch (k) {
-    case 1: return serve_launch<1>(a, segs, n, blocks, s, seg_done, seg_flag, seq);
-    case 2: return serve_launch<2>(a, segs, n, blocks, s, seg_done, seg_flag, seq);
-    case 4: return serve_launch<4>(a, segs, n, blocks, s, seg_done, seg_flag, seq);
-    case 8: return serve_launch<8>(a, segs, n, blocks, s, seg_done, seg_flag, seq);
-    case 16: return serve_launch<16>(a, segs, n, blocks, s, seg_done, seg_flag, seq);
-    default: return serve_launch<32>(a, segs, n, blocks, s, seg_done, seg_flag, seq);
+    case 1: return serve_launch<1>(a, segs, begins, n, blocks, s, live);
+    case 2: return serve_launch<2>(a, segs, begins, n, blocks, s, live);
+    case 4: return serve_launch<4>(a, segs, begins, n, blocks, s, live);
+    case 8: return serve_launch<8>(a, segs, begins, n, blocks, s, live);
+    case 16: return serve_launch<16>(a, segs, begins, n, blocks, s, live);
+    default: return serve_launch<32>(a, segs, begins, n, blocks, s, live);
     }
 }
 
@@ -79,6 +83,7 @@ struct SrvReq {
     double t_admit = 0;
     size_t out_bytes = 0;      // > 0: the server allocates the output from its arena at admission
     int pending_segs = 0;      // segments scheduled in steps and not yet complete
+    std::vector<std::pair<unsigned, unsigned>> retry;   // {first item, count}: ranges a launch did not trace
 };
 
 // First-fit allocator over the output arena (offsets on the host, 256-byte granules).
@@ -137,10 +142,10 @@ struct Arena {
 };
 
 // A step slot: each has its own stream, per-slot lists and queue counter, so that the next
-// step's blocks take the SMs the previous step's blocks leave while its slowest warps finish.
-// Completion is per segment: the warp that finishes a segment's last tile raises the
-// segment's flag in pinned host memory, so a request is reported as soon as its own tiles are
-// done, not when the whole step ends.
+// launch's blocks take the SMs the previous launch's blocks leave while its slowest warps
+// finish. Completion is per segment (a piece of a request): the warp that finishes a
+// segment's last tile raises the segment's flag in pinned host memory, so a request is
+// reported as soon as its own tiles are done, not when the launch ends.
 struct SrvStep {
     cudaEvent_t ev = nullptr;
     cudaStream_t s = nullptr;  // slot 0: the server's stream; the others: created by the server
@@ -148,12 +153,26 @@ struct SrvStep {
     void *ws = nullptr;        // checkpoint and eviction lists of this slot's launches
     ServeSeg *h = nullptr;     // pinned host copy of the segment table
     ServeSeg *d = nullptr;     // device segment table
+    unsigned *h_begins = nullptr, *d_begins = nullptr;   // each segment's first launch item (pinned / device)
     unsigned *d_done = nullptr;     // device: items finished per segment
     unsigned *h_flag = nullptr;     // pinned, mapped: the step's sequence number once a segment is done
     unsigned *d_flag = nullptr;     // device address of h_flag
     unsigned seq = 0;               // this launch's sequence number
     std::vector<SrvReq *> seg_req;  // request of each segment
     std::vector<char> seg_seen;     // segment completion already taken into account
+    std::vector<unsigned> seg_begin, seg_item;   // each segment's first launch item and request item
+    // appends to the running launch: published {items, closed} (device), the pinned staging of
+    // the item counts (one word per publication, so that a copy still queued never reads a
+    // later count), the list of claims given up, and the count of warps that gave up (device,
+    // and its mapped host mirror)
+    unsigned *d_avail = nullptr, *h_avail = nullptr, *d_lost = nullptr;
+    unsigned *d_exited = nullptr, *h_exited = nullptr, *d_exited_host = nullptr;
+    unsigned *h_claimed = nullptr, *d_claimed_host = nullptr;   // claims so far (mapped, approximate)
+    cudaEvent_t ready = nullptr;    // recorded before the launch: appends are copied after it
+    unsigned n_items = 0;           // items published to this launch
+    int n_pub = 0;                  // publications used (staging words)
+    bool closed = false;            // the host appends nothing more to this launch
+    double t_pub = 0;               // host time of the launch's last publication
     bool busy = false;
 };
 
@@ -164,6 +183,7 @@ struct grtx_server {
     grtx_params p;
     int64_t max_rays = 0;
     int max_inflight = 0;
+    int seg_cap = 0;            // segment records per launch (4 per admitted request)
     int64_t budget = 0;         // device bytes the server may hold (0: no cap)
     cudaStream_t s = nullptr;
     std::deque<SrvReq *> pending;
@@ -179,6 +199,14 @@ struct grtx_server {
     unsigned *queue = nullptr;  // one ray-queue counter per step slot
     Arena arena;                // server-owned outputs (budget > 0)
     unsigned seq = 0;           // launches so far (segment flags carry their launch's number)
+    cudaStream_t ctl = nullptr; // copies of segments appended to running launches
+    unsigned lost_cap = 0;      // warps of a launch
+    std::vector<unsigned> h_lost;
+    unsigned *h_one = nullptr;  // pinned word 1 (the copy that closes a launch)
+    int live = -1;              // slot of the launch new work is appended to (-1: none)
+    int64_t n_launches = 0, n_appends = 0, n_retried = 0;
+    unsigned linger_ns = kLingerNs;
+    double size_ns = kSizeNs;   // deadline weight of a request's size (see take_pieces)
 };
 
 namespace {
@@ -187,90 +215,205 @@ void server_free(grtx_server *v)
 {
     for (auto &st : v->steps)
         if (st.ev) cudaStreamSynchronize(st.s);     // (unused slots have no event)
+    if (v->ctl) {
+        cudaStreamSynchronize(v->ctl);
+        cudaStreamDestroy(v->ctl);
+    }
     for (auto &st : v->steps) {
         if (st.ev) cudaEventDestroy(st.ev);
+        if (st.ready) cudaEventDestroy(st.ready);
+        if (st.d_avail) cudaFree(st.d_avail);
+        if (st.h_avail) cudaFreeHost(st.h_avail);
+        if (st.d_lost) cudaFree(st.d_lost);
+        if (st.d_exited) cudaFree(st.d_exited);
+        if (st.h_exited) cudaFreeHost(st.h_exited);
+        if (st.h_claimed) cudaFreeHost(st.h_claimed);
         if (st.h) cudaFreeHost(st.h);
         if (st.d) cudaFree(st.d);
+        if (st.h_begins) cudaFreeHost(st.h_begins);
+        if (st.d_begins) cudaFree(st.d_begins);
         if (st.d_done) cudaFree(st.d_done);
         if (st.h_flag) cudaFreeHost(st.h_flag);
         if (st.ws) cudaFree(st.ws);
         if (st.own_stream) cudaStreamDestroy(st.s);
     }
     if (v->queue) cudaFree(v->queue);
+    if (v->h_one) cudaFreeHost(v->h_one);
     if (v->arena.base) cudaFree(v->arena.base);
     for (auto *r : v->pending) delete r;
     for (auto *r : v->active) delete r;
     delete v;
 }
 
-// Enqueue one step over the admitted requests' unscheduled items: requests are taken in
-// admission order up to max_rays, and the step's queue hands out the smaller pieces first, so
-// that small requests, reported per segment, finish early in the step.
-int schedule_step(grtx_server *v, int si)
+struct Piece {
+    SrvReq *r;
+    unsigned begin, count;
+};
+
+// Unscheduled work, up to `budget` items (a multiple of 32) and `max_pieces` pieces, request
+// by request in order of deadline: admission time plus size_ns per ray of the whole request
+// (0: admission order; large: smallest request first). A request's ranges that a launch did
+// not trace come first, then its next items.
+std::vector<Piece> take_pieces(grtx_server *v, int64_t budget, int max_pieces)
 {
-    SrvStep &st = v->steps[si];
-    st.seg_req.clear();
-    st.seg_seen.clear();
-    int64_t budget = std::max<int64_t>(32, v->max_rays / 32 * 32);
-    struct Piece {
-        SrvReq *r;
-        unsigned begin, count;
-    };
-    std::vector<Piece> pieces;
+    std::vector<std::pair<double, SrvReq *>> order;
     for (SrvReq *r : v->active) {
-        if (r->next >= r->n_items) continue;
-        if (budget <= 0) break;
+        if (r->next >= r->n_items && r->retry.empty()) continue;
+        order.push_back({r->t_admit + 1e-9 * v->size_ns * (double)r->n_items, r});
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [](const std::pair<double, SrvReq *> &x, const std::pair<double, SrvReq *> &y) {
+                         return x.first < y.first;
+                     });
+    std::vector<Piece> pieces;
+    for (const auto &o : order) {
+        SrvReq *r = o.second;
+        while (!r->retry.empty() && budget > 0 && (int)pieces.size() < max_pieces) {
+            auto &rg = r->retry.back();
+            const unsigned take = (unsigned)std::min<int64_t>(rg.second, budget);
+            pieces.push_back({r, rg.first, take});
+            rg.first += take;
+            rg.second -= take;
+            if (rg.second == 0) r->retry.pop_back();
+            budget -= take;
+        }
+        if (r->next >= r->n_items || budget <= 0 || (int)pieces.size() >= max_pieces) continue;
         unsigned take = (unsigned)std::min<int64_t>((int64_t)(r->n_items - r->next), budget);
         pieces.push_back({r, r->next, take});
         r->next += take;
         budget -= take;
     }
-    std::stable_sort(pieces.begin(), pieces.end(), [](const Piece &x, const Piece &y) { return x.count < y.count; });
-    unsigned total = 0;
-    int n = 0;
+    return pieces;
+}
+
+// Segment records of `pieces` from segment j0 on, the launch's items from item0 on.
+void fill_segments(grtx_server *v, SrvStep &st, const std::vector<Piece> &pieces)
+{
     for (const Piece &pc : pieces) {
-        ServeSeg &g = st.h[n];
+        const int j = (int)st.seg_req.size();
+        ServeSeg &g = st.h[j];
         g.sc = grtx_scene_ref(v->scenes[pc.r->r.scene_id]);
         g.cam = pc.r->cam;
         g.out = (float4 *)pc.r->r.d_rgbT;
         g.item_begin = pc.begin;
-        g.step_begin = total;
+        g.step_begin = st.n_items;
         g.count = pc.count;
         g.pad = 0;
-        total += pc.count;
+        st.h_begins[j] = st.n_items;
         st.seg_req.push_back(pc.r);
         st.seg_seen.push_back(0);
+        st.seg_begin.push_back(st.n_items);
+        st.seg_item.push_back(pc.begin);
+        st.n_items += pc.count;
         pc.r->pending_segs++;
-        ++n;
     }
-    if (n == 0) return GRTX_OK;
+}
+
+// Launch one step over unscheduled work (up to max_rays items, least remaining work first);
+// more is appended to it as its warps use up what was published.
+int schedule_step(grtx_server *v, int si)
+{
+    SrvStep &st = v->steps[si];
+    std::vector<Piece> pieces = take_pieces(v, v->max_rays, v->seg_cap);
+    if (pieces.empty()) return GRTX_OK;
+    st.seg_req.clear();
+    st.seg_seen.clear();
+    st.seg_begin.clear();
+    st.seg_item.clear();
+    st.n_items = 0;
+    fill_segments(v, st, pieces);
+    const int n = (int)st.seg_req.size();
     TraceArgs a = v->a;
     const size_t S = (size_t)a.n_slots;
     a.ck0 = (uint2 *)st.ws;
     a.ck1 = a.ck0 + S * a.ckpt_cap;
     a.ev = a.ck0 + S * 2 * a.ckpt_cap;
     a.queue = v->queue + kQueueStride * si;
-    a.n_items = total;
+    a.n_items = st.n_items;
     set_list_offsets(a, 2 * (size_t)a.ckpt_cap + (size_t)a.evict_cap);   // size checked at creation
     a.discard = lists_discardable(a);
+    st.h_avail[0] = st.n_items;
+    *reinterpret_cast<volatile unsigned *>(st.h_exited) = 0;
+    *reinterpret_cast<volatile unsigned *>(st.h_claimed) = 0;
     GRTX_CUDA(cudaMemcpyAsync(st.d, st.h, sizeof(ServeSeg) * n, cudaMemcpyHostToDevice, st.s));
+    GRTX_CUDA(cudaMemsetAsync(st.d_begins, 0xff, sizeof(unsigned) * v->seg_cap, st.s));
+    GRTX_CUDA(cudaMemcpyAsync(st.d_begins, st.h_begins, sizeof(unsigned) * n, cudaMemcpyHostToDevice, st.s));
+    GRTX_CUDA(cudaMemcpyAsync(st.d_avail, st.h_avail, sizeof(unsigned), cudaMemcpyHostToDevice, st.s));
+    GRTX_CUDA(cudaMemsetAsync(st.d_avail + 1, 0, sizeof(unsigned), st.s));
     GRTX_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned), st.s));
-    GRTX_CUDA(cudaMemsetAsync(st.d_done, 0, sizeof(unsigned) * n, st.s));
+    GRTX_CUDA(cudaMemsetAsync(st.d_done, 0, sizeof(unsigned) * v->seg_cap, st.s));
+    GRTX_CUDA(cudaMemsetAsync(st.d_lost, 0, sizeof(unsigned), st.s));
+    GRTX_CUDA(cudaMemsetAsync(st.d_exited, 0, sizeof(unsigned), st.s));
+    GRTX_CUDA(cudaEventRecord(st.ready, st.s));
+    st.n_pub = 1;
     st.seq = ++v->seq;
-    if (serve_launch_k(v->p.k, a, st.d, n, v->blocks, st.s, st.d_done, st.d_flag, st.seq) != GRTX_OK) {
+    ServeLive live;
+    live.seg_done = st.d_done;
+    live.seg_flag = st.d_flag;
+    live.seq = st.seq;
+    live.avail = st.d_avail;
+    live.lost = st.d_lost;
+    live.lost_cap = v->lost_cap;
+    live.exited = st.d_exited;
+    live.exited_host = st.d_exited_host;
+    live.linger_ns = v->linger_ns;
+    live.claimed_host = st.d_claimed_host;
+    if (serve_launch_k(v->p.k, a, st.d, st.d_begins, v->seg_cap, v->blocks, st.s, live) != GRTX_OK) {
         cudaError_t e = cudaGetLastError();
         return grtx_cuda_fail(e == cudaSuccess ? cudaErrorLaunchFailure : e, "serve step launch");
     }
     GRTX_CUDA(cudaEventRecord(st.ev, st.s));
     st.busy = true;
+    st.closed = false;
+    st.t_pub = now_s();
     v->inflight.push_back(si);
+    v->live = si;
+    ++v->n_launches;
     return GRTX_OK;
+}
+
+// Append unscheduled work to the running launch of slot si (its warps pick it up without a
+// new launch): the records, then the segment count, then the item count, on the control
+// stream after the launch's own copies. Returns false when the launch's segment table (or
+// its staging) is full.
+bool append_to_step(grtx_server *v, int si)
+{
+    SrvStep &st = v->steps[si];
+    const int room = std::min(v->seg_cap - (int)st.seg_req.size(), v->seg_cap - st.n_pub);
+    // (item numbers stay below 2^31, with room for the claims of every warp past the end)
+    if (room <= 0 || (uint64_t)st.n_items + (uint64_t)v->max_rays + 32ull * v->lost_cap >= (1ull << 31)) return false;
+    std::vector<Piece> pieces = take_pieces(v, v->max_rays, room);
+    if (pieces.empty()) return false;
+    const int j0 = (int)st.seg_req.size();
+    fill_segments(v, st, pieces);
+    const int n = (int)st.seg_req.size();
+    unsigned *count = st.h_avail + st.n_pub++;
+    *count = st.n_items;
+    cudaStreamWaitEvent(v->ctl, st.ready, 0);
+    cudaMemcpyAsync(st.d + j0, st.h + j0, sizeof(ServeSeg) * (n - j0), cudaMemcpyHostToDevice, v->ctl);
+    cudaMemcpyAsync(st.d_begins + j0, st.h_begins + j0, sizeof(unsigned) * (n - j0), cudaMemcpyHostToDevice, v->ctl);
+    cudaMemcpyAsync(st.d_avail, count, sizeof(unsigned), cudaMemcpyHostToDevice, v->ctl);
+    st.t_pub = now_s();
+    ++v->n_appends;
+    return true;
+}
+
+// Nothing more is appended to the launch of slot si: its waiting warps stop (after the
+// launch's appends, on the control stream).
+void close_step(grtx_server *v, int si)
+{
+    SrvStep &st = v->steps[si];
+    if (st.closed) return;
+    cudaStreamWaitEvent(v->ctl, st.ready, 0);
+    cudaMemcpyAsync(st.d_avail + 1, v->h_one, sizeof(unsigned), cudaMemcpyHostToDevice, v->ctl);
+    st.closed = true;
+    if (v->live == si) v->live = -1;
 }
 
 bool has_unscheduled(const grtx_server *v)
 {
     for (const SrvReq *r : v->active)
-        if (r->next < r->n_items) return true;
+        if (r->next < r->n_items || !r->retry.empty()) return true;
     return false;
 }
 
@@ -292,8 +435,8 @@ extern "C" GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scen
     }
     if (max_rays_per_step < 0 || max_inflight < 0 || max_inflight > 4096 || mem_budget_bytes < 0)
         return grtx_fail(GRTX_ERR_INVALID_ARG, "bad server limits");
-    const int64_t max_rays = max_rays_per_step > 0 ? max_rays_per_step : (int64_t)4 << 20;
     const int inflight_cap = max_inflight > 0 ? max_inflight : 64;
+    const int seg_cap = 4 * inflight_cap;
     const size_t C = p->ckpt_capacity > 0 ? p->ckpt_capacity : GRTX_DEFAULT_CKPT_CAPACITY;
     const size_t E = p->evict_capacity > 0 ? p->evict_capacity : GRTX_DEFAULT_EVICT_CAPACITY;
     int bps = 0, dev = 0, sms = 0;
@@ -307,8 +450,12 @@ extern "C" GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scen
     const int blocks_full = sms * bps;
     if ((size_t)blocks_full * 128 * (2 * C + E) >= ((size_t)1 << 31))
         return grtx_fail(GRTX_ERR_INVALID_ARG, "checkpoint/eviction capacities too large for the resident ray slots");
-    const size_t tables = kSteps * kQueueStride * sizeof(unsigned) +
-                          (size_t)kSteps * (sizeof(ServeSeg) + sizeof(unsigned)) * inflight_cap;
+    // segment tables, completion counts, publication words and given-up claims of each slot
+    auto tables_for = [&](int steps, int nblocks) {
+        return kSteps * kQueueStride * sizeof(unsigned) +
+               (size_t)steps * ((sizeof(ServeSeg) + 2 * sizeof(unsigned)) * seg_cap +
+                                sizeof(unsigned) * (4 + (size_t)nblocks * (kBlock / 32)));
+    };
     int n_steps = kSteps, blocks = blocks_full;
     size_t arena = 0;
     if (mem_budget_bytes > 0) {
@@ -322,6 +469,7 @@ extern "C" GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scen
                                                        " bytes is below twice one block of lists (" +
                                                        std::to_string(per_block) + " bytes)");
         size_t lists = (size_t)n_steps * blocks * per_block;
+        const size_t tables = tables_for(n_steps, blocks);
         if (lists + tables > budget) return grtx_fail(GRTX_ERR_INVALID_ARG, "memory budget too small");
         arena = (budget - lists - tables) / 256 * 256;
     }
@@ -329,8 +477,11 @@ extern "C" GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scen
     if (!v) return grtx_fail(GRTX_ERR_OOM, "host allocation failed");
     v->scenes.assign(scenes, scenes + n_scenes);
     v->p = *p;
-    v->max_rays = max_rays;
+    // work published to a launch at a time: by default two rounds of its warps' tiles
+    v->max_rays = max_rays_per_step > 0 ? std::max<int64_t>(32, std::min<int64_t>(max_rays_per_step, (int64_t)1 << 28) / 32 * 32)
+                                        : (int64_t)2 * 32 * blocks * (kBlock / 32);
     v->max_inflight = inflight_cap;
+    v->seg_cap = seg_cap;
     v->budget = mem_budget_bytes;
     v->n_steps = n_steps;
     v->blocks = blocks;
@@ -348,10 +499,14 @@ extern "C" GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scen
     a.packet_stack = p->packet_stack > 0 ? std::min(p->packet_stack, kPacketStack) : kPacketStack;
     int n_slots = v->blocks * 128;
     size_t ws = (size_t)blocks * per_block;
+    v->lost_cap = (unsigned)blocks * (kBlock / 32);
     // earlier work on any stream (the scenes' builds) completes before steps run on the
     // server's own streams
     cudaError_t e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaMalloc((void **)&v->queue, kSteps * kQueueStride * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&v->ctl, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&v->h_one, sizeof(unsigned));
+    if (e == cudaSuccess) *v->h_one = 1;
     for (int i = 0; i < n_steps && e == cudaSuccess; ++i) {
         SrvStep &sst = v->steps[i];
         if (i == 0) {
@@ -362,15 +517,32 @@ extern "C" GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scen
         }
         if (e == cudaSuccess) e = cudaMalloc(&sst.ws, ws);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sst.ev, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaMallocHost((void **)&sst.h, sizeof(ServeSeg) * v->max_inflight);
-        if (e == cudaSuccess) e = cudaMalloc((void **)&sst.d, sizeof(ServeSeg) * v->max_inflight);
-        if (e == cudaSuccess) e = cudaMalloc((void **)&sst.d_done, sizeof(unsigned) * v->max_inflight);
-        if (e == cudaSuccess) e = cudaHostAlloc((void **)&sst.h_flag, sizeof(unsigned) * v->max_inflight,
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&sst.h, sizeof(ServeSeg) * seg_cap);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&sst.d, sizeof(ServeSeg) * seg_cap);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&sst.d_done, sizeof(unsigned) * seg_cap);
+        if (e == cudaSuccess) e = cudaHostAlloc((void **)&sst.h_flag, sizeof(unsigned) * seg_cap,
                                                 cudaHostAllocMapped);
         if (e == cudaSuccess) {
-            std::memset(sst.h_flag, 0, sizeof(unsigned) * v->max_inflight);
+            std::memset(sst.h_flag, 0, sizeof(unsigned) * seg_cap);
             e = cudaHostGetDevicePointer((void **)&sst.d_flag, sst.h_flag, 0);
         }
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&sst.h_begins, sizeof(unsigned) * seg_cap);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&sst.d_begins, sizeof(unsigned) * seg_cap);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&sst.d_avail, 2 * sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&sst.h_avail, sizeof(unsigned) * (seg_cap + 1));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&sst.d_lost, sizeof(unsigned) * (1 + (size_t)v->lost_cap));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&sst.d_exited, sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaHostAlloc((void **)&sst.h_exited, sizeof(unsigned), cudaHostAllocMapped);
+        if (e == cudaSuccess) {
+            *sst.h_exited = 0;
+            e = cudaHostGetDevicePointer((void **)&sst.d_exited_host, sst.h_exited, 0);
+        }
+        if (e == cudaSuccess) e = cudaHostAlloc((void **)&sst.h_claimed, sizeof(unsigned), cudaHostAllocMapped);
+        if (e == cudaSuccess) {
+            *sst.h_claimed = 0;
+            e = cudaHostGetDevicePointer((void **)&sst.d_claimed_host, sst.h_claimed, 0);
+        }
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sst.ready, cudaEventDisableTiming);
     }
     char *arena_base = nullptr;
     if (e == cudaSuccess && arena > 0) e = cudaMalloc((void **)&arena_base, arena);
@@ -381,8 +553,7 @@ extern "C" GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scen
     }
     v->arena.reset(arena_base, arena);
     v->list_bytes = (size_t)n_steps * ws;
-    v->device_bytes = v->list_bytes + arena + kSteps * kQueueStride * sizeof(unsigned) +
-                      (size_t)n_steps * (sizeof(ServeSeg) + sizeof(unsigned)) * v->max_inflight;
+    v->device_bytes = v->list_bytes + arena + tables_for(n_steps, blocks);
     a.n_slots = n_slots;
     *out = v;
     return GRTX_OK;
@@ -433,12 +604,12 @@ extern "C" GRTX_API int grtx_server_poll(grtx_server *v, grtx_completion *done, 
     if (!v || !n_done || max_done < 0 || (max_done > 0 && !done)) return grtx_fail(GRTX_ERR_INVALID_ARG, "bad poll arguments");
     *n_done = 0;
     int got = 0;
-    // a segment is complete: the request is reported once all of its items have been
-    // scheduled and all of its segments are complete
+    // a segment is complete (or its launch ended): the request is reported once all of its
+    // items have been scheduled, traced, and all of its segments are complete
     auto segment_done = [&](SrvStep &st, size_t j, double t) {
         st.seg_seen[j] = 1;
         SrvReq *r = st.seg_req[j];
-        if (--r->pending_segs > 0 || r->next < r->n_items) return;
+        if (--r->pending_segs > 0 || r->next < r->n_items || !r->retry.empty()) return;
         grtx_completion c;
         c.tag = r->r.tag;
         c.status = GRTX_OK;
@@ -451,6 +622,40 @@ extern "C" GRTX_API int grtx_server_poll(grtx_server *v, grtx_completion *done, 
         delete r;
         ++got;
     };
+    // tiles of an ended launch that no warp traced (claims given up before the host published
+    // them, or items published after the last warp stopped) go back to their requests, as
+    // ranges of consecutive items
+    auto recover = [&](SrvStep &st, int si) -> int {
+        unsigned q = 0, n_lost = 0;
+        GRTX_CUDA(cudaStreamSynchronize(v->ctl));            // appends of this launch have landed
+        GRTX_CUDA(cudaMemcpy(&q, v->queue + kQueueStride * si, sizeof(unsigned), cudaMemcpyDeviceToHost));
+        GRTX_CUDA(cudaMemcpy(&n_lost, st.d_lost, sizeof(unsigned), cudaMemcpyDeviceToHost));
+        n_lost = std::min(n_lost, v->lost_cap);
+        std::vector<std::pair<SrvReq *, unsigned>> tiles;    // {request, first item}
+        auto add = [&](unsigned b) {
+            const size_t j = (size_t)(std::upper_bound(st.seg_begin.begin(), st.seg_begin.end(), b) -
+                                      st.seg_begin.begin()) - 1;
+            tiles.push_back({st.seg_req[j], st.seg_item[j] + (b - st.seg_begin[j])});
+        };
+        if (n_lost) {
+            v->h_lost.resize(n_lost);
+            GRTX_CUDA(cudaMemcpy(v->h_lost.data(), st.d_lost + 1, sizeof(unsigned) * n_lost, cudaMemcpyDeviceToHost));
+            for (unsigned b : v->h_lost)
+                if (b < st.n_items) add(b);
+        }
+        for (unsigned b = q / 32 * 32; b < st.n_items; b += 32) add(b);
+        std::sort(tiles.begin(), tiles.end());
+        v->n_retried += (int64_t)tiles.size();
+        for (size_t i = 0; i < tiles.size();) {
+            size_t e = i + 1;
+            while (e < tiles.size() && tiles[e].first == tiles[i].first &&
+                   tiles[e].second == tiles[e - 1].second + 32)
+                ++e;
+            tiles[i].first->retry.push_back({tiles[i].second, (unsigned)(32 * (e - i))});
+            i = e;
+        }
+        return GRTX_OK;
+    };
     for (;;) {
         // segments finished inside running steps
         double t = now_s();
@@ -460,19 +665,29 @@ extern "C" GRTX_API int grtx_server_poll(grtx_server *v, grtx_completion *done, 
             for (size_t j = 0; j < st.seg_req.size(); ++j)
                 if (!st.seg_seen[j] && flag[j] == st.seq) segment_done(st, j, t);
         }
-        // finished steps free their slots (every segment is complete once the launch is)
-        while (!v->inflight.empty()) {
-            SrvStep &st = v->steps[v->inflight.front()];
+        // ended launches free their slots: untraced tiles go back to their requests, and
+        // every other segment of the launch is complete
+        for (size_t i = 0; i < v->inflight.size();) {
+            const int si = v->inflight[i];
+            SrvStep &st = v->steps[si];
             cudaError_t q = cudaEventQuery(st.ev);
-            if (q == cudaErrorNotReady) break;
+            if (q == cudaErrorNotReady) {
+                ++i;
+                continue;
+            }
             if (q != cudaSuccess) return grtx_cuda_fail(q, "serve step");
+            int rs = recover(st, si);
+            if (rs != GRTX_OK) return rs;
             t = now_s();
             for (size_t j = 0; j < st.seg_req.size(); ++j)
                 if (!st.seg_seen[j]) segment_done(st, j, t);
             st.seg_req.clear();
             st.seg_seen.clear();
+            st.seg_begin.clear();
+            st.seg_item.clear();
             st.busy = false;
-            v->inflight.pop_front();
+            if (v->live == si) v->live = -1;
+            v->inflight.erase(v->inflight.begin() + (long)i);
         }
         // admission of pending requests into free slots, in submission order; a request
         // whose server-owned output does not fit the arena holds the ones behind it
@@ -487,18 +702,39 @@ extern "C" GRTX_API int grtx_server_poll(grtx_server *v, grtx_completion *done, 
             r->t_admit = now_s();
             v->active.push_back(r);
         }
-        // keep up to n_steps steps enqueued, one per slot
-        while ((int)v->inflight.size() < v->n_steps && has_unscheduled(v)) {
+        // new work joins the live launch: the host publishes up to max_rays more items (in
+        // deadline order) whenever less than half of that is left unclaimed, so that a request
+        // that arrives waits for at most that much work of others. The launch's warps take it as
+        // they come free; warps without work wait until linger_ns pass without a publication.
+        // The host closes the live launch (its waiting warps stop, so that the next launch gets
+        // their SMs) when its segment table is full, when some of its warps have stopped
+        // waiting, or when it has run out of work and its last publication is half of
+        // linger_ns old (its warps might stop before an append lands); the next work starts a
+        // launch in a free slot.
+        if (v->live >= 0) {
+            SrvStep &st = v->steps[v->live];
+            const unsigned claimed = *reinterpret_cast<volatile unsigned *>(st.h_claimed);
+            const int64_t left = (int64_t)st.n_items - (int64_t)claimed;
+            if (*reinterpret_cast<volatile unsigned *>(st.h_exited) != 0) {
+                close_step(v, v->live);
+            } else if (has_unscheduled(v)) {
+                if (left <= 0 && now_s() - st.t_pub >= 0.5e-9 * v->linger_ns) close_step(v, v->live);
+                else if (2 * left < v->max_rays && !append_to_step(v, v->live)) close_step(v, v->live);
+            }
+        }
+        if (v->live < 0 && (int)v->inflight.size() < v->n_steps && has_unscheduled(v)) {
             int si = -1;
             for (int i = 0; i < v->n_steps; ++i)
                 if (!v->steps[i].busy) { si = i; break; }
-            if (si < 0) break;
-            int st = schedule_step(v, si);
-            if (st != GRTX_OK) return st;
+            if (si >= 0) {
+                int st = schedule_step(v, si);
+                if (st != GRTX_OK) return st;
+            }
         }
-        if (!wait || got > 0 || v->inflight.empty()) break;
-        cudaError_t e = cudaEventSynchronize(v->steps[v->inflight.front()].ev);
-        if (e != cudaSuccess) return grtx_cuda_fail(e, "serve step");
+        // (a live launch with nothing admitted is waiting for new requests, not running)
+        if (!wait || got > 0 || v->inflight.empty() || v->active.empty()) break;
+        timespec ts = {0, 20000};                 // wait for a flag or an ended launch
+        nanosleep(&ts, nullptr);
     }
     while (*n_done < max_done && !v->backlog.empty()) {
         done[(*n_done)++] = v->backlog.front();
@@ -544,6 +780,22 @@ extern "C" GRTX_API int grtx_server_release(grtx_server *v, float *d_rgbT)
     return GRTX_OK;
 }
 
+extern "C" GRTX_API int grtx_server_set_linger(grtx_server *v, int64_t linger_ns)
+{
+    if (!v) return grtx_fail(GRTX_ERR_INVALID_ARG, "server is NULL");
+    if (linger_ns < 0 || linger_ns > 1000000000) return grtx_fail(GRTX_ERR_INVALID_ARG, "linger_ns must be in [0, 1e9]");
+    v->linger_ns = (unsigned)linger_ns;
+    return GRTX_OK;
+}
+
+extern "C" GRTX_API int grtx_server_set_order(grtx_server *v, double size_ns_per_ray)
+{
+    if (!v) return grtx_fail(GRTX_ERR_INVALID_ARG, "server is NULL");
+    if (!(size_ns_per_ray >= 0.0 && size_ns_per_ray <= 1e9)) return grtx_fail(GRTX_ERR_INVALID_ARG, "size_ns_per_ray must be in [0, 1e9]");
+    v->size_ns = size_ns_per_ray;
+    return GRTX_OK;
+}
+
 extern "C" GRTX_API int grtx_server_get_info(const grtx_server *v, grtx_server_info *info)
 {
     if (!v || !info) return grtx_fail(GRTX_ERR_INVALID_ARG, "NULL argument");
@@ -555,10 +807,15 @@ extern "C" GRTX_API int grtx_server_get_info(const grtx_server *v, grtx_server_i
     info->device_bytes = (int64_t)v->device_bytes;
     info->n_inflight = (int32_t)v->active.size();
     info->n_pending = (int32_t)v->pending.size();
+    info->n_launches = v->n_launches;
+    info->n_appends = v->n_appends;
+    info->n_retried_tiles = v->n_retried;
     return GRTX_OK;
 }
 
 extern "C" GRTX_API void grtx_server_destroy(grtx_server *v)
 {
-    if (v) server_free(v);
+    if (!v) return;
+    for (int si : v->inflight) close_step(v, si);
+    server_free(v);
 }

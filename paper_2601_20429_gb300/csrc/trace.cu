@@ -19,8 +19,8 @@ GRTX_EXTERN_TRACE(16)
 GRTX_EXTERN_TRACE(32)
 
 #define GRTX_EXTERN_SEGMENTS(K)                                                                          \
-    extern template int serve_launch<K>(const TraceArgs &, const ServeSeg *, int, int, cudaStream_t, unsigned *, \
-                                        unsigned *, unsigned);                                               \
+    extern template int serve_launch<K>(const TraceArgs &, const ServeSeg *, const unsigned *, int, int, cudaStream_t, \
+                                        ServeLive);                                                                  \
     extern template int serve_occupancy<K>(int *);
 GRTX_EXTERN_SEGMENTS(1)
 GRTX_EXTERN_SEGMENTS(2)
@@ -362,15 +362,15 @@ extern "C" GRTX_API int grtx_trace_forward(grtx_scene *sc, const grtx_camera *ca
 
 namespace {
 
-int segments_launch_k(int k, const TraceArgs &a, const ServeSeg *segs, int n, int blocks, cudaStream_t s)
+int segments_launch_k(int k, const TraceArgs &a, const ServeSeg *segs, const unsigned *begins, int n, int blocks, cudaStream_t s)
 {
     switch (k) {
-    case 1: return serve_launch<1>(a, segs, n, blocks, s, nullptr, nullptr, 0u);
-    case 2: return serve_launch<2>(a, segs, n, blocks, s, nullptr, nullptr, 0u);
-    case 4: return serve_launch<4>(a, segs, n, blocks, s, nullptr, nullptr, 0u);
-    case 8: return serve_launch<8>(a, segs, n, blocks, s, nullptr, nullptr, 0u);
-    case 16: return serve_launch<16>(a, segs, n, blocks, s, nullptr, nullptr, 0u);
-    default: return serve_launch<32>(a, segs, n, blocks, s, nullptr, nullptr, 0u);
+    case 1: return serve_launch<1>(a, segs, begins, n, blocks, s, ServeLive{});
+    case 2: return serve_launch<2>(a, segs, begins, n, blocks, s, ServeLive{});
+    case 4: return serve_launch<4>(a, segs, begins, n, blocks, s, ServeLive{});
+    case 8: return serve_launch<8>(a, segs, begins, n, blocks, s, ServeLive{});
+    case 16: return serve_launch<16>(a, segs, begins, n, blocks, s, ServeLive{});
+    default: return serve_launch<32>(a, segs, begins, n, blocks, s, ServeLive{});
     }
 }
 
@@ -400,7 +400,7 @@ extern "C" GRTX_API int grtx_trace_forward_batch(grtx_scene *sc, const grtx_came
     if (a.traversal == GRTX_TRAVERSAL_SINGLE)
         return grtx_fail(GRTX_ERR_INVALID_ARG, "batched traces take checkpoint or restart traversal");
     ServeSeg v[GRTX_MAX_BATCH], h[GRTX_MAX_BATCH];
-    unsigned items[GRTX_MAX_BATCH];
+    unsigned items[GRTX_MAX_BATCH], begins[GRTX_MAX_BATCH];
     uint64_t all = 0;
     for (int i = 0; i < n_cams; ++i) {
         if (!rgbT[i] || ((uintptr_t)rgbT[i] & 15))
@@ -426,6 +426,7 @@ extern "C" GRTX_API int grtx_trace_forward_batch(grtx_scene *sc, const grtx_came
     for (int j = 0; j < n_cams; ++j) {
         h[j] = v[order[j]];
         h[j].step_begin = total;
+        begins[j] = total;
         h[j].count = items[order[j]];
         total += items[order[j]];
     }
@@ -448,12 +449,14 @@ extern "C" GRTX_API int grtx_trace_forward_batch(grtx_scene *sc, const grtx_came
     if (!set_list_offsets(a, 2 * C + E))
         return grtx_fail(GRTX_ERR_INVALID_ARG, "checkpoint/eviction capacities too large for the resident ray slots");
     a.discard = lists_discardable(a);
-    ServeSeg *d = nullptr;
-    st = grtx_malloc_async((void **)&d, sizeof(ServeSeg) * n_cams, s);
+    ServeSeg *d = nullptr;      // the records, then the begins array
+    st = grtx_malloc_async((void **)&d, (sizeof(ServeSeg) + sizeof(unsigned)) * n_cams, s);
     if (st) return st;
+    unsigned *d_begins = reinterpret_cast<unsigned *>(d + n_cams);
     GRTX_CUDA(cudaMemcpyAsync(d, h, sizeof(ServeSeg) * n_cams, cudaMemcpyHostToDevice, s));
+    GRTX_CUDA(cudaMemcpyAsync(d_begins, begins, sizeof(unsigned) * n_cams, cudaMemcpyHostToDevice, s));
     GRTX_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned), s));
-    int launched = segments_launch_k(p->k, a, d, n_cams, blocks, s);
+    int launched = segments_launch_k(p->k, a, d, d_begins, n_cams, blocks, s);
     cudaFreeAsync(d, s);
     if (launched != GRTX_OK) {
         cudaError_t e = cudaGetLastError();

@@ -80,12 +80,49 @@ struct TraceArgs {
 
 // One request of a serving step: its scene, camera, output, and which of its queue items
 // this step covers (items [item_begin, item_begin + count) of the request map to step items
-// [step_begin, step_begin + count)). Counts are multiples of 32.
-struct ServeSeg {
+// [step_begin, step_begin + count)). Counts are multiples of 32. The kernel finds a tile's
+// segment by a search over a separate array `begins` of the segments' step_begin values
+// (ascending; entries past the last segment hold 0xffffffff, so that a launch's n_segs may be
+// its table's capacity while the host appends segments).
+// Records are 256-byte aligned so that a record the host appends while a launch runs shares
+// no cache line with one the launch has already read.
+struct __align__(256) ServeSeg {
     SceneRef sc;
     CamRef cam;
     float4 *out;
     unsigned item_begin, step_begin, count, pad;
+};
+
+// Controls of a serving launch (all NULL / 0 for a plain batched launch):
+//   seg_done, seg_flag, seq: per-segment completion. The warp that finishes a segment's last
+//     tile writes seq to seg_flag[segment] (pinned host memory mapped into the device).
+//   avail: {items, closed}. The host appends segments while the launch runs: it writes their
+//     records and begins entries, then raises the item count, and last, once it appends no
+//     more, sets closed = 1. NULL: the launch's n_items is final. A warp claims its next tile
+//     whether or not it is published yet and waits for it (sleeping between checks) until it
+//     is published, the launch is closed, or linger_ns pass without any publication.
+//   lost: [0] a count, then the first item of each tile a warp claimed and gave up on after
+//     linger_ns; the host traces those again if it published them after all. lost_cap: the
+//     launch's warps, since a warp stops after giving up.
+//   exited: a count of warps that gave up, mirrored into exited_host (mapped host memory) so
+//     that the host stops appending to a launch that has begun to wind down.
+//   claimed_host: mapped host memory; every 16th claim, and every claim a warp has to wait
+//     for, writes its end there, so that the host sees how much published work is left and
+//     publishes more only when it runs low (the host chooses what runs next, instead of a long
+//     queue fixing it).
+static_assert(sizeof(ServeSeg) == 256, "a segment record fills one 256-byte slot");
+
+struct ServeLive {
+    unsigned *seg_done;
+    unsigned *seg_flag;
+    unsigned seq;
+    const unsigned *avail;
+    unsigned *lost;
+    unsigned lost_cap;
+    unsigned *exited;
+    unsigned *exited_host;
+    unsigned linger_ns;
+    unsigned *claimed_host;
 };
 
 struct Counters {
@@ -1600,16 +1637,69 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, PASS == PASS_BWD))
     }
 }
 
+// Acquire load (of a count the host raises after writing what it covers).
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr unsigned kLingerChecks = 1u << 16;   // bound on the checks of one wait (at most 8 us apart)
+
+// Lane 0 of a warp of a serving launch that holds the claim `base`: returns base once the
+// host has published the tile, or kNoWork when the launch is closed with base past its last
+// item, or when linger_ns pass without any publication (each one restarts the wait). A warp
+// that gives up puts its claim on the lost list (the host may publish it yet) and counts
+// itself as exited. A warp about to wait writes its claim's end to claimed_host, so that the
+// host sees the launch has run out of work.
+__device__ __forceinline__ unsigned await_published(const ServeLive &live, unsigned base)
+{
+    const unsigned kNoWork = 0xffffffffu;
+    unsigned seen = ld_acquire(live.avail);
+    if (base < seen) return base;
+    *reinterpret_cast<volatile unsigned *>(live.claimed_host) = base + 32u;
+    uint64_t t0 = global_ns();
+    unsigned nap = 64;
+    for (unsigned it = 0; it < kLingerChecks; ++it) {
+        const unsigned closed = ld_acquire(live.avail + 1);
+        const unsigned n = ld_acquire(live.avail);
+        if (base < n) return base;
+        if (closed) return kNoWork;
+        const uint64_t now = global_ns();
+        if (n != seen) {
+            seen = n;
+            t0 = now;
+        } else if (now - t0 > live.linger_ns) {
+            break;
+        }
+        __nanosleep(nap);
+        nap = min(2 * nap, 8192u);
+    }
+    const unsigned i = atomicAdd(live.lost, 1u);
+    if (i < live.lost_cap) live.lost[1 + i] = base;
+    const unsigned e = atomicAdd(live.exited, 1u) + 1u;
+    *reinterpret_cast<volatile unsigned *>(live.exited_host) = e;
+    return kNoWork;
+}
+
 // Serving step: one persistent launch over the queue items of several requests (each with
 // its own scene, camera and output); a warp's 32 items always belong to one request.
 template <int K>
 __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, false))
-    k_serve(TraceArgs a, const ServeSeg *__restrict__ segs, int n_segs, unsigned *seg_done, unsigned *seg_flag,
-            unsigned seq)
+    k_serve(TraceArgs a, const ServeSeg *segs, const unsigned *begins, int n_segs, ServeLive live)
 {
     __shared__ float s_kt[K * kBlock];
     __shared__ uint32_t s_ki[K * kBlock];
     __shared__ uint4 s_pst[kBlock / 32][kPacketStack];
+    const unsigned kNoWork = 0xffffffffu;
     const int slot = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     KBuf<K> kb;
@@ -1618,14 +1708,26 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, false))
     Counters cnt = {0, 0, 0, 0, 0, 0, 0, 0, 0, nullptr, 0, 0};
     for (;;) {
         unsigned base = 0;
-        if (lane == 0) base = atomicAdd(a.queue, 32u);
+        if (lane == 0) {
+            base = atomicAdd(a.queue, 32u);
+            if (live.avail) {
+                if ((base & 511u) == 0) *reinterpret_cast<volatile unsigned *>(live.claimed_host) = base + 32u;
+                base = await_published(live, base);
+            } else if (base >= a.n_items) {
+                base = kNoWork;
+            }
+        }
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= a.n_items) break;
-        int lo = 0, hi = n_segs - 1;              // last segment with step_begin <= base
+        if (base == kNoWork) break;
+        // last segment with begins[] <= base (read past L1: the host appends entries while the
+        // launch runs; the entries not yet written hold 0xffffffff)
+        int lo = 0, hi = n_segs - 1;
         while (lo < hi) {
             int mid = (lo + hi + 1) >> 1;
-            if (segs[mid].step_begin <= base) lo = mid; else hi = mid - 1;
+            if (__ldcg(begins + mid) <= base) lo = mid; else hi = mid - 1;
         }
+        // (a record is read only once its items are published, and fills whole cache lines of
+        // its own, so no cache holds an older copy of it)
         const ServeSeg &sg = segs[lo];
         SceneRef sc = sg.sc;
         CamRef cam = sg.cam;
@@ -1640,16 +1742,16 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, false))
         else
             trace_warp<K, FORM_SPHERE, false, PASS_FWD>(a, sc, sg.out, slot, valid, pix, o, d, tn, tf, kb, cnt,
                                                      s_pst[threadIdx.x >> 5]);
-        if (seg_done) {
+        if (live.seg_done) {
             // the tile's pixels are written; the warp that completes the segment raises its
             // flag in host memory (each lane's writes fenced before the count)
             __threadfence();
             __syncwarp();
             if (lane == 0) {
-                const unsigned old = atomicAdd(seg_done + lo, 32u);
+                const unsigned old = atomicAdd(live.seg_done + lo, 32u);
                 if (old + 32u >= sg.count) {
                     __threadfence_system();
-                    *reinterpret_cast<volatile unsigned *>(seg_flag + lo) = seq;
+                    *reinterpret_cast<volatile unsigned *>(live.seg_flag + lo) = live.seq;
                 }
             }
         }
@@ -1728,12 +1830,12 @@ inline int kernel_form(int scene_form, bool wide = false, bool quant = false)
            : wide ? (quant ? FORM_SPHERE4Q : FORM_SPHERE4) : FORM_SPHERE;
 }
 
-// seg_done / seg_flag / seq: per-segment completion (see k_serve); NULL for none.
+// live: the serving controls (see ServeLive); all zero for a plain batched launch.
 template <int K>
-int serve_launch(const TraceArgs &a, const ServeSeg *segs, int n_segs, int blocks, cudaStream_t s,
-                 unsigned *seg_done = nullptr, unsigned *seg_flag = nullptr, unsigned seq = 0)
+int serve_launch(const TraceArgs &a, const ServeSeg *segs, const unsigned *begins, int n_segs, int blocks,
+                 cudaStream_t s, ServeLive live)
 {
-    k_serve<K><<<blocks, 128, 0, s>>>(a, segs, n_segs, seg_done, seg_flag, seq);
+    k_serve<K><<<blocks, 128, 0, s>>>(a, segs, begins, n_segs, live);
     return cudaGetLastError() == cudaSuccess ? GRTX_OK : GRTX_ERR_CUDA;
 }
 
@@ -1747,6 +1849,5 @@ int serve_occupancy(int *blocks_per_sm)
 #define GRTX_INSTANTIATE_TRACE(K)                                                                  \
     template int trace_launch<K>(const TraceArgs &, int, bool, int, int, cudaStream_t);           \
     template int trace_occupancy<K>(int, bool, int, int *);                                         \
-    template int serve_launch<K>(const TraceArgs &, const ServeSeg *, int, int, cudaStream_t, unsigned *,    \
-                                 unsigned *, unsigned);                                                    \
+    template int serve_launch<K>(const TraceArgs &, const ServeSeg *, const unsigned *, int, int, cudaStream_t, ServeLive);   \
     template int serve_occupancy<K>(int *);

@@ -161,7 +161,8 @@ class grtx_completion(C.Structure):
 class grtx_server_info(C.Structure):
     _fields_ = [("n_step_slots", C.c_int32), ("blocks_per_step", C.c_int32), ("list_bytes", C.c_int64),
                 ("arena_bytes", C.c_int64), ("arena_used", C.c_int64), ("device_bytes", C.c_int64),
-                ("n_inflight", C.c_int32), ("n_pending", C.c_int32)]
+                ("n_inflight", C.c_int32), ("n_pending", C.c_int32), ("n_launches", C.c_int64),
+                ("n_appends", C.c_int64), ("n_retried_tiles", C.c_int64)]
 
 
 # every symbol declared in include/grtx.h with its ctypes signature
@@ -207,6 +208,8 @@ _SIGS = {
                                      _fp, C.POINTER(_fp)]),
     "grtx_server_release": (C.c_int, [_fp, _fp]),
     "grtx_server_get_info": (C.c_int, [_fp, C.POINTER(grtx_server_info)]),
+    "grtx_server_set_linger": (C.c_int, [_fp, C.c_int64]),
+    "grtx_server_set_order": (C.c_int, [_fp, C.c_double]),
     "grtx_server_submit": (C.c_int, [_fp, C.POINTER(grtx_request), C.c_int]),
     "grtx_server_poll": (C.c_int, [_fp, C.POINTER(grtx_completion), C.c_int, C.POINTER(C.c_int), C.c_int]),
     "grtx_render_requests": (C.c_int, [_fp, C.POINTER(grtx_request), C.c_int, C.POINTER(grtx_completion),

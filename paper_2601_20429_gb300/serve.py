@@ -13,7 +13,8 @@ from .render import Scene, trace_params
 
 class Server:
     def __init__(self, scenes: list[Scene], k=16, traversal="checkpoint", max_rays_per_step=0, max_inflight=0,
-                 stream: torch.cuda.Stream | None = None, mem_budget_bytes=0, **params):
+                 stream: torch.cuda.Stream | None = None, mem_budget_bytes=0, linger_us: float | None = None,
+                 size_ns_per_ray: float | None = None, **params):
         self.scenes = list(scenes)
         self.stream = stream or torch.cuda.Stream()
         alpha_min = self.scenes[0].alpha_min
@@ -25,6 +26,12 @@ class Server:
                                            C.c_void_p(self.stream.cuda_stream), C.byref(out)),
                 "grtx_server_create")
         self.handle = out.value
+        if linger_us is not None:
+            N.check(N.lib().grtx_server_set_linger(C.c_void_p(self.handle), int(round(linger_us * 1000))),
+                    "grtx_server_set_linger")
+        if size_ns_per_ray is not None:
+            N.check(N.lib().grtx_server_set_order(C.c_void_p(self.handle), float(size_ns_per_ray)),
+                    "grtx_server_set_order")
         self._keep = {}
         self._shape = {}
 

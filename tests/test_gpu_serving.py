@@ -91,25 +91,76 @@ def test_requests_admitted_while_others_run(world):
 
 def test_small_request_completes_before_the_large_one_in_its_step(world):
     """A request is reported when its own tiles are done, not when its whole step is: in one
-    step holding a 333x217 view and a 64x64 view (submitted in that order), the small view's
-    tiles run first and it completes no later than the large one, with both images equal to
-    the lone renders."""
+    step holding a 3840x2160 view (about 50 times as many 32-ray tiles as the launch has warps)
+    and a 64x64 view from the same pose, submitted in that order, the small view's tiles are
+    handed out first and it completes before the large one, with both images equal to the lone
+    renders. (A request's latency is at least its slowest tile's, up to a millisecond or two
+    for rays through dense Gaussians, so the large view must take several times that.)"""
     sc, reqs, alone = world
-    big = next(j for j, r in enumerate(reqs) if (r["camera"]["width"], r["camera"]["height"]) == (333, 217))
-    small = next(j for j, r in enumerate(reqs) if (r["camera"]["width"], r["camera"]["height"]) == (64, 64))
-    srv = Server(sc, k=16, max_rays_per_step=1 << 22, max_inflight=8)
-    bufs = _bufs(reqs)
-    done = {}
+    big_cam = scenes.pinhole_camera(3840, 2160, (0.0, 0.5, -3.0), (0.0, 0.0, 0.0), 60.0)
+    small_cam = scenes.pinhole_camera(64, 64, (0.0, 0.5, -3.0), (0.0, 0.0, 0.0), 60.0)
+    big_alone = R.render(sc[2], big_cam, k=16)["rgbT"].clone()
+    small_alone = R.render(sc[2], small_cam, k=16)["rgbT"].clone()
+    srv = Server(sc, k=16, max_rays_per_step=1 << 24, max_inflight=8)
+    big_buf = torch.full_like(big_alone, -1.0)
+    small_buf = torch.full_like(small_alone, -1.0)
     for _ in range(3):
-        srv.submit([(reqs[j]["scene"], reqs[j]["camera"], bufs[j], j) for j in (big, small)])
+        srv.submit([(2, big_cam, big_buf, 0), (2, small_cam, small_buf, 1)])
         got = []
         while len(got) < 2:
             got += srv.poll(wait=True)
         torch.cuda.synchronize()
         done = {c["tag"]: c for c in got}
-        assert done[small]["t_done"] <= done[big]["t_done"]
-    _same(alone[big], bufs[big])
-    _same(alone[small], bufs[small])
+        assert done[1]["t_done"] < done[0]["t_done"]
+    _same(big_alone, big_buf)
+    _same(small_alone, small_buf)
+    srv.close()
+
+
+def test_new_requests_join_the_running_launch(world):
+    """Requests submitted while a step launch still runs (or its warps wait for work) are
+    appended to that launch instead of starting another, and render the lone images."""
+    sc, reqs, alone = world
+    srv = Server(sc, k=16, max_rays_per_step=1 << 22, max_inflight=16, linger_us=200_000)
+    bufs = _bufs(reqs)
+    srv.submit([(reqs[0]["scene"], reqs[0]["camera"], bufs[0], 0)])
+    got = []
+    while len(got) < 1:
+        got += srv.poll(wait=True)
+    # the launch's warps now wait (up to 200 ms) for more work
+    srv.submit([(r["scene"], r["camera"], b, 1 + i) for i, (r, b) in enumerate(zip(reqs[1:6], bufs[1:6]))])
+    while len(got) < 6:
+        got += srv.poll(wait=True)
+    torch.cuda.synchronize()
+    info = srv.info()
+    assert info["n_launches"] == 1 and info["n_appends"] >= 1, info
+    assert sorted(d["tag"] for d in got) == list(range(6))
+    for j in range(6):
+        _same(alone[j], bufs[j])
+    srv.close()
+
+
+@pytest.mark.parametrize("linger_us", [0, 3, 30])
+def test_short_waits_lose_no_tiles(world, linger_us):
+    """With waits too short to bridge the gaps between submissions, launches end while work is
+    being appended to them: tiles a warp gave up on, and items published after the last warp
+    stopped, are traced by later launches, and every image is still the lone render."""
+    sc, reqs, alone = world
+    srv = Server(sc, k=16, max_rays_per_step=6_000, max_inflight=6, linger_us=linger_us)
+    bufs = _bufs(reqs)
+    got = []
+    for i, (r, b) in enumerate(zip(reqs, bufs)):
+        srv.submit([(r["scene"], r["camera"], b, i)])
+        got += srv.poll()
+    while len(got) < len(reqs):
+        got += srv.poll(wait=True)
+    torch.cuda.synchronize()
+    assert sorted(d["tag"] for d in got) == list(range(len(reqs)))
+    worst = max(_same(a, b) for a, b in zip(alone, bufs))
+    assert worst <= 1e-5
+    info = srv.info()
+    print(f"linger {linger_us} us: {info['n_launches']} launches, {info['n_appends']} appends, "
+          f"{info['n_retried_tiles']} tiles retried")
     srv.close()
 
 
@@ -125,6 +176,10 @@ def test_server_errors(world):
         srv.submit([(0, cam, buf, 0)])
     assert e.value.status == 1
     assert srv.load() == (0, 0)
+    for bad in (-1, 2_000_000):
+        with pytest.raises(N.GrtxError) as e:
+            N.check(N.lib().grtx_server_set_linger(srv.handle, int(bad * 1000)), "grtx_server_set_linger")
+        assert e.value.status == 1
     srv.close()
     plain = R.Scene.from_params(scenes.surface_scene(n=1000, seed=1), form="proxy20")
     with pytest.raises(N.GrtxError):
