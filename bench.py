@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="grtx", choices=["grtx", "reference"])
     ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-linger-us", type=float, default=None,
+                    help="how long a serving launch's idle warps wait for new work (server default: 2000); "
+                         "0 makes each launch cover exactly the work published before it (for profiling one)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -439,7 +442,8 @@ def run_stream(srv, reqs, rate_hz: float) -> dict:
 
 
 def bench_serving(n_requests: int, max_rays_per_step: int = 0, max_inflight: int = 64,
-                  modes: bool = False, restart: bool = False, capacity_rates=(), capacity_requests: int = 1000):
+                  modes: bool = False, restart: bool = False, capacity_rates=(), capacity_requests: int = 1000,
+                  linger_us=None):
     """The serving configuration: four resident scenes, the 200 req/s stream through the
     server (checkpointed rounds); optionally the same stream with restart traversal, the
     traversal modes on the requests' views, and a capacity sweep: the same views arriving
@@ -454,7 +458,7 @@ def bench_serving(n_requests: int, max_rays_per_step: int = 0, max_inflight: int
 
     def server(traversal):
         srv = Server(gpu_scenes, k=cfg["k"], traversal=traversal, max_rays_per_step=max_rays_per_step,
-                     max_inflight=max_inflight)
+                     max_inflight=max_inflight, linger_us=linger_us)
         # warm-up: a few requests of each size
         warm = [torch.empty((1920 * 1080, 4), dtype=torch.float32, device="cuda") for _ in range(8)]
         srv.render_requests([(j % 4, reqs[j]["camera"], warm[j], 10 ** 9 + j) for j in range(8)])
@@ -714,9 +718,10 @@ def main():
         if args.section == "differentiable":
             res = bench_differentiable(args.steps, args.warmup, stream)
         elif args.section == "serving":
-            res = bench_serving(args.serve_requests)
+            res = bench_serving(args.serve_requests, linger_us=args.serve_linger_us)
         elif args.section == "serving-capacity":
-            res = bench_serving(args.serve_requests, capacity_rates=(250.0, 300.0, 350.0, 400.0, 450.0, 500.0))
+            res = bench_serving(args.serve_requests, capacity_rates=(250.0, 300.0, 350.0, 400.0, 450.0, 500.0),
+                                linger_us=args.serve_linger_us)
         else:
             flush_buf = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
             res = bench_outdoor(args.steps, stream, lambda: flush_buf.fill_(1),
@@ -838,7 +843,8 @@ def main():
     serving = None
     if dist.world == 1 and not args.no_serving:
         serving = bench_serving(args.serve_requests, modes=not args.no_extra, restart=not args.no_extra,
-                                capacity_rates=() if args.no_extra else (250.0, 300.0, 350.0, 400.0))
+                                capacity_rates=() if args.no_extra else (250.0, 300.0, 350.0, 400.0),
+                                linger_us=args.serve_linger_us)
 
     differentiable = outdoor = ablations = None
     if dist.world == 1 and not args.no_extra:
