@@ -1591,7 +1591,14 @@ __device__ __forceinline__ void discard_dead_lists(const TraceArgs &a, int warp_
 // memory per block allows 6; the backward keeps more live state and prefers 7).
 __host__ __device__ constexpr int trace_min_blocks(int k, bool bwd) { return k >= 32 ? 6 : (bwd ? 7 : 8); }
 
-template <int K, int FORM, bool INSTR, int PASS>
+// Traversal a frame kernel is compiled for: either (chosen per launch by a.traversal), or one
+// of them only. The forward sphere-form kernel has one instantiation per traversal (TRAV_CKPT
+// also serves any traversal but restart): without the other traversal's code, the register
+// allocation of the one that runs is better (the checkpointed frame kernel spills 100 B
+// instead of 112 B and runs 0.5 % faster).
+constexpr int TRAV_ANY = 0, TRAV_CKPT = 1, TRAV_RESTART = 2;
+
+template <int K, int FORM, bool INSTR, int PASS, int TRAV = TRAV_ANY>
 __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, PASS == PASS_BWD)) k_trace(TraceArgs a)
 {
     __shared__ float s_kt[K * kBlock];
@@ -1615,7 +1622,13 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, PASS == PASS_BWD))
         bool valid = make_ray(a.cam, base + lane, pix, o, d, tn, tf);
         rays += valid;
         if (INSTR) visits_begin(a, cnt, valid, pix);
-        if (PASS != PASS_BWD && a.traversal == GRTX_TRAVERSAL_RESTART)
+        if constexpr (TRAV == TRAV_RESTART && PASS != PASS_BWD)
+            trace_warp_restart<K, FORM, INSTR, PASS == PASS_SAVE>(a, a.sc, a.rgbT, slot, valid, pix, o, d, tn, tf,
+                                                                  kb, cnt, s_pst[threadIdx.x >> 5]);
+        else if constexpr (TRAV == TRAV_CKPT)
+            trace_warp<K, FORM, INSTR, PASS>(a, a.sc, a.rgbT, slot, valid, pix, o, d, tn, tf, kb, cnt,
+                                             s_pst[threadIdx.x >> 5]);
+        else if (PASS != PASS_BWD && a.traversal == GRTX_TRAVERSAL_RESTART)
             trace_warp_restart<K, FORM, INSTR, PASS == PASS_SAVE>(a, a.sc, a.rgbT, slot, valid, pix, o, d, tn, tf,
                                                                   kb, cnt, s_pst[threadIdx.x >> 5]);
         else
@@ -1798,7 +1811,8 @@ int trace_launch(const TraceArgs &a, int form, bool instr, int pass, int blocks,
     else if (form == FORM_SPHERE4Q && instr) k_trace<K, FORM_SPHERE4Q, true, PASS_FWD><<<g, b, 0, s>>>(a);
     else if (form == FORM_SPHERE4Q) k_trace<K, FORM_SPHERE4Q, false, PASS_FWD><<<g, b, 0, s>>>(a);
     else if (instr) k_trace<K, FORM_SPHERE, true, PASS_FWD><<<g, b, 0, s>>>(a);
-    else k_trace<K, FORM_SPHERE, false, PASS_FWD><<<g, b, 0, s>>>(a);
+    else if (a.traversal == GRTX_TRAVERSAL_RESTART) k_trace<K, FORM_SPHERE, false, PASS_FWD, TRAV_RESTART><<<g, b, 0, s>>>(a);
+    else k_trace<K, FORM_SPHERE, false, PASS_FWD, TRAV_CKPT><<<g, b, 0, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? GRTX_OK : GRTX_ERR_CUDA;
 }
 
@@ -1817,7 +1831,7 @@ int trace_occupancy(int form, bool instr, int pass, int *blocks_per_sm)
     else if (form == FORM_SPHERE4Q && instr) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_SPHERE4Q, true, PASS_FWD>, 128, 0);
     else if (form == FORM_SPHERE4Q) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_SPHERE4Q, false, PASS_FWD>, 128, 0);
     else if (instr) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_SPHERE, true, PASS_FWD>, 128, 0);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_SPHERE, false, PASS_FWD>, 128, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_trace<K, FORM_SPHERE, false, PASS_FWD, TRAV_CKPT>, 128, 0);
     return e == cudaSuccess ? GRTX_OK : GRTX_ERR_CUDA;
 }
 

@@ -904,7 +904,10 @@ def test_saved_blend_lists_give_the_replay_gradients(dense, traversal):
             np.testing.assert_array_equal(leaf_ids[leaves[r, :m]], ids[r, :m])
         if cap == 3:
             assert (n > cap).mean() > 0.02 and (n <= cap).mean() > 0.02   # both paths exercised
-        got = R.backward(sc, cam, res["rgbT"], w, k=8, traversal=traversal, saved=res["saved"])
+        # the same forward image for both backwards: the saving forward is another kernel
+        # instantiation, whose image may differ by an ulp, and the gradient terms at a blend
+        # near full opacity divide by (1 - alpha)
+        got = R.backward(sc, cam, plain, w, k=8, traversal=traversal, saved=res["saved"])
         for key, v in got.items():
             np.testing.assert_allclose(v.cpu().numpy(), replay[key], rtol=1e-4, atol=1e-6)
     sc.close()
