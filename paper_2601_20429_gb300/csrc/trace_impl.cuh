@@ -1705,7 +1705,7 @@ __device__ __forceinline__ unsigned await_published(const ServeLive &live, unsig
 
 // Serving step: one persistent launch over the queue items of several requests (each with
 // its own scene, camera and output); a warp's 32 items always belong to one request.
-template <int K>
+template <int K, int TRAV>
 __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, false))
     k_serve(TraceArgs a, const ServeSeg *segs, const unsigned *begins, int n_segs, ServeLive live)
 {
@@ -1749,7 +1749,7 @@ __global__ void __launch_bounds__(kBlock, trace_min_blocks(K, false))
         float3 o, d;
         float tn, tf;
         bool valid = make_ray(cam, item, pix, o, d, tn, tf);
-        if (a.traversal == GRTX_TRAVERSAL_RESTART)
+        if constexpr (TRAV == TRAV_RESTART)
             trace_warp_restart<K, FORM_SPHERE, false, false>(a, sc, sg.out, slot, valid, pix, o, d, tn, tf, kb, cnt,
                                                       s_pst[threadIdx.x >> 5]);
         else
@@ -1849,14 +1849,15 @@ template <int K>
 int serve_launch(const TraceArgs &a, const ServeSeg *segs, const unsigned *begins, int n_segs, int blocks,
                  cudaStream_t s, ServeLive live)
 {
-    k_serve<K><<<blocks, 128, 0, s>>>(a, segs, begins, n_segs, live);
+    if (a.traversal == GRTX_TRAVERSAL_RESTART) k_serve<K, TRAV_RESTART><<<blocks, 128, 0, s>>>(a, segs, begins, n_segs, live);
+    else k_serve<K, TRAV_CKPT><<<blocks, 128, 0, s>>>(a, segs, begins, n_segs, live);
     return cudaGetLastError() == cudaSuccess ? GRTX_OK : GRTX_ERR_CUDA;
 }
 
 template <int K>
 int serve_occupancy(int *blocks_per_sm)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_serve<K>, 128, 0) == cudaSuccess
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_serve<K, TRAV_CKPT>, 128, 0) == cudaSuccess
                ? GRTX_OK : GRTX_ERR_CUDA;
 }
 
