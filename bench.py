@@ -220,6 +220,29 @@ def oracle_rate(g, cam, seconds: float, seed: int = 0, max_rays: int = 1 << 16):
         n = min(max_rays, max(n * 2, int(n * seconds / max(dt, 1e-3) * 1.05)))
 
 
+def oracle_rounds_rate(g, cam, seconds: float, k: int, seed: int = 1, max_rays: int = 1 << 20):
+    """Rays per second of the oracle's round tracer (FP64, its own median-split BVH,
+    checkpointed rounds of k, the same algorithm as the GPU path) on a seeded sample of the
+    camera's rays, sized to take about `seconds`: a CPU baseline that, unlike the brute-force
+    oracle, also walks a BVH. Returns (rays/s, sample size, cores, BVH build seconds)."""
+    from oracle import oracle as O
+    S = O.Scene.from_params(g)
+    t0 = time.perf_counter()
+    S.bvh()
+    build_s = time.perf_counter() - t0
+    o, d, tn, tf = O.camera_rays(cam)
+    rng = np.random.default_rng(seed)
+    n = 256
+    while True:
+        idx = rng.choice(o.shape[0], n, replace=False)
+        t0 = time.perf_counter()
+        S.render_rounds((o[idx], d[idx], tn[idx], tf[idx]), k=k, checkpoint=True)
+        dt = time.perf_counter() - t0
+        if dt >= seconds or n >= max_rays:
+            return n / dt, n, O.num_threads(), build_s
+        n = min(max_rays, max(n * 2, int(n * seconds / max(dt, 1e-3) * 1.05)))
+
+
 def run_reference(args, dist: Dist):
     """The FP64 CPU oracle as the reference arm: each step traces a bounded sample of the
     workload's rays on the host cores; same metric and unit as the GPU arm."""
@@ -858,6 +881,11 @@ def main():
         rate, nsamp, cores = oracle_rate(g, cam, args.cpu_seconds)
         cpu = {"value": rate / 1e6, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
                "sample": f"{nsamp} seeded random pixels of the 1920x1080 frame (FP64 brute force over 1M Gaussians)"}
+        rrate, rsamp, rcores, rbuild = oracle_rounds_rate(g, cam, args.cpu_seconds / 2, k)
+        cpu["rounds_tracer"] = {
+            "value": rrate / 1e6, "unit": "Mrays/s", "cores": rcores, "kind": "oracle round tracer",
+            "sample": f"{rsamp} seeded random pixels of the 1920x1080 frame (FP64, median-split BVH built in "
+                      f"{rbuild:.1f} s, checkpointed rounds of k={k})"}
 
     if dist.rank == 0:
         plain_mrays = n_rays / (statistics.mean(times_plain) / 1e3) / 1e6
