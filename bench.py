@@ -56,17 +56,20 @@ def parse():
 
 
 # Device code that decides what the profiled trace kernel does: its source, its k = 16
-# instantiation unit, the shared internal constants, and the BVH builder (the tree it walks).
+# instantiation unit, the shared internal constants, the BVH builder (the tree it walks) and
+# the public header (whose constants, such as the packet stack size, the kernels compile in).
 # Host-only files are left out, so a host-side change keeps a capture valid, and a change to
 # any of these files invalidates it until it is re-captured.
-PROFILED_SOURCES = ("trace_impl.cuh", "trace_k16.cu", "grtx_internal.cuh", "build.cu")
+PROFILED_SOURCES = ("paper_2601_20429_gb300/csrc/trace_impl.cuh", "paper_2601_20429_gb300/csrc/trace_k16.cu",
+                    "paper_2601_20429_gb300/csrc/grtx_internal.cuh", "paper_2601_20429_gb300/csrc/build.cu",
+                    "include/grtx.h")
 
 
 def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
     for f in PROFILED_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_2601_20429_gb300", "csrc", f), "rb").read())
+        h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 
 

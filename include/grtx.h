@@ -121,7 +121,11 @@ enum { GRTX_TRAVERSAL_CHECKPOINT = 0, /* resume from checkpointed nodes + evicti
  * codes, grtx_radix_tree). The tree shape changes the cost of a trace, never its result.
  * packet_stack: entries of the per-warp stack that a warp-packet traversal may use (0: all
  * GRTX_PACKET_STACK); a packet that would need more falls back to tracing its rays one by
- * one, with the same result. Smaller values exist to exercise that fallback.
+ * one, with the same result. Smaller values exist to exercise that fallback. (The stack holds
+ * the far children still pending along the warp's path: 48 entries of 16 bytes per warp, so
+ * that with the k-buffer a 128-ray block takes 19 KB of shared memory, and 8 blocks leave
+ * the SM a 92 KB L1 instead of 60 KB; no packet overflowed it on the 111-level tree of the
+ * 6M outdoor scene.)
  * bvh_width (the paper traverses a 6-wide BVH, Sec. V-A): 0 or 2, binary nodes; 4, the build
  * of a sphere-form scene also collapses the binary tree into 4-wide nodes (each binary node at
  * even depth becomes a node over its grandchildren, 128 bytes: lo x, lo y, lo z, hi x, hi y,
@@ -134,7 +138,7 @@ enum { GRTX_TRAVERSAL_CHECKPOINT = 0, /* resume from checkpointed nodes + evicti
  * step per axis, then per child and axis an 8-bit lower and upper grid coordinate, rounded
  * outwards so that the decoded box (corner + q * step, one FMA) contains the child's box;
  * then the four child refs. A trace reads whichever format the scene was built with. */
-#define GRTX_PACKET_STACK 64
+#define GRTX_PACKET_STACK 48
 enum { GRTX_CODES_SIZED = 0, GRTX_CODES_CENTROID = 1 };
 enum { GRTX_BUILDER_PLOC = 0, GRTX_BUILDER_LBVH = 1 };
 #define GRTX_PLOC_RADIUS 16
