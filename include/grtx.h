@@ -656,8 +656,8 @@ typedef struct grtx_request {
 } grtx_request;
 
 /* A finished request: tag, status, host wall-clock times in seconds (CLOCK_MONOTONIC) of
- * admission (work first enqueued) and completion (its last step observed complete), and the
- * device image [W*H][4] it was rendered into (the request's own buffer or a server-owned one). */
+ * admission and completion (the host saw its last tile written), and the device image
+ * [W*H][4] it was rendered into (the request's own buffer or a server-owned one). */
 typedef struct grtx_completion {
     uint64_t tag;
     int32_t status;
@@ -770,7 +770,8 @@ GRTX_API int grtx_render_requests(grtx_server *srv, const grtx_request *reqs, in
 /* Number of requests admitted but not yet completed, and pending in the queue. */
 GRTX_API int grtx_server_load(const grtx_server *srv, int *n_inflight, int *n_pending);
 
-/* Wait for all in-flight work and release the server (NULL is a no-op). */
+/* Close the running launches (their waiting warps stop), wait for all in-flight work and
+ * release the server (NULL is a no-op). */
 GRTX_API void grtx_server_destroy(grtx_server *srv);
 
 #ifdef __cplusplus
