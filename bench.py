@@ -56,13 +56,14 @@ def parse():
 
 
 # Device code that decides what the profiled trace kernel does: its source, its k = 16
-# instantiation unit, the shared internal constants, the BVH builder (the tree it walks) and
-# the public header (whose constants, such as the packet stack size, the kernels compile in).
-# Host-only files are left out, so a host-side change keeps a capture valid, and a change to
-# any of these files invalidates it until it is re-captured.
+# instantiation unit, the shared internal constants, the BVH builder (the tree it walks), and
+# the constants and enumerations of the public header that the kernels compile in (such as the
+# packet stack size; its prose and host declarations are left out). Host-only files are left
+# out too, so a host-side change keeps a capture valid, and a change to any of these inputs
+# invalidates it until it is re-captured.
 PROFILED_SOURCES = ("paper_2601_20429_gb300/csrc/trace_impl.cuh", "paper_2601_20429_gb300/csrc/trace_k16.cu",
-                    "paper_2601_20429_gb300/csrc/grtx_internal.cuh", "paper_2601_20429_gb300/csrc/build.cu",
-                    "include/grtx.h")
+                    "paper_2601_20429_gb300/csrc/grtx_internal.cuh", "paper_2601_20429_gb300/csrc/build.cu")
+PROFILED_HEADER = "include/grtx.h"
 
 
 def kernel_source_hash() -> str:
@@ -70,6 +71,14 @@ def kernel_source_hash() -> str:
     h = hashlib.sha256()
     for f in PROFILED_SOURCES:
         h.update(open(os.path.join(ROOT, f), "rb").read())
+    in_enum = False
+    for line in open(os.path.join(ROOT, PROFILED_HEADER), "rb").read().splitlines():
+        t = line.split(b"/*")[0].strip()                    # code only, not the comments
+        in_enum = in_enum or t.startswith(b"enum")
+        if in_enum or t.startswith(b"#define"):
+            h.update(t + b"\n")
+        if in_enum and b"}" in t:
+            in_enum = False
     return h.hexdigest()[:16]
 
 
