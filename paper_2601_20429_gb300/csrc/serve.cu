@@ -286,7 +286,8 @@ std::vector<Piece> take_pieces(grtx_server *v, int64_t budget, int max_pieces)
     return pieces;
 }
 
-// Segment records of `pieces` from segment j0 on, the launch's items from item0 on.
+// Segment records (and begins entries) of `pieces`, after the launch's current segments and
+// items.
 void fill_segments(grtx_server *v, SrvStep &st, const std::vector<Piece> &pieces)
 {
     for (const Piece &pc : pieces) {
@@ -373,9 +374,9 @@ int schedule_step(grtx_server *v, int si)
 }
 
 // Append unscheduled work to the running launch of slot si (its warps pick it up without a
-// new launch): the records, then the segment count, then the item count, on the control
-// stream after the launch's own copies. Returns false when the launch's segment table (or
-// its staging) is full.
+// new launch): the records and their entries of the begins array, then the item count, on
+// the control stream after the launch's own copies. Returns false when the launch's segment
+// table (or its staging) is full, or its item numbers would come near 2^31.
 bool append_to_step(grtx_server *v, int si)
 {
     SrvStep &st = v->steps[si];
