@@ -724,6 +724,13 @@ GRTX_API int grtx_server_release(grtx_server *srv, float *d_rgbT);
  * GRTX_ERR_INVALID_ARG if linger_ns is negative or above 1 s. */
 GRTX_API int grtx_server_set_linger(grtx_server *srv, int64_t linger_ns);
 
+/* on = 1 (the default): the host appends to a launch that has run out of work only while its
+ * last publication is less than linger_ns / 2 old (see grtx_server_set_linger). on = 0: it
+ * appends to any launch none of whose warps it has seen stop, so that appends race with warps
+ * giving up; tiles published to warps that have stopped are then traced by a later launch
+ * (the recovery every launch has, exercised often). Same images either way. Host call. */
+GRTX_API int grtx_server_set_append_guard(grtx_server *srv, int on);
+
 /* Order in which admitted requests' work is published to the running launch: by deadline,
  * admission time + size_ns_per_ray x the request's rays (default 10 ns per ray). 0: admission
  * order; large: the smallest request first. Host call. GRTX_ERR_INVALID_ARG unless

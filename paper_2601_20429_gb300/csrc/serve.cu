@@ -207,6 +207,7 @@ struct grtx_server {
     int64_t n_launches = 0, n_appends = 0, n_retried = 0;
     unsigned linger_ns = kLingerNs;
     double size_ns = kSizeNs;   // deadline weight of a request's size (see take_pieces)
+    bool append_guard = true;   // see grtx_server_set_append_guard
 };
 
 namespace {
@@ -719,7 +720,8 @@ extern "C" GRTX_API int grtx_server_poll(grtx_server *v, grtx_completion *done, 
             if (*reinterpret_cast<volatile unsigned *>(st.h_exited) != 0) {
                 close_step(v, v->live);
             } else if (has_unscheduled(v)) {
-                if (left <= 0 && now_s() - st.t_pub >= 0.5e-9 * v->linger_ns) close_step(v, v->live);
+                if (left <= 0 && v->append_guard && now_s() - st.t_pub >= 0.5e-9 * v->linger_ns)
+                    close_step(v, v->live);
                 else if (2 * left < v->max_rays && !append_to_step(v, v->live)) close_step(v, v->live);
             }
         }
@@ -786,6 +788,13 @@ extern "C" GRTX_API int grtx_server_set_linger(grtx_server *v, int64_t linger_ns
     if (!v) return grtx_fail(GRTX_ERR_INVALID_ARG, "server is NULL");
     if (linger_ns < 0 || linger_ns > 1000000000) return grtx_fail(GRTX_ERR_INVALID_ARG, "linger_ns must be in [0, 1e9]");
     v->linger_ns = (unsigned)linger_ns;
+    return GRTX_OK;
+}
+
+extern "C" GRTX_API int grtx_server_set_append_guard(grtx_server *v, int on)
+{
+    if (!v) return grtx_fail(GRTX_ERR_INVALID_ARG, "server is NULL");
+    v->append_guard = on != 0;
     return GRTX_OK;
 }
 

@@ -210,6 +210,7 @@ _SIGS = {
     "grtx_server_get_info": (C.c_int, [_fp, C.POINTER(grtx_server_info)]),
     "grtx_server_set_linger": (C.c_int, [_fp, C.c_int64]),
     "grtx_server_set_order": (C.c_int, [_fp, C.c_double]),
+    "grtx_server_set_append_guard": (C.c_int, [_fp, C.c_int]),
     "grtx_server_submit": (C.c_int, [_fp, C.POINTER(grtx_request), C.c_int]),
     "grtx_server_poll": (C.c_int, [_fp, C.POINTER(grtx_completion), C.c_int, C.POINTER(C.c_int), C.c_int]),
     "grtx_render_requests": (C.c_int, [_fp, C.POINTER(grtx_request), C.c_int, C.POINTER(grtx_completion),

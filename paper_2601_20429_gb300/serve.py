@@ -14,7 +14,7 @@ from .render import Scene, trace_params
 class Server:
     def __init__(self, scenes: list[Scene], k=16, traversal="checkpoint", max_rays_per_step=0, max_inflight=0,
                  stream: torch.cuda.Stream | None = None, mem_budget_bytes=0, linger_us: float | None = None,
-                 size_ns_per_ray: float | None = None, **params):
+                 size_ns_per_ray: float | None = None, append_guard: bool = True, **params):
         self.scenes = list(scenes)
         self.stream = stream or torch.cuda.Stream()
         alpha_min = self.scenes[0].alpha_min
@@ -29,6 +29,8 @@ class Server:
         if linger_us is not None:
             N.check(N.lib().grtx_server_set_linger(C.c_void_p(self.handle), int(round(linger_us * 1000))),
                     "grtx_server_set_linger")
+        if not append_guard:
+            N.check(N.lib().grtx_server_set_append_guard(C.c_void_p(self.handle), 0), "grtx_server_set_append_guard")
         if size_ns_per_ray is not None:
             N.check(N.lib().grtx_server_set_order(C.c_void_p(self.handle), float(size_ns_per_ray)),
                     "grtx_server_set_order")

@@ -64,6 +64,7 @@ def test_host_side_argument_errors(lib):
     assert lib.grtx_server_get_info(None, None) == 1
     assert lib.grtx_server_set_linger(None, 0) == 1
     assert lib.grtx_server_set_order(None, 0.0) == 1
+    assert lib.grtx_server_set_append_guard(None, 1) == 1
 
 
 def test_host_side_errors_of_the_extensions(lib):

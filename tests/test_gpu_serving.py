@@ -140,13 +140,14 @@ def test_new_requests_join_the_running_launch(world):
     srv.close()
 
 
-@pytest.mark.parametrize("linger_us", [0, 3, 30])
-def test_short_waits_lose_no_tiles(world, linger_us):
+@pytest.mark.parametrize("linger_us,guard", [(0, True), (3, True), (30, True), (0, False), (3, False)])
+def test_short_waits_lose_no_tiles(world, linger_us, guard):
     """With waits too short to bridge the gaps between submissions, launches end while work is
-    being appended to them: tiles a warp gave up on, and items published after the last warp
-    stopped, are traced by later launches, and every image is still the lone render."""
+    appended to them (without the host's guard, often: it then appends to any launch it has
+    not seen stop): tiles a warp gave up on, and items published after the last warp stopped,
+    are traced by later launches, and every image is still the lone render."""
     sc, reqs, alone = world
-    srv = Server(sc, k=16, max_rays_per_step=6_000, max_inflight=6, linger_us=linger_us)
+    srv = Server(sc, k=16, max_rays_per_step=6_000, max_inflight=6, linger_us=linger_us, append_guard=guard)
     bufs = _bufs(reqs)
     got = []
     for i, (r, b) in enumerate(zip(reqs, bufs)):
@@ -159,8 +160,40 @@ def test_short_waits_lose_no_tiles(world, linger_us):
     worst = max(_same(a, b) for a, b in zip(alone, bufs))
     assert worst <= 1e-5
     info = srv.info()
-    print(f"linger {linger_us} us: {info['n_launches']} launches, {info['n_appends']} appends, "
+    print(f"linger {linger_us} us, guard {guard}: {info['n_launches']} launches, {info['n_appends']} appends, "
           f"{info['n_retried_tiles']} tiles retried")
+    srv.close()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_random_schedules_give_the_lone_images(world, seed):
+    """Randomised use of the server: requests submitted in random bursts between blocking and
+    non-blocking polls, under a random wait of idle warps (0, 5 us, the default, 200 ms), a
+    random publication order (admission order, the default deadline weight, smallest first),
+    small or default publications, and a segment table of 4 x 2 pieces (launches close when
+    it fills). Every request completes once, with the lone image."""
+    sc, reqs, alone = world
+    rng = np.random.default_rng(seed)
+    linger = [0.0, 5.0, None, 200_000.0][rng.integers(4)]
+    order = [0.0, None, 1e6][rng.integers(3)]
+    chunk = int(rng.choice([0, 4096, 20_000]))
+    srv = Server(sc, k=16, max_rays_per_step=chunk, max_inflight=2, linger_us=linger, size_ns_per_ray=order)
+    bufs = _bufs(reqs)
+    todo = list(rng.permutation(len(reqs)))
+    got = []
+    while todo or len(got) < len(reqs):
+        if todo and rng.random() < 0.5:
+            burst = [int(todo.pop()) for _ in range(min(len(todo), int(rng.integers(1, 5))))]
+            srv.submit([(reqs[j]["scene"], reqs[j]["camera"], bufs[j], j) for j in burst])
+        got += srv.poll(wait=bool(rng.random() < 0.3) and not todo)
+    torch.cuda.synchronize()
+    assert sorted(d["tag"] for d in got) == list(range(len(reqs)))
+    assert all(d["status"] == 0 and d["t_done"] >= d["t_admit"] for d in got)
+    for a, b in zip(alone, bufs):
+        _same(a, b)
+    info = srv.info()
+    print(f"seed {seed}: linger {linger}, order {order}, chunk {chunk}: {info['n_launches']} launches, "
+          f"{info['n_appends']} appends, {info['n_retried_tiles']} tiles retried")
     srv.close()
 
 
