@@ -685,16 +685,17 @@ typedef struct grtx_completion {
  * finishes. max_inflight: requests admitted at once (0: 64).
  *
  * Memory (the paper sizes its checkpoint and eviction buffers per resident ray slot and
- * reports their total, Sec. V-E). The server runs up to 4 step slots, each with its own
- * stream (slot 0 uses `stream`, the others streams the server creates), queue counter and
+ * reports their total, Sec. V-E). The server runs up to 2 step slots, each with its own
+ * stream (slot 0 uses `stream`, the other a stream the server creates), queue counter and
  * checkpoint/eviction lists, so that a new launch fills the SMs the finishing launch's last
- * warps leave. One step slot's lists take (resident ray slots) x (2 ckpt_capacity +
- * evict_capacity) x 8 bytes: about 1.3 GB with the default capacities at full residency on
- * 152 SMs.
- *   - mem_budget_bytes = 0: no cap. 4 step slots at full residency; requests must bring their
+ * warps leave (a third slot gave the same latency and throughput; a single slot makes each
+ * new launch wait for the previous one to end). One step slot's lists take (resident ray
+ * slots) x (2 ckpt_capacity + evict_capacity) x 8 bytes: about 1.2 GB with the default
+ * capacities at full residency on 152 SMs.
+ *   - mem_budget_bytes = 0: no cap. 2 step slots at full residency; requests must bring their
  *     own output (d_rgbT = NULL is rejected with GRTX_ERR_INVALID_ARG).
  *   - mem_budget_bytes > 0: the server's device memory never exceeds it. The step slots' lists
- *     take at most half of it: as many full-residency step slots as fit (1 to 4), or one slot
+ *     take at most half of it: as many full-residency step slots as fit (1 or 2), or one slot
  *     with as many 128-ray blocks as fit; GRTX_ERR_INVALID_ARG if not even one block of lists
  *     fits. The rest (less the small segment tables) is reserved as an output arena. A request
  *     with d_rgbT = NULL needs W*H*16 bytes of it: requests are admitted in submission order,
@@ -739,7 +740,7 @@ GRTX_API int grtx_server_set_order(grtx_server *srv, double size_ns_per_ray);
 
 /* Sizes chosen at creation and current use (host call). */
 typedef struct grtx_server_info {
-    int32_t n_step_slots;        /* step slots (streams) the server runs, 1..4             */
+    int32_t n_step_slots;        /* step slots (streams) the server runs, 1 or 2           */
     int32_t blocks_per_step;     /* 128-ray blocks of one step's persistent launch          */
     int64_t list_bytes;          /* checkpoint/eviction lists of all step slots             */
     int64_t arena_bytes;         /* output arena reserved for server-owned outputs          */

@@ -38,7 +38,7 @@ int grtx_check_params(const grtx_params *p);
 namespace {
 
 constexpr int kMaxPending = 65536;
-constexpr int kSteps = 4;         // step slots (streams) in flight
+constexpr int kSteps = 2;         // step slots (streams): the live launch and one finishing
 constexpr int kQueueStride = 32;   // the slots' queue counters on separate 128-byte lines
 constexpr unsigned kLingerNs = 2000000;   // default wait of a live launch's warps for new work
 constexpr double kSizeNs = 10.0;          // default deadline weight: 10 ns per ray

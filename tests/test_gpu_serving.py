@@ -304,7 +304,7 @@ def test_memory_budget_mixes_owned_and_caller_outputs_and_rejects_oversize(world
     with pytest.raises(N.GrtxError) as e:
         plain.submit([(0, reqs[0]["camera"], None, 0)])
     assert e.value.status == 1
-    assert plain.info()["n_step_slots"] == 4 and plain.info()["arena_bytes"] == 0
+    assert plain.info()["n_step_slots"] == 2 and plain.info()["arena_bytes"] == 0
     plain.close()
     with pytest.raises(N.GrtxError) as e:
         Server(sc, k=16, mem_budget_bytes=PER_BLOCK, max_inflight=8, **CAPS)   # half is below a block
