@@ -82,7 +82,10 @@ __device__ __forceinline__ bool world_round(const WorldArgs &W, float3 o, float3
                                             Counters &cnt)
 {
     const size_t S = (size_t)W.a.n_slots;
-    uint4 stack[kWorldStack];
+    // far children still to visit: node ref and instance (a popped node is entered without the
+    // t_max test of its entry, -inf: its children are tested, which is exact and halves the
+    // stack's local-memory traffic against keeping the entry distance)
+    uint2 stack[kWorldStack];
     int sp = 0, si = 0;
     float tmax = kb.tmax;
     uint32_t ref, inst;
@@ -177,7 +180,7 @@ __device__ __forceinline__ bool world_round(const WorldArgs &W, float3 o, float3
                         if (INSTR) cnt.ckpt++;
                     }
                 } else if (sp < kWorldStack) {
-                    stack[sp++] = make_uint4(far_ref, __float_as_uint(far_t), inst, 0u);
+                    stack[sp++] = make_uint2(far_ref, inst);
                 } else if (INSTR) {
                     cnt.overflow++;
                 }
@@ -192,8 +195,8 @@ __device__ __forceinline__ bool world_round(const WorldArgs &W, float3 o, float3
         if (sp > 0) {
             --sp;
             ref = stack[sp].x;
-            te = __uint_as_float(stack[sp].y);
-            inst = stack[sp].z;
+            te = -GRTX_INF;
+            inst = stack[sp].y;
         } else if (si < n_src) {
             uint4 v = src[(size_t)si * S];
             ++si;
