@@ -508,7 +508,8 @@ def bench_serving(n_requests: int, max_rays_per_step: int = 0, max_inflight: int
     chunk = max_rays_per_step or 2 * 32 * 4 * i0["blocks_per_step"]
     res.update(max_rays_per_step=chunk, max_inflight=max_inflight, traversal="checkpoint",
                launches=i1["n_launches"] - i0["n_launches"], appends=i1["n_appends"] - i0["n_appends"],
-               retried_tiles=i1["n_retried_tiles"] - i0["n_retried_tiles"])
+               retried_tiles=i1["n_retried_tiles"] - i0["n_retried_tiles"], step_slots=i0["n_step_slots"],
+               list_bytes=i0["list_bytes"], device_bytes=i0["device_bytes"])
     if capacity_rates:
         sweep = []
         for rate in capacity_rates:
