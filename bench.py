@@ -494,9 +494,13 @@ def bench_serving(n_requests: int, max_rays_per_step: int = 0, max_inflight: int
     def server(traversal):
         srv = Server(gpu_scenes, k=cfg["k"], traversal=traversal, max_rays_per_step=max_rays_per_step,
                      max_inflight=max_inflight, linger_us=linger_us)
-        # warm-up: a few requests of each size
+        # warm-up: a few requests of each size, then one second of another stream at the
+        # configured rate (other views), so that the timed stream meets a server in its steady
+        # state
         warm = [torch.empty((1920 * 1080, 4), dtype=torch.float32, device="cuda") for _ in range(8)]
         srv.render_requests([(j % 4, reqs[j]["camera"], warm[j], 10 ** 9 + j) for j in range(8)])
+        run_stream(srv, scenes.request_stream(n_requests=200, rate_hz=200.0, n_scenes=len(gpu_scenes), seed=1004),
+                   200.0)
         torch.cuda.synchronize()
         return srv
 

@@ -713,27 +713,29 @@ GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scenes, const g
  * GRTX_ERR_NOT_FOUND if d_rgbT is not a live server-owned output. */
 GRTX_API int grtx_server_release(grtx_server *srv, float *d_rgbT);
 
-/* How long, in nanoseconds, the warps of a running step launch that has run out of work
- * wait for more (default 2,000,000: 2 ms; each new publication restarts the wait). Work that
- * arrives while a launch runs, or while its warps wait, is appended to that launch (its warps
- * take it without a new launch); the host appends to a launch without work only while its
- * last publication is less than linger_ns / 2 old, so that no warp stops before the append
- * lands (a tile published to a warp that has stopped all the same is traced by a later
- * launch). Waiting warps keep their SMs: kernels of other streams start on them once the
- * launch ends, at most linger_ns after its last publication. 0: a launch ends as soon as its
- * published work is taken. Applies to launches started after the call. Host call.
- * GRTX_ERR_INVALID_ARG if linger_ns is negative or above 1 s. */
+/* How long, in nanoseconds, a running step launch that has run out of work stays open for
+ * more while admitted requests are still in flight (default 2,000,000: 2 ms). Work that
+ * arrives while a launch is open is appended to it (its warps take it without a new launch);
+ * the host closes the launch (its waiting warps stop) when no admitted request is left, when it
+ * has had no work for linger_ns (checked by grtx_server_poll), or when its segment table is
+ * full. As a backstop for a caller that stops polling, waiting warps stop on their own after
+ * 16 x linger_ns without a publication (at least 20 ms, at most 1 s); a tile published to a
+ * warp that has stopped is traced by a later launch. Waiting warps keep their SMs: kernels of
+ * other streams start on them once the launch ends. 0: a launch ends as soon as its published
+ * work is taken (its warps do not wait). Applies to launches started after the call. Host
+ * call. GRTX_ERR_INVALID_ARG if linger_ns is negative or above 1 s. */
 GRTX_API int grtx_server_set_linger(grtx_server *srv, int64_t linger_ns);
 
-/* on = 1 (the default): the host appends to a launch that has run out of work only while its
- * last publication is less than linger_ns / 2 old (see grtx_server_set_linger). on = 0: it
- * appends to any launch none of whose warps it has seen stop, so that appends race with warps
- * giving up; tiles published to warps that have stopped are then traced by a later launch
- * (the recovery every launch has, exercised often). Same images either way. Host call. */
+/* on = 1 (the default): waiting warps stop on their own only after the backstop described at
+ * grtx_server_set_linger, so that appends do not race with warps giving up. on = 0: they stop
+ * linger_ns after the last publication, and the host appends to any launch none of whose warps
+ * it has seen stop, so that appends race with warps giving up; tiles published to warps that
+ * have stopped are then traced by a later launch (the recovery every launch has, exercised
+ * often). Same images either way. Applies to launches started after the call. Host call. */
 GRTX_API int grtx_server_set_append_guard(grtx_server *srv, int on);
 
 /* Order in which admitted requests' work is published to the running launch: by deadline,
- * admission time + size_ns_per_ray x the request's rays (default 10 ns per ray). 0: admission
+ * admission time + size_ns_per_ray x the request's rays (default 5 ns per ray). 0: admission
  * order; large: the smallest request first. Host call. GRTX_ERR_INVALID_ARG unless
  * 0 <= size_ns_per_ray <= 1e9. */
 GRTX_API int grtx_server_set_order(grtx_server *srv, double size_ns_per_ray);
@@ -746,7 +748,7 @@ typedef struct grtx_server_info {
     int64_t arena_bytes;         /* output arena reserved for server-owned outputs          */
     int64_t arena_used;          /* bytes of the arena held by admitted, unreleased outputs */
     int64_t device_bytes;        /* all device memory the server holds                      */
-    int32_t n_inflight;          /* admitted, not yet completed                            */
+    int32_t n_inflight;          /* admitted, not yet returned by grtx_server_poll           */
     int32_t n_pending;           /* submitted, not yet admitted                            */
     int64_t n_launches;          /* step launches so far                                    */
     int64_t n_appends;           /* publications of new work to a running launch so far     */
@@ -760,13 +762,15 @@ GRTX_API int grtx_server_get_info(const grtx_server *srv, grtx_server_info *info
  * GRTX_ERR_INVALID_ARG); GRTX_ERR_NOT_FOUND for an unknown scene id. */
 GRTX_API int grtx_server_submit(grtx_server *srv, const grtx_request *reqs, int n);
 
-/* Advance the server: admit pending requests (continuous batching), publish work to the live
- * launch or start a launch (see grtx_server_create), and report requests whose tiles have all
- * been traced (each piece of a request raises a flag in host memory when its last tile is
- * written). Writes at most max_done completions to done (host) and their count to *n_done.
- * Non-blocking unless wait != 0, in which case it blocks until at least one request
- * completes or none is admitted. Call it often while requests are in flight: work is
- * published only when it runs. */
+/* Take completed requests. The server's scheduler thread (started by grtx_server_create, ended
+ * by grtx_server_destroy) does the rest on its own, every 20 us while there is work: it admits
+ * pending requests (continuous batching), publishes work to the live launch or starts a launch
+ * (see grtx_server_create), and completes requests whose tiles have all been traced (each piece
+ * of a request raises a flag in host memory when its last tile is written). Writes at most
+ * max_done completions to done (host) and their count to *n_done. Non-blocking unless
+ * wait != 0, in which case it blocks until at least one request has completed or none is
+ * admitted. A failure of the scheduler thread (a CUDA error) is returned by every poll from
+ * then on. The server's calls may come from any host thread. */
 GRTX_API int grtx_server_poll(grtx_server *srv, grtx_completion *done, int max_done, int *n_done,
                               int wait);
 
@@ -775,11 +779,12 @@ GRTX_API int grtx_server_poll(grtx_server *srv, grtx_completion *done, int max_d
 GRTX_API int grtx_render_requests(grtx_server *srv, const grtx_request *reqs, int n,
                                   grtx_completion *done, int *n_done, void *stream);
 
-/* Number of requests admitted but not yet completed, and pending in the queue. */
+/* Number of requests admitted but not yet returned by grtx_server_poll, and pending in the
+ * queue. */
 GRTX_API int grtx_server_load(const grtx_server *srv, int *n_inflight, int *n_pending);
 
-/* Close the running launches (their waiting warps stop), wait for all in-flight work and
- * release the server (NULL is a no-op). */
+/* Stop the scheduler thread, close the running launches (their waiting warps stop), wait for
+ * all in-flight work and release the server (NULL is a no-op). */
 GRTX_API void grtx_server_destroy(grtx_server *srv);
 
 #ifdef __cplusplus

@@ -7,15 +7,21 @@
 // never drains into a tail while work is waiting. Its warps wait a short while for more work
 // when there is none. A full or idle launch is closed and the next one starts in another step
 // slot (own stream and lists), taking the SMs the old one's last warps leave.
+// A scheduler thread of the server does all of this; callers only queue requests and take
+// completions.
 #include <cuda_runtime.h>
 #include <time.h>
 
 #include <algorithm>
+#include <chrono>
+#include <condition_variable>
 #include <cstring>
 #include <deque>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "trace_impl.cuh"
@@ -41,7 +47,7 @@ constexpr int kMaxPending = 65536;
 constexpr int kSteps = 2;         // step slots (streams): the live launch and one finishing
 constexpr int kQueueStride = 32;   // the slots' queue counters on separate 128-byte lines
 constexpr unsigned kLingerNs = 2000000;   // default wait of a live launch's warps for new work
-constexpr double kSizeNs = 10.0;          // default deadline weight: 10 ns per ray
+constexpr double kSizeNs = 5.0;           // default deadline weight: 5 ns per ray
 
 double now_s()
 {
@@ -173,6 +179,7 @@ struct SrvStep {
     int n_pub = 0;                  // publications used (staging words)
     bool closed = false;            // the host appends nothing more to this launch
     double t_pub = 0;               // host time of the launch's last publication
+    unsigned claimed_max = 0;       // largest claim mirror the host has read
     bool busy = false;
 };
 
@@ -202,12 +209,23 @@ struct grtx_server {
     cudaStream_t ctl = nullptr; // copies of segments appended to running launches
     unsigned lost_cap = 0;      // warps of a launch
     std::vector<unsigned> h_lost;
-    unsigned *h_one = nullptr;  // pinned word 1 (the copy that closes a launch)
+    unsigned *h_one = nullptr;  // pinned: word 1 (the copy that closes a launch), then read-back words
     int live = -1;              // slot of the launch new work is appended to (-1: none)
     int64_t n_launches = 0, n_appends = 0, n_retried = 0;
     unsigned linger_ns = kLingerNs;
     double size_ns = kSizeNs;   // deadline weight of a request's size (see take_pieces)
     bool append_guard = true;   // see grtx_server_set_append_guard
+    // the scheduler thread: it admits, publishes, starts and closes launches, and collects
+    // completions, every 20 us while there is work; callers only queue requests and take
+    // completions. Every field above is guarded by mu.
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::thread worker;
+    bool stop = false;
+    bool admit_blocked = false; // pending requests wait for arena memory (after an admission pass)
+    int dev = 0;
+    int err = GRTX_OK;          // a failure of the scheduler thread, reported by every later poll
+    std::string err_msg;
 };
 
 namespace {
@@ -358,7 +376,13 @@ int schedule_step(grtx_server *v, int si)
     live.lost_cap = v->lost_cap;
     live.exited = st.d_exited;
     live.exited_host = st.d_exited_host;
-    live.linger_ns = v->linger_ns;
+    // the warps' own bound on a wait without any publication. With the guard (the default) it
+    // is a backstop for a host that stops polling, well past the host's own linger, so that an
+    // append never races with warps giving up; without it, the linger itself
+    live.linger_ns = (!v->append_guard || v->linger_ns == 0)
+                         ? v->linger_ns
+                         : (unsigned)std::min<uint64_t>(1000000000ull,
+                                                        std::max<uint64_t>(20000000ull, 16ull * v->linger_ns));
     live.claimed_host = st.d_claimed_host;
     if (serve_launch_k(v->p.k, a, st.d, st.d_begins, v->seg_cap, v->blocks, st.s, live) != GRTX_OK) {
         cudaError_t e = cudaGetLastError();
@@ -368,6 +392,7 @@ int schedule_step(grtx_server *v, int si)
     st.busy = true;
     st.closed = false;
     st.t_pub = now_s();
+    st.claimed_max = 0;
     v->inflight.push_back(si);
     v->live = si;
     ++v->n_launches;
@@ -420,6 +445,10 @@ bool has_unscheduled(const grtx_server *v)
 }
 
 }  // namespace
+
+namespace {
+void scheduler(grtx_server *v);
+}
 
 extern "C" GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scenes, const grtx_params *p,
                                            int64_t mem_budget_bytes, int64_t max_rays_per_step, int max_inflight,
@@ -507,7 +536,7 @@ extern "C" GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scen
     cudaError_t e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaMalloc((void **)&v->queue, kSteps * kQueueStride * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&v->ctl, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&v->h_one, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&v->h_one, 4 * sizeof(unsigned));
     if (e == cudaSuccess) *v->h_one = 1;
     for (int i = 0; i < n_steps && e == cudaSuccess; ++i) {
         SrvStep &sst = v->steps[i];
@@ -557,6 +586,13 @@ extern "C" GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scen
     v->list_bytes = (size_t)n_steps * ws;
     v->device_bytes = v->list_bytes + arena + tables_for(n_steps, blocks);
     a.n_slots = n_slots;
+    cudaGetDevice(&v->dev);
+    try {
+        v->worker = std::thread(scheduler, v);
+    } catch (...) {
+        server_free(v);
+        return grtx_fail(GRTX_ERR_OOM, "could not start the server's scheduler thread");
+    }
     *out = v;
     return GRTX_OK;
 }
@@ -564,6 +600,7 @@ extern "C" GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scen
 extern "C" GRTX_API int grtx_server_submit(grtx_server *v, const grtx_request *reqs, int n)
 {
     if (!v || (n > 0 && !reqs) || n < 0) return grtx_fail(GRTX_ERR_INVALID_ARG, "bad submit arguments");
+    std::lock_guard<std::mutex> lk(v->mu);
     if ((int64_t)v->pending.size() + n > kMaxPending) return grtx_fail(GRTX_ERR_BUSY, "pending queue is full");
     std::vector<SrvReq *> add;
     for (int i = 0; i < n; ++i) {
@@ -598,14 +635,20 @@ extern "C" GRTX_API int grtx_server_submit(grtx_server *v, const grtx_request *r
         add.push_back(r);
     }
     for (auto *r : add) v->pending.push_back(r);
+    if (!add.empty()) {
+        v->admit_blocked = false;          // until the scheduler's next admission pass
+        v->cv_work.notify_one();
+    }
     return GRTX_OK;
 }
 
-extern "C" GRTX_API int grtx_server_poll(grtx_server *v, grtx_completion *done, int max_done, int *n_done, int wait)
+namespace {
+
+// One pass of the scheduler (the caller holds v->mu): segments finished inside running
+// launches, ended launches (their untraced tiles go back to their requests), admission,
+// publication to the live launch, and a new launch when the live one is gone.
+int advance(grtx_server *v)
 {
-    if (!v || !n_done || max_done < 0 || (max_done > 0 && !done)) return grtx_fail(GRTX_ERR_INVALID_ARG, "bad poll arguments");
-    *n_done = 0;
-    int got = 0;
     // a segment is complete (or its launch ended): the request is reported once all of its
     // items have been scheduled, traced, and all of its segments are complete
     auto segment_done = [&](SrvStep &st, size_t j, double t) {
@@ -622,17 +665,19 @@ extern "C" GRTX_API int grtx_server_poll(grtx_server *v, grtx_completion *done, 
         v->backlog.push_back(c);
         v->active.erase(std::find(v->active.begin(), v->active.end(), r));
         delete r;
-        ++got;
     };
     // tiles of an ended launch that no warp traced (claims given up before the host published
     // them, or items published after the last warp stopped) go back to their requests, as
     // ranges of consecutive items
     auto recover = [&](SrvStep &st, int si) -> int {
-        unsigned q = 0, n_lost = 0;
-        GRTX_CUDA(cudaStreamSynchronize(v->ctl));            // appends of this launch have landed
-        GRTX_CUDA(cudaMemcpy(&q, v->queue + kQueueStride * si, sizeof(unsigned), cudaMemcpyDeviceToHost));
-        GRTX_CUDA(cudaMemcpy(&n_lost, st.d_lost, sizeof(unsigned), cudaMemcpyDeviceToHost));
-        n_lost = std::min(n_lost, v->lost_cap);
+        // (copies on the control stream, after the launch's appends; the launch has ended, and a
+        // synchronous copy would also wait for the other streams' work)
+        unsigned *qn = v->h_one + 1;                         // pinned: queue counter, lost count
+        GRTX_CUDA(cudaMemcpyAsync(qn, v->queue + kQueueStride * si, sizeof(unsigned), cudaMemcpyDeviceToHost, v->ctl));
+        GRTX_CUDA(cudaMemcpyAsync(qn + 1, st.d_lost, sizeof(unsigned), cudaMemcpyDeviceToHost, v->ctl));
+        GRTX_CUDA(cudaStreamSynchronize(v->ctl));
+        const unsigned q = qn[0];
+        unsigned n_lost = std::min(qn[1], v->lost_cap);
         std::vector<std::pair<SrvReq *, unsigned>> tiles;    // {request, first item}
         auto add = [&](unsigned b) {
             const size_t j = (size_t)(std::upper_bound(st.seg_begin.begin(), st.seg_begin.end(), b) -
@@ -641,7 +686,9 @@ extern "C" GRTX_API int grtx_server_poll(grtx_server *v, grtx_completion *done, 
         };
         if (n_lost) {
             v->h_lost.resize(n_lost);
-            GRTX_CUDA(cudaMemcpy(v->h_lost.data(), st.d_lost + 1, sizeof(unsigned) * n_lost, cudaMemcpyDeviceToHost));
+            GRTX_CUDA(cudaMemcpyAsync(v->h_lost.data(), st.d_lost + 1, sizeof(unsigned) * n_lost, cudaMemcpyDeviceToHost,
+                                      v->ctl));
+            GRTX_CUDA(cudaStreamSynchronize(v->ctl));
             for (unsigned b : v->h_lost)
                 if (b < st.n_items) add(b);
         }
@@ -658,98 +705,142 @@ extern "C" GRTX_API int grtx_server_poll(grtx_server *v, grtx_completion *done, 
         }
         return GRTX_OK;
     };
-    for (;;) {
-        // segments finished inside running steps
-        double t = now_s();
-        for (int si : v->inflight) {
-            SrvStep &st = v->steps[si];
-            const volatile unsigned *flag = st.h_flag;
-            for (size_t j = 0; j < st.seg_req.size(); ++j)
-                if (!st.seg_seen[j] && flag[j] == st.seq) segment_done(st, j, t);
-        }
-        // ended launches free their slots: untraced tiles go back to their requests, and
-        // every other segment of the launch is complete
-        for (size_t i = 0; i < v->inflight.size();) {
-            const int si = v->inflight[i];
-            SrvStep &st = v->steps[si];
-            cudaError_t q = cudaEventQuery(st.ev);
-            if (q == cudaErrorNotReady) {
-                ++i;
-                continue;
-            }
-            if (q != cudaSuccess) return grtx_cuda_fail(q, "serve step");
-            int rs = recover(st, si);
-            if (rs != GRTX_OK) return rs;
-            t = now_s();
-            for (size_t j = 0; j < st.seg_req.size(); ++j)
-                if (!st.seg_seen[j]) segment_done(st, j, t);
-            st.seg_req.clear();
-            st.seg_seen.clear();
-            st.seg_begin.clear();
-            st.seg_item.clear();
-            st.busy = false;
-            if (v->live == si) v->live = -1;
-            v->inflight.erase(v->inflight.begin() + (long)i);
-        }
-        // admission of pending requests into free slots, in submission order; a request
-        // whose server-owned output does not fit the arena holds the ones behind it
-        while ((int)v->active.size() < v->max_inflight && !v->pending.empty()) {
-            SrvReq *r = v->pending.front();
-            if (r->out_bytes) {
-                char *o = v->arena.alloc(r->out_bytes);
-                if (!o) break;
-                r->r.d_rgbT = (float *)o;
-            }
-            v->pending.pop_front();
-            r->t_admit = now_s();
-            v->active.push_back(r);
-        }
-        // new work joins the live launch: the host publishes up to max_rays more items (in
-        // deadline order) whenever less than half of that is left unclaimed, so that a request
-        // that arrives waits for at most that much work of others. The launch's warps take it as
-        // they come free; warps without work wait until linger_ns pass without a publication.
-        // The host closes the live launch (its waiting warps stop, so that the next launch gets
-        // their SMs) when its segment table is full, when some of its warps have stopped
-        // waiting, or when it has run out of work and its last publication is half of
-        // linger_ns old (its warps might stop before an append lands); the next work starts a
-        // launch in a free slot.
-        if (v->live >= 0) {
-            SrvStep &st = v->steps[v->live];
-            const unsigned claimed = *reinterpret_cast<volatile unsigned *>(st.h_claimed);
-            const int64_t left = (int64_t)st.n_items - (int64_t)claimed;
-            if (*reinterpret_cast<volatile unsigned *>(st.h_exited) != 0) {
-                close_step(v, v->live);
-            } else if (has_unscheduled(v)) {
-                if (left <= 0 && v->append_guard && now_s() - st.t_pub >= 0.5e-9 * v->linger_ns)
-                    close_step(v, v->live);
-                else if (2 * left < v->max_rays && !append_to_step(v, v->live)) close_step(v, v->live);
-            }
-        }
-        if (v->live < 0 && (int)v->inflight.size() < v->n_steps && has_unscheduled(v)) {
-            int si = -1;
-            for (int i = 0; i < v->n_steps; ++i)
-                if (!v->steps[i].busy) { si = i; break; }
-            if (si >= 0) {
-                int st = schedule_step(v, si);
-                if (st != GRTX_OK) return st;
-            }
-        }
-        // (a live launch with nothing admitted is waiting for new requests, not running)
-        if (!wait || got > 0 || v->inflight.empty() || v->active.empty()) break;
-        timespec ts = {0, 20000};                 // wait for a flag or an ended launch
-        nanosleep(&ts, nullptr);
+    // segments finished inside running steps
+    double t = now_s();
+    for (int si : v->inflight) {
+        SrvStep &st = v->steps[si];
+        const volatile unsigned *flag = st.h_flag;
+        for (size_t j = 0; j < st.seg_req.size(); ++j)
+            if (!st.seg_seen[j] && flag[j] == st.seq) segment_done(st, j, t);
     }
+    // ended launches free their slots: untraced tiles go back to their requests, and
+    // every other segment of the launch is complete
+    for (size_t i = 0; i < v->inflight.size();) {
+        const int si = v->inflight[i];
+        SrvStep &st = v->steps[si];
+        cudaError_t q = cudaEventQuery(st.ev);
+        if (q == cudaErrorNotReady) {
+            ++i;
+            continue;
+        }
+        if (q != cudaSuccess) return grtx_cuda_fail(q, "serve step");
+        int rs = recover(st, si);
+        if (rs != GRTX_OK) return rs;
+        t = now_s();
+        for (size_t j = 0; j < st.seg_req.size(); ++j)
+            if (!st.seg_seen[j]) segment_done(st, j, t);
+        st.seg_req.clear();
+        st.seg_seen.clear();
+        st.seg_begin.clear();
+        st.seg_item.clear();
+        st.busy = false;
+        if (v->live == si) v->live = -1;
+        v->inflight.erase(v->inflight.begin() + (long)i);
+    }
+    // admission of pending requests into free slots, in submission order; a request
+    // whose server-owned output does not fit the arena holds the ones behind it
+    while ((int)v->active.size() < v->max_inflight && !v->pending.empty()) {
+        SrvReq *r = v->pending.front();
+        if (r->out_bytes) {
+            char *o = v->arena.alloc(r->out_bytes);
+            if (!o) break;
+            r->r.d_rgbT = (float *)o;
+        }
+        v->pending.pop_front();
+        r->t_admit = now_s();
+        v->active.push_back(r);
+    }
+    // new work joins the live launch: the host publishes up to max_rays more items (in
+    // deadline order) whenever less than half of that is left unclaimed, so that a request
+    // that arrives waits for at most that much work of others. The launch's warps take it as
+    // they come free and wait for more when there is none. The host closes the live launch
+    // (its waiting warps stop, so that the next launch gets their SMs) when no admitted
+    // request is left, when it has had no work for linger_ns, when its segment table is
+    // full, or when some of its warps have stopped waiting on their own (a host that did not
+    // poll for the warps' backstop); the next work starts a launch in a free slot. (Without
+    // the append guard the warps stop linger_ns after the last publication and the host
+    // appends all the same: appends then race with warps giving up, which tests use.)
+    if (v->live >= 0) {
+        SrvStep &st = v->steps[v->live];
+        // the mirror's writes come from many warps and may land out of order: keep the
+        // largest value read (a lower bound of the claims, so `left` errs high, which only
+        // delays the next publication)
+        const unsigned mirror = *reinterpret_cast<volatile unsigned *>(st.h_claimed);
+        st.claimed_max = std::max(st.claimed_max, mirror);
+        const int64_t left = (int64_t)st.n_items - (int64_t)st.claimed_max;
+        if (*reinterpret_cast<volatile unsigned *>(st.h_exited) != 0 || v->active.empty()) {
+            close_step(v, v->live);
+        } else if (has_unscheduled(v)) {
+            if (2 * left < v->max_rays && !append_to_step(v, v->live)) close_step(v, v->live);
+        } else if (left <= 0 && now_s() - st.t_pub >= 1e-9 * v->linger_ns) {
+            close_step(v, v->live);
+        }
+    }
+    if (v->live < 0 && (int)v->inflight.size() < v->n_steps && has_unscheduled(v)) {
+        int si = -1;
+        for (int i = 0; i < v->n_steps; ++i)
+            if (!v->steps[i].busy) { si = i; break; }
+        if (si >= 0) {
+            int st = schedule_step(v, si);
+            if (st != GRTX_OK) return st;
+        }
+    }
+    v->admit_blocked = !v->pending.empty();
+    return GRTX_OK;
+}
+
+// The scheduler thread: passes every 20 us while requests are queued, admitted or launches run;
+// otherwise it sleeps until a submit, a release or the server's end.
+void scheduler(grtx_server *v)
+{
+    cudaSetDevice(v->dev);
+    std::unique_lock<std::mutex> lk(v->mu);
+    while (!v->stop) {
+        const bool busy = !v->pending.empty() || !v->active.empty() || !v->inflight.empty();
+        if (v->err != GRTX_OK || !busy || (v->admit_blocked && v->active.empty() && v->inflight.empty())) {
+            v->cv_done.notify_all();
+            v->cv_work.wait_for(lk, std::chrono::milliseconds(50));
+            continue;
+        }
+        const size_t before = v->backlog.size();
+        const int st = advance(v);
+        if (st != GRTX_OK) {
+            v->err = st;
+            v->err_msg = grtx_last_error();
+        }
+        if (v->backlog.size() != before || st != GRTX_OK || v->active.empty()) v->cv_done.notify_all();
+        lk.unlock();
+        timespec ts = {0, 20000};
+        nanosleep(&ts, nullptr);
+        lk.lock();
+    }
+}
+
+}  // namespace
+
+extern "C" GRTX_API int grtx_server_poll(grtx_server *v, grtx_completion *done, int max_done, int *n_done, int wait)
+{
+    if (!v || !n_done || max_done < 0 || (max_done > 0 && !done)) return grtx_fail(GRTX_ERR_INVALID_ARG, "bad poll arguments");
+    *n_done = 0;
+    std::unique_lock<std::mutex> lk(v->mu);
+    // (with wait: until a completion, a failure, or nothing admitted that could complete)
+    auto ready = [&] {
+        return !v->backlog.empty() || v->err != GRTX_OK ||
+               (v->active.empty() && (v->pending.empty() || v->admit_blocked));
+    };
+    while (wait && !ready()) v->cv_done.wait_for(lk, std::chrono::milliseconds(1));
     while (*n_done < max_done && !v->backlog.empty()) {
         done[(*n_done)++] = v->backlog.front();
         v->backlog.pop_front();
     }
+    if (v->err != GRTX_OK && *n_done == 0) return grtx_fail(v->err, v->err_msg);
     return GRTX_OK;
 }
 
 extern "C" GRTX_API int grtx_render_requests(grtx_server *v, const grtx_request *reqs, int n, grtx_completion *done,
                                              int *n_done, void *stream)
 {
-    (void)stream;   // all server work runs on the server's stream
+    (void)stream;   // all server work runs on the server's streams
     if (!v || !n_done || (n > 0 && !done)) return grtx_fail(GRTX_ERR_INVALID_ARG, "bad arguments");
     int st = grtx_server_submit(v, reqs, n);
     if (st) return st;
@@ -759,19 +850,24 @@ extern "C" GRTX_API int grtx_render_requests(grtx_server *v, const grtx_request 
         st = grtx_server_poll(v, done + *n_done, n - *n_done, &got, 1);
         if (st) return st;
         *n_done += got;
-        if (got == 0 && v->inflight.empty() && v->active.empty() && v->backlog.empty()) {
-            if (!v->pending.empty())          // held until outputs are released, which cannot happen here
-                return grtx_fail(GRTX_ERR_BUSY, "requests are held: the output arena is full until outputs are released");
-            break;
+        if (got == 0) {
+            std::lock_guard<std::mutex> lk(v->mu);
+            if (v->active.empty() && v->backlog.empty()) {
+                if (!v->pending.empty())      // held until outputs are released, which cannot happen here
+                    return grtx_fail(GRTX_ERR_BUSY, "requests are held: the output arena is full until outputs are released");
+                break;
+            }
         }
     }
     return GRTX_OK;
 }
 
-extern "C" GRTX_API int grtx_server_load(const grtx_server *v, int *n_inflight, int *n_pending)
+extern "C" GRTX_API int grtx_server_load(const grtx_server *cv, int *n_inflight, int *n_pending)
 {
-    if (!v) return grtx_fail(GRTX_ERR_INVALID_ARG, "server is NULL");
-    if (n_inflight) *n_inflight = (int)v->active.size();
+    if (!cv) return grtx_fail(GRTX_ERR_INVALID_ARG, "server is NULL");
+    grtx_server *v = const_cast<grtx_server *>(cv);   // (the lock)
+    std::lock_guard<std::mutex> lk(v->mu);
+    if (n_inflight) *n_inflight = (int)(v->active.size() + v->backlog.size());
     if (n_pending) *n_pending = (int)v->pending.size();
     return GRTX_OK;
 }
@@ -779,7 +875,10 @@ extern "C" GRTX_API int grtx_server_load(const grtx_server *v, int *n_inflight, 
 extern "C" GRTX_API int grtx_server_release(grtx_server *v, float *d_rgbT)
 {
     if (!v) return grtx_fail(GRTX_ERR_INVALID_ARG, "server is NULL");
+    std::lock_guard<std::mutex> lk(v->mu);
     if (!v->arena.release((char *)d_rgbT)) return grtx_fail(GRTX_ERR_NOT_FOUND, "not a live server-owned output");
+    v->admit_blocked = false;
+    v->cv_work.notify_one();
     return GRTX_OK;
 }
 
@@ -787,6 +886,7 @@ extern "C" GRTX_API int grtx_server_set_linger(grtx_server *v, int64_t linger_ns
 {
     if (!v) return grtx_fail(GRTX_ERR_INVALID_ARG, "server is NULL");
     if (linger_ns < 0 || linger_ns > 1000000000) return grtx_fail(GRTX_ERR_INVALID_ARG, "linger_ns must be in [0, 1e9]");
+    std::lock_guard<std::mutex> lk(v->mu);
     v->linger_ns = (unsigned)linger_ns;
     return GRTX_OK;
 }
@@ -794,6 +894,7 @@ extern "C" GRTX_API int grtx_server_set_linger(grtx_server *v, int64_t linger_ns
 extern "C" GRTX_API int grtx_server_set_append_guard(grtx_server *v, int on)
 {
     if (!v) return grtx_fail(GRTX_ERR_INVALID_ARG, "server is NULL");
+    std::lock_guard<std::mutex> lk(v->mu);
     v->append_guard = on != 0;
     return GRTX_OK;
 }
@@ -802,20 +903,23 @@ extern "C" GRTX_API int grtx_server_set_order(grtx_server *v, double size_ns_per
 {
     if (!v) return grtx_fail(GRTX_ERR_INVALID_ARG, "server is NULL");
     if (!(size_ns_per_ray >= 0.0 && size_ns_per_ray <= 1e9)) return grtx_fail(GRTX_ERR_INVALID_ARG, "size_ns_per_ray must be in [0, 1e9]");
+    std::lock_guard<std::mutex> lk(v->mu);
     v->size_ns = size_ns_per_ray;
     return GRTX_OK;
 }
 
-extern "C" GRTX_API int grtx_server_get_info(const grtx_server *v, grtx_server_info *info)
+extern "C" GRTX_API int grtx_server_get_info(const grtx_server *cv, grtx_server_info *info)
 {
-    if (!v || !info) return grtx_fail(GRTX_ERR_INVALID_ARG, "NULL argument");
+    if (!cv || !info) return grtx_fail(GRTX_ERR_INVALID_ARG, "NULL argument");
+    grtx_server *v = const_cast<grtx_server *>(cv);   // (the lock)
+    std::lock_guard<std::mutex> lk(v->mu);
     info->n_step_slots = v->n_steps;
     info->blocks_per_step = v->blocks;
     info->list_bytes = (int64_t)v->list_bytes;
     info->arena_bytes = (int64_t)v->arena.bytes;
     info->arena_used = (int64_t)v->arena.used;
     info->device_bytes = (int64_t)v->device_bytes;
-    info->n_inflight = (int32_t)v->active.size();
+    info->n_inflight = (int32_t)(v->active.size() + v->backlog.size());
     info->n_pending = (int32_t)v->pending.size();
     info->n_launches = v->n_launches;
     info->n_appends = v->n_appends;
@@ -826,6 +930,12 @@ extern "C" GRTX_API int grtx_server_get_info(const grtx_server *v, grtx_server_i
 extern "C" GRTX_API void grtx_server_destroy(grtx_server *v)
 {
     if (!v) return;
+    {
+        std::lock_guard<std::mutex> lk(v->mu);
+        v->stop = true;
+    }
+    v->cv_work.notify_all();
+    if (v->worker.joinable()) v->worker.join();
     for (int si : v->inflight) close_step(v, si);
     server_free(v);
 }

@@ -118,24 +118,26 @@ def test_small_request_completes_before_the_large_one_in_its_step(world):
 
 
 def test_new_requests_join_the_running_launch(world):
-    """Requests submitted while a step launch still runs (or its warps wait for work) are
-    appended to that launch instead of starting another, and render the lone images."""
+    """Requests submitted while a step launch still runs are appended to that launch instead of
+    starting another, and render the lone images."""
     sc, reqs, alone = world
-    srv = Server(sc, k=16, max_rays_per_step=1 << 22, max_inflight=16, linger_us=200_000)
+    big_cam = scenes.pinhole_camera(1920, 1080, (0.0, 0.5, -3.0), (0.0, 0.0, 0.0), 60.0)
+    big_alone = R.render(sc[2], big_cam, k=16)["rgbT"].clone()
+    srv = Server(sc, k=16, max_inflight=16)
     bufs = _bufs(reqs)
-    srv.submit([(reqs[0]["scene"], reqs[0]["camera"], bufs[0], 0)])
-    got = []
-    while len(got) < 1:
-        got += srv.poll(wait=True)
-    # the launch's warps now wait (up to 200 ms) for more work
-    srv.submit([(r["scene"], r["camera"], b, 1 + i) for i, (r, b) in enumerate(zip(reqs[1:6], bufs[1:6]))])
+    big_buf = torch.full_like(big_alone, -1.0)
+    srv.submit([(2, big_cam, big_buf, 100)])
+    got = srv.poll()                               # starts the launch over the large view
+    # the launch is still tracing the large view (about a millisecond of work)
+    srv.submit([(r["scene"], r["camera"], b, i) for i, (r, b) in enumerate(zip(reqs[:5], bufs[:5]))])
     while len(got) < 6:
         got += srv.poll(wait=True)
     torch.cuda.synchronize()
     info = srv.info()
     assert info["n_launches"] == 1 and info["n_appends"] >= 1, info
-    assert sorted(d["tag"] for d in got) == list(range(6))
-    for j in range(6):
+    assert sorted(d["tag"] for d in got) == [0, 1, 2, 3, 4, 100]
+    _same(big_alone, big_buf)
+    for j in range(5):
         _same(alone[j], bufs[j])
     srv.close()
 
