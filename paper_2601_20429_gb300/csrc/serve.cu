@@ -24,7 +24,10 @@
 #include <thread>
 #include <vector>
 
+#include "serve_host.h"
 #include "trace_impl.cuh"
+
+using grtx_serve::Arena;
 
 #define GRTX_EXTERN_SERVE(K)                                                                                 \
     extern template int serve_launch<K>(const TraceArgs &, const ServeSeg *, const unsigned *, int, int,            \
@@ -92,60 +95,6 @@ struct SrvReq {
     std::vector<std::pair<unsigned, unsigned>> retry;   // {first item, count}: ranges a launch did not trace
 };
 
-// First-fit allocator over the output arena (offsets on the host, 256-byte granules).
-struct Arena {
-    char *base = nullptr;
-    size_t bytes = 0, used = 0;
-    std::map<size_t, size_t> free_;     // offset -> size, coalesced
-    std::map<size_t, size_t> live;      // offset -> size of outputs handed out
-    void reset(char *b, size_t n)
-    {
-        base = b;
-        bytes = n;
-        used = 0;
-        free_.clear();
-        live.clear();
-        if (n) free_[0] = n;
-    }
-    static size_t round(size_t n) { return (n + 255) / 256 * 256; }
-    char *alloc(size_t n)
-    {
-        n = round(n);
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second < n) continue;
-            size_t off = it->first, sz = it->second;
-            free_.erase(it);
-            if (sz > n) free_[off + n] = sz - n;
-            live[off] = n;
-            used += n;
-            return base + off;
-        }
-        return nullptr;
-    }
-    bool release(char *p)
-    {
-        if (!base || p < base || p >= base + bytes) return false;
-        auto it = live.find((size_t)(p - base));
-        if (it == live.end()) return false;
-        size_t off = it->first, n = it->second;
-        live.erase(it);
-        used -= n;
-        auto nx = free_.lower_bound(off);
-        if (nx != free_.end() && off + n == nx->first) {      // merge with the next free block
-            n += nx->second;
-            nx = free_.erase(nx);
-        }
-        if (nx != free_.begin()) {                              // and with the previous one
-            auto pv = std::prev(nx);
-            if (pv->first + pv->second == off) {
-                pv->second += n;
-                return true;
-            }
-        }
-        free_[off] = n;
-        return true;
-    }
-};
 
 // A step slot: each has its own stream, per-slot lists and queue counter, so that the next
 // launch's blocks take the SMs the previous launch's blocks leave while its slowest warps
@@ -264,45 +213,13 @@ void server_free(grtx_server *v)
     delete v;
 }
 
-struct Piece {
-    SrvReq *r;
-    unsigned begin, count;
-};
+using Piece = grtx_serve::Piece<SrvReq>;
 
-// Unscheduled work, up to `budget` items (a multiple of 32) and `max_pieces` pieces, request
-// by request in order of deadline: admission time plus size_ns per ray of the whole request
-// (0: admission order; large: smallest request first). A request's ranges that a launch did
-// not trace come first, then its next items.
+
+// Unscheduled work in deadline order (see grtx_serve::take_pieces).
 std::vector<Piece> take_pieces(grtx_server *v, int64_t budget, int max_pieces)
 {
-    std::vector<std::pair<double, SrvReq *>> order;
-    for (SrvReq *r : v->active) {
-        if (r->next >= r->n_items && r->retry.empty()) continue;
-        order.push_back({r->t_admit + 1e-9 * v->size_ns * (double)r->n_items, r});
-    }
-    std::stable_sort(order.begin(), order.end(),
-                     [](const std::pair<double, SrvReq *> &x, const std::pair<double, SrvReq *> &y) {
-                         return x.first < y.first;
-                     });
-    std::vector<Piece> pieces;
-    for (const auto &o : order) {
-        SrvReq *r = o.second;
-        while (!r->retry.empty() && budget > 0 && (int)pieces.size() < max_pieces) {
-            auto &rg = r->retry.back();
-            const unsigned take = (unsigned)std::min<int64_t>(rg.second, budget);
-            pieces.push_back({r, rg.first, take});
-            rg.first += take;
-            rg.second -= take;
-            if (rg.second == 0) r->retry.pop_back();
-            budget -= take;
-        }
-        if (r->next >= r->n_items || budget <= 0 || (int)pieces.size() >= max_pieces) continue;
-        unsigned take = (unsigned)std::min<int64_t>((int64_t)(r->n_items - r->next), budget);
-        pieces.push_back({r, r->next, take});
-        r->next += take;
-        budget -= take;
-    }
-    return pieces;
+    return grtx_serve::take_pieces<SrvReq>(v->active, v->size_ns, budget, max_pieces);
 }
 
 // Segment records (and begins entries) of `pieces`, after the launch's current segments and
@@ -693,16 +610,7 @@ int advance(grtx_server *v)
                 if (b < st.n_items) add(b);
         }
         for (unsigned b = q / 32 * 32; b < st.n_items; b += 32) add(b);
-        std::sort(tiles.begin(), tiles.end());
-        v->n_retried += (int64_t)tiles.size();
-        for (size_t i = 0; i < tiles.size();) {
-            size_t e = i + 1;
-            while (e < tiles.size() && tiles[e].first == tiles[i].first &&
-                   tiles[e].second == tiles[e - 1].second + 32)
-                ++e;
-            tiles[i].first->retry.push_back({tiles[i].second, (unsigned)(32 * (e - i))});
-            i = e;
-        }
+        v->n_retried += (int64_t)grtx_serve::give_back_tiles(tiles);
         return GRTX_OK;
     };
     // segments finished inside running steps

@@ -37,7 +37,8 @@ def _sources():
 
 
 def _deps():
-    return _sources() + glob.glob(os.path.join(_CSRC, "*.cuh")) + glob.glob(os.path.join(_INCLUDE, "*.h"))
+    return (_sources() + glob.glob(os.path.join(_CSRC, "*.cuh")) + glob.glob(os.path.join(_CSRC, "*.h")) +
+            glob.glob(os.path.join(_INCLUDE, "*.h")))
 
 
 def needs_build() -> bool:
