@@ -3,12 +3,28 @@ include/grtx.h). Argument marshalling only: admission, step scheduling and compl
 tracking run in the library."""
 from __future__ import annotations
 
+import atexit
 import ctypes as C
+import weakref
 
 import torch
 
 from . import native as N
 from .render import Scene, trace_params
+
+
+# servers still open when the interpreter exits are closed first (each runs a native scheduler
+# thread, which must stop before the CUDA runtime is torn down)
+_open_servers: "weakref.WeakSet[Server]" = weakref.WeakSet()
+
+
+@atexit.register
+def _close_open_servers():
+    for srv in list(_open_servers):
+        try:
+            srv.close()
+        except Exception:
+            pass
 
 
 class Server:
@@ -26,6 +42,7 @@ class Server:
                                            C.c_void_p(self.stream.cuda_stream), C.byref(out)),
                 "grtx_server_create")
         self.handle = out.value
+        _open_servers.add(self)
         if linger_us is not None:
             N.check(N.lib().grtx_server_set_linger(C.c_void_p(self.handle), int(round(linger_us * 1000))),
                     "grtx_server_set_linger")
