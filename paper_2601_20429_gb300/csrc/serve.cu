@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -365,6 +366,25 @@ bool has_unscheduled(const grtx_server *v)
 
 namespace {
 void scheduler(grtx_server *v);
+
+// Servers whose scheduler threads run: a process that exits without grtx_server_destroy stops
+// them first (an exit handler registered after the CUDA runtime's own, so it runs before them).
+std::mutex g_servers_mu;
+std::vector<grtx_server *> g_servers;
+
+void stop_servers_at_exit()
+{
+    std::lock_guard<std::mutex> g(g_servers_mu);
+    for (grtx_server *v : g_servers) {
+        {
+            std::lock_guard<std::mutex> lk(v->mu);
+            v->stop = true;
+        }
+        v->cv_work.notify_all();
+        if (v->worker.joinable()) v->worker.join();
+    }
+    g_servers.clear();
+}
 }
 
 extern "C" GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scenes, const grtx_params *p,
@@ -509,6 +529,12 @@ extern "C" GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scen
     } catch (...) {
         server_free(v);
         return grtx_fail(GRTX_ERR_OOM, "could not start the server's scheduler thread");
+    }
+    {
+        static std::once_flag registered;
+        std::call_once(registered, [] { std::atexit(stop_servers_at_exit); });
+        std::lock_guard<std::mutex> g(g_servers_mu);
+        g_servers.push_back(v);
     }
     *out = v;
     return GRTX_OK;
@@ -838,6 +864,10 @@ extern "C" GRTX_API int grtx_server_get_info(const grtx_server *cv, grtx_server_
 extern "C" GRTX_API void grtx_server_destroy(grtx_server *v)
 {
     if (!v) return;
+    {
+        std::lock_guard<std::mutex> g(g_servers_mu);
+        g_servers.erase(std::remove(g_servers.begin(), g_servers.end(), v), g_servers.end());
+    }
     {
         std::lock_guard<std::mutex> lk(v->mu);
         v->stop = true;
