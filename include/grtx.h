@@ -690,7 +690,7 @@ typedef struct grtx_completion {
  * checkpoint/eviction lists, so that a new launch fills the SMs the finishing launch's last
  * warps leave (a third slot gave the same latency and throughput; a single slot makes each
  * new launch wait for the previous one to end). One step slot's lists take (resident ray
- * slots) x (2 ckpt_capacity + evict_capacity) x 8 bytes: about 1.2 GB with the default
+ * slots) x (2 ckpt_capacity + evict_capacity) x 8 bytes: 1.27 GB with the default
  * capacities at full residency on 152 SMs.
  *   - mem_budget_bytes = 0: no cap. 2 step slots at full residency; requests must bring their
  *     own output (d_rgbT = NULL is rejected with GRTX_ERR_INVALID_ARG).
