@@ -422,14 +422,15 @@ def traversal_modes_on_views(gpu_scenes, reqs, per_scene: int = 20) -> dict:
     return res
 
 
-def run_stream(srv, reqs, rate_hz: float) -> dict:
+def run_stream(srv, reqs, rate_hz: float, device: str = "cuda") -> dict:
     """Replay a request stream against a server in real time: each request is submitted at its
     arrival time (or as soon as an output buffer is free), completions are polled without
-    blocking. Latency = completion - arrival."""
+    blocking. Latency = completion - arrival (the server's completion times are CLOCK_MONOTONIC
+    seconds, as time.monotonic())."""
     import torch
-    max_px = 1920 * 1080
+    max_px = max(r["camera"]["width"] * r["camera"]["height"] for r in reqs)
     n_buffers = min(80, max(16, len(reqs) // 4))          # output buffers in flight
-    pool = deque(torch.empty((max_px, 4), dtype=torch.float32, device="cuda") for _ in range(n_buffers))
+    pool = deque(torch.empty((max_px, 4), dtype=torch.float32, device=device) for _ in range(n_buffers))
     n = len(reqs)
     lat = [None] * n
     busy = {}

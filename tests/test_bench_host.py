@@ -1,6 +1,7 @@
 """Host-side helpers of bench.py: figures read from an ncu summary only while the kernel
-source hash recorded beside them matches, and the clock record taken during the timed
-region (median SM clock, throttle reasons). CPU only."""
+source hash recorded beside them matches, the clock record taken during the timed region
+(median SM clock, throttle reasons), and the replay of a request stream against a server
+(latency, per-size buckets, rates; a fake server here). CPU only."""
 import os
 
 import pytest
@@ -74,3 +75,46 @@ def test_clock_record_reports_each_slowdown(tmp_path, reason_col, name):
 def test_clock_record_without_samples(tmp_path):
     assert _sampler(tmp_path, []).stop()["reasons"] == ["no samples"]
     assert bench.ClockSampler(0).stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+class _FakeServer:
+    """Completes every request a fixed service time after its submission (CLOCK_MONOTONIC)."""
+
+    def __init__(self, service_s):
+        import time
+        self.time = time
+        self.service = service_s
+        self.inflight = []
+
+    def submit(self, batch):
+        t = self.time.monotonic()
+        for sid, cam, buf, tag in batch:
+            assert buf.numel() >= cam["width"] * cam["height"] * 4
+            self.inflight.append((t + self.service, tag))
+
+    def poll(self, wait=False):
+        now = self.time.monotonic()
+        done = [dict(tag=tag, status=0, t_admit=t - self.service, t_done=t) for t, tag in self.inflight if t <= now]
+        self.inflight = [(t, tag) for t, tag in self.inflight if t > now]
+        return done
+
+
+def test_request_stream_replay_latency_and_buckets():
+    """The serving benchmark's replay: every request completes once, latency is completion -
+    arrival (here the fake server's 3 ms service plus polling granularity), per-size buckets
+    cover the sizes in the stream, and the rate is rays over the makespan."""
+    import numpy as np
+    reqs = []
+    sizes = [(64, 64), (128, 96)]
+    for j in range(60):
+        w, h = sizes[j % 2]
+        reqs.append(dict(scene=0, camera=dict(width=w, height=h), arrival=0.001 * j))
+    res = bench.run_stream(_FakeServer(0.003), reqs, 1000.0, device="cpu")
+    assert res["requests"] == 60
+    assert 3.0 <= res["p50_ms"] <= 6.0 and res["p99_ms"] < 20.0
+    assert sorted(res["latency_by_pixels"]) == sorted(str(w * h) for w, h in sizes)
+    assert all(v["n"] == 30 for v in res["latency_by_pixels"].values())
+    rays = sum(r["camera"]["width"] * r["camera"]["height"] for r in reqs)
+    assert abs(res["Mrays_per_s"] - rays / res["makespan_s"] / 1e6) < 1e-9
+    assert 0.059 <= res["makespan_s"] < 0.2
+    assert np.isclose(res["offered_Mrays_per_s"], rays / 0.059 / 1e6)
