@@ -419,28 +419,18 @@ extern "C" GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scen
     if ((size_t)blocks_full * 128 * (2 * C + E) >= ((size_t)1 << 31))
         return grtx_fail(GRTX_ERR_INVALID_ARG, "checkpoint/eviction capacities too large for the resident ray slots");
     // segment tables, completion counts, publication words and given-up claims of each slot
-    auto tables_for = [&](int steps, int nblocks) {
-        return kSteps * kQueueStride * sizeof(unsigned) +
-               (size_t)steps * ((sizeof(ServeSeg) + 2 * sizeof(unsigned)) * seg_cap +
-                                sizeof(unsigned) * (4 + (size_t)nblocks * (kBlock / 32)));
-    };
-    int n_steps = kSteps, blocks = blocks_full;
-    size_t arena = 0;
-    if (mem_budget_bytes > 0) {
-        const size_t budget = (size_t)mem_budget_bytes;
-        const size_t list_cap = budget / 2;
-        const size_t full_step = (size_t)blocks_full * per_block;
-        n_steps = (int)std::min<size_t>(kSteps, std::max<size_t>(1, list_cap / full_step));
-        blocks = (int)std::min<size_t>((size_t)blocks_full, list_cap / ((size_t)n_steps * per_block));
-        if (blocks < 1)
-            return grtx_fail(GRTX_ERR_INVALID_ARG, "memory budget of " + std::to_string(budget) +
-                                                       " bytes is below twice one block of lists (" +
-                                                       std::to_string(per_block) + " bytes)");
-        size_t lists = (size_t)n_steps * blocks * per_block;
-        const size_t tables = tables_for(n_steps, blocks);
-        if (lists + tables > budget) return grtx_fail(GRTX_ERR_INVALID_ARG, "memory budget too small");
-        arena = (budget - lists - tables) / 256 * 256;
-    }
+    // (the tables: queue counters, and per slot the segment records, begins and completion
+    // counts, four control words, and one given-up claim per warp)
+    const grtx_serve::BudgetPlan plan = grtx_serve::plan_budget(
+        (size_t)mem_budget_bytes, kSteps, blocks_full, per_block, kSteps * kQueueStride * sizeof(unsigned),
+        (sizeof(ServeSeg) + 2 * sizeof(unsigned)) * seg_cap + 4 * sizeof(unsigned), sizeof(unsigned) * (kBlock / 32));
+    if (plan.below_one_block)
+        return grtx_fail(GRTX_ERR_INVALID_ARG, "memory budget of " + std::to_string(mem_budget_bytes) +
+                                                   " bytes is below twice one block of lists (" +
+                                                   std::to_string(per_block) + " bytes)");
+    if (!plan.fits) return grtx_fail(GRTX_ERR_INVALID_ARG, "memory budget too small");
+    const int n_steps = plan.n_steps, blocks = plan.blocks;
+    const size_t arena = plan.arena;
     grtx_server *v = new (std::nothrow) grtx_server();
     if (!v) return grtx_fail(GRTX_ERR_OOM, "host allocation failed");
     v->scenes.assign(scenes, scenes + n_scenes);
@@ -521,7 +511,7 @@ extern "C" GRTX_API int grtx_server_create(grtx_scene *const *scenes, int n_scen
     }
     v->arena.reset(arena_base, arena);
     v->list_bytes = (size_t)n_steps * ws;
-    v->device_bytes = v->list_bytes + arena + tables_for(n_steps, blocks);
+    v->device_bytes = v->list_bytes + arena + plan.tables;
     a.n_slots = n_slots;
     cudaGetDevice(&v->dev);
     try {

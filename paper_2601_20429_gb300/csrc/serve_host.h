@@ -1,6 +1,6 @@
 // Host-only scheduling logic of the request server (no CUDA types, so that it is also built and
-// tested on its own): the first-fit output arena, the choice of the work published next, and
-// the regrouping of untraced tiles into ranges.
+// tested on its own): the first-fit output arena, the choice of the work published next, the
+// regrouping of untraced tiles into ranges, and the division of a memory budget.
 #pragma once
 
 #include <stddef.h>
@@ -130,6 +130,49 @@ size_t give_back_tiles(std::vector<std::pair<Req *, unsigned>> &tiles)
         i = e;
     }
     return tiles.size();
+}
+
+// Device memory of a server under a budget (0: none). The step slots' lists take at most half
+// of the budget: as many full-residency slots as fit (1 to max_steps), else one slot of as
+// many 128-ray blocks as fit; the small tables (table_fixed + per slot table_per_step +
+// table_per_block per block) come next, and the rest, in 256-byte granules, is the output
+// arena. fits is false when not even one block of lists fits in half the budget
+// (below_one_block) or the lists and tables exceed it.
+struct BudgetPlan {
+    int n_steps = 0, blocks = 0;
+    size_t lists = 0, tables = 0, arena = 0;
+    bool fits = false, below_one_block = false;
+};
+
+inline BudgetPlan plan_budget(size_t budget, int max_steps, int blocks_full, size_t per_block, size_t table_fixed,
+                              size_t table_per_step, size_t table_per_block)
+{
+    BudgetPlan pl;
+    auto tables = [&](int steps, int blocks) {
+        return table_fixed + (size_t)steps * (table_per_step + table_per_block * (size_t)blocks);
+    };
+    if (budget == 0) {
+        pl.n_steps = max_steps;
+        pl.blocks = blocks_full;
+        pl.lists = (size_t)max_steps * blocks_full * per_block;
+        pl.tables = tables(max_steps, blocks_full);
+        pl.fits = true;
+        return pl;
+    }
+    const size_t list_cap = budget / 2;
+    const size_t full_step = (size_t)blocks_full * per_block;
+    pl.n_steps = (int)std::min<size_t>((size_t)max_steps, std::max<size_t>(1, list_cap / full_step));
+    pl.blocks = (int)std::min<size_t>((size_t)blocks_full, list_cap / ((size_t)pl.n_steps * per_block));
+    if (pl.blocks < 1) {
+        pl.below_one_block = true;
+        return pl;
+    }
+    pl.lists = (size_t)pl.n_steps * pl.blocks * per_block;
+    pl.tables = tables(pl.n_steps, pl.blocks);
+    if (pl.lists + pl.tables > budget) return pl;
+    pl.arena = (budget - pl.lists - pl.tables) / 256 * 256;
+    pl.fits = true;
+    return pl;
 }
 
 }  // namespace grtx_serve

@@ -1,7 +1,8 @@
 """The request server's host-only scheduling logic (csrc/serve_host.h), built with the host C++
 compiler and run on the CPU: the deadline order of the work published next, budgets and
 piece counts, ranges a launch did not trace going first, the regrouping of untraced tiles into
-ranges, and the first-fit output arena with coalescing."""
+ranges, the first-fit output arena with coalescing, and the division of a memory budget into
+step slots, tables and the arena."""
 import os
 import shutil
 import subprocess
@@ -114,6 +115,31 @@ int main()
         CHECK(ar.release(w) && ar.release(x) && ar.release(z) && ar.used == 0);
         CHECK(ar.free_.size() == 1 && ar.free_.begin()->first == 0 && ar.free_.begin()->second == 4096);
         CHECK(ar.alloc(4096) == mem && ar.alloc(1) == nullptr);
+    }
+    // budget plans: 64 KiB blocks of lists, 1216 blocks a full slot, up to 2 slots
+    {
+        const size_t blk = 65536, fixed = 256, per_step = 264 * 32 + 16, per_blk = 16;
+        BudgetPlan none = plan_budget(0, 2, 1216, blk, fixed, per_step, per_blk);
+        CHECK(none.fits && none.n_steps == 2 && none.blocks == 1216 && none.arena == 0);
+        CHECK(none.lists == 2 * 1216 * blk);
+        // one block of lists (its half holds one block, not two) and one 64 KiB output
+        const size_t b1 = blk + 65536 + 16384;
+        BudgetPlan p1 = plan_budget(b1, 2, 1216, blk, fixed, per_step, per_blk);
+        CHECK(p1.fits && p1.n_steps == 1 && p1.blocks == 1 && p1.lists == blk);
+        CHECK(p1.tables == fixed + per_step + per_blk && p1.arena % 256 == 0);
+        CHECK(p1.arena >= 65536 && p1.arena < 2 * 65536 && p1.lists + p1.tables + p1.arena <= b1);
+        // half the budget holds one full slot but not two: one full slot
+        BudgetPlan pf = plan_budget(3 * 1216 * blk, 2, 1216, blk, fixed, per_step, per_blk);
+        CHECK(pf.fits && pf.n_steps == 1 && pf.blocks == 1216);
+        // room for two full slots
+        BudgetPlan p2 = plan_budget(5 * 1216 * blk, 2, 1216, blk, fixed, per_step, per_blk);
+        CHECK(p2.fits && p2.n_steps == 2 && p2.blocks == 1216 && p2.lists + p2.tables + p2.arena <= 5 * 1216 * blk);
+        // below one block in half the budget
+        BudgetPlan pb = plan_budget(blk, 2, 1216, blk, fixed, per_step, per_blk);
+        CHECK(!pb.fits && pb.below_one_block);
+        // lists fit in half but the tables do not fit beside them
+        BudgetPlan pt = plan_budget(2 * blk, 2, 1216, blk, fixed, 2 * blk, per_blk);
+        CHECK(!pt.fits && !pt.below_one_block);
     }
     if (failures) return 1;
     std::printf("ok\n");
